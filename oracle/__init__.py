@@ -1,0 +1,232 @@
+"""CPU oracle for Picasso (arXiv 2401.06713) -- TEST INFRASTRUCTURE ONLY.
+
+Plain C (``picasso_oracle.c``) behind ctypes.  Only ``tests/``, the smoke check
+in ``__graft_entry__`` and the CPU-baseline leg of ``bench.py`` may import this
+package.  It shares no code with the CUDA library: the Pauli predicate uses
+the paper's 3-bit code (Sec. III-A), Philox4x32-10 and Floyd's sampling are
+written out again from their published definitions.
+
+Function map (paper passage each follows):
+  philox4x32_10     Salmon et al., SC'11 (the counter-based generator)
+  draw_list         Alg. 1 assign_rand_list_colors, Floyd's sampling
+  priority          static Random order of Sec. III-B
+  commute_chars     Sec. III-A, character comparison (anticommute iff odd count)
+  encode3/commute3  Sec. III-A, inverse one-hot code + AND + popcount parity
+  conflict_*        Alg. 1 construct_conflict_graph (color-major rows)
+  color_greedy      Sec. III-B static order, first available list color
+  round_params      Table I / Sec. VI parameter rule
+  run               Alg. 1, all rounds
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "picasso_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+TAG_LIST = 1
+TAG_PRIO = 2
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", _SRC, "-o", _LIB, "-lm"]
+        )
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.orc_draw_u32.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                   ctypes.c_uint32]
+        L.orc_draw_u32.restype = ctypes.c_uint32
+        L.orc_priority.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64]
+        L.orc_priority.restype = ctypes.c_uint32
+        L.orc_draw_list.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int32, ctypes.c_int64, _i64p]
+        L.orc_commute_chars.argtypes = [_u8p, _u8p, ctypes.c_int32]
+        L.orc_commute_chars.restype = ctypes.c_int
+        L.orc_words3.argtypes = [ctypes.c_int32]
+        L.orc_words3.restype = ctypes.c_int32
+        L.orc_encode3.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, _u32p]
+        L.orc_commute3.argtypes = [_u32p, _u32p, ctypes.c_int32]
+        L.orc_commute3.restype = ctypes.c_int
+        L.orc_min_shared.argtypes = [_i64p, _i64p, ctypes.c_int32]
+        L.orc_min_shared.restype = ctypes.c_int64
+        L.orc_conflict_rows.argtypes = [ctypes.c_int64, _u32p, ctypes.c_int32, _i64p, ctypes.c_int32, _i64p,
+                                        ctypes.c_int64, _i64p, _i64p, _i32p, ctypes.c_int32]
+        L.orc_conflict_nnz.argtypes = [ctypes.c_int64, _u32p, ctypes.c_int32, _i64p, ctypes.c_int32, _i64p,
+                                       ctypes.c_int32]
+        L.orc_conflict_nnz.restype = ctypes.c_int64
+        L.orc_conflict_fill.argtypes = [ctypes.c_int64, _u32p, ctypes.c_int32, _i64p, ctypes.c_int32, _i64p,
+                                        _i64p, _i32p, ctypes.c_int32]
+        L.orc_color_greedy.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, _i64p, _i64p,
+                                       ctypes.c_int32, _i64p, _i32p, ctypes.c_int64, ctypes.c_int64, _i64p]
+        L.orc_color_greedy.restype = ctypes.c_int64
+        L.orc_round_params.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                       _i64p, _i32p]
+        L.orc_run.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
+                              ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _i64p, _i64p]
+        L.orc_run.restype = ctypes.c_int32
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c, _u32p), _p(k, _u32p), _p(out, _u32p))
+    return out
+
+
+def draw_u32(seed: int, rnd: int, gid: int, tag: int, i: int) -> int:
+    return int(lib().orc_draw_u32(seed, rnd, gid, tag, i))
+
+
+def priority(seed: int, rnd: int, gid: int) -> int:
+    return int(lib().orc_priority(seed, rnd, gid))
+
+
+def priorities(seed: int, rnd: int, gids) -> np.ndarray:
+    return np.array([priority(seed, rnd, int(g)) for g in gids], dtype=np.uint32)
+
+
+def draw_list(seed: int, rnd: int, gid: int, P: int, L: int, base: int = 0) -> np.ndarray:
+    out = np.zeros(max(L, 1), dtype=np.int64)
+    lib().orc_draw_list(seed, rnd, gid, P, L, base, _p(out, _i64p))
+    return out[:L]
+
+
+def draw_lists(seed: int, rnd: int, gids, P: int, L: int, base: int = 0) -> np.ndarray:
+    gids = np.asarray(gids, dtype=np.int64)
+    out = np.zeros((len(gids), L), dtype=np.int64)
+    for i, g in enumerate(gids):
+        out[i] = draw_list(seed, rnd, int(g), P, L, base)
+    return out
+
+
+def commute_chars(a, b) -> bool:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint8))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.uint8))
+    return bool(lib().orc_commute_chars(_p(a, _u8p), _p(b, _u8p), len(a)))
+
+
+def encode3(chars: np.ndarray) -> np.ndarray:
+    chars = np.ascontiguousarray(chars, dtype=np.uint8)
+    n, q = chars.shape
+    w3 = int(lib().orc_words3(q))
+    enc = np.zeros((n, w3), dtype=np.uint32)
+    lib().orc_encode3(_p(chars, _u8p), n, q, _p(enc, _u32p))
+    return enc
+
+
+def commute3(ea, eb) -> bool:
+    ea = np.ascontiguousarray(ea, dtype=np.uint32)
+    eb = np.ascontiguousarray(eb, dtype=np.uint32)
+    return bool(lib().orc_commute3(_p(ea, _u32p), _p(eb, _u32p), len(ea)))
+
+
+def min_shared(a, b) -> int:
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    b = np.ascontiguousarray(b, dtype=np.int64)
+    return int(lib().orc_min_shared(_p(a, _i64p), _p(b, _i64p), len(a)))
+
+
+def round_params(n: int, num: int, den: int, alpha: float):
+    P = ctypes.c_int64()
+    L = ctypes.c_int32()
+    lib().orc_round_params(n, num, den, alpha, ctypes.byref(P), ctypes.byref(L))
+    return int(P.value), int(L.value)
+
+
+def conflict_csr(enc: np.ndarray, lists: np.ndarray, threads: int | None = None):
+    """Whole conflict CSR (off int64 [n+1], col int32) of one round."""
+    enc = np.ascontiguousarray(enc, dtype=np.uint32)
+    lists = np.ascontiguousarray(lists, dtype=np.int64)
+    n, w3 = enc.shape
+    L = lists.shape[1]
+    threads = threads or default_threads()
+    lens = np.zeros(n + 1, dtype=np.int64)
+    nnz = lib().orc_conflict_nnz(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(lens, _i64p), threads)
+    off = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(max(nnz, 1), dtype=np.int32)
+    lib().orc_conflict_fill(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(lens, _i64p), _p(off, _i64p),
+                            _p(col, _i32p), threads)
+    return off, col[:nnz]
+
+
+def conflict_rows(enc: np.ndarray, lists: np.ndarray, rows, threads: int | None = None):
+    """Selected rows: returns (lens int64 [m], list of int32 arrays)."""
+    enc = np.ascontiguousarray(enc, dtype=np.uint32)
+    lists = np.ascontiguousarray(lists, dtype=np.int64)
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    n, w3 = enc.shape
+    L = lists.shape[1]
+    m = len(rows)
+    threads = threads or default_threads()
+    lens = np.zeros(m + 1, dtype=np.int64)
+    lib().orc_conflict_rows(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(rows, _i64p), m, _p(lens, _i64p),
+                            None, None, threads)
+    off = np.zeros(m + 1, dtype=np.int64)
+    off[1:] = np.cumsum(lens[:m])
+    col = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
+    lib().orc_conflict_rows(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(rows, _i64p), m, None,
+                            _p(off, _i64p), _p(col, _i32p), threads)
+    return lens[:m], [col[off[i]:off[i + 1]].copy() for i in range(m)]
+
+
+def color_greedy(seed: int, rnd: int, gids, lists, off, col, P: int, base: int) -> np.ndarray:
+    gids = np.ascontiguousarray(np.asarray(gids, dtype=np.int64))
+    lists = np.ascontiguousarray(lists, dtype=np.int64)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = len(gids)
+    L = lists.shape[1] if lists.ndim == 2 else 0
+    out = np.zeros(max(n, 1), dtype=np.int64)
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.int32)
+    lib().orc_color_greedy(seed, rnd, n, _p(gids, _i64p), _p(lists, _i64p), L, _p(off, _i64p), _p(col, _i32p),
+                           P, base, _p(out, _i64p))
+    return out[:n]
+
+
+def run(chars: np.ndarray, seed: int, num: int, den: int, alpha: float, max_rounds: int = 4096,
+        threads: int | None = None):
+    """Alg. 1 end to end.  Returns (color int64 [N], rounds, stats [rounds][6])
+    with stats columns (n, P, L, base, nnz, colored)."""
+    chars = np.ascontiguousarray(chars, dtype=np.uint8)
+    N, q = chars.shape
+    color = np.zeros(max(N, 1), dtype=np.int64)
+    stats = np.zeros((max_rounds, 6), dtype=np.int64)
+    r = lib().orc_run(_p(chars, _u8p), N, q, seed, num, den, alpha, max_rounds, threads or default_threads(),
+                      _p(color, _i64p), _p(stats, _i64p))
+    if r < 0:
+        raise RuntimeError("oracle run hit max_rounds")
+    return color[:N], int(r), stats[:r].copy()

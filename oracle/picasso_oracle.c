@@ -1,0 +1,458 @@
+/*
+ * picasso_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct CPU statement of one Picasso round and of
+ * the whole iterative algorithm (Ferdous et al., "Picasso: Memory-Efficient
+ * Graph Coloring Using Palettes With Applications in Quantum Computing",
+ * arXiv 2401.06713).  Only the test-suite, the smoke check and the timed CPU
+ * baseline of the benchmark may load this library.  The product (the CUDA
+ * library) never links, calls or reads anything here, and nothing here is
+ * shared with it: the Pauli predicate uses the paper's 3-bit code instead of
+ * the product's symplectic words, and Philox / Floyd are written out again.
+ *
+ * Every function follows a passage of the paper (section / algorithm /
+ * equation given beside it) or a published definition it relies on.  There
+ * is no blocking, fusion or reordering beyond what those definitions state;
+ * threads are used only over independent rows of the conflict graph.
+ *
+ * Readings where the paper is silent (they bind product and oracle alike):
+ *   - the colored graph is the complement G' of the anticommutation graph:
+ *     u != v are adjacent iff they commute (Sec. II, Def. 1 and the complement
+ *     construction; Sec. III-A "in our case, a non-edge");
+ *   - P_l = max(1, ceil(n_l * num / den)), L_l = min(P_l, max(1,
+ *     ceil(alpha * ln n_l))) (Table I: P a fraction of |V|, L = alpha log|V|);
+ *   - palette of round l is [base_l, base_l + P_l), base_l = sum of earlier
+ *     P (Alg. 1 text: colors of a round are never reused later);
+ *   - a list is L distinct colors drawn uniformly (Floyd's sampling), sorted;
+ *   - conflict coloring is the static Random order of Sec. III-B with
+ *     first-fit: vertices in ascending (priority, global id) order take the
+ *     smallest list color not used by an already-colored conflict neighbour;
+ *     unconflicted vertices therefore get their smallest list color;
+ *   - conflict rows are stored "color-major": row u lists, for each color c
+ *     of u's list in ascending order, the neighbours v whose smallest shared
+ *     color with u is c, in ascending v.  Every edge appears once per
+ *     direction.
+ *
+ * Parity pins (what fixes this file against something other than itself) are
+ * in the test-suite: Philox known-answer vectors, the 16-entry Pauli truth
+ * table, the complete-4^q degree invariant, brute force over character
+ * strings, exact Floyd distributions and the closed-form conflict count.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TAG_LIST 1u
+#define ORC_TAG_PRIO 2u
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, J. Salmon, M. Moraes, R. Dror, D. Shaw, "Parallel Random   */
+/* Numbers: As Easy as 1, 2, 3", SC'11: ten rounds of two 32x32->64 bit      */
+/* multiplies; the key is bumped by the Weyl constants between rounds.       */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                       uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* The i-th 32-bit draw of stream (seed, round, gid, tag): counter word 0/1 =
+ * gid, word 2 = round, word 3 = tag << 24 | block, block = i / 4.           */
+static uint32_t orc_draw(uint64_t seed, int32_t round, int64_t gid,
+                         uint32_t tag, uint32_t i) {
+  uint32_t ctr[4], key[2], out[4];
+  ctr[0] = (uint32_t)((uint64_t)gid & 0xffffffffu);
+  ctr[1] = (uint32_t)((uint64_t)gid >> 32);
+  ctr[2] = (uint32_t)round;
+  ctr[3] = (tag << 24) | (i / 4u);
+  key[0] = (uint32_t)(seed & 0xffffffffu);
+  key[1] = (uint32_t)(seed >> 32);
+  orc_philox4x32_10(ctr, key, out);
+  return out[i % 4u];
+}
+
+uint32_t orc_draw_u32(uint64_t seed, int32_t round, int64_t gid, uint32_t tag,
+                      uint32_t i) {
+  return orc_draw(seed, round, gid, tag, i);
+}
+
+/* Priority of a vertex in round l: first draw of its PRIO stream.  The
+ * coloring order is ascending (priority, gid).                             */
+uint32_t orc_priority(uint64_t seed, int32_t round, int64_t gid) {
+  return orc_draw(seed, round, gid, ORC_TAG_PRIO, 0u);
+}
+
+static int cmp_i64(const void* a, const void* b) {
+  int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+  return (x > y) - (x < y);
+}
+
+/* Alg. 1 assign_rand_list_colors for one vertex: L distinct colors drawn
+ * uniformly from the round palette.  Floyd's sampling (J. Bentley, R. Floyd,
+ * "A sample of brilliance", CACM 1987): for j = P-L .. P-1 draw t uniform in
+ * [0, j]; keep t unless already kept, in which case keep j.  A draw x maps to
+ * [0, j] as floor(x * (j+1) / 2^32).  The list is returned sorted and
+ * shifted by base.                                                          */
+void orc_draw_list(uint64_t seed, int32_t round, int64_t gid, int64_t P,
+                   int32_t L, int64_t base, int64_t* out) {
+  int32_t m = 0;
+  for (int64_t j = P - L; j < P; ++j) {
+    uint32_t x = orc_draw(seed, round, gid, ORC_TAG_LIST, (uint32_t)m);
+    int64_t t = (int64_t)(((uint64_t)x * (uint64_t)(j + 1)) >> 32);
+    int seen = 0;
+    for (int32_t a = 0; a < m; ++a)
+      if (out[a] == t) seen = 1;
+    out[m++] = seen ? j : t;
+  }
+  qsort(out, (size_t)L, sizeof(int64_t), cmp_i64);
+  for (int32_t a = 0; a < L; ++a) out[a] += base;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pauli predicate (Sec. III-A).  Characters are codes 0=I 1=X 2=Y 3=Z.      */
+/* ------------------------------------------------------------------------ */
+
+/* Direct statement: two strings anticommute iff an odd number of positions
+ * hold two different non-identity Paulis.  Returns 1 if they commute.      */
+int orc_commute_chars(const uint8_t* a, const uint8_t* b, int32_t q) {
+  int count = 0;
+  for (int32_t i = 0; i < q; ++i)
+    if (a[i] != 0 && b[i] != 0 && a[i] != b[i]) ++count;
+  return (count % 2) == 0;
+}
+
+/* The paper's "inverse one-hot" code: X=110, Y=101, Z=011, I=000, ten
+ * characters per 32-bit word (character i of a word in bits 3i..3i+2).    */
+static uint32_t orc_code3(uint8_t ch) {
+  switch (ch) {
+    case 1: return 6u; /* X = 110 */
+    case 2: return 5u; /* Y = 101 */
+    case 3: return 3u; /* Z = 011 */
+    default: return 0u; /* I = 000 */
+  }
+}
+
+int32_t orc_words3(int32_t q) { return (q + 9) / 10; }
+
+void orc_encode3(const uint8_t* chars, int64_t n, int32_t q, uint32_t* enc) {
+  int32_t w3 = orc_words3(q);
+  for (int64_t v = 0; v < n; ++v) {
+    for (int32_t w = 0; w < w3; ++w) enc[v * w3 + w] = 0u;
+    for (int32_t i = 0; i < q; ++i)
+      enc[v * w3 + i / 10] |= orc_code3(chars[v * (int64_t)q + i]) << (3 * (i % 10));
+  }
+}
+
+static int orc_popcount32(uint32_t x) {
+  int c = 0;
+  while (x) {
+    c += (int)(x & 1u);
+    x >>= 1;
+  }
+  return c;
+}
+
+/* AND the codes and count ones: the count's parity is the parity of the
+ * number of mismatching non-identity positions.  Returns 1 if they commute. */
+int orc_commute3(const uint32_t* a, const uint32_t* b, int32_t w3) {
+  int ones = 0;
+  for (int32_t w = 0; w < w3; ++w) ones += orc_popcount32(a[w] & b[w]);
+  return (ones % 2) == 0;
+}
+
+/* Index in a of the smallest color in both sorted lists, or -1 if they are
+ * disjoint (Sec. III-A: with sorted lists the test takes O(L)).             */
+static int32_t orc_min_shared_index(const int64_t* a, const int64_t* b, int32_t L) {
+  int32_t i = 0, j = 0;
+  while (i < L && j < L) {
+    if (a[i] == b[j]) return i;
+    if (a[i] < b[j])
+      ++i;
+    else
+      ++j;
+  }
+  return -1;
+}
+
+int64_t orc_min_shared(const int64_t* a, const int64_t* b, int32_t L) {
+  int32_t i = orc_min_shared_index(a, b, L);
+  return i < 0 ? -1 : a[i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Conflict graph (Alg. 1 construct_conflict_graph; Sec. III-A).            */
+/* ------------------------------------------------------------------------ */
+
+/* One row in color-major order.  enc: [n][w3] codes of the round's vertices
+ * (round-local ids), lists: [n][L] sorted global colors.  kv: scratch [n],
+ * cnt: scratch [L+1].  Writes the row into out (may be NULL to count) and
+ * returns its length.  Each other vertex v is tested once (commute, then the
+ * smallest shared color); hits are then laid out by that color's index.    */
+int64_t orc_conflict_row(int64_t u, int64_t n, const uint32_t* enc, int32_t w3,
+                         const int64_t* lists, int32_t L, int32_t* kv,
+                         int64_t* cnt, int32_t* out) {
+  for (int32_t k = 0; k <= L; ++k) cnt[k] = 0;
+  int64_t len = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    kv[v] = -1;
+    if (v == u) continue;
+    if (!orc_commute3(enc + u * w3, enc + v * w3, w3)) continue;
+    int32_t k = orc_min_shared_index(lists + u * L, lists + v * L, L);
+    if (k < 0) continue;
+    kv[v] = k;
+    cnt[k + 1]++;
+    ++len;
+  }
+  if (out) {
+    for (int32_t k = 0; k < L; ++k) cnt[k + 1] += cnt[k];
+    for (int64_t v = 0; v < n; ++v)
+      if (kv[v] >= 0) out[cnt[kv[v]]++] = (int32_t)v;
+  }
+  return len;
+}
+
+typedef struct {
+  int64_t n, r0, r1, stride;
+  const uint32_t* enc;
+  int32_t w3;
+  const int64_t* lists;
+  int32_t L;
+  const int64_t* rows; /* NULL: rows 0..count-1 themselves */
+  int64_t* lens;
+  const int64_t* off;
+  int32_t* col;
+} orc_rows_job;
+
+static void* orc_rows_worker(void* arg) {
+  orc_rows_job* j = (orc_rows_job*)arg;
+  int32_t* kv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(j->n + 1));
+  int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)(j->L + 2));
+  for (int64_t i = j->r0; i < j->r1; i += j->stride) {
+    int64_t u = j->rows ? j->rows[i] : i;
+    int32_t* dst = j->col ? j->col + j->off[i] : NULL;
+    int64_t len = orc_conflict_row(u, j->n, j->enc, j->w3, j->lists, j->L, kv, cnt, dst);
+    if (j->lens) j->lens[i] = len;
+  }
+  free(kv);
+  free(cnt);
+  return NULL;
+}
+
+static void orc_run_rows(orc_rows_job proto, int64_t count, int32_t threads) {
+  if (threads < 1) threads = 1;
+  if (threads > 256) threads = 256;
+  pthread_t tid[256];
+  orc_rows_job jobs[256];
+  for (int32_t t = 0; t < threads; ++t) {
+    jobs[t] = proto;
+    jobs[t].r0 = t;
+    jobs[t].r1 = count;
+    jobs[t].stride = threads;
+    pthread_create(&tid[t], NULL, orc_rows_worker, &jobs[t]);
+  }
+  for (int32_t t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
+}
+
+/* Selected rows (round-local ids rows[0..m)) of the conflict graph.  With
+ * col == NULL only lens is filled; otherwise off[m] gives where each row
+ * goes.                                                                    */
+void orc_conflict_rows(int64_t n, const uint32_t* enc, int32_t w3,
+                       const int64_t* lists, int32_t L, const int64_t* rows,
+                       int64_t m, int64_t* lens, const int64_t* off,
+                       int32_t* col, int32_t threads) {
+  orc_rows_job p;
+  memset(&p, 0, sizeof(p));
+  p.n = n;
+  p.enc = enc;
+  p.w3 = w3;
+  p.lists = lists;
+  p.L = L;
+  p.rows = rows;
+  p.lens = lens;
+  p.off = off;
+  p.col = col;
+  orc_run_rows(p, m, threads);
+}
+
+/* Whole CSR: row lengths, then off[n+1] (int64) and col.                   */
+int64_t orc_conflict_nnz(int64_t n, const uint32_t* enc, int32_t w3,
+                         const int64_t* lists, int32_t L, int64_t* lens,
+                         int32_t threads) {
+  orc_conflict_rows(n, enc, w3, lists, L, NULL, n, lens, NULL, NULL, threads);
+  int64_t s = 0;
+  for (int64_t u = 0; u < n; ++u) s += lens[u];
+  return s;
+}
+
+void orc_conflict_fill(int64_t n, const uint32_t* enc, int32_t w3,
+                       const int64_t* lists, int32_t L, const int64_t* lens,
+                       int64_t* off, int32_t* col, int32_t threads) {
+  off[0] = 0;
+  for (int64_t u = 0; u < n; ++u) off[u + 1] = off[u] + lens[u];
+  orc_conflict_rows(n, enc, w3, lists, L, NULL, n, NULL, off, col, threads);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coloring of the conflict graph: static Random order, first fit (Sec.      */
+/* III-B "static order schemes"; Alg. 1 color_unconflicted_vertices and      */
+/* color_conflict_graph).                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  uint64_t key;
+  int64_t v;
+} orc_key;
+
+static int cmp_key(const void* a, const void* b) {
+  uint64_t x = ((const orc_key*)a)->key, y = ((const orc_key*)b)->key;
+  return (x > y) - (x < y);
+}
+
+/* gids[n]: global ids of the round's vertices (round-local id = index).
+ * color_local[n] receives the global color or -1.  Returns colored count.  */
+int64_t orc_color_greedy(uint64_t seed, int32_t round, int64_t n,
+                         const int64_t* gids, const int64_t* lists, int32_t L,
+                         const int64_t* off, const int32_t* col, int64_t P,
+                         int64_t base, int64_t* color_local) {
+  orc_key* order = (orc_key*)malloc(sizeof(orc_key) * (size_t)(n > 0 ? n : 1));
+  int64_t* stamp = (int64_t*)malloc(sizeof(int64_t) * (size_t)P);
+  for (int64_t c = 0; c < P; ++c) stamp[c] = -1;
+  for (int64_t v = 0; v < n; ++v) {
+    uint64_t pr = orc_priority(seed, round, gids[v]);
+    order[v].key = (pr << 32) | (uint64_t)(uint32_t)gids[v];
+    order[v].v = v;
+    color_local[v] = -1;
+  }
+  qsort(order, (size_t)n, sizeof(orc_key), cmp_key);
+  int64_t colored = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t v = order[i].v;
+    for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+      int64_t cu = color_local[col[e]];
+      if (cu >= 0) stamp[cu - base] = v;
+    }
+    for (int32_t k = 0; k < L; ++k) {
+      int64_t c = lists[v * L + k];
+      if (stamp[c - base] != v) {
+        color_local[v] = c;
+        ++colored;
+        break;
+      }
+    }
+  }
+  free(order);
+  free(stamp);
+  return colored;
+}
+
+/* Round parameters (Table I; Sec. VI "P a percentage of |V|, L = alpha
+ * log|V|, the same percentage and alpha in every iteration").              */
+void orc_round_params(int64_t n, int64_t num, int64_t den, double alpha,
+                      int64_t* P, int32_t* L) {
+  int64_t p = (n * num + den - 1) / den;
+  if (p < 1) p = 1;
+  double l = ceil(alpha * log((double)n));
+  int64_t li = (int64_t)l;
+  if (li < 1) li = 1;
+  if (li > p) li = p;
+  *P = p;
+  *L = (int32_t)li;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 1: the whole iterative algorithm.                                    */
+/* chars [N][q]; color[N] receives global colors.  Per-round statistics      */
+/* (n, P, L, base, nnz, colored) go to stats[6 * r] for r < max_rounds.      */
+/* Returns the number of rounds run, or -1 if max_rounds was hit first.      */
+/* ------------------------------------------------------------------------ */
+int32_t orc_run(const uint8_t* chars, int64_t N, int32_t q, uint64_t seed,
+                int64_t num, int64_t den, double alpha, int32_t max_rounds,
+                int32_t threads, int64_t* color, int64_t* stats) {
+  int32_t w3 = orc_words3(q);
+  uint32_t* enc_all = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(N * w3 + 1));
+  orc_encode3(chars, N, q, enc_all);
+  for (int64_t v = 0; v < N; ++v) color[v] = -1;
+  int64_t* gids = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N + 1));
+  int64_t n = N;
+  for (int64_t v = 0; v < N; ++v) gids[v] = v;
+  int64_t base = 0;
+  int32_t round = 1;
+  while (n > 0) {
+    if (round > max_rounds) {
+      free(enc_all);
+      free(gids);
+      return -1;
+    }
+    int64_t P;
+    int32_t L;
+    orc_round_params(n, num, den, alpha, &P, &L);
+    uint32_t* enc = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n * w3 + 1));
+    int64_t* lists = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n * L + 1));
+    for (int64_t v = 0; v < n; ++v) {
+      memcpy(enc + v * w3, enc_all + gids[v] * w3, sizeof(uint32_t) * (size_t)w3);
+      orc_draw_list(seed, round, gids[v], P, L, base, lists + v * L);
+    }
+    int64_t* lens = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t nnz = orc_conflict_nnz(n, enc, w3, lists, L, lens, threads);
+    int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz + 1));
+    orc_conflict_fill(n, enc, w3, lists, L, lens, off, col, threads);
+    int64_t* cl = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t colored =
+        orc_color_greedy(seed, round, n, gids, lists, L, off, col, P, base, cl);
+    if (stats) {
+      int64_t* s = stats + 6 * (round - 1);
+      s[0] = n;
+      s[1] = P;
+      s[2] = L;
+      s[3] = base;
+      s[4] = nnz;
+      s[5] = colored;
+    }
+    /* Alg. 1, end of an iteration: carry the uncolored vertices (ascending gid). */
+    int64_t m = 0;
+    for (int64_t v = 0; v < n; ++v) {
+      if (cl[v] >= 0)
+        color[gids[v]] = cl[v];
+      else
+        gids[m++] = gids[v];
+    }
+    n = m;
+    base += P;
+    ++round;
+    free(enc);
+    free(lists);
+    free(lens);
+    free(off);
+    free(col);
+    free(cl);
+  }
+  free(enc_all);
+  free(gids);
+  return round - 1;
+}
