@@ -1,0 +1,202 @@
+/*
+ * picasso.h -- C ABI of libpicasso, a B300 (sm_103a) implementation of the
+ * round hot path of Picasso (Ferdous et al., arXiv 2401.06713): palette-based
+ * list coloring of the commutation graph of n Pauli strings.
+ *
+ * One round (Alg. 1 of the paper) over the still-uncolored vertex set V_l:
+ *   assign lists   every v in V_l draws L_l distinct colors of the round's
+ *                  palette [base_l, base_l + P_l)   (Alg. 1, list assignment)
+ *   build          the conflict graph G_c: u != v are adjacent iff they commute
+ *                  (an edge of the complement graph G', Sec. II) and their
+ *                  lists intersect (Sec. III-A)
+ *   color          static Random order with first fit (Sec. III-B): in
+ *                  ascending (priority, global id) order, v takes the smallest
+ *                  color of its list not taken by a conflict neighbour that
+ *                  comes earlier; if none is left v stays uncolored
+ *   carry          the uncolored vertices form V_{l+1} (Alg. 1, end of an
+ *                  iteration); the next round uses a fresh palette.
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are device pointers on the device that was current
+ *     when picasso_init ran; h_* are host pointers.  The caller owns every
+ *     buffer it passes in; the context owns (and frees in picasso_destroy)
+ *     every buffer it hands out.
+ *   - Strings are packed as symplectic words: for q <= 64 qubits each string
+ *     is two uint64 words [x, z]; qubit i sets bit i of x for X and Y, bit i
+ *     of z for Z and Y.  Two strings commute iff popcount((x_u & z_v) ^
+ *     (z_u & x_v)) is even.
+ *   - Character codes are 0=I 1=X 2=Y 3=Z.
+ *   - Random numbers are Philox4x32-10 (Salmon et al., SC'11).  Draw i of the
+ *     stream (seed, round, gid, tag) is word i%4 of the block with counter
+ *     (gid_lo, gid_hi, round, tag<<24 | i/4) and key (seed_lo, seed_hi); tag 1
+ *     draws lists (Floyd's sampling, a draw x maps to [0, j] as x*(j+1)>>32),
+ *     tag 2 draws the priority (draw 0).
+ *   - Every call returns a picasso_status; no call aborts the process.  A
+ *     CUDA error is reported as PICASSO_ERR_CUDA and leaves the context
+ *     unusable except for picasso_destroy.
+ *   - All work is ordered on the stream given to picasso_init.  Calls that
+ *     return sizes (build, carry, round, run) synchronise that stream.
+ */
+#ifndef PICASSO_H
+#define PICASSO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PICASSO_OK = 0,
+  PICASSO_ERR_INVALID_ARG = 1, /* null pointer, size out of range, bad order */
+  PICASSO_ERR_OOM = 2,         /* device allocation failed                   */
+  PICASSO_ERR_CUDA = 3,        /* a CUDA call or kernel failed               */
+  PICASSO_ERR_BUDGET = 4,      /* conflict graph larger than byte_budget     */
+  PICASSO_ERR_TIMEOUT = 5,     /* a bounded device wait gave up              */
+  PICASSO_ERR_INTERNAL = 6,    /* an internal consistency check failed       */
+  PICASSO_ERR_UNSUPPORTED = 7, /* valid request outside this build's limits  */
+  PICASSO_ERR_STATE = 8        /* call out of order for the context's state  */
+} picasso_status;
+
+/* Conflict-graph construction strategy.  Both produce the same CSR. */
+typedef enum {
+  PICASSO_CONFLICT_AUTO = 0,
+  PICASSO_CONFLICT_ALLPAIRS = 1, /* every pair tested (the paper's GPU kernel) */
+  PICASSO_CONFLICT_BUCKET = 2    /* pairs joined through per-color buckets   */
+} picasso_conflict_algo;
+
+typedef struct {
+  uint64_t seed;         /* Philox key                                        */
+  int64_t palette_num;   /* P_l = max(1, ceil(n_l * num / den))  (Table I)    */
+  int64_t palette_den;
+  double alpha;          /* L_l = min(P_l, max(1, ceil(alpha * ln n_l)))     */
+  int32_t conflict_algo; /* picasso_conflict_algo                             */
+  int32_t max_rounds;    /* picasso_run gives up with ERR_INTERNAL beyond it  */
+  int64_t byte_budget;   /* max bytes of one round's conflict CSR (off + col
+                            + the extras side list); 0 = no limit            */
+} picasso_config;
+
+/* Conflict CSR of the current round, owned by the context and valid until
+ * the next assign/build/carry or destroy.  Ids are round-local: row r is the
+ * r-th uncolored vertex in ascending global id.  Rows are color-major: row u
+ * lists, for each color c of u's list in ascending order, the neighbours v
+ * whose smallest shared color with u is c, ascending in v.  Every edge of
+ * G_c appears exactly once per direction (nnz = 2|E_c|).                    */
+typedef struct {
+  const int64_t* d_off; /* [n_rows + 1]                                      */
+  const int32_t* d_col; /* [nnz]                                             */
+  int64_t n_rows;
+  int64_t nnz;
+} picasso_csr;
+
+/* Per-round record kept by the context (the last round's values). */
+typedef struct {
+  int32_t round;       /* current round number (1-based)                     */
+  int64_t n_total;     /* N                                                  */
+  int64_t n_round;     /* n_l, vertices of the current round                 */
+  int64_t P;           /* P_l of the last assign (0 before)                  */
+  int32_t L;           /* L_l of the last assign                            */
+  int64_t base;        /* base_l of the last assign                         */
+  int64_t nnz;         /* 2|E_c| of the last build                           */
+  int64_t n_extra;     /* entries of the multi-shared side list              */
+  int64_t colored;     /* vertices colored by the last color step            */
+  int64_t colors_used; /* base after the last carry = sum of P of done rounds */
+  int64_t peak_bytes;  /* high-water mark of context-owned device memory      */
+  int32_t conflict_algo_used;
+  int32_t jp_sweeps;   /* sweeps of the last color step                      */
+  int64_t max_bucket;  /* largest color bucket of the last build             */
+} picasso_stats;
+
+/* Fill *cfg with the defaults: seed 0, P = n/8, alpha = 2 (the paper's normal
+ * mode, Sec. VI), AUTO, max_rounds 100000, no budget.                       */
+int picasso_config_default(picasso_config* cfg);
+
+/* Pack n strings of q character codes (row-major uint8 [n][q]) into
+ * symplectic words d_xz [n][2] (q <= 64).  Sec. III-A encodes characters in
+ * bits; this is the product's two-word form of that idea.  Asynchronous.   */
+int picasso_pack(const uint8_t* d_codes, int64_t n, int32_t q, uint64_t* d_xz,
+                 void* stream);
+
+/* Create a context over d_xz [n][2] (read-only, must outlive the context;
+ * 1 <= n < 2^30, 1 <= q <= 64).  stream is a cudaStream_t (NULL = legacy
+ * default stream).  Round 1 starts with V_1 = all n strings, all colors -1. */
+int picasso_init(void** ctx, const picasso_config* cfg, const uint64_t* d_xz,
+                 int64_t n, int32_t q, void* stream);
+
+/* Parameters the configuration gives the current round: P_l, L_l, base_l
+ * (Table I rule; base_l = sum of the earlier rounds' P).                    */
+int picasso_round_params(void* ctx, int64_t* P, int32_t* L, int64_t* base);
+
+/* Alg. 1 list assignment for V_l with explicit P, L (1 <= L <= min(P, 512))
+ * and base.  Also draws the round's priorities.  Asynchronous.             */
+int picasso_assign_lists(void* ctx, int64_t P, int32_t L, int64_t base);
+
+/* Alg. 1 conflict-graph construction (Sec. III-A, Alg. 3's count / offsets /
+ * fill structure).  Synchronises to size the CSR; returns ERR_BUDGET, before
+ * allocating, if the CSR would exceed cfg.byte_budget.                     */
+int picasso_build_conflicts(void* ctx, picasso_csr* out);
+
+/* Alg. 1 coloring of the unconflicted vertices and of G_c (Sec. III-B static
+ * Random order, first fit), run as a dependency-driven parallel sweep that
+ * reproduces the sequential order exactly.  Synchronises.  Writes the
+ * round's colors into the context's color array.                           */
+int picasso_color(void* ctx, int64_t* n_colored);
+
+/* Alg. 1 carry: V_{l+1} = uncolored vertices of V_l, next palette base, next
+ * round.  Synchronises; *n_remaining = |V_{l+1}|.                           */
+int picasso_carry(void* ctx, int64_t* n_remaining);
+
+/* One whole round: params, assign, build, color, carry.                    */
+int picasso_round(void* ctx, int64_t* n_remaining);
+
+/* Rounds until every vertex is colored; then copies the global colors to
+ * d_color_out [n] (may be NULL) and sets *n_rounds (may be NULL).          */
+int picasso_run(void* ctx, int32_t* d_color_out, int32_t* n_rounds);
+
+/* Copy the global color array [n] (-1 = not yet colored) to d_out.         */
+int picasso_get_colors(void* ctx, int32_t* d_out);
+
+/* Inspection of the current round, for tests and tools.
+ *   d_gid   [n_l]    global ids of V_l (ascending)
+ *   d_lists [n_l][L] round-local colors (add base for global), ascending
+ *   d_prio  [n_l]    priorities (smaller = earlier)
+ * Any pointer may be NULL.                                                  */
+int picasso_get_round(void* ctx, int32_t* d_gid, int32_t* d_lists,
+                      uint32_t* d_prio);
+
+/* Run structure of the last build: d_runoff [n_l*L + 1] int64 where run k of
+ * row u is col[runoff[u*L+k] .. runoff[u*L+k+1]); and the multi-shared side
+ * list: d_xoff [n_l*L + 1] int64, d_xcol [n_extra] int32 where entries
+ * xoff[u*L+k] .. xoff[u*L+k+1] are the neighbours v of u that hold u's k-th
+ * color although a smaller color is their smallest shared one (ascending
+ * v).  Pointers are owned by the context.  Any output may be NULL.        */
+int picasso_get_runs(void* ctx, const int64_t** d_runoff,
+                     const int64_t** d_xoff, const int32_t** d_xcol,
+                     int64_t* n_extra);
+
+/* Copy the last build's CSR into caller-owned device buffers: d_off
+ * [n_rows + 1] int64, d_col [nnz] int32 (either may be NULL).  Asynchronous. */
+int picasso_copy_csr(void* ctx, int64_t* d_off, int32_t* d_col);
+
+/* Copy the last build's run offsets and side list (layout as in
+ * picasso_get_runs) into caller-owned buffers.  Asynchronous.             */
+int picasso_copy_runs(void* ctx, int64_t* d_runoff, int64_t* d_xoff,
+                      int32_t* d_xcol);
+
+int picasso_get_stats(void* ctx, picasso_stats* out);
+
+/* Fill d_out[i] with draw i0+i of stream (seed, round, gid, tag), i < count.
+ * Exposes the device generator for parity checks against a CPU Philox.      */
+int picasso_philox_draws(uint64_t seed, int32_t round, int64_t gid,
+                         uint32_t tag, uint32_t i0, int32_t count,
+                         uint32_t* d_out, void* stream);
+
+int picasso_destroy(void* ctx);
+
+const char* picasso_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PICASSO_H */

@@ -81,6 +81,12 @@ def lib():
         L.orc_color_greedy.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, _i64p, _i64p,
                                        ctypes.c_int32, _i64p, _i32p, ctypes.c_int64, ctypes.c_int64, _i64p]
         L.orc_color_greedy.restype = ctypes.c_int64
+        L.orc_draw_lists_many.argtypes = [ctypes.c_uint64, ctypes.c_int32, _i64p, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int32, ctypes.c_int64, _i64p]
+        L.orc_priorities_many.argtypes = [ctypes.c_uint64, ctypes.c_int32, _i64p, ctypes.c_int64, _u32p]
+        L.orc_side_row.argtypes = [ctypes.c_int64, ctypes.c_int64, _u32p, ctypes.c_int32, _i64p, ctypes.c_int32,
+                                   _i64p, _i32p]
+        L.orc_side_row.restype = ctypes.c_int64
         L.orc_round_params.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                        _i64p, _i32p]
         L.orc_run.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
@@ -115,7 +121,11 @@ def priority(seed: int, rnd: int, gid: int) -> int:
 
 
 def priorities(seed: int, rnd: int, gids) -> np.ndarray:
-    return np.array([priority(seed, rnd, int(g)) for g in gids], dtype=np.uint32)
+    gids = np.ascontiguousarray(np.asarray(list(gids) if not isinstance(gids, np.ndarray) else gids,
+                                           dtype=np.int64))
+    out = np.zeros(max(len(gids), 1), dtype=np.uint32)
+    lib().orc_priorities_many(seed, rnd, _p(gids, _i64p), len(gids), _p(out, _u32p))
+    return out[:len(gids)]
 
 
 def draw_list(seed: int, rnd: int, gid: int, P: int, L: int, base: int = 0) -> np.ndarray:
@@ -125,11 +135,10 @@ def draw_list(seed: int, rnd: int, gid: int, P: int, L: int, base: int = 0) -> n
 
 
 def draw_lists(seed: int, rnd: int, gids, P: int, L: int, base: int = 0) -> np.ndarray:
-    gids = np.asarray(gids, dtype=np.int64)
-    out = np.zeros((len(gids), L), dtype=np.int64)
-    for i, g in enumerate(gids):
-        out[i] = draw_list(seed, rnd, int(g), P, L, base)
-    return out
+    gids = np.ascontiguousarray(np.asarray(gids, dtype=np.int64))
+    out = np.zeros((max(len(gids), 1), L), dtype=np.int64)
+    lib().orc_draw_lists_many(seed, rnd, _p(gids, _i64p), len(gids), P, L, base, _p(out, _i64p))
+    return out[:len(gids)]
 
 
 def commute_chars(a, b) -> bool:
@@ -200,6 +209,25 @@ def conflict_rows(enc: np.ndarray, lists: np.ndarray, rows, threads: int | None 
     lib().orc_conflict_rows(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(rows, _i64p), m, None,
                             _p(off, _i64p), _p(col, _i32p), threads)
     return lens[:m], [col[off[i]:off[i + 1]].copy() for i in range(m)]
+
+
+def side_rows(enc: np.ndarray, lists: np.ndarray, rows):
+    """Side-list rows of the given round-local vertices: list of int32 arrays
+    (k-major, ascending v) and per-row per-k lengths [m][L]."""
+    enc = np.ascontiguousarray(enc, dtype=np.uint32)
+    lists = np.ascontiguousarray(lists, dtype=np.int64)
+    n, w3 = enc.shape
+    L = lists.shape[1]
+    outs, lens = [], []
+    cnt = np.zeros(L + 2, dtype=np.int64)
+    for u in rows:
+        m = lib().orc_side_row(int(u), n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(cnt, _i64p), None)
+        per_k = cnt[1:L + 1].copy()
+        buf = np.zeros(max(m, 1), dtype=np.int32)
+        lib().orc_side_row(int(u), n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(cnt, _i64p), _p(buf, _i32p))
+        outs.append(buf[:m].copy())
+        lens.append(per_k)
+    return outs, np.array(lens, dtype=np.int64).reshape(len(outs), L)
 
 
 def color_greedy(seed: int, rnd: int, gids, lists, off, col, P: int, base: int) -> np.ndarray:

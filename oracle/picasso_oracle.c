@@ -134,6 +134,19 @@ void orc_draw_list(uint64_t seed, int32_t round, int64_t gid, int64_t P,
   for (int32_t a = 0; a < L; ++a) out[a] += base;
 }
 
+/* orc_draw_list for many vertices: out[m][L].                               */
+void orc_draw_lists_many(uint64_t seed, int32_t round, const int64_t* gids,
+                         int64_t m, int64_t P, int32_t L, int64_t base,
+                         int64_t* out) {
+  for (int64_t i = 0; i < m; ++i)
+    orc_draw_list(seed, round, gids[i], P, L, base, out + i * L);
+}
+
+void orc_priorities_many(uint64_t seed, int32_t round, const int64_t* gids,
+                         int64_t m, uint32_t* out) {
+  for (int64_t i = 0; i < m; ++i) out[i] = orc_priority(seed, round, gids[i]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Pauli predicate (Sec. III-A).  Characters are codes 0=I 1=X 2=Y 3=Z.      */
 /* ------------------------------------------------------------------------ */
@@ -233,6 +246,52 @@ int64_t orc_conflict_row(int64_t u, int64_t n, const uint32_t* enc, int32_t w3,
     for (int32_t k = 0; k < L; ++k) cnt[k + 1] += cnt[k];
     for (int64_t v = 0; v < n; ++v)
       if (kv[v] >= 0) out[cnt[kv[v]]++] = (int32_t)v;
+  }
+  return len;
+}
+
+/* Side list of row u: for each color c_k of u's list (ascending k), the
+ * neighbours v (commuting, v != u) that hold c_k although a smaller color is
+ * their smallest shared one, ascending in v.  Same calling convention as
+ * orc_conflict_row; cnt must hold L+1 entries.                              */
+int64_t orc_side_row(int64_t u, int64_t n, const uint32_t* enc, int32_t w3,
+                     const int64_t* lists, int32_t L, int64_t* cnt, int32_t* out) {
+  for (int32_t k = 0; k <= L; ++k) cnt[k] = 0;
+  int64_t len = 0;
+  for (int pass = 0; pass < (out ? 2 : 1); ++pass) {
+    if (pass == 1) {
+      int64_t run = 0;
+      for (int32_t k = 0; k < L; ++k) {
+        int64_t c = cnt[k + 1];
+        cnt[k + 1] = run;
+        run += c;
+      }
+    }
+    for (int64_t v = 0; v < n; ++v) {
+      if (v == u) continue;
+      if (!orc_commute3(enc + u * w3, enc + v * w3, w3)) continue;
+      const int64_t* a = lists + u * L;
+      const int64_t* b = lists + v * L;
+      int32_t i = 0, j = 0, seen = 0;
+      while (i < L && j < L) {
+        if (a[i] == b[j]) {
+          if (seen++) {
+            if (pass == 0) {
+              cnt[i + 1]++;
+              ++len;
+            } else {
+              out[cnt[i + 1]++] = (int32_t)v;
+            }
+          }
+          ++i;
+          ++j;
+        } else if (a[i] < b[j]) {
+          ++i;
+        } else {
+          ++j;
+        }
+      }
+    }
   }
   return len;
 }

@@ -1,0 +1,694 @@
+// capi.cu -- the C ABI of libpicasso: context, round driver (Alg. 1) and
+// device-memory bookkeeping.  All device work is launched on the context's
+// stream; the host only computes the round parameters and reads back sizes.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <unordered_map>
+
+#include "common.cuh"
+
+using namespace picasso;
+
+namespace {
+
+struct Ctx {
+  picasso_config cfg{};
+  cudaStream_t s = nullptr;
+  int dev = 0;
+  int64_t N = 0;
+  int32_t q = 0;
+  const uint64_t* xz_user = nullptr;
+
+  int32_t round = 1;
+  int64_t n = 0;          // |V_l|
+  int64_t next_base = 0;  // sum of P over finished rounds
+  int32_t* gid = nullptr; // [n] (nullptr in round 1: identity)
+  uint64_t* xz = nullptr; // [n][2] (nullptr in round 1: xz_user)
+  int32_t* color = nullptr;
+
+  // assign
+  bool assigned = false;
+  int64_t P = 0, base = 0;
+  int32_t L = 0;
+  int32_t* lists = nullptr;
+  uint32_t* prio = nullptr;
+  // build
+  bool built = false;
+  int64_t nnz = 0, nx = 0, max_bucket = 0;
+  int32_t algo_used = 0;
+  int64_t* off = nullptr;
+  int32_t* col = nullptr;
+  int64_t* runoff = nullptr;
+  int64_t* xoff = nullptr;
+  int32_t* xcol = nullptr;
+  // color
+  bool colored_done = false;
+  int64_t n_colored = 0, n_remaining = 0;
+  int32_t sweeps = 0;
+  uint32_t* word = nullptr;
+  uint32_t* flag = nullptr;
+  int64_t* pos = nullptr;
+
+  int32_t* d_err = nullptr;
+  int64_t* h_buf = nullptr;  // pinned readback buffer [16]
+  int sticky = PICASSO_OK;
+
+  std::unordered_map<void*, size_t> sizes;
+  int64_t cur_bytes = 0, peak_bytes = 0;
+
+  const uint64_t* round_xz() const { return xz ? xz : xz_user; }
+};
+
+int map_err(cudaError_t e) {
+  if (e == cudaSuccess) return PICASSO_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return PICASSO_ERR_OOM;
+  }
+  return PICASSO_ERR_CUDA;
+}
+
+#define CK(expr)                                  \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) {                      \
+      int _st = map_err(_e);                      \
+      if (_st == PICASSO_ERR_CUDA) c->sticky = _st; \
+      return _st;                                 \
+    }                                             \
+  } while (0)
+
+#define ST(expr)                    \
+  do {                              \
+    int _st = (expr);               \
+    if (_st != PICASSO_OK) return _st; \
+  } while (0)
+
+template <class T>
+int alloc(Ctx* c, T** p, int64_t count) {
+  *p = nullptr;
+  const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+  cudaError_t e = cudaMallocAsync((void**)p, bytes, c->s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return map_err(e);
+  }
+  c->sizes[(void*)*p] = bytes;
+  c->cur_bytes += (int64_t)bytes;
+  if (c->cur_bytes > c->peak_bytes) c->peak_bytes = c->cur_bytes;
+  return PICASSO_OK;
+}
+
+template <class T>
+void release(Ctx* c, T** p) {
+  if (*p) {
+    auto it = c->sizes.find((void*)*p);
+    if (it != c->sizes.end()) {
+      c->cur_bytes -= (int64_t)it->second;
+      c->sizes.erase(it);
+    }
+    cudaFreeAsync((void*)*p, c->s);
+    *p = nullptr;
+  }
+}
+
+void free_color(Ctx* c) {
+  release(c, &c->word);
+  release(c, &c->flag);
+  release(c, &c->pos);
+  c->colored_done = false;
+}
+
+void free_build(Ctx* c) {
+  release(c, &c->off);
+  release(c, &c->col);
+  release(c, &c->runoff);
+  release(c, &c->xoff);
+  release(c, &c->xcol);
+  c->built = false;
+  c->nnz = c->nx = 0;
+}
+
+void free_assign(Ctx* c) {
+  release(c, &c->lists);
+  release(c, &c->prio);
+  c->assigned = false;
+}
+
+int check(Ctx* c) {
+  if (!c) return PICASSO_ERR_INVALID_ARG;
+  if (c->sticky != PICASSO_OK) return c->sticky;
+  cudaError_t e = cudaSetDevice(c->dev);
+  if (e != cudaSuccess) return map_err(e);
+  return PICASSO_OK;
+}
+
+void params_for(const picasso_config& cfg, int64_t n, int64_t* P, int32_t* L) {
+  int64_t p = (n * cfg.palette_num + cfg.palette_den - 1) / cfg.palette_den;
+  if (p < 1) p = 1;
+  double l = std::ceil(cfg.alpha * std::log((double)n));
+  int64_t li = (int64_t)l;
+  if (li < 1) li = 1;
+  if (li > p) li = p;
+  *P = p;
+  *L = (int32_t)li;
+}
+
+int build_conflicts(Ctx* c) {
+  const int64_t n = c->n, P = c->P;
+  const int32_t L = c->L;
+  const int64_t nl = n * L;
+  cudaStream_t s = c->s;
+
+  uint32_t *cnt = nullptr, *xcnt = nullptr, *bcount = nullptr, *bcursor = nullptr, *dmax = nullptr;
+  int64_t* boff = nullptr;
+  int32_t* bmem = nullptr;
+  void* tmp = nullptr;
+  int st = PICASSO_OK;
+  auto cleanup = [&]() {
+    release(c, &cnt);
+    release(c, &xcnt);
+    release(c, &bcount);
+    release(c, &bcursor);
+    release(c, &dmax);
+    release(c, &boff);
+    release(c, &bmem);
+    release(c, (uint8_t**)&tmp);
+  };
+#define TRY(expr)                  \
+  do {                             \
+    st = (expr);                   \
+    if (st != PICASSO_OK) {        \
+      cleanup();                   \
+      return st;                   \
+    }                              \
+  } while (0)
+#define TRYC(expr)                                   \
+  do {                                               \
+    cudaError_t _e = (expr);                         \
+    if (_e != cudaSuccess) {                         \
+      st = map_err(_e);                              \
+      if (st == PICASSO_ERR_CUDA) c->sticky = st;    \
+      cleanup();                                     \
+      return st;                                     \
+    }                                                \
+  } while (0)
+
+  const size_t tmp_bytes = scan_tmp_bytes(nl > P ? nl : P);
+  TRY(alloc(c, (uint8_t**)&tmp, (int64_t)tmp_bytes));
+  TRY(alloc(c, &cnt, nl));
+  TRY(alloc(c, &xcnt, nl));
+  TRYC(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));
+
+  int algo = c->cfg.conflict_algo;
+  // color buckets: sizes, offsets, largest bucket
+  TRY(alloc(c, &bcount, P));
+  TRY(alloc(c, &boff, P + 1));
+  TRY(alloc(c, &dmax, 2));
+  TRYC(cudaMemsetAsync(bcount, 0, sizeof(uint32_t) * P, s));
+  TRYC(launch_bucket_hist(c->lists, n, L, bcount, s));
+  TRYC(launch_max_u32(bcount, P, dmax, s));
+  TRYC(cudaMemcpyAsync(c->h_buf, dmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaStreamSynchronize(s));
+  const int64_t smax = (int64_t)(*(uint32_t*)c->h_buf);
+  c->max_bucket = smax;
+  const bool bucket_ok = smax <= kBucketCap && P < kBucketMaxP;
+  if (algo == PICASSO_CONFLICT_AUTO) algo = bucket_ok ? PICASSO_CONFLICT_BUCKET : PICASSO_CONFLICT_ALLPAIRS;
+  if (algo == PICASSO_CONFLICT_BUCKET && !bucket_ok) {
+    cleanup();
+    return PICASSO_ERR_UNSUPPORTED;
+  }
+  c->algo_used = algo;
+
+  ConflictArgs a{};
+  a.n = n;
+  a.L = L;
+  a.P = P;
+  a.xz = c->round_xz();
+  a.lists = c->lists;
+  a.cnt = cnt;
+  a.xcnt = xcnt;
+  a.err = c->d_err;
+
+  if (algo == PICASSO_CONFLICT_BUCKET) {
+    TRYC(launch_scan_u32(bcount, P, boff, tmp, s));
+    TRY(alloc(c, &bcursor, P));
+    TRY(alloc(c, &bmem, nl));
+    TRYC(cudaMemsetAsync(bcursor, 0, sizeof(uint32_t) * P, s));
+    TRYC(launch_bucket_fill(c->lists, n, L, boff, bcursor, bmem, s));
+    release(c, &bcursor);
+    TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, s));
+    TRYC(launch_bucket_pairs(a, boff, bmem, (int32_t)smax, false, s));
+  } else {
+    TRYC(launch_allpairs(a, false, s));
+  }
+  release(c, &bcount);
+
+  TRY(alloc(c, &c->runoff, nl + 1));
+  TRY(alloc(c, &c->xoff, nl + 1));
+  TRYC(launch_scan_u32(cnt, nl, c->runoff, tmp, s));
+  TRYC(launch_scan_u32(xcnt, nl, c->xoff, tmp, s));
+  release(c, &cnt);
+  release(c, &xcnt);
+  TRYC(cudaMemcpyAsync(c->h_buf, c->runoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaMemcpyAsync(c->h_buf + 1, c->xoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaMemcpyAsync(c->h_buf + 2, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaStreamSynchronize(s));
+  const int64_t nnz = c->h_buf[0], nx = c->h_buf[1];
+  if ((int32_t)c->h_buf[2] != 0) {
+    cleanup();
+    return PICASSO_ERR_INTERNAL;
+  }
+  const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz + 4 * nx;
+  if (c->cfg.byte_budget > 0 && csr_bytes > c->cfg.byte_budget) {
+    cleanup();
+    release(c, &c->runoff);
+    release(c, &c->xoff);
+    return PICASSO_ERR_BUDGET;
+  }
+  TRY(alloc(c, &c->off, n + 1));
+  TRY(alloc(c, &c->col, nnz));
+  TRY(alloc(c, &c->xcol, nx));
+  a.runoff = c->runoff;
+  a.xoff = c->xoff;
+  a.col = c->col;
+  a.xcol = c->xcol;
+  if (algo == PICASSO_CONFLICT_BUCKET) {
+    TRYC(launch_bucket_pairs(a, boff, bmem, (int32_t)smax, true, s));
+  } else {
+    TRYC(launch_allpairs(a, true, s));
+  }
+  TRYC(launch_row_offsets(c->runoff, n, L, c->off, s));
+  cleanup();
+  c->nnz = nnz;
+  c->nx = nx;
+  c->built = true;
+#undef TRY
+#undef TRYC
+  return PICASSO_OK;
+}
+
+int color_round(Ctx* c) {
+  const int64_t n = c->n;
+  cudaStream_t s = c->s;
+  int32_t *wa = nullptr, *wb = nullptr, *nw = nullptr;
+  uint16_t* kcur = nullptr;
+  void* tmp = nullptr;
+  int st = PICASSO_OK;
+  auto cleanup = [&]() {
+    release(c, &wa);
+    release(c, &wb);
+    release(c, &nw);
+    release(c, &kcur);
+    release(c, (uint8_t**)&tmp);
+  };
+#define TRY(expr)           \
+  do {                      \
+    st = (expr);            \
+    if (st != PICASSO_OK) { \
+      cleanup();            \
+      return st;            \
+    }                       \
+  } while (0)
+#define TRYC(expr)                                \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) {                      \
+      st = map_err(_e);                           \
+      if (st == PICASSO_ERR_CUDA) c->sticky = st; \
+      cleanup();                                  \
+      return st;                                  \
+    }                                             \
+  } while (0)
+  free_color(c);
+  TRY(alloc(c, &c->word, n));
+  TRY(alloc(c, &kcur, n));
+  TRY(alloc(c, &wa, n));
+  TRY(alloc(c, &wb, n));
+  constexpr int kBatch = 4;
+  TRY(alloc(c, &nw, 2 * kBatch + 2));
+  ColorArgs a{};
+  a.n = n;
+  a.L = c->L;
+  a.lists = c->lists;
+  a.prio = c->prio;
+  a.runoff = c->runoff;
+  a.col = c->col;
+  a.xoff = c->xoff;
+  a.xcol = c->xcol;
+  a.word = c->word;
+  a.kcur = kcur;
+  // nw[0] is the initial count; sweep i reads nw[i] and writes nw[i+1]
+  int32_t* counts = nw;
+  TRYC(launch_color_init(a, wa, counts, s));
+  int32_t sweeps = 0;
+  const int64_t max_sweeps = n + 4;
+  bool done = n == 0;
+  while (!done) {
+    for (int b = 0; b < kBatch; ++b) {
+      int32_t* in = (b & 1) ? wb : wa;
+      int32_t* out = (b & 1) ? wa : wb;
+      TRYC(cudaMemsetAsync(counts + b + 1, 0, sizeof(int32_t), s));
+      TRYC(launch_color_sweep(a, in, counts + b, out, counts + b + 1, s));
+    }
+    TRYC(cudaMemcpyAsync(c->h_buf, counts, sizeof(int32_t) * (kBatch + 1), cudaMemcpyDeviceToHost, s));
+    TRYC(cudaStreamSynchronize(s));
+    const int32_t* h = (const int32_t*)c->h_buf;
+    for (int b = 0; b < kBatch; ++b) {
+      if (h[b] > 0) ++sweeps;
+      if (h[b + 1] == 0) {
+        done = true;
+        break;
+      }
+    }
+    if (!done) {
+      // the batch ended in buffer wa (even number of sweeps); carry its count
+      TRYC(cudaMemcpyAsync(counts, counts + kBatch, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      if (sweeps > max_sweeps) {
+        cleanup();
+        return PICASSO_ERR_INTERNAL;
+      }
+    }
+  }
+  c->sweeps = sweeps;
+  // colors to the global array; flags + positions of the uncolored
+  TRY(alloc(c, &c->flag, n));
+  TRY(alloc(c, &c->pos, n + 1));
+  TRY(alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(n)));
+  TRYC(launch_carry_flags(c->word, n, c->gid, c->base, c->color, c->flag, s));
+  TRYC(launch_scan_u32(c->flag, n, c->pos, tmp, s));
+  TRYC(cudaMemcpyAsync(c->h_buf, c->pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaStreamSynchronize(s));
+  c->n_remaining = c->h_buf[0];
+  c->n_colored = n - c->n_remaining;
+  c->colored_done = true;
+  cleanup();
+#undef TRY
+#undef TRYC
+  return PICASSO_OK;
+}
+
+int carry_round(Ctx* c) {
+  const int64_t m = c->n_remaining;
+  int32_t* gid2 = nullptr;
+  uint64_t* xz2 = nullptr;
+  if (m > 0) {
+    ST(alloc(c, &gid2, m));
+    ST(alloc(c, &xz2, 2 * m));
+    CK(launch_carry_gather(c->flag, c->pos, c->n, c->gid, c->round_xz(), gid2, xz2, c->s));
+  }
+  release(c, &c->gid);
+  release(c, &c->xz);
+  c->gid = gid2;
+  c->xz = xz2;
+  free_color(c);
+  free_build(c);
+  free_assign(c);
+  c->next_base = c->base + c->P;
+  c->n = m;
+  c->round += 1;
+  if (m == 0) {
+    // keep a valid (empty) vertex set; later calls see n == 0
+  }
+  return PICASSO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int picasso_config_default(picasso_config* cfg) {
+  if (!cfg) return PICASSO_ERR_INVALID_ARG;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->seed = 0;
+  cfg->palette_num = 1;
+  cfg->palette_den = 8;
+  cfg->alpha = 2.0;
+  cfg->conflict_algo = PICASSO_CONFLICT_AUTO;
+  cfg->max_rounds = 100000;
+  cfg->byte_budget = 0;
+  return PICASSO_OK;
+}
+
+int picasso_pack(const uint8_t* d_codes, int64_t n, int32_t q, uint64_t* d_xz, void* stream) {
+  if (n < 0 || q < 1 || q > 64) return q > 64 ? PICASSO_ERR_UNSUPPORTED : PICASSO_ERR_INVALID_ARG;
+  if (n > 0 && (!d_codes || !d_xz)) return PICASSO_ERR_INVALID_ARG;
+  return map_err(launch_pack(d_codes, n, q, d_xz, (cudaStream_t)stream));
+}
+
+int picasso_philox_draws(uint64_t seed, int32_t round, int64_t gid, uint32_t tag, uint32_t i0, int32_t count,
+                         uint32_t* d_out, void* stream) {
+  if (count < 0 || (count > 0 && !d_out) || tag > 255u) return PICASSO_ERR_INVALID_ARG;
+  return map_err(launch_philox_draws(seed, round, gid, tag, i0, count, d_out, (cudaStream_t)stream));
+}
+
+int picasso_init(void** out, const picasso_config* cfg, const uint64_t* d_xz, int64_t n, int32_t q, void* stream) {
+  if (!out || !cfg || !d_xz) return PICASSO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || n >= (int64_t(1) << 30) || q < 1) return PICASSO_ERR_INVALID_ARG;
+  if (q > 64) return PICASSO_ERR_UNSUPPORTED;
+  if (cfg->palette_num < 1 || cfg->palette_den < 1 || cfg->palette_num > (int64_t(1) << 32) ||
+      cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
+      cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2)
+    return PICASSO_ERR_INVALID_ARG;
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) return PICASSO_ERR_OOM;
+  c->cfg = *cfg;
+  c->s = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&c->dev);
+  if (e != cudaSuccess) {
+    delete c;
+    return map_err(e);
+  }
+  c->N = n;
+  c->q = q;
+  c->xz_user = d_xz;
+  c->n = n;
+  e = cudaMallocHost((void**)&c->h_buf, sizeof(int64_t) * 16);
+  if (e != cudaSuccess) {
+    delete c;
+    return map_err(e);
+  }
+  int st = alloc(c, &c->color, n);
+  if (st == PICASSO_OK) st = alloc(c, &c->d_err, 4);
+  if (st == PICASSO_OK) st = map_err(launch_fill_i32(c->color, n, -1, c->s));
+  if (st != PICASSO_OK) {
+    release(c, &c->color);
+    release(c, &c->d_err);
+    cudaFreeHost(c->h_buf);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return PICASSO_OK;
+}
+
+int picasso_round_params(void* ctx, int64_t* P, int32_t* L, int64_t* base) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (c->n == 0) return PICASSO_ERR_STATE;
+  int64_t p;
+  int32_t l;
+  params_for(c->cfg, c->n, &p, &l);
+  if (P) *P = p;
+  if (L) *L = l;
+  if (base) *base = c->next_base;
+  return PICASSO_OK;
+}
+
+int picasso_assign_lists(void* ctx, int64_t P, int32_t L, int64_t base) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (c->n == 0) return PICASSO_ERR_STATE;
+  if (P < 1 || L < 1 || L > P || base < 0 || base + P > (int64_t)0x7fffffff) return PICASSO_ERR_INVALID_ARG;
+  if (L > kMaxL || P >= (int64_t(1) << 30)) return PICASSO_ERR_UNSUPPORTED;
+  free_color(c);
+  free_build(c);
+  free_assign(c);
+  c->P = P;
+  c->L = L;
+  c->base = base;
+  ST(alloc(c, &c->lists, c->n * L));
+  ST(alloc(c, &c->prio, c->n));
+  CK(launch_assign_lists(c->cfg.seed, c->round, c->gid, c->n, P, L, c->lists, c->prio, c->s));
+  c->assigned = true;
+  return PICASSO_OK;
+}
+
+int picasso_build_conflicts(void* ctx, picasso_csr* out) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (!c->assigned) return PICASSO_ERR_STATE;
+  free_color(c);
+  free_build(c);
+  ST(build_conflicts(c));
+  if (out) {
+    out->d_off = c->off;
+    out->d_col = c->col;
+    out->n_rows = c->n;
+    out->nnz = c->nnz;
+  }
+  return PICASSO_OK;
+}
+
+int picasso_color(void* ctx, int64_t* n_colored) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (!c->built) return PICASSO_ERR_STATE;
+  ST(color_round(c));
+  if (n_colored) *n_colored = c->n_colored;
+  return PICASSO_OK;
+}
+
+int picasso_carry(void* ctx, int64_t* n_remaining) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (!c->colored_done) return PICASSO_ERR_STATE;
+  ST(carry_round(c));
+  if (n_remaining) *n_remaining = c->n;
+  return PICASSO_OK;
+}
+
+int picasso_round(void* ctx, int64_t* n_remaining) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (c->n == 0) {
+    if (n_remaining) *n_remaining = 0;
+    return PICASSO_OK;
+  }
+  int64_t P, base;
+  int32_t L;
+  ST(picasso_round_params(ctx, &P, &L, &base));
+  ST(picasso_assign_lists(ctx, P, L, base));
+  ST(picasso_build_conflicts(ctx, nullptr));
+  ST(picasso_color(ctx, nullptr));
+  return picasso_carry(ctx, n_remaining);
+}
+
+int picasso_run(void* ctx, int32_t* d_color_out, int32_t* n_rounds) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  while (c->n > 0) {
+    if (c->round > c->cfg.max_rounds) return PICASSO_ERR_INTERNAL;
+    ST(picasso_round(ctx, nullptr));
+  }
+  if (d_color_out) ST(picasso_get_colors(ctx, d_color_out));
+  if (n_rounds) *n_rounds = c->round - 1;
+  return PICASSO_OK;
+}
+
+int picasso_get_colors(void* ctx, int32_t* d_out) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (!d_out) return PICASSO_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(d_out, c->color, sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, c->s));
+  return PICASSO_OK;
+}
+
+int picasso_get_round(void* ctx, int32_t* d_gid, int32_t* d_lists, uint32_t* d_prio) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (d_gid && c->n > 0) {
+    if (c->gid)
+      CK(cudaMemcpyAsync(d_gid, c->gid, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->s));
+    else
+      CK(launch_iota(d_gid, c->n, c->s));
+  }
+  if (d_lists || d_prio) {
+    if (!c->assigned) return PICASSO_ERR_STATE;
+    if (d_lists)
+      CK(cudaMemcpyAsync(d_lists, c->lists, sizeof(int32_t) * c->n * c->L, cudaMemcpyDeviceToDevice, c->s));
+    if (d_prio) CK(cudaMemcpyAsync(d_prio, c->prio, sizeof(uint32_t) * c->n, cudaMemcpyDeviceToDevice, c->s));
+  }
+  return PICASSO_OK;
+}
+
+int picasso_get_runs(void* ctx, const int64_t** d_runoff, const int64_t** d_xoff, const int32_t** d_xcol,
+                     int64_t* n_extra) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (!c->built) return PICASSO_ERR_STATE;
+  if (d_runoff) *d_runoff = c->runoff;
+  if (d_xoff) *d_xoff = c->xoff;
+  if (d_xcol) *d_xcol = c->xcol;
+  if (n_extra) *n_extra = c->nx;
+  return PICASSO_OK;
+}
+
+int picasso_copy_csr(void* ctx, int64_t* d_off, int32_t* d_col) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (!c->built) return PICASSO_ERR_STATE;
+  if (d_off) CK(cudaMemcpyAsync(d_off, c->off, sizeof(int64_t) * (c->n + 1), cudaMemcpyDeviceToDevice, c->s));
+  if (d_col && c->nnz > 0)
+    CK(cudaMemcpyAsync(d_col, c->col, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToDevice, c->s));
+  return PICASSO_OK;
+}
+
+int picasso_copy_runs(void* ctx, int64_t* d_runoff, int64_t* d_xoff, int32_t* d_xcol) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (!c->built) return PICASSO_ERR_STATE;
+  const int64_t nl = c->n * c->L + 1;
+  if (d_runoff) CK(cudaMemcpyAsync(d_runoff, c->runoff, sizeof(int64_t) * nl, cudaMemcpyDeviceToDevice, c->s));
+  if (d_xoff) CK(cudaMemcpyAsync(d_xoff, c->xoff, sizeof(int64_t) * nl, cudaMemcpyDeviceToDevice, c->s));
+  if (d_xcol && c->nx > 0)
+    CK(cudaMemcpyAsync(d_xcol, c->xcol, sizeof(int32_t) * c->nx, cudaMemcpyDeviceToDevice, c->s));
+  return PICASSO_OK;
+}
+
+int picasso_get_stats(void* ctx, picasso_stats* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !out) return PICASSO_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->round = c->round;
+  out->n_total = c->N;
+  out->n_round = c->n;
+  out->P = c->P;
+  out->L = c->L;
+  out->base = c->base;
+  out->nnz = c->nnz;
+  out->n_extra = c->nx;
+  out->colored = c->n_colored;
+  out->colors_used = c->next_base;
+  out->peak_bytes = c->peak_bytes;
+  out->conflict_algo_used = c->algo_used;
+  out->jp_sweeps = c->sweeps;
+  out->max_bucket = c->max_bucket;
+  return PICASSO_OK;
+}
+
+int picasso_destroy(void* ctx) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return PICASSO_ERR_INVALID_ARG;
+  cudaSetDevice(c->dev);
+  free_color(c);
+  free_build(c);
+  free_assign(c);
+  release(c, &c->gid);
+  release(c, &c->xz);
+  release(c, &c->color);
+  release(c, &c->d_err);
+  cudaStreamSynchronize(c->s);
+  if (c->h_buf) cudaFreeHost(c->h_buf);
+  delete c;
+  return PICASSO_OK;
+}
+
+const char* picasso_strerror(int status) {
+  switch (status) {
+    case PICASSO_OK: return "ok";
+    case PICASSO_ERR_INVALID_ARG: return "invalid argument";
+    case PICASSO_ERR_OOM: return "device out of memory";
+    case PICASSO_ERR_CUDA: return "CUDA error";
+    case PICASSO_ERR_BUDGET: return "conflict graph exceeds the byte budget";
+    case PICASSO_ERR_TIMEOUT: return "bounded device wait expired";
+    case PICASSO_ERR_INTERNAL: return "internal consistency check failed";
+    case PICASSO_ERR_UNSUPPORTED: return "outside this build's limits";
+    case PICASSO_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// common.cuh -- device helpers and internal launcher declarations of
+// libpicasso (sm_103a).  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/picasso.h"
+
+namespace picasso {
+
+constexpr uint32_t kTagList = 1u;
+constexpr uint32_t kTagPrio = 2u;
+constexpr int kMaxL = 512;           // longest list a round may draw
+constexpr int kBucketCap = 2048;     // largest color bucket of the bucket join
+constexpr int kBucketMaxP = 1 << 21; // palette limit of the bucket join
+constexpr uint32_t kFailedColor = 0x3FFFFFFFu;
+
+// Vertex state word of the coloring: bits 31..2 a round-local color, bits
+// 1..0 the state.  Undecided: the color is the current candidate.
+constexpr uint32_t kUndecided = 0u, kColored = 1u, kFailed = 2u;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products; the key advances by the Weyl constants between
+// rounds.
+// ---------------------------------------------------------------------------
+struct u32x4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = u32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+  }
+  return c;
+}
+
+// Block b of stream (seed, round, gid, tag).
+__device__ __forceinline__ u32x4 philox_block(uint64_t seed, int32_t round, int64_t gid,
+                                              uint32_t tag, uint32_t b) {
+  u32x4 c{(uint32_t)((uint64_t)gid & 0xffffffffu), (uint32_t)((uint64_t)gid >> 32), (uint32_t)round,
+          (tag << 24) | b};
+  return philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+}
+
+__device__ __forceinline__ uint32_t pick(const u32x4& v, uint32_t i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Symplectic commutation test for one-word strings.
+__device__ __forceinline__ bool commute1(uint64_t xu, uint64_t zu, uint64_t xv, uint64_t zv) {
+  return (__popcll((xu & zv) ^ (zu & xv)) & 1) == 0;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (host functions defined in the kernel .cu files).
+// ---------------------------------------------------------------------------
+cudaError_t launch_pack(const uint8_t* codes, int64_t n, int32_t q, uint64_t* xz, cudaStream_t s);
+cudaError_t launch_philox_draws(uint64_t seed, int32_t round, int64_t gid, uint32_t tag, uint32_t i0,
+                                int32_t count, uint32_t* out, cudaStream_t s);
+cudaError_t launch_assign_lists(uint64_t seed, int32_t round, const int32_t* gid, int64_t n, int64_t P,
+                                int32_t L, int32_t* lists, uint32_t* prio, cudaStream_t s);
+
+// Exclusive scan of n uint32 counts into out[n+1] (int64); tmp needs
+// scan_tmp_bytes(n) bytes.
+size_t scan_tmp_bytes(int64_t n);
+cudaError_t launch_scan_u32(const uint32_t* in, int64_t n, int64_t* out, void* tmp, cudaStream_t s);
+
+// Conflict build.
+struct ConflictArgs {
+  int64_t n;
+  int32_t L;
+  int64_t P;
+  const uint64_t* xz;    // [n][2]
+  const int32_t* lists;  // [n][L] round-local colors, ascending
+  uint32_t* cnt;         // [n*L] run lengths          (count pass)
+  uint32_t* xcnt;        // [n*L] side-list lengths    (count pass)
+  const int64_t* runoff; // [n*L+1]                    (fill pass)
+  const int64_t* xoff;   // [n*L+1]                    (fill pass)
+  int32_t* col;          // [nnz]                      (fill pass)
+  int32_t* xcol;         // [n_extra]                  (fill pass)
+  int32_t* err;          // device error word
+};
+
+// Buckets: members of color c are bmem[boff[c] .. boff[c+1]) ascending.
+cudaError_t launch_bucket_hist(const int32_t* lists, int64_t n, int32_t L, uint32_t* bcount,
+                               cudaStream_t s);
+cudaError_t launch_bucket_fill(const int32_t* lists, int64_t n, int32_t L, const int64_t* boff,
+                               uint32_t* bcursor, int32_t* bmem, cudaStream_t s);
+cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err,
+                               cudaStream_t s);
+cudaError_t launch_max_u32(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s);
+cudaError_t launch_bucket_pairs(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
+                                int32_t smax, bool fill, cudaStream_t s);
+cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s);
+cudaError_t launch_row_offsets(const int64_t* runoff, int64_t n, int32_t L, int64_t* off,
+                               cudaStream_t s);
+
+// Coloring and carry.
+struct ColorArgs {
+  int64_t n;
+  int32_t L;
+  const int32_t* lists;
+  const uint32_t* prio;
+  const int64_t* runoff;
+  const int32_t* col;
+  const int64_t* xoff;
+  const int32_t* xcol;
+  uint32_t* word;   // [n] state words
+  uint16_t* kcur;   // [n] index of the current candidate in the list
+};
+cudaError_t launch_color_init(const ColorArgs& a, int32_t* work, int32_t* nwork, cudaStream_t s);
+cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const int32_t* nwork_in,
+                               int32_t* work_out, int32_t* nwork_out, cudaStream_t s);
+cudaError_t launch_carry_flags(const uint32_t* word, int64_t n, const int32_t* gid, int64_t base,
+                               int32_t* color, uint32_t* flag, cudaStream_t s);
+cudaError_t launch_carry_gather(const uint32_t* flag, const int64_t* pos, int64_t n, const int32_t* gid,
+                                const uint64_t* xz, int32_t* gid_out, uint64_t* xz_out, cudaStream_t s);
+cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t n, uint64_t* xz_out,
+                             cudaStream_t s);
+cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t* out, int64_t n, int32_t v, cudaStream_t s);
+
+}  // namespace picasso

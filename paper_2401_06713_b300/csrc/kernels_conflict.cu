@@ -1,0 +1,489 @@
+// kernels_conflict.cu -- Alg. 1 construct_conflict_graph on sm_103a.
+//
+// G_c keeps a pair {u, v} of the round's vertices iff the two strings commute
+// (edge of the complement graph G', Sec. II) and their color lists intersect
+// (Sec. III-A).  Rows are color-major: row u holds, for each color c of u's
+// list in ascending order, the neighbours v whose smallest shared color with
+// u is c, ascending in v (one "run" per list color).  Pairs sharing more than
+// one color also go to a side list at each non-smallest shared color; the
+// coloring step uses runs and side list to find, per list color, exactly the
+// neighbours that hold it.
+//
+// Both strategies below run a count pass (run lengths), an exclusive scan to
+// offsets, and a fill pass that recomputes every test and writes each run in
+// ascending order with warp ballots -- no atomics on output positions, so
+// the CSR is deterministic.
+//
+//   bucket join   one CTA per color c: the members of bucket c (vertices
+//                 holding c) are staged in shared memory and every pair of
+//                 members is tested there; a pair is a run entry at c iff c
+//                 is the pair's smallest shared color, found exactly through
+//                 a shared-memory hash of the members' smaller colors.
+//   all pairs     one warp per row u sweeping every column v (the paper's GPU
+//                 kernel tests all |V|(|V|-1)/2 pairs, Sec. IV); the list
+//                 intersection is a two-pointer merge.
+#include <algorithm>
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace picasso {
+
+// ---------------------------------------------------------------------------
+// Color buckets
+// ---------------------------------------------------------------------------
+__global__ void k_bucket_hist(const int32_t* __restrict__ lists, int64_t total, uint32_t* __restrict__ bcount) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&bcount[lists[i]], 1u);
+}
+
+cudaError_t launch_bucket_hist(const int32_t* lists, int64_t n, int32_t L, uint32_t* bcount, cudaStream_t s) {
+  const int64_t total = n * L;
+  if (total <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 148 * 16);
+  k_bucket_hist<<<blocks, 256, 0, s>>>(lists, total, bcount);
+  return cudaGetLastError();
+}
+
+__global__ void k_bucket_fill(const int32_t* __restrict__ lists, int64_t total, int32_t L,
+                              const int64_t* __restrict__ boff, uint32_t* __restrict__ bcursor,
+                              int32_t* __restrict__ bmem) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = lists[i];
+    const uint32_t pos = atomicAdd(&bcursor[c], 1u);
+    bmem[boff[c] + pos] = (int32_t)(i / L);
+  }
+}
+
+cudaError_t launch_bucket_fill(const int32_t* lists, int64_t n, int32_t L, const int64_t* boff, uint32_t* bcursor,
+                               int32_t* bmem, cudaStream_t s) {
+  const int64_t total = n * L;
+  if (total <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 148 * 16);
+  k_bucket_fill<<<blocks, 256, 0, s>>>(lists, total, L, boff, bcursor, bmem);
+  return cudaGetLastError();
+}
+
+// Ascending order inside each bucket: a shared-memory bitonic sort per bucket.
+__global__ void __launch_bounds__(512) k_bucket_sort(const int64_t* __restrict__ boff, int64_t P,
+                                                     int32_t* __restrict__ bmem, int32_t* err) {
+  __shared__ int32_t key[kBucketCap];
+  for (int64_t b = blockIdx.x; b < P; b += gridDim.x) {
+    const int64_t o = boff[b];
+    const int s = (int)(boff[b + 1] - o);
+    if (s <= 1) continue;
+    if (s > kBucketCap) {
+      if (threadIdx.x == 0) atomicExch(err, 1);
+      continue;
+    }
+    int m = 1;
+    while (m < s) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) key[i] = i < s ? bmem[o + i] : 0x7fffffff;
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          const int p = i ^ j;
+          if (p > i) {
+            const bool up = (i & k) == 0;
+            const int32_t a = key[i], c = key[p];
+            if ((a > c) == up) {
+              key[i] = c;
+              key[p] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < s; i += blockDim.x) bmem[o + i] = key[i];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, cudaStream_t s) {
+  const unsigned blocks = (unsigned)std::min<int64_t>(P, 148 * 8);
+  k_bucket_sort<<<blocks, 256, 0, s>>>(boff, P, bmem, err);
+  return cudaGetLastError();
+}
+
+__global__ void k_max_u32(const uint32_t* __restrict__ in, int64_t n, uint32_t* out) {
+  uint32_t m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, in[i]);
+  for (int d = 16; d; d >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+cudaError_t launch_max_u32(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess || n <= 0) return e;
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 4);
+  k_max_u32<<<blocks, 256, 0, s>>>(in, n, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Bucket join
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kPairThreads = 512;
+constexpr int kExCap = 2048;  // exclusion pairs per bucket before the exact fallback
+
+struct BucketSmem {
+  uint64_t* sx;
+  uint64_t* sz;
+  int32_t* sid;
+  uint16_t* kk;
+  int32_t* exo;   // [smax + 1]
+  int32_t* excur; // [smax]
+  uint16_t* exv;  // [2 * kExCap]
+  uint32_t* expair;
+  uint32_t* tab;  // [hs]
+  int32_t* misc;  // [4]: E, nexcl, slow
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t bucket_smem_bytes(int smax, int hs) {
+  size_t b = 0;
+  b += align16(sizeof(uint64_t) * smax) * 2;
+  b += align16(sizeof(int32_t) * smax);
+  b += align16(sizeof(uint16_t) * smax);
+  b += align16(sizeof(int32_t) * (smax + 1));
+  b += align16(sizeof(int32_t) * smax);
+  b += align16(sizeof(uint16_t) * 2 * kExCap);
+  b += align16(sizeof(uint32_t) * kExCap);
+  b += align16(sizeof(uint32_t) * hs);
+  b += align16(sizeof(int32_t) * 4);
+  return b;
+}
+
+__device__ inline BucketSmem carve(uint8_t* p, int smax, int hs) {
+  BucketSmem m;
+  m.sx = (uint64_t*)p; p += align16(sizeof(uint64_t) * smax);
+  m.sz = (uint64_t*)p; p += align16(sizeof(uint64_t) * smax);
+  m.sid = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
+  m.kk = (uint16_t*)p; p += align16(sizeof(uint16_t) * smax);
+  m.exo = (int32_t*)p; p += align16(sizeof(int32_t) * (smax + 1));
+  m.excur = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
+  m.exv = (uint16_t*)p; p += align16(sizeof(uint16_t) * 2 * kExCap);
+  m.expair = (uint32_t*)p; p += align16(sizeof(uint32_t) * kExCap);
+  m.tab = (uint32_t*)p; p += align16(sizeof(uint32_t) * hs);
+  m.misc = (int32_t*)p;
+  return m;
+}
+
+// Does a[0..ka) meet b[0..kb)?  (both ascending)
+__device__ inline bool share_prefix(const int32_t* __restrict__ a, int ka, const int32_t* __restrict__ b, int kb) {
+  int i = 0, j = 0;
+  while (i < ka && j < kb) {
+    const int32_t x = __ldg(a + i), y = __ldg(b + j);
+    if (x == y) return true;
+    if (x < y)
+      ++i;
+    else
+      ++j;
+  }
+  return false;
+}
+
+__device__ inline int find_in_list(const int32_t* __restrict__ lst, int L, int32_t c) {
+  int lo = 0, hi = L - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(lst + mid) < c)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace
+
+template <bool FILL>
+__global__ void __launch_bounds__(kPairThreads) k_bucket_pairs(ConflictArgs a, const int64_t* __restrict__ boff,
+                                                               const int32_t* __restrict__ bmem, int smax,
+                                                               int hs_log2) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int hs = 1 << hs_log2;
+  BucketSmem S = carve(smem_raw, smax, hs);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int L = a.L;
+  const uint32_t lt = lanemask_lt();
+
+  for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
+    const int64_t o = boff[b];
+    const int s = (int)(boff[b + 1] - o);
+    if (s == 0) continue;
+    if (threadIdx.x < 4) S.misc[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) {
+      const int32_t v = bmem[o + i];
+      S.sid[i] = v;
+      S.sx[i] = a.xz[2 * (int64_t)v];
+      S.sz[i] = a.xz[2 * (int64_t)v + 1];
+      S.kk[i] = (uint16_t)find_in_list(a.lists + (int64_t)v * L, L, (int32_t)b);
+      S.excur[i] = 0;
+    }
+    __syncthreads();
+    // E = number of (member, smaller color) entries
+    {
+      int e = 0;
+      for (int i = threadIdx.x; i < s; i += blockDim.x) e += S.kk[i];
+      for (int d = 16; d; d >>= 1) e += __shfl_xor_sync(0xffffffffu, e, d);
+      if (lane == 0 && e) atomicAdd(&S.misc[0], e);
+    }
+    __syncthreads();
+    if (S.misc[0] * 10 > hs * 7) {
+      if (threadIdx.x == 0) S.misc[2] = 1;
+    } else if (S.misc[0] > 0) {
+      for (int i = threadIdx.x; i < hs; i += blockDim.x) S.tab[i] = 0u;
+      __syncthreads();
+      // Insert every smaller color of every member; an insert that passes an
+      // entry of the same color found a pair sharing that color.
+      for (int i = wid; i < s; i += nw) {
+        const int32_t* lst = a.lists + (int64_t)S.sid[i] * L;
+        for (int t = lane; t < S.kk[i]; t += 32) {
+          const uint32_t c = (uint32_t)__ldg(lst + t);
+          const uint32_t key = ((c + 1u) << 11) | (uint32_t)i;
+          uint32_t slot = (c * 0x9E3779B1u) >> (32 - hs_log2);
+          while (true) {
+            const uint32_t old = atomicCAS(&S.tab[slot], 0u, key);
+            if (old == 0u) break;
+            if ((old >> 11) == c + 1u) {
+              const int q = atomicAdd(&S.misc[1], 1);
+              if (q < kExCap)
+                S.expair[q] = ((old & 2047u) << 16) | (uint32_t)i;
+              else
+                S.misc[2] = 1;
+            }
+            slot = (slot + 1) & (hs - 1);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const bool slow = S.misc[2] != 0;
+    const int npairs = min(S.misc[1], kExCap);
+    if (!slow) {
+      // per-member exclusion lists (counting sort of the pairs by member)
+      for (int i = threadIdx.x; i <= s; i += blockDim.x) S.exo[i] = 0;
+      __syncthreads();
+      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        atomicAdd(&S.exo[(S.expair[p] >> 16) + 1], 1);
+        atomicAdd(&S.exo[(S.expair[p] & 0xffffu) + 1], 1);
+      }
+      __syncthreads();
+      if (wid == 0) {
+        int carry = 0;
+        for (int i0 = 1; i0 <= s; i0 += 32) {
+          const int i = i0 + lane;
+          int x = i <= s ? S.exo[i] : 0;
+          for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+          }
+          if (i <= s) S.exo[i] = x + carry;
+          carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+      }
+      __syncthreads();
+      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        const int i1 = S.expair[p] >> 16, i2 = S.expair[p] & 0xffff;
+        S.exv[S.exo[i1] + atomicAdd(&S.excur[i1], 1)] = (uint16_t)i2;
+        S.exv[S.exo[i2] + atomicAdd(&S.excur[i2], 1)] = (uint16_t)i1;
+      }
+      __syncthreads();
+    }
+
+    // One warp per member row; lanes sweep partners in ascending order.
+    for (int i = wid; i < s; i += nw) {
+      const uint64_t xi = S.sx[i], zi = S.sz[i];
+      const int32_t v = S.sid[i];
+      const int k = S.kk[i];
+      const int64_t slot = (int64_t)v * L + k;
+      int64_t rpos = 0, xpos = 0;
+      if (FILL) {
+        rpos = a.runoff[slot];
+        xpos = a.xoff[slot];
+      }
+      uint32_t rc = 0, xc = 0;
+      for (int j0 = 0; j0 < s; j0 += 32) {
+        const int j = j0 + lane;
+        const bool bit = j < s && j != i && commute1(xi, zi, S.sx[j], S.sz[j]);
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        if (m == 0u) continue;
+        uint32_t exm = 0u;
+        if (!slow) {
+          for (int e = S.exo[i]; e < S.exo[i + 1]; ++e) {
+            const uint32_t d = (uint32_t)S.exv[e] - (uint32_t)j0;
+            if (d < 32u) exm |= 1u << d;
+          }
+        } else {
+          const bool ex = bit && share_prefix(a.lists + (int64_t)v * L, k, a.lists + (int64_t)S.sid[j] * L, S.kk[j]);
+          exm = __ballot_sync(0xffffffffu, ex);
+        }
+        const uint32_t rm = m & ~exm, xm = m & exm;
+        if (FILL) {
+          if ((rm >> lane) & 1u) a.col[rpos + rc + __popc(rm & lt)] = S.sid[j];
+          if ((xm >> lane) & 1u) a.xcol[xpos + xc + __popc(xm & lt)] = S.sid[j];
+        }
+        rc += __popc(rm);
+        xc += __popc(xm);
+      }
+      if (!FILL && lane == 0) {
+        a.cnt[slot] = rc;
+        a.xcnt[slot] = xc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_bucket_pairs(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, int32_t smax,
+                                bool fill, cudaStream_t s) {
+  if (a.P <= 0 || a.n <= 0) return cudaSuccess;
+  smax = max(smax, 1);
+  int64_t want = (int64_t)smax * (int64_t)max(a.L - 1, 1) * 3 / 2;
+  int hs_log2 = 8;
+  while ((1ll << hs_log2) < want && hs_log2 < 14) ++hs_log2;
+  const size_t bytes = bucket_smem_bytes(smax, 1 << hs_log2);
+  auto kern = fill ? k_bucket_pairs<true> : k_bucket_pairs<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPairThreads, bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
+  kern<<<(unsigned)blocks, kPairThreads, bytes, s>>>(a, boff, bmem, smax, hs_log2);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// All pairs: warp per row, two-pointer list merge for commuting pairs.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kApWarps = 8;
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(kApWarps * 32) k_allpairs(ConflictArgs a) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int L = a.L;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // per warp: row list [L] int32, run counters/cursors [L] int64, side [L] int64
+  int32_t* rl = (int32_t*)smem_raw + (size_t)wid * L;
+  int64_t* cur = (int64_t*)(smem_raw + align16(sizeof(int32_t) * L * kApWarps)) + (size_t)wid * 2 * L;
+  int64_t* xcur = cur + L;
+  const uint32_t lt = lanemask_lt();
+  for (int64_t u = (int64_t)blockIdx.x * kApWarps + wid; u < a.n; u += (int64_t)gridDim.x * kApWarps) {
+    const int32_t* lu = a.lists + u * L;
+    for (int t = lane; t < L; t += 32) {
+      rl[t] = lu[t];
+      cur[t] = FILL ? a.runoff[u * L + t] : 0;
+      xcur[t] = FILL ? a.xoff[u * L + t] : 0;
+    }
+    __syncwarp();
+    const uint64_t xu = a.xz[2 * u], zu = a.xz[2 * u + 1];
+    for (int64_t v0 = 0; v0 < a.n; v0 += 32) {
+      const int64_t v = v0 + lane;
+      int k0 = -1, nshared = 0;
+      if (v < a.n && v != u && commute1(xu, zu, a.xz[2 * v], a.xz[2 * v + 1])) {
+        const int32_t* lv = a.lists + v * L;
+        int i = 0, j = 0;
+        while (i < L && j < L) {
+          const int32_t x = rl[i], y = __ldg(lv + j);
+          if (x == y) {
+            if (k0 < 0) {
+              k0 = i;
+            } else if (!FILL) {
+              atomicAdd((unsigned long long*)&xcur[i], 1ull);
+            }
+            ++nshared;
+            ++i;
+            ++j;
+          } else if (x < y) {
+            ++i;
+          } else {
+            ++j;
+          }
+        }
+      }
+      if (!FILL) {
+        if (k0 >= 0) atomicAdd((unsigned long long*)&cur[k0], 1ull);
+      } else {
+        // run entries: lanes with the same run write in lane (= v) order
+        const uint32_t act = __ballot_sync(0xffffffffu, k0 >= 0);
+        if (act) {
+          const uint32_t grp = __match_any_sync(0xffffffffu, k0);
+          if (k0 >= 0) {
+            const int64_t pos = cur[k0] + __popc(grp & lt);
+            a.col[pos] = (int32_t)v;
+          }
+          __syncwarp();
+          if (k0 >= 0 && (grp & lt) == 0u) cur[k0] += __popc(grp);
+          __syncwarp();
+        }
+        // side-list entries, one lane at a time in lane order
+        uint32_t more = __ballot_sync(0xffffffffu, nshared > 1);
+        while (more) {
+          const int l = __ffs(more) - 1;
+          more &= more - 1;
+          if (lane == l) {
+            const int32_t* lv = a.lists + v * L;
+            int i = 0, j = 0, seen = 0;
+            while (i < L && j < L) {
+              const int32_t x = rl[i], y = __ldg(lv + j);
+              if (x == y) {
+                if (seen++) a.xcol[xcur[i]++] = (int32_t)v;
+                ++i;
+                ++j;
+              } else if (x < y) {
+                ++i;
+              } else {
+                ++j;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    __syncwarp();
+    if (!FILL) {
+      for (int t = lane; t < L; t += 32) {
+        a.cnt[u * L + t] = (uint32_t)cur[t];
+        a.xcnt[u * L + t] = (uint32_t)xcur[t];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const size_t bytes = align16(sizeof(int32_t) * a.L * kApWarps) + sizeof(int64_t) * 2 * a.L * kApWarps;
+  auto kern = fill ? k_allpairs<true> : k_allpairs<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = std::min<int64_t>((a.n + kApWarps - 1) / kApWarps, 148 * 8);
+  kern<<<(unsigned)blocks, kApWarps * 32, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void k_row_offsets(const int64_t* __restrict__ runoff, int64_t n, int32_t L, int64_t* __restrict__ off) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u <= n) off[u] = runoff[u * L];
+}
+
+cudaError_t launch_row_offsets(const int64_t* runoff, int64_t n, int32_t L, int64_t* off, cudaStream_t s) {
+  k_row_offsets<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(runoff, n, L, off);
+  return cudaGetLastError();
+}
+
+}  // namespace picasso

@@ -1,0 +1,99 @@
+// kernels_lists.cu -- string packing and Alg. 1 list assignment (sm_103a).
+#include "common.cuh"
+
+namespace picasso {
+
+// Characters -> symplectic words.  One thread per string; the block's rows
+// are staged through shared memory so global reads are coalesced.
+__global__ void k_pack(const uint8_t* __restrict__ codes, int64_t n, int32_t q, uint64_t* __restrict__ xz) {
+  __shared__ uint8_t tile[256 * 64];
+  const int64_t row0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t rows = min((int64_t)blockDim.x, n - row0);
+  const int64_t bytes = rows * q;
+  const uint8_t* src = codes + row0 * q;
+  for (int64_t i = threadIdx.x; i < bytes; i += blockDim.x) tile[i] = src[i];
+  __syncthreads();
+  if (threadIdx.x >= rows) return;
+  uint64_t x = 0, z = 0;
+  const uint8_t* s = tile + (int64_t)threadIdx.x * q;
+  for (int i = 0; i < q; ++i) {
+    const uint32_t c = s[i];
+    x |= (uint64_t)(c == 1u || c == 2u) << i;
+    z |= (uint64_t)(c == 3u || c == 2u) << i;
+  }
+  xz[2 * (row0 + threadIdx.x)] = x;
+  xz[2 * (row0 + threadIdx.x) + 1] = z;
+}
+
+cudaError_t launch_pack(const uint8_t* codes, int64_t n, int32_t q, uint64_t* xz, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  k_pack<<<(unsigned)blocks, 256, 0, s>>>(codes, n, q, xz);
+  return cudaGetLastError();
+}
+
+__global__ void k_philox_draws(uint64_t seed, int32_t round, int64_t gid, uint32_t tag, uint32_t i0,
+                               int32_t count, uint32_t* out) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const uint32_t d = i0 + (uint32_t)i;
+  out[i] = pick(philox_block(seed, round, gid, tag, d / 4u), d % 4u);
+}
+
+cudaError_t launch_philox_draws(uint64_t seed, int32_t round, int64_t gid, uint32_t tag, uint32_t i0,
+                                int32_t count, uint32_t* out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_philox_draws<<<(count + 255) / 256, 256, 0, s>>>(seed, round, gid, tag, i0, count, out);
+  return cudaGetLastError();
+}
+
+// Alg. 1 assign_rand_list_colors: one thread per vertex.  Floyd's sampling of
+// L distinct values of [0, P) (Bentley & Floyd, CACM 1987): for j = P-L ..
+// P-1 draw t in [0, j] (x*(j+1) >> 32 of the next Philox word); keep t, or j
+// if t was already kept.  Then an insertion sort; lists hold round-local
+// colors.  The priority is draw 0 of the PRIO stream.
+template <int LCAP>
+__global__ void k_assign_lists(uint64_t seed, int32_t round, const int32_t* __restrict__ gid, int64_t n,
+                               int64_t P, int32_t L, int32_t* __restrict__ lists, uint32_t* __restrict__ prio) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int64_t g = gid ? (int64_t)gid[v] : v;
+  uint32_t sel[LCAP];
+  u32x4 blk{0, 0, 0, 0};
+  for (int m = 0; m < L; ++m) {
+    if ((m & 3) == 0) blk = philox_block(seed, round, g, kTagList, (uint32_t)(m >> 2));
+    const uint32_t x = pick(blk, (uint32_t)(m & 3));
+    const uint64_t j = (uint64_t)(P - L + m);
+    const uint32_t t = (uint32_t)(((uint64_t)x * (j + 1)) >> 32);
+    bool seen = false;
+    for (int a = 0; a < m; ++a) seen |= (sel[a] == t);
+    sel[m] = seen ? (uint32_t)j : t;
+  }
+  for (int a = 1; a < L; ++a) {
+    const uint32_t key = sel[a];
+    int b = a - 1;
+    while (b >= 0 && sel[b] > key) {
+      sel[b + 1] = sel[b];
+      --b;
+    }
+    sel[b + 1] = key;
+  }
+  int32_t* out = lists + v * L;
+  for (int a = 0; a < L; ++a) out[a] = (int32_t)sel[a];
+  prio[v] = philox_block(seed, round, g, kTagPrio, 0u).x;
+}
+
+cudaError_t launch_assign_lists(uint64_t seed, int32_t round, const int32_t* gid, int64_t n, int64_t P,
+                                int32_t L, int32_t* lists, uint32_t* prio, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + 127) / 128);
+  if (L <= 32)
+    k_assign_lists<32><<<blocks, 128, 0, s>>>(seed, round, gid, n, P, L, lists, prio);
+  else if (L <= 128)
+    k_assign_lists<128><<<blocks, 128, 0, s>>>(seed, round, gid, n, P, L, lists, prio);
+  else
+    k_assign_lists<kMaxL><<<blocks, 128, 0, s>>>(seed, round, gid, n, P, L, lists, prio);
+  return cudaGetLastError();
+}
+
+}  // namespace picasso

@@ -1,0 +1,280 @@
+"""Python binding of libpicasso (ctypes).  Argument marshalling only: every
+step of the Picasso round runs in the library's CUDA kernels; torch supplies
+device memory and the current stream.  There is no CPU fallback -- if the
+library is missing this module raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpicasso.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "picasso.h")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_INTERNAL, ERR_UNSUPPORTED, ERR_STATE = range(9)
+ALGOS = {"auto": 0, "allpairs": 1, "bucket": 2}
+
+
+class PicassoError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib().picasso_strerror(status).decode() if _LIB is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("palette_num", ctypes.c_int64),
+        ("palette_den", ctypes.c_int64),
+        ("alpha", ctypes.c_double),
+        ("conflict_algo", ctypes.c_int32),
+        ("max_rounds", ctypes.c_int32),
+        ("byte_budget", ctypes.c_int64),
+    ]
+
+
+class CSR(ctypes.Structure):
+    _fields_ = [("d_off", ctypes.c_void_p), ("d_col", ctypes.c_void_p), ("n_rows", ctypes.c_int64),
+                ("nnz", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("round", ctypes.c_int32),
+        ("n_total", ctypes.c_int64),
+        ("n_round", ctypes.c_int64),
+        ("P", ctypes.c_int64),
+        ("L", ctypes.c_int32),
+        ("base", ctypes.c_int64),
+        ("nnz", ctypes.c_int64),
+        ("n_extra", ctypes.c_int64),
+        ("colored", ctypes.c_int64),
+        ("colors_used", ctypes.c_int64),
+        ("peak_bytes", ctypes.c_int64),
+        ("conflict_algo_used", ctypes.c_int32),
+        ("jp_sweeps", ctypes.c_int32),
+        ("max_bucket", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_pi64 = ctypes.POINTER(ctypes.c_int64)
+_pi32 = ctypes.POINTER(ctypes.c_int32)
+
+_SIGS = {
+    "picasso_config_default": [ctypes.POINTER(Config)],
+    "picasso_pack": [_vp, _i64, _i32, _vp, _vp],
+    "picasso_init": [ctypes.POINTER(_vp), ctypes.POINTER(Config), _vp, _i64, _i32, _vp],
+    "picasso_round_params": [_vp, _pi64, _pi32, _pi64],
+    "picasso_assign_lists": [_vp, _i64, _i32, _i64],
+    "picasso_build_conflicts": [_vp, ctypes.POINTER(CSR)],
+    "picasso_color": [_vp, _pi64],
+    "picasso_carry": [_vp, _pi64],
+    "picasso_round": [_vp, _pi64],
+    "picasso_run": [_vp, _vp, _pi32],
+    "picasso_get_colors": [_vp, _vp],
+    "picasso_get_round": [_vp, _vp, _vp, _vp],
+    "picasso_get_runs": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _pi64],
+    "picasso_copy_csr": [_vp, _vp, _vp],
+    "picasso_copy_runs": [_vp, _vp, _vp, _vp],
+    "picasso_get_stats": [_vp, ctypes.POINTER(Stats)],
+    "picasso_philox_draws": [ctypes.c_uint64, _i32, _i64, ctypes.c_uint32, ctypes.c_uint32, _i32, _vp, _vp],
+    "picasso_destroy": [_vp],
+}
+
+
+def header_symbols(path: str = HEADER):
+    """Names of the functions include/picasso.h declares."""
+    text = open(path).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(picasso_\w+)\s*\(", text, re.M)))
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libpicasso.so not built ({LIB_PATH}); run paper_2401_06713_b300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.picasso_strerror.argtypes = [ctypes.c_int]
+        L.picasso_strerror.restype = ctypes.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def lib():
+    return _lib()
+
+
+def _ck(status: int, where: str):
+    if status != OK:
+        raise PicassoError(status, where)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def pack(codes: torch.Tensor, stream=None) -> torch.Tensor:
+    """uint8 codes [n, q] (0=I 1=X 2=Y 3=Z) on the GPU -> symplectic words
+    int64 [n, 2] (bit patterns of uint64 x, z)."""
+    assert codes.is_cuda and codes.dtype == torch.uint8 and codes.dim() == 2
+    codes = codes.contiguous()
+    n, q = codes.shape
+    xz = torch.empty((n, 2), dtype=torch.int64, device=codes.device)
+    _ck(_lib().picasso_pack(_ptr(codes), n, q, _ptr(xz), _stream(stream)), "picasso_pack")
+    return xz
+
+
+def philox_draws(seed: int, rnd: int, gid: int, tag: int, i0: int, count: int, device="cuda") -> torch.Tensor:
+    out = torch.empty(count, dtype=torch.int32, device=device)
+    _ck(_lib().picasso_philox_draws(seed, rnd, gid, tag, i0, count, _ptr(out), _stream()), "picasso_philox_draws")
+    return out
+
+
+class Picasso:
+    """A context over packed strings ``xz`` (int64 [n, 2] on the GPU)."""
+
+    def __init__(self, xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
+                 algo: str = "auto", max_rounds: int = 100000, byte_budget: int = 0, stream=None):
+        assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2
+        self.xz = xz.contiguous()
+        self.n = int(xz.shape[0])
+        self.q = q
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg = Config()
+        _ck(_lib().picasso_config_default(ctypes.byref(cfg)), "picasso_config_default")
+        cfg.seed = seed
+        cfg.palette_num, cfg.palette_den = palette
+        cfg.alpha = alpha
+        cfg.conflict_algo = ALGOS[algo]
+        cfg.max_rounds = max_rounds
+        cfg.byte_budget = byte_budget
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        _ck(_lib().picasso_init(ctypes.byref(h), ctypes.byref(cfg), _ptr(self.xz), self.n, q,
+                                ctypes.c_void_p(self.stream.cuda_stream)), "picasso_init")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib().picasso_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- Alg. 1 steps
+    def round_params(self):
+        P, L, b = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+        _ck(_lib().picasso_round_params(self.h, ctypes.byref(P), ctypes.byref(L), ctypes.byref(b)),
+            "picasso_round_params")
+        return int(P.value), int(L.value), int(b.value)
+
+    def assign_lists(self, P: int, L: int, base: int):
+        _ck(_lib().picasso_assign_lists(self.h, P, L, base), "picasso_assign_lists")
+
+    def build_conflicts(self):
+        csr = CSR()
+        _ck(_lib().picasso_build_conflicts(self.h, ctypes.byref(csr)), "picasso_build_conflicts")
+        return int(csr.n_rows), int(csr.nnz)
+
+    def color(self) -> int:
+        k = ctypes.c_int64()
+        _ck(_lib().picasso_color(self.h, ctypes.byref(k)), "picasso_color")
+        return int(k.value)
+
+    def carry(self) -> int:
+        k = ctypes.c_int64()
+        _ck(_lib().picasso_carry(self.h, ctypes.byref(k)), "picasso_carry")
+        return int(k.value)
+
+    def round(self) -> int:
+        k = ctypes.c_int64()
+        _ck(_lib().picasso_round(self.h, ctypes.byref(k)), "picasso_round")
+        return int(k.value)
+
+    def run(self, out: torch.Tensor | None = None):
+        """All rounds; returns (colors int32 [n] on the GPU, rounds)."""
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.int32, device=self.xz.device)
+        r = ctypes.c_int32()
+        _ck(_lib().picasso_run(self.h, _ptr(out), ctypes.byref(r)), "picasso_run")
+        return out, int(r.value)
+
+    # -- inspection
+    def colors(self) -> torch.Tensor:
+        out = torch.empty(self.n, dtype=torch.int32, device=self.xz.device)
+        _ck(_lib().picasso_get_colors(self.h, _ptr(out)), "picasso_get_colors")
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        _ck(_lib().picasso_get_stats(self.h, ctypes.byref(s)), "picasso_get_stats")
+        return s.as_dict()
+
+    def round_state(self, L: int | None = None):
+        """(gid int32 [n_l], lists int32 [n_l, L] round-local, prio int32 [n_l])."""
+        st = self.stats()
+        n = st["n_round"]
+        L = st["L"] if L is None else L
+        dev = self.xz.device
+        gid = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        lists = torch.empty((max(n, 1), max(L, 1)), dtype=torch.int32, device=dev)
+        prio = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        _ck(_lib().picasso_get_round(self.h, _ptr(gid), _ptr(lists), _ptr(prio)), "picasso_get_round")
+        return gid[:n], lists[:n, :L], prio[:n]
+
+    def csr(self):
+        st = self.stats()
+        n, nnz = st["n_round"], st["nnz"]
+        dev = self.xz.device
+        off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+        _ck(_lib().picasso_copy_csr(self.h, _ptr(off), _ptr(col)), "picasso_copy_csr")
+        return off, col[:nnz]
+
+    def runs(self):
+        st = self.stats()
+        n, L, nx = st["n_round"], st["L"], st["n_extra"]
+        dev = self.xz.device
+        runoff = torch.empty(n * L + 1, dtype=torch.int64, device=dev)
+        xoff = torch.empty(n * L + 1, dtype=torch.int64, device=dev)
+        xcol = torch.empty(max(nx, 1), dtype=torch.int32, device=dev)
+        _ck(_lib().picasso_copy_runs(self.h, _ptr(runoff), _ptr(xoff), _ptr(xcol)), "picasso_copy_runs")
+        return runoff, xoff, xcol[:nx]
+
+
+def color_strings(codes: torch.Tensor, seed: int = 0, palette=(1, 8), alpha: float = 2.0, algo: str = "auto"):
+    """Convenience: pack + all rounds.  Returns (colors int32 [n], rounds, stats)."""
+    xz = pack(codes)
+    with Picasso(xz, codes.shape[1], seed=seed, palette=palette, alpha=alpha, algo=algo) as p:
+        colors, rounds = p.run()
+        return colors, rounds, p.stats()

@@ -1,0 +1,285 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer work throughout, so every comparison is bit-exact: Philox draws,
+packed words, lists, priorities, conflict CSR (row offsets, color-major
+columns, run offsets, side list), the round's coloring and whole runs of
+Alg. 1.  At the full workload sizes the oracle checks sampled rows exactly
+and the whole coloring through properties that hold at any size.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2401_06713_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_2401_06713_b300 import build, picasso
+
+    build.build()
+    assert torch.cuda.is_available()
+    return picasso
+
+
+def _xz(pc, chars):
+    return pc.pack(torch.from_numpy(np.ascontiguousarray(chars)).cuda())
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+# ------------------------------------------------------------------ generators
+def test_philox_draws(pc, orc):
+    for (seed, rnd, gid, tag) in [(0, 1, 0, 1), (0xDEADBEEF12345678, 7, 123456, 2), (5, 3, (1 << 33) + 9, 1)]:
+        got = _u32(pc.philox_draws(seed, rnd, gid, tag, 0, 64))
+        ref = [orc.draw_u32(seed, rnd, gid, tag, i) for i in range(64)]
+        assert got.tolist() == ref
+    got = _u32(pc.philox_draws(9, 2, 77, 1, 1000, 8))
+    assert got.tolist() == [orc.draw_u32(9, 2, 77, 1, 1000 + i) for i in range(8)]
+
+
+@pytest.mark.parametrize("q", [1, 13, 20, 48, 64])
+def test_pack_words(pc, orc, q):
+    chars = synth.pauli_uniform(777, q, seed=q)
+    xz = _xz(pc, chars).cpu().numpy().view(np.uint64)
+    bits = np.uint64(1) << np.arange(q, dtype=np.uint64)
+    x = (((chars == 1) | (chars == 2)).astype(np.uint64) * bits).sum(1, dtype=np.uint64)
+    z = (((chars == 3) | (chars == 2)).astype(np.uint64) * bits).sum(1, dtype=np.uint64)
+    assert np.array_equal(xz[:, 0], x) and np.array_equal(xz[:, 1], z)
+    # the packed commutation test agrees with the oracle's 3-bit predicate
+    enc = orc.encode3(chars)
+    rng = np.random.default_rng(q)
+    for _ in range(300):
+        u, v = rng.integers(0, 777, 2)
+        par = bin(int((xz[u, 0] & xz[v, 1]) ^ (xz[u, 1] & xz[v, 0]))).count("1") % 2
+        assert (par == 0) == orc.commute3(enc[u], enc[v])
+
+
+@pytest.mark.parametrize("n,P,L", [(2000, 250, 16), (5000, 7, 7), (300, 1000, 100), (150, 400, 300), (3, 1, 1)])
+def test_lists_and_priorities(pc, orc, n, P, L):
+    chars = synth.pauli_uniform(n, 8, seed=1)
+    with pc.Picasso(_xz(pc, chars), 8, seed=42) as p:
+        p.assign_lists(P, L, 17)
+        gid, lists, prio = p.round_state()
+        lists = lists.cpu().numpy().astype(np.int64)
+        ref = orc.draw_lists(42, 1, np.arange(n), P, L, 0)
+        assert np.array_equal(lists, ref)
+        assert np.array_equal(_u32(prio), orc.priorities(42, 1, range(n)))
+        assert np.array_equal(gid.cpu().numpy(), np.arange(n))
+
+
+# ------------------------------------------------------------------ conflict graph
+def _check_build(pc, orc, chars, seed, P, L, algo):
+    n = len(chars)
+    enc = orc.encode3(chars)
+    lists = orc.draw_lists(seed, 1, np.arange(n), P, L, 0)
+    off_r, col_r = orc.conflict_csr(enc, lists)
+    with pc.Picasso(_xz(pc, chars), chars.shape[1], seed=seed, algo=algo) as p:
+        p.assign_lists(P, L, 0)
+        n_rows, nnz = p.build_conflicts()
+        assert (n_rows, nnz) == (n, len(col_r))
+        off, col = p.csr()
+        assert np.array_equal(off.cpu().numpy(), off_r)
+        assert np.array_equal(col.cpu().numpy(), col_r)
+        runoff, xoff, xcol = p.runs()
+        runoff = runoff.cpu().numpy()
+        xoff = xoff.cpu().numpy()
+        xcol = xcol.cpu().numpy()
+        # run k of row u holds the entries whose smallest shared color is c_k
+        rows = np.arange(n)
+        side, side_len = orc.side_rows(enc, lists, rows)
+        assert xoff[0] == 0 and xoff[-1] == sum(len(s) for s in side)
+        for u in rows:
+            if u < 150:
+                for k in range(L):
+                    seg = col_r[runoff[u * L + k]:runoff[u * L + k + 1]]
+                    assert all(orc.min_shared(lists[u], lists[v]) == lists[u][k] for v in seg)
+            assert runoff[u * L] == off_r[u]
+            got_side = xcol[xoff[u * L]:xoff[(u + 1) * L]]
+            assert np.array_equal(got_side, side[u])
+            assert np.array_equal(np.diff(xoff[u * L:(u + 1) * L + 1]), side_len[u])
+        st = p.stats()
+        assert st["conflict_algo_used"] == pc.ALGOS[algo] or algo == "auto"
+
+
+@pytest.mark.parametrize("algo", ["allpairs", "bucket"])
+def test_conflict_workload_small(pc, orc, algo):
+    # n=2000 strings on q=20 qubits, uniform I/X/Y/Z, P=n/8, L=ceil(2 ln n)
+    _check_build(pc, orc, synth.pauli_uniform(2000, 20, seed=0), 0, 250, 16, algo)
+
+
+@pytest.mark.parametrize("algo", ["allpairs", "bucket"])
+@pytest.mark.parametrize("n,q,P,L", [(1, 5, 3, 2), (2, 3, 2, 1), (33, 64, 5, 3), (1000, 48, 40, 6),
+                                     (777, 20, 97, 21), (2500, 64, 30, 30)])
+def test_conflict_shapes(pc, orc, algo, n, q, P, L):
+    _check_build(pc, orc, synth.pauli_weighted(n, q, 0.3, seed=n + q), 3, P, L, algo)
+
+
+def test_conflict_identity_and_duplicates(pc, orc):
+    chars = synth.pauli_weighted(600, 24, 0.2, seed=9)
+    chars[:50] = 0           # identity strings commute with everything
+    chars[50:100] = chars[100]  # duplicated strings commute with each other
+    for algo in ("allpairs", "bucket"):
+        _check_build(pc, orc, chars, 1, 60, 8, algo)
+
+
+def test_conflict_weighted_mid(pc, orc):
+    # the weighted law at n=6000, q=48 (P=n/8, alpha=2): bucket path, exact
+    n = 6000
+    P, L = orc.round_params(n, 1, 8, 2.0)
+    _check_build(pc, orc, synth.pauli_weighted(n, 48, 0.25, seed=4), 7, P, L, "auto")
+
+
+def test_budget_rejects_before_allocation(pc):
+    chars = synth.pauli_uniform(2000, 20, seed=0)
+    with pc.Picasso(_xz(pc, chars), 20, seed=0, byte_budget=1000) as p:
+        p.assign_lists(250, 16, 0)
+        with pytest.raises(pc.PicassoError) as e:
+            p.build_conflicts()
+        assert e.value.status == pc.ERR_BUDGET
+        # the context stays usable: lift nothing, just re-run with a new one
+    with pc.Picasso(_xz(pc, chars), 20, seed=0) as p:
+        p.assign_lists(250, 16, 0)
+        assert p.build_conflicts()[1] > 0
+
+
+# ------------------------------------------------------------------ coloring
+@pytest.mark.parametrize("algo", ["allpairs", "bucket"])
+def test_round_coloring_exact(pc, orc, algo):
+    n, q, P, L, seed = 3000, 48, 375, 17, 11
+    chars = synth.pauli_weighted(n, q, 0.25, seed=2)
+    enc = orc.encode3(chars)
+    lists = orc.draw_lists(seed, 1, np.arange(n), P, L, 0)
+    off_r, col_r = orc.conflict_csr(enc, lists)
+    ref = orc.color_greedy(seed, 1, np.arange(n), lists, off_r, col_r, P, 0)
+    with pc.Picasso(_xz(pc, chars), q, seed=seed, algo=algo) as p:
+        p.assign_lists(P, L, 0)
+        p.build_conflicts()
+        k = p.color()
+        got = p.colors().cpu().numpy()
+        assert k == int((ref >= 0).sum())
+        assert np.array_equal(got, ref)
+
+
+def _run_both(pc, orc, chars, seed, num, den, alpha, algo="auto"):
+    ref, rounds, stats = orc.run(chars, seed, num, den, alpha)
+    with pc.Picasso(_xz(pc, chars), chars.shape[1], seed=seed, palette=(num, den), alpha=alpha, algo=algo) as p:
+        got, r = p.run()
+        got = got.cpu().numpy()
+        assert r == rounds
+        assert np.array_equal(got, ref)
+        assert p.stats()["colors_used"] == int(stats[:, 1].sum())
+    return ref
+
+
+def test_run_workload_small(pc, orc):
+    # n=2000, q=20 uniform, P=n/8, alpha=2, seed 0: every round, every color
+    _run_both(pc, orc, synth.pauli_uniform(2000, 20, seed=0), 0, 1, 8, 2.0)
+
+
+@pytest.mark.parametrize("algo", ["allpairs", "bucket"])
+def test_run_weighted(pc, orc, algo):
+    _run_both(pc, orc, synth.pauli_weighted(4000, 48, 0.25, seed=1), 5, 1, 8, 2.0, algo)
+
+
+def test_run_throughput_law_small(pc, orc):
+    # the n=1M law (q=64, p=0.25, P=n/16, alpha=1.5) at a size the oracle runs
+    _run_both(pc, orc, synth.pauli_weighted(5000, 64, 0.25, seed=3), 0, 1, 16, 1.5)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 257])
+def test_run_edge_sizes(pc, orc, n):
+    _run_both(pc, orc, synth.pauli_uniform(n, 6, seed=n), 2, 1, 8, 2.0)
+
+
+def test_run_all_identity(pc, orc):
+    # G' is complete: each round colors exactly min(P, ...) vertices
+    chars = np.zeros((300, 10), dtype=np.uint8)
+    _run_both(pc, orc, chars, 1, 1, 8, 2.0)
+
+
+def test_run_aggressive_small(pc, orc):
+    # the paper's aggressive mode (P = 3%, alpha = 30) on a small set
+    _run_both(pc, orc, synth.pauli_weighted(1500, 24, 0.3, seed=8), 4, 3, 100, 30.0)
+
+
+# ------------------------------------------------------------------ full sizes
+def _enc_np(orc, chars):
+    return orc.encode3(chars)
+
+
+def _anticommute_pairs(enc, a, b):
+    x = np.bitwise_and(enc[a], enc[b])
+    return (np.bitwise_count(x).sum(axis=1) % 2) == 1
+
+
+def _check_cliques(enc, colors):
+    """Every color class is a clique of G (mutually anticommuting)."""
+    order = np.argsort(colors, kind="stable")
+    cs = colors[order]
+    n = len(cs)
+    d = 1
+    while True:
+        same = cs[d:] == cs[:-d] if d < n else np.zeros(0, bool)
+        if not same.any():
+            break
+        a = order[:-d][same]
+        b = order[d:][same]
+        assert _anticommute_pairs(enc, a, b).all()
+        d += 1
+
+
+def _full_size(pc, orc, n, q, p_w, num, den, alpha, seed, samples):
+    chars = synth.pauli_weighted(n, q, p_w, seed=seed)
+    enc = _enc_np(orc, chars)
+    P, L = orc.round_params(n, num, den, alpha)
+    rng = np.random.default_rng(seed + 1)
+    rows = np.sort(rng.choice(n, samples, replace=False))
+    with pc.Picasso(_xz(pc, chars), q, seed=seed, palette=(num, den), alpha=alpha) as p:
+        P2, L2, b = p.round_params()
+        assert (P2, L2, b) == (P, L, 0)
+        p.assign_lists(P, L, 0)
+        p.build_conflicts()
+        off, col = p.csr()
+        off = off.cpu().numpy()
+        # the oracle draws every list and priority itself
+        lists_all = orc.draw_lists(seed, 1, np.arange(n), P, L, 0)
+        prio_ref = orc.priorities(seed, 1, np.arange(n))
+        _, glists, gprio = p.round_state()
+        assert np.array_equal(glists.cpu().numpy().astype(np.int64), lists_all)
+        assert np.array_equal(_u32(gprio), prio_ref)
+        lens, ref_rows = orc.conflict_rows(enc, lists_all, rows)
+        for i, u in enumerate(rows):
+            got = col[off[u]:off[u + 1]].cpu().numpy()
+            assert np.array_equal(got, ref_rows[i])
+        p.color()
+        c1 = p.colors().cpu().numpy()
+        prio = prio_ref.astype(np.uint64)
+        # first fit in priority order at every sampled vertex
+        for i, u in enumerate(rows):
+            nb = ref_rows[i]
+            key_u = (int(prio[u]) << 32) | int(u)
+            earlier = [v for v in nb if ((int(prio[v]) << 32) | int(v)) < key_u]
+            taken = {int(c1[v]) for v in earlier if c1[v] >= 0}
+            want = next((int(c) for c in lists_all[u] if int(c) not in taken), -1)
+            assert int(c1[u]) == want
+        p.carry()
+        colors, rounds = p.run()
+        colors = colors.cpu().numpy()
+    assert (colors >= 0).all()
+    _check_cliques(enc, colors)
+    return colors, rounds
+
+
+def test_full_size_n100k(pc, orc):
+    # n=100,000, q=48, p=0.25, P=n/8, alpha=2
+    _full_size(pc, orc, 100_000, 48, 0.25, 1, 8, 2.0, 0, 120)
+
+
+def test_full_size_n1m(pc, orc):
+    # n=1,000,000, q=64, p=0.25, P=n/16, alpha=1.5 (the throughput workload)
+    _full_size(pc, orc, 1_000_000, 64, 0.25, 1, 16, 1.5, 0, 24)
