@@ -114,9 +114,24 @@ def test_conflict_workload_small(pc, orc, algo):
 
 @pytest.mark.parametrize("algo", ["allpairs", "bucket"])
 @pytest.mark.parametrize("n,q,P,L", [(1, 5, 3, 2), (2, 3, 2, 1), (33, 64, 5, 3), (1000, 48, 40, 6),
-                                     (777, 20, 97, 21), (2500, 64, 30, 30)])
+                                     (777, 20, 97, 21), (2000, 64, 30, 30)])
 def test_conflict_shapes(pc, orc, algo, n, q, P, L):
     _check_build(pc, orc, synth.pauli_weighted(n, q, 0.3, seed=n + q), 3, P, L, algo)
+
+
+def test_bucket_cap_reported(pc):
+    # every vertex holds all P colors: 2500 members per bucket exceed the
+    # bucket join's cap, which says so; AUTO then takes the all-pairs path
+    chars = synth.pauli_weighted(2500, 64, 0.3, seed=1)
+    with pc.Picasso(_xz(pc, chars), 64, seed=3, algo="bucket") as p:
+        p.assign_lists(30, 30, 0)
+        with pytest.raises(pc.PicassoError) as e:
+            p.build_conflicts()
+        assert e.value.status == pc.ERR_UNSUPPORTED
+    with pc.Picasso(_xz(pc, chars), 64, seed=3, algo="auto") as p:
+        p.assign_lists(30, 30, 0)
+        p.build_conflicts()
+        assert p.stats()["conflict_algo_used"] == pc.ALGOS["allpairs"]
 
 
 def test_conflict_identity_and_duplicates(pc, orc):
