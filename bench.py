@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the Picasso round hot path on B300.
+
+A step is one whole run of Alg. 1 (pack the strings, then every round: list
+assignment, conflict build, coloring, carry) over n = 1,000,000 synthetic
+Pauli strings on q = 64 qubits (each qubit non-identity w.p. 0.25, X/Y/Z
+equiprobable), P = n/16, alpha = 1.5, inputs resident in HBM.
+
+  value   colored strings/s over the whole job (all ranks)
+  e2e     the same through the C ABI from pinned host codes (host->device
+          copy of the codes and device->host copy of the colors inside the
+          timed region)
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+this host's cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT, Q, P_W, NUM, DEN, ALPHA = 1_000_000, 64, 0.25, 1, 16, 1.5
+METRIC = "pair tests/s (conflict build) and colored strings/s at n=1M; colors, peak bytes"
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n):
+    return {"workload": f"picasso n={n} q={Q} p={P_W} P=n/{DEN} alpha={ALPHA}", "n": n, "q": Q,
+            "weight_p": P_W, "palette": f"{NUM}/{DEN}", "alpha": ALPHA, "seed": "rank",
+            "l2": "working set > L2 (round-1 conflict CSR is ~14 GB); no explicit flush"}
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={SMI_FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------- CPU oracle timing
+def oracle_sample(n, seed, budget_s, threads=None):
+    """Time the oracle's round-1 conflict rows for a sample of vertices.
+    Returns (pair tests/s, rows, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+    from paper_2401_06713_b300 import synth
+
+    threads = threads or oracle.default_threads()
+    chars = synth.pauli_weighted(n, Q, P_W, seed=seed)
+    P, L = oracle.round_params(n, NUM, DEN, ALPHA)
+    enc = oracle.encode3(chars)
+    lists = oracle.draw_lists(seed, 1, np.arange(n), P, L, 0)
+    rng = np.random.default_rng(seed)
+    rows_done, secs = 0, 0.0
+    batch = threads
+    while secs < budget_s:
+        rows = rng.choice(n, batch, replace=False)
+        t0 = time.perf_counter()
+        oracle.conflict_rows(enc, lists, rows, threads=threads)
+        secs += time.perf_counter() - t0
+        rows_done += batch
+    return rows_done * (n - 1) / secs, rows_done, secs, threads
+
+
+def oracle_strings_per_s(pairs_per_s, round_sizes, n):
+    """Extrapolate the oracle's whole-run rate: round l tests n_l (n_l - 1)
+    ordered pairs (the oracle builds each row in full)."""
+    work = sum(m * (m - 1) for m in round_sizes)
+    return n / (work / pairs_per_s)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2401_06713_b300 import build as pbuild
+    from paper_2401_06713_b300 import picasso, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pbuild.build()
+    n = args.n
+    chars = synth.pauli_weighted(n, Q, P_W, seed=rank)
+    codes_host = torch.from_numpy(chars).pin_memory()
+    codes = codes_host.cuda()
+    stream = torch.cuda.current_stream()
+
+    def step(codes_dev, out=None):
+        xz = picasso.pack(codes_dev)
+        with picasso.Picasso(xz, Q, seed=rank, palette=(NUM, DEN), alpha=ALPHA) as p:
+            colors, rounds = p.run(out)
+            st = p.stats()
+        return colors, rounds, st
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        colors, rounds, st = step(codes)
+    torch.cuda.synchronize()
+
+    # device-resident timed region
+    launches0 = picasso.kernel_launches()
+    stats = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            colors, rounds, st = step(codes)
+            stats.append(st)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        barrier()
+    launches = picasso.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+
+    # end to end: pinned host codes in, host colors out
+    colors_host = torch.empty(n, dtype=torch.int32).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dev_codes = codes_host.to("cuda", non_blocking=True)
+        c, _, _ = step(dev_codes)
+        colors_host.copy_(c, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+
+    def allmax(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms = allmax(ms)
+    ms_e2e = allmax(ms_e2e)
+    colors_np = colors.cpu().numpy()
+    assert (colors_np >= 0).all(), "uncolored vertices after a full run"
+    st = stats[-1]
+    # the library's counters are per context and there is one context per step
+    per_step = {k: st[k] for k in ("t_assign_ms", "t_build_ms", "t_color_ms", "t_carry_ms", "t_pairs_ms")}
+    steps_ms = ms / args.steps
+    value = world * n / (steps_ms / 1e3)
+    pair_rate = st["logical_pairs"] / (st["t_build_ms"] / 1e3)
+
+    peaks, peak_src = measured_peaks()
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2032.0)
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    # pair-test kernel: one POPC per tested pair (parity of popc(lo ^ hi));
+    # POPC issues at 16 lanes/clk/SM
+    peak_pairs = n_sm * sm_mhz * 1e6 * 16
+    achieved = st["tested_pairs"] / (st["t_pairs_ms"] / 1e3)
+    roofline = {"bound": "alu", "kernel": "k_bucket_pairs (count+fill)", "achieved": achieved / 1e9,
+                "peak": peak_pairs / 1e9, "unit": "Gpair-tests/s", "frac": achieved / peak_pairs,
+                "traffic": None,
+                "peak_source": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median under load) x 16 POPC/clk/SM",
+                "avg_launch_ms": st["t_pairs_ms"] / max(st["pairs_launches"], 1),
+                "tested_pairs_per_launch": st["tested_pairs"] / max(st["pairs_launches"], 1)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # round sizes of this run (the oracle and GPU agree on them)
+        sizes = round_sizes_from(colors_np, st)
+        pps, rows, secs, threads = oracle_sample(n, 0, args.cpu_budget)
+        cpu = {"value": oracle_strings_per_s(pps, sizes, n), "unit": "strings/s", "cores": threads,
+               "kind": "oracle",
+               "sample": f"round-1 conflict rows of {rows} random vertices at n={n} ({secs:.1f} s); "
+                         f"whole run extrapolated over the rounds' n_l(n_l-1) ordered pairs",
+               "pair_tests_per_s": pps}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "strings/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": steps_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64/i32 (bitwise integer)",
+        "data": "synthetic (seeded Pauli strings; the paper's molecules are not available)",
+        "config": dict(workload(n), parallelism=f"replicas{world}" if world > 1 else "single"),
+        "pair_tests_per_s": pair_rate, "colors": int(len(np.unique(colors_np))), "rounds": rounds,
+        "peak_bytes": st["peak_bytes"], "breakdown_ms_per_step": per_step,
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": world * n / (ms_e2e / args.steps / 1e3), "unit": "strings/s",
+                "h2d_bytes_per_step": n * Q, "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": launches, "clocks": clocks, "wall_s": t_wall,
+        "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def round_sizes_from(colors, st):
+    """n_l of every round, read off the palette ranges: colors of round l lie
+    in [base_l, base_l + P_l) and P_l = ceil(n_l * NUM / DEN)."""
+    import numpy as np
+
+    n = len(colors)
+    sizes = []
+    remaining = n
+    base = 0
+    while remaining > 0:
+        P = max(1, -(-remaining * NUM // DEN))
+        sizes.append(remaining)
+        done = int(((colors >= base) & (colors < base + P)).sum())
+        remaining -= done
+        base += P
+        if done == 0:
+            break
+    return sizes
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n = args.n
+    # round sizes follow from the oracle's own sample law: estimate them with a
+    # geometric tail measured on a small oracle run of the same law
+    import oracle
+    from paper_2401_06713_b300 import synth
+
+    small = 4000
+    _, _, st = oracle.run(synth.pauli_weighted(small, Q, P_W, seed=0), 0, NUM, DEN, ALPHA)
+    frac = [int(r[0]) / small for r in st]
+    sizes = [max(1, int(round(f * n))) for f in frac]
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(n, 0, min(args.cpu_budget, 3.0))
+    for _ in range(args.steps):
+        pps, rows, secs, threads = oracle_sample(n, 0, args.cpu_budget / max(args.steps, 1))
+        vals.append(oracle_strings_per_s(pps, sizes, n))
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "strings/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int (CPU oracle)",
+        "data": "synthetic", "config": workload(n),
+        "cpu_baseline": {"value": value, "unit": "strings/s", "cores": threads, "kind": "oracle",
+                         "sample": f"per step: round-1 conflict rows of random vertices at n={n}; whole run "
+                                   f"extrapolated with round sizes from an oracle run of the same law at "
+                                   f"n={small}"},
+        "e2e": {"value": value, "unit": "strings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="picasso", choices=["picasso", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -105,6 +105,18 @@ typedef struct {
   int32_t conflict_algo_used;
   int32_t jp_sweeps;   /* sweeps of the last color step                      */
   int64_t max_bucket;  /* largest color bucket of the last build             */
+  /* cumulative since picasso_init (CUDA events on the context's stream) */
+  int32_t rounds_done;
+  double t_assign_ms;   /* list assignment                                   */
+  double t_build_ms;    /* conflict build (buckets, count, scans, fill)      */
+  double t_color_ms;    /* coloring sweeps + color write-back                */
+  double t_carry_ms;    /* compaction of the uncolored vertices              */
+  double t_pairs_ms;    /* the pair-test kernels alone (count and fill)      */
+  int64_t pairs_launches;     /* launches of the pair-test kernels           */
+  int64_t logical_pairs;      /* sum over builds of n_l (n_l - 1) / 2        */
+  int64_t tested_pairs;       /* sum over pair-kernel launches of the ordered
+                                 pairs it tested (bucket join: sum over
+                                 buckets of s (s - 1); all pairs: n (n - 1)) */
 } picasso_stats;
 
 /* Fill *cfg with the defaults: seed 0, P = n/8, alpha = 2 (the paper's normal
@@ -190,6 +202,9 @@ int picasso_get_stats(void* ctx, picasso_stats* out);
 int picasso_philox_draws(uint64_t seed, int32_t round, int64_t gid,
                          uint32_t tag, uint32_t i0, int32_t count,
                          uint32_t* d_out, void* stream);
+
+/* Process-wide count of kernels this library has launched (all contexts). */
+int picasso_kernel_launches(int64_t* out);
 
 int picasso_destroy(void* ctx);
 

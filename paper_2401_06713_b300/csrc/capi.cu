@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of libpicasso: context, round driver (Alg. 1) and
 // device-memory bookkeeping.  All device work is launched on the context's
 // stream; the host only computes the round parameters and reads back sizes.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -9,6 +10,14 @@
 #include "common.cuh"
 
 using namespace picasso;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+namespace picasso {
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace picasso
 
 namespace {
 
@@ -56,6 +65,12 @@ struct Ctx {
 
   std::unordered_map<void*, size_t> sizes;
   int64_t cur_bytes = 0, peak_bytes = 0;
+
+  // timing (CUDA events on s): ev[0..1] phase, ev[2..5] pair kernels
+  cudaEvent_t ev[6] = {};
+  int32_t rounds_done = 0;
+  double t_assign = 0, t_build = 0, t_color = 0, t_carry = 0, t_pairs = 0;
+  int64_t pairs_launches = 0, logical_pairs = 0, tested_pairs = 0;
 
   const uint64_t* round_xz() const { return xz ? xz : xz_user; }
 };
@@ -144,6 +159,24 @@ int check(Ctx* c) {
   return PICASSO_OK;
 }
 
+void phase_begin(Ctx* c) { cudaEventRecord(c->ev[0], c->s); }
+
+// Records the end event, waits for it and adds the elapsed time to *acc.
+cudaError_t phase_end(Ctx* c, double* acc) {
+  cudaError_t e = cudaEventRecord(c->ev[1], c->s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(c->ev[1]);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+  if (e == cudaSuccess) *acc += ms;
+  return e;
+}
+
+double elapsed(Ctx* c, int a, int b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) return 0.0;
+  return ms;
+}
+
 void params_for(const picasso_config& cfg, int64_t n, int64_t* P, int32_t* L) {
   int64_t p = (n * cfg.palette_num + cfg.palette_den - 1) / cfg.palette_den;
   if (p < 1) p = 1;
@@ -162,6 +195,7 @@ int build_conflicts(Ctx* c) {
   cudaStream_t s = c->s;
 
   uint32_t *cnt = nullptr, *xcnt = nullptr, *bcount = nullptr, *bcursor = nullptr, *dmax = nullptr;
+  unsigned long long* dsq = nullptr;
   int64_t* boff = nullptr;
   int32_t* bmem = nullptr;
   void* tmp = nullptr;
@@ -172,6 +206,7 @@ int build_conflicts(Ctx* c) {
     release(c, &bcount);
     release(c, &bcursor);
     release(c, &dmax);
+    release(c, &dsq);
     release(c, &boff);
     release(c, &bmem);
     release(c, (uint8_t**)&tmp);
@@ -206,12 +241,15 @@ int build_conflicts(Ctx* c) {
   TRY(alloc(c, &bcount, P));
   TRY(alloc(c, &boff, P + 1));
   TRY(alloc(c, &dmax, 2));
+  TRY(alloc(c, &dsq, 1));
   TRYC(cudaMemsetAsync(bcount, 0, sizeof(uint32_t) * P, s));
   TRYC(launch_bucket_hist(c->lists, n, L, bcount, s));
-  TRYC(launch_max_u32(bcount, P, dmax, s));
+  TRYC(launch_bucket_stats(bcount, P, dmax, dsq, s));
   TRYC(cudaMemcpyAsync(c->h_buf, dmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaMemcpyAsync(c->h_buf + 1, dsq, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
   const int64_t smax = (int64_t)(*(uint32_t*)c->h_buf);
+  const int64_t bucket_pairs = c->h_buf[1];
   c->max_bucket = smax;
   const bool bucket_ok = smax <= kBucketCap && P < kBucketMaxP;
   if (algo == PICASSO_CONFLICT_AUTO) algo = bucket_ok ? PICASSO_CONFLICT_BUCKET : PICASSO_CONFLICT_ALLPAIRS;
@@ -239,10 +277,15 @@ int build_conflicts(Ctx* c) {
     TRYC(launch_bucket_fill(c->lists, n, L, boff, bcursor, bmem, s));
     release(c, &bcursor);
     TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, s));
+    TRYC(cudaEventRecord(c->ev[2], s));
     TRYC(launch_bucket_pairs(a, boff, bmem, (int32_t)smax, false, s));
+    TRYC(cudaEventRecord(c->ev[3], s));
   } else {
+    TRYC(cudaEventRecord(c->ev[2], s));
     TRYC(launch_allpairs(a, false, s));
+    TRYC(cudaEventRecord(c->ev[3], s));
   }
+  const int64_t tested = algo == PICASSO_CONFLICT_BUCKET ? bucket_pairs : n * (n - 1);
   release(c, &bcount);
 
   TRY(alloc(c, &c->runoff, nl + 1));
@@ -274,12 +317,19 @@ int build_conflicts(Ctx* c) {
   a.xoff = c->xoff;
   a.col = c->col;
   a.xcol = c->xcol;
+  TRYC(cudaEventRecord(c->ev[4], s));
   if (algo == PICASSO_CONFLICT_BUCKET) {
     TRYC(launch_bucket_pairs(a, boff, bmem, (int32_t)smax, true, s));
   } else {
     TRYC(launch_allpairs(a, true, s));
   }
+  TRYC(cudaEventRecord(c->ev[5], s));
   TRYC(launch_row_offsets(c->runoff, n, L, c->off, s));
+  TRYC(cudaEventSynchronize(c->ev[5]));
+  c->t_pairs += elapsed(c, 2, 3) + elapsed(c, 4, 5);
+  c->pairs_launches += 2;
+  c->tested_pairs += 2 * tested;
+  c->logical_pairs += n * (n - 1) / 2;
   cleanup();
   c->nnz = nnz;
   c->nx = nx;
@@ -470,7 +520,9 @@ int picasso_init(void** out, const picasso_config* cfg, const uint64_t* d_xz, in
     delete c;
     return map_err(e);
   }
-  int st = alloc(c, &c->color, n);
+  int st = PICASSO_OK;
+  for (int i = 0; i < 6 && st == PICASSO_OK; ++i) st = map_err(cudaEventCreate(&c->ev[i]));
+  if (st == PICASSO_OK) st = alloc(c, &c->color, n);
   if (st == PICASSO_OK) st = alloc(c, &c->d_err, 4);
   if (st == PICASSO_OK) st = map_err(launch_fill_i32(c->color, n, -1, c->s));
   if (st != PICASSO_OK) {
@@ -511,7 +563,9 @@ int picasso_assign_lists(void* ctx, int64_t P, int32_t L, int64_t base) {
   c->base = base;
   ST(alloc(c, &c->lists, c->n * L));
   ST(alloc(c, &c->prio, c->n));
+  phase_begin(c);
   CK(launch_assign_lists(c->cfg.seed, c->round, c->gid, c->n, P, L, c->lists, c->prio, c->s));
+  CK(phase_end(c, &c->t_assign));
   c->assigned = true;
   return PICASSO_OK;
 }
@@ -522,7 +576,9 @@ int picasso_build_conflicts(void* ctx, picasso_csr* out) {
   if (!c->assigned) return PICASSO_ERR_STATE;
   free_color(c);
   free_build(c);
+  phase_begin(c);
   ST(build_conflicts(c));
+  CK(phase_end(c, &c->t_build));
   if (out) {
     out->d_off = c->off;
     out->d_col = c->col;
@@ -536,7 +592,9 @@ int picasso_color(void* ctx, int64_t* n_colored) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (!c->built) return PICASSO_ERR_STATE;
+  phase_begin(c);
   ST(color_round(c));
+  CK(phase_end(c, &c->t_color));
   if (n_colored) *n_colored = c->n_colored;
   return PICASSO_OK;
 }
@@ -545,7 +603,10 @@ int picasso_carry(void* ctx, int64_t* n_remaining) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (!c->colored_done) return PICASSO_ERR_STATE;
+  phase_begin(c);
   ST(carry_round(c));
+  CK(phase_end(c, &c->t_carry));
+  c->rounds_done += 1;
   if (n_remaining) *n_remaining = c->n;
   return PICASSO_OK;
 }
@@ -656,6 +717,21 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->conflict_algo_used = c->algo_used;
   out->jp_sweeps = c->sweeps;
   out->max_bucket = c->max_bucket;
+  out->rounds_done = c->rounds_done;
+  out->t_assign_ms = c->t_assign;
+  out->t_build_ms = c->t_build;
+  out->t_color_ms = c->t_color;
+  out->t_carry_ms = c->t_carry;
+  out->t_pairs_ms = c->t_pairs;
+  out->pairs_launches = c->pairs_launches;
+  out->logical_pairs = c->logical_pairs;
+  out->tested_pairs = c->tested_pairs;
+  return PICASSO_OK;
+}
+
+int picasso_kernel_launches(int64_t* out) {
+  if (!out) return PICASSO_ERR_INVALID_ARG;
+  *out = (int64_t)g_launches.load();
   return PICASSO_OK;
 }
 
@@ -671,6 +747,8 @@ int picasso_destroy(void* ctx) {
   release(c, &c->color);
   release(c, &c->d_err);
   cudaStreamSynchronize(c->s);
+  for (int i = 0; i < 6; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->h_buf) cudaFreeHost(c->h_buf);
   delete c;
   return PICASSO_OK;

@@ -66,6 +66,9 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// Process-wide launch counter (capi.cu); every launcher adds its launches.
+void count_launches(int k);
+
 // ---------------------------------------------------------------------------
 // Launchers (host functions defined in the kernel .cu files).
 // ---------------------------------------------------------------------------
@@ -103,7 +106,9 @@ cudaError_t launch_bucket_fill(const int32_t* lists, int64_t n, int32_t L, const
                                uint32_t* bcursor, int32_t* bmem, cudaStream_t s);
 cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err,
                                cudaStream_t s);
-cudaError_t launch_max_u32(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s);
+// out32[0] = max bucket size; out64[0] = sum over buckets of s (s - 1).
+cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out32,
+                                unsigned long long* out64, cudaStream_t s);
 cudaError_t launch_bucket_pairs(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
                                 int32_t smax, bool fill, cudaStream_t s);
 cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s);

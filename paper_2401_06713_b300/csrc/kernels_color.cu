@@ -31,6 +31,7 @@ __global__ void k_color_init(ColorArgs a, int32_t* __restrict__ work, int32_t* _
 cudaError_t launch_color_init(const ColorArgs& a, int32_t* work, int32_t* nwork, cudaStream_t s) {
   const int64_t blocks = (a.n + 255) / 256;
   k_color_init<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(a, work, nwork);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -101,6 +102,7 @@ cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const
   const int64_t want = (a.n + 7) / 8;
   const int64_t blocks = want < (int64_t)sms * 8 ? (want > 0 ? want : 1) : (int64_t)sms * 8;
   k_color_sweep<<<(unsigned)blocks, 256, 0, s>>>(a, work_in, nwork_in, work_out, nwork_out);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -119,6 +121,7 @@ cudaError_t launch_carry_flags(const uint32_t* word, int64_t n, const int32_t* g
                                uint32_t* flag, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_carry_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(word, n, gid, base, color, flag);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -138,6 +141,7 @@ cudaError_t launch_carry_gather(const uint32_t* flag, const int64_t* pos, int64_
                                 const uint64_t* xz, int32_t* gid_out, uint64_t* xz_out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_carry_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(flag, pos, n, gid, xz, gid_out, xz_out);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -154,6 +158,7 @@ cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t
                              cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_gather_xz<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xz_all, gid, n, xz_out);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -165,12 +170,14 @@ __global__ void k_fill_i32(int32_t* out, int64_t n, int32_t v, int32_t step) {
 cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_fill_i32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, 0, 1);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_i32(int32_t* out, int64_t n, int32_t v, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_fill_i32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, v, 0);
+  count_launches(1);
   return cudaGetLastError();
 }
 

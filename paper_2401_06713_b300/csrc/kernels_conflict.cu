@@ -42,6 +42,7 @@ cudaError_t launch_bucket_hist(const int32_t* lists, int64_t n, int32_t L, uint3
   if (total <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 148 * 16);
   k_bucket_hist<<<blocks, 256, 0, s>>>(lists, total, bcount);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -61,6 +62,7 @@ cudaError_t launch_bucket_fill(const int32_t* lists, int64_t n, int32_t L, const
   if (total <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 148 * 16);
   k_bucket_fill<<<blocks, 256, 0, s>>>(lists, total, L, boff, bcursor, bmem);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -104,22 +106,37 @@ __global__ void __launch_bounds__(512) k_bucket_sort(const int64_t* __restrict__
 cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, cudaStream_t s) {
   const unsigned blocks = (unsigned)std::min<int64_t>(P, 148 * 8);
   k_bucket_sort<<<blocks, 256, 0, s>>>(boff, P, bmem, err);
+  count_launches(1);
   return cudaGetLastError();
 }
 
-__global__ void k_max_u32(const uint32_t* __restrict__ in, int64_t n, uint32_t* out) {
+__global__ void k_bucket_stats(const uint32_t* __restrict__ in, int64_t n, uint32_t* out32,
+                               unsigned long long* out64) {
   uint32_t m = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    m = max(m, in[i]);
-  for (int d = 16; d; d >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+  unsigned long long q = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = in[i];
+    m = max(m, x);
+    q += (unsigned long long)x * (x > 0 ? x - 1 : 0);
+  }
+  for (int d = 16; d; d >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
+    q += __shfl_xor_sync(0xffffffffu, q, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out32, m);
+    atomicAdd(out64, q);
+  }
 }
 
-cudaError_t launch_max_u32(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
-  if (e != cudaSuccess || n <= 0) return e;
-  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 4);
-  k_max_u32<<<blocks, 256, 0, s>>>(in, n, out);
+cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out32, unsigned long long* out64,
+                                cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out32, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(out64, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess || P <= 0) return e;
+  const unsigned blocks = (unsigned)std::min<int64_t>((P + 255) / 256, 148 * 4);
+  k_bucket_stats<<<blocks, 256, 0, s>>>(bcount, P, out32, out64);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -361,6 +378,7 @@ cudaError_t launch_bucket_pairs(const ConflictArgs& a, const int64_t* boff, cons
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
   kern<<<(unsigned)blocks, kPairThreads, bytes, s>>>(a, boff, bmem, smax, hs_log2);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -473,6 +491,7 @@ cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const int64_t blocks = std::min<int64_t>((a.n + kApWarps - 1) / kApWarps, 148 * 8);
   kern<<<(unsigned)blocks, kApWarps * 32, bytes, s>>>(a);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -483,6 +502,7 @@ __global__ void k_row_offsets(const int64_t* __restrict__ runoff, int64_t n, int
 
 cudaError_t launch_row_offsets(const int64_t* runoff, int64_t n, int32_t L, int64_t* off, cudaStream_t s) {
   k_row_offsets<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(runoff, n, L, off);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ cudaError_t launch_pack(const uint8_t* codes, int64_t n, int32_t q, uint64_t* xz
   if (n <= 0) return cudaSuccess;
   const int64_t blocks = (n + 255) / 256;
   k_pack<<<(unsigned)blocks, 256, 0, s>>>(codes, n, q, xz);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -44,6 +45,7 @@ cudaError_t launch_philox_draws(uint64_t seed, int32_t round, int64_t gid, uint3
                                 int32_t count, uint32_t* out, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   k_philox_draws<<<(count + 255) / 256, 256, 0, s>>>(seed, round, gid, tag, i0, count, out);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -87,12 +89,14 @@ cudaError_t launch_assign_lists(uint64_t seed, int32_t round, const int32_t* gid
                                 int32_t L, int32_t* lists, uint32_t* prio, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n + 127) / 128);
-  if (L <= 32)
+  if (L <= 32) {
     k_assign_lists<32><<<blocks, 128, 0, s>>>(seed, round, gid, n, P, L, lists, prio);
-  else if (L <= 128)
+  } else if (L <= 128) {
     k_assign_lists<128><<<blocks, 128, 0, s>>>(seed, round, gid, n, P, L, lists, prio);
-  else
+  } else {
     k_assign_lists<kMaxL><<<blocks, 128, 0, s>>>(seed, round, gid, n, P, L, lists, prio);
+  }
+  count_launches(1);
   return cudaGetLastError();
 }
 

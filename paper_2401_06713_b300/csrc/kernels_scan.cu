@@ -80,17 +80,20 @@ cudaError_t scan_rec(const T* in, int64_t n, int64_t* out, int64_t* tmp, cudaStr
   const int64_t nb = nblocks(n);
   if (nb <= 1) {
     k_scan<T><<<1, kThreads, 0, s>>>(in, n, nullptr, out);
+    count_launches(1);
     return cudaGetLastError();
   }
   int64_t* partial = tmp;
   int64_t* partial_scan = tmp + nb;
   int64_t* rest = partial_scan + nb + 1;
   k_reduce<T><<<(unsigned)nb, kThreads, 0, s>>>(in, n, partial);
+  count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = scan_rec<int64_t>(partial, nb, partial_scan, rest, s);
   if (e != cudaSuccess) return e;
   k_scan<T><<<(unsigned)nb, kThreads, 0, s>>>(in, n, partial_scan, out);
+  count_launches(1);
   return cudaGetLastError();
 }
 }  // namespace

@@ -58,6 +58,15 @@ class Stats(ctypes.Structure):
         ("conflict_algo_used", ctypes.c_int32),
         ("jp_sweeps", ctypes.c_int32),
         ("max_bucket", ctypes.c_int64),
+        ("rounds_done", ctypes.c_int32),
+        ("t_assign_ms", ctypes.c_double),
+        ("t_build_ms", ctypes.c_double),
+        ("t_color_ms", ctypes.c_double),
+        ("t_carry_ms", ctypes.c_double),
+        ("t_pairs_ms", ctypes.c_double),
+        ("pairs_launches", ctypes.c_int64),
+        ("logical_pairs", ctypes.c_int64),
+        ("tested_pairs", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -89,6 +98,7 @@ _SIGS = {
     "picasso_copy_runs": [_vp, _vp, _vp, _vp],
     "picasso_get_stats": [_vp, ctypes.POINTER(Stats)],
     "picasso_philox_draws": [ctypes.c_uint64, _i32, _i64, ctypes.c_uint32, ctypes.c_uint32, _i32, _vp, _vp],
+    "picasso_kernel_launches": [_pi64],
     "picasso_destroy": [_vp],
 }
 
@@ -142,6 +152,13 @@ def pack(codes: torch.Tensor, stream=None) -> torch.Tensor:
     xz = torch.empty((n, 2), dtype=torch.int64, device=codes.device)
     _ck(_lib().picasso_pack(_ptr(codes), n, q, _ptr(xz), _stream(stream)), "picasso_pack")
     return xz
+
+
+def kernel_launches() -> int:
+    """Process-wide count of kernels libpicasso has launched."""
+    k = ctypes.c_int64()
+    _ck(_lib().picasso_kernel_launches(ctypes.byref(k)), "picasso_kernel_launches")
+    return int(k.value)
 
 
 def philox_draws(seed: int, rnd: int, gid: int, tag: int, i0: int, count: int, device="cuda") -> torch.Tensor:
