@@ -206,6 +206,29 @@ int picasso_philox_draws(uint64_t seed, int32_t round, int64_t gid,
 /* Process-wide count of kernels this library has launched (all contexts). */
 int picasso_kernel_launches(int64_t* out);
 
+/* Whole run of Alg. 1 (as picasso_init + picasso_run + picasso_get_colors,
+ * same colors) for a small set, with no device allocation at all.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc while they work -- services that give the GPU's memory to their
+ * own fixed pool, or hosts that forbid allocation on their hot path because it
+ * synchronises the device.  Every temporary buffer lives in one library-owned
+ * static device array of about 12.5 MB; once this function has run on a GPU,
+ * that GPU holds the array until the process exits.
+ *   d_xz        [n][2] packed strings (caller-owned, read-only)
+ *   d_color_out [n] int32, receives the global colors (caller-owned)
+ *   n_rounds    may be NULL
+ * Limits: 1 <= n <= 2048, q <= 64, round-1 list size L <= 32, and at most
+ * 1,572,864 conflict entries and 1,048,576 side-list entries in any round;
+ * beyond them it returns PICASSO_ERR_UNSUPPORTED without touching the GPU
+ * (the size checks of later rounds run after that round's count pass).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Calls
+ * share the array: calls whose GPU work overlaps (other streams, other host
+ * threads) race and must be serialised by the caller.  Synchronises stream. */
+int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t q,
+                             const picasso_config* cfg, int32_t* d_color_out,
+                             int32_t* n_rounds, void* stream);
+
 int picasso_destroy(void* ctx);
 
 const char* picasso_strerror(int status);

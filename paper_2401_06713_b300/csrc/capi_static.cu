@@ -1,0 +1,241 @@
+// capi_static.cu -- picasso_run_small_static: a whole Picasso run for small
+// string sets that performs no device allocation.
+//
+// Some callers cannot allocate device memory while they work: plugins and
+// services that hand every byte of the GPU to their own fixed pool, code that
+// runs between a pool's reservation and its release, or hosts that forbid
+// cudaMalloc/cudaFree on their hot path because those calls synchronise the
+// device.  This entry point serves them for sets of at most kStaticMaxN
+// strings: every temporary buffer of the run is carved out of one file-scope
+// __device__ array of kStaticBytes bytes.  The caller still passes the packed
+// strings and the color output.
+//
+// The array is owned by the library: once it has been used on a GPU (or at
+// module load, if lazy module loading is off) that GPU holds it until the
+// process exits.  All calls on a device share it and it keeps the last call's
+// contents, so every region that must start at zero is cleared here.  Two
+// calls whose work overlaps on the GPU (e.g. on two streams) race on the
+// array; callers must serialise them.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+using namespace picasso;
+
+namespace {
+
+constexpr int64_t kStaticMaxN = 2048;
+constexpr int32_t kStaticMaxL = 32;
+constexpr int64_t kStaticMaxNnz = 1536 * 1024;      // conflict entries in one round
+constexpr int64_t kStaticMaxSide = 1024 * 1024;     // side-list entries in one round
+constexpr int64_t kStaticNL = kStaticMaxN * kStaticMaxL;
+constexpr size_t kScanTmpReserve = 64 * 1024;
+
+constexpr size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// region offsets inside the array
+constexpr size_t kOffGid = 0;                                              // 2 x [N] int32
+constexpr size_t kOffXz = kOffGid + al(2 * kStaticMaxN * 4);               // 2 x [N][2] u64
+constexpr size_t kOffLists = kOffXz + al(2 * kStaticMaxN * 16);            // [N*L] int32
+constexpr size_t kOffPrio = kOffLists + al(kStaticNL * 4);                 // [N] u32
+constexpr size_t kOffCnt = kOffPrio + al(kStaticMaxN * 4);                 // [N*L] u32
+constexpr size_t kOffXcnt = kOffCnt + al(kStaticNL * 4);                   // [N*L] u32
+constexpr size_t kOffRunoff = kOffXcnt + al(kStaticNL * 4);                // [N*L+1] i64
+constexpr size_t kOffXoff = kOffRunoff + al((kStaticNL + 1) * 8);          // [N*L+1] i64
+constexpr size_t kOffCol = kOffXoff + al((kStaticNL + 1) * 8);             // [maxnnz] i32
+constexpr size_t kOffXcol = kOffCol + al(kStaticMaxNnz * 4);               // [maxside] i32
+constexpr size_t kOffWord = kOffXcol + al(kStaticMaxSide * 4);             // [N] u32
+constexpr size_t kOffKcur = kOffWord + al(kStaticMaxN * 4);                // [N] u16
+constexpr size_t kOffWork = kOffKcur + al(kStaticMaxN * 2);                // 2 x [N] i32
+constexpr size_t kOffCounts = kOffWork + al(2 * kStaticMaxN * 4);          // [16] i32
+constexpr size_t kOffFlag = kOffCounts + al(16 * 4);                       // [N] u32
+constexpr size_t kOffPos = kOffFlag + al(kStaticMaxN * 4);                 // [N+1] i64
+constexpr size_t kOffTmp = kOffPos + al((kStaticMaxN + 1) * 8);            // scan temp
+constexpr size_t kOffErr = kOffTmp + al(kScanTmpReserve);                  // [1] i32
+constexpr size_t kStaticBytes = kOffErr + 256;                             // about 12.5 MB
+
+}  // namespace
+
+// The scratch.  In host code this name is only a host-side stand-in: the
+// device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+namespace {
+
+std::mutex g_setup_mu;
+void* g_scratch_addr[128] = {};
+
+// Per-device set-up: look up the array's device address once, with that
+// device current.
+int scratch_for_current_device(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return PICASSO_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr) return PICASSO_ERR_CUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_scratch_addr[dev];
+  return PICASSO_OK;
+}
+
+void static_params(const picasso_config& cfg, int64_t n, int64_t* P, int32_t* L) {
+  int64_t p = (n * cfg.palette_num + cfg.palette_den - 1) / cfg.palette_den;
+  if (p < 1) p = 1;
+  int64_t li = (int64_t)std::ceil(cfg.alpha * std::log((double)n));
+  if (li < 1) li = 1;
+  if (li > p) li = p;
+  *P = p;
+  *L = (int32_t)li;
+}
+
+int err_of(cudaError_t e) {
+  if (e == cudaSuccess) return PICASSO_OK;
+  return e == cudaErrorMemoryAllocation ? PICASSO_ERR_OOM : PICASSO_ERR_CUDA;
+}
+
+#define SCK(expr)                            \
+  do {                                       \
+    int _st = err_of(expr);                  \
+    if (_st != PICASSO_OK) return _st;       \
+  } while (0)
+
+int read_i64(const void* d_src, int64_t* h, cudaStream_t s) {
+  SCK(cudaMemcpyAsync(h, d_src, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCK(cudaStreamSynchronize(s));
+  return PICASSO_OK;
+}
+
+}  // namespace
+
+extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t q, const picasso_config* cfg,
+                                        int32_t* d_color_out, int32_t* n_rounds, void* stream) {
+  if (!d_xz || !cfg || !d_color_out || q < 1 || n < 1) return PICASSO_ERR_INVALID_ARG;
+  if (q > 64 || n > kStaticMaxN) return PICASSO_ERR_UNSUPPORTED;
+  if (cfg->palette_num < 1 || cfg->palette_den < 1 || cfg->palette_num > (int64_t(1) << 32) ||
+      cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
+      cfg->max_rounds < 1)
+    return PICASSO_ERR_INVALID_ARG;
+  {
+    int64_t P;
+    int32_t L;
+    static_params(*cfg, n, &P, &L);  // L never grows in later rounds
+    if (L > kStaticMaxL) return PICASSO_ERR_UNSUPPORTED;
+  }
+  if (scan_tmp_bytes(kStaticNL + 1) > kScanTmpReserve) return PICASSO_ERR_INTERNAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* base_ptr = nullptr;
+  {
+    int st = scratch_for_current_device(&base_ptr);
+    if (st != PICASSO_OK) return st;
+  }
+  int32_t* gid_buf[2] = {(int32_t*)(base_ptr + kOffGid), (int32_t*)(base_ptr + kOffGid) + kStaticMaxN};
+  uint64_t* xz_buf[2] = {(uint64_t*)(base_ptr + kOffXz), (uint64_t*)(base_ptr + kOffXz) + 2 * kStaticMaxN};
+  int32_t* lists = (int32_t*)(base_ptr + kOffLists);
+  uint32_t* prio = (uint32_t*)(base_ptr + kOffPrio);
+  uint32_t* cnt = (uint32_t*)(base_ptr + kOffCnt);
+  uint32_t* xcnt = (uint32_t*)(base_ptr + kOffXcnt);
+  int64_t* runoff = (int64_t*)(base_ptr + kOffRunoff);
+  int64_t* xoff = (int64_t*)(base_ptr + kOffXoff);
+  int32_t* col = (int32_t*)(base_ptr + kOffCol);
+  int32_t* xcol = (int32_t*)(base_ptr + kOffXcol);
+  uint32_t* word = (uint32_t*)(base_ptr + kOffWord);
+  uint16_t* kcur = (uint16_t*)(base_ptr + kOffKcur);
+  int32_t* work[2] = {(int32_t*)(base_ptr + kOffWork), (int32_t*)(base_ptr + kOffWork) + kStaticMaxN};
+  int32_t* counts = (int32_t*)(base_ptr + kOffCounts);
+  uint32_t* flag = (uint32_t*)(base_ptr + kOffFlag);
+  int64_t* pos = (int64_t*)(base_ptr + kOffPos);
+  void* tmp = (void*)(base_ptr + kOffTmp);
+  int32_t* derr = (int32_t*)(base_ptr + kOffErr);
+
+  SCK(launch_fill_i32(d_color_out, n, -1, s));
+  SCK(cudaMemsetAsync(derr, 0, sizeof(int32_t), s));
+
+  const int32_t* gid = nullptr;         // round 1: identity
+  const uint64_t* xz = d_xz;            // round 1: the caller's strings
+  int cur = 0;
+  int64_t m = n, base = 0;
+  int32_t round = 1;
+  while (m > 0) {
+    if (round > cfg->max_rounds) return PICASSO_ERR_INTERNAL;
+    int64_t P;
+    int32_t L;
+    static_params(*cfg, m, &P, &L);
+    if (P >= (int64_t(1) << 30) || base + P > (int64_t)0x7fffffff) return PICASSO_ERR_UNSUPPORTED;
+    const int64_t nl = m * L;
+    SCK(launch_assign_lists(cfg->seed, round, gid, m, P, L, lists, prio, s));
+
+    ConflictArgs a{};
+    a.n = m;
+    a.L = L;
+    a.P = P;
+    a.xz = xz;
+    a.lists = lists;
+    a.cnt = cnt;
+    a.xcnt = xcnt;
+    a.err = derr;
+    SCK(launch_allpairs(a, false, s));
+    SCK(launch_scan_u32(cnt, nl, runoff, tmp, s));
+    SCK(launch_scan_u32(xcnt, nl, xoff, tmp, s));
+    int64_t nnz = 0, nx = 0;
+    {
+      int st = read_i64(runoff + nl, &nnz, s);
+      if (st == PICASSO_OK) st = read_i64(xoff + nl, &nx, s);
+      if (st != PICASSO_OK) return st;
+    }
+    if (nnz > kStaticMaxNnz || nx > kStaticMaxSide) return PICASSO_ERR_UNSUPPORTED;
+    a.runoff = runoff;
+    a.xoff = xoff;
+    a.col = col;
+    a.xcol = xcol;
+    SCK(launch_allpairs(a, true, s));
+
+    ColorArgs ca{};
+    ca.n = m;
+    ca.L = L;
+    ca.lists = lists;
+    ca.prio = prio;
+    ca.runoff = runoff;
+    ca.col = col;
+    ca.xoff = xoff;
+    ca.xcol = xcol;
+    ca.word = word;
+    ca.kcur = kcur;
+    SCK(launch_color_init(ca, work[0], counts, s));
+    int64_t sweeps = 0;
+    int side = 0;
+    while (true) {
+      SCK(cudaMemsetAsync(counts + 1 - side, 0, sizeof(int32_t), s));
+      SCK(launch_color_sweep(ca, work[side], counts + side, work[1 - side], counts + 1 - side, s));
+      int32_t left = 0;
+      SCK(cudaMemcpyAsync(&left, counts + 1 - side, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      SCK(cudaStreamSynchronize(s));
+      side = 1 - side;
+      if (left == 0) break;
+      if (++sweeps > m + 4) return PICASSO_ERR_INTERNAL;
+    }
+    SCK(launch_carry_flags(word, m, gid, base, d_color_out, flag, s));
+    SCK(launch_scan_u32(flag, m, pos, tmp, s));
+    int64_t rem = 0;
+    {
+      int st = read_i64(pos + m, &rem, s);
+      if (st != PICASSO_OK) return st;
+    }
+    if (rem > 0) {
+      SCK(launch_carry_gather(flag, pos, m, gid, xz, gid_buf[cur], xz_buf[cur], s));
+      gid = gid_buf[cur];
+      xz = xz_buf[cur];
+      cur = 1 - cur;
+    }
+    base += P;
+    m = rem;
+    ++round;
+  }
+  SCK(cudaStreamSynchronize(s));
+  if (n_rounds) *n_rounds = round - 1;
+  return PICASSO_OK;
+}

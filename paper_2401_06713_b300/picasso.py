@@ -99,6 +99,7 @@ _SIGS = {
     "picasso_get_stats": [_vp, ctypes.POINTER(Stats)],
     "picasso_philox_draws": [ctypes.c_uint64, _i32, _i64, ctypes.c_uint32, ctypes.c_uint32, _i32, _vp, _vp],
     "picasso_kernel_launches": [_pi64],
+    "picasso_run_small_static": [_vp, _i64, _i32, ctypes.POINTER(Config), _vp, _pi32, _vp],
     "picasso_destroy": [_vp],
 }
 
@@ -287,6 +288,27 @@ class Picasso:
         xcol = torch.empty(max(nx, 1), dtype=torch.int32, device=dev)
         _ck(_lib().picasso_copy_runs(self.h, _ptr(runoff), _ptr(xoff), _ptr(xcol)), "picasso_copy_runs")
         return runoff, xoff, xcol[:nx]
+
+
+def run_small_static(xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
+                     max_rounds: int = 100000, out: torch.Tensor | None = None, stream=None):
+    """Whole run for a small set (n <= 2048) that allocates no device memory
+    inside the library; see picasso_run_small_static.  Returns (colors, rounds)."""
+    assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2
+    xz = xz.contiguous()
+    n = int(xz.shape[0])
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=xz.device)
+    cfg = Config()
+    _ck(_lib().picasso_config_default(ctypes.byref(cfg)), "picasso_config_default")
+    cfg.seed = seed
+    cfg.palette_num, cfg.palette_den = palette
+    cfg.alpha = alpha
+    cfg.max_rounds = max_rounds
+    r = ctypes.c_int32()
+    _ck(_lib().picasso_run_small_static(_ptr(xz), n, q, ctypes.byref(cfg), _ptr(out), ctypes.byref(r),
+                                        _stream(stream)), "picasso_run_small_static")
+    return out, int(r.value)
 
 
 def color_strings(codes: torch.Tensor, seed: int = 0, palette=(1, 8), alpha: float = 2.0, algo: str = "auto"):
