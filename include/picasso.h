@@ -36,6 +36,9 @@
  *     unusable except for picasso_destroy.
  *   - All work is ordered on the stream given to picasso_init.  Calls that
  *     return sizes (build, carry, round, run) synchronise that stream.
+ *   - Contexts allocate from one library-owned memory pool per device.  Freed
+ *     blocks stay reserved for the next round or context (no page mapping on
+ *     the hot path) until picasso_trim_memory returns them.
  */
 #ifndef PICASSO_H
 #define PICASSO_H
@@ -114,9 +117,10 @@ typedef struct {
   double t_pairs_ms;    /* the pair-test kernels alone (count and fill)      */
   int64_t pairs_launches;     /* launches of the pair-test kernels           */
   int64_t logical_pairs;      /* sum over builds of n_l (n_l - 1) / 2        */
-  int64_t tested_pairs;       /* sum over pair-kernel launches of the ordered
-                                 pairs it tested (bucket join: sum over
-                                 buckets of s (s - 1); all pairs: n (n - 1)) */
+  int64_t tested_pairs;       /* pair tests of the pair-test kernels: per
+                                 build, bucket join 1.5 sum_c s_c (s_c - 1)
+                                 (count pass: unordered pairs, fill pass:
+                                 ordered), all pairs 2 n (n - 1)            */
 } picasso_stats;
 
 /* Fill *cfg with the defaults: seed 0, P = n/8, alpha = 2 (the paper's normal
@@ -202,6 +206,10 @@ int picasso_get_stats(void* ctx, picasso_stats* out);
 int picasso_philox_draws(uint64_t seed, int32_t round, int64_t gid,
                          uint32_t tag, uint32_t i0, int32_t count,
                          uint32_t* d_out, void* stream);
+
+/* Return cached pool memory of the current device to the driver, keeping at
+ * most keep_bytes reserved.  Synchronises the device.                      */
+int picasso_trim_memory(int64_t keep_bytes);
 
 /* Process-wide count of kernels this library has launched (all contexts). */
 int picasso_kernel_launches(int64_t* out);

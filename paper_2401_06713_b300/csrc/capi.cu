@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <unordered_map>
 
@@ -20,11 +21,44 @@ void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed);
 }  // namespace picasso
 
 namespace {
+// One memory pool per device, owned by the library.  Freed blocks stay
+// reserved (release threshold = max) so the next round or context reuses
+// them without mapping new pages; picasso_trim_memory hands them back.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[128] = {};
+
+cudaError_t pool_for(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t thr = ~0ull;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+namespace {
 
 struct Ctx {
   picasso_config cfg{};
   cudaStream_t s = nullptr;
   int dev = 0;
+  cudaMemPool_t pool = nullptr;
   int64_t N = 0;
   int32_t q = 0;
   const uint64_t* xz_user = nullptr;
@@ -55,7 +89,7 @@ struct Ctx {
   bool colored_done = false;
   int64_t n_colored = 0, n_remaining = 0;
   int32_t sweeps = 0;
-  uint32_t* word = nullptr;
+  uint64_t* state = nullptr;
   uint32_t* flag = nullptr;
   int64_t* pos = nullptr;
 
@@ -104,7 +138,7 @@ template <class T>
 int alloc(Ctx* c, T** p, int64_t count) {
   *p = nullptr;
   const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
-  cudaError_t e = cudaMallocAsync((void**)p, bytes, c->s);
+  cudaError_t e = cudaMallocFromPoolAsync((void**)p, bytes, c->pool, c->s);
   if (e != cudaSuccess) {
     *p = nullptr;
     return map_err(e);
@@ -129,7 +163,7 @@ void release(Ctx* c, T** p) {
 }
 
 void free_color(Ctx* c) {
-  release(c, &c->word);
+  release(c, &c->state);
   release(c, &c->flag);
   release(c, &c->pos);
   c->colored_done = false;
@@ -251,7 +285,7 @@ int build_conflicts(Ctx* c) {
   const int64_t smax = (int64_t)(*(uint32_t*)c->h_buf);
   const int64_t bucket_pairs = c->h_buf[1];
   c->max_bucket = smax;
-  const bool bucket_ok = smax <= kBucketCap && P < kBucketMaxP;
+  const bool bucket_ok = smax <= kBucketCap && P < kBucketMaxP && nl < (int64_t(1) << 31);
   if (algo == PICASSO_CONFLICT_AUTO) algo = bucket_ok ? PICASSO_CONFLICT_BUCKET : PICASSO_CONFLICT_ALLPAIRS;
   if (algo == PICASSO_CONFLICT_BUCKET && !bucket_ok) {
     cleanup();
@@ -328,7 +362,9 @@ int build_conflicts(Ctx* c) {
   TRYC(cudaEventSynchronize(c->ev[5]));
   c->t_pairs += elapsed(c, 2, 3) + elapsed(c, 4, 5);
   c->pairs_launches += 2;
-  c->tested_pairs += 2 * tested;
+  // the bucket count pass tests each unordered pair once, the fill pass both
+  // orders; the all-pairs kernel tests every ordered pair in both passes
+  c->tested_pairs += algo == PICASSO_CONFLICT_BUCKET ? tested + tested / 2 : 2 * tested;
   c->logical_pairs += n * (n - 1) / 2;
   cleanup();
   c->nnz = nnz;
@@ -342,15 +378,24 @@ int build_conflicts(Ctx* c) {
 int color_round(Ctx* c) {
   const int64_t n = c->n;
   cudaStream_t s = c->s;
-  int32_t *wa = nullptr, *wb = nullptr, *nw = nullptr;
+  int32_t *wa = nullptr, *wb = nullptr, *wact = nullptr, *nw = nullptr;
   uint16_t* kcur = nullptr;
+  uint32_t *rcur = nullptr, *hist = nullptr, *blkw = nullptr;
+  int32_t* blk = nullptr;
+  int64_t* hoff = nullptr;
   void* tmp = nullptr;
   int st = PICASSO_OK;
   auto cleanup = [&]() {
     release(c, &wa);
     release(c, &wb);
+    release(c, &wact);
     release(c, &nw);
     release(c, &kcur);
+    release(c, &rcur);
+    release(c, &blk);
+    release(c, &blkw);
+    release(c, &hist);
+    release(c, &hoff);
     release(c, (uint8_t**)&tmp);
   };
 #define TRY(expr)           \
@@ -372,26 +417,39 @@ int color_round(Ctx* c) {
     }                                             \
   } while (0)
   free_color(c);
-  TRY(alloc(c, &c->word, n));
+  const int nbins = prio_bins_for(n);
+  TRY(alloc(c, &c->state, n));
   TRY(alloc(c, &kcur, n));
+  TRY(alloc(c, &rcur, n));
+  TRY(alloc(c, &blk, n));
+  TRY(alloc(c, &blkw, n));
   TRY(alloc(c, &wa, n));
   TRY(alloc(c, &wb, n));
+  TRY(alloc(c, &wact, n));
+  TRY(alloc(c, &hist, nbins));
+  TRY(alloc(c, &hoff, nbins + 1));
+  const int64_t scan_n = n > nbins ? n : nbins;
+  TRY(alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(scan_n)));
   constexpr int kBatch = 4;
   TRY(alloc(c, &nw, 2 * kBatch + 2));
+  int32_t* nact = nw + kBatch + 1;
   ColorArgs a{};
   a.n = n;
   a.L = c->L;
   a.lists = c->lists;
-  a.prio = c->prio;
   a.runoff = c->runoff;
   a.col = c->col;
   a.xoff = c->xoff;
   a.xcol = c->xcol;
-  a.word = c->word;
+  a.state = c->state;
   a.kcur = kcur;
+  a.rcur = rcur;
+  a.blk = blk;
+  a.blkw = blkw;
   // nw[0] is the initial count; sweep i reads nw[i] and writes nw[i+1]
   int32_t* counts = nw;
-  TRYC(launch_color_init(a, wa, counts, s));
+  TRYC(launch_prio_order(c->prio, n, nbins, hist, hoff, tmp, wa, s));
+  TRYC(launch_color_init(a, c->prio, counts, s));
   int32_t sweeps = 0;
   const int64_t max_sweeps = n + 4;
   bool done = n == 0;
@@ -400,7 +458,9 @@ int color_round(Ctx* c) {
       int32_t* in = (b & 1) ? wb : wa;
       int32_t* out = (b & 1) ? wa : wb;
       TRYC(cudaMemsetAsync(counts + b + 1, 0, sizeof(int32_t), s));
-      TRYC(launch_color_sweep(a, in, counts + b, out, counts + b + 1, s));
+      TRYC(cudaMemsetAsync(nact, 0, sizeof(int32_t), s));
+      TRYC(launch_color_wake(a, in, counts + b, wact, nact, out, counts + b + 1, s));
+      TRYC(launch_color_sweep(a, wact, nact, out, counts + b + 1, s));
     }
     TRYC(cudaMemcpyAsync(c->h_buf, counts, sizeof(int32_t) * (kBatch + 1), cudaMemcpyDeviceToHost, s));
     TRYC(cudaStreamSynchronize(s));
@@ -425,8 +485,7 @@ int color_round(Ctx* c) {
   // colors to the global array; flags + positions of the uncolored
   TRY(alloc(c, &c->flag, n));
   TRY(alloc(c, &c->pos, n + 1));
-  TRY(alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(n)));
-  TRYC(launch_carry_flags(c->word, n, c->gid, c->base, c->color, c->flag, s));
+  TRYC(launch_carry_flags(c->state, n, c->gid, c->base, c->color, c->flag, s));
   TRYC(launch_scan_u32(c->flag, n, c->pos, tmp, s));
   TRYC(cudaMemcpyAsync(c->h_buf, c->pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
@@ -507,6 +566,11 @@ int picasso_init(void** out, const picasso_config* cfg, const uint64_t* d_xz, in
   c->cfg = *cfg;
   c->s = (cudaStream_t)stream;
   cudaError_t e = cudaGetDevice(&c->dev);
+  if (e != cudaSuccess) {
+    delete c;
+    return map_err(e);
+  }
+  e = pool_for(c->dev, &c->pool);
   if (e != cudaSuccess) {
     delete c;
     return map_err(e);
@@ -727,6 +791,22 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->logical_pairs = c->logical_pairs;
   out->tested_pairs = c->tested_pairs;
   return PICASSO_OK;
+}
+
+int picasso_trim_memory(int64_t keep_bytes) {
+  if (keep_bytes < 0) return PICASSO_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return map_err(e);
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (dev >= 0 && dev < 128) pool = g_pool[dev];
+  }
+  if (!pool) return PICASSO_OK;
+  e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, (size_t)keep_bytes);
+  return map_err(e);
 }
 
 int picasso_kernel_launches(int64_t* out) {

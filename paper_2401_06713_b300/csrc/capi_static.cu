@@ -46,10 +46,15 @@ constexpr size_t kOffRunoff = kOffXcnt + al(kStaticNL * 4);                // [N
 constexpr size_t kOffXoff = kOffRunoff + al((kStaticNL + 1) * 8);          // [N*L+1] i64
 constexpr size_t kOffCol = kOffXoff + al((kStaticNL + 1) * 8);             // [maxnnz] i32
 constexpr size_t kOffXcol = kOffCol + al(kStaticMaxNnz * 4);               // [maxside] i32
-constexpr size_t kOffWord = kOffXcol + al(kStaticMaxSide * 4);             // [N] u32
-constexpr size_t kOffKcur = kOffWord + al(kStaticMaxN * 4);                // [N] u16
-constexpr size_t kOffWork = kOffKcur + al(kStaticMaxN * 2);                // 2 x [N] i32
-constexpr size_t kOffCounts = kOffWork + al(2 * kStaticMaxN * 4);          // [16] i32
+constexpr size_t kOffState = kOffXcol + al(kStaticMaxSide * 4);            // [N] u64
+constexpr size_t kOffRcur = kOffState + al(kStaticMaxN * 8);               // [N] u32
+constexpr size_t kOffBlk = kOffRcur + al(kStaticMaxN * 4);                 // [N] i32
+constexpr size_t kOffBlkw = kOffBlk + al(kStaticMaxN * 4);                 // [N] u32
+constexpr size_t kOffHist = kOffBlkw + al(kStaticMaxN * 4);                // [N] u32 (prio bins)
+constexpr size_t kOffHoff = kOffHist + al(kStaticMaxN * 4);                // [N+1] i64
+constexpr size_t kOffKcur = kOffHoff + al((kStaticMaxN + 1) * 8);          // [N] u16
+constexpr size_t kOffWork = kOffKcur + al(kStaticMaxN * 2);                // 3 x [N] i32
+constexpr size_t kOffCounts = kOffWork + al(3 * kStaticMaxN * 4);          // [16] i32
 constexpr size_t kOffFlag = kOffCounts + al(16 * 4);                       // [N] u32
 constexpr size_t kOffPos = kOffFlag + al(kStaticMaxN * 4);                 // [N+1] i64
 constexpr size_t kOffTmp = kOffPos + al((kStaticMaxN + 1) * 8);            // scan temp
@@ -143,9 +148,15 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
   int64_t* xoff = (int64_t*)(base_ptr + kOffXoff);
   int32_t* col = (int32_t*)(base_ptr + kOffCol);
   int32_t* xcol = (int32_t*)(base_ptr + kOffXcol);
-  uint32_t* word = (uint32_t*)(base_ptr + kOffWord);
+  uint64_t* state = (uint64_t*)(base_ptr + kOffState);
+  uint32_t* rcur = (uint32_t*)(base_ptr + kOffRcur);
+  int32_t* blk = (int32_t*)(base_ptr + kOffBlk);
+  uint32_t* blkw = (uint32_t*)(base_ptr + kOffBlkw);
+  uint32_t* hist = (uint32_t*)(base_ptr + kOffHist);
+  int64_t* hoff = (int64_t*)(base_ptr + kOffHoff);
   uint16_t* kcur = (uint16_t*)(base_ptr + kOffKcur);
   int32_t* work[2] = {(int32_t*)(base_ptr + kOffWork), (int32_t*)(base_ptr + kOffWork) + kStaticMaxN};
+  int32_t* wact = (int32_t*)(base_ptr + kOffWork) + 2 * kStaticMaxN;
   int32_t* counts = (int32_t*)(base_ptr + kOffCounts);
   uint32_t* flag = (uint32_t*)(base_ptr + kOffFlag);
   int64_t* pos = (int64_t*)(base_ptr + kOffPos);
@@ -198,19 +209,24 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
     ca.n = m;
     ca.L = L;
     ca.lists = lists;
-    ca.prio = prio;
     ca.runoff = runoff;
     ca.col = col;
     ca.xoff = xoff;
     ca.xcol = xcol;
-    ca.word = word;
+    ca.state = state;
     ca.kcur = kcur;
-    SCK(launch_color_init(ca, work[0], counts, s));
+    ca.rcur = rcur;
+    ca.blk = blk;
+    ca.blkw = blkw;
+    SCK(launch_prio_order(prio, m, prio_bins_for(m), hist, hoff, tmp, work[0], s));
+    SCK(launch_color_init(ca, prio, counts, s));
     int64_t sweeps = 0;
     int side = 0;
     while (true) {
       SCK(cudaMemsetAsync(counts + 1 - side, 0, sizeof(int32_t), s));
-      SCK(launch_color_sweep(ca, work[side], counts + side, work[1 - side], counts + 1 - side, s));
+      SCK(cudaMemsetAsync(counts + 2, 0, sizeof(int32_t), s));
+      SCK(launch_color_wake(ca, work[side], counts + side, wact, counts + 2, work[1 - side], counts + 1 - side, s));
+      SCK(launch_color_sweep(ca, wact, counts + 2, work[1 - side], counts + 1 - side, s));
       int32_t left = 0;
       SCK(cudaMemcpyAsync(&left, counts + 1 - side, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       SCK(cudaStreamSynchronize(s));
@@ -218,7 +234,7 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
       if (left == 0) break;
       if (++sweeps > m + 4) return PICASSO_ERR_INTERNAL;
     }
-    SCK(launch_carry_flags(word, m, gid, base, d_color_out, flag, s));
+    SCK(launch_carry_flags(state, m, gid, base, d_color_out, flag, s));
     SCK(launch_scan_u32(flag, m, pos, tmp, s));
     int64_t rem = 0;
     {

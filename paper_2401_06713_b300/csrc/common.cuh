@@ -120,18 +120,30 @@ struct ColorArgs {
   int64_t n;
   int32_t L;
   const int32_t* lists;
-  const uint32_t* prio;
   const int64_t* runoff;
   const int32_t* col;
   const int64_t* xoff;
   const int32_t* xcol;
-  uint32_t* word;   // [n] state words
+  uint64_t* state;  // [n] priority << 32 | state word
   uint16_t* kcur;   // [n] index of the current candidate in the list
+  uint32_t* rcur;   // [n] resolved prefix of the current candidate's run
+  int32_t* blk;     // [n] neighbour the vertex waited on last, or -1
+  uint32_t* blkw;   // [n] that neighbour's state word when it was seen
 };
-cudaError_t launch_color_init(const ColorArgs& a, int32_t* work, int32_t* nwork, cudaStream_t s);
+// Work list of all n vertices in (approximately) ascending priority: a
+// counting sort on the top log2(nbins) priority bits.  hist needs nbins
+// uint32, hoff nbins + 1 int64, tmp scan_tmp_bytes(nbins) bytes.
+int prio_bins_for(int64_t n);
+cudaError_t launch_prio_order(const uint32_t* prio, int64_t n, int nbins, uint32_t* hist, int64_t* hoff,
+                              void* tmp, int32_t* work, cudaStream_t s);
+cudaError_t launch_color_init(const ColorArgs& a, const uint32_t* prio, int32_t* nwork, cudaStream_t s);
+// One sweep = wake (pending -> active or stays pending) + sweep (evaluate
+// the active vertices; those still waiting join the pending list again).
+cudaError_t launch_color_wake(const ColorArgs& a, const int32_t* work_in, const int32_t* nwork_in, int32_t* active,
+                              int32_t* nactive, int32_t* work_out, int32_t* nwork_out, cudaStream_t s);
 cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const int32_t* nwork_in,
                                int32_t* work_out, int32_t* nwork_out, cudaStream_t s);
-cudaError_t launch_carry_flags(const uint32_t* word, int64_t n, const int32_t* gid, int64_t base,
+cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* gid, int64_t base,
                                int32_t* color, uint32_t* flag, cudaStream_t s);
 cudaError_t launch_carry_gather(const uint32_t* flag, const int64_t* pos, int64_t n, const int32_t* gid,
                                 const uint64_t* xz, int32_t* gid_out, uint64_t* xz_out, cudaStream_t s);

@@ -52,7 +52,7 @@ __global__ void k_bucket_fill(const int32_t* __restrict__ lists, int64_t total, 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = lists[i];
     const uint32_t pos = atomicAdd(&bcursor[c], 1u);
-    bmem[boff[c] + pos] = (int32_t)(i / L);
+    bmem[boff[c] + pos] = (int32_t)i;  // v * L + k: ascending i is ascending v
   }
 }
 
@@ -155,6 +155,8 @@ struct BucketSmem {
   uint16_t* kk;
   int32_t* exo;   // [smax + 1]
   int32_t* excur; // [smax]
+  int32_t* scnt;  // [smax] run counts (count pass)
+  int32_t* sxcnt; // [smax] side-list counts (count pass)
   uint16_t* exv;  // [2 * kExCap]
   uint32_t* expair;
   uint32_t* tab;  // [hs]
@@ -170,6 +172,7 @@ __host__ __device__ inline size_t bucket_smem_bytes(int smax, int hs) {
   b += align16(sizeof(uint16_t) * smax);
   b += align16(sizeof(int32_t) * (smax + 1));
   b += align16(sizeof(int32_t) * smax);
+  b += align16(sizeof(int32_t) * smax) * 2;
   b += align16(sizeof(uint16_t) * 2 * kExCap);
   b += align16(sizeof(uint32_t) * kExCap);
   b += align16(sizeof(uint32_t) * hs);
@@ -185,6 +188,8 @@ __device__ inline BucketSmem carve(uint8_t* p, int smax, int hs) {
   m.kk = (uint16_t*)p; p += align16(sizeof(uint16_t) * smax);
   m.exo = (int32_t*)p; p += align16(sizeof(int32_t) * (smax + 1));
   m.excur = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
+  m.scnt = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
+  m.sxcnt = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
   m.exv = (uint16_t*)p; p += align16(sizeof(uint16_t) * 2 * kExCap);
   m.expair = (uint32_t*)p; p += align16(sizeof(uint32_t) * kExCap);
   m.tab = (uint32_t*)p; p += align16(sizeof(uint32_t) * hs);
@@ -206,22 +211,158 @@ __device__ inline bool share_prefix(const int32_t* __restrict__ a, int ka, const
   return false;
 }
 
-__device__ inline int find_in_list(const int32_t* __restrict__ lst, int L, int32_t c) {
-  int lo = 0, hi = L - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(lst + mid) < c)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
-}
 
 }  // namespace
 
-template <bool FILL>
-__global__ void __launch_bounds__(kPairThreads) k_bucket_pairs(ConflictArgs a, const int64_t* __restrict__ boff,
+// Row state of the pair loops: a member row's words split in 32-bit halves
+// and a cursor into its ascending exclusion list (partners that share a
+// smaller color, so their entry belongs to the side list at this color).
+struct PairRow {
+  uint32_t xl, xh, zl, zh;
+  int ep, ee;   // exclusion list cursor / end
+  int nextex;   // next excluded partner (or a large value)
+};
+
+__device__ __forceinline__ void row_init(PairRow& R, const BucketSmem& S, int i, int s, bool slow) {
+  const bool ok = i < s;
+  const uint64_t x = ok ? S.sx[i] : 0ull, z = ok ? S.sz[i] : 0ull;
+  R.xl = (uint32_t)x;
+  R.xh = (uint32_t)(x >> 32);
+  R.zl = (uint32_t)z;
+  R.zh = (uint32_t)(z >> 32);
+  R.ep = R.ee = 0;
+  if (ok && !slow) {
+    R.ep = S.exo[i];
+    R.ee = S.exo[i + 1];
+  }
+  R.nextex = R.ep < R.ee ? (int)S.exv[R.ep] : 0x7fffffff;
+}
+
+// Bits of the excluded partners inside chunk [j0, j0 + 32); the cursor only
+// moves forward because chunks are visited in ascending order.
+__device__ __forceinline__ uint32_t row_excl(PairRow& R, const BucketSmem& S, int j0) {
+  uint32_t exm = 0u;
+  while (R.nextex < j0 + 32) {
+    if (R.nextex >= j0) exm |= 1u << (R.nextex - j0);
+    ++R.ep;
+    R.nextex = R.ep < R.ee ? (int)S.exv[R.ep] : 0x7fffffff;
+  }
+  return exm;
+}
+
+__device__ __forceinline__ bool row_commutes(const PairRow& R, uint32_t xjl, uint32_t xjh, uint32_t zjl,
+                                             uint32_t zjh) {
+  const uint32_t t = ((R.xl & zjl) ^ (R.zl & xjl)) ^ ((R.xh & zjh) ^ (R.zh & xjh));
+  return (__popc(t) & 1) == 0;
+}
+
+// Count pass over unordered pairs {i, j}, j > i: each hit adds one to the
+// row's count (registers) and one to the partner's (a per-lane column count
+// added to shared memory once per chunk).
+template <int R, bool SLOW>
+__device__ void count_rows(const ConflictArgs& a, BucketSmem& S, int s, int L, int lane, int wid, int nw) {
+  for (int i0 = wid * R; i0 < s; i0 += nw * R) {
+    PairRow row[R];
+    uint32_t rc[R], xc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      row_init(row[r], S, i0 + r, s, SLOW);
+      rc[r] = xc[r] = 0u;
+    }
+    for (int j0 = (i0 + 1) & ~31; j0 < s; j0 += 32) {
+      const int j = j0 + lane;
+      const bool valid = j < s;
+      const uint64_t xj = valid ? S.sx[j] : 0ull, zj = valid ? S.sz[j] : 0ull;
+      const uint32_t xjl = (uint32_t)xj, xjh = (uint32_t)(xj >> 32);
+      const uint32_t zjl = (uint32_t)zj, zjh = (uint32_t)(zj >> 32);
+      int colr = 0, colx = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = i0 + r;
+        const bool hit = valid && j > i && i < s && row_commutes(row[r], xjl, xjh, zjl, zjh);
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        uint32_t exm;
+        if (!SLOW) {
+          exm = row_excl(row[r], S, j0);
+        } else {
+          const bool ex = hit && share_prefix(a.lists + (int64_t)S.sid[i] * L, S.kk[i],
+                                              a.lists + (int64_t)S.sid[j] * L, S.kk[j]);
+          exm = __ballot_sync(0xffffffffu, ex);
+        }
+        const uint32_t rm = m & ~exm, xm = m & exm;
+        rc[r] += __popc(rm);
+        xc[r] += __popc(xm);
+        colr += (int)((rm >> lane) & 1u);
+        colx += (int)((xm >> lane) & 1u);
+      }
+      if (colr) atomicAdd(&S.scnt[j], colr);
+      if (colx) atomicAdd(&S.sxcnt[j], colx);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (i0 + r < s) {
+          if (rc[r]) atomicAdd(&S.scnt[i0 + r], (int)rc[r]);
+          if (xc[r]) atomicAdd(&S.sxcnt[i0 + r], (int)xc[r]);
+        }
+      }
+    }
+  }
+}
+
+// Fill pass over ordered pairs: row i's partners in ascending j, written at
+// the run's offset with ballot + prefix popcount (deterministic order).
+template <int R, bool SLOW>
+__device__ void fill_rows(const ConflictArgs& a, BucketSmem& S, int s, int L, int lane, int wid, int nw,
+                          uint32_t lt) {
+  for (int i0 = wid * R; i0 < s; i0 += nw * R) {
+    PairRow row[R];
+    int32_t* rp[R];
+    int32_t* xp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = i0 + r;
+      row_init(row[r], S, i, s, SLOW);
+      rp[r] = a.col;
+      xp[r] = a.xcol;
+      if (i < s) {
+        const int64_t slot = (int64_t)S.sid[i] * L + S.kk[i];
+        rp[r] = a.col + a.runoff[slot];
+        xp[r] = a.xcol + a.xoff[slot];
+      }
+    }
+    for (int j0 = 0; j0 < s; j0 += 32) {
+      const int j = j0 + lane;
+      const bool valid = j < s;
+      const uint64_t xj = valid ? S.sx[j] : 0ull, zj = valid ? S.sz[j] : 0ull;
+      const uint32_t xjl = (uint32_t)xj, xjh = (uint32_t)(xj >> 32);
+      const uint32_t zjl = (uint32_t)zj, zjh = (uint32_t)(zj >> 32);
+      const int32_t vj = valid ? S.sid[j] : 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = i0 + r;
+        const bool hit = valid && j != i && i < s && row_commutes(row[r], xjl, xjh, zjl, zjh);
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        uint32_t exm;
+        if (!SLOW) {
+          exm = row_excl(row[r], S, j0);
+        } else {
+          const bool ex = hit && share_prefix(a.lists + (int64_t)S.sid[i] * L, S.kk[i],
+                                              a.lists + (int64_t)vj * L, S.kk[j]);
+          exm = __ballot_sync(0xffffffffu, ex);
+        }
+        const uint32_t rm = m & ~exm, xm = m & exm;
+        if ((rm >> lane) & 1u) rp[r][__popc(rm & lt)] = vj;
+        if ((xm >> lane) & 1u) xp[r][__popc(xm & lt)] = vj;
+        rp[r] += __popc(rm);
+        xp[r] += __popc(xm);
+      }
+    }
+  }
+}
+
+template <bool FILL, int kRows>
+__global__ void __launch_bounds__(kPairThreads, 2) k_bucket_pairs(ConflictArgs a, const int64_t* __restrict__ boff,
                                                                const int32_t* __restrict__ bmem, int smax,
                                                                int hs_log2) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -237,12 +378,15 @@ __global__ void __launch_bounds__(kPairThreads) k_bucket_pairs(ConflictArgs a, c
     if (s == 0) continue;
     if (threadIdx.x < 4) S.misc[threadIdx.x] = 0;
     for (int i = threadIdx.x; i < s; i += blockDim.x) {
-      const int32_t v = bmem[o + i];
+      const int32_t flat = bmem[o + i];  // v * L + k, k = position of color b in v's list
+      const int32_t v = flat / L;
       S.sid[i] = v;
       S.sx[i] = a.xz[2 * (int64_t)v];
       S.sz[i] = a.xz[2 * (int64_t)v + 1];
-      S.kk[i] = (uint16_t)find_in_list(a.lists + (int64_t)v * L, L, (int32_t)b);
+      S.kk[i] = (uint16_t)(flat - v * L);
       S.excur[i] = 0;
+      S.scnt[i] = 0;
+      S.sxcnt[i] = 0;
     }
     __syncthreads();
     // E = number of (member, smaller color) entries
@@ -260,10 +404,12 @@ __global__ void __launch_bounds__(kPairThreads) k_bucket_pairs(ConflictArgs a, c
       __syncthreads();
       // Insert every smaller color of every member; an insert that passes an
       // entry of the same color found a pair sharing that color.
-      for (int i = wid; i < s; i += nw) {
-        const int32_t* lst = a.lists + (int64_t)S.sid[i] * L;
-        for (int t = lane; t < S.kk[i]; t += 32) {
-          const uint32_t c = (uint32_t)__ldg(lst + t);
+      // flattened over (member, list position) so that every thread's list
+      // load is independent and the block's loads overlap
+      for (int idx = threadIdx.x; idx < s * L; idx += blockDim.x) {
+        const int i = idx / L, t = idx - i * L;
+        if (t < S.kk[i]) {
+          const uint32_t c = (uint32_t)__ldg(a.lists + (int64_t)S.sid[i] * L + t);
           const uint32_t key = ((c + 1u) << 11) | (uint32_t)i;
           uint32_t slot = (c * 0x9E3779B1u) >> (32 - hs_log2);
           while (true) {
@@ -313,46 +459,38 @@ __global__ void __launch_bounds__(kPairThreads) k_bucket_pairs(ConflictArgs a, c
         S.exv[S.exo[i2] + atomicAdd(&S.excur[i2], 1)] = (uint16_t)i1;
       }
       __syncthreads();
+      // ascending partners per member (lists are short: insertion sort)
+      for (int i = threadIdx.x; i < s; i += blockDim.x) {
+        uint16_t* e = S.exv + S.exo[i];
+        const int m = S.exo[i + 1] - S.exo[i];
+        for (int x = 1; x < m; ++x) {
+          const uint16_t key = e[x];
+          int y = x - 1;
+          while (y >= 0 && e[y] > key) {
+            e[y + 1] = e[y];
+            --y;
+          }
+          e[y + 1] = key;
+        }
+      }
+      __syncthreads();
     }
 
-    // One warp per member row; lanes sweep partners in ascending order.
-    for (int i = wid; i < s; i += nw) {
-      const uint64_t xi = S.sx[i], zi = S.sz[i];
-      const int32_t v = S.sid[i];
-      const int k = S.kk[i];
-      const int64_t slot = (int64_t)v * L + k;
-      int64_t rpos = 0, xpos = 0;
-      if (FILL) {
-        rpos = a.runoff[slot];
-        xpos = a.xoff[slot];
-      }
-      uint32_t rc = 0, xc = 0;
-      for (int j0 = 0; j0 < s; j0 += 32) {
-        const int j = j0 + lane;
-        const bool bit = j < s && j != i && commute1(xi, zi, S.sx[j], S.sz[j]);
-        const uint32_t m = __ballot_sync(0xffffffffu, bit);
-        if (m == 0u) continue;
-        uint32_t exm = 0u;
-        if (!slow) {
-          for (int e = S.exo[i]; e < S.exo[i + 1]; ++e) {
-            const uint32_t d = (uint32_t)S.exv[e] - (uint32_t)j0;
-            if (d < 32u) exm |= 1u << d;
-          }
-        } else {
-          const bool ex = bit && share_prefix(a.lists + (int64_t)v * L, k, a.lists + (int64_t)S.sid[j] * L, S.kk[j]);
-          exm = __ballot_sync(0xffffffffu, ex);
-        }
-        const uint32_t rm = m & ~exm, xm = m & exm;
-        if (FILL) {
-          if ((rm >> lane) & 1u) a.col[rpos + rc + __popc(rm & lt)] = S.sid[j];
-          if ((xm >> lane) & 1u) a.xcol[xpos + xc + __popc(xm & lt)] = S.sid[j];
-        }
-        rc += __popc(rm);
-        xc += __popc(xm);
-      }
-      if (!FILL && lane == 0) {
-        a.cnt[slot] = rc;
-        a.xcnt[slot] = xc;
+    if (FILL) {
+      if (slow)
+        fill_rows<kRows, true>(a, S, s, L, lane, wid, nw, lt);
+      else
+        fill_rows<kRows, false>(a, S, s, L, lane, wid, nw, lt);
+    } else {
+      if (slow)
+        count_rows<kRows, true>(a, S, s, L, lane, wid, nw);
+      else
+        count_rows<kRows, false>(a, S, s, L, lane, wid, nw);
+      __syncthreads();
+      for (int i = threadIdx.x; i < s; i += blockDim.x) {
+        const int64_t slot = (int64_t)S.sid[i] * L + S.kk[i];
+        a.cnt[slot] = (uint32_t)S.scnt[i];
+        a.xcnt[slot] = (uint32_t)S.sxcnt[i];
       }
     }
     __syncthreads();
@@ -367,7 +505,9 @@ cudaError_t launch_bucket_pairs(const ConflictArgs& a, const int64_t* boff, cons
   int hs_log2 = 8;
   while ((1ll << hs_log2) < want && hs_log2 < 14) ++hs_log2;
   const size_t bytes = bucket_smem_bytes(smax, 1 << hs_log2);
-  auto kern = fill ? k_bucket_pairs<true> : k_bucket_pairs<false>;
+  // member rows per warp: 4 in the count pass, 2 in the fill pass (which
+  // keeps two output cursors per row in registers)
+  auto kern = fill ? k_bucket_pairs<true, 2> : k_bucket_pairs<false, 4>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

@@ -99,6 +99,7 @@ _SIGS = {
     "picasso_get_stats": [_vp, ctypes.POINTER(Stats)],
     "picasso_philox_draws": [ctypes.c_uint64, _i32, _i64, ctypes.c_uint32, ctypes.c_uint32, _i32, _vp, _vp],
     "picasso_kernel_launches": [_pi64],
+    "picasso_trim_memory": [_i64],
     "picasso_run_small_static": [_vp, _i64, _i32, ctypes.POINTER(Config), _vp, _pi32, _vp],
     "picasso_destroy": [_vp],
 }
@@ -160,6 +161,11 @@ def kernel_launches() -> int:
     k = ctypes.c_int64()
     _ck(_lib().picasso_kernel_launches(ctypes.byref(k)), "picasso_kernel_launches")
     return int(k.value)
+
+
+def trim_memory(keep_bytes: int = 0):
+    """Return the library's cached device memory (current device) to the driver."""
+    _ck(_lib().picasso_trim_memory(keep_bytes), "picasso_trim_memory")
 
 
 def philox_draws(seed: int, rnd: int, gid: int, tag: int, i0: int, count: int, device="cuda") -> torch.Tensor:
