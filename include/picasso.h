@@ -77,7 +77,15 @@ typedef struct {
   int32_t max_rounds;    /* picasso_run gives up with ERR_INTERNAL beyond it  */
   int64_t byte_budget;   /* max bytes of one round's conflict CSR (off + col
                             + the extras side list); 0 = no limit            */
+  int32_t color_algo;    /* picasso_color_algo                                */
+  int32_t reserved;
 } picasso_config;
+
+/* Coloring strategy (same colors either way). */
+typedef enum {
+  PICASSO_COLOR_AUTO = 0,  /* ordered persistent pass; sweeps if it gives up */
+  PICASSO_COLOR_SWEEP = 1  /* dependency sweeps only                         */
+} picasso_color_algo;
 
 /* Conflict CSR of the current round, owned by the context and valid until
  * the next assign/build/carry or destroy.  Ids are round-local: row r is the
@@ -106,7 +114,8 @@ typedef struct {
   int64_t colors_used; /* base after the last carry = sum of P of done rounds */
   int64_t peak_bytes;  /* high-water mark of context-owned device memory      */
   int32_t conflict_algo_used;
-  int32_t jp_sweeps;   /* sweeps of the last color step                      */
+  int32_t jp_sweeps;   /* sweeps of the last color step (0: ordered pass)    */
+  int32_t ordered_fallbacks; /* rounds whose ordered pass gave up (sweeps ran) */
   int64_t max_bucket;  /* largest color bucket of the last build             */
   /* cumulative since picasso_init (CUDA events on the context's stream) */
   int32_t rounds_done;
@@ -121,6 +130,11 @@ typedef struct {
                                  build, bucket join 1.5 sum_c s_c (s_c - 1)
                                  (count pass: unordered pairs, fill pass:
                                  ordered), all pairs 2 n (n - 1)            */
+  /* the last color step's first 64 sweeps: vertices pending at the start,
+   * vertices re-evaluated, and duration in microseconds (0 for the last) */
+  int32_t sweep_pending[64];
+  int32_t sweep_active[64];
+  float sweep_us[64];
 } picasso_stats;
 
 /* Fill *cfg with the defaults: seed 0, P = n/8, alpha = 2 (the paper's normal

@@ -95,6 +95,8 @@ struct Ctx {
 
   int32_t* d_err = nullptr;
   int64_t* h_buf = nullptr;  // pinned readback buffer [16]
+  int32_t sweep_log[kCtlWords] = {};
+  int32_t ordered_fallbacks = 0;
   int sticky = PICASSO_OK;
 
   std::unordered_map<void*, size_t> sizes;
@@ -430,9 +432,8 @@ int color_round(Ctx* c) {
   TRY(alloc(c, &hoff, nbins + 1));
   const int64_t scan_n = n > nbins ? n : nbins;
   TRY(alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(scan_n)));
-  constexpr int kBatch = 4;
-  TRY(alloc(c, &nw, 2 * kBatch + 2));
-  int32_t* nact = nw + kBatch + 1;
+  TRY(alloc(c, &nw, kCtlWords));
+  int32_t* ctl = nw;
   ColorArgs a{};
   a.n = n;
   a.L = c->L;
@@ -446,39 +447,30 @@ int color_round(Ctx* c) {
   a.rcur = rcur;
   a.blk = blk;
   a.blkw = blkw;
-  // nw[0] is the initial count; sweep i reads nw[i] and writes nw[i+1]
-  int32_t* counts = nw;
+  // Ordered persistent pass; if one of its bounded waits runs out (ctl[5]),
+  // recolor the round with the sweep kernel from a fresh state.
+  TRYC(cudaMemsetAsync(ctl, 0, sizeof(int32_t) * kCtlWords, s));
   TRYC(launch_prio_order(c->prio, n, nbins, hist, hoff, tmp, wa, s));
-  TRYC(launch_color_init(a, c->prio, counts, s));
+  TRYC(launch_color_init(a, c->prio, ctl, s));
   int32_t sweeps = 0;
-  const int64_t max_sweeps = n + 4;
-  bool done = n == 0;
-  while (!done) {
-    for (int b = 0; b < kBatch; ++b) {
-      int32_t* in = (b & 1) ? wb : wa;
-      int32_t* out = (b & 1) ? wa : wb;
-      TRYC(cudaMemsetAsync(counts + b + 1, 0, sizeof(int32_t), s));
-      TRYC(cudaMemsetAsync(nact, 0, sizeof(int32_t), s));
-      TRYC(launch_color_wake(a, in, counts + b, wact, nact, out, counts + b + 1, s));
-      TRYC(launch_color_sweep(a, wact, nact, out, counts + b + 1, s));
-    }
-    TRYC(cudaMemcpyAsync(c->h_buf, counts, sizeof(int32_t) * (kBatch + 1), cudaMemcpyDeviceToHost, s));
+  bool need_sweeps = c->cfg.color_algo == PICASSO_COLOR_SWEEP;
+  if (!need_sweeps) {
+    TRYC(launch_color_ordered(a, wa, ctl + 5, s));
+    TRYC(cudaMemcpyAsync(c->sweep_log, ctl, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s));
     TRYC(cudaStreamSynchronize(s));
-    const int32_t* h = (const int32_t*)c->h_buf;
-    for (int b = 0; b < kBatch; ++b) {
-      if (h[b] > 0) ++sweeps;
-      if (h[b + 1] == 0) {
-        done = true;
-        break;
-      }
-    }
-    if (!done) {
-      // the batch ended in buffer wa (even number of sweeps); carry its count
-      TRYC(cudaMemcpyAsync(counts, counts + kBatch, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-      if (sweeps > max_sweeps) {
-        cleanup();
-        return PICASSO_ERR_INTERNAL;
-      }
+    need_sweeps = c->sweep_log[5] != 0;
+    c->ordered_fallbacks += need_sweeps ? 1 : 0;
+  }
+  if (need_sweeps) {
+    TRYC(cudaMemsetAsync(ctl, 0, sizeof(int32_t) * kCtlWords, s));
+    TRYC(launch_color_init(a, c->prio, ctl, s));
+    TRYC(launch_color_all(a, wa, wb, wact, ctl, s));
+    TRYC(cudaMemcpyAsync(c->sweep_log, ctl, sizeof(int32_t) * kCtlWords, cudaMemcpyDeviceToHost, s));
+    TRYC(cudaStreamSynchronize(s));
+    sweeps = c->sweep_log[3];
+    if (c->sweep_log[4] != 0 || c->sweep_log[0] != 0) {
+      cleanup();
+      return PICASSO_ERR_INTERNAL;
     }
   }
   c->sweeps = sweeps;
@@ -559,7 +551,8 @@ int picasso_init(void** out, const picasso_config* cfg, const uint64_t* d_xz, in
   if (q > 64) return PICASSO_ERR_UNSUPPORTED;
   if (cfg->palette_num < 1 || cfg->palette_den < 1 || cfg->palette_num > (int64_t(1) << 32) ||
       cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
-      cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2)
+      cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2 ||
+      cfg->color_algo < 0 || cfg->color_algo > 1)
     return PICASSO_ERR_INVALID_ARG;
   Ctx* c = new (std::nothrow) Ctx();
   if (!c) return PICASSO_ERR_OOM;
@@ -780,6 +773,7 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->peak_bytes = c->peak_bytes;
   out->conflict_algo_used = c->algo_used;
   out->jp_sweeps = c->sweeps;
+  out->ordered_fallbacks = c->ordered_fallbacks;
   out->max_bucket = c->max_bucket;
   out->rounds_done = c->rounds_done;
   out->t_assign_ms = c->t_assign;
@@ -790,6 +784,13 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->pairs_launches = c->pairs_launches;
   out->logical_pairs = c->logical_pairs;
   out->tested_pairs = c->tested_pairs;
+  const int ns = c->sweeps < kSweepLog ? c->sweeps : kSweepLog;
+  const unsigned long long* t = reinterpret_cast<const unsigned long long*>(c->sweep_log + 8 + kSweepLog);
+  for (int i = 0; i < ns; ++i) {
+    out->sweep_pending[i] = c->sweep_log[8 + i];
+    out->sweep_active[i] = c->sweep_log[8 + 3 * kSweepLog + i];
+    out->sweep_us[i] = (float)((i + 1 < ns ? (double)(t[i + 1] - t[i]) : 0.0) / 1000.0);
+  }
   return PICASSO_OK;
 }
 

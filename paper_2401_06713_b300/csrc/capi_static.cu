@@ -54,8 +54,8 @@ constexpr size_t kOffHist = kOffBlkw + al(kStaticMaxN * 4);                // [N
 constexpr size_t kOffHoff = kOffHist + al(kStaticMaxN * 4);                // [N+1] i64
 constexpr size_t kOffKcur = kOffHoff + al((kStaticMaxN + 1) * 8);          // [N] u16
 constexpr size_t kOffWork = kOffKcur + al(kStaticMaxN * 2);                // 3 x [N] i32
-constexpr size_t kOffCounts = kOffWork + al(3 * kStaticMaxN * 4);          // [16] i32
-constexpr size_t kOffFlag = kOffCounts + al(16 * 4);                       // [N] u32
+constexpr size_t kOffCounts = kOffWork + al(3 * kStaticMaxN * 4);          // [kCtlWords] i32
+constexpr size_t kOffFlag = kOffCounts + al(kCtlWords * 4);                // [N] u32
 constexpr size_t kOffPos = kOffFlag + al(kStaticMaxN * 4);                 // [N+1] i64
 constexpr size_t kOffTmp = kOffPos + al((kStaticMaxN + 1) * 8);            // scan temp
 constexpr size_t kOffErr = kOffTmp + al(kScanTmpReserve);                  // [1] i32
@@ -218,21 +218,22 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
     ca.rcur = rcur;
     ca.blk = blk;
     ca.blkw = blkw;
+    SCK(cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCtlWords, s));
     SCK(launch_prio_order(prio, m, prio_bins_for(m), hist, hoff, tmp, work[0], s));
     SCK(launch_color_init(ca, prio, counts, s));
-    int64_t sweeps = 0;
-    int side = 0;
-    while (true) {
-      SCK(cudaMemsetAsync(counts + 1 - side, 0, sizeof(int32_t), s));
-      SCK(cudaMemsetAsync(counts + 2, 0, sizeof(int32_t), s));
-      SCK(launch_color_wake(ca, work[side], counts + side, wact, counts + 2, work[1 - side], counts + 1 - side, s));
-      SCK(launch_color_sweep(ca, wact, counts + 2, work[1 - side], counts + 1 - side, s));
-      int32_t left = 0;
-      SCK(cudaMemcpyAsync(&left, counts + 1 - side, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SCK(launch_color_ordered(ca, work[0], counts + 5, s));
+    {
+      int32_t h[8];
+      SCK(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, s));
       SCK(cudaStreamSynchronize(s));
-      side = 1 - side;
-      if (left == 0) break;
-      if (++sweeps > m + 4) return PICASSO_ERR_INTERNAL;
+      if (h[5] != 0) {  // a bounded wait ran out: recolor with the sweep kernel
+        SCK(cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCtlWords, s));
+        SCK(launch_color_init(ca, prio, counts, s));
+        SCK(launch_color_all(ca, work[0], work[1], wact, counts, s));
+        SCK(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, s));
+        SCK(cudaStreamSynchronize(s));
+        if (h[4] != 0 || h[0] != 0) return PICASSO_ERR_INTERNAL;
+      }
     }
     SCK(launch_carry_flags(state, m, gid, base, d_color_out, flag, s));
     SCK(launch_scan_u32(flag, m, pos, tmp, s));

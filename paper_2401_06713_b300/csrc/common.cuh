@@ -128,10 +128,10 @@ struct ColorArgs {
   uint16_t* kcur;   // [n] index of the current candidate in the list
   uint32_t* rcur;   // [n] resolved prefix of the current candidate's run
   int32_t* blk;     // [n] neighbour the vertex waited on last, or -1
-  uint32_t* blkw;   // [n] that neighbour's state word when it was seen
+  uint32_t* blkw;   // [n] the vertex's candidate color when it started waiting
 };
-// Work list of all n vertices in (approximately) ascending priority: a
-// counting sort on the top log2(nbins) priority bits.  hist needs nbins
+// Work list of all n vertices in ascending (priority, id): a counting sort on
+// the top log2(nbins) priority bits, then a sort inside each bin.  hist needs nbins
 // uint32, hoff nbins + 1 int64, tmp scan_tmp_bytes(nbins) bytes.
 int prio_bins_for(int64_t n);
 cudaError_t launch_prio_order(const uint32_t* prio, int64_t n, int nbins, uint32_t* hist, int64_t* hoff,
@@ -143,6 +143,21 @@ cudaError_t launch_color_wake(const ColorArgs& a, const int32_t* work_in, const 
                               int32_t* nactive, int32_t* work_out, int32_t* nwork_out, cudaStream_t s);
 cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const int32_t* nwork_in,
                                int32_t* work_out, int32_t* nwork_out, cudaStream_t s);
+// Every sweep of a round in one cooperative launch.  ctl [kCtlWords] int32:
+// ctl[0] holds the pending count of wa on entry (launch_color_init writes
+// it), the rest must be zero; on exit ctl[3] = sweeps, ctl[4] = 1 if the
+// sweep limit (n + 4) ran out.  For the first kSweepLog sweeps the kernel
+// logs the pending count (ctl[8 + s]), the globaltimer at the sweep's start
+// (uint64 at ctl + 8 + kSweepLog, entry s) and the active count
+// (ctl[8 + 3 kSweepLog + s]).
+// Ordered persistent coloring of a round: `order` must list the vertices in
+// exact (priority, id) order (launch_prio_order gives it).  On return *err
+// is 1 if a bounded wait ran out (then recolor with launch_color_all).
+cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32_t* err, cudaStream_t s);
+constexpr int kSweepLog = 64;
+constexpr int kCtlWords = 8 + 4 * kSweepLog;
+cudaError_t launch_color_all(const ColorArgs& a, int32_t* wa, int32_t* wb, int32_t* wact, int32_t* ctl,
+                             cudaStream_t s);
 cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* gid, int64_t base,
                                int32_t* color, uint32_t* flag, cudaStream_t s);
 cudaError_t launch_carry_gather(const uint32_t* flag, const int64_t* pos, int64_t n, const int32_t* gid,

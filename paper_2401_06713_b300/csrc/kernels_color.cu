@@ -2,26 +2,34 @@
 //
 // The order is the static Random order of Sec. III-B with first fit: in
 // ascending (priority, round-local id) order each vertex takes the smallest
-// list color that no earlier conflict neighbour took.  The sweep below
-// reproduces that sequential result in parallel.  A vertex v with candidate
+// list color that no earlier conflict neighbour took.  The sweeps below
+// reproduce that sequential result in parallel.  A vertex v with candidate
 // c (its k-th list color) looks only at the earlier neighbours that hold c --
 // run k of its row plus side-list k -- and
 //   * moves to its next list color as soon as one of them is colored c;
 //   * takes c once every one of them is colored differently, failed, or still
 //     undecided with a candidate above c (candidates only grow, so such a
 //     neighbour can never take c);
-//   * otherwise waits for the next sweep.
+//   * otherwise records the first neighbour it waits on and is looked at
+//     again only once that neighbour no longer holds it up (decided, or
+//     undecided with a candidate above c).
 // Each state word changes only along undecided(c0) -> undecided(c1) -> ... ->
 // colored / failed, so any value a concurrent reader sees is a true past
 // state and every decision taken from it is final.  The earliest undecided
 // vertex never waits, so every sweep makes progress.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace picasso {
 
-// Approximate priority order of the work list: counting sort on the top
-// priority bits.  The order only affects how fast decisions propagate
+// ---------------------------------------------------------------------------
+// Approximate priority order of the first work list: counting sort on the
+// top priority bits.  The order only affects how fast decisions propagate
 // inside one sweep (warps pick work in list order), never the result.
+// ---------------------------------------------------------------------------
 __global__ void k_prio_hist(const uint32_t* __restrict__ prio, int64_t n, int shift, uint32_t* __restrict__ hist) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v < n) atomicAdd(&hist[prio[v] >> shift], 1u);
@@ -34,6 +42,28 @@ __global__ void k_prio_scatter(const uint32_t* __restrict__ prio, int64_t n, int
   if (v >= n) return;
   const uint32_t b = prio[v] >> shift;
   work[hoff[b] + atomicAdd(&cursor[b], 1u)] = (int32_t)v;
+}
+
+// Exact order inside each bin: insertion sort of the bin's (short) segment by
+// (priority, vertex).  After it the whole list is in ascending (priority,
+// round-local id) order, the coloring order.
+__global__ void k_prio_bin_sort(const uint32_t* __restrict__ prio, const int64_t* __restrict__ hoff, int nbins,
+                                int32_t* __restrict__ work) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  const int64_t lo = hoff[b], hi = hoff[b + 1];
+  for (int64_t x = lo + 1; x < hi; ++x) {
+    const int32_t v = work[x];
+    const uint64_t kv = ((uint64_t)prio[v] << 32) | (uint32_t)v;
+    int64_t y = x - 1;
+    while (y >= lo) {
+      const int32_t w = work[y];
+      if ((((uint64_t)prio[w] << 32) | (uint32_t)w) <= kv) break;
+      work[y + 1] = w;
+      --y;
+    }
+    work[y + 1] = v;
+  }
 }
 
 int prio_bins_for(int64_t n) {
@@ -58,6 +88,8 @@ cudaError_t launch_prio_order(const uint32_t* prio, int64_t n, int nbins, uint32
   e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nbins, s);
   if (e != cudaSuccess) return e;
   k_prio_scatter<<<blocks, 256, 0, s>>>(prio, n, shift, hoff, hist, work);
+  count_launches(1);
+  k_prio_bin_sort<<<(unsigned)((nbins + 255) / 256), 256, 0, s>>>(prio, hoff, nbins, work);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -85,39 +117,66 @@ __device__ __forceinline__ void publish(uint64_t* state, int32_t v, uint32_t w) 
   __stcg(reinterpret_cast<uint32_t*>(state + v), w);
 }
 
-__global__ void __launch_bounds__(256, 4) k_color_sweep(ColorArgs a, const int32_t* __restrict__ work_in,
-                                                        const int32_t* __restrict__ nwork_in,
-                                                        int32_t* __restrict__ work_out,
-                                                        int32_t* __restrict__ nwork_out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t nin = *nwork_in;
+// ---------------------------------------------------------------------------
+// Evaluation of one vertex by one warp: advance past blocked candidates, then
+// take the candidate, fail, or record what v waits on and append v to
+// work_out.  The loop runs at most L + 1 times.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* __restrict__ work_out,
+                                            int32_t* __restrict__ nwork_out) {
   const int L = a.L;
-  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nin; w += nwarps) {
-    const int32_t v = work_in[w];
-    const uint32_t pv = (uint32_t)(__ldcg(&a.state[v]) >> 32);
-    int k = a.kcur[v];
-    uint32_t cur = a.rcur[v];
-    const int64_t row = (int64_t)v * L;
-    while (true) {
-      if (k >= L) {
-        if (lane == 0) publish(a.state, v, (kFailedColor << 2) | kFailed);
+  const uint32_t pv = (uint32_t)(__ldcg(&a.state[v]) >> 32);
+  int k = a.kcur[v];
+  uint32_t cur = a.rcur[v];
+  const int64_t row = (int64_t)v * L;
+  while (true) {
+    if (k >= L) {
+      if (lane == 0) publish(a.state, v, (kFailedColor << 2) | kFailed);
+      return;
+    }
+    const uint32_t c = (uint32_t)a.lists[row + k];
+    const int64_t rs = a.runoff[row + k], r1 = a.runoff[row + k + 1];
+    bool blocked = false;
+    int64_t first_wait = -1;
+    int32_t wait_u = -1;
+    // the run of c: earlier neighbours whose smallest shared color is c
+    for (int64_t e0 = rs + cur; e0 < r1; e0 += 32) {
+      const int64_t e = e0 + lane;
+      bool lb = false, lw = false;
+      int32_t u = -1;
+      uint32_t wu = 0;
+      if (e < r1) {
+        u = a.col[e];
+        const uint64_t su = __ldcg(&a.state[u]);
+        const uint32_t pu = (uint32_t)(su >> 32);
+        if (pu < pv || (pu == pv && u < v)) {
+          wu = (uint32_t)su;
+          const uint32_t st = wu & 3u, cu = wu >> 2;
+          lb = st == kColored && cu == c;
+          lw = st == kUndecided && cu <= c;
+        }
+      }
+      if (__any_sync(0xffffffffu, lb)) {
+        blocked = true;
         break;
       }
-      const uint32_t c = (uint32_t)a.lists[row + k];
-      const int64_t rs = a.runoff[row + k], r1 = a.runoff[row + k + 1];
-      bool blocked = false;
-      int64_t first_wait = -1;
-      int32_t wait_u = -1;
-      uint32_t wait_w = 0;
-      // the run of c: earlier neighbours whose smallest shared color is c
-      for (int64_t e0 = rs + cur; e0 < r1; e0 += 32) {
+      const uint32_t wm = __ballot_sync(0xffffffffu, lw);
+      if (wm && first_wait < 0) {
+        const int src = __ffs(wm) - 1;
+        first_wait = e0 + src;
+        wait_u = __shfl_sync(0xffffffffu, u, src);
+      }
+    }
+    // side list of c: earlier neighbours holding c with a smaller shared color
+    if (!blocked) {
+      const int64_t x0 = a.xoff[row + k], x1 = a.xoff[row + k + 1];
+      for (int64_t e0 = x0; e0 < x1; e0 += 32) {
         const int64_t e = e0 + lane;
         bool lb = false, lw = false;
         int32_t u = -1;
         uint32_t wu = 0;
-        if (e < r1) {
-          u = a.col[e];
+        if (e < x1) {
+          u = a.xcol[e];
           const uint64_t su = __ldcg(&a.state[u]);
           const uint32_t pu = (uint32_t)(su >> 32);
           if (pu < pv || (pu == pv && u < v)) {
@@ -132,104 +191,256 @@ __global__ void __launch_bounds__(256, 4) k_color_sweep(ColorArgs a, const int32
           break;
         }
         const uint32_t wm = __ballot_sync(0xffffffffu, lw);
-        if (wm && first_wait < 0) {
+        if (wm && wait_u < 0) {
           const int src = __ffs(wm) - 1;
-          first_wait = e0 + src;
           wait_u = __shfl_sync(0xffffffffu, u, src);
-          wait_w = __shfl_sync(0xffffffffu, wu, src);
         }
       }
-      // side list of c: earlier neighbours holding c with a smaller shared color
-      if (!blocked) {
-        const int64_t x0 = a.xoff[row + k], x1 = a.xoff[row + k + 1];
-        for (int64_t e0 = x0; e0 < x1; e0 += 32) {
-          const int64_t e = e0 + lane;
-          bool lb = false, lw = false;
-          int32_t u = -1;
-          uint32_t wu = 0;
-          if (e < x1) {
-            u = a.xcol[e];
-            const uint64_t su = __ldcg(&a.state[u]);
-            const uint32_t pu = (uint32_t)(su >> 32);
-            if (pu < pv || (pu == pv && u < v)) {
-              wu = (uint32_t)su;
-              const uint32_t st = wu & 3u, cu = wu >> 2;
-              lb = st == kColored && cu == c;
-              lw = st == kUndecided && cu <= c;
-            }
-          }
-          if (__any_sync(0xffffffffu, lb)) {
-            blocked = true;
-            break;
-          }
-          const uint32_t wm = __ballot_sync(0xffffffffu, lw);
-          if (wm && wait_u < 0) {
-            const int src = __ffs(wm) - 1;
-            wait_u = __shfl_sync(0xffffffffu, u, src);
-            wait_w = __shfl_sync(0xffffffffu, wu, src);
-          }
-        }
-      }
-      if (blocked) {
-        ++k;
-        cur = 0;
-        if (k < L && lane == 0) publish(a.state, v, ((uint32_t)a.lists[row + k] << 2) | kUndecided);
-        continue;
-      }
-      if (wait_u >= 0) {
-        if (lane == 0) {
-          a.kcur[v] = (uint16_t)k;
-          a.rcur[v] = (uint32_t)((first_wait >= 0 ? first_wait : r1) - rs);
-          a.blk[v] = wait_u;
-          a.blkw[v] = wait_w;
-          work_out[atomicAdd(nwork_out, 1)] = v;
-        }
-        break;
-      }
-      if (lane == 0) publish(a.state, v, (c << 2) | kColored);
-      break;
     }
+    if (blocked) {
+      ++k;
+      cur = 0;
+      if (k < L && lane == 0) publish(a.state, v, ((uint32_t)a.lists[row + k] << 2) | kUndecided);
+      continue;
+    }
+    if (wait_u >= 0) {
+      if (lane == 0) {
+        a.kcur[v] = (uint16_t)k;
+        a.rcur[v] = (uint32_t)((first_wait >= 0 ? first_wait : r1) - rs);
+        a.blk[v] = wait_u;
+        a.blkw[v] = c;
+        work_out[atomicAdd(nwork_out, 1)] = v;
+      }
+      return;
+    }
+    if (lane == 0) publish(a.state, v, (c << 2) | kColored);
+    return;
   }
 }
 
-// Wake check, one thread per pending vertex: nothing can have changed for v
-// while the neighbour it waited on still shows the state word v saw, so v
-// stays pending without a rescan; otherwise v goes to the active list that
-// the sweep evaluates.  Appends are warp-aggregated.
-__global__ void __launch_bounds__(256) k_color_wake(const int32_t* __restrict__ blk, const uint32_t* __restrict__ blkw,
-                                                    const uint64_t* __restrict__ state,
-                                                    const int32_t* __restrict__ work_in,
+// Wake check of the pending items [b0, b0 + 32) of `in` by one warp: v stays
+// pending without a rescan while the neighbour it waited on is still
+// undecided with a candidate at or below v's candidate color (v could not
+// decide anything new); otherwise v goes to the active list.  Appends are
+// warp-aggregated.
+__device__ __forceinline__ void wake_chunk(const ColorArgs& a, const int32_t* __restrict__ in, int64_t nin,
+                                           int64_t b0, int lane, uint32_t lt, int32_t* __restrict__ active,
+                                           int32_t* __restrict__ nactive, int32_t* __restrict__ out,
+                                           int32_t* __restrict__ nout) {
+  const int64_t w = b0 + lane;
+  int32_t v = -1;
+  bool stay = false;
+  if (w < nin) {
+    v = __ldcg(&in[w]);
+    const int32_t b = a.blk[v];
+    if (b >= 0) {
+      const uint32_t wb = (uint32_t)__ldcg(&a.state[b]);
+      stay = (wb & 3u) == kUndecided && (wb >> 2) <= a.blkw[v];
+    }
+  }
+  const uint32_t ms = __ballot_sync(0xffffffffu, w < nin && stay);
+  const uint32_t ma = __ballot_sync(0xffffffffu, w < nin && !stay);
+  int32_t bs = 0, ba = 0;
+  if (lane == 0) {
+    if (ms) bs = atomicAdd(nout, __popc(ms));
+    if (ma) ba = atomicAdd(nactive, __popc(ma));
+  }
+  bs = __shfl_sync(0xffffffffu, bs, 0);
+  ba = __shfl_sync(0xffffffffu, ba, 0);
+  if (w < nin) {
+    if (stay)
+      out[bs + __popc(ms & lt)] = v;
+    else
+      active[ba + __popc(ma & lt)] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// All sweeps of one round in a single cooperative launch: per sweep, a wake
+// phase (thread per pending vertex) and an evaluation phase (warp per active
+// vertex), separated by grid barriers; no host round trip between sweeps.
+// ctl[0] pending count, ctl[1] next pending count, ctl[2] active count,
+// ctl[3] sweeps run, ctl[4] set to 1 if max_sweeps ran out.  Every thread
+// takes every barrier: the loop exits depend only on values all threads read
+// after the same barrier.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 4) k_color_all(ColorArgs a, int32_t* __restrict__ wa, int32_t* __restrict__ wb,
+                                                      int32_t* __restrict__ wact, int32_t* __restrict__ ctl,
+                                                      int32_t max_sweeps) {
+  cg::grid_group g = cg::this_grid();
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
+  const int64_t gwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t wid = tid >> 5;
+  int32_t* in = wa;
+  int32_t* out = wb;
+  int32_t sweep = 0;
+  while (true) {
+    const int32_t nin = __ldcg(&ctl[0]);
+    if (nin == 0) break;
+    if (sweep >= max_sweeps) {
+      if (tid == 0) ctl[4] = 1;
+      break;
+    }
+    if (tid == 0 && sweep < kSweepLog) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      ctl[8 + sweep] = nin;
+      reinterpret_cast<unsigned long long*>(ctl + 8 + kSweepLog)[sweep] = t;
+    }
+    for (int64_t b0 = wid * 32; b0 < nin; b0 += gwarps * 32)
+      wake_chunk(a, in, nin, b0, lane, lt, wact, &ctl[2], out, &ctl[1]);
+    g.sync();
+    const int32_t nact = __ldcg(&ctl[2]);
+    for (int64_t w = wid; w < nact; w += gwarps) eval_vertex(a, __ldcg(&wact[w]), lane, out, &ctl[1]);
+    g.sync();
+    if (tid == 0) {
+      ctl[0] = __ldcg(&ctl[1]);
+      ctl[1] = 0;
+      ctl[2] = 0;
+      ctl[3] = sweep + 1;
+      if (sweep < kSweepLog) ctl[8 + 3 * kSweepLog + sweep] = nact;
+    }
+    g.sync();
+    int32_t* t = in;
+    in = out;
+    out = t;
+    ++sweep;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Ordered persistent coloring.  `order` lists the round's vertices in exact
+// coloring order; warp w takes positions w, w + W, w + 2W, ... (W = warps in
+// the grid).  A vertex that has to wait polls the neighbour holding it up
+// instead of leaving for a later sweep.  No deadlock: the earliest unfinished
+// position's warp is working on it (all its earlier positions are done), and
+// that vertex waits only on earlier positions, which are finished; the
+// cooperative launch guarantees every warp is resident.  A poll budget
+// bounds every wait: when it runs out the kernel sets *err = 1 and the warp
+// returns; the caller then recolors the round with the sweep kernel.
+// ---------------------------------------------------------------------------
+constexpr int kMaxPolls = 1 << 20;
+
+__device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
+  const int L = a.L;
+  const uint32_t pv = (uint32_t)(__ldcg(&a.state[v]) >> 32);
+  const int64_t row = (int64_t)v * L;
+  int polls = 0;
+  for (int k = 0; k < L; ++k) {
+    const uint32_t c = (uint32_t)a.lists[row + k];
+    if (k > 0 && lane == 0) publish(a.state, v, (c << 2) | kUndecided);
+    const int64_t rs = a.runoff[row + k], r1 = a.runoff[row + k + 1];
+    const int64_t x0 = a.xoff[row + k], x1 = a.xoff[row + k + 1];
+    const int64_t nrun = r1 - rs, ntot = nrun + (x1 - x0);
+    bool blocked = false;
+    // entries of the run then of the side list, in chunks of 32; a chunk
+    // with an undecided earlier neighbour at or below c is rescanned after
+    // that neighbour moves
+    for (int64_t e0 = 0; e0 < ntot && !blocked;) {
+      const int64_t e = e0 + lane;
+      bool lb = false, lw = false;
+      int32_t u = -1;
+      if (e < ntot) {
+        u = e < nrun ? a.col[rs + e] : a.xcol[x0 + (e - nrun)];
+        const uint64_t su = __ldcg(&a.state[u]);
+        const uint32_t pu = (uint32_t)(su >> 32);
+        if (pu < pv || (pu == pv && u < v)) {
+          const uint32_t wu = (uint32_t)su, st = wu & 3u, cu = wu >> 2;
+          lb = st == kColored && cu == c;
+          lw = st == kUndecided && cu <= c;
+        }
+      }
+      if (__any_sync(0xffffffffu, lb)) {
+        blocked = true;
+        break;
+      }
+      const uint32_t wm = __ballot_sync(0xffffffffu, lw);
+      if (wm == 0u) {
+        e0 += 32;
+        continue;
+      }
+      // wait for the first neighbour holding us up, then rescan this chunk
+      const int32_t wu_id = __shfl_sync(0xffffffffu, u, __ffs(wm) - 1);
+      while (true) {
+        const uint32_t w = (uint32_t)__ldcg(&a.state[wu_id]);
+        if ((w & 3u) != kUndecided || (w >> 2) > c) break;
+        if (++polls > kMaxPolls) {
+          if (lane == 0) atomicExch(err, 1);
+          return false;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (!blocked) {
+      if (lane == 0) publish(a.state, v, (c << 2) | kColored);
+      return true;
+    }
+  }
+  if (lane == 0) publish(a.state, v, (kFailedColor << 2) | kFailed);
+  return true;
+}
+
+__global__ void __launch_bounds__(256, 4) k_color_ordered(ColorArgs a, const int32_t* __restrict__ order,
+                                                          int32_t* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t t = wid; t < a.n; t += gwarps) {
+    if (!ordered_vertex(a, __ldcg(&order[t]), lane, err)) return;
+  }
+}
+
+cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32_t* err, cudaStream_t s) {
+  int dev = 0, sms = 148, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_color_ordered, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  int64_t blocks = (int64_t)per_sm * sms;
+  const int64_t want = (a.n + 7) / 8;
+  if (want < blocks) blocks = want > 0 ? want : 1;
+  ColorArgs args = a;
+  void* params[] = {(void*)&args, (void*)&order, (void*)&err};
+  e = cudaLaunchCooperativeKernel((const void*)k_color_ordered, dim3((unsigned)blocks), dim3(256), params, 0, s);
+  count_launches(1);
+  return e;
+}
+
+cudaError_t launch_color_all(const ColorArgs& a, int32_t* wa, int32_t* wb, int32_t* wact, int32_t* ctl,
+                             cudaStream_t s) {
+  int dev = 0, sms = 148, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_color_all, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  int64_t blocks = (int64_t)per_sm * sms;
+  const int64_t want = (a.n + 7) / 8;  // one warp per vertex at most
+  if (want < blocks) blocks = want > 0 ? want : 1;
+  ColorArgs args = a;
+  int32_t max_sweeps = (int32_t)(a.n + 4 < 0x7fffffff ? a.n + 4 : 0x7fffffff);
+  void* params[] = {(void*)&args, (void*)&wa, (void*)&wb, (void*)&wact, (void*)&ctl, (void*)&max_sweeps};
+  e = cudaLaunchCooperativeKernel((const void*)k_color_all, dim3((unsigned)blocks), dim3(256), params, 0, s);
+  count_launches(1);
+  return e;
+}
+
+// Single-sweep kernels (the same two phases, one launch each), for callers
+// that drive the sweeps from the host.
+__global__ void __launch_bounds__(256) k_color_wake(ColorArgs a, const int32_t* __restrict__ work_in,
                                                     const int32_t* __restrict__ nwork_in, int32_t* __restrict__ active,
                                                     int32_t* __restrict__ nactive, int32_t* __restrict__ work_out,
                                                     int32_t* __restrict__ nwork_out) {
   const int64_t nin = *nwork_in;
   const int lane = threadIdx.x & 31;
   const uint32_t lt = lanemask_lt();
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nin; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t w = base + threadIdx.x;
-    int32_t v = -1;
-    bool stay = false;
-    if (w < nin) {
-      v = work_in[w];
-      const int32_t b = blk[v];
-      stay = b >= 0 && (uint32_t)__ldcg(&state[b]) == blkw[v];
-    }
-    const uint32_t ms = __ballot_sync(0xffffffffu, w < nin && stay);
-    const uint32_t ma = __ballot_sync(0xffffffffu, w < nin && !stay);
-    int32_t bs = 0, ba = 0;
-    if (lane == 0) {
-      if (ms) bs = atomicAdd(nwork_out, __popc(ms));
-      if (ma) ba = atomicAdd(nactive, __popc(ma));
-    }
-    bs = __shfl_sync(0xffffffffu, bs, 0);
-    ba = __shfl_sync(0xffffffffu, ba, 0);
-    if (w < nin) {
-      if (stay)
-        work_out[bs + __popc(ms & lt)] = v;
-      else
-        active[ba + __popc(ma & lt)] = v;
-    }
-  }
+  const int64_t gwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t b0 = wid * 32; b0 < nin; b0 += gwarps * 32)
+    wake_chunk(a, work_in, nin, b0, lane, lt, active, nactive, work_out, nwork_out);
 }
 
 cudaError_t launch_color_wake(const ColorArgs& a, const int32_t* work_in, const int32_t* nwork_in, int32_t* active,
@@ -239,10 +450,20 @@ cudaError_t launch_color_wake(const ColorArgs& a, const int32_t* work_in, const 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = (a.n + 255) / 256;
   const int64_t blocks = want < (int64_t)sms * 8 ? (want > 0 ? want : 1) : (int64_t)sms * 8;
-  k_color_wake<<<(unsigned)blocks, 256, 0, s>>>(a.blk, a.blkw, a.state, work_in, nwork_in, active, nactive, work_out,
-                                               nwork_out);
+  k_color_wake<<<(unsigned)blocks, 256, 0, s>>>(a, work_in, nwork_in, active, nactive, work_out, nwork_out);
   count_launches(1);
   return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256, 4) k_color_sweep(ColorArgs a, const int32_t* __restrict__ work_in,
+                                                        const int32_t* __restrict__ nwork_in,
+                                                        int32_t* __restrict__ work_out,
+                                                        int32_t* __restrict__ nwork_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t nin = *nwork_in;
+  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nin; w += nwarps)
+    eval_vertex(a, work_in[w], lane, work_out, nwork_out);
 }
 
 cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const int32_t* nwork_in,
@@ -257,7 +478,10 @@ cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const
   return cudaGetLastError();
 }
 
-// Carry: write colors to the global array and flag the vertices that failed.
+// ---------------------------------------------------------------------------
+// Carry
+// ---------------------------------------------------------------------------
+// Write colors to the global array and flag the vertices that failed.
 __global__ void k_carry_flags(const uint64_t* __restrict__ state, int64_t n, const int32_t* __restrict__ gid,
                               int64_t base, int32_t* __restrict__ color, uint32_t* __restrict__ flag) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -16,6 +16,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "picasso.h")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_INTERNAL, ERR_UNSUPPORTED, ERR_STATE = range(9)
 ALGOS = {"auto": 0, "allpairs": 1, "bucket": 2}
+COLOR_ALGOS = {"auto": 0, "sweep": 1}
 
 
 class PicassoError(RuntimeError):
@@ -34,6 +35,8 @@ class Config(ctypes.Structure):
         ("conflict_algo", ctypes.c_int32),
         ("max_rounds", ctypes.c_int32),
         ("byte_budget", ctypes.c_int64),
+        ("color_algo", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -57,6 +60,7 @@ class Stats(ctypes.Structure):
         ("peak_bytes", ctypes.c_int64),
         ("conflict_algo_used", ctypes.c_int32),
         ("jp_sweeps", ctypes.c_int32),
+        ("ordered_fallbacks", ctypes.c_int32),
         ("max_bucket", ctypes.c_int64),
         ("rounds_done", ctypes.c_int32),
         ("t_assign_ms", ctypes.c_double),
@@ -67,10 +71,17 @@ class Stats(ctypes.Structure):
         ("pairs_launches", ctypes.c_int64),
         ("logical_pairs", ctypes.c_int64),
         ("tested_pairs", ctypes.c_int64),
+        ("sweep_pending", ctypes.c_int32 * 64),
+        ("sweep_active", ctypes.c_int32 * 64),
+        ("sweep_us", ctypes.c_float * 64),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if hasattr(v, "__len__") else v
+        return d
 
 
 _LIB = None
@@ -178,7 +189,8 @@ class Picasso:
     """A context over packed strings ``xz`` (int64 [n, 2] on the GPU)."""
 
     def __init__(self, xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
-                 algo: str = "auto", max_rounds: int = 100000, byte_budget: int = 0, stream=None):
+                 algo: str = "auto", max_rounds: int = 100000, byte_budget: int = 0, stream=None,
+                 color: str = "auto"):
         assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2
         self.xz = xz.contiguous()
         self.n = int(xz.shape[0])
@@ -192,6 +204,7 @@ class Picasso:
         cfg.conflict_algo = ALGOS[algo]
         cfg.max_rounds = max_rounds
         cfg.byte_budget = byte_budget
+        cfg.color_algo = COLOR_ALGOS[color]
         self.cfg = cfg
         h = ctypes.c_void_p()
         _ck(_lib().picasso_init(ctypes.byref(h), ctypes.byref(cfg), _ptr(self.xz), self.n, q,

@@ -163,26 +163,28 @@ def test_budget_rejects_before_allocation(pc):
 
 
 # ------------------------------------------------------------------ coloring
-@pytest.mark.parametrize("algo", ["allpairs", "bucket"])
-def test_round_coloring_exact(pc, orc, algo):
+@pytest.mark.parametrize("algo,color", [("allpairs", "auto"), ("bucket", "auto"), ("bucket", "sweep")])
+def test_round_coloring_exact(pc, orc, algo, color):
     n, q, P, L, seed = 3000, 48, 375, 17, 11
     chars = synth.pauli_weighted(n, q, 0.25, seed=2)
     enc = orc.encode3(chars)
     lists = orc.draw_lists(seed, 1, np.arange(n), P, L, 0)
     off_r, col_r = orc.conflict_csr(enc, lists)
     ref = orc.color_greedy(seed, 1, np.arange(n), lists, off_r, col_r, P, 0)
-    with pc.Picasso(_xz(pc, chars), q, seed=seed, algo=algo) as p:
+    with pc.Picasso(_xz(pc, chars), q, seed=seed, algo=algo, color=color) as p:
         p.assign_lists(P, L, 0)
         p.build_conflicts()
         k = p.color()
+        assert p.stats()["ordered_fallbacks"] == 0
         got = p.colors().cpu().numpy()
         assert k == int((ref >= 0).sum())
         assert np.array_equal(got, ref)
 
 
-def _run_both(pc, orc, chars, seed, num, den, alpha, algo="auto"):
+def _run_both(pc, orc, chars, seed, num, den, alpha, algo="auto", color="auto"):
     ref, rounds, stats = orc.run(chars, seed, num, den, alpha)
-    with pc.Picasso(_xz(pc, chars), chars.shape[1], seed=seed, palette=(num, den), alpha=alpha, algo=algo) as p:
+    with pc.Picasso(_xz(pc, chars), chars.shape[1], seed=seed, palette=(num, den), alpha=alpha, algo=algo,
+                    color=color) as p:
         got, r = p.run()
         got = got.cpu().numpy()
         assert r == rounds
@@ -191,9 +193,10 @@ def _run_both(pc, orc, chars, seed, num, den, alpha, algo="auto"):
     return ref
 
 
-def test_run_workload_small(pc, orc):
+@pytest.mark.parametrize("color", ["auto", "sweep"])
+def test_run_workload_small(pc, orc, color):
     # n=2000, q=20 uniform, P=n/8, alpha=2, seed 0: every round, every color
-    _run_both(pc, orc, synth.pauli_uniform(2000, 20, seed=0), 0, 1, 8, 2.0)
+    _run_both(pc, orc, synth.pauli_uniform(2000, 20, seed=0), 0, 1, 8, 2.0, color=color)
 
 
 @pytest.mark.parametrize("algo", ["allpairs", "bucket"])
@@ -201,9 +204,10 @@ def test_run_weighted(pc, orc, algo):
     _run_both(pc, orc, synth.pauli_weighted(4000, 48, 0.25, seed=1), 5, 1, 8, 2.0, algo)
 
 
-def test_run_throughput_law_small(pc, orc):
+@pytest.mark.parametrize("color", ["auto", "sweep"])
+def test_run_throughput_law_small(pc, orc, color):
     # the n=1M law (q=64, p=0.25, P=n/16, alpha=1.5) at a size the oracle runs
-    _run_both(pc, orc, synth.pauli_weighted(5000, 64, 0.25, seed=3), 0, 1, 16, 1.5)
+    _run_both(pc, orc, synth.pauli_weighted(5000, 64, 0.25, seed=3), 0, 1, 16, 1.5, color=color)
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 257])
