@@ -224,7 +224,8 @@ def run_gpu(args):
     assert (colors_np >= 0).all(), "uncolored vertices after a full run"
     st = stats[-1]
     # the library's counters are per context and there is one context per step
-    per_step = {k: st[k] for k in ("t_assign_ms", "t_build_ms", "t_color_ms", "t_carry_ms", "t_pairs_ms")}
+    per_step = {k: st[k] for k in ("t_assign_ms", "t_build_ms", "t_color_ms", "t_carry_ms", "t_pairs_ms",
+                                   "t_emit_ms")}
     steps_ms = ms / args.steps
     value = world * n / (steps_ms / 1e3)
     pair_rate = st["logical_pairs"] / (st["t_build_ms"] / 1e3)

@@ -123,13 +123,19 @@ typedef struct {
   double t_build_ms;    /* conflict build (buckets, count, scans, fill)      */
   double t_color_ms;    /* coloring sweeps + color write-back                */
   double t_carry_ms;    /* compaction of the uncolored vertices              */
-  double t_pairs_ms;    /* the pair-test kernels alone (count and fill)      */
+  double t_pairs_ms;    /* the pair-test kernels alone (bucket join: mask
+                           pass; all pairs: count and fill)                 */
   int64_t pairs_launches;     /* launches of the pair-test kernels           */
   int64_t logical_pairs;      /* sum over builds of n_l (n_l - 1) / 2        */
   int64_t tested_pairs;       /* pair tests of the pair-test kernels: per
-                                 build, bucket join 1.5 sum_c s_c (s_c - 1)
-                                 (count pass: unordered pairs, fill pass:
-                                 ordered), all pairs 2 n (n - 1)            */
+                                 build, bucket join sum_c s_c (s_c - 1) / 2
+                                 (the mask pass tests each unordered pair of
+                                 a bucket once), all pairs 2 n (n - 1)      */
+  double t_emit_ms;           /* bucket join's emit pass (CSR writes)        */
+  int64_t emit_launches;
+  int64_t emit_bytes;         /* bytes the emit passes move: mask words read,
+                                 CSR and side list written, member ids and
+                                 run/side offsets read                      */
   /* the last color step's first 64 sweeps: vertices pending at the start,
    * vertices re-evaluated, and duration in microseconds (0 for the last) */
   int32_t sweep_pending[64];

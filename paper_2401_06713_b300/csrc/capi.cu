@@ -105,8 +105,8 @@ struct Ctx {
   // timing (CUDA events on s): ev[0..1] phase, ev[2..5] pair kernels
   cudaEvent_t ev[6] = {};
   int32_t rounds_done = 0;
-  double t_assign = 0, t_build = 0, t_color = 0, t_carry = 0, t_pairs = 0;
-  int64_t pairs_launches = 0, logical_pairs = 0, tested_pairs = 0;
+  double t_assign = 0, t_build = 0, t_color = 0, t_carry = 0, t_pairs = 0, t_emit = 0;
+  int64_t pairs_launches = 0, logical_pairs = 0, tested_pairs = 0, emit_launches = 0, emit_bytes = 0;
 
   const uint64_t* round_xz() const { return xz ? xz : xz_user; }
 };
@@ -231,8 +231,9 @@ int build_conflicts(Ctx* c) {
   cudaStream_t s = c->s;
 
   uint32_t *cnt = nullptr, *xcnt = nullptr, *bcount = nullptr, *bcursor = nullptr, *dmax = nullptr;
+  uint32_t *words = nullptr, *rmask = nullptr, *xmask = nullptr;
   unsigned long long* dsq = nullptr;
-  int64_t* boff = nullptr;
+  int64_t *boff = nullptr, *moff = nullptr;
   int32_t* bmem = nullptr;
   void* tmp = nullptr;
   int st = PICASSO_OK;
@@ -245,6 +246,10 @@ int build_conflicts(Ctx* c) {
     release(c, &dsq);
     release(c, &boff);
     release(c, &bmem);
+    release(c, &words);
+    release(c, &moff);
+    release(c, &rmask);
+    release(c, &xmask);
     release(c, (uint8_t**)&tmp);
   };
 #define TRY(expr)                  \
@@ -313,9 +318,23 @@ int build_conflicts(Ctx* c) {
     TRYC(launch_bucket_fill(c->lists, n, L, boff, bcursor, bmem, s));
     release(c, &bcursor);
     TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, s));
+    // mask words: bucket c holds s_c rows of ceil(s_c / 32) words
+    TRY(alloc(c, &words, P));
+    TRY(alloc(c, &moff, P + 1));
+    TRYC(launch_bucket_words(bcount, P, words, s));
+    TRYC(launch_scan_u32(words, P, moff, tmp, s));
+    TRYC(cudaMemcpyAsync(c->h_buf, moff + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TRYC(cudaStreamSynchronize(s));
+    const int64_t nwords = c->h_buf[0];
+    release(c, &words);
+    TRY(alloc(c, &rmask, nwords));
+    TRY(alloc(c, &xmask, nwords));
+    a.rmask = rmask;
+    a.xmask = xmask;
     TRYC(cudaEventRecord(c->ev[2], s));
-    TRYC(launch_bucket_pairs(a, boff, bmem, (int32_t)smax, false, s));
+    TRYC(launch_bucket_mask(a, boff, bmem, moff, (int32_t)smax, s));
     TRYC(cudaEventRecord(c->ev[3], s));
+    c->emit_bytes += 8 * nwords;  // the emit pass reads both words of every row chunk
   } else {
     TRYC(cudaEventRecord(c->ev[2], s));
     TRYC(launch_allpairs(a, false, s));
@@ -355,18 +374,28 @@ int build_conflicts(Ctx* c) {
   a.xcol = c->xcol;
   TRYC(cudaEventRecord(c->ev[4], s));
   if (algo == PICASSO_CONFLICT_BUCKET) {
-    TRYC(launch_bucket_pairs(a, boff, bmem, (int32_t)smax, true, s));
+    TRYC(launch_bucket_emit(a, boff, bmem, moff, (int32_t)smax, s));
   } else {
     TRYC(launch_allpairs(a, true, s));
   }
   TRYC(cudaEventRecord(c->ev[5], s));
   TRYC(launch_row_offsets(c->runoff, n, L, c->off, s));
   TRYC(cudaEventSynchronize(c->ev[5]));
-  c->t_pairs += elapsed(c, 2, 3) + elapsed(c, 4, 5);
-  c->pairs_launches += 2;
-  // the bucket count pass tests each unordered pair once, the fill pass both
-  // orders; the all-pairs kernel tests every ordered pair in both passes
-  c->tested_pairs += algo == PICASSO_CONFLICT_BUCKET ? tested + tested / 2 : 2 * tested;
+  if (algo == PICASSO_CONFLICT_BUCKET) {
+    // the mask pass tests every unordered pair of a bucket once; the emit
+    // pass streams the words and writes the CSR
+    c->t_pairs += elapsed(c, 2, 3);
+    c->pairs_launches += 1;
+    c->tested_pairs += tested / 2;
+    c->t_emit += elapsed(c, 4, 5);
+    c->emit_launches += 1;
+    c->emit_bytes += 4 * (nnz + nx) + 4 * nl + 16 * nl;  // CSR writes, member ids, run/side offsets
+  } else {
+    // the all-pairs kernel tests every ordered pair in both passes
+    c->t_pairs += elapsed(c, 2, 3) + elapsed(c, 4, 5);
+    c->pairs_launches += 2;
+    c->tested_pairs += 2 * tested;
+  }
   c->logical_pairs += n * (n - 1) / 2;
   cleanup();
   c->nnz = nnz;
@@ -784,6 +813,9 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->pairs_launches = c->pairs_launches;
   out->logical_pairs = c->logical_pairs;
   out->tested_pairs = c->tested_pairs;
+  out->t_emit_ms = c->t_emit;
+  out->emit_launches = c->emit_launches;
+  out->emit_bytes = c->emit_bytes;
   const int ns = c->sweeps < kSweepLog ? c->sweeps : kSweepLog;
   const unsigned long long* t = reinterpret_cast<const unsigned long long*>(c->sweep_log + 8 + kSweepLog);
   for (int i = 0; i < ns; ++i) {

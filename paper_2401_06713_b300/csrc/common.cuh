@@ -97,6 +97,9 @@ struct ConflictArgs {
   int32_t* col;          // [nnz]                      (fill pass)
   int32_t* xcol;         // [n_extra]                  (fill pass)
   int32_t* err;          // device error word
+  uint32_t* rmask;       // bucket join: run words      (mask pass -> emit)
+  uint32_t* xmask;       // bucket join: side-list words (mask pass -> emit)
+  int32_t smax;          // bucket join: largest bucket (emit pass)
 };
 
 // Buckets: members of color c are bmem[boff[c] .. boff[c+1]) ascending.
@@ -109,8 +112,13 @@ cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, in
 // out32[0] = max bucket size; out64[0] = sum over buckets of s (s - 1).
 cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out32,
                                 unsigned long long* out64, cudaStream_t s);
-cudaError_t launch_bucket_pairs(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
-                                int32_t smax, bool fill, cudaStream_t s);
+// Bucket join: mask words per bucket (k_bucket_words + scan -> moff), the
+// mask pass (pair tests, counts, words), then the emit pass (CSR writes).
+cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, uint32_t* words, cudaStream_t s);
+cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
+                               const int64_t* moff, int32_t smax, cudaStream_t s);
+cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
+                               const int64_t* moff, int32_t smax, cudaStream_t s);
 cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s);
 cudaError_t launch_row_offsets(const int64_t* runoff, int64_t n, int32_t L, int64_t* off,
                                cudaStream_t s);

@@ -155,8 +155,8 @@ struct BucketSmem {
   uint16_t* kk;
   int32_t* exo;   // [smax + 1]
   int32_t* excur; // [smax]
-  int32_t* scnt;  // [smax] run counts (count pass)
-  int32_t* sxcnt; // [smax] side-list counts (count pass)
+  int32_t* scnt;  // [smax] run counts
+  int32_t* sxcnt; // [smax] side-list counts
   uint16_t* exv;  // [2 * kExCap]
   uint32_t* expair;
   uint32_t* tab;  // [hs]
@@ -214,163 +214,101 @@ __device__ inline bool share_prefix(const int32_t* __restrict__ a, int ka, const
 
 }  // namespace
 
-// Row state of the pair loops: a member row's words split in 32-bit halves
-// and a cursor into its ascending exclusion list (partners that share a
-// smaller color, so their entry belongs to the side list at this color).
-struct PairRow {
-  uint32_t xl, xh, zl, zh;
-  int ep, ee;   // exclusion list cursor / end
-  int nextex;   // next excluded partner (or a large value)
-};
-
-__device__ __forceinline__ void row_init(PairRow& R, const BucketSmem& S, int i, int s, bool slow) {
-  const bool ok = i < s;
-  const uint64_t x = ok ? S.sx[i] : 0ull, z = ok ? S.sz[i] : 0ull;
-  R.xl = (uint32_t)x;
-  R.xh = (uint32_t)(x >> 32);
-  R.zl = (uint32_t)z;
-  R.zh = (uint32_t)(z >> 32);
-  R.ep = R.ee = 0;
-  if (ok && !slow) {
-    R.ep = S.exo[i];
-    R.ee = S.exo[i + 1];
-  }
-  R.nextex = R.ep < R.ee ? (int)S.exv[R.ep] : 0x7fffffff;
-}
-
-// Bits of the excluded partners inside chunk [j0, j0 + 32); the cursor only
-// moves forward because chunks are visited in ascending order.
-__device__ __forceinline__ uint32_t row_excl(PairRow& R, const BucketSmem& S, int j0) {
+// Mask pass over the pairs of a bucket, one 32 x 32 block (row chunk I,
+// partner chunk J >= I) per warp step.  Lane t tests partner J*32 + t
+// against each row of chunk I; the ballots give row words (partners of
+// chunk J), and a 32-ballot bit transpose gives the words of the rows of
+// chunk J for partners of chunk I -- every relation used (commutation,
+// sharing a smaller color, i != j) is symmetric, so each unordered pair is
+// tested once.  The run word keeps partners whose smallest shared color with
+// the row is this bucket's color; the side word keeps the others.  Words of
+// row i, chunk w live at masks + i * nwb + w; per-row counts accumulate in
+// shared memory.
+__device__ __forceinline__ uint32_t excl_bits(const BucketSmem& S, int i, int j0) {
   uint32_t exm = 0u;
-  while (R.nextex < j0 + 32) {
-    if (R.nextex >= j0) exm |= 1u << (R.nextex - j0);
-    ++R.ep;
-    R.nextex = R.ep < R.ee ? (int)S.exv[R.ep] : 0x7fffffff;
+  for (int e = S.exo[i], e1 = S.exo[i + 1]; e < e1; ++e) {
+    const uint32_t d = (uint32_t)S.exv[e] - (uint32_t)j0;
+    if (d < 32u) exm |= 1u << d;
   }
   return exm;
 }
 
-__device__ __forceinline__ bool row_commutes(const PairRow& R, uint32_t xjl, uint32_t xjh, uint32_t zjl,
-                                             uint32_t zjh) {
-  const uint32_t t = ((R.xl & zjl) ^ (R.zl & xjl)) ^ ((R.xh & zjh) ^ (R.zh & xjh));
-  return (__popc(t) & 1) == 0;
+__device__ __forceinline__ void store_words(BucketSmem& S, int row, int s, int nwb, int w, uint32_t rm, uint32_t xm,
+                                            uint32_t* __restrict__ rmask, uint32_t* __restrict__ xmask) {
+  if (row < s) {
+    rmask[(int64_t)row * nwb + w] = rm;
+    xmask[(int64_t)row * nwb + w] = xm;
+    if (rm) atomicAdd(&S.scnt[row], __popc(rm));
+    if (xm) atomicAdd(&S.sxcnt[row], __popc(xm));
+  }
 }
 
-// Count pass over unordered pairs {i, j}, j > i: each hit adds one to the
-// row's count (registers) and one to the partner's (a per-lane column count
-// added to shared memory once per chunk).
-template <int R, bool SLOW>
-__device__ void count_rows(const ConflictArgs& a, BucketSmem& S, int s, int L, int lane, int wid, int nw) {
-  for (int i0 = wid * R; i0 < s; i0 += nw * R) {
-    PairRow row[R];
-    uint32_t rc[R], xc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      row_init(row[r], S, i0 + r, s, SLOW);
-      rc[r] = xc[r] = 0u;
+template <bool SLOW>
+__device__ void mask_blocks(const ConflictArgs& a, BucketSmem& S, int s, int L, int lane, int wid, int nw,
+                            uint32_t* __restrict__ rmask, uint32_t* __restrict__ xmask) {
+  const int nwb = (s + 31) >> 5;
+  const int nblk = nwb * (nwb + 1) / 2;
+  for (int q = wid; q < nblk; q += nw) {
+    // q -> (I, J), J >= I, row-major over the upper triangle
+    int I = 0, rem = q;
+    while (rem >= nwb - I) {
+      rem -= nwb - I;
+      ++I;
     }
-    for (int j0 = (i0 + 1) & ~31; j0 < s; j0 += 32) {
-      const int j = j0 + lane;
-      const bool valid = j < s;
-      const uint64_t xj = valid ? S.sx[j] : 0ull, zj = valid ? S.sz[j] : 0ull;
-      const uint32_t xjl = (uint32_t)xj, xjh = (uint32_t)(xj >> 32);
-      const uint32_t zjl = (uint32_t)zj, zjh = (uint32_t)(zj >> 32);
-      int colr = 0, colx = 0;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int i = i0 + r;
-        const bool hit = valid && j > i && i < s && row_commutes(row[r], xjl, xjh, zjl, zjh);
-        const uint32_t m = __ballot_sync(0xffffffffu, hit);
-        uint32_t exm;
-        if (!SLOW) {
-          exm = row_excl(row[r], S, j0);
-        } else {
-          const bool ex = hit && share_prefix(a.lists + (int64_t)S.sid[i] * L, S.kk[i],
-                                              a.lists + (int64_t)S.sid[j] * L, S.kk[j]);
-          exm = __ballot_sync(0xffffffffu, ex);
-        }
-        const uint32_t rm = m & ~exm, xm = m & exm;
-        rc[r] += __popc(rm);
-        xc[r] += __popc(xm);
-        colr += (int)((rm >> lane) & 1u);
-        colx += (int)((xm >> lane) & 1u);
+    const int J = I + rem;
+    const int j = (J << 5) + lane;
+    const bool valid = j < s;
+    const uint64_t xj = valid ? S.sx[j] : 0ull, zj = valid ? S.sz[j] : 0ull;
+    const uint32_t xjl = (uint32_t)xj, xjh = (uint32_t)(xj >> 32);
+    const uint32_t zjl = (uint32_t)zj, zjh = (uint32_t)(zj >> 32);
+    uint32_t my_r = 0u, my_x = 0u;
+    const int rows = min(32, s - (I << 5));
+    for (int r = 0; r < rows; ++r) {
+      const int i = (I << 5) + r;
+      const uint64_t xi = S.sx[i], zi = S.sz[i];
+      const uint32_t t = (((uint32_t)xi & zjl) ^ ((uint32_t)zi & xjl)) ^
+                         (((uint32_t)(xi >> 32) & zjh) ^ ((uint32_t)(zi >> 32) & xjh));
+      const bool hit = valid && j != i && (__popc(t) & 1) == 0;
+      const uint32_t m = __ballot_sync(0xffffffffu, hit);
+      uint32_t exm;
+      if (!SLOW) {
+        exm = S.exo[i + 1] > S.exo[i] ? excl_bits(S, i, J << 5) : 0u;
+      } else {
+        const bool ex = ((m >> lane) & 1u) && share_prefix(a.lists + (int64_t)S.sid[i] * L, S.kk[i],
+                                                           a.lists + (int64_t)S.sid[j] * L, S.kk[j]);
+        exm = __ballot_sync(0xffffffffu, ex);
       }
-      if (colr) atomicAdd(&S.scnt[j], colr);
-      if (colx) atomicAdd(&S.sxcnt[j], colx);
+      if (lane == r) {
+        my_r = m & ~exm;
+        my_x = m & exm;
+      }
     }
-    if (lane == 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (i0 + r < s) {
-          if (rc[r]) atomicAdd(&S.scnt[i0 + r], (int)rc[r]);
-          if (xc[r]) atomicAdd(&S.sxcnt[i0 + r], (int)xc[r]);
+    store_words(S, (I << 5) + lane, s, nwb, J, my_r, my_x, rmask, xmask);
+    if (J != I) {
+      uint32_t tr = 0u, tx = 0u;
+#pragma unroll 8
+      for (int b = 0; b < 32; ++b) {
+        const uint32_t cr = __ballot_sync(0xffffffffu, (my_r >> b) & 1u);
+        const uint32_t cx = __ballot_sync(0xffffffffu, (my_x >> b) & 1u);
+        if (lane == b) {
+          tr = cr;
+          tx = cx;
         }
       }
+      store_words(S, (J << 5) + lane, s, nwb, I, tr, tx, rmask, xmask);
     }
   }
 }
 
-// Fill pass over ordered pairs: row i's partners in ascending j, written at
-// the run's offset with ballot + prefix popcount (deterministic order).
-template <int R, bool SLOW>
-__device__ void fill_rows(const ConflictArgs& a, BucketSmem& S, int s, int L, int lane, int wid, int nw,
-                          uint32_t lt) {
-  for (int i0 = wid * R; i0 < s; i0 += nw * R) {
-    PairRow row[R];
-    int32_t* rp[R];
-    int32_t* xp[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int i = i0 + r;
-      row_init(row[r], S, i, s, SLOW);
-      rp[r] = a.col;
-      xp[r] = a.xcol;
-      if (i < s) {
-        const int64_t slot = (int64_t)S.sid[i] * L + S.kk[i];
-        rp[r] = a.col + a.runoff[slot];
-        xp[r] = a.xcol + a.xoff[slot];
-      }
-    }
-    for (int j0 = 0; j0 < s; j0 += 32) {
-      const int j = j0 + lane;
-      const bool valid = j < s;
-      const uint64_t xj = valid ? S.sx[j] : 0ull, zj = valid ? S.sz[j] : 0ull;
-      const uint32_t xjl = (uint32_t)xj, xjh = (uint32_t)(xj >> 32);
-      const uint32_t zjl = (uint32_t)zj, zjh = (uint32_t)(zj >> 32);
-      const int32_t vj = valid ? S.sid[j] : 0;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int i = i0 + r;
-        const bool hit = valid && j != i && i < s && row_commutes(row[r], xjl, xjh, zjl, zjh);
-        const uint32_t m = __ballot_sync(0xffffffffu, hit);
-        uint32_t exm;
-        if (!SLOW) {
-          exm = row_excl(row[r], S, j0);
-        } else {
-          const bool ex = hit && share_prefix(a.lists + (int64_t)S.sid[i] * L, S.kk[i],
-                                              a.lists + (int64_t)vj * L, S.kk[j]);
-          exm = __ballot_sync(0xffffffffu, ex);
-        }
-        const uint32_t rm = m & ~exm, xm = m & exm;
-        if ((rm >> lane) & 1u) rp[r][__popc(rm & lt)] = vj;
-        if ((xm >> lane) & 1u) xp[r][__popc(xm & lt)] = vj;
-        rp[r] += __popc(rm);
-        xp[r] += __popc(xm);
-      }
-    }
-  }
-}
-
-template <bool FILL, int kRows>
-__global__ void __launch_bounds__(kPairThreads, 2) k_bucket_pairs(ConflictArgs a, const int64_t* __restrict__ boff,
-                                                               const int32_t* __restrict__ bmem, int smax,
-                                                               int hs_log2) {
+__global__ void __launch_bounds__(kPairThreads, 2) k_bucket_mask(ConflictArgs a, const int64_t* __restrict__ boff,
+                                                              const int32_t* __restrict__ bmem,
+                                                              const int64_t* __restrict__ moff, int smax,
+                                                              int hs_log2) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int hs = 1 << hs_log2;
   BucketSmem S = carve(smem_raw, smax, hs);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int L = a.L;
-  const uint32_t lt = lanemask_lt();
 
   for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
     const int64_t o = boff[b];
@@ -476,38 +414,29 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_bucket_pairs(ConflictArgs a
       __syncthreads();
     }
 
-    if (FILL) {
-      if (slow)
-        fill_rows<kRows, true>(a, S, s, L, lane, wid, nw, lt);
-      else
-        fill_rows<kRows, false>(a, S, s, L, lane, wid, nw, lt);
-    } else {
-      if (slow)
-        count_rows<kRows, true>(a, S, s, L, lane, wid, nw);
-      else
-        count_rows<kRows, false>(a, S, s, L, lane, wid, nw);
-      __syncthreads();
-      for (int i = threadIdx.x; i < s; i += blockDim.x) {
-        const int64_t slot = (int64_t)S.sid[i] * L + S.kk[i];
-        a.cnt[slot] = (uint32_t)S.scnt[i];
-        a.xcnt[slot] = (uint32_t)S.sxcnt[i];
-      }
+    if (slow)
+      mask_blocks<true>(a, S, s, L, lane, wid, nw, a.rmask + moff[b], a.xmask + moff[b]);
+    else
+      mask_blocks<false>(a, S, s, L, lane, wid, nw, a.rmask + moff[b], a.xmask + moff[b]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < s; i += blockDim.x) {
+      const int64_t slot = (int64_t)S.sid[i] * L + S.kk[i];
+      a.cnt[slot] = (uint32_t)S.scnt[i];
+      a.xcnt[slot] = (uint32_t)S.sxcnt[i];
     }
     __syncthreads();
   }
 }
 
-cudaError_t launch_bucket_pairs(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, int32_t smax,
-                                bool fill, cudaStream_t s) {
+cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
+                               int32_t smax, cudaStream_t s) {
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   smax = max(smax, 1);
   int64_t want = (int64_t)smax * (int64_t)max(a.L - 1, 1) * 3 / 2;
   int hs_log2 = 8;
   while ((1ll << hs_log2) < want && hs_log2 < 14) ++hs_log2;
   const size_t bytes = bucket_smem_bytes(smax, 1 << hs_log2);
-  // member rows per warp: 4 in the count pass, 2 in the fill pass (which
-  // keeps two output cursors per row in registers)
-  auto kern = fill ? k_bucket_pairs<true, 2> : k_bucket_pairs<false, 4>;
+  auto kern = k_bucket_mask;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -517,7 +446,97 @@ cudaError_t launch_bucket_pairs(const ConflictArgs& a, const int64_t* boff, cons
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
-  kern<<<(unsigned)blocks, kPairThreads, bytes, s>>>(a, boff, bmem, smax, hs_log2);
+  kern<<<(unsigned)blocks, kPairThreads, bytes, s>>>(a, boff, bmem, moff, smax, hs_log2);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Mask words of bucket c: s_c rows of ceil(s_c / 32) words.
+__global__ void k_bucket_words(const uint32_t* __restrict__ bcount, int64_t P, uint32_t* __restrict__ words) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < P) words[b] = bcount[b] * ((bcount[b] + 31u) >> 5);
+}
+
+cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, uint32_t* words, cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  k_bucket_words<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(bcount, P, words);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Emit pass: streaming compaction of the mask words into the CSR.  One warp
+// per member row; the run's entries are written in ascending partner order
+// (ballot positions within a word, words in ascending order).
+__global__ void __launch_bounds__(512) k_bucket_emit(ConflictArgs a, const int64_t* __restrict__ boff,
+                                                     const int32_t* __restrict__ bmem,
+                                                     const int64_t* __restrict__ moff) {
+  extern __shared__ __align__(16) int32_t emit_smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int L = a.L;
+  const uint32_t lt = lanemask_lt();
+  const int smax = a.smax;
+  int32_t* vid = emit_smem;          // [smax] member vertex ids
+  int32_t* flat = emit_smem + smax;  // [smax] v * L + k
+  for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
+    const int64_t o = boff[b];
+    const int s = (int)(boff[b + 1] - o);
+    if (s == 0) continue;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) {
+      const int32_t f = bmem[o + i];
+      flat[i] = f;
+      vid[i] = f / L;
+    }
+    __syncthreads();
+    const int nwb = (s + 31) >> 5;
+    const uint32_t* rmb = a.rmask + moff[b];
+    const uint32_t* xmb = a.xmask + moff[b];
+    for (int i = wid; i < s; i += nw) {
+      const int64_t slot = flat[i];
+      int32_t* rp = a.col + a.runoff[slot];
+      const int64_t x0 = a.xoff[slot], x1 = a.xoff[slot + 1];
+      const uint32_t* rrow = rmb + (int64_t)i * nwb;
+      for (int w0 = 0; w0 < nwb; w0 += 32) {
+        // each lane loads one word; the warp then walks them in order and
+        // writes each word's partners with one coalesced store
+        const int wl = w0 + lane;
+        const uint32_t rml = wl < nwb ? __ldg(rrow + wl) : 0u;
+        const int nwords = min(32, nwb - w0);
+#pragma unroll 4
+        for (int t = 0; t < nwords; ++t) {
+          const uint32_t rm = __shfl_sync(0xffffffffu, rml, t);
+          const int j = ((w0 + t) << 5) + lane;
+          if ((rm >> lane) & 1u) rp[__popc(rm & lt)] = vid[j];
+          rp += __popc(rm);
+        }
+      }
+      if (x1 > x0) {  // side-list entries are rare: only rows that have some
+        int32_t* xp = a.xcol + x0;
+        const uint32_t* xrow = xmb + (int64_t)i * nwb;
+        for (int w = 0; w < nwb; ++w) {
+          const uint32_t xm = __ldg(xrow + w);
+          const int j = (w << 5) + lane;
+          if ((xm >> lane) & 1u) xp[__popc(xm & lt)] = vid[j];
+          xp += __popc(xm);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
+                               int32_t smax, cudaStream_t s) {
+  if (a.P <= 0 || a.n <= 0) return cudaSuccess;
+  const size_t bytes = 2 * sizeof(int32_t) * (size_t)max(smax, 1);
+  ConflictArgs args = a;
+  args.smax = max(smax, 1);
+  cudaError_t e = cudaFuncSetAttribute(k_bucket_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * 4);
+  k_bucket_emit<<<(unsigned)blocks, 512, bytes, s>>>(args, boff, bmem, moff);
   count_launches(1);
   return cudaGetLastError();
 }

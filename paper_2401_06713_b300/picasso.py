@@ -71,6 +71,9 @@ class Stats(ctypes.Structure):
         ("pairs_launches", ctypes.c_int64),
         ("logical_pairs", ctypes.c_int64),
         ("tested_pairs", ctypes.c_int64),
+        ("t_emit_ms", ctypes.c_double),
+        ("emit_launches", ctypes.c_int64),
+        ("emit_bytes", ctypes.c_int64),
         ("sweep_pending", ctypes.c_int32 * 64),
         ("sweep_active", ctypes.c_int32 * 64),
         ("sweep_us", ctypes.c_float * 64),
