@@ -243,6 +243,32 @@ __device__ __forceinline__ void store_words(BucketSmem& S, int row, int s, int n
   }
 }
 
+// The 32 rows of chunk I against this lane's partner j: ballot words, the
+// one for row I*32 + r kept by lane r.  DIAG: the block is on the diagonal
+// (J == I), so partner j may be the row itself.
+template <bool DIAG>
+__device__ __forceinline__ uint32_t block_rows(const BucketSmem& S, int s, int ib, int j, bool valid, int lane,
+                                               uint32_t xjl, uint32_t xjh, uint32_t zjl, uint32_t zjh) {
+  uint32_t my_m = 0u;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const int i = ib + r;
+    const bool rowok = i < s;
+    uint64_t xi = 0ull, zi = 0ull;
+    if (rowok) {
+      xi = S.sx[i];
+      zi = S.sz[i];
+    }
+    const uint32_t t = (((uint32_t)xi & zjl) ^ ((uint32_t)zi & xjl)) ^
+                       (((uint32_t)(xi >> 32) & zjh) ^ ((uint32_t)(zi >> 32) & xjh));
+    bool hit = valid && rowok && (__popc(t) & 1) == 0;
+    if (DIAG) hit = hit && j != i;
+    const uint32_t m = __ballot_sync(0xffffffffu, hit);
+    my_m = lane == r ? m : my_m;
+  }
+  return my_m;
+}
+
 template <bool SLOW>
 __device__ void mask_blocks(const ConflictArgs& a, BucketSmem& S, int s, int L, int lane, int wid, int nw,
                             uint32_t* __restrict__ rmask, uint32_t* __restrict__ xmask) {
@@ -256,43 +282,40 @@ __device__ void mask_blocks(const ConflictArgs& a, BucketSmem& S, int s, int L, 
       ++I;
     }
     const int J = I + rem;
+    const int ib = I << 5;
     const int j = (J << 5) + lane;
     const bool valid = j < s;
     const uint64_t xj = valid ? S.sx[j] : 0ull, zj = valid ? S.sz[j] : 0ull;
     const uint32_t xjl = (uint32_t)xj, xjh = (uint32_t)(xj >> 32);
     const uint32_t zjl = (uint32_t)zj, zjh = (uint32_t)(zj >> 32);
-    uint32_t my_r = 0u, my_x = 0u;
-    const int rows = min(32, s - (I << 5));
-    for (int r = 0; r < rows; ++r) {
-      const int i = (I << 5) + r;
-      const uint64_t xi = S.sx[i], zi = S.sz[i];
-      const uint32_t t = (((uint32_t)xi & zjl) ^ ((uint32_t)zi & xjl)) ^
-                         (((uint32_t)(xi >> 32) & zjh) ^ ((uint32_t)(zi >> 32) & xjh));
-      const bool hit = valid && j != i && (__popc(t) & 1) == 0;
-      const uint32_t m = __ballot_sync(0xffffffffu, hit);
-      uint32_t exm;
-      if (!SLOW) {
-        exm = S.exo[i + 1] > S.exo[i] ? excl_bits(S, i, J << 5) : 0u;
-      } else {
-        const bool ex = ((m >> lane) & 1u) && share_prefix(a.lists + (int64_t)S.sid[i] * L, S.kk[i],
-                                                           a.lists + (int64_t)S.sid[j] * L, S.kk[j]);
-        exm = __ballot_sync(0xffffffffu, ex);
-      }
-      if (lane == r) {
-        my_r = m & ~exm;
-        my_x = m & exm;
+    const uint32_t my_m = J == I ? block_rows<true>(S, s, ib, j, valid, lane, xjl, xjh, zjl, zjh)
+                                 : block_rows<false>(S, s, ib, j, valid, lane, xjl, xjh, zjl, zjh);
+    // partners of this lane's row that share a smaller color go to the side word
+    const int ir = ib + lane;
+    uint32_t myex = 0u;
+    if (!SLOW) {
+      if (ir < s && S.exo[ir + 1] > S.exo[ir]) myex = excl_bits(S, ir, J << 5) & my_m;
+    } else if (ir < s) {
+      for (uint32_t bits = my_m; bits; bits &= bits - 1) {
+        const int jj = (J << 5) + __ffs(bits) - 1;
+        if (share_prefix(a.lists + (int64_t)S.sid[ir] * L, S.kk[ir], a.lists + (int64_t)S.sid[jj] * L, S.kk[jj]))
+          myex |= bits & (0u - bits);
       }
     }
-    store_words(S, (I << 5) + lane, s, nwb, J, my_r, my_x, rmask, xmask);
+    const uint32_t my_r = my_m & ~myex, my_x = myex;
+    store_words(S, ir, s, nwb, J, my_r, my_x, rmask, xmask);
     if (J != I) {
       uint32_t tr = 0u, tx = 0u;
-#pragma unroll 8
+#pragma unroll
       for (int b = 0; b < 32; ++b) {
         const uint32_t cr = __ballot_sync(0xffffffffu, (my_r >> b) & 1u);
-        const uint32_t cx = __ballot_sync(0xffffffffu, (my_x >> b) & 1u);
-        if (lane == b) {
-          tr = cr;
-          tx = cx;
+        tr = lane == b ? cr : tr;
+      }
+      if (__any_sync(0xffffffffu, my_x != 0u)) {
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+          const uint32_t cx = __ballot_sync(0xffffffffu, (my_x >> b) & 1u);
+          tx = lane == b ? cx : tx;
         }
       }
       store_words(S, (J << 5) + lane, s, nwb, I, tr, tx, rmask, xmask);
