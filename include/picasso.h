@@ -105,9 +105,9 @@ typedef struct {
   int32_t round;       /* current round number (1-based)                     */
   int64_t n_total;     /* N                                                  */
   int64_t n_round;     /* n_l, vertices of the current round                 */
-  int64_t P;           /* P_l of the last assign (0 before)                  */
-  int32_t L;           /* L_l of the last assign                            */
-  int64_t base;        /* base_l of the last assign                         */
+  int64_t P;           /* P_l of the last assign (batch: sum over the sets)  */
+  int32_t L;           /* L_l of the last assign (batch: the largest)        */
+  int64_t base;        /* base_l of the last assign (batch: of set 0)        */
   int64_t nnz;         /* 2|E_c| of the last build                           */
   int64_t n_extra;     /* entries of the multi-shared side list              */
   int64_t colored;     /* vertices colored by the last color step            */
@@ -158,6 +158,20 @@ int picasso_pack(const uint8_t* d_codes, int64_t n, int32_t q, uint64_t* d_xz,
  * default stream).  Round 1 starts with V_1 = all n strings, all colors -1. */
 int picasso_init(void** ctx, const picasso_config* cfg, const uint64_t* d_xz,
                  int64_t n, int32_t q, void* stream);
+
+/* A batch of independent string sets in one context (one launch per step
+ * for the whole batch).  d_xz [N][2] holds the sets back to back; set k is
+ * the global ids h_set_offsets[k] .. h_set_offsets[k+1] (host array of
+ * nsets + 1 entries, h_set_offsets[0] = 0, N = h_set_offsets[nsets] < 2^30).
+ * Set k is colored exactly as picasso_init on its own strings with seed
+ * h_seeds[k] (host, NULL: cfg.seed + k) would color it; its colors start at
+ * 0 and are written at its global ids by picasso_run / picasso_get_colors.
+ * All sets run their rounds together; a set that is done has no vertices.
+ * picasso_round_params and picasso_assign_lists need a single-set context. */
+int picasso_init_batch(void** ctx, const picasso_config* cfg,
+                       const uint64_t* d_xz, const int64_t* h_set_offsets,
+                       int32_t nsets, const uint64_t* h_seeds, int32_t q,
+                       void* stream);
 
 /* Parameters the configuration gives the current round: P_l, L_l, base_l
  * (Table I rule; base_l = sum of the earlier rounds' P).                    */
@@ -240,7 +254,7 @@ int picasso_kernel_launches(int64_t* out);
  * cudaMalloc while they work -- services that give the GPU's memory to their
  * own fixed pool, or hosts that forbid allocation on their hot path because it
  * synchronises the device.  Every temporary buffer lives in one library-owned
- * static device array of about 12.5 MB; once this function has run on a GPU,
+ * static device array of about 12.8 MB; once this function has run on a GPU,
  * that GPU holds the array until the process exits.
  *   d_xz        [n][2] packed strings (caller-owned, read-only)
  *   d_color_out [n] int32, receives the global colors (caller-owned)

@@ -1,12 +1,17 @@
 // capi.cu -- the C ABI of libpicasso: context, round driver (Alg. 1) and
-// device-memory bookkeeping.  All device work is launched on the context's
-// stream; the host only computes the round parameters and reads back sizes.
+// device-memory bookkeeping.  A context holds one string set or a batch of
+// independent sets that advance through their rounds together (one launch
+// per step for the whole batch).  All device work is launched on the
+// context's stream; the host only computes the round parameters of every
+// set and reads back sizes.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <unordered_map>
+#include <vector>
 
 #include "common.cuh"
 
@@ -63,17 +68,29 @@ struct Ctx {
   int32_t q = 0;
   const uint64_t* xz_user = nullptr;
 
+  // the sets of the batch (one for a plain context)
+  int32_t nsets = 1;
+  std::vector<int64_t> soff;        // [nsets+1] global id offsets
+  std::vector<uint64_t> seed;       // [nsets]
+  std::vector<int64_t> remaining;   // [nsets] |V_l| of every set
+  std::vector<int64_t> set_base;    // [nsets] palette base of the next round
+  std::vector<SetRound> sets;       // [nsets] this round's parameters
+  int64_t* d_soff = nullptr;        // device copy of soff
+  SetRound* d_sets = nullptr;       // device copy of sets
+  uint32_t* d_hist = nullptr;       // [nsets] per-set counts
+
   int32_t round = 1;
-  int64_t n = 0;          // |V_l|
-  int64_t next_base = 0;  // sum of P over finished rounds
-  int32_t* gid = nullptr; // [n] (nullptr in round 1: identity)
+  int64_t n = 0;          // vertices of the round (all sets)
+  int32_t* gid = nullptr; // [n] batch-global ids (nullptr in round 1: identity)
   uint64_t* xz = nullptr; // [n][2] (nullptr in round 1: xz_user)
   int32_t* color = nullptr;
 
   // assign
   bool assigned = false;
-  int64_t P = 0, base = 0;
-  int32_t L = 0;
+  int64_t Ptot = 0, E = 0;
+  int32_t Lmax = 0, Lu = 0;
+  int64_t* loff = nullptr;
+  int32_t* ent_v = nullptr;
   int32_t* lists = nullptr;
   uint32_t* prio = nullptr;
   // build
@@ -120,19 +137,19 @@ int map_err(cudaError_t e) {
   return PICASSO_ERR_CUDA;
 }
 
-#define CK(expr)                                  \
-  do {                                            \
-    cudaError_t _e = (expr);                      \
-    if (_e != cudaSuccess) {                      \
-      int _st = map_err(_e);                      \
+#define CK(expr)                                    \
+  do {                                              \
+    cudaError_t _e = (expr);                        \
+    if (_e != cudaSuccess) {                        \
+      int _st = map_err(_e);                        \
       if (_st == PICASSO_ERR_CUDA) c->sticky = _st; \
-      return _st;                                 \
-    }                                             \
+      return _st;                                   \
+    }                                               \
   } while (0)
 
-#define ST(expr)                    \
-  do {                              \
-    int _st = (expr);               \
+#define ST(expr)                       \
+  do {                                 \
+    int _st = (expr);                  \
     if (_st != PICASSO_OK) return _st; \
   } while (0)
 
@@ -184,6 +201,8 @@ void free_build(Ctx* c) {
 void free_assign(Ctx* c) {
   release(c, &c->lists);
   release(c, &c->prio);
+  release(c, &c->loff);
+  release(c, &c->ent_v);
   c->assigned = false;
 }
 
@@ -213,6 +232,7 @@ double elapsed(Ctx* c, int a, int b) {
   return ms;
 }
 
+// Table I rule: P = max(1, ceil(n num / den)), L = min(P, max(1, ceil(alpha ln n))).
 void params_for(const picasso_config& cfg, int64_t n, int64_t* P, int32_t* L) {
   int64_t p = (n * cfg.palette_num + cfg.palette_den - 1) / cfg.palette_den;
   if (p < 1) p = 1;
@@ -224,10 +244,80 @@ void params_for(const picasso_config& cfg, int64_t n, int64_t* P, int32_t* L) {
   *L = (int32_t)li;
 }
 
+// Every set's parameters for the current round from the configuration.
+void plan_round(Ctx* c) {
+  for (int k = 0; k < c->nsets; ++k) {
+    SetRound& sr = c->sets[k];
+    sr.seed = c->seed[k];
+    sr.base = c->set_base[k];
+    sr.P = 0;
+    sr.L = 0;
+    if (c->remaining[k] > 0) {
+      int64_t P;
+      int32_t L;
+      params_for(c->cfg, c->remaining[k], &P, &L);
+      sr.P = P;
+      sr.L = L;
+    }
+  }
+}
+
+// Lists of the round from c->sets (P, L, base already set): bucket-color
+// offsets, list offsets, entry owners, lists and priorities.
+int assign_round(Ctx* c) {
+  int64_t cofs = 0;
+  int32_t Lmax = 0;
+  for (int k = 0; k < c->nsets; ++k) {
+    SetRound& sr = c->sets[k];
+    if (sr.P > 0 && (sr.L < 1 || sr.L > sr.P)) return PICASSO_ERR_INVALID_ARG;
+    if (sr.L > kMaxL) return PICASSO_ERR_UNSUPPORTED;
+    sr.cofs = cofs;
+    cofs += sr.P;
+    Lmax = std::max(Lmax, sr.L);
+  }
+  if (cofs >= (int64_t(1) << 30)) return PICASSO_ERR_UNSUPPORTED;
+  for (int k = 0; k < c->nsets; ++k)
+    if (c->sets[k].base + c->sets[k].P > (int64_t)0x7fffffff) return PICASSO_ERR_UNSUPPORTED;
+  free_color(c);
+  free_build(c);
+  free_assign(c);
+  c->Ptot = cofs;
+  c->Lmax = Lmax;
+  const int64_t n = c->n;
+  cudaStream_t s = c->s;
+  CK(cudaMemcpyAsync(c->d_sets, c->sets.data(), sizeof(SetRound) * c->nsets, cudaMemcpyHostToDevice, s));
+  uint32_t* len = nullptr;
+  void* tmp = nullptr;
+  ST(alloc(c, &c->loff, n + 1));
+  ST(alloc(c, &len, n));
+  int st = alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(n));
+  if (st != PICASSO_OK) {
+    release(c, &len);
+    return st;
+  }
+  cudaError_t e = launch_list_offsets(c->gid, n, c->d_soff, c->nsets, c->d_sets, len, c->loff, tmp, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_buf, c->loff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release(c, &len);
+  release(c, (uint8_t**)&tmp);
+  CK(e);
+  c->E = c->h_buf[0];
+  // with one list length (a single set) owners follow from e / L
+  c->Lu = c->nsets == 1 ? Lmax : 0;
+  ST(alloc(c, &c->lists, c->E));
+  ST(alloc(c, &c->prio, n));
+  if (!c->Lu) {
+    ST(alloc(c, &c->ent_v, c->E));
+    CK(launch_entry_owner(c->loff, n, c->ent_v, s));
+  }
+  CK(launch_assign_lists(c->round, c->gid, n, c->d_soff, c->nsets, c->d_sets, Lmax, c->loff, c->lists, c->prio,
+                         s));
+  c->assigned = true;
+  return PICASSO_OK;
+}
+
 int build_conflicts(Ctx* c) {
-  const int64_t n = c->n, P = c->P;
-  const int32_t L = c->L;
-  const int64_t nl = n * L;
+  const int64_t n = c->n, P = c->Ptot, E = c->E;
   cudaStream_t s = c->s;
 
   uint32_t *cnt = nullptr, *xcnt = nullptr, *bcount = nullptr, *bcursor = nullptr, *dmax = nullptr;
@@ -252,29 +342,29 @@ int build_conflicts(Ctx* c) {
     release(c, &xmask);
     release(c, (uint8_t**)&tmp);
   };
-#define TRY(expr)                  \
-  do {                             \
-    st = (expr);                   \
-    if (st != PICASSO_OK) {        \
-      cleanup();                   \
-      return st;                   \
-    }                              \
+#define TRY(expr)           \
+  do {                      \
+    st = (expr);            \
+    if (st != PICASSO_OK) { \
+      cleanup();            \
+      return st;            \
+    }                       \
   } while (0)
-#define TRYC(expr)                                   \
-  do {                                               \
-    cudaError_t _e = (expr);                         \
-    if (_e != cudaSuccess) {                         \
-      st = map_err(_e);                              \
-      if (st == PICASSO_ERR_CUDA) c->sticky = st;    \
-      cleanup();                                     \
-      return st;                                     \
-    }                                                \
+#define TRYC(expr)                                \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) {                      \
+      st = map_err(_e);                           \
+      if (st == PICASSO_ERR_CUDA) c->sticky = st; \
+      cleanup();                                  \
+      return st;                                  \
+    }                                             \
   } while (0)
 
-  const size_t tmp_bytes = scan_tmp_bytes(nl > P ? nl : P);
+  const size_t tmp_bytes = scan_tmp_bytes(E > P ? E : P);
   TRY(alloc(c, (uint8_t**)&tmp, (int64_t)tmp_bytes));
-  TRY(alloc(c, &cnt, nl));
-  TRY(alloc(c, &xcnt, nl));
+  TRY(alloc(c, &cnt, E));
+  TRY(alloc(c, &xcnt, E));
   TRYC(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));
 
   int algo = c->cfg.conflict_algo;
@@ -284,7 +374,7 @@ int build_conflicts(Ctx* c) {
   TRY(alloc(c, &dmax, 2));
   TRY(alloc(c, &dsq, 1));
   TRYC(cudaMemsetAsync(bcount, 0, sizeof(uint32_t) * P, s));
-  TRYC(launch_bucket_hist(c->lists, n, L, bcount, s));
+  TRYC(launch_bucket_hist(c->lists, E, bcount, s));
   TRYC(launch_bucket_stats(bcount, P, dmax, dsq, s));
   TRYC(cudaMemcpyAsync(c->h_buf, dmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   TRYC(cudaMemcpyAsync(c->h_buf + 1, dsq, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -292,7 +382,7 @@ int build_conflicts(Ctx* c) {
   const int64_t smax = (int64_t)(*(uint32_t*)c->h_buf);
   const int64_t bucket_pairs = c->h_buf[1];
   c->max_bucket = smax;
-  const bool bucket_ok = smax <= kBucketCap && P < kBucketMaxP && nl < (int64_t(1) << 31);
+  const bool bucket_ok = smax <= kBucketCap && P < kBucketMaxP && E < (int64_t(1) << 31);
   if (algo == PICASSO_CONFLICT_AUTO) algo = bucket_ok ? PICASSO_CONFLICT_BUCKET : PICASSO_CONFLICT_ALLPAIRS;
   if (algo == PICASSO_CONFLICT_BUCKET && !bucket_ok) {
     cleanup();
@@ -302,10 +392,14 @@ int build_conflicts(Ctx* c) {
 
   ConflictArgs a{};
   a.n = n;
-  a.L = L;
+  a.E = E;
+  a.Lmax = c->Lmax;
+  a.Lu = c->Lu;
   a.P = P;
   a.xz = c->round_xz();
   a.lists = c->lists;
+  a.loff = c->loff;
+  a.ent_v = c->ent_v;
   a.cnt = cnt;
   a.xcnt = xcnt;
   a.err = c->d_err;
@@ -313,9 +407,9 @@ int build_conflicts(Ctx* c) {
   if (algo == PICASSO_CONFLICT_BUCKET) {
     TRYC(launch_scan_u32(bcount, P, boff, tmp, s));
     TRY(alloc(c, &bcursor, P));
-    TRY(alloc(c, &bmem, nl));
+    TRY(alloc(c, &bmem, E));
     TRYC(cudaMemsetAsync(bcursor, 0, sizeof(uint32_t) * P, s));
-    TRYC(launch_bucket_fill(c->lists, n, L, boff, bcursor, bmem, s));
+    TRYC(launch_bucket_fill(c->lists, E, boff, bcursor, bmem, s));
     release(c, &bcursor);
     TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, s));
     // mask words: bucket c holds s_c rows of ceil(s_c / 32) words
@@ -343,14 +437,14 @@ int build_conflicts(Ctx* c) {
   const int64_t tested = algo == PICASSO_CONFLICT_BUCKET ? bucket_pairs : n * (n - 1);
   release(c, &bcount);
 
-  TRY(alloc(c, &c->runoff, nl + 1));
-  TRY(alloc(c, &c->xoff, nl + 1));
-  TRYC(launch_scan_u32(cnt, nl, c->runoff, tmp, s));
-  TRYC(launch_scan_u32(xcnt, nl, c->xoff, tmp, s));
+  TRY(alloc(c, &c->runoff, E + 1));
+  TRY(alloc(c, &c->xoff, E + 1));
+  TRYC(launch_scan_u32(cnt, E, c->runoff, tmp, s));
+  TRYC(launch_scan_u32(xcnt, E, c->xoff, tmp, s));
   release(c, &cnt);
   release(c, &xcnt);
-  TRYC(cudaMemcpyAsync(c->h_buf, c->runoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  TRYC(cudaMemcpyAsync(c->h_buf + 1, c->xoff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaMemcpyAsync(c->h_buf, c->runoff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaMemcpyAsync(c->h_buf + 1, c->xoff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   TRYC(cudaMemcpyAsync(c->h_buf + 2, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
   const int64_t nnz = c->h_buf[0], nx = c->h_buf[1];
@@ -379,7 +473,7 @@ int build_conflicts(Ctx* c) {
     TRYC(launch_allpairs(a, true, s));
   }
   TRYC(cudaEventRecord(c->ev[5], s));
-  TRYC(launch_row_offsets(c->runoff, n, L, c->off, s));
+  TRYC(launch_row_offsets(c->runoff, c->loff, n, c->off, s));
   TRYC(cudaEventSynchronize(c->ev[5]));
   if (algo == PICASSO_CONFLICT_BUCKET) {
     // the mask pass tests every unordered pair of a bucket once; the emit
@@ -389,14 +483,14 @@ int build_conflicts(Ctx* c) {
     c->tested_pairs += tested / 2;
     c->t_emit += elapsed(c, 4, 5);
     c->emit_launches += 1;
-    c->emit_bytes += 4 * (nnz + nx) + 4 * nl + 16 * nl;  // CSR writes, member ids, run/side offsets
+    c->emit_bytes += 4 * (nnz + nx) + 4 * E + 16 * E;  // CSR writes, member ids, run/side offsets
   } else {
     // the all-pairs kernel tests every ordered pair in both passes
     c->t_pairs += elapsed(c, 2, 3) + elapsed(c, 4, 5);
     c->pairs_launches += 2;
     c->tested_pairs += 2 * tested;
   }
-  c->logical_pairs += n * (n - 1) / 2;
+  for (int k = 0; k < c->nsets; ++k) c->logical_pairs += c->remaining[k] * (c->remaining[k] - 1) / 2;
   cleanup();
   c->nnz = nnz;
   c->nx = nx;
@@ -465,8 +559,8 @@ int color_round(Ctx* c) {
   int32_t* ctl = nw;
   ColorArgs a{};
   a.n = n;
-  a.L = c->L;
   a.lists = c->lists;
+  a.loff = c->loff;
   a.runoff = c->runoff;
   a.col = c->col;
   a.xoff = c->xoff;
@@ -503,10 +597,10 @@ int color_round(Ctx* c) {
     }
   }
   c->sweeps = sweeps;
-  // colors to the global array; flags + positions of the uncolored
+  // colors to the output; flags + positions of the uncolored
   TRY(alloc(c, &c->flag, n));
   TRY(alloc(c, &c->pos, n + 1));
-  TRYC(launch_carry_flags(c->state, n, c->gid, c->base, c->color, c->flag, s));
+  TRYC(launch_carry_flags(c->state, n, c->gid, c->d_soff, c->nsets, c->d_sets, c->color, c->flag, s));
   TRYC(launch_scan_u32(c->flag, n, c->pos, tmp, s));
   TRYC(cudaMemcpyAsync(c->h_buf, c->pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
@@ -535,12 +629,95 @@ int carry_round(Ctx* c) {
   free_color(c);
   free_build(c);
   free_assign(c);
-  c->next_base = c->base + c->P;
+  // next palette base and remaining vertices of every set
+  for (int k = 0; k < c->nsets; ++k) c->set_base[k] = c->sets[k].base + c->sets[k].P;
+  if (c->nsets == 1) {
+    c->remaining[0] = m;
+  } else {
+    CK(launch_set_counts(c->gid, m, c->d_soff, c->nsets, c->d_hist, c->s));
+    std::vector<uint32_t> h(c->nsets);
+    CK(cudaMemcpyAsync(h.data(), c->d_hist, sizeof(uint32_t) * c->nsets, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    for (int k = 0; k < c->nsets; ++k) c->remaining[k] = h[k];
+  }
   c->n = m;
   c->round += 1;
-  if (m == 0) {
-    // keep a valid (empty) vertex set; later calls see n == 0
+  return PICASSO_OK;
+}
+
+int validate_cfg(const picasso_config* cfg) {
+  if (cfg->palette_num < 1 || cfg->palette_den < 1 || cfg->palette_num > (int64_t(1) << 32) ||
+      cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
+      cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2 ||
+      cfg->color_algo < 0 || cfg->color_algo > 1)
+    return PICASSO_ERR_INVALID_ARG;
+  return PICASSO_OK;
+}
+
+int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, const int64_t* h_soff, int32_t nsets,
+                const uint64_t* h_seeds, int32_t q, void* stream) {
+  if (!out || !cfg || !d_xz || !h_soff || nsets < 1) return PICASSO_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int64_t n = h_soff[nsets];
+  if (h_soff[0] != 0 || n < 1 || n >= (int64_t(1) << 30) || q < 1) return PICASSO_ERR_INVALID_ARG;
+  for (int k = 0; k < nsets; ++k)
+    if (h_soff[k + 1] < h_soff[k]) return PICASSO_ERR_INVALID_ARG;
+  if (q > 64) return PICASSO_ERR_UNSUPPORTED;
+  ST(validate_cfg(cfg));
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) return PICASSO_ERR_OOM;
+  c->cfg = *cfg;
+  c->s = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&c->dev);
+  if (e == cudaSuccess) e = pool_for(c->dev, &c->pool);
+  if (e != cudaSuccess) {
+    delete c;
+    return map_err(e);
   }
+  c->N = n;
+  c->q = q;
+  c->xz_user = d_xz;
+  c->n = n;
+  c->nsets = nsets;
+  c->soff.assign(h_soff, h_soff + nsets + 1);
+  c->seed.resize(nsets);
+  c->remaining.resize(nsets);
+  c->set_base.assign(nsets, 0);
+  c->sets.assign(nsets, SetRound{});
+  for (int k = 0; k < nsets; ++k) {
+    c->seed[k] = h_seeds ? h_seeds[k] : cfg->seed + (uint64_t)k;
+    c->remaining[k] = h_soff[k + 1] - h_soff[k];
+  }
+  e = cudaMallocHost((void**)&c->h_buf, sizeof(int64_t) * 16);
+  if (e != cudaSuccess) {
+    delete c;
+    return map_err(e);
+  }
+  int st = PICASSO_OK;
+  for (int i = 0; i < 6 && st == PICASSO_OK; ++i) st = map_err(cudaEventCreate(&c->ev[i]));
+  if (st == PICASSO_OK) st = alloc(c, &c->color, n);
+  if (st == PICASSO_OK) st = alloc(c, &c->d_err, 4);
+  if (st == PICASSO_OK) st = alloc(c, &c->d_soff, nsets + 1);
+  if (st == PICASSO_OK) st = alloc(c, &c->d_sets, nsets);
+  if (st == PICASSO_OK) st = alloc(c, &c->d_hist, nsets);
+  if (st == PICASSO_OK)
+    st = map_err(cudaMemcpyAsync(c->d_soff, c->soff.data(), sizeof(int64_t) * (nsets + 1), cudaMemcpyHostToDevice,
+                                 c->s));
+  if (st == PICASSO_OK) st = map_err(launch_fill_i32(c->color, n, -1, c->s));
+  if (st == PICASSO_OK) st = map_err(cudaStreamSynchronize(c->s));
+  if (st != PICASSO_OK) {
+    release(c, &c->color);
+    release(c, &c->d_err);
+    release(c, &c->d_soff);
+    release(c, &c->d_sets);
+    release(c, &c->d_hist);
+    for (int i = 0; i < 6; ++i)
+      if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    cudaFreeHost(c->h_buf);
+    delete c;
+    return st;
+  }
+  *out = c;
   return PICASSO_OK;
 }
 
@@ -558,6 +735,7 @@ int picasso_config_default(picasso_config* cfg) {
   cfg->conflict_algo = PICASSO_CONFLICT_AUTO;
   cfg->max_rounds = 100000;
   cfg->byte_budget = 0;
+  cfg->color_algo = PICASSO_COLOR_AUTO;
   return PICASSO_OK;
 }
 
@@ -574,85 +752,45 @@ int picasso_philox_draws(uint64_t seed, int32_t round, int64_t gid, uint32_t tag
 }
 
 int picasso_init(void** out, const picasso_config* cfg, const uint64_t* d_xz, int64_t n, int32_t q, void* stream) {
-  if (!out || !cfg || !d_xz) return PICASSO_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (n < 1 || n >= (int64_t(1) << 30) || q < 1) return PICASSO_ERR_INVALID_ARG;
-  if (q > 64) return PICASSO_ERR_UNSUPPORTED;
-  if (cfg->palette_num < 1 || cfg->palette_den < 1 || cfg->palette_num > (int64_t(1) << 32) ||
-      cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
-      cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2 ||
-      cfg->color_algo < 0 || cfg->color_algo > 1)
-    return PICASSO_ERR_INVALID_ARG;
-  Ctx* c = new (std::nothrow) Ctx();
-  if (!c) return PICASSO_ERR_OOM;
-  c->cfg = *cfg;
-  c->s = (cudaStream_t)stream;
-  cudaError_t e = cudaGetDevice(&c->dev);
-  if (e != cudaSuccess) {
-    delete c;
-    return map_err(e);
-  }
-  e = pool_for(c->dev, &c->pool);
-  if (e != cudaSuccess) {
-    delete c;
-    return map_err(e);
-  }
-  c->N = n;
-  c->q = q;
-  c->xz_user = d_xz;
-  c->n = n;
-  e = cudaMallocHost((void**)&c->h_buf, sizeof(int64_t) * 16);
-  if (e != cudaSuccess) {
-    delete c;
-    return map_err(e);
-  }
-  int st = PICASSO_OK;
-  for (int i = 0; i < 6 && st == PICASSO_OK; ++i) st = map_err(cudaEventCreate(&c->ev[i]));
-  if (st == PICASSO_OK) st = alloc(c, &c->color, n);
-  if (st == PICASSO_OK) st = alloc(c, &c->d_err, 4);
-  if (st == PICASSO_OK) st = map_err(launch_fill_i32(c->color, n, -1, c->s));
-  if (st != PICASSO_OK) {
-    release(c, &c->color);
-    release(c, &c->d_err);
-    cudaFreeHost(c->h_buf);
-    delete c;
-    return st;
-  }
-  *out = c;
-  return PICASSO_OK;
+  if (!cfg) return PICASSO_ERR_INVALID_ARG;
+  const int64_t soff[2] = {0, n};
+  const uint64_t seed = cfg->seed;
+  return init_common(out, cfg, d_xz, soff, 1, &seed, q, stream);
+}
+
+int picasso_init_batch(void** out, const picasso_config* cfg, const uint64_t* d_xz, const int64_t* h_set_offsets,
+                       int32_t nsets, const uint64_t* h_seeds, int32_t q, void* stream) {
+  return init_common(out, cfg, d_xz, h_set_offsets, nsets, h_seeds, q, stream);
 }
 
 int picasso_round_params(void* ctx, int64_t* P, int32_t* L, int64_t* base) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (c->n == 0) return PICASSO_ERR_STATE;
+  if (c->nsets != 1) return PICASSO_ERR_STATE;
   int64_t p;
   int32_t l;
   params_for(c->cfg, c->n, &p, &l);
   if (P) *P = p;
   if (L) *L = l;
-  if (base) *base = c->next_base;
+  if (base) *base = c->set_base[0];
   return PICASSO_OK;
 }
 
 int picasso_assign_lists(void* ctx, int64_t P, int32_t L, int64_t base) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
-  if (c->n == 0) return PICASSO_ERR_STATE;
+  if (c->n == 0 || c->nsets != 1) return PICASSO_ERR_STATE;
   if (P < 1 || L < 1 || L > P || base < 0 || base + P > (int64_t)0x7fffffff) return PICASSO_ERR_INVALID_ARG;
   if (L > kMaxL || P >= (int64_t(1) << 30)) return PICASSO_ERR_UNSUPPORTED;
-  free_color(c);
-  free_build(c);
-  free_assign(c);
-  c->P = P;
-  c->L = L;
-  c->base = base;
-  ST(alloc(c, &c->lists, c->n * L));
-  ST(alloc(c, &c->prio, c->n));
+  SetRound& sr = c->sets[0];
+  sr.seed = c->seed[0];
+  sr.P = P;
+  sr.L = L;
+  sr.base = base;
   phase_begin(c);
-  CK(launch_assign_lists(c->cfg.seed, c->round, c->gid, c->n, P, L, c->lists, c->prio, c->s));
+  ST(assign_round(c));
   CK(phase_end(c, &c->t_assign));
-  c->assigned = true;
   return PICASSO_OK;
 }
 
@@ -704,10 +842,10 @@ int picasso_round(void* ctx, int64_t* n_remaining) {
     if (n_remaining) *n_remaining = 0;
     return PICASSO_OK;
   }
-  int64_t P, base;
-  int32_t L;
-  ST(picasso_round_params(ctx, &P, &L, &base));
-  ST(picasso_assign_lists(ctx, P, L, base));
+  plan_round(c);
+  phase_begin(c);
+  ST(assign_round(c));
+  CK(phase_end(c, &c->t_assign));
   ST(picasso_build_conflicts(ctx, nullptr));
   ST(picasso_color(ctx, nullptr));
   return picasso_carry(ctx, n_remaining);
@@ -744,8 +882,7 @@ int picasso_get_round(void* ctx, int32_t* d_gid, int32_t* d_lists, uint32_t* d_p
   }
   if (d_lists || d_prio) {
     if (!c->assigned) return PICASSO_ERR_STATE;
-    if (d_lists)
-      CK(cudaMemcpyAsync(d_lists, c->lists, sizeof(int32_t) * c->n * c->L, cudaMemcpyDeviceToDevice, c->s));
+    if (d_lists) CK(cudaMemcpyAsync(d_lists, c->lists, sizeof(int32_t) * c->E, cudaMemcpyDeviceToDevice, c->s));
     if (d_prio) CK(cudaMemcpyAsync(d_prio, c->prio, sizeof(uint32_t) * c->n, cudaMemcpyDeviceToDevice, c->s));
   }
   return PICASSO_OK;
@@ -777,9 +914,9 @@ int picasso_copy_runs(void* ctx, int64_t* d_runoff, int64_t* d_xoff, int32_t* d_
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (!c->built) return PICASSO_ERR_STATE;
-  const int64_t nl = c->n * c->L + 1;
-  if (d_runoff) CK(cudaMemcpyAsync(d_runoff, c->runoff, sizeof(int64_t) * nl, cudaMemcpyDeviceToDevice, c->s));
-  if (d_xoff) CK(cudaMemcpyAsync(d_xoff, c->xoff, sizeof(int64_t) * nl, cudaMemcpyDeviceToDevice, c->s));
+  const int64_t ne = c->E + 1;
+  if (d_runoff) CK(cudaMemcpyAsync(d_runoff, c->runoff, sizeof(int64_t) * ne, cudaMemcpyDeviceToDevice, c->s));
+  if (d_xoff) CK(cudaMemcpyAsync(d_xoff, c->xoff, sizeof(int64_t) * ne, cudaMemcpyDeviceToDevice, c->s));
   if (d_xcol && c->nx > 0)
     CK(cudaMemcpyAsync(d_xcol, c->xcol, sizeof(int32_t) * c->nx, cudaMemcpyDeviceToDevice, c->s));
   return PICASSO_OK;
@@ -792,13 +929,15 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->round = c->round;
   out->n_total = c->N;
   out->n_round = c->n;
-  out->P = c->P;
-  out->L = c->L;
-  out->base = c->base;
+  out->P = c->Ptot;
+  out->L = c->Lmax;
+  out->base = c->sets.empty() ? 0 : c->sets[0].base;
   out->nnz = c->nnz;
   out->n_extra = c->nx;
   out->colored = c->n_colored;
-  out->colors_used = c->next_base;
+  int64_t used = 0;
+  for (int k = 0; k < c->nsets; ++k) used += c->set_base[k];
+  out->colors_used = used;
   out->peak_bytes = c->peak_bytes;
   out->conflict_algo_used = c->algo_used;
   out->jp_sweeps = c->sweeps;
@@ -859,6 +998,9 @@ int picasso_destroy(void* ctx) {
   release(c, &c->xz);
   release(c, &c->color);
   release(c, &c->d_err);
+  release(c, &c->d_soff);
+  release(c, &c->d_sets);
+  release(c, &c->d_hist);
   cudaStreamSynchronize(c->s);
   for (int i = 0; i < 6; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);

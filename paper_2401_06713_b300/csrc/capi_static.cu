@@ -59,7 +59,12 @@ constexpr size_t kOffFlag = kOffCounts + al(kCtlWords * 4);                // [N
 constexpr size_t kOffPos = kOffFlag + al(kStaticMaxN * 4);                 // [N+1] i64
 constexpr size_t kOffTmp = kOffPos + al((kStaticMaxN + 1) * 8);            // scan temp
 constexpr size_t kOffErr = kOffTmp + al(kScanTmpReserve);                  // [1] i32
-constexpr size_t kStaticBytes = kOffErr + 256;                             // about 12.5 MB
+constexpr size_t kOffLoff = kOffErr + 256;                                 // [N+1] i64
+constexpr size_t kOffEnt = kOffLoff + al((kStaticMaxN + 1) * 8);           // [N*L] i32
+constexpr size_t kOffLen = kOffEnt + al(kStaticNL * 4);                    // [N] u32
+constexpr size_t kOffSoff = kOffLen + al(kStaticMaxN * 4);                 // [2] i64
+constexpr size_t kOffSet = kOffSoff + 256;                                 // [1] SetRound
+constexpr size_t kStaticBytes = kOffSet + 256;                             // about 12.8 MB
 
 }  // namespace
 
@@ -162,9 +167,19 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
   int64_t* pos = (int64_t*)(base_ptr + kOffPos);
   void* tmp = (void*)(base_ptr + kOffTmp);
   int32_t* derr = (int32_t*)(base_ptr + kOffErr);
+  int64_t* loff = (int64_t*)(base_ptr + kOffLoff);
+  int32_t* ent_v = (int32_t*)(base_ptr + kOffEnt);
+  uint32_t* len = (uint32_t*)(base_ptr + kOffLen);
+  int64_t* soff = (int64_t*)(base_ptr + kOffSoff);
+  SetRound* dset = (SetRound*)(base_ptr + kOffSet);
+  static_assert(sizeof(SetRound) <= 256, "set table slot");
 
   SCK(launch_fill_i32(d_color_out, n, -1, s));
   SCK(cudaMemsetAsync(derr, 0, sizeof(int32_t), s));
+  {
+    const int64_t h_soff[2] = {0, n};
+    SCK(cudaMemcpyAsync(soff, h_soff, sizeof(h_soff), cudaMemcpyHostToDevice, s));
+  }
 
   const int32_t* gid = nullptr;         // round 1: identity
   const uint64_t* xz = d_xz;            // round 1: the caller's strings
@@ -178,14 +193,27 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
     static_params(*cfg, m, &P, &L);
     if (P >= (int64_t(1) << 30) || base + P > (int64_t)0x7fffffff) return PICASSO_ERR_UNSUPPORTED;
     const int64_t nl = m * L;
-    SCK(launch_assign_lists(cfg->seed, round, gid, m, P, L, lists, prio, s));
+    SetRound sr{};
+    sr.seed = cfg->seed;
+    sr.P = P;
+    sr.cofs = 0;
+    sr.base = base;
+    sr.L = L;
+    SCK(cudaMemcpyAsync(dset, &sr, sizeof(sr), cudaMemcpyHostToDevice, s));
+    SCK(launch_list_offsets(gid, m, soff, 1, dset, len, loff, tmp, s));
+    SCK(launch_entry_owner(loff, m, ent_v, s));
+    SCK(launch_assign_lists(round, gid, m, soff, 1, dset, L, loff, lists, prio, s));
 
     ConflictArgs a{};
     a.n = m;
-    a.L = L;
+    a.E = nl;
+    a.Lmax = L;
+    a.Lu = L;
     a.P = P;
     a.xz = xz;
     a.lists = lists;
+    a.loff = loff;
+    a.ent_v = ent_v;
     a.cnt = cnt;
     a.xcnt = xcnt;
     a.err = derr;
@@ -207,8 +235,8 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
 
     ColorArgs ca{};
     ca.n = m;
-    ca.L = L;
     ca.lists = lists;
+    ca.loff = loff;
     ca.runoff = runoff;
     ca.col = col;
     ca.xoff = xoff;
@@ -235,7 +263,7 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
         if (h[4] != 0 || h[0] != 0) return PICASSO_ERR_INTERNAL;
       }
     }
-    SCK(launch_carry_flags(state, m, gid, base, d_color_out, flag, s));
+    SCK(launch_carry_flags(state, m, gid, soff, 1, dset, d_color_out, flag, s));
     SCK(launch_scan_u32(flag, m, pos, tmp, s));
     int64_t rem = 0;
     {

@@ -1,5 +1,13 @@
 // common.cuh -- device helpers and internal launcher declarations of
 // libpicasso (sm_103a).  Nothing here is part of the C ABI.
+//
+// A round works on a batch of one or more independent string sets at once,
+// as one disjoint-union instance.  Vertices are ordered by set, then by
+// global id; every vertex v owns the list entries loff[v] .. loff[v+1]
+// (L of its set), and list colors are "bucket colors": the round-local
+// color of the set plus the set's color offset cofs, so the color buckets of
+// different sets never meet and no pair of vertices of different sets is
+// ever tested.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -13,12 +21,22 @@ constexpr uint32_t kTagList = 1u;
 constexpr uint32_t kTagPrio = 2u;
 constexpr int kMaxL = 512;           // longest list a round may draw
 constexpr int kBucketCap = 2048;     // largest color bucket of the bucket join
-constexpr int kBucketMaxP = 1 << 21; // palette limit of the bucket join
+constexpr int kBucketMaxP = 1 << 21; // bucket colors of one round (bucket join)
 constexpr uint32_t kFailedColor = 0x3FFFFFFFu;
 
-// Vertex state word of the coloring: bits 31..2 a round-local color, bits
-// 1..0 the state.  Undecided: the color is the current candidate.
+// Vertex state word of the coloring: bits 31..2 a bucket color, bits 1..0 the
+// state.  Undecided: the color is the current candidate.
 constexpr uint32_t kUndecided = 0u, kColored = 1u, kFailed = 2u;
+
+// One set's parameters in the current round (device table, one entry per set).
+struct SetRound {
+  uint64_t seed;  // Philox key of the set
+  int64_t P;      // palette size P_l of the set
+  int64_t cofs;   // bucket-color offset of the set in this round
+  int64_t base;   // the set's palette base: final color = base + (c - cofs)
+  int32_t L;      // list size L_l of the set
+  int32_t pad;
+};
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -66,6 +84,19 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// Set of batch-global vertex id g: the k with soff[k] <= g < soff[k+1].
+__device__ __forceinline__ int set_of(const int64_t* __restrict__ soff, int nsets, int64_t g) {
+  int lo = 0, hi = nsets - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (soff[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 // Process-wide launch counter (capi.cu); every launcher adds its launches.
 void count_launches(int k);
 
@@ -75,40 +106,55 @@ void count_launches(int k);
 cudaError_t launch_pack(const uint8_t* codes, int64_t n, int32_t q, uint64_t* xz, cudaStream_t s);
 cudaError_t launch_philox_draws(uint64_t seed, int32_t round, int64_t gid, uint32_t tag, uint32_t i0,
                                 int32_t count, uint32_t* out, cudaStream_t s);
-cudaError_t launch_assign_lists(uint64_t seed, int32_t round, const int32_t* gid, int64_t n, int64_t P,
-                                int32_t L, int32_t* lists, uint32_t* prio, cudaStream_t s);
+
+// Round vertices: gid[v] is the batch-global id (nullptr: identity), soff
+// [nsets+1] the batch's set offsets (global ids), sets [nsets] this round's
+// set table.  List lengths -> loff (len: [n] scratch, tmp: scan scratch).
+cudaError_t launch_list_offsets(const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
+                                const SetRound* sets, uint32_t* len, int64_t* loff, void* tmp, cudaStream_t s);
+// ent_v[e] = vertex owning list entry e.
+cudaError_t launch_entry_owner(const int64_t* loff, int64_t n, int32_t* ent_v, cudaStream_t s);
+// Alg. 1 list assignment: lists[loff[v] ..] = sorted bucket colors, prio[v].
+cudaError_t launch_assign_lists(int32_t round, const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
+                                const SetRound* sets, int32_t Lmax, const int64_t* loff, int32_t* lists,
+                                uint32_t* prio, cudaStream_t s);
 
 // Exclusive scan of n uint32 counts into out[n+1] (int64); tmp needs
 // scan_tmp_bytes(n) bytes.
 size_t scan_tmp_bytes(int64_t n);
 cudaError_t launch_scan_u32(const uint32_t* in, int64_t n, int64_t* out, void* tmp, cudaStream_t s);
 
-// Conflict build.
+// Conflict build.  Run k of row v is runoff[loff[v] + k] .. runoff[loff[v]+k+1].
 struct ConflictArgs {
-  int64_t n;
-  int32_t L;
-  int64_t P;
+  int64_t n;             // vertices of the round
+  int64_t E;             // list entries (= loff[n])
+  int32_t Lmax;          // longest list of the round
+  int32_t Lu;            // L of every vertex when all lists have one length
+                         // (loff[v] = v * Lu; ent_v unused), else 0
+  int64_t P;             // bucket colors of the round (sum of the sets' P)
   const uint64_t* xz;    // [n][2]
-  const int32_t* lists;  // [n][L] round-local colors, ascending
-  uint32_t* cnt;         // [n*L] run lengths          (count pass)
-  uint32_t* xcnt;        // [n*L] side-list lengths    (count pass)
-  const int64_t* runoff; // [n*L+1]                    (fill pass)
-  const int64_t* xoff;   // [n*L+1]                    (fill pass)
-  int32_t* col;          // [nnz]                      (fill pass)
-  int32_t* xcol;         // [n_extra]                  (fill pass)
+  const int32_t* lists;  // [E] bucket colors, ascending within each vertex
+  const int64_t* loff;   // [n+1]
+  const int32_t* ent_v;  // [E] vertex of each list entry
+  uint32_t* cnt;         // [E] run lengths          (count / mask pass)
+  uint32_t* xcnt;        // [E] side-list lengths    (count / mask pass)
+  const int64_t* runoff; // [E+1]                    (fill / emit pass)
+  const int64_t* xoff;   // [E+1]                    (fill / emit pass)
+  int32_t* col;          // [nnz]                    (fill / emit pass)
+  int32_t* xcol;         // [n_extra]                (fill / emit pass)
   int32_t* err;          // device error word
   uint32_t* rmask;       // bucket join: run words      (mask pass -> emit)
   uint32_t* xmask;       // bucket join: side-list words (mask pass -> emit)
   int32_t smax;          // bucket join: largest bucket (emit pass)
 };
 
-// Buckets: members of color c are bmem[boff[c] .. boff[c+1]) ascending.
-cudaError_t launch_bucket_hist(const int32_t* lists, int64_t n, int32_t L, uint32_t* bcount,
-                               cudaStream_t s);
-cudaError_t launch_bucket_fill(const int32_t* lists, int64_t n, int32_t L, const int64_t* boff,
-                               uint32_t* bcursor, int32_t* bmem, cudaStream_t s);
-cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err,
-                               cudaStream_t s);
+// Buckets: members of color c are bmem[boff[c] .. boff[c+1]) ascending; a
+// member is stored as its list-entry index e (owner ent_v[e], position
+// e - loff[owner]).
+cudaError_t launch_bucket_hist(const int32_t* lists, int64_t E, uint32_t* bcount, cudaStream_t s);
+cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* boff, uint32_t* bcursor,
+                               int32_t* bmem, cudaStream_t s);
+cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, cudaStream_t s);
 // out32[0] = max bucket size; out64[0] = sum over buckets of s (s - 1).
 cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out32,
                                 unsigned long long* out64, cudaStream_t s);
@@ -120,14 +166,15 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
 cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
                                const int64_t* moff, int32_t smax, cudaStream_t s);
 cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s);
-cudaError_t launch_row_offsets(const int64_t* runoff, int64_t n, int32_t L, int64_t* off,
+// off[u] = runoff[loff[u]], u <= n.
+cudaError_t launch_row_offsets(const int64_t* runoff, const int64_t* loff, int64_t n, int64_t* off,
                                cudaStream_t s);
 
 // Coloring and carry.
 struct ColorArgs {
   int64_t n;
-  int32_t L;
   const int32_t* lists;
+  const int64_t* loff;
   const int64_t* runoff;
   const int32_t* col;
   const int64_t* xoff;
@@ -139,8 +186,8 @@ struct ColorArgs {
   uint32_t* blkw;   // [n] the vertex's candidate color when it started waiting
 };
 // Work list of all n vertices in ascending (priority, id): a counting sort on
-// the top log2(nbins) priority bits, then a sort inside each bin.  hist needs nbins
-// uint32, hoff nbins + 1 int64, tmp scan_tmp_bytes(nbins) bytes.
+// the top log2(nbins) priority bits, then a sort inside each bin.  hist needs
+// nbins uint32, hoff nbins + 1 int64, tmp scan_tmp_bytes(nbins) bytes.
 int prio_bins_for(int64_t n);
 cudaError_t launch_prio_order(const uint32_t* prio, int64_t n, int nbins, uint32_t* hist, int64_t* hoff,
                               void* tmp, int32_t* work, cudaStream_t s);
@@ -151,6 +198,10 @@ cudaError_t launch_color_wake(const ColorArgs& a, const int32_t* work_in, const 
                               int32_t* nactive, int32_t* work_out, int32_t* nwork_out, cudaStream_t s);
 cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const int32_t* nwork_in,
                                int32_t* work_out, int32_t* nwork_out, cudaStream_t s);
+// Ordered persistent coloring of a round: `order` must list the vertices in
+// exact (priority, id) order (launch_prio_order gives it).  On return *err
+// is 1 if a bounded wait ran out (then recolor with launch_color_all).
+cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32_t* err, cudaStream_t s);
 // Every sweep of a round in one cooperative launch.  ctl [kCtlWords] int32:
 // ctl[0] holds the pending count of wa on entry (launch_color_init writes
 // it), the rest must be zero; on exit ctl[3] = sweeps, ctl[4] = 1 if the
@@ -158,18 +209,20 @@ cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const
 // logs the pending count (ctl[8 + s]), the globaltimer at the sweep's start
 // (uint64 at ctl + 8 + kSweepLog, entry s) and the active count
 // (ctl[8 + 3 kSweepLog + s]).
-// Ordered persistent coloring of a round: `order` must list the vertices in
-// exact (priority, id) order (launch_prio_order gives it).  On return *err
-// is 1 if a bounded wait ran out (then recolor with launch_color_all).
-cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32_t* err, cudaStream_t s);
 constexpr int kSweepLog = 64;
 constexpr int kCtlWords = 8 + 4 * kSweepLog;
 cudaError_t launch_color_all(const ColorArgs& a, int32_t* wa, int32_t* wb, int32_t* wact, int32_t* ctl,
                              cudaStream_t s);
-cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* gid, int64_t base,
-                               int32_t* color, uint32_t* flag, cudaStream_t s);
+// Colors to the output (final color = base + bucket color - cofs of the
+// vertex's set, written at its batch-global id) and flags of the uncolored.
+cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* gid, const int64_t* soff,
+                               int32_t nsets, const SetRound* sets, int32_t* color, uint32_t* flag,
+                               cudaStream_t s);
 cudaError_t launch_carry_gather(const uint32_t* flag, const int64_t* pos, int64_t n, const int32_t* gid,
                                 const uint64_t* xz, int32_t* gid_out, uint64_t* xz_out, cudaStream_t s);
+// Remaining vertices per set after a carry: hist[k] += 1 for each gid.
+cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets, uint32_t* hist,
+                              cudaStream_t s);
 cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t n, uint64_t* xz_out,
                              cudaStream_t s);
 cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s);

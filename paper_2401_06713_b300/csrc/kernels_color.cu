@@ -98,7 +98,7 @@ __global__ void k_color_init(ColorArgs a, const uint32_t* __restrict__ prio, int
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v == 0) *nwork = (int32_t)a.n;
   if (v >= a.n) return;
-  a.state[v] = ((uint64_t)prio[v] << 32) | (((uint64_t)(uint32_t)a.lists[v * a.L] << 2) | kUndecided);
+  a.state[v] = ((uint64_t)prio[v] << 32) | (((uint64_t)(uint32_t)a.lists[a.loff[v]] << 2) | kUndecided);
   a.kcur[v] = 0;
   a.rcur[v] = 0;
   a.blk[v] = -1;
@@ -124,11 +124,11 @@ __device__ __forceinline__ void publish(uint64_t* state, int32_t v, uint32_t w) 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* __restrict__ work_out,
                                             int32_t* __restrict__ nwork_out) {
-  const int L = a.L;
+  const int64_t row = a.loff[v];
+  const int L = (int)(a.loff[v + 1] - row);
   const uint32_t pv = (uint32_t)(__ldcg(&a.state[v]) >> 32);
   int k = a.kcur[v];
   uint32_t cur = a.rcur[v];
-  const int64_t row = (int64_t)v * L;
   while (true) {
     if (k >= L) {
       if (lane == 0) publish(a.state, v, (kFailedColor << 2) | kFailed);
@@ -324,9 +324,9 @@ __global__ void __launch_bounds__(256, 4) k_color_all(ColorArgs a, int32_t* __re
 constexpr int kMaxPolls = 1 << 20;
 
 __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
-  const int L = a.L;
+  const int64_t row = a.loff[v];
+  const int L = (int)(a.loff[v + 1] - row);
   const uint32_t pv = (uint32_t)(__ldcg(&a.state[v]) >> 32);
-  const int64_t row = (int64_t)v * L;
   int polls = 0;
   for (int k = 0; k < L; ++k) {
     const uint32_t c = (uint32_t)a.lists[row + k];
@@ -481,21 +481,46 @@ cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const
 // ---------------------------------------------------------------------------
 // Carry
 // ---------------------------------------------------------------------------
-// Write colors to the global array and flag the vertices that failed.
+// Write colors to the output and flag the vertices that failed: the final
+// color of a vertex of set k is base_k + (bucket color - cofs_k), written at
+// its batch-global id.
 __global__ void k_carry_flags(const uint64_t* __restrict__ state, int64_t n, const int32_t* __restrict__ gid,
-                              int64_t base, int32_t* __restrict__ color, uint32_t* __restrict__ flag) {
+                              const int64_t* __restrict__ soff, int nsets, const SetRound* __restrict__ sets,
+                              int32_t* __restrict__ color, uint32_t* __restrict__ flag) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const uint32_t w = (uint32_t)state[v];
   const uint32_t st = w & 3u;
-  if (st == kColored) color[gid ? gid[v] : v] = (int32_t)(base + (int64_t)(w >> 2));
+  if (st == kColored) {
+    const int64_t g = gid ? (int64_t)gid[v] : v;
+    const SetRound& sr = sets[nsets > 1 ? set_of(soff, nsets, g) : 0];
+    color[g] = (int32_t)(sr.base + ((int64_t)(w >> 2) - sr.cofs));
+  }
   flag[v] = st == kColored ? 0u : 1u;
 }
 
-cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* gid, int64_t base, int32_t* color,
-                               uint32_t* flag, cudaStream_t s) {
+cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* gid, const int64_t* soff,
+                               int32_t nsets, const SetRound* sets, int32_t* color, uint32_t* flag,
+                               cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_carry_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(state, n, gid, base, color, flag);
+  k_carry_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(state, n, gid, soff, nsets, sets, color, flag);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void k_set_counts(const int32_t* __restrict__ gid, int64_t n, const int64_t* __restrict__ soff, int nsets,
+                             uint32_t* __restrict__ hist) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int64_t g = gid ? (int64_t)gid[v] : v;
+  atomicAdd(&hist[nsets > 1 ? set_of(soff, nsets, g) : 0], 1u);
+}
+
+cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets, uint32_t* hist,
+                              cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nsets, s);
+  if (e != cudaSuccess || n <= 0) return e;
+  k_set_counts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gid, n, soff, nsets, hist);
   count_launches(1);
   return cudaGetLastError();
 }

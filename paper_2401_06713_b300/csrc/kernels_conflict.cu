@@ -37,8 +37,8 @@ __global__ void k_bucket_hist(const int32_t* __restrict__ lists, int64_t total, 
     atomicAdd(&bcount[lists[i]], 1u);
 }
 
-cudaError_t launch_bucket_hist(const int32_t* lists, int64_t n, int32_t L, uint32_t* bcount, cudaStream_t s) {
-  const int64_t total = n * L;
+cudaError_t launch_bucket_hist(const int32_t* lists, int64_t E, uint32_t* bcount, cudaStream_t s) {
+  const int64_t total = E;
   if (total <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 148 * 16);
   k_bucket_hist<<<blocks, 256, 0, s>>>(lists, total, bcount);
@@ -46,22 +46,21 @@ cudaError_t launch_bucket_hist(const int32_t* lists, int64_t n, int32_t L, uint3
   return cudaGetLastError();
 }
 
-__global__ void k_bucket_fill(const int32_t* __restrict__ lists, int64_t total, int32_t L,
-                              const int64_t* __restrict__ boff, uint32_t* __restrict__ bcursor,
-                              int32_t* __restrict__ bmem) {
+__global__ void k_bucket_fill(const int32_t* __restrict__ lists, int64_t total, const int64_t* __restrict__ boff,
+                              uint32_t* __restrict__ bcursor, int32_t* __restrict__ bmem) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = lists[i];
     const uint32_t pos = atomicAdd(&bcursor[c], 1u);
-    bmem[boff[c] + pos] = (int32_t)i;  // v * L + k: ascending i is ascending v
+    bmem[boff[c] + pos] = (int32_t)i;  // list entry: ascending entry is ascending vertex
   }
 }
 
-cudaError_t launch_bucket_fill(const int32_t* lists, int64_t n, int32_t L, const int64_t* boff, uint32_t* bcursor,
+cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* boff, uint32_t* bcursor,
                                int32_t* bmem, cudaStream_t s) {
-  const int64_t total = n * L;
+  const int64_t total = E;
   if (total <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 148 * 16);
-  k_bucket_fill<<<blocks, 256, 0, s>>>(lists, total, L, boff, bcursor, bmem);
+  k_bucket_fill<<<blocks, 256, 0, s>>>(lists, total, boff, bcursor, bmem);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -151,8 +150,9 @@ constexpr int kExCap = 2048;  // exclusion pairs per bucket before the exact fal
 struct BucketSmem {
   uint64_t* sx;
   uint64_t* sz;
-  int32_t* sid;
-  uint16_t* kk;
+  int32_t* sid;   // member vertex
+  int32_t* sfl;   // member's list entry (bucket color's position)
+  uint16_t* kk;   // position of the bucket color in the member's list
   int32_t* exo;   // [smax + 1]
   int32_t* excur; // [smax]
   int32_t* scnt;  // [smax] run counts
@@ -168,7 +168,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 __host__ __device__ inline size_t bucket_smem_bytes(int smax, int hs) {
   size_t b = 0;
   b += align16(sizeof(uint64_t) * smax) * 2;
-  b += align16(sizeof(int32_t) * smax);
+  b += align16(sizeof(int32_t) * smax) * 2;
   b += align16(sizeof(uint16_t) * smax);
   b += align16(sizeof(int32_t) * (smax + 1));
   b += align16(sizeof(int32_t) * smax);
@@ -185,6 +185,7 @@ __device__ inline BucketSmem carve(uint8_t* p, int smax, int hs) {
   m.sx = (uint64_t*)p; p += align16(sizeof(uint64_t) * smax);
   m.sz = (uint64_t*)p; p += align16(sizeof(uint64_t) * smax);
   m.sid = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
+  m.sfl = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
   m.kk = (uint16_t*)p; p += align16(sizeof(uint16_t) * smax);
   m.exo = (int32_t*)p; p += align16(sizeof(int32_t) * (smax + 1));
   m.excur = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
@@ -298,7 +299,7 @@ __device__ void mask_blocks(const ConflictArgs& a, BucketSmem& S, int s, int L, 
     } else if (ir < s) {
       for (uint32_t bits = my_m; bits; bits &= bits - 1) {
         const int jj = (J << 5) + __ffs(bits) - 1;
-        if (share_prefix(a.lists + (int64_t)S.sid[ir] * L, S.kk[ir], a.lists + (int64_t)S.sid[jj] * L, S.kk[jj]))
+        if (share_prefix(a.lists + (S.sfl[ir] - S.kk[ir]), S.kk[ir], a.lists + (S.sfl[jj] - S.kk[jj]), S.kk[jj]))
           myex |= bits & (0u - bits);
       }
     }
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_bucket_mask(ConflictArgs a,
   const int hs = 1 << hs_log2;
   BucketSmem S = carve(smem_raw, smax, hs);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int L = a.L;
+  const int L = a.Lmax;
 
   for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
     const int64_t o = boff[b];
@@ -339,12 +340,13 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_bucket_mask(ConflictArgs a,
     if (s == 0) continue;
     if (threadIdx.x < 4) S.misc[threadIdx.x] = 0;
     for (int i = threadIdx.x; i < s; i += blockDim.x) {
-      const int32_t flat = bmem[o + i];  // v * L + k, k = position of color b in v's list
-      const int32_t v = flat / L;
+      const int32_t flat = bmem[o + i];  // list entry of color b in member v's list
+      const int32_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
       S.sid[i] = v;
+      S.sfl[i] = flat;
       S.sx[i] = a.xz[2 * (int64_t)v];
       S.sz[i] = a.xz[2 * (int64_t)v + 1];
-      S.kk[i] = (uint16_t)(flat - v * L);
+      S.kk[i] = (uint16_t)(flat - (a.Lu ? (int64_t)v * a.Lu : a.loff[v]));
       S.excur[i] = 0;
       S.scnt[i] = 0;
       S.sxcnt[i] = 0;
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_bucket_mask(ConflictArgs a,
       for (int idx = threadIdx.x; idx < s * L; idx += blockDim.x) {
         const int i = idx / L, t = idx - i * L;
         if (t < S.kk[i]) {
-          const uint32_t c = (uint32_t)__ldg(a.lists + (int64_t)S.sid[i] * L + t);
+          const uint32_t c = (uint32_t)__ldg(a.lists + (int64_t)(S.sfl[i] - S.kk[i]) + t);
           const uint32_t key = ((c + 1u) << 11) | (uint32_t)i;
           uint32_t slot = (c * 0x9E3779B1u) >> (32 - hs_log2);
           while (true) {
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_bucket_mask(ConflictArgs a,
       mask_blocks<false>(a, S, s, L, lane, wid, nw, a.rmask + moff[b], a.xmask + moff[b]);
     __syncthreads();
     for (int i = threadIdx.x; i < s; i += blockDim.x) {
-      const int64_t slot = (int64_t)S.sid[i] * L + S.kk[i];
+      const int64_t slot = S.sfl[i];
       a.cnt[slot] = (uint32_t)S.scnt[i];
       a.xcnt[slot] = (uint32_t)S.sxcnt[i];
     }
@@ -455,7 +457,7 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
                                int32_t smax, cudaStream_t s) {
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   smax = max(smax, 1);
-  int64_t want = (int64_t)smax * (int64_t)max(a.L - 1, 1) * 3 / 2;
+  int64_t want = (int64_t)smax * (int64_t)max(a.Lmax - 1, 1) * 3 / 2;
   int hs_log2 = 8;
   while ((1ll << hs_log2) < want && hs_log2 < 14) ++hs_log2;
   const size_t bytes = bucket_smem_bytes(smax, 1 << hs_log2);
@@ -495,11 +497,10 @@ __global__ void __launch_bounds__(512) k_bucket_emit(ConflictArgs a, const int64
                                                      const int64_t* __restrict__ moff) {
   extern __shared__ __align__(16) int32_t emit_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int L = a.L;
   const uint32_t lt = lanemask_lt();
   const int smax = a.smax;
   int32_t* vid = emit_smem;          // [smax] member vertex ids
-  int32_t* flat = emit_smem + smax;  // [smax] v * L + k
+  int32_t* flat = emit_smem + smax;  // [smax] member list entries
   for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
     const int64_t o = boff[b];
     const int s = (int)(boff[b + 1] - o);
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(512) k_bucket_emit(ConflictArgs a, const int64
     for (int i = threadIdx.x; i < s; i += blockDim.x) {
       const int32_t f = bmem[o + i];
       flat[i] = f;
-      vid[i] = f / L;
+      vid[i] = a.Lu ? f / a.Lu : a.ent_v[f];
     }
     __syncthreads();
     const int nwb = (s + 31) >> 5;
@@ -574,19 +575,20 @@ constexpr int kApWarps = 8;
 template <bool FILL>
 __global__ void __launch_bounds__(kApWarps * 32) k_allpairs(ConflictArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  const int L = a.L;
+  const int Lm = a.Lmax;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // per warp: row list [L] int32, run counters/cursors [L] int64, side [L] int64
-  int32_t* rl = (int32_t*)smem_raw + (size_t)wid * L;
-  int64_t* cur = (int64_t*)(smem_raw + align16(sizeof(int32_t) * L * kApWarps)) + (size_t)wid * 2 * L;
-  int64_t* xcur = cur + L;
+  // per warp: row list [Lmax] int32, run counters/cursors [Lmax] int64, side [Lmax] int64
+  int32_t* rl = (int32_t*)smem_raw + (size_t)wid * Lm;
+  int64_t* cur = (int64_t*)(smem_raw + align16(sizeof(int32_t) * Lm * kApWarps)) + (size_t)wid * 2 * Lm;
+  int64_t* xcur = cur + Lm;
   const uint32_t lt = lanemask_lt();
   for (int64_t u = (int64_t)blockIdx.x * kApWarps + wid; u < a.n; u += (int64_t)gridDim.x * kApWarps) {
-    const int32_t* lu = a.lists + u * L;
-    for (int t = lane; t < L; t += 32) {
-      rl[t] = lu[t];
-      cur[t] = FILL ? a.runoff[u * L + t] : 0;
-      xcur[t] = FILL ? a.xoff[u * L + t] : 0;
+    const int64_t ru = a.loff[u];
+    const int Lu = (int)(a.loff[u + 1] - ru);
+    for (int t = lane; t < Lu; t += 32) {
+      rl[t] = a.lists[ru + t];
+      cur[t] = FILL ? a.runoff[ru + t] : 0;
+      xcur[t] = FILL ? a.xoff[ru + t] : 0;
     }
     __syncwarp();
     const uint64_t xu = a.xz[2 * u], zu = a.xz[2 * u + 1];
@@ -594,9 +596,10 @@ __global__ void __launch_bounds__(kApWarps * 32) k_allpairs(ConflictArgs a) {
       const int64_t v = v0 + lane;
       int k0 = -1, nshared = 0;
       if (v < a.n && v != u && commute1(xu, zu, a.xz[2 * v], a.xz[2 * v + 1])) {
-        const int32_t* lv = a.lists + v * L;
+        const int32_t* lv = a.lists + a.loff[v];
+        const int Lv = (int)(a.loff[v + 1] - a.loff[v]);
         int i = 0, j = 0;
-        while (i < L && j < L) {
+        while (i < Lu && j < Lv) {
           const int32_t x = rl[i], y = __ldg(lv + j);
           if (x == y) {
             if (k0 < 0) {
@@ -635,9 +638,10 @@ __global__ void __launch_bounds__(kApWarps * 32) k_allpairs(ConflictArgs a) {
           const int l = __ffs(more) - 1;
           more &= more - 1;
           if (lane == l) {
-            const int32_t* lv = a.lists + v * L;
+            const int32_t* lv = a.lists + a.loff[v];
+            const int Lv = (int)(a.loff[v + 1] - a.loff[v]);
             int i = 0, j = 0, seen = 0;
-            while (i < L && j < L) {
+            while (i < Lu && j < Lv) {
               const int32_t x = rl[i], y = __ldg(lv + j);
               if (x == y) {
                 if (seen++) a.xcol[xcur[i]++] = (int32_t)v;
@@ -656,9 +660,9 @@ __global__ void __launch_bounds__(kApWarps * 32) k_allpairs(ConflictArgs a) {
     }
     __syncwarp();
     if (!FILL) {
-      for (int t = lane; t < L; t += 32) {
-        a.cnt[u * L + t] = (uint32_t)cur[t];
-        a.xcnt[u * L + t] = (uint32_t)xcur[t];
+      for (int t = lane; t < Lu; t += 32) {
+        a.cnt[ru + t] = (uint32_t)cur[t];
+        a.xcnt[ru + t] = (uint32_t)xcur[t];
       }
     }
     __syncwarp();
@@ -667,7 +671,7 @@ __global__ void __launch_bounds__(kApWarps * 32) k_allpairs(ConflictArgs a) {
 
 cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const size_t bytes = align16(sizeof(int32_t) * a.L * kApWarps) + sizeof(int64_t) * 2 * a.L * kApWarps;
+  const size_t bytes = align16(sizeof(int32_t) * a.Lmax * kApWarps) + sizeof(int64_t) * 2 * a.Lmax * kApWarps;
   auto kern = fill ? k_allpairs<true> : k_allpairs<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
@@ -677,13 +681,14 @@ cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-__global__ void k_row_offsets(const int64_t* __restrict__ runoff, int64_t n, int32_t L, int64_t* __restrict__ off) {
+__global__ void k_row_offsets(const int64_t* __restrict__ runoff, const int64_t* __restrict__ loff, int64_t n,
+                              int64_t* __restrict__ off) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u <= n) off[u] = runoff[u * L];
+  if (u <= n) off[u] = runoff[loff[u]];
 }
 
-cudaError_t launch_row_offsets(const int64_t* runoff, int64_t n, int32_t L, int64_t* off, cudaStream_t s) {
-  k_row_offsets<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(runoff, n, L, off);
+cudaError_t launch_row_offsets(const int64_t* runoff, const int64_t* loff, int64_t n, int64_t* off, cudaStream_t s) {
+  k_row_offsets<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(runoff, loff, n, off);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -49,21 +49,63 @@ cudaError_t launch_philox_draws(uint64_t seed, int32_t round, int64_t gid, uint3
   return cudaGetLastError();
 }
 
-// Alg. 1 assign_rand_list_colors: one thread per vertex.  Floyd's sampling of
-// L distinct values of [0, P) (Bentley & Floyd, CACM 1987): for j = P-L ..
-// P-1 draw t in [0, j] (x*(j+1) >> 32 of the next Philox word); keep t, or j
-// if t was already kept.  Then an insertion sort; lists hold round-local
-// colors.  The priority is draw 0 of the PRIO stream.
-template <int LCAP>
-__global__ void k_assign_lists(uint64_t seed, int32_t round, const int32_t* __restrict__ gid, int64_t n,
-                               int64_t P, int32_t L, int32_t* __restrict__ lists, uint32_t* __restrict__ prio) {
+// List length of every round vertex (the L of its set), then offsets.
+__global__ void k_list_len(const int32_t* __restrict__ gid, int64_t n, const int64_t* __restrict__ soff, int nsets,
+                           const SetRound* __restrict__ sets, uint32_t* __restrict__ len) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const int64_t g = gid ? (int64_t)gid[v] : v;
+  len[v] = (uint32_t)sets[nsets > 1 ? set_of(soff, nsets, g) : 0].L;
+}
+
+cudaError_t launch_list_offsets(const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
+                                const SetRound* sets, uint32_t* len, int64_t* loff, void* tmp, cudaStream_t s) {
+  if (n > 0) {
+    k_list_len<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gid, n, soff, nsets, sets, len);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return launch_scan_u32(len, n, loff, tmp, s);
+}
+
+__global__ void k_entry_owner(const int64_t* __restrict__ loff, int64_t n, int32_t* __restrict__ ent_v) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  for (int64_t e = loff[v]; e < loff[v + 1]; ++e) ent_v[e] = (int32_t)v;
+}
+
+cudaError_t launch_entry_owner(const int64_t* loff, int64_t n, int32_t* ent_v, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_entry_owner<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(loff, n, ent_v);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Alg. 1 assign_rand_list_colors: one thread per vertex, with the P, L and
+// seed of the vertex's set; Philox is keyed by the set's seed and the
+// vertex's id within its set.  Floyd's sampling of L distinct values of
+// [0, P) (Bentley & Floyd, CACM 1987): for j = P-L .. P-1 draw t in [0, j]
+// (x*(j+1) >> 32 of the next Philox word); keep t, or j if t was already
+// kept.  Then an insertion sort; lists hold bucket colors (round-local color
+// + the set's offset cofs).  The priority is draw 0 of the PRIO stream.
+template <int LCAP>
+__global__ void k_assign_lists(int32_t round, const int32_t* __restrict__ gid, int64_t n,
+                               const int64_t* __restrict__ soff, int nsets, const SetRound* __restrict__ sets,
+                               const int64_t* __restrict__ loff, int32_t* __restrict__ lists,
+                               uint32_t* __restrict__ prio) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int64_t gg = gid ? (int64_t)gid[v] : v;
+  const int k = nsets > 1 ? set_of(soff, nsets, gg) : 0;
+  const SetRound sr = sets[k];
+  const int64_t g = gg - soff[k];  // id within the set
+  const int64_t P = sr.P;
+  const int L = sr.L;
   uint32_t sel[LCAP];
   u32x4 blk{0, 0, 0, 0};
   for (int m = 0; m < L; ++m) {
-    if ((m & 3) == 0) blk = philox_block(seed, round, g, kTagList, (uint32_t)(m >> 2));
+    if ((m & 3) == 0) blk = philox_block(sr.seed, round, g, kTagList, (uint32_t)(m >> 2));
     const uint32_t x = pick(blk, (uint32_t)(m & 3));
     const uint64_t j = (uint64_t)(P - L + m);
     const uint32_t t = (uint32_t)(((uint64_t)x * (j + 1)) >> 32);
@@ -80,21 +122,22 @@ __global__ void k_assign_lists(uint64_t seed, int32_t round, const int32_t* __re
     }
     sel[b + 1] = key;
   }
-  int32_t* out = lists + v * L;
-  for (int a = 0; a < L; ++a) out[a] = (int32_t)sel[a];
-  prio[v] = philox_block(seed, round, g, kTagPrio, 0u).x;
+  int32_t* out = lists + loff[v];
+  for (int a = 0; a < L; ++a) out[a] = (int32_t)(sr.cofs + sel[a]);
+  prio[v] = philox_block(sr.seed, round, g, kTagPrio, 0u).x;
 }
 
-cudaError_t launch_assign_lists(uint64_t seed, int32_t round, const int32_t* gid, int64_t n, int64_t P,
-                                int32_t L, int32_t* lists, uint32_t* prio, cudaStream_t s) {
+cudaError_t launch_assign_lists(int32_t round, const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
+                                const SetRound* sets, int32_t Lmax, const int64_t* loff, int32_t* lists,
+                                uint32_t* prio, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n + 127) / 128);
-  if (L <= 32) {
-    k_assign_lists<32><<<blocks, 128, 0, s>>>(seed, round, gid, n, P, L, lists, prio);
-  } else if (L <= 128) {
-    k_assign_lists<128><<<blocks, 128, 0, s>>>(seed, round, gid, n, P, L, lists, prio);
+  if (Lmax <= 32) {
+    k_assign_lists<32><<<blocks, 128, 0, s>>>(round, gid, n, soff, nsets, sets, loff, lists, prio);
+  } else if (Lmax <= 128) {
+    k_assign_lists<128><<<blocks, 128, 0, s>>>(round, gid, n, soff, nsets, sets, loff, lists, prio);
   } else {
-    k_assign_lists<kMaxL><<<blocks, 128, 0, s>>>(seed, round, gid, n, P, L, lists, prio);
+    k_assign_lists<kMaxL><<<blocks, 128, 0, s>>>(round, gid, n, soff, nsets, sets, loff, lists, prio);
   }
   count_launches(1);
   return cudaGetLastError();

@@ -98,6 +98,8 @@ _SIGS = {
     "picasso_config_default": [ctypes.POINTER(Config)],
     "picasso_pack": [_vp, _i64, _i32, _vp, _vp],
     "picasso_init": [ctypes.POINTER(_vp), ctypes.POINTER(Config), _vp, _i64, _i32, _vp],
+    "picasso_init_batch": [ctypes.POINTER(_vp), ctypes.POINTER(Config), _vp, _pi64, _i32,
+                           ctypes.POINTER(ctypes.c_uint64), _i32, _vp],
     "picasso_round_params": [_vp, _pi64, _pi32, _pi64],
     "picasso_assign_lists": [_vp, _i64, _i32, _i64],
     "picasso_build_conflicts": [_vp, ctypes.POINTER(CSR)],
@@ -193,7 +195,10 @@ class Picasso:
 
     def __init__(self, xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
                  algo: str = "auto", max_rounds: int = 100000, byte_budget: int = 0, stream=None,
-                 color: str = "auto"):
+                 color: str = "auto", set_offsets=None, seeds=None):
+        """One set, or with ``set_offsets`` (host, nsets + 1 ints) a batch of
+        independent sets stored back to back in ``xz`` (seeds default to
+        seed + k)."""
         assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2
         self.xz = xz.contiguous()
         self.n = int(xz.shape[0])
@@ -210,8 +215,17 @@ class Picasso:
         cfg.color_algo = COLOR_ALGOS[color]
         self.cfg = cfg
         h = ctypes.c_void_p()
-        _ck(_lib().picasso_init(ctypes.byref(h), ctypes.byref(cfg), _ptr(self.xz), self.n, q,
-                                ctypes.c_void_p(self.stream.cuda_stream)), "picasso_init")
+        if set_offsets is None:
+            _ck(_lib().picasso_init(ctypes.byref(h), ctypes.byref(cfg), _ptr(self.xz), self.n, q,
+                                    ctypes.c_void_p(self.stream.cuda_stream)), "picasso_init")
+        else:
+            offs = (ctypes.c_int64 * len(set_offsets))(*[int(x) for x in set_offsets])
+            nsets = len(set_offsets) - 1
+            sd = None
+            if seeds is not None:
+                sd = (ctypes.c_uint64 * nsets)(*[int(x) for x in seeds])
+            _ck(_lib().picasso_init_batch(ctypes.byref(h), ctypes.byref(cfg), _ptr(self.xz), offs, nsets, sd, q,
+                                          ctypes.c_void_p(self.stream.cuda_stream)), "picasso_init_batch")
         self.h = h
 
     def close(self):
