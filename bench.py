@@ -245,6 +245,8 @@ def run_gpu(args):
                 "avg_launch_ms": st["t_pairs_ms"] / max(st["pairs_launches"], 1),
                 "tested_pairs_per_launch": st["tested_pairs"] / max(st["pairs_launches"], 1)}
 
+    batch = None if args.no_batch else bench_batch(rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         # round sizes of this run (the oracle and GPU agree on them)
@@ -264,7 +266,7 @@ def run_gpu(args):
         "config": dict(workload(n), parallelism=f"replicas{world}" if world > 1 else "single"),
         "pair_tests_per_s": pair_rate, "colors": int(len(np.unique(colors_np))), "rounds": rounds,
         "peak_bytes": st["peak_bytes"], "breakdown_ms_per_step": per_step,
-        "roofline": roofline, "cpu_baseline": cpu,
+        "roofline": roofline, "cpu_baseline": cpu, "batch": batch,
         "e2e": {"value": world * n / (ms_e2e / args.steps / 1e3), "unit": "strings/s",
                 "h2d_bytes_per_step": n * Q, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": launches, "clocks": clocks, "wall_s": t_wall,
@@ -276,6 +278,59 @@ def run_gpu(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def bench_batch(rank, nsets=256):
+    """The batched workload: 256 independent sets (n log-uniform in [1e3,
+    5e4], q uniform in {16,24,32,48,64}, weight p uniform in [0.1, 0.5],
+    P = n/8, alpha = 2) colored in one batched context, against the same sets
+    run one after another through the single-set entry points."""
+    import numpy as np
+    import torch
+
+    from paper_2401_06713_b300 import picasso, synth
+
+    specs = synth.batch_specs(nsets, seed=rank)
+    sets = [synth.pauli_weighted(n, q, p, seed=rank, stream=i + 1) for i, (n, q, p) in enumerate(specs)]
+    offs = [0]
+    for c in sets:
+        offs.append(offs[-1] + len(c))
+    pad = np.zeros((offs[-1], 64), dtype=np.uint8)
+    for k, c in enumerate(sets):
+        pad[offs[k]:offs[k + 1], :c.shape[1]] = c
+    xz = picasso.pack(torch.from_numpy(pad).cuda())
+    seeds = [rank * 100003 + k for k in range(nsets)]
+    parts = [xz[offs[k]:offs[k + 1]].contiguous() for k in range(nsets)]
+
+    def batched():
+        with picasso.Picasso(xz, 64, set_offsets=offs, seeds=seeds) as p:
+            return p.run()[0]
+
+    def sequential():
+        out = []
+        for k in range(nsets):
+            with picasso.Picasso(parts[k], 64, seed=seeds[k]) as p:
+                out.append(p.run()[0])
+        return out
+
+    for _ in range(3):
+        batched()
+    sequential()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    cb = batched()
+    ev[1].record()
+    ev[2].record()
+    cs = sequential()
+    ev[3].record()
+    torch.cuda.synchronize()
+    tb, ts = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    same = all(torch.equal(cb[offs[k]:offs[k + 1]], cs[k]) for k in range(nsets))
+    return {"workload": f"{nsets} sets, n log-uniform [1e3, 5e4], q in {{16,24,32,48,64}}, p in U[0.1,0.5], "
+                        f"P=n/8, alpha=2", "strings": offs[-1], "batched_ms": tb, "sequential_ms": ts,
+            "batched_strings_per_s": offs[-1] / (tb / 1e3), "sequential_strings_per_s": offs[-1] / (ts / 1e3),
+            "speedup": ts / tb, "identical_colors": same}
 
 
 def round_sizes_from(colors, st):
@@ -343,6 +398,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
