@@ -16,6 +16,10 @@ Function map (paper passage each follows):
   color_greedy      Sec. III-B static order, first available list color
   round_params      Table I / Sec. VI parameter rule
   run               Alg. 1, all rounds
+  feature_counts    instance features of the Sec. V regressor (counts)
+  features          the five regressor inputs from those counts
+  mlp (module)      the Sec. V regressor as a 5-64-64-2 MLP, fp64 forward /
+                    backward / AdamW (``oracle.mlp``)
 """
 from __future__ import annotations
 
@@ -92,6 +96,8 @@ def lib():
         L.orc_run.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
                               ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _i64p, _i64p]
         L.orc_run.restype = ctypes.c_int32
+        L.orc_feature_counts.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
+                                         _i64p]
         _lib = L
     return _lib
 
@@ -258,3 +264,24 @@ def run(chars: np.ndarray, seed: int, num: int, den: int, alpha: float, max_roun
     if r < 0:
         raise RuntimeError("oracle run hit max_rounds")
     return color[:N], int(r), stats[:r].copy()
+
+
+def feature_counts(chars: np.ndarray, seed: int, samples: int) -> tuple[int, int]:
+    """(non-identity characters, commuting pairs among the Philox-drawn sample)."""
+    chars = np.ascontiguousarray(chars, dtype=np.uint8)
+    n, q = chars.shape
+    out = np.zeros(2, dtype=np.int64)
+    lib().orc_feature_counts(_p(chars, _u8p), n, q, seed, samples, _p(out, _i64p))
+    return int(out[0]), int(out[1])
+
+
+def features(chars: np.ndarray, seed: int, samples: int, budget_bytes: float) -> np.ndarray:
+    """The five regressor inputs (fp64): ln n / 16, q / 64, mean weight / q,
+    commuting fraction of the sample (1 without samples), log2(budget / n) / 16."""
+    import math
+
+    n, q = chars.shape
+    w, c = feature_counts(chars, seed, samples)
+    s = samples if n >= 2 else 0
+    return np.array([math.log(n) / 16.0, q / 64.0, w / (n * q), c / s if s > 0 else 1.0,
+                     (math.log2(budget_bytes) - math.log2(n)) / 16.0], dtype=np.float64)

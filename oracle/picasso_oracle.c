@@ -515,3 +515,31 @@ int32_t orc_run(const uint8_t* chars, int64_t N, int32_t q, uint64_t seed,
   free(gids);
   return round - 1;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Instance features for the parameter regressor of Sec. V.  The paper feeds */
+/* its regressor (beta, |V|, |E|); here the inputs are the size, the qubit   */
+/* count, the mean Pauli weight, a sampled commuting fraction (the edge      */
+/* density of G') and the memory budget.  This part counts:                  */
+/*   out[0] = non-identity characters over all n strings                     */
+/*   out[1] = commuting pairs among `samples` pairs of distinct strings; pair */
+/*            p takes draws 0 and 1 of stream (seed, round 0, gid p, tag 3): */
+/*            first string floor(d0 n / 2^32), second floor(d1 (n-1) / 2^32), */
+/*            plus one when not below the first.                              */
+/* ------------------------------------------------------------------------ */
+void orc_feature_counts(const uint8_t* chars, int64_t n, int32_t q, uint64_t seed,
+                        int64_t samples, int64_t out[2]) {
+  int64_t weight = 0, commuting = 0;
+  for (int64_t v = 0; v < n; ++v)
+    for (int32_t i = 0; i < q; ++i) weight += chars[v * (int64_t)q + i] != 0;
+  if (n < 2) samples = 0;
+  for (int64_t p = 0; p < samples; ++p) {
+    uint32_t d0 = orc_draw(seed, 0, p, 3u, 0u), d1 = orc_draw(seed, 0, p, 3u, 1u);
+    int64_t a = (int64_t)(((uint64_t)d0 * (uint64_t)n) >> 32);
+    int64_t b = (int64_t)(((uint64_t)d1 * (uint64_t)(n - 1)) >> 32);
+    if (b >= a) ++b;
+    commuting += orc_commute_chars(chars + a * (int64_t)q, chars + b * (int64_t)q, q);
+  }
+  out[0] = weight;
+  out[1] = commuting;
+}

@@ -60,3 +60,32 @@ def batch_sets(count: int, seed: int, **kw):
     for i, (n, q, p) in enumerate(batch_specs(count, seed, **kw)):
         sets.append((pauli_weighted(n, q, p, seed, stream=i + 1), n, q, p))
     return sets
+
+
+def budget_bytes(n: int, g: np.random.Generator, lo: float = 9.0, hi: float = 15.0) -> float:
+    """A memory budget for one instance's conflict structure: n * 2^u bytes,
+    u uniform in [lo, hi] (from about 128 to 8192 int32 entries per vertex)."""
+    return float(n) * 2.0 ** g.uniform(lo, hi)
+
+
+def learned_specs(count: int, seed: int, n_lo: int = 1000, n_hi: int = 50000, qs=(16, 24, 32, 48, 64),
+                  p_lo: float = 0.1, p_hi: float = 0.5, budget_lo: float = 9.0, budget_hi: float = 15.0):
+    """Instances of the parameter-regressor data set: (n, q, p, budget_bytes,
+    string seed, stream); shapes as ``batch_specs``, plus a budget."""
+    g = _rng(seed, 1 << 21)
+    out = []
+    for i, (n, q, p) in enumerate(batch_specs(count, seed, n_lo=n_lo, n_hi=n_hi, qs=qs, p_lo=p_lo, p_hi=p_hi)):
+        out.append((n, q, p, budget_bytes(n, g, budget_lo, budget_hi), seed, i + 1))
+    return out
+
+
+def mlp_init(seed: int, n_in: int = 5, n_hid: int = 64, n_out: int = 2) -> np.ndarray:
+    """Initial weights of the n_in-n_hid-n_hid-n_out regressor as one float32
+    vector W1 | b1 | W2 | b2 | W3 | b3 (row-major): weights normal with std
+    sqrt(2 / fan_in), biases zero."""
+    g = _rng(seed, 1 << 22)
+    parts = []
+    for rows, cols in ((n_hid, n_in), (n_hid, n_hid), (n_out, n_hid)):
+        parts.append(g.normal(0.0, math.sqrt(2.0 / cols), size=rows * cols))
+        parts.append(np.zeros(rows))
+    return np.concatenate(parts).astype(np.float32)
