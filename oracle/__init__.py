@@ -276,12 +276,15 @@ def feature_counts(chars: np.ndarray, seed: int, samples: int) -> tuple[int, int
 
 
 def features(chars: np.ndarray, seed: int, samples: int, budget_bytes: float) -> np.ndarray:
-    """The five regressor inputs (fp64): ln n / 16, q / 64, mean weight / q,
-    commuting fraction of the sample (1 without samples), log2(budget / n) / 16."""
+    """The five regressor inputs (fp64): log2(ln n) - 3 (-3 for n = 1), q / 64,
+    mean weight / q, commuting fraction of the sample (1 without samples),
+    log2(budget / n) / 4 - 3.  Conflict entries per vertex grow like
+    density * (alpha ln n)^2 / (P / n), so size and budget enter on log scales."""
     import math
 
     n, q = chars.shape
     w, c = feature_counts(chars, seed, samples)
     s = samples if n >= 2 else 0
-    return np.array([math.log(n) / 16.0, q / 64.0, w / (n * q), c / s if s > 0 else 1.0,
-                     (math.log2(budget_bytes) - math.log2(n)) / 16.0], dtype=np.float64)
+    return np.array([math.log2(math.log(n)) - 3.0 if n > 1 else -3.0, q / 64.0, w / (n * q),
+                     c / s if s > 0 else 1.0, (math.log2(budget_bytes) - math.log2(n)) / 4.0 - 3.0],
+                    dtype=np.float64)

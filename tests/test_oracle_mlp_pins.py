@@ -186,4 +186,6 @@ def test_feature_density_closed_form():
     p = (1 + 0.25 ** q) / 2
     assert abs(f[3] - p) < 5 * math.sqrt(p * (1 - p) / s)
     assert abs(f[2] - 0.75) < 0.01
-    assert f[0] == pytest.approx(math.log(n) / 16) and f[1] == q / 64 and f[4] == pytest.approx(10 / 16)
+    # n = 4000, budget 1024 bytes per string: log2(ln 4000) - 3 and 10 / 4 - 3
+    assert f[0] == pytest.approx(math.log2(8.294049640102028) - 3) and f[1] == q / 64
+    assert f[4] == pytest.approx(-0.5)
