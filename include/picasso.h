@@ -235,6 +235,68 @@ int picasso_copy_runs(void* ctx, int64_t* d_runoff, int64_t* d_xoff,
 
 int picasso_get_stats(void* ctx, picasso_stats* out);
 
+/* Per-set results of a (batched) context, each array nsets long, host
+ * memory owned by the caller, any may be NULL:
+ *   h_colors[k]     colors set k has used so far: the sum of its finished
+ *                   rounds' palette sizes, the paper's count C = sum_l P_l
+ *                   (Sec. III-C);
+ *   h_peak_bytes[k] largest conflict structure set k had in one round so
+ *                   far, counted like cfg.byte_budget: 8 (n_k + 1) + 4 nnz_k
+ *                   + 4 n_extra_k bytes (row offsets, conflict entries in
+ *                   both directions, side entries);
+ *   h_remaining[k]  set k's uncolored vertices.                            */
+int picasso_get_set_stats(void* ctx, int64_t* h_colors, int64_t* h_peak_bytes,
+                          int64_t* h_remaining);
+
+/* ---- Parameter prediction (Sec. V) -------------------------------------
+ * Sec. V predicts (P' = P/n, alpha) from instance features with a regressor
+ * trained on grid-search labels.  Here the regressor is a 5-64-64-2 MLP with
+ * GELU, bf16 weights and fp32 accumulation; these entries are its device
+ * kernels and the feature extraction.  All pointers are device memory owned
+ * by the caller; all calls are asynchronous on `stream`.
+ *
+ * Parameter vector (fp32 master weights and their bf16 copy share it):
+ *   W1[64][5] | b1[64] | W2[64][64] | b2[64] | W3[2][64] | b3[2]
+ * row-major, y = W3 gelu(W2 gelu(W1 x + b1) + b2) + b3 with the exact
+ * (erf) GELU; picasso_mlp_param_count() elements.                          */
+
+/* Instance features of n packed strings: d_counts[0] = non-identity positions
+ * over all strings, d_counts[1] = commuting pairs among `samples` pairs of
+ * distinct strings drawn by Philox (key seed, round 0, tag 3, counter = pair
+ * index; first string floor(r0 n / 2^32), second floor(r1 (n-1) / 2^32),
+ * plus one when not below the first).  d_feat[0..4] = log2(ln n) - 3
+ * (-3 when n = 1), q / 64, d_counts[0] / (n q), d_counts[1] / samples (1 when
+ * samples = 0), log2(budget_bytes / n) / 4 - 3.  n >= 1, budget_bytes > 0. */
+int picasso_features(const uint64_t* d_xz, int64_t n, int32_t q,
+                     uint64_t seed, int64_t samples, double budget_bytes,
+                     int64_t* d_counts, float* d_feat, void* stream);
+
+int32_t picasso_mlp_param_count(void);
+
+/* d_y[b][0..1] = MLP(d_w, d_x[b][0..4]) for b < batch (fp32 in and out). */
+int picasso_mlp_forward(const uint16_t* d_w, const float* d_x, int32_t batch,
+                        float* d_y, void* stream);
+
+/* Gradient of loss = (1/batch) sum_b sum_o weight_o (y_bo - d_t[b][o])^2 / 2
+ * with respect to the parameters, written to d_grad (fp32, overwritten);
+ * d_loss (may be NULL) receives the loss.  batch >= 1.                      */
+int picasso_mlp_backward(const uint16_t* d_w, const float* d_x,
+                         const float* d_t, float weight0, float weight1,
+                         int32_t batch, float* d_grad, float* d_loss,
+                         void* stream);
+
+/* One AdamW step (decoupled weight decay; Loshchilov & Hutter) on the fp32
+ * master weights with moments d_m, d_v; step >= 1 is the 1-based step used
+ * for bias correction; d_w receives the rounded-to-nearest-even bf16 copy. */
+int picasso_mlp_adamw(float* d_master, uint16_t* d_w, const float* d_grad,
+                      float* d_m, float* d_v, float lr, float beta1,
+                      float beta2, float eps, float weight_decay,
+                      int32_t step, void* stream);
+
+/* d_dst[i] = bf16(d_src[i]), round to nearest even, i < count. */
+int picasso_mlp_to_bf16(const float* d_src, uint16_t* d_dst, int32_t count,
+                        void* stream);
+
 /* Fill d_out[i] with draw i0+i of stream (seed, round, gid, tag), i < count.
  * Exposes the device generator for parity checks against a CPU Philox.      */
 int picasso_philox_draws(uint64_t seed, int32_t round, int64_t gid,

@@ -78,6 +78,8 @@ struct Ctx {
   int64_t* d_soff = nullptr;        // device copy of soff
   SetRound* d_sets = nullptr;       // device copy of sets
   uint32_t* d_hist = nullptr;       // [nsets] per-set counts
+  int64_t* d_set_bytes = nullptr;   // [nsets] conflict-structure bytes of every set this round
+  std::vector<int64_t> set_peak_bytes;  // [nsets] max over built rounds of those bytes
 
   int32_t round = 1;
   int64_t n = 0;          // vertices of the round (all sets)
@@ -474,6 +476,15 @@ int build_conflicts(Ctx* c) {
   }
   TRYC(cudaEventRecord(c->ev[5], s));
   TRYC(launch_row_offsets(c->runoff, c->loff, n, c->off, s));
+  if (c->nsets > 1) {
+    std::vector<int64_t> h(c->nsets);
+    TRYC(launch_set_csr_bytes(c->loff, c->runoff, c->xoff, c->gid, n, c->d_soff, c->nsets, c->d_set_bytes, s));
+    TRYC(cudaMemcpyAsync(h.data(), c->d_set_bytes, sizeof(int64_t) * c->nsets, cudaMemcpyDeviceToHost, s));
+    TRYC(cudaStreamSynchronize(s));
+    for (int k = 0; k < c->nsets; ++k) c->set_peak_bytes[k] = std::max(c->set_peak_bytes[k], h[k]);
+  } else {
+    c->set_peak_bytes[0] = std::max(c->set_peak_bytes[0], csr_bytes);
+  }
   TRYC(cudaEventSynchronize(c->ev[5]));
   if (algo == PICASSO_CONFLICT_BUCKET) {
     // the mask pass tests every unordered pair of a bucket once; the emit
@@ -683,6 +694,7 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
   c->seed.resize(nsets);
   c->remaining.resize(nsets);
   c->set_base.assign(nsets, 0);
+  c->set_peak_bytes.assign(nsets, 0);
   c->sets.assign(nsets, SetRound{});
   for (int k = 0; k < nsets; ++k) {
     c->seed[k] = h_seeds ? h_seeds[k] : cfg->seed + (uint64_t)k;
@@ -700,6 +712,7 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
   if (st == PICASSO_OK) st = alloc(c, &c->d_soff, nsets + 1);
   if (st == PICASSO_OK) st = alloc(c, &c->d_sets, nsets);
   if (st == PICASSO_OK) st = alloc(c, &c->d_hist, nsets);
+  if (st == PICASSO_OK) st = alloc(c, &c->d_set_bytes, nsets);
   if (st == PICASSO_OK)
     st = map_err(cudaMemcpyAsync(c->d_soff, c->soff.data(), sizeof(int64_t) * (nsets + 1), cudaMemcpyHostToDevice,
                                  c->s));
@@ -711,6 +724,7 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
     release(c, &c->d_soff);
     release(c, &c->d_sets);
     release(c, &c->d_hist);
+    release(c, &c->d_set_bytes);
     for (int i = 0; i < 6; ++i)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     cudaFreeHost(c->h_buf);
@@ -965,6 +979,55 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   return PICASSO_OK;
 }
 
+int picasso_get_set_stats(void* ctx, int64_t* h_colors, int64_t* h_peak_bytes, int64_t* h_remaining) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return PICASSO_ERR_INVALID_ARG;
+  for (int k = 0; k < c->nsets; ++k) {
+    if (h_colors) h_colors[k] = c->set_base[k];
+    if (h_peak_bytes) h_peak_bytes[k] = c->set_peak_bytes[k];
+    if (h_remaining) h_remaining[k] = c->remaining[k];
+  }
+  return PICASSO_OK;
+}
+
+int picasso_features(const uint64_t* d_xz, int64_t n, int32_t q, uint64_t seed, int64_t samples,
+                     double budget_bytes, int64_t* d_counts, float* d_feat, void* stream) {
+  if (!d_xz || !d_counts || !d_feat || n < 1 || n >= (int64_t(1) << 31) || q < 1 || samples < 0 ||
+      !(budget_bytes > 0.0) || !std::isfinite(budget_bytes))
+    return PICASSO_ERR_INVALID_ARG;
+  if (q > 64) return PICASSO_ERR_UNSUPPORTED;
+  return map_err(launch_features(d_xz, n, q, seed, samples, std::log2(budget_bytes),
+                                 reinterpret_cast<unsigned long long*>(d_counts), d_feat, (cudaStream_t)stream));
+}
+
+int32_t picasso_mlp_param_count(void) { return mlp_param_count(); }
+
+int picasso_mlp_forward(const uint16_t* d_w, const float* d_x, int32_t batch, float* d_y, void* stream) {
+  if (batch < 0 || (batch > 0 && (!d_w || !d_x || !d_y))) return PICASSO_ERR_INVALID_ARG;
+  return map_err(launch_mlp_forward(d_w, d_x, batch, d_y, (cudaStream_t)stream));
+}
+
+int picasso_mlp_backward(const uint16_t* d_w, const float* d_x, const float* d_t, float weight0, float weight1,
+                         int32_t batch, float* d_grad, float* d_loss, void* stream) {
+  if (batch < 1 || !d_w || !d_x || !d_t || !d_grad || !std::isfinite(weight0) || !std::isfinite(weight1))
+    return PICASSO_ERR_INVALID_ARG;
+  return map_err(launch_mlp_backward(d_w, d_x, d_t, weight0, weight1, batch, d_grad, d_loss, (cudaStream_t)stream));
+}
+
+int picasso_mlp_adamw(float* d_master, uint16_t* d_w, const float* d_grad, float* d_m, float* d_v, float lr,
+                      float beta1, float beta2, float eps, float weight_decay, int32_t step, void* stream) {
+  if (!d_master || !d_w || !d_grad || !d_m || !d_v || step < 1 || !(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) ||
+      !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f) || !(weight_decay >= 0.f))
+    return PICASSO_ERR_INVALID_ARG;
+  return map_err(launch_mlp_adamw(d_master, d_w, d_grad, d_m, d_v, lr, beta1, beta2, eps, weight_decay, step,
+                                  (cudaStream_t)stream));
+}
+
+int picasso_mlp_to_bf16(const float* d_src, uint16_t* d_dst, int32_t count, void* stream) {
+  if (count < 0 || (count > 0 && (!d_src || !d_dst))) return PICASSO_ERR_INVALID_ARG;
+  return map_err(launch_to_bf16(d_src, d_dst, count, (cudaStream_t)stream));
+}
+
 int picasso_trim_memory(int64_t keep_bytes) {
   if (keep_bytes < 0) return PICASSO_ERR_INVALID_ARG;
   int dev = 0;
@@ -1001,6 +1064,7 @@ int picasso_destroy(void* ctx) {
   release(c, &c->d_soff);
   release(c, &c->d_sets);
   release(c, &c->d_hist);
+  release(c, &c->d_set_bytes);
   cudaStreamSynchronize(c->s);
   for (int i = 0; i < 6; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);

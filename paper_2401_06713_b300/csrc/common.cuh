@@ -225,7 +225,20 @@ cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff
                               cudaStream_t s);
 cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t n, uint64_t* xz_out,
                              cudaStream_t s);
+cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int64_t* xoff, const int32_t* gid,
+                                 int64_t n, const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s);
 cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s);
+
+// Parameter predictor and instance features (kernels_mlp.cu).
+int mlp_param_count();
+cudaError_t launch_mlp_forward(const void* w, const float* x, int B, float* y, cudaStream_t s);
+cudaError_t launch_mlp_backward(const void* w, const float* x, const float* t, float wo0, float wo1, int B, float* grad,
+                                float* loss, cudaStream_t s);
+cudaError_t launch_mlp_adamw(float* master, void* w, const float* g, float* m, float* v, float lr, float b1,
+                             float b2, float eps, float wd, int step, cudaStream_t s);
+cudaError_t launch_to_bf16(const float* a, void* b, int n, cudaStream_t s);
+cudaError_t launch_features(const uint64_t* xz, int64_t n, int32_t q, uint64_t seed, int64_t samples,
+                            double log2_budget, unsigned long long* counts, float* feat, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t* out, int64_t n, int32_t v, cudaStream_t s);
 
 }  // namespace picasso

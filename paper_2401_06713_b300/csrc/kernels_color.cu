@@ -525,6 +525,42 @@ cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff
   return cudaGetLastError();
 }
 
+// Conflict-structure bytes of every set in this round, counted like the
+// byte budget: 8 (n_k + 1) row offsets + 4 per conflict entry + 4 per side
+// entry.  The round's vertices are in ascending global id, so set k owns the
+// rows [lower_bound(soff[k]), lower_bound(soff[k+1])) and, through loff, a
+// contiguous range of list entries whose run / side offsets give its counts.
+__device__ __forceinline__ int64_t lower_bound_gid(const int32_t* __restrict__ gid, int64_t n, int64_t g) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)gid[mid] < g)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_set_csr_bytes(const int64_t* __restrict__ loff, const int64_t* __restrict__ runoff,
+                                const int64_t* __restrict__ xoff, const int32_t* __restrict__ gid, int64_t n,
+                                const int64_t* __restrict__ soff, int nsets, int64_t* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nsets) return;
+  const int64_t a = gid ? lower_bound_gid(gid, n, soff[k]) : min(soff[k], n);
+  const int64_t b = gid ? lower_bound_gid(gid, n, soff[k + 1]) : min(soff[k + 1], n);
+  const int64_t ea = loff[a], eb = loff[b];
+  out[k] = b > a ? 8 * (b - a + 1) + 4 * (runoff[eb] - runoff[ea]) + 4 * (xoff[eb] - xoff[ea]) : 0;
+}
+
+cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int64_t* xoff, const int32_t* gid,
+                                 int64_t n, const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s) {
+  if (nsets <= 0) return cudaSuccess;
+  k_set_csr_bytes<<<(nsets + 127) / 128, 128, 0, s>>>(loff, runoff, xoff, gid, n, soff, nsets, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // Stable compaction of the flagged vertices (ascending global id is kept).
 __global__ void k_carry_gather(const uint32_t* __restrict__ flag, const int64_t* __restrict__ pos, int64_t n,
                                const int32_t* __restrict__ gid, const uint64_t* __restrict__ xz,

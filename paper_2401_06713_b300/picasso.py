@@ -118,13 +118,21 @@ _SIGS = {
     "picasso_trim_memory": [_i64],
     "picasso_run_small_static": [_vp, _i64, _i32, ctypes.POINTER(Config), _vp, _pi32, _vp],
     "picasso_destroy": [_vp],
+    "picasso_get_set_stats": [_vp, _pi64, _pi64, _pi64],
+    "picasso_features": [_vp, _i64, _i32, ctypes.c_uint64, _i64, ctypes.c_double, _vp, _vp, _vp],
+    "picasso_mlp_param_count": [],
+    "picasso_mlp_forward": [_vp, _vp, _i32, _vp, _vp],
+    "picasso_mlp_backward": [_vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _i32, _vp, _vp, _vp],
+    "picasso_mlp_adamw": [_vp, _vp, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, _i32, _vp],
+    "picasso_mlp_to_bf16": [_vp, _vp, _i32, _vp],
 }
 
 
 def header_symbols(path: str = HEADER):
     """Names of the functions include/picasso.h declares."""
     text = open(path).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(picasso_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int32_t|const char\*)\s+(picasso_\w+)\s*\(", text, re.M)))
 
 
 def _lib():
@@ -204,6 +212,7 @@ class Picasso:
         self.n = int(xz.shape[0])
         self.q = q
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.set_offsets = None if set_offsets is None else [int(x) for x in set_offsets]
         cfg = Config()
         _ck(_lib().picasso_config_default(ctypes.byref(cfg)), "picasso_config_default")
         cfg.seed = seed
@@ -315,6 +324,14 @@ class Picasso:
         _ck(_lib().picasso_copy_csr(self.h, _ptr(off), _ptr(col)), "picasso_copy_csr")
         return off, col[:nnz]
 
+    def set_stats(self):
+        """Per set: (colors used so far, peak conflict-structure bytes of one
+        round, uncolored vertices), three lists of ints."""
+        k = len(self.set_offsets) - 1 if self.set_offsets is not None else 1
+        c, b, r = (ctypes.c_int64 * k)(), (ctypes.c_int64 * k)(), (ctypes.c_int64 * k)()
+        _ck(_lib().picasso_get_set_stats(self.h, c, b, r), "picasso_get_set_stats")
+        return list(c), list(b), list(r)
+
     def runs(self):
         st = self.stats()
         n, L, nx = st["n_round"], st["L"], st["n_extra"]
@@ -353,3 +370,56 @@ def color_strings(codes: torch.Tensor, seed: int = 0, palette=(1, 8), alpha: flo
     with Picasso(xz, codes.shape[1], seed=seed, palette=palette, alpha=alpha, algo=algo) as p:
         colors, rounds = p.run()
         return colors, rounds, p.stats()
+
+
+def features(xz: torch.Tensor, q: int, seed: int, budget_bytes: float, samples: int = 1 << 16, stream=None):
+    """Regressor inputs of one set (Sec. V): (counts int64 [2], feat float32 [5])
+    on the GPU; see picasso_features."""
+    assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2
+    xz = xz.contiguous()
+    counts = torch.empty(2, dtype=torch.int64, device=xz.device)
+    feat = torch.empty(5, dtype=torch.float32, device=xz.device)
+    _ck(_lib().picasso_features(_ptr(xz), int(xz.shape[0]), q, seed, samples, float(budget_bytes), _ptr(counts),
+                                _ptr(feat), _stream(stream)), "picasso_features")
+    return counts, feat
+
+
+def mlp_param_count() -> int:
+    return int(_lib().picasso_mlp_param_count())
+
+
+def mlp_forward(w_bf16: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """y [B, 2] fp32 = MLP(bf16 weights, x [B, 5] fp32)."""
+    assert w_bf16.dtype == torch.bfloat16 and x.dtype == torch.float32 and x.shape[-1] == 5
+    x = x.contiguous()
+    B = int(x.shape[0])
+    if out is None:
+        out = torch.empty((B, 2), dtype=torch.float32, device=x.device)
+    _ck(_lib().picasso_mlp_forward(_ptr(w_bf16), _ptr(x), B, _ptr(out), _stream(stream)), "picasso_mlp_forward")
+    return out
+
+
+def mlp_backward(w_bf16: torch.Tensor, x: torch.Tensor, t: torch.Tensor, grad: torch.Tensor,
+                 loss: torch.Tensor | None = None, weights=(1.0, 1.0), stream=None):
+    """Gradient of the weighted half mean squared error into ``grad`` (fp32)."""
+    assert grad.dtype == torch.float32 and grad.numel() == w_bf16.numel()
+    x = x.contiguous()
+    t = t.contiguous()
+    _ck(_lib().picasso_mlp_backward(_ptr(w_bf16), _ptr(x), _ptr(t), float(weights[0]), float(weights[1]),
+                                    int(x.shape[0]), _ptr(grad), _ptr(loss) if loss is not None else None,
+                                    _stream(stream)), "picasso_mlp_backward")
+
+
+def mlp_adamw(master: torch.Tensor, w_bf16: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
+              step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+              weight_decay: float = 0.0, stream=None):
+    _ck(_lib().picasso_mlp_adamw(_ptr(master), _ptr(w_bf16), _ptr(grad), _ptr(m), _ptr(v), lr, beta1, beta2, eps,
+                                 weight_decay, step, _stream(stream)), "picasso_mlp_adamw")
+
+
+def mlp_to_bf16(src: torch.Tensor, dst: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    assert src.dtype == torch.float32
+    if dst is None:
+        dst = torch.empty(src.shape, dtype=torch.bfloat16, device=src.device)
+    _ck(_lib().picasso_mlp_to_bf16(_ptr(src), _ptr(dst), src.numel(), _stream(stream)), "picasso_mlp_to_bf16")
+    return dst
