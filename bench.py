@@ -238,14 +238,22 @@ def run_gpu(args):
     # POPC issues at 16 lanes/clk/SM
     peak_pairs = n_sm * sm_mhz * 1e6 * 16
     achieved = st["tested_pairs"] / (st["t_pairs_ms"] / 1e3)
-    roofline = {"bound": "alu", "kernel": "k_bucket_pairs (count+fill)", "achieved": achieved / 1e9,
+    roofline = {"bound": "alu", "kernel": "k_bucket_mask", "achieved": achieved / 1e9,
                 "peak": peak_pairs / 1e9, "unit": "Gpair-tests/s", "frac": achieved / peak_pairs,
                 "traffic": None,
                 "peak_source": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median under load) x 16 POPC/clk/SM",
                 "avg_launch_ms": st["t_pairs_ms"] / max(st["pairs_launches"], 1),
                 "tested_pairs_per_launch": st["tested_pairs"] / max(st["pairs_launches"], 1)}
 
+    # CSR emit pass: streams the mask words and writes the conflict CSR
+    emit_gbs = st["emit_bytes"] / (st["t_emit_ms"] / 1e3) / 1e9 if st["t_emit_ms"] > 0 else None
+    roofline_emit = {"bound": "hbm", "kernel": "k_bucket_emit", "achieved": emit_gbs,
+                     "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": emit_gbs / peaks["hbm_gbs"] if emit_gbs and peaks.get("hbm_gbs") else None,
+                     "bytes_per_step": st["emit_bytes"], "launches_per_step": st["emit_launches"]}
+
     batch = None if args.no_batch else bench_batch(rank)
+    learned_form = None if args.no_learned else bench_learned(rank)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -264,9 +272,10 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "u64/i32 (bitwise integer)",
         "data": "synthetic (seeded Pauli strings; the paper's molecules are not available)",
         "config": dict(workload(n), parallelism=f"replicas{world}" if world > 1 else "single"),
-        "pair_tests_per_s": pair_rate, "colors": int(len(np.unique(colors_np))), "rounds": rounds,
+        "pair_tests_per_s": pair_rate, "colors": int(len(np.unique(colors_np))),
+        "colors_sum_P": st["colors_used"], "rounds": rounds,
         "peak_bytes": st["peak_bytes"], "breakdown_ms_per_step": per_step,
-        "roofline": roofline, "cpu_baseline": cpu, "batch": batch,
+        "roofline": roofline, "roofline_emit": roofline_emit, "cpu_baseline": cpu, "batch": batch, "learned": learned_form,
         "e2e": {"value": world * n / (ms_e2e / args.steps / 1e3), "unit": "strings/s",
                 "h2d_bytes_per_step": n * Q, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": launches, "clocks": clocks, "wall_s": t_wall,
@@ -331,6 +340,50 @@ def bench_batch(rank, nsets=256):
                         f"P=n/8, alpha=2", "strings": offs[-1], "batched_ms": tb, "sequential_ms": ts,
             "batched_strings_per_s": offs[-1] / (tb / 1e3), "sequential_strings_per_s": offs[-1] / (ts / 1e3),
             "speedup": ts / tb, "identical_colors": same}
+
+
+def bench_learned(rank, count=16):
+    """The learned-parameter form on held-out n = 200,000, q = 56 sets, each
+    with its own byte budget: the committed regressor's pick (features, MLP
+    forward, budget-guarded runs, all library kernels) against the paper's
+    normal mode P/n = 1/8, alpha = 2 and the grid's best point."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2401_06713_b300 import learned, synth
+
+    reg = learned.Regressor.load()
+    specs = synth.learned_specs(count, 90001 + rank, n_lo=200000, n_hi=200000, qs=(56,))
+    rows = []
+    t_learned = 0.0
+    for i, spec in enumerate(specs):
+        xz, q, budget = learned.instance(spec)
+        seed = 7 * 10 ** 6 + i
+        grid = learned.grid_search(xz, q, seed, budget)
+        best = learned.best_of(grid)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d, a, c, b, tries = learned.run_learned(reg, xz, q, seed, budget)
+        torch.cuda.synchronize()
+        t_learned += time.perf_counter() - t0
+        dc, db, dok = learned.run_config(xz, q, seed, *learned.DEFAULT, None)
+        rows.append((grid[best][2], grid[best][0], c, dc, db <= budget, db / budget, tries))
+    fit = [r for r in rows if r[0]]
+    near = lambda x, best: x is not None and x <= 1.05 * best
+    return {"workload": f"{count} held-out sets, n=200000 q=56 p~U[0.1,0.5], budget n*2^U[9,15] bytes",
+            "grid_best_fits": len(fit),
+            "learned_fits": sum(1 for r in fit if r[2] is not None),
+            "learned_within_5pct_of_best": sum(1 for r in fit if near(r[2], r[1])),
+            "learned_mean_colors_over_best": float(np.mean([r[2] / r[1] for r in fit if r[2] is not None]))
+            if fit else None,
+            "default_fits": sum(1 for r in fit if r[4]),
+            "default_within_5pct_of_best": sum(1 for r in fit if r[4] and near(r[3], r[1])),
+            "default_mean_colors_over_best": float(np.mean([r[3] / r[1] for r in fit])) if fit else None,
+            "default_mean_peak_over_budget": float(np.mean([r[5] for r in rows])),
+            "learned_ms_per_set": 1e3 * t_learned / count,
+            "learned_mean_attempts": float(np.mean([r[6] for r in rows]))}
 
 
 def round_sizes_from(colors, st):
@@ -399,6 +452,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -75,8 +75,8 @@ typedef struct {
   double alpha;          /* L_l = min(P_l, max(1, ceil(alpha * ln n_l)))     */
   int32_t conflict_algo; /* picasso_conflict_algo                             */
   int32_t max_rounds;    /* picasso_run gives up with ERR_INTERNAL beyond it  */
-  int64_t byte_budget;   /* max bytes of one round's conflict CSR (off + col
-                            + the extras side list); 0 = no limit            */
+  int64_t byte_budget;   /* max bytes of one round's conflict CSR, 8 (n_l + 1)
+                            + 4 nnz; 0 = no limit                            */
   int32_t color_algo;    /* picasso_color_algo                                */
   int32_t reserved;
 } picasso_config;
@@ -90,9 +90,11 @@ typedef enum {
 /* Conflict CSR of the current round, owned by the context and valid until
  * the next assign/build/carry or destroy.  Ids are round-local: row r is the
  * r-th uncolored vertex in ascending global id.  Rows are color-major: row u
- * lists, for each color c of u's list in ascending order, the neighbours v
- * whose smallest shared color with u is c, ascending in v.  Every edge of
- * G_c appears exactly once per direction (nnz = 2|E_c|).                    */
+ * lists, for each color c of u's list in ascending order (its "run"), the
+ * neighbours v that also hold c, ascending in v.  An edge of G_c whose two
+ * lists share m colors appears in m runs of each of its rows, so nnz =
+ * 2 * sum over edges of m (2|E_c| when no pair shares two colors); the run
+ * of c is exactly what the coloring step needs to test color c.            */
 typedef struct {
   const int64_t* d_off; /* [n_rows + 1]                                      */
   const int32_t* d_col; /* [nnz]                                             */
@@ -108,8 +110,7 @@ typedef struct {
   int64_t P;           /* P_l of the last assign (batch: sum over the sets)  */
   int32_t L;           /* L_l of the last assign (batch: the largest)        */
   int64_t base;        /* base_l of the last assign (batch: of set 0)        */
-  int64_t nnz;         /* 2|E_c| of the last build                           */
-  int64_t n_extra;     /* entries of the multi-shared side list              */
+  int64_t nnz;         /* run entries of the last build (see picasso_csr)    */
   int64_t colored;     /* vertices colored by the last color step            */
   int64_t colors_used; /* base after the last carry = sum of P of done rounds */
   int64_t peak_bytes;  /* high-water mark of context-owned device memory      */
@@ -134,8 +135,8 @@ typedef struct {
   double t_emit_ms;           /* bucket join's emit pass (CSR writes)        */
   int64_t emit_launches;
   int64_t emit_bytes;         /* bytes the emit passes move: mask words read,
-                                 CSR and side list written, member ids and
-                                 run/side offsets read                      */
+                                 CSR written, member ids and run offsets
+                                 read                                       */
   /* the last color step's first 64 sweeps: vertices pending at the start,
    * vertices re-evaluated, and duration in microseconds (0 for the last) */
   int32_t sweep_pending[64];
@@ -214,24 +215,18 @@ int picasso_get_colors(void* ctx, int32_t* d_out);
 int picasso_get_round(void* ctx, int32_t* d_gid, int32_t* d_lists,
                       uint32_t* d_prio);
 
-/* Run structure of the last build: d_runoff [n_l*L + 1] int64 where run k of
- * row u is col[runoff[u*L+k] .. runoff[u*L+k+1]); and the multi-shared side
- * list: d_xoff [n_l*L + 1] int64, d_xcol [n_extra] int32 where entries
- * xoff[u*L+k] .. xoff[u*L+k+1] are the neighbours v of u that hold u's k-th
- * color although a smaller color is their smallest shared one (ascending
- * v).  Pointers are owned by the context.  Any output may be NULL.        */
-int picasso_get_runs(void* ctx, const int64_t** d_runoff,
-                     const int64_t** d_xoff, const int32_t** d_xcol,
-                     int64_t* n_extra);
+/* Run structure of the last build: d_runoff [E + 1] int64 (E = the round's
+ * list entries; with one list length L, entry u*L+k) where the run of row
+ * u's k-th color is col[runoff[e] .. runoff[e+1]).  Owned by the context.  */
+int picasso_get_runs(void* ctx, const int64_t** d_runoff);
 
 /* Copy the last build's CSR into caller-owned device buffers: d_off
  * [n_rows + 1] int64, d_col [nnz] int32 (either may be NULL).  Asynchronous. */
 int picasso_copy_csr(void* ctx, int64_t* d_off, int32_t* d_col);
 
-/* Copy the last build's run offsets and side list (layout as in
- * picasso_get_runs) into caller-owned buffers.  Asynchronous.             */
-int picasso_copy_runs(void* ctx, int64_t* d_runoff, int64_t* d_xoff,
-                      int32_t* d_xcol);
+/* Copy the last build's run offsets (layout as in picasso_get_runs) into a
+ * caller-owned buffer.  Asynchronous.                                      */
+int picasso_copy_runs(void* ctx, int64_t* d_runoff);
 
 int picasso_get_stats(void* ctx, picasso_stats* out);
 
@@ -240,13 +235,28 @@ int picasso_get_stats(void* ctx, picasso_stats* out);
  *   h_colors[k]     colors set k has used so far: the sum of its finished
  *                   rounds' palette sizes, the paper's count C = sum_l P_l
  *                   (Sec. III-C);
- *   h_peak_bytes[k] largest conflict structure set k had in one round so
- *                   far, counted like cfg.byte_budget: 8 (n_k + 1) + 4 nnz_k
- *                   + 4 n_extra_k bytes (row offsets, conflict entries in
- *                   both directions, side entries);
+ *   h_peak_bytes[k] largest conflict CSR set k had in one round so far,
+ *                   counted like cfg.byte_budget: 8 (n_k + 1) + 4 nnz_k
+ *                   bytes (row offsets, run entries);
  *   h_remaining[k]  set k's uncolored vertices.                            */
 int picasso_get_set_stats(void* ctx, int64_t* h_colors, int64_t* h_peak_bytes,
                           int64_t* h_remaining);
+
+/* Checkpoint of a context between rounds (after picasso_carry or before the
+ * first round): the round number, every string's color so far, the global
+ * ids of the uncolored strings and the per-set counters.  Lists, priorities
+ * and palettes are functions of (seed, round, global id), so a context that
+ * loads this state and runs on colors exactly as the uninterrupted one.
+ * picasso_save_state writes *bytes_out = the size; with h_buf == NULL that is
+ * all it does, with capacity < size it returns INVALID_ARG.  The buffer is
+ * host memory owned by the caller; the call synchronises the stream.
+ * picasso_load_state wants a fresh or between-round context over the same
+ * strings, sets, seeds and parameters (INVALID_ARG otherwise, with nothing
+ * changed); both return ERR_STATE in the middle of a round.  The paper has
+ * no counterpart.                                                          */
+int picasso_save_state(void* ctx, void* h_buf, int64_t capacity,
+                       int64_t* bytes_out);
+int picasso_load_state(void* ctx, const void* h_buf, int64_t bytes);
 
 /* ---- Parameter prediction (Sec. V) -------------------------------------
  * Sec. V predicts (P' = P/n, alpha) from instance features with a regressor
@@ -316,13 +326,13 @@ int picasso_kernel_launches(int64_t* out);
  * cudaMalloc while they work -- services that give the GPU's memory to their
  * own fixed pool, or hosts that forbid allocation on their hot path because it
  * synchronises the device.  Every temporary buffer lives in one library-owned
- * static device array of about 12.8 MB; once this function has run on a GPU,
+ * static device array of about 12.1 MB; once this function has run on a GPU,
  * that GPU holds the array until the process exits.
  *   d_xz        [n][2] packed strings (caller-owned, read-only)
  *   d_color_out [n] int32, receives the global colors (caller-owned)
  *   n_rounds    may be NULL
  * Limits: 1 <= n <= 2048, q <= 64, round-1 list size L <= 32, and at most
- * 1,572,864 conflict entries and 1,048,576 side-list entries in any round;
+ * 2,621,440 run entries in any round;
  * beyond them it returns PICASSO_ERR_UNSUPPORTED without touching the GPU
  * (the size checks of later rounds run after that round's count pass).
  * The first call on a device looks up the array's device address with that

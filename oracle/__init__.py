@@ -12,7 +12,8 @@ Function map (paper passage each follows):
   priority          static Random order of Sec. III-B
   commute_chars     Sec. III-A, character comparison (anticommute iff odd count)
   encode3/commute3  Sec. III-A, inverse one-hot code + AND + popcount parity
-  conflict_*        Alg. 1 construct_conflict_graph (color-major rows)
+  conflict_*        Alg. 1 construct_conflict_graph (color-major rows: per
+                    list color, the commuting vertices holding it)
   color_greedy      Sec. III-B static order, first available list color
   round_params      Table I / Sec. VI parameter rule
   run               Alg. 1, all rounds
@@ -88,9 +89,6 @@ def lib():
         L.orc_draw_lists_many.argtypes = [ctypes.c_uint64, ctypes.c_int32, _i64p, ctypes.c_int64, ctypes.c_int64,
                                           ctypes.c_int32, ctypes.c_int64, _i64p]
         L.orc_priorities_many.argtypes = [ctypes.c_uint64, ctypes.c_int32, _i64p, ctypes.c_int64, _u32p]
-        L.orc_side_row.argtypes = [ctypes.c_int64, ctypes.c_int64, _u32p, ctypes.c_int32, _i64p, ctypes.c_int32,
-                                   _i64p, _i32p]
-        L.orc_side_row.restype = ctypes.c_int64
         L.orc_round_params.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                        _i64p, _i32p]
         L.orc_run.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
@@ -215,25 +213,6 @@ def conflict_rows(enc: np.ndarray, lists: np.ndarray, rows, threads: int | None 
     lib().orc_conflict_rows(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(rows, _i64p), m, None,
                             _p(off, _i64p), _p(col, _i32p), threads)
     return lens[:m], [col[off[i]:off[i + 1]].copy() for i in range(m)]
-
-
-def side_rows(enc: np.ndarray, lists: np.ndarray, rows):
-    """Side-list rows of the given round-local vertices: list of int32 arrays
-    (k-major, ascending v) and per-row per-k lengths [m][L]."""
-    enc = np.ascontiguousarray(enc, dtype=np.uint32)
-    lists = np.ascontiguousarray(lists, dtype=np.int64)
-    n, w3 = enc.shape
-    L = lists.shape[1]
-    outs, lens = [], []
-    cnt = np.zeros(L + 2, dtype=np.int64)
-    for u in rows:
-        m = lib().orc_side_row(int(u), n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(cnt, _i64p), None)
-        per_k = cnt[1:L + 1].copy()
-        buf = np.zeros(max(m, 1), dtype=np.int32)
-        lib().orc_side_row(int(u), n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(cnt, _i64p), _p(buf, _i32p))
-        outs.append(buf[:m].copy())
-        lens.append(per_k)
-    return outs, np.array(lens, dtype=np.int64).reshape(len(outs), L)
 
 
 def color_greedy(seed: int, rnd: int, gids, lists, off, col, P: int, base: int) -> np.ndarray:

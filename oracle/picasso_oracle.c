@@ -29,9 +29,10 @@
  *     smallest list color not used by an already-colored conflict neighbour;
  *     unconflicted vertices therefore get their smallest list color;
  *   - conflict rows are stored "color-major": row u lists, for each color c
- *     of u's list in ascending order, the neighbours v whose smallest shared
- *     color with u is c, in ascending v.  Every edge appears once per
- *     direction.
+ *     of u's list in ascending order, the neighbours v that also hold c, in
+ *     ascending v; an edge whose lists share m colors appears in m runs of
+ *     each of its two rows (the coloring step tests color c against exactly
+ *     the run of c).
  *
  * Parity pins (what fixes this file against something other than itself) are
  * in the test-suite: Philox known-answer vectors, the 16-entry Pauli truth
@@ -223,39 +224,15 @@ int64_t orc_min_shared(const int64_t* a, const int64_t* b, int32_t L) {
 /* ------------------------------------------------------------------------ */
 
 /* One row in color-major order.  enc: [n][w3] codes of the round's vertices
- * (round-local ids), lists: [n][L] sorted global colors.  kv: scratch [n],
- * cnt: scratch [L+1].  Writes the row into out (may be NULL to count) and
- * returns its length.  Each other vertex v is tested once (commute, then the
- * smallest shared color); hits are then laid out by that color's index.    */
+ * (round-local ids), lists: [n][L] sorted global colors.  cnt: scratch
+ * [L+1].  Row u lists, for each color c_k of u's list (ascending k), every
+ * other vertex v that commutes with u and also holds c_k, ascending in v; a
+ * neighbour sharing m colors with u therefore appears in m of u's runs.
+ * Writes the row into out (may be NULL to count) and returns its length.
+ * The first pass counts per color index, the second lays the row out.     */
 int64_t orc_conflict_row(int64_t u, int64_t n, const uint32_t* enc, int32_t w3,
-                         const int64_t* lists, int32_t L, int32_t* kv,
-                         int64_t* cnt, int32_t* out) {
-  for (int32_t k = 0; k <= L; ++k) cnt[k] = 0;
-  int64_t len = 0;
-  for (int64_t v = 0; v < n; ++v) {
-    kv[v] = -1;
-    if (v == u) continue;
-    if (!orc_commute3(enc + u * w3, enc + v * w3, w3)) continue;
-    int32_t k = orc_min_shared_index(lists + u * L, lists + v * L, L);
-    if (k < 0) continue;
-    kv[v] = k;
-    cnt[k + 1]++;
-    ++len;
-  }
-  if (out) {
-    for (int32_t k = 0; k < L; ++k) cnt[k + 1] += cnt[k];
-    for (int64_t v = 0; v < n; ++v)
-      if (kv[v] >= 0) out[cnt[kv[v]]++] = (int32_t)v;
-  }
-  return len;
-}
-
-/* Side list of row u: for each color c_k of u's list (ascending k), the
- * neighbours v (commuting, v != u) that hold c_k although a smaller color is
- * their smallest shared one, ascending in v.  Same calling convention as
- * orc_conflict_row; cnt must hold L+1 entries.                              */
-int64_t orc_side_row(int64_t u, int64_t n, const uint32_t* enc, int32_t w3,
-                     const int64_t* lists, int32_t L, int64_t* cnt, int32_t* out) {
+                         const int64_t* lists, int32_t L, int64_t* cnt,
+                         int32_t* out) {
   for (int32_t k = 0; k <= L; ++k) cnt[k] = 0;
   int64_t len = 0;
   for (int pass = 0; pass < (out ? 2 : 1); ++pass) {
@@ -272,16 +249,14 @@ int64_t orc_side_row(int64_t u, int64_t n, const uint32_t* enc, int32_t w3,
       if (!orc_commute3(enc + u * w3, enc + v * w3, w3)) continue;
       const int64_t* a = lists + u * L;
       const int64_t* b = lists + v * L;
-      int32_t i = 0, j = 0, seen = 0;
+      int32_t i = 0, j = 0;
       while (i < L && j < L) {
         if (a[i] == b[j]) {
-          if (seen++) {
-            if (pass == 0) {
-              cnt[i + 1]++;
-              ++len;
-            } else {
-              out[cnt[i + 1]++] = (int32_t)v;
-            }
+          if (pass == 0) {
+            cnt[i + 1]++;
+            ++len;
+          } else {
+            out[cnt[i + 1]++] = (int32_t)v;
           }
           ++i;
           ++j;
@@ -310,15 +285,13 @@ typedef struct {
 
 static void* orc_rows_worker(void* arg) {
   orc_rows_job* j = (orc_rows_job*)arg;
-  int32_t* kv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(j->n + 1));
   int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)(j->L + 2));
   for (int64_t i = j->r0; i < j->r1; i += j->stride) {
     int64_t u = j->rows ? j->rows[i] : i;
     int32_t* dst = j->col ? j->col + j->off[i] : NULL;
-    int64_t len = orc_conflict_row(u, j->n, j->enc, j->w3, j->lists, j->L, kv, cnt, dst);
+    int64_t len = orc_conflict_row(u, j->n, j->enc, j->w3, j->lists, j->L, cnt, dst);
     if (j->lens) j->lens[i] = len;
   }
-  free(kv);
   free(cnt);
   return NULL;
 }

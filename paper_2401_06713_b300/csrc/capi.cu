@@ -97,13 +97,11 @@ struct Ctx {
   uint32_t* prio = nullptr;
   // build
   bool built = false;
-  int64_t nnz = 0, nx = 0, max_bucket = 0;
+  int64_t nnz = 0, max_bucket = 0;
   int32_t algo_used = 0;
   int64_t* off = nullptr;
   int32_t* col = nullptr;
   int64_t* runoff = nullptr;
-  int64_t* xoff = nullptr;
-  int32_t* xcol = nullptr;
   // color
   bool colored_done = false;
   int64_t n_colored = 0, n_remaining = 0;
@@ -194,10 +192,8 @@ void free_build(Ctx* c) {
   release(c, &c->off);
   release(c, &c->col);
   release(c, &c->runoff);
-  release(c, &c->xoff);
-  release(c, &c->xcol);
   c->built = false;
-  c->nnz = c->nx = 0;
+  c->nnz = 0;
 }
 
 void free_assign(Ctx* c) {
@@ -322,16 +318,15 @@ int build_conflicts(Ctx* c) {
   const int64_t n = c->n, P = c->Ptot, E = c->E;
   cudaStream_t s = c->s;
 
-  uint32_t *cnt = nullptr, *xcnt = nullptr, *bcount = nullptr, *bcursor = nullptr, *dmax = nullptr;
-  uint32_t *words = nullptr, *rmask = nullptr, *xmask = nullptr;
+  uint32_t *cnt = nullptr, *bcount = nullptr, *bcursor = nullptr, *dmax = nullptr;
+  uint32_t *words = nullptr, *rmask = nullptr;
   unsigned long long* dsq = nullptr;
-  int64_t *boff = nullptr, *moff = nullptr;
+  int64_t *boff = nullptr, *moff = nullptr, *jboff = nullptr;
   int32_t* bmem = nullptr;
   void* tmp = nullptr;
   int st = PICASSO_OK;
   auto cleanup = [&]() {
     release(c, &cnt);
-    release(c, &xcnt);
     release(c, &bcount);
     release(c, &bcursor);
     release(c, &dmax);
@@ -340,8 +335,8 @@ int build_conflicts(Ctx* c) {
     release(c, &bmem);
     release(c, &words);
     release(c, &moff);
+    release(c, &jboff);
     release(c, &rmask);
-    release(c, &xmask);
     release(c, (uint8_t**)&tmp);
   };
 #define TRY(expr)           \
@@ -366,7 +361,6 @@ int build_conflicts(Ctx* c) {
   const size_t tmp_bytes = scan_tmp_bytes(E > P ? E : P);
   TRY(alloc(c, (uint8_t**)&tmp, (int64_t)tmp_bytes));
   TRY(alloc(c, &cnt, E));
-  TRY(alloc(c, &xcnt, E));
   TRYC(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));
 
   int algo = c->cfg.conflict_algo;
@@ -403,7 +397,6 @@ int build_conflicts(Ctx* c) {
   a.loff = c->loff;
   a.ent_v = c->ent_v;
   a.cnt = cnt;
-  a.xcnt = xcnt;
   a.err = c->d_err;
 
   if (algo == PICASSO_CONFLICT_BUCKET) {
@@ -414,23 +407,25 @@ int build_conflicts(Ctx* c) {
     TRYC(launch_bucket_fill(c->lists, E, boff, bcursor, bmem, s));
     release(c, &bcursor);
     TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, s));
-    // mask words: bucket c holds s_c rows of ceil(s_c / 32) words
+    // mask words: bucket c holds nwb x nwb blocks of 32 words, nwb = ceil(s_c / 32)
     TRY(alloc(c, &words, P));
     TRY(alloc(c, &moff, P + 1));
     TRYC(launch_bucket_words(bcount, P, words, s));
     TRYC(launch_scan_u32(words, P, moff, tmp, s));
     TRYC(cudaMemcpyAsync(c->h_buf, moff + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    // emit work items: the 32-row blocks of every bucket
+    TRY(alloc(c, &jboff, P + 1));
+    TRYC(launch_bucket_jblocks(bcount, P, words, s));
+    TRYC(launch_scan_u32(words, P, jboff, tmp, s));
     TRYC(cudaStreamSynchronize(s));
     const int64_t nwords = c->h_buf[0];
     release(c, &words);
     TRY(alloc(c, &rmask, nwords));
-    TRY(alloc(c, &xmask, nwords));
     a.rmask = rmask;
-    a.xmask = xmask;
     TRYC(cudaEventRecord(c->ev[2], s));
-    TRYC(launch_bucket_mask(a, boff, bmem, moff, (int32_t)smax, s));
+    TRYC(launch_bucket_mask(a, boff, bmem, moff, (int32_t)smax, c->q, s));
     TRYC(cudaEventRecord(c->ev[3], s));
-    c->emit_bytes += 8 * nwords;  // the emit pass reads both words of every row chunk
+    c->emit_bytes += 4 * nwords;  // the emit pass reads every run word
   } else {
     TRYC(cudaEventRecord(c->ev[2], s));
     TRYC(launch_allpairs(a, false, s));
@@ -440,37 +435,29 @@ int build_conflicts(Ctx* c) {
   release(c, &bcount);
 
   TRY(alloc(c, &c->runoff, E + 1));
-  TRY(alloc(c, &c->xoff, E + 1));
   TRYC(launch_scan_u32(cnt, E, c->runoff, tmp, s));
-  TRYC(launch_scan_u32(xcnt, E, c->xoff, tmp, s));
   release(c, &cnt);
-  release(c, &xcnt);
   TRYC(cudaMemcpyAsync(c->h_buf, c->runoff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  TRYC(cudaMemcpyAsync(c->h_buf + 1, c->xoff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   TRYC(cudaMemcpyAsync(c->h_buf + 2, c->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
-  const int64_t nnz = c->h_buf[0], nx = c->h_buf[1];
+  const int64_t nnz = c->h_buf[0];
   if ((int32_t)c->h_buf[2] != 0) {
     cleanup();
     return PICASSO_ERR_INTERNAL;
   }
-  const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz + 4 * nx;
+  const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
   if (c->cfg.byte_budget > 0 && csr_bytes > c->cfg.byte_budget) {
     cleanup();
     release(c, &c->runoff);
-    release(c, &c->xoff);
     return PICASSO_ERR_BUDGET;
   }
   TRY(alloc(c, &c->off, n + 1));
   TRY(alloc(c, &c->col, nnz));
-  TRY(alloc(c, &c->xcol, nx));
   a.runoff = c->runoff;
-  a.xoff = c->xoff;
   a.col = c->col;
-  a.xcol = c->xcol;
   TRYC(cudaEventRecord(c->ev[4], s));
   if (algo == PICASSO_CONFLICT_BUCKET) {
-    TRYC(launch_bucket_emit(a, boff, bmem, moff, (int32_t)smax, s));
+    TRYC(launch_bucket_emit(a, boff, bmem, moff, jboff, c->d_err + 2, s));
   } else {
     TRYC(launch_allpairs(a, true, s));
   }
@@ -478,7 +465,7 @@ int build_conflicts(Ctx* c) {
   TRYC(launch_row_offsets(c->runoff, c->loff, n, c->off, s));
   if (c->nsets > 1) {
     std::vector<int64_t> h(c->nsets);
-    TRYC(launch_set_csr_bytes(c->loff, c->runoff, c->xoff, c->gid, n, c->d_soff, c->nsets, c->d_set_bytes, s));
+    TRYC(launch_set_csr_bytes(c->loff, c->runoff, c->gid, n, c->d_soff, c->nsets, c->d_set_bytes, s));
     TRYC(cudaMemcpyAsync(h.data(), c->d_set_bytes, sizeof(int64_t) * c->nsets, cudaMemcpyDeviceToHost, s));
     TRYC(cudaStreamSynchronize(s));
     for (int k = 0; k < c->nsets; ++k) c->set_peak_bytes[k] = std::max(c->set_peak_bytes[k], h[k]);
@@ -494,7 +481,7 @@ int build_conflicts(Ctx* c) {
     c->tested_pairs += tested / 2;
     c->t_emit += elapsed(c, 4, 5);
     c->emit_launches += 1;
-    c->emit_bytes += 4 * (nnz + nx) + 4 * E + 16 * E;  // CSR writes, member ids, run/side offsets
+    c->emit_bytes += 4 * nnz + 4 * E + 8 * E;  // CSR writes, member ids, run offsets
   } else {
     // the all-pairs kernel tests every ordered pair in both passes
     c->t_pairs += elapsed(c, 2, 3) + elapsed(c, 4, 5);
@@ -504,7 +491,6 @@ int build_conflicts(Ctx* c) {
   for (int k = 0; k < c->nsets; ++k) c->logical_pairs += c->remaining[k] * (c->remaining[k] - 1) / 2;
   cleanup();
   c->nnz = nnz;
-  c->nx = nx;
   c->built = true;
 #undef TRY
 #undef TRYC
@@ -574,8 +560,6 @@ int color_round(Ctx* c) {
   a.loff = c->loff;
   a.runoff = c->runoff;
   a.col = c->col;
-  a.xoff = c->xoff;
-  a.xcol = c->xcol;
   a.state = c->state;
   a.kcur = kcur;
   a.rcur = rcur;
@@ -902,15 +886,11 @@ int picasso_get_round(void* ctx, int32_t* d_gid, int32_t* d_lists, uint32_t* d_p
   return PICASSO_OK;
 }
 
-int picasso_get_runs(void* ctx, const int64_t** d_runoff, const int64_t** d_xoff, const int32_t** d_xcol,
-                     int64_t* n_extra) {
+int picasso_get_runs(void* ctx, const int64_t** d_runoff) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (!c->built) return PICASSO_ERR_STATE;
   if (d_runoff) *d_runoff = c->runoff;
-  if (d_xoff) *d_xoff = c->xoff;
-  if (d_xcol) *d_xcol = c->xcol;
-  if (n_extra) *n_extra = c->nx;
   return PICASSO_OK;
 }
 
@@ -924,15 +904,12 @@ int picasso_copy_csr(void* ctx, int64_t* d_off, int32_t* d_col) {
   return PICASSO_OK;
 }
 
-int picasso_copy_runs(void* ctx, int64_t* d_runoff, int64_t* d_xoff, int32_t* d_xcol) {
+int picasso_copy_runs(void* ctx, int64_t* d_runoff) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (!c->built) return PICASSO_ERR_STATE;
-  const int64_t ne = c->E + 1;
-  if (d_runoff) CK(cudaMemcpyAsync(d_runoff, c->runoff, sizeof(int64_t) * ne, cudaMemcpyDeviceToDevice, c->s));
-  if (d_xoff) CK(cudaMemcpyAsync(d_xoff, c->xoff, sizeof(int64_t) * ne, cudaMemcpyDeviceToDevice, c->s));
-  if (d_xcol && c->nx > 0)
-    CK(cudaMemcpyAsync(d_xcol, c->xcol, sizeof(int32_t) * c->nx, cudaMemcpyDeviceToDevice, c->s));
+  if (d_runoff)
+    CK(cudaMemcpyAsync(d_runoff, c->runoff, sizeof(int64_t) * (c->E + 1), cudaMemcpyDeviceToDevice, c->s));
   return PICASSO_OK;
 }
 
@@ -947,7 +924,6 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->L = c->Lmax;
   out->base = c->sets.empty() ? 0 : c->sets[0].base;
   out->nnz = c->nnz;
-  out->n_extra = c->nx;
   out->colored = c->n_colored;
   int64_t used = 0;
   for (int k = 0; k < c->nsets; ++k) used += c->set_base[k];
@@ -976,6 +952,133 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
     out->sweep_active[i] = c->sweep_log[8 + 3 * kSweepLog + i];
     out->sweep_us[i] = (float)((i + 1 < ns ? (double)(t[i + 1] - t[i]) : 0.0) / 1000.0);
   }
+  return PICASSO_OK;
+}
+
+// Between-round state: header, per-set arrays, the colors of all strings and
+// the global ids of the round's vertices.  Layout (little-endian, host):
+//   int64 magic, version, N, nsets, round, n, rounds_done, seed0, num, den
+//   double alpha
+//   int64 soff[nsets+1], seed[nsets], set_base[nsets], remaining[nsets],
+//         set_peak_bytes[nsets]
+//   int32 color[N], gid[n]
+namespace {
+constexpr int64_t kStateMagic = 0x5049434153534f31ll;  // "PICASSO1"
+
+int64_t state_bytes(const Ctx* c) {
+  return 8 * 10 + 8 + 8 * (int64_t)(c->nsets + 1) + 8 * 4 * (int64_t)c->nsets + 4 * c->N + 4 * c->n;
+}
+
+bool between_rounds(const Ctx* c) { return !c->assigned && !c->built && !c->colored_done; }
+}  // namespace
+
+int picasso_save_state(void* ctx, void* h_buf, int64_t capacity, int64_t* bytes_out) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (!bytes_out) return PICASSO_ERR_INVALID_ARG;
+  if (!between_rounds(c)) return PICASSO_ERR_STATE;
+  const int64_t need = state_bytes(c);
+  *bytes_out = need;
+  if (!h_buf) return PICASSO_OK;
+  if (capacity < need) return PICASSO_ERR_INVALID_ARG;
+  uint8_t* p = (uint8_t*)h_buf;
+  auto put64 = [&](int64_t v) { std::memcpy(p, &v, 8); p += 8; };
+  put64(kStateMagic);
+  put64(1);
+  put64(c->N);
+  put64(c->nsets);
+  put64(c->round);
+  put64(c->n);
+  put64(c->rounds_done);
+  put64((int64_t)c->cfg.seed);
+  put64(c->cfg.palette_num);
+  put64(c->cfg.palette_den);
+  std::memcpy(p, &c->cfg.alpha, 8);
+  p += 8;
+  for (int k = 0; k <= c->nsets; ++k) put64(c->soff[k]);
+  for (int k = 0; k < c->nsets; ++k) put64((int64_t)c->seed[k]);
+  for (int k = 0; k < c->nsets; ++k) put64(c->set_base[k]);
+  for (int k = 0; k < c->nsets; ++k) put64(c->remaining[k]);
+  for (int k = 0; k < c->nsets; ++k) put64(c->set_peak_bytes[k]);
+  CK(cudaMemcpyAsync(p, c->color, 4 * c->N, cudaMemcpyDeviceToHost, c->s));
+  p += 4 * c->N;
+  if (c->n > 0) {
+    if (c->gid) {
+      CK(cudaMemcpyAsync(p, c->gid, 4 * c->n, cudaMemcpyDeviceToHost, c->s));
+      CK(cudaStreamSynchronize(c->s));
+    } else {
+      CK(cudaStreamSynchronize(c->s));
+      int32_t* g = (int32_t*)p;
+      for (int64_t v = 0; v < c->n; ++v) g[v] = (int32_t)v;  // round 1: identity
+    }
+  } else {
+    CK(cudaStreamSynchronize(c->s));
+  }
+  return PICASSO_OK;
+}
+
+int picasso_load_state(void* ctx, const void* h_buf, int64_t bytes) {
+  Ctx* c = (Ctx*)ctx;
+  ST(check(c));
+  if (!h_buf || bytes < 8 * 11) return PICASSO_ERR_INVALID_ARG;
+  if (!between_rounds(c)) return PICASSO_ERR_STATE;
+  const uint8_t* p = (const uint8_t*)h_buf;
+  auto get64 = [&]() {
+    int64_t v;
+    std::memcpy(&v, p, 8);
+    p += 8;
+    return v;
+  };
+  const int64_t magic = get64(), version = get64(), N = get64(), nsets = get64(), round = get64(), n = get64(),
+                rounds_done = get64(), seed0 = get64(), num = get64(), den = get64();
+  double alpha;
+  std::memcpy(&alpha, p, 8);
+  p += 8;
+  if (magic != kStateMagic || version != 1 || N != c->N || nsets != c->nsets || (uint64_t)seed0 != c->cfg.seed ||
+      num != c->cfg.palette_num || den != c->cfg.palette_den || alpha != c->cfg.alpha || n < 0 || n > N ||
+      round < 1)
+    return PICASSO_ERR_INVALID_ARG;
+  const int64_t need = 8 * 10 + 8 + 8 * (nsets + 1) + 8 * 4 * nsets + 4 * N + 4 * n;
+  if (bytes < need) return PICASSO_ERR_INVALID_ARG;
+  for (int k = 0; k <= c->nsets; ++k)
+    if (get64() != c->soff[k]) return PICASSO_ERR_INVALID_ARG;
+  for (int k = 0; k < c->nsets; ++k)
+    if ((uint64_t)get64() != c->seed[k]) return PICASSO_ERR_INVALID_ARG;
+  std::vector<int64_t> base(c->nsets), rem(c->nsets), peak(c->nsets);
+  for (int k = 0; k < c->nsets; ++k) base[k] = get64();
+  for (int k = 0; k < c->nsets; ++k) rem[k] = get64();
+  for (int k = 0; k < c->nsets; ++k) peak[k] = get64();
+  int64_t rem_sum = 0;
+  for (int k = 0; k < c->nsets; ++k) rem_sum += rem[k];
+  if (rem_sum != n) return PICASSO_ERR_INVALID_ARG;
+  const int32_t* color = (const int32_t*)p;
+  const int32_t* gid = color + N;
+  for (int64_t v = 0; v < n; ++v)
+    if (gid[v] < 0 || gid[v] >= N || (v > 0 && gid[v] <= gid[v - 1])) return PICASSO_ERR_INVALID_ARG;
+  int32_t* gid2 = nullptr;
+  uint64_t* xz2 = nullptr;
+  if (n > 0) {
+    ST(alloc(c, &gid2, n));
+    int st = alloc(c, &xz2, 2 * n);
+    if (st != PICASSO_OK) {
+      release(c, &gid2);
+      return st;
+    }
+    CK(cudaMemcpyAsync(gid2, gid, 4 * n, cudaMemcpyHostToDevice, c->s));
+    CK(launch_gather_xz(c->xz_user, gid2, n, xz2, c->s));
+  }
+  CK(cudaMemcpyAsync(c->color, color, 4 * N, cudaMemcpyHostToDevice, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  release(c, &c->gid);
+  release(c, &c->xz);
+  c->gid = gid2;
+  c->xz = xz2;
+  c->round = (int32_t)round;
+  c->n = n;
+  c->rounds_done = (int32_t)rounds_done;
+  c->set_base = base;
+  c->remaining = rem;
+  c->set_peak_bytes = peak;
   return PICASSO_OK;
 }
 

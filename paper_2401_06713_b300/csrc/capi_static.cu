@@ -28,8 +28,7 @@ namespace {
 
 constexpr int64_t kStaticMaxN = 2048;
 constexpr int32_t kStaticMaxL = 32;
-constexpr int64_t kStaticMaxNnz = 1536 * 1024;      // conflict entries in one round
-constexpr int64_t kStaticMaxSide = 1024 * 1024;     // side-list entries in one round
+constexpr int64_t kStaticMaxNnz = 2560 * 1024;      // run entries in one round
 constexpr int64_t kStaticNL = kStaticMaxN * kStaticMaxL;
 constexpr size_t kScanTmpReserve = 64 * 1024;
 
@@ -41,12 +40,9 @@ constexpr size_t kOffXz = kOffGid + al(2 * kStaticMaxN * 4);               // 2 
 constexpr size_t kOffLists = kOffXz + al(2 * kStaticMaxN * 16);            // [N*L] int32
 constexpr size_t kOffPrio = kOffLists + al(kStaticNL * 4);                 // [N] u32
 constexpr size_t kOffCnt = kOffPrio + al(kStaticMaxN * 4);                 // [N*L] u32
-constexpr size_t kOffXcnt = kOffCnt + al(kStaticNL * 4);                   // [N*L] u32
-constexpr size_t kOffRunoff = kOffXcnt + al(kStaticNL * 4);                // [N*L+1] i64
-constexpr size_t kOffXoff = kOffRunoff + al((kStaticNL + 1) * 8);          // [N*L+1] i64
-constexpr size_t kOffCol = kOffXoff + al((kStaticNL + 1) * 8);             // [maxnnz] i32
-constexpr size_t kOffXcol = kOffCol + al(kStaticMaxNnz * 4);               // [maxside] i32
-constexpr size_t kOffState = kOffXcol + al(kStaticMaxSide * 4);            // [N] u64
+constexpr size_t kOffRunoff = kOffCnt + al(kStaticNL * 4);                 // [N*L+1] i64
+constexpr size_t kOffCol = kOffRunoff + al((kStaticNL + 1) * 8);           // [maxnnz] i32
+constexpr size_t kOffState = kOffCol + al(kStaticMaxNnz * 4);              // [N] u64
 constexpr size_t kOffRcur = kOffState + al(kStaticMaxN * 8);               // [N] u32
 constexpr size_t kOffBlk = kOffRcur + al(kStaticMaxN * 4);                 // [N] i32
 constexpr size_t kOffBlkw = kOffBlk + al(kStaticMaxN * 4);                 // [N] u32
@@ -64,7 +60,7 @@ constexpr size_t kOffEnt = kOffLoff + al((kStaticMaxN + 1) * 8);           // [N
 constexpr size_t kOffLen = kOffEnt + al(kStaticNL * 4);                    // [N] u32
 constexpr size_t kOffSoff = kOffLen + al(kStaticMaxN * 4);                 // [2] i64
 constexpr size_t kOffSet = kOffSoff + 256;                                 // [1] SetRound
-constexpr size_t kStaticBytes = kOffSet + 256;                             // about 12.8 MB
+constexpr size_t kStaticBytes = kOffSet + 256;                             // about 12.1 MB
 
 }  // namespace
 
@@ -148,11 +144,8 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
   int32_t* lists = (int32_t*)(base_ptr + kOffLists);
   uint32_t* prio = (uint32_t*)(base_ptr + kOffPrio);
   uint32_t* cnt = (uint32_t*)(base_ptr + kOffCnt);
-  uint32_t* xcnt = (uint32_t*)(base_ptr + kOffXcnt);
   int64_t* runoff = (int64_t*)(base_ptr + kOffRunoff);
-  int64_t* xoff = (int64_t*)(base_ptr + kOffXoff);
   int32_t* col = (int32_t*)(base_ptr + kOffCol);
-  int32_t* xcol = (int32_t*)(base_ptr + kOffXcol);
   uint64_t* state = (uint64_t*)(base_ptr + kOffState);
   uint32_t* rcur = (uint32_t*)(base_ptr + kOffRcur);
   int32_t* blk = (int32_t*)(base_ptr + kOffBlk);
@@ -215,22 +208,17 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
     a.loff = loff;
     a.ent_v = ent_v;
     a.cnt = cnt;
-    a.xcnt = xcnt;
     a.err = derr;
     SCK(launch_allpairs(a, false, s));
     SCK(launch_scan_u32(cnt, nl, runoff, tmp, s));
-    SCK(launch_scan_u32(xcnt, nl, xoff, tmp, s));
-    int64_t nnz = 0, nx = 0;
+    int64_t nnz = 0;
     {
       int st = read_i64(runoff + nl, &nnz, s);
-      if (st == PICASSO_OK) st = read_i64(xoff + nl, &nx, s);
       if (st != PICASSO_OK) return st;
     }
-    if (nnz > kStaticMaxNnz || nx > kStaticMaxSide) return PICASSO_ERR_UNSUPPORTED;
+    if (nnz > kStaticMaxNnz) return PICASSO_ERR_UNSUPPORTED;
     a.runoff = runoff;
-    a.xoff = xoff;
     a.col = col;
-    a.xcol = xcol;
     SCK(launch_allpairs(a, true, s));
 
     ColorArgs ca{};
@@ -239,8 +227,6 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
     ca.loff = loff;
     ca.runoff = runoff;
     ca.col = col;
-    ca.xoff = xoff;
-    ca.xcol = xcol;
     ca.state = state;
     ca.kcur = kcur;
     ca.rcur = rcur;

@@ -137,15 +137,10 @@ struct ConflictArgs {
   const int64_t* loff;   // [n+1]
   const int32_t* ent_v;  // [E] vertex of each list entry
   uint32_t* cnt;         // [E] run lengths          (count / mask pass)
-  uint32_t* xcnt;        // [E] side-list lengths    (count / mask pass)
   const int64_t* runoff; // [E+1]                    (fill / emit pass)
-  const int64_t* xoff;   // [E+1]                    (fill / emit pass)
   int32_t* col;          // [nnz]                    (fill / emit pass)
-  int32_t* xcol;         // [n_extra]                (fill / emit pass)
   int32_t* err;          // device error word
-  uint32_t* rmask;       // bucket join: run words      (mask pass -> emit)
-  uint32_t* xmask;       // bucket join: side-list words (mask pass -> emit)
-  int32_t smax;          // bucket join: largest bucket (emit pass)
+  uint32_t* rmask;       // bucket join: run words (mask pass -> emit)
 };
 
 // Buckets: members of color c are bmem[boff[c] .. boff[c+1]) ascending; a
@@ -162,9 +157,11 @@ cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out
 // mask pass (pair tests, counts, words), then the emit pass (CSR writes).
 cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, uint32_t* words, cudaStream_t s);
 cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
-                               const int64_t* moff, int32_t smax, cudaStream_t s);
+                               const int64_t* moff, int32_t smax, int32_t q, cudaStream_t s);
+cudaError_t launch_bucket_jblocks(const uint32_t* bcount, int64_t P, uint32_t* out, cudaStream_t s);
+// jboff [P+1]: prefix of ceil(s_c / 32); counter: one device int32 (reset here)
 cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
-                               const int64_t* moff, int32_t smax, cudaStream_t s);
+                               const int64_t* moff, const int64_t* jboff, int32_t* counter, cudaStream_t s);
 cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s);
 // off[u] = runoff[loff[u]], u <= n.
 cudaError_t launch_row_offsets(const int64_t* runoff, const int64_t* loff, int64_t n, int64_t* off,
@@ -177,8 +174,6 @@ struct ColorArgs {
   const int64_t* loff;
   const int64_t* runoff;
   const int32_t* col;
-  const int64_t* xoff;
-  const int32_t* xcol;
   uint64_t* state;  // [n] priority << 32 | state word
   uint16_t* kcur;   // [n] index of the current candidate in the list
   uint32_t* rcur;   // [n] resolved prefix of the current candidate's run
@@ -225,8 +220,8 @@ cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff
                               cudaStream_t s);
 cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t n, uint64_t* xz_out,
                              cudaStream_t s);
-cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int64_t* xoff, const int32_t* gid,
-                                 int64_t n, const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s);
+cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int32_t* gid, int64_t n,
+                                 const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s);
 cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s);
 
 // Parameter predictor and instance features (kernels_mlp.cu).

@@ -4,8 +4,8 @@
 // ascending (priority, round-local id) order each vertex takes the smallest
 // list color that no earlier conflict neighbour took.  The sweeps below
 // reproduce that sequential result in parallel.  A vertex v with candidate
-// c (its k-th list color) looks only at the earlier neighbours that hold c --
-// run k of its row plus side-list k -- and
+// c (its k-th list color) looks only at the earlier neighbours that hold c
+// (run k of its row) and
 //   * moves to its next list color as soon as one of them is colored c;
 //   * takes c once every one of them is colored differently, failed, or still
 //     undecided with a candidate above c (candidates only grow, so such a
@@ -139,7 +139,7 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
     bool blocked = false;
     int64_t first_wait = -1;
     int32_t wait_u = -1;
-    // the run of c: earlier neighbours whose smallest shared color is c
+    // the run of c: the neighbours that hold c
     for (int64_t e0 = rs + cur; e0 < r1; e0 += 32) {
       const int64_t e = e0 + lane;
       bool lb = false, lw = false;
@@ -165,36 +165,6 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
         const int src = __ffs(wm) - 1;
         first_wait = e0 + src;
         wait_u = __shfl_sync(0xffffffffu, u, src);
-      }
-    }
-    // side list of c: earlier neighbours holding c with a smaller shared color
-    if (!blocked) {
-      const int64_t x0 = a.xoff[row + k], x1 = a.xoff[row + k + 1];
-      for (int64_t e0 = x0; e0 < x1; e0 += 32) {
-        const int64_t e = e0 + lane;
-        bool lb = false, lw = false;
-        int32_t u = -1;
-        uint32_t wu = 0;
-        if (e < x1) {
-          u = a.xcol[e];
-          const uint64_t su = __ldcg(&a.state[u]);
-          const uint32_t pu = (uint32_t)(su >> 32);
-          if (pu < pv || (pu == pv && u < v)) {
-            wu = (uint32_t)su;
-            const uint32_t st = wu & 3u, cu = wu >> 2;
-            lb = st == kColored && cu == c;
-            lw = st == kUndecided && cu <= c;
-          }
-        }
-        if (__any_sync(0xffffffffu, lb)) {
-          blocked = true;
-          break;
-        }
-        const uint32_t wm = __ballot_sync(0xffffffffu, lw);
-        if (wm && wait_u < 0) {
-          const int src = __ffs(wm) - 1;
-          wait_u = __shfl_sync(0xffffffffu, u, src);
-        }
       }
     }
     if (blocked) {
@@ -332,18 +302,17 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
     const uint32_t c = (uint32_t)a.lists[row + k];
     if (k > 0 && lane == 0) publish(a.state, v, (c << 2) | kUndecided);
     const int64_t rs = a.runoff[row + k], r1 = a.runoff[row + k + 1];
-    const int64_t x0 = a.xoff[row + k], x1 = a.xoff[row + k + 1];
-    const int64_t nrun = r1 - rs, ntot = nrun + (x1 - x0);
+    const int64_t ntot = r1 - rs;
     bool blocked = false;
-    // entries of the run then of the side list, in chunks of 32; a chunk
-    // with an undecided earlier neighbour at or below c is rescanned after
-    // that neighbour moves
+    // the run of c (the neighbours holding c) in chunks of 32; a chunk with
+    // an undecided earlier neighbour at or below c is rescanned after that
+    // neighbour moves
     for (int64_t e0 = 0; e0 < ntot && !blocked;) {
       const int64_t e = e0 + lane;
       bool lb = false, lw = false;
       int32_t u = -1;
       if (e < ntot) {
-        u = e < nrun ? a.col[rs + e] : a.xcol[x0 + (e - nrun)];
+        u = a.col[rs + e];
         const uint64_t su = __ldcg(&a.state[u]);
         const uint32_t pu = (uint32_t)(su >> 32);
         if (pu < pv || (pu == pv && u < v)) {
@@ -526,10 +495,10 @@ cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff
 }
 
 // Conflict-structure bytes of every set in this round, counted like the
-// byte budget: 8 (n_k + 1) row offsets + 4 per conflict entry + 4 per side
-// entry.  The round's vertices are in ascending global id, so set k owns the
-// rows [lower_bound(soff[k]), lower_bound(soff[k+1])) and, through loff, a
-// contiguous range of list entries whose run / side offsets give its counts.
+// byte budget: 8 (n_k + 1) row offsets + 4 per run entry.  The round's
+// vertices are in ascending global id, so set k owns the rows
+// [lower_bound(soff[k]), lower_bound(soff[k+1])) and, through loff, a
+// contiguous range of list entries whose run offsets give its entries.
 __device__ __forceinline__ int64_t lower_bound_gid(const int32_t* __restrict__ gid, int64_t n, int64_t g) {
   int64_t lo = 0, hi = n;
   while (lo < hi) {
@@ -543,20 +512,19 @@ __device__ __forceinline__ int64_t lower_bound_gid(const int32_t* __restrict__ g
 }
 
 __global__ void k_set_csr_bytes(const int64_t* __restrict__ loff, const int64_t* __restrict__ runoff,
-                                const int64_t* __restrict__ xoff, const int32_t* __restrict__ gid, int64_t n,
-                                const int64_t* __restrict__ soff, int nsets, int64_t* __restrict__ out) {
+                                const int32_t* __restrict__ gid, int64_t n, const int64_t* __restrict__ soff,
+                                int nsets, int64_t* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nsets) return;
   const int64_t a = gid ? lower_bound_gid(gid, n, soff[k]) : min(soff[k], n);
   const int64_t b = gid ? lower_bound_gid(gid, n, soff[k + 1]) : min(soff[k + 1], n);
-  const int64_t ea = loff[a], eb = loff[b];
-  out[k] = b > a ? 8 * (b - a + 1) + 4 * (runoff[eb] - runoff[ea]) + 4 * (xoff[eb] - xoff[ea]) : 0;
+  out[k] = b > a ? 8 * (b - a + 1) + 4 * (runoff[loff[b]] - runoff[loff[a]]) : 0;
 }
 
-cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int64_t* xoff, const int32_t* gid,
-                                 int64_t n, const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s) {
+cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int32_t* gid, int64_t n,
+                                 const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s) {
   if (nsets <= 0) return cudaSuccess;
-  k_set_csr_bytes<<<(nsets + 127) / 128, 128, 0, s>>>(loff, runoff, xoff, gid, n, soff, nsets, out);
+  k_set_csr_bytes<<<(nsets + 127) / 128, 128, 0, s>>>(loff, runoff, gid, n, soff, nsets, out);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -3,22 +3,19 @@
 // G_c keeps a pair {u, v} of the round's vertices iff the two strings commute
 // (edge of the complement graph G', Sec. II) and their color lists intersect
 // (Sec. III-A).  Rows are color-major: row u holds, for each color c of u's
-// list in ascending order, the neighbours v whose smallest shared color with
-// u is c, ascending in v (one "run" per list color).  Pairs sharing more than
-// one color also go to a side list at each non-smallest shared color; the
-// coloring step uses runs and side list to find, per list color, exactly the
-// neighbours that hold it.
+// list in ascending order, the neighbours v that also hold c, ascending in v
+// (one "run" per list color).  A pair sharing m colors is listed in m runs of
+// each row; the coloring step reads run k to find exactly the neighbours
+// that hold the candidate color c_k.
 //
 // Both strategies below run a count pass (run lengths), an exclusive scan to
-// offsets, and a fill pass that recomputes every test and writes each run in
-// ascending order with warp ballots -- no atomics on output positions, so
-// the CSR is deterministic.
+// offsets, and a fill pass that writes each run in ascending order -- no
+// atomics on output positions, so the CSR is deterministic.
 //
 //   bucket join   one CTA per color c: the members of bucket c (vertices
 //                 holding c) are staged in shared memory and every pair of
-//                 members is tested there; a pair is a run entry at c iff c
-//                 is the pair's smallest shared color, found exactly through
-//                 a shared-memory hash of the members' smaller colors.
+//                 members is tested there; the commuting pairs of bucket c
+//                 are exactly run c of both rows.
 //   all pairs     one warp per row u sweeping every column v (the paper's GPU
 //                 kernel tests all |V|(|V|-1)/2 pairs, Sec. IV); the list
 //                 intersection is a two-pointer merge.
@@ -141,345 +138,234 @@ cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out
 
 // ---------------------------------------------------------------------------
 // Bucket join
+//
+// Inside a bucket the commutation relation of all member pairs is a GF(2)
+// bilinear form: bit(u, v) = parity(popc((x_u & z_v) ^ (z_u & x_v))) =
+// sum_k x_u[k] z_v[k] + z_u[k] x_v[k] mod 2.  It is evaluated 32 x 32 pairs
+// at a time by the "four Russians" method: for a block of 32 rows, the rows'
+// bits are transposed into 32-bit columns a_k (bit r = bit k of row r) and,
+// for every 4-bit chunk of the 128 (x|z) positions, the 16 XOR combinations
+// of the chunk's four columns go to a shared-memory table.  A partner v then
+// gets all 32 of its row bits with one table lookup per chunk, indexed by the
+// chunk's 4 bits of v's (z|x) words: 32 lookups and 16 XORs for 32 pairs,
+// where a direct test costs a POPC per pair.  The 16-entry tables sit in 16
+// consecutive banks, so the warp's lookups never conflict.
+//
+// Mask words are stored block-major: the word of member row r (block R = r/32)
+// for partners of block W is at base + (R * nwb + W) * 32 + (r % 32), so each
+// 32 x 32 block is one coalesced 128-byte line.
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kPairThreads = 512;
-constexpr int kExCap = 2048;  // exclusion pairs per bucket before the exact fallback
-
-struct BucketSmem {
-  uint64_t* sx;
-  uint64_t* sz;
-  int32_t* sid;   // member vertex
-  int32_t* sfl;   // member's list entry (bucket color's position)
-  uint16_t* kk;   // position of the bucket color in the member's list
-  int32_t* exo;   // [smax + 1]
-  int32_t* excur; // [smax]
-  int32_t* scnt;  // [smax] run counts
-  int32_t* sxcnt; // [smax] side-list counts
-  uint16_t* exv;  // [2 * kExCap]
-  uint32_t* expair;
-  uint32_t* tab;  // [hs]
-  int32_t* misc;  // [4]: E, nexcl, slow
-};
+constexpr int kMaskThreads = 256;
+constexpr int kMaskWarps = kMaskThreads / 32;
+constexpr int kTabWords = 32 * 16;  // one warp's tables: 32 chunks x 16 entries
+constexpr int kEmitThreads = 256;
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t bucket_smem_bytes(int smax, int hs) {
-  size_t b = 0;
-  b += align16(sizeof(uint64_t) * smax) * 2;
-  b += align16(sizeof(int32_t) * smax) * 2;
-  b += align16(sizeof(uint16_t) * smax);
-  b += align16(sizeof(int32_t) * (smax + 1));
-  b += align16(sizeof(int32_t) * smax);
-  b += align16(sizeof(int32_t) * smax) * 2;
-  b += align16(sizeof(uint16_t) * 2 * kExCap);
-  b += align16(sizeof(uint32_t) * kExCap);
-  b += align16(sizeof(uint32_t) * hs);
-  b += align16(sizeof(int32_t) * 4);
-  return b;
+__host__ __device__ inline size_t mask_smem_bytes(int smax) {
+  const int nwb = (smax + 31) >> 5;
+  return align16(sizeof(uint4) * smax) + align16(sizeof(int32_t) * smax) * 2 + 256 +
+         sizeof(uint32_t) * ((size_t)nwb * 128 + 64 + (size_t)kMaskWarps * kTabWords);
 }
 
-__device__ inline BucketSmem carve(uint8_t* p, int smax, int hs) {
-  BucketSmem m;
-  m.sx = (uint64_t*)p; p += align16(sizeof(uint64_t) * smax);
-  m.sz = (uint64_t*)p; p += align16(sizeof(uint64_t) * smax);
-  m.sid = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
-  m.sfl = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
-  m.kk = (uint16_t*)p; p += align16(sizeof(uint16_t) * smax);
-  m.exo = (int32_t*)p; p += align16(sizeof(int32_t) * (smax + 1));
-  m.excur = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
-  m.scnt = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
-  m.sxcnt = (int32_t*)p; p += align16(sizeof(int32_t) * smax);
-  m.exv = (uint16_t*)p; p += align16(sizeof(uint16_t) * 2 * kExCap);
-  m.expair = (uint32_t*)p; p += align16(sizeof(uint32_t) * kExCap);
-  m.tab = (uint32_t*)p; p += align16(sizeof(uint32_t) * hs);
-  m.misc = (int32_t*)p;
-  return m;
-}
-
-// Does a[0..ka) meet b[0..kb)?  (both ascending)
-__device__ inline bool share_prefix(const int32_t* __restrict__ a, int ka, const int32_t* __restrict__ b, int kb) {
-  int i = 0, j = 0;
-  while (i < ka && j < kb) {
-    const int32_t x = __ldg(a + i), y = __ldg(b + j);
-    if (x == y) return true;
-    if (x < y)
-      ++i;
-    else
-      ++j;
+// 32 x 32 bit transpose across the warp: on entry lane r holds row r (bit k =
+// M[r][k]); on exit lane k holds column k (bit r = M[r][k]).  Five butterfly
+// stages exchange ever smaller off-diagonal sub-blocks.
+__device__ __forceinline__ uint32_t transpose32(uint32_t w, int lane) {
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu : j == 2 ? 0x33333333u
+                                                                                                   : 0x55555555u;
+    const uint32_t t = __shfl_xor_sync(0xffffffffu, w, j);
+    w = (lane & j) ? ((w & ~m) | ((t >> j) & m)) : ((w & m) | ((t << j) & ~m));
   }
-  return false;
+  return w;
 }
 
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+template <int QW>
+__device__ __forceinline__ uint32_t word_of(const uint4& w, int g) {
+  // table word order: x_lo, [x_hi], z_lo, [z_hi]
+  if (QW == 2) return g == 0 ? w.x : g == 1 ? w.y : g == 2 ? w.z : w.w;
+  return g == 0 ? w.x : w.z;
+}
+
+// Build this warp's tables for one row block from the block's bit columns.
+template <int QW>
+__device__ __forceinline__ void build_tables(const uint32_t* __restrict__ colw, uint32_t* __restrict__ tab, int lane) {
+  constexpr int NG = 2 * QW;
+  __syncwarp();  // the warp's lookups in the old tables are done
+  if (lane < 8 * NG) {
+    const int g = lane >> 3, qn = lane & 7;
+    const uint4 a = *reinterpret_cast<const uint4*>(colw + g * 32 + 4 * qn);
+    const uint32_t t3 = a.x ^ a.y, t5 = a.z ^ a.x, t6 = a.z ^ a.y, t7 = a.z ^ t3;
+    uint4* o = reinterpret_cast<uint4*>(tab + lane * 16);
+    o[0] = make_uint4(0u, a.x, a.y, t3);
+    o[1] = make_uint4(a.z, t5, t6, t7);
+    o[2] = make_uint4(a.w, a.w ^ a.x, a.w ^ a.y, a.w ^ t3);
+    o[3] = make_uint4(a.w ^ a.z, a.w ^ t5, a.w ^ t6, a.w ^ t7);
+  }
+  __syncwarp();
+}
+
+// Anticommutation bits of partner words `cw` against the 32 rows whose
+// tables start at shared address tab_addr (bit r = row r).
+template <int QW>
+__device__ __forceinline__ uint32_t lookup(const uint4& cw, uint32_t tab_addr) {
+  constexpr int NG = 2 * QW;
+  uint32_t acc = 0u;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    // a row's x part meets the partner's z part and vice versa
+    const uint32_t idx = word_of<QW>(cw, (g + QW) % NG);
+    const uint32_t wl = (idx << 2) & 0x3C3C3C3Cu, wh = (idx >> 2) & 0x3C3C3C3Cu;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // table base | (nibble * 4) in the low byte, chunk offset added
+      const uint32_t lo = lds32(__byte_perm(wl, tab_addr, 0x7650u + k) + (uint32_t)((g * 8 + 2 * k) * 64));
+      const uint32_t hi = lds32(__byte_perm(wh, tab_addr, 0x7650u + k) + (uint32_t)((g * 8 + 2 * k + 1) * 64));
+      acc ^= lo ^ hi;
+    }
+  }
+  return acc;
+}
 
 }  // namespace
 
-// Mask pass over the pairs of a bucket, one 32 x 32 block (row chunk I,
-// partner chunk J >= I) per warp step.  Lane t tests partner J*32 + t
-// against each row of chunk I; the ballots give row words (partners of
-// chunk J), and a 32-ballot bit transpose gives the words of the rows of
-// chunk J for partners of chunk I -- every relation used (commutation,
-// sharing a smaller color, i != j) is symmetric, so each unordered pair is
-// tested once.  The run word keeps partners whose smallest shared color with
-// the row is this bucket's color; the side word keeps the others.  Words of
-// row i, chunk w live at masks + i * nwb + w; per-row counts accumulate in
-// shared memory.
-__device__ __forceinline__ uint32_t excl_bits(const BucketSmem& S, int i, int j0) {
-  uint32_t exm = 0u;
-  for (int e = S.exo[i], e1 = S.exo[i + 1]; e < e1; ++e) {
-    const uint32_t d = (uint32_t)S.exv[e] - (uint32_t)j0;
-    if (d < 32u) exm |= 1u << d;
-  }
-  return exm;
-}
-
-__device__ __forceinline__ void store_words(BucketSmem& S, int row, int s, int nwb, int w, uint32_t rm, uint32_t xm,
-                                            uint32_t* __restrict__ rmask, uint32_t* __restrict__ xmask) {
-  if (row < s) {
-    rmask[(int64_t)row * nwb + w] = rm;
-    xmask[(int64_t)row * nwb + w] = xm;
-    if (rm) atomicAdd(&S.scnt[row], __popc(rm));
-    if (xm) atomicAdd(&S.sxcnt[row], __popc(xm));
-  }
-}
-
-// The 32 rows of chunk I against this lane's partner j: ballot words, the
-// one for row I*32 + r kept by lane r.  DIAG: the block is on the diagonal
-// (J == I), so partner j may be the row itself.
-template <bool DIAG>
-__device__ __forceinline__ uint32_t block_rows(const BucketSmem& S, int s, int ib, int j, bool valid, int lane,
-                                               uint32_t xjl, uint32_t xjh, uint32_t zjl, uint32_t zjh) {
-  uint32_t my_m = 0u;
-#pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    const int i = ib + r;
-    const bool rowok = i < s;
-    uint64_t xi = 0ull, zi = 0ull;
-    if (rowok) {
-      xi = S.sx[i];
-      zi = S.sz[i];
-    }
-    const uint32_t t = (((uint32_t)xi & zjl) ^ ((uint32_t)zi & xjl)) ^
-                       (((uint32_t)(xi >> 32) & zjh) ^ ((uint32_t)(zi >> 32) & xjh));
-    bool hit = valid && rowok && (__popc(t) & 1) == 0;
-    if (DIAG) hit = hit && j != i;
-    const uint32_t m = __ballot_sync(0xffffffffu, hit);
-    my_m = lane == r ? m : my_m;
-  }
-  return my_m;
-}
-
-template <bool SLOW>
-__device__ void mask_blocks(const ConflictArgs& a, BucketSmem& S, int s, int L, int lane, int wid, int nw,
-                            uint32_t* __restrict__ rmask, uint32_t* __restrict__ xmask) {
-  const int nwb = (s + 31) >> 5;
-  const int nblk = nwb * (nwb + 1) / 2;
-  for (int q = wid; q < nblk; q += nw) {
-    // q -> (I, J), J >= I, row-major over the upper triangle
-    int I = 0, rem = q;
-    while (rem >= nwb - I) {
-      rem -= nwb - I;
-      ++I;
-    }
-    const int J = I + rem;
-    const int ib = I << 5;
-    const int j = (J << 5) + lane;
-    const bool valid = j < s;
-    const uint64_t xj = valid ? S.sx[j] : 0ull, zj = valid ? S.sz[j] : 0ull;
-    const uint32_t xjl = (uint32_t)xj, xjh = (uint32_t)(xj >> 32);
-    const uint32_t zjl = (uint32_t)zj, zjh = (uint32_t)(zj >> 32);
-    const uint32_t my_m = J == I ? block_rows<true>(S, s, ib, j, valid, lane, xjl, xjh, zjl, zjh)
-                                 : block_rows<false>(S, s, ib, j, valid, lane, xjl, xjh, zjl, zjh);
-    // partners of this lane's row that share a smaller color go to the side word
-    const int ir = ib + lane;
-    uint32_t myex = 0u;
-    if (!SLOW) {
-      if (ir < s && S.exo[ir + 1] > S.exo[ir]) myex = excl_bits(S, ir, J << 5) & my_m;
-    } else if (ir < s) {
-      for (uint32_t bits = my_m; bits; bits &= bits - 1) {
-        const int jj = (J << 5) + __ffs(bits) - 1;
-        if (share_prefix(a.lists + (S.sfl[ir] - S.kk[ir]), S.kk[ir], a.lists + (S.sfl[jj] - S.kk[jj]), S.kk[jj]))
-          myex |= bits & (0u - bits);
-      }
-    }
-    const uint32_t my_r = my_m & ~myex, my_x = myex;
-    store_words(S, ir, s, nwb, J, my_r, my_x, rmask, xmask);
-    if (J != I) {
-      uint32_t tr = 0u, tx = 0u;
-#pragma unroll
-      for (int b = 0; b < 32; ++b) {
-        const uint32_t cr = __ballot_sync(0xffffffffu, (my_r >> b) & 1u);
-        tr = lane == b ? cr : tr;
-      }
-      if (__any_sync(0xffffffffu, my_x != 0u)) {
-#pragma unroll
-        for (int b = 0; b < 32; ++b) {
-          const uint32_t cx = __ballot_sync(0xffffffffu, (my_x >> b) & 1u);
-          tx = lane == b ? cx : tx;
-        }
-      }
-      store_words(S, (J << 5) + lane, s, nwb, I, tr, tx, rmask, xmask);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kPairThreads, 2) k_bucket_mask(ConflictArgs a, const int64_t* __restrict__ boff,
+// Mask pass over one bucket per CTA iteration:
+//  1. the members' words to shared memory;
+//  2. bit columns of every 32-row block;
+//  3. the blocks (I, J >= I) of the upper triangle, split evenly over the
+//     warps: lane j of block (I, J) gets the word of row J*32+j against rows
+//     I*32.. (commuting, i != j); a warp transpose gives the words of rows
+//     I*32.. against partners J*32..; the relation is symmetric, so each
+//     unordered pair is tested once.
+// Per-row counts go to cnt at the member's list entry (the run of this
+// bucket's color in the member's row).
+template <int QW>
+__global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a, const int64_t* __restrict__ boff,
                                                               const int32_t* __restrict__ bmem,
-                                                              const int64_t* __restrict__ moff, int smax,
-                                                              int hs_log2) {
+                                                              const int64_t* __restrict__ moff, int smax) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  const int hs = 1 << hs_log2;
-  BucketSmem S = carve(smem_raw, smax, hs);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int L = a.Lmax;
+  uint8_t* p = smem_raw;
+  uint4* w4 = (uint4*)p;
+  p += align16(sizeof(uint4) * smax);
+  int32_t* sfl = (int32_t*)p;
+  p += align16(sizeof(int32_t) * smax);
+  int32_t* cnt = (int32_t*)p;
+  p += align16(sizeof(int32_t) * smax);
+  // 256-byte aligned region: bit columns, then per-warp tables (table bases
+  // need a zero low byte)
+  {
+    const uint32_t ad = (uint32_t)__cvta_generic_to_shared(p);
+    p += (256u - (ad & 255u)) & 255u;
+  }
+  uint32_t* colw = (uint32_t*)p;  // [nwb][2 QW][32]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
   for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
     const int64_t o = boff[b];
     const int s = (int)(boff[b + 1] - o);
     if (s == 0) continue;
-    if (threadIdx.x < 4) S.misc[threadIdx.x] = 0;
-    for (int i = threadIdx.x; i < s; i += blockDim.x) {
-      const int32_t flat = bmem[o + i];  // list entry of color b in member v's list
-      const int32_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
-      S.sid[i] = v;
-      S.sfl[i] = flat;
-      S.sx[i] = a.xz[2 * (int64_t)v];
-      S.sz[i] = a.xz[2 * (int64_t)v + 1];
-      S.kk[i] = (uint16_t)(flat - (a.Lu ? (int64_t)v * a.Lu : a.loff[v]));
-      S.excur[i] = 0;
-      S.scnt[i] = 0;
-      S.sxcnt[i] = 0;
+    for (int i = threadIdx.x; i < s; i += kMaskThreads) {
+      const int32_t flat = bmem[o + i];
+      const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
+      const uint64_t x = a.xz[2 * v], z = a.xz[2 * v + 1];
+      w4[i] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
+      sfl[i] = flat;
+      cnt[i] = 0;
     }
     __syncthreads();
-    // E = number of (member, smaller color) entries
-    {
-      int e = 0;
-      for (int i = threadIdx.x; i < s; i += blockDim.x) e += S.kk[i];
-      for (int d = 16; d; d >>= 1) e += __shfl_xor_sync(0xffffffffu, e, d);
-      if (lane == 0 && e) atomicAdd(&S.misc[0], e);
+    const int nwb = (s + 31) >> 5;
+    for (int I = wid; I < nwb; I += kMaskWarps) {
+      const int r = (I << 5) + lane;
+      const uint4 w = r < s ? w4[r] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int g = 0; g < 2 * QW; ++g) colw[(I * 2 * QW + g) * 32 + lane] = transpose32(word_of<QW>(w, g), lane);
     }
+    const uint32_t tab_off = ((uint32_t)(nwb * 2 * QW * 32) + 63u) & ~63u;  // words; 256-byte aligned
+    uint32_t* tab = colw + tab_off + wid * kTabWords;
+    const uint32_t tab_addr = (uint32_t)__cvta_generic_to_shared(tab);
     __syncthreads();
-    if (S.misc[0] * 10 > hs * 7) {
-      if (threadIdx.x == 0) S.misc[2] = 1;
-    } else if (S.misc[0] > 0) {
-      for (int i = threadIdx.x; i < hs; i += blockDim.x) S.tab[i] = 0u;
-      __syncthreads();
-      // Insert every smaller color of every member; an insert that passes an
-      // entry of the same color found a pair sharing that color.
-      // flattened over (member, list position) so that every thread's list
-      // load is independent and the block's loads overlap
-      for (int idx = threadIdx.x; idx < s * L; idx += blockDim.x) {
-        const int i = idx / L, t = idx - i * L;
-        if (t < S.kk[i]) {
-          const uint32_t c = (uint32_t)__ldg(a.lists + (int64_t)(S.sfl[i] - S.kk[i]) + t);
-          const uint32_t key = ((c + 1u) << 11) | (uint32_t)i;
-          uint32_t slot = (c * 0x9E3779B1u) >> (32 - hs_log2);
-          while (true) {
-            const uint32_t old = atomicCAS(&S.tab[slot], 0u, key);
-            if (old == 0u) break;
-            if ((old >> 11) == c + 1u) {
-              const int q = atomicAdd(&S.misc[1], 1);
-              if (q < kExCap)
-                S.expair[q] = ((old & 2047u) << 16) | (uint32_t)i;
-              else
-                S.misc[2] = 1;
-            }
-            slot = (slot + 1) & (hs - 1);
-          }
-        }
-      }
-    }
-    __syncthreads();
-    const bool slow = S.misc[2] != 0;
-    const int npairs = min(S.misc[1], kExCap);
-    if (!slow) {
-      // per-member exclusion lists (counting sort of the pairs by member)
-      for (int i = threadIdx.x; i <= s; i += blockDim.x) S.exo[i] = 0;
-      __syncthreads();
-      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-        atomicAdd(&S.exo[(S.expair[p] >> 16) + 1], 1);
-        atomicAdd(&S.exo[(S.expair[p] & 0xffffu) + 1], 1);
-      }
-      __syncthreads();
-      if (wid == 0) {
-        int carry = 0;
-        for (int i0 = 1; i0 <= s; i0 += 32) {
-          const int i = i0 + lane;
-          int x = i <= s ? S.exo[i] : 0;
-          for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d) x += y;
-          }
-          if (i <= s) S.exo[i] = x + carry;
-          carry += __shfl_sync(0xffffffffu, x, 31);
-        }
-      }
-      __syncthreads();
-      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-        const int i1 = S.expair[p] >> 16, i2 = S.expair[p] & 0xffff;
-        S.exv[S.exo[i1] + atomicAdd(&S.excur[i1], 1)] = (uint16_t)i2;
-        S.exv[S.exo[i2] + atomicAdd(&S.excur[i2], 1)] = (uint16_t)i1;
-      }
-      __syncthreads();
-      // ascending partners per member (lists are short: insertion sort)
-      for (int i = threadIdx.x; i < s; i += blockDim.x) {
-        uint16_t* e = S.exv + S.exo[i];
-        const int m = S.exo[i + 1] - S.exo[i];
-        for (int x = 1; x < m; ++x) {
-          const uint16_t key = e[x];
-          int y = x - 1;
-          while (y >= 0 && e[y] > key) {
-            e[y + 1] = e[y];
-            --y;
-          }
-          e[y + 1] = key;
-        }
-      }
-      __syncthreads();
-    }
 
-    if (slow)
-      mask_blocks<true>(a, S, s, L, lane, wid, nw, a.rmask + moff[b], a.xmask + moff[b]);
-    else
-      mask_blocks<false>(a, S, s, L, lane, wid, nw, a.rmask + moff[b], a.xmask + moff[b]);
-    __syncthreads();
-    for (int i = threadIdx.x; i < s; i += blockDim.x) {
-      const int64_t slot = S.sfl[i];
-      a.cnt[slot] = (uint32_t)S.scnt[i];
-      a.xcnt[slot] = (uint32_t)S.sxcnt[i];
+    uint32_t* rmb = a.rmask + moff[b];
+    const int nblk = nwb * (nwb + 1) / 2;
+    const int q0 = (int)((int64_t)nblk * wid / kMaskWarps), q1 = (int)((int64_t)nblk * (wid + 1) / kMaskWarps);
+    int I = 0, J = 0;
+    {
+      int rem = q0;
+      while (rem >= nwb - I) {
+        rem -= nwb - I;
+        ++I;
+      }
+      J = I + rem;
     }
+    int tab_I = -1;
+    for (int q = q0; q < q1; ++q) {
+      if (tab_I != I) {
+        build_tables<QW>(colw + I * 2 * QW * 32, tab, lane);
+        tab_I = I;
+      }
+      const int ib = I << 5;
+      const int j = (J << 5) + lane;
+      const bool jv = j < s;
+      const uint4 cwj = jv ? w4[j] : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t anti = lookup<QW>(cwj, tab_addr);
+      const uint32_t rows_ok = s - ib >= 32 ? 0xffffffffu : ((1u << (s - ib)) - 1u);
+      uint32_t cw = jv ? (~anti & rows_ok) : 0u;
+      if (I == J) cw &= ~(1u << lane);
+      rmb[(J * nwb + I) * 32 + lane] = cw;
+      if (cw) atomicAdd(&cnt[j], __popc(cw));
+      if (I != J) {
+        const uint32_t tr = transpose32(cw, lane);
+        rmb[(I * nwb + J) * 32 + lane] = tr;
+        if (tr) atomicAdd(&cnt[ib + lane], __popc(tr));
+      }
+      if (++J == nwb) {
+        ++I;
+        J = I;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
     __syncthreads();
   }
 }
 
 cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
-                               int32_t smax, cudaStream_t s) {
+                               int32_t smax, int32_t q, cudaStream_t s) {
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   smax = max(smax, 1);
-  int64_t want = (int64_t)smax * (int64_t)max(a.Lmax - 1, 1) * 3 / 2;
-  int hs_log2 = 8;
-  while ((1ll << hs_log2) < want && hs_log2 < 14) ++hs_log2;
-  const size_t bytes = bucket_smem_bytes(smax, 1 << hs_log2);
-  auto kern = k_bucket_mask;
+  const size_t bytes = mask_smem_bytes(smax);
+  auto kern = q <= 32 ? k_bucket_mask<1> : k_bucket_mask<2>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPairThreads, bytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMaskThreads, bytes);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
-  kern<<<(unsigned)blocks, kPairThreads, bytes, s>>>(a, boff, bmem, moff, smax, hs_log2);
+  kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, moff, smax);
   count_launches(1);
   return cudaGetLastError();
 }
 
-// Mask words of bucket c: s_c rows of ceil(s_c / 32) words.
+// Mask words of bucket c: nwb x nwb blocks of 32 words, nwb = ceil(s_c / 32).
 __global__ void k_bucket_words(const uint32_t* __restrict__ bcount, int64_t P, uint32_t* __restrict__ words) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < P) words[b] = bcount[b] * ((bcount[b] + 31u) >> 5);
+  if (b < P) {
+    const uint32_t nwb = (bcount[b] + 31u) >> 5;
+    words[b] = nwb * nwb * 32u;
+  }
 }
 
 cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, uint32_t* words, cudaStream_t s) {
@@ -489,98 +375,155 @@ cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, uint32_t* wor
   return cudaGetLastError();
 }
 
-// Emit pass: streaming compaction of the mask words into the CSR.  One warp
-// per member row; the run's entries are written in ascending partner order
-// (ballot positions within a word, words in ascending order).
-__global__ void __launch_bounds__(512) k_bucket_emit(ConflictArgs a, const int64_t* __restrict__ boff,
-                                                     const int32_t* __restrict__ bmem,
-                                                     const int64_t* __restrict__ moff) {
-  extern __shared__ __align__(16) int32_t emit_smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Row blocks of bucket c: nwb = ceil(s_c / 32) (the emit pass's work items).
+__global__ void k_bucket_jblocks(const uint32_t* __restrict__ bcount, int64_t P, uint32_t* __restrict__ out) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < P) out[b] = (bcount[b] + 31u) >> 5;
+}
+
+cudaError_t launch_bucket_jblocks(const uint32_t* bcount, int64_t P, uint32_t* out, cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  k_bucket_jblocks<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(bcount, P, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Emit pass: the mask words become CSR runs.  Work items are the 32-row
+// blocks of all buckets (jboff = prefix of ceil(s_c / 32)); every warp takes
+// items from a global counter, so no warp waits for another.  For an item the
+// warp stages the rows' words, 16 partner blocks at a time (one coalesced
+// 128-byte line each), and the partners' vertex ids in registers; it then
+// writes the rows one after the other: the partners of a row's word go to
+// consecutive positions (lane i writes partner i at the row's cursor plus the
+// set bits below i), so each run comes out in ascending partner order and is
+// written in one burst of stores.
+constexpr int kEmitChunk = 16;
+
+__global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, const int64_t* __restrict__ boff,
+                                                              const int32_t* __restrict__ bmem,
+                                                              const int64_t* __restrict__ moff,
+                                                              const int64_t* __restrict__ jboff,
+                                                              int32_t* __restrict__ counter) {
+  __shared__ int64_t rcur_s[kEmitThreads / 32][32];
+  __shared__ uint32_t wbuf_s[kEmitThreads / 32][kEmitChunk * 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
-  const int smax = a.smax;
-  int32_t* vid = emit_smem;          // [smax] member vertex ids
-  int32_t* flat = emit_smem + smax;  // [smax] member list entries
-  for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
+  int64_t* rcur = rcur_s[wid];
+  uint32_t* wbuf = wbuf_s[wid];
+  const int64_t items = jboff[a.P];
+  // flat / Lu as the high word of flat * ceil(2^64 / Lu): exact for flat < 2^32
+  const uint64_t invL = a.Lu > 1 ? ~0ull / (uint64_t)a.Lu + 1ull : 0ull;
+  while (true) {
+    int64_t item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= items) break;
+    // bucket of the item: the last b with jboff[b] <= item
+    int64_t lo = 0, hi = a.P - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (jboff[mid] <= item)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const int64_t b = lo;
+    const int J = (int)(item - jboff[b]);
     const int64_t o = boff[b];
     const int s = (int)(boff[b + 1] - o);
-    if (s == 0) continue;
-    for (int i = threadIdx.x; i < s; i += blockDim.x) {
-      const int32_t f = bmem[o + i];
-      flat[i] = f;
-      vid[i] = a.Lu ? f / a.Lu : a.ent_v[f];
-    }
-    __syncthreads();
     const int nwb = (s + 31) >> 5;
     const uint32_t* rmb = a.rmask + moff[b];
-    const uint32_t* xmb = a.xmask + moff[b];
-    for (int i = wid; i < s; i += nw) {
-      const int64_t slot = flat[i];
-      int32_t* rp = a.col + a.runoff[slot];
-      const int64_t x0 = a.xoff[slot], x1 = a.xoff[slot + 1];
-      const uint32_t* rrow = rmb + (int64_t)i * nwb;
-      for (int w0 = 0; w0 < nwb; w0 += 32) {
-        // each lane loads one word; the warp then walks them in order and
-        // writes each word's partners with one coalesced store
-        const int wl = w0 + lane;
-        const uint32_t rml = wl < nwb ? __ldg(rrow + wl) : 0u;
-        const int nwords = min(32, nwb - w0);
-#pragma unroll 4
-        for (int t = 0; t < nwords; ++t) {
-          const uint32_t rm = __shfl_sync(0xffffffffu, rml, t);
-          const int j = ((w0 + t) << 5) + lane;
-          if ((rm >> lane) & 1u) rp[__popc(rm & lt)] = vid[j];
-          rp += __popc(rm);
+    const int r = (J << 5) + lane;
+    if (r < s) rcur[lane] = a.runoff[bmem[o + r]];
+    const int nrows = min(32, s - (J << 5));
+    for (int I0 = 0; I0 < nwb; I0 += kEmitChunk) {
+      const int nI = min(kEmitChunk, nwb - I0);
+      int32_t pv[kEmitChunk];
+#pragma unroll
+      for (int t = 0; t < kEmitChunk; ++t) {
+        pv[t] = 0;
+        if (t < nI) {
+          wbuf[t * 32 + lane] = __ldg(rmb + (J * nwb + I0 + t) * 32 + lane);
+          const int pi = ((I0 + t) << 5) + lane;
+          if (pi < s) {
+            const int32_t f = __ldg(bmem + o + pi);
+            pv[t] = a.Lu > 1 ? (int32_t)__umul64hi((uint64_t)f, invL) : a.Lu == 1 ? f : __ldg(a.ent_v + f);
+          }
         }
       }
-      if (x1 > x0) {  // side-list entries are rare: only rows that have some
-        int32_t* xp = a.xcol + x0;
-        const uint32_t* xrow = xmb + (int64_t)i * nwb;
-        for (int w = 0; w < nwb; ++w) {
-          const uint32_t xm = __ldg(xrow + w);
-          const int j = (w << 5) + lane;
-          if ((xm >> lane) & 1u) xp[__popc(xm & lt)] = vid[j];
-          xp += __popc(xm);
+      __syncwarp();
+      for (int rr = 0; rr < nrows; ++rr) {
+        int32_t* dst = a.col + rcur[rr];
+        int32_t at = 0;
+#pragma unroll
+        for (int t = 0; t < kEmitChunk; ++t) {
+          if (t < nI) {
+            const uint32_t w = wbuf[t * 32 + rr];
+            if ((w >> lane) & 1u) dst[at + __popc(w & lt)] = pv[t];
+            at += __popc(w);
+          }
         }
+        __syncwarp();
+        if (lane == 0) rcur[rr] += at;
+        __syncwarp();
       }
     }
-    __syncthreads();
   }
 }
 
 cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
-                               int32_t smax, cudaStream_t s) {
+                               const int64_t* jboff, int32_t* counter, cudaStream_t s) {
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
-  const size_t bytes = 2 * sizeof(int32_t) * (size_t)max(smax, 1);
-  ConflictArgs args = a;
-  args.smax = max(smax, 1);
-  cudaError_t e = cudaFuncSetAttribute(k_bucket_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bucket_emit, kEmitThreads, 0);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * 4);
-  k_bucket_emit<<<(unsigned)blocks, 512, bytes, s>>>(args, boff, bmem, moff);
+  k_bucket_emit<<<(unsigned)(sms * max(per_sm, 1)), kEmitThreads, 0, s>>>(a, boff, bmem, moff, jboff, counter);
   count_launches(1);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// All pairs: warp per row, two-pointer list merge for commuting pairs.
+// All pairs: warp per row u, lanes over the columns v; a commuting v joins
+// u's run of every color the two lists share (two-pointer merge).
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kApWarps = 8;
+constexpr int kNoShare = 0x7fffffff;
+
+// Next shared color index of u's list (rl) and v's list (lv) at or after the
+// merge position (i, j); kNoShare when the lists have no further match.
+__device__ __forceinline__ int next_shared(const int32_t* __restrict__ rl, int Lu, const int32_t* __restrict__ lv,
+                                           int Lv, int& i, int& j) {
+  while (i < Lu && j < Lv) {
+    const int32_t x = rl[i], y = __ldg(lv + j);
+    if (x == y) {
+      const int k = i;
+      ++i;
+      ++j;
+      return k;
+    }
+    if (x < y)
+      ++i;
+    else
+      ++j;
+  }
+  return kNoShare;
 }
+}  // namespace
 
 template <bool FILL>
 __global__ void __launch_bounds__(kApWarps * 32) k_allpairs(ConflictArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int Lm = a.Lmax;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // per warp: row list [Lmax] int32, run counters/cursors [Lmax] int64, side [Lmax] int64
+  // per warp: row list [Lmax] int32, run counters / cursors [Lmax] int64
   int32_t* rl = (int32_t*)smem_raw + (size_t)wid * Lm;
-  int64_t* cur = (int64_t*)(smem_raw + align16(sizeof(int32_t) * Lm * kApWarps)) + (size_t)wid * 2 * Lm;
-  int64_t* xcur = cur + Lm;
+  int64_t* cur = (int64_t*)(smem_raw + ((sizeof(int32_t) * Lm * kApWarps + 15) & ~(size_t)15)) + (size_t)wid * Lm;
   const uint32_t lt = lanemask_lt();
   for (int64_t u = (int64_t)blockIdx.x * kApWarps + wid; u < a.n; u += (int64_t)gridDim.x * kApWarps) {
     const int64_t ru = a.loff[u];
@@ -588,90 +531,49 @@ __global__ void __launch_bounds__(kApWarps * 32) k_allpairs(ConflictArgs a) {
     for (int t = lane; t < Lu; t += 32) {
       rl[t] = a.lists[ru + t];
       cur[t] = FILL ? a.runoff[ru + t] : 0;
-      xcur[t] = FILL ? a.xoff[ru + t] : 0;
     }
     __syncwarp();
     const uint64_t xu = a.xz[2 * u], zu = a.xz[2 * u + 1];
     for (int64_t v0 = 0; v0 < a.n; v0 += 32) {
       const int64_t v = v0 + lane;
-      int k0 = -1, nshared = 0;
+      const int32_t* lv = nullptr;
+      int Lv = 0, i = 0, j = 0, k = kNoShare;
       if (v < a.n && v != u && commute1(xu, zu, a.xz[2 * v], a.xz[2 * v + 1])) {
-        const int32_t* lv = a.lists + a.loff[v];
-        const int Lv = (int)(a.loff[v + 1] - a.loff[v]);
-        int i = 0, j = 0;
-        while (i < Lu && j < Lv) {
-          const int32_t x = rl[i], y = __ldg(lv + j);
-          if (x == y) {
-            if (k0 < 0) {
-              k0 = i;
-            } else if (!FILL) {
-              atomicAdd((unsigned long long*)&xcur[i], 1ull);
-            }
-            ++nshared;
-            ++i;
-            ++j;
-          } else if (x < y) {
-            ++i;
-          } else {
-            ++j;
-          }
-        }
+        lv = a.lists + a.loff[v];
+        Lv = (int)(a.loff[v + 1] - a.loff[v]);
+        k = next_shared(rl, Lu, lv, Lv, i, j);
       }
       if (!FILL) {
-        if (k0 >= 0) atomicAdd((unsigned long long*)&cur[k0], 1ull);
-      } else {
-        // run entries: lanes with the same run write in lane (= v) order
-        const uint32_t act = __ballot_sync(0xffffffffu, k0 >= 0);
-        if (act) {
-          const uint32_t grp = __match_any_sync(0xffffffffu, k0);
-          if (k0 >= 0) {
-            const int64_t pos = cur[k0] + __popc(grp & lt);
-            a.col[pos] = (int32_t)v;
-          }
-          __syncwarp();
-          if (k0 >= 0 && (grp & lt) == 0u) cur[k0] += __popc(grp);
-          __syncwarp();
+        while (k != kNoShare) {
+          atomicAdd((unsigned long long*)&cur[k], 1ull);
+          k = next_shared(rl, Lu, lv, Lv, i, j);
         }
-        // side-list entries, one lane at a time in lane order
-        uint32_t more = __ballot_sync(0xffffffffu, nshared > 1);
-        while (more) {
-          const int l = __ffs(more) - 1;
-          more &= more - 1;
-          if (lane == l) {
-            const int32_t* lv = a.lists + a.loff[v];
-            const int Lv = (int)(a.loff[v + 1] - a.loff[v]);
-            int i = 0, j = 0, seen = 0;
-            while (i < Lu && j < Lv) {
-              const int32_t x = rl[i], y = __ldg(lv + j);
-              if (x == y) {
-                if (seen++) a.xcol[xcur[i]++] = (int32_t)v;
-                ++i;
-                ++j;
-              } else if (x < y) {
-                ++i;
-              } else {
-                ++j;
-              }
-            }
-          }
+      } else {
+        // runs in ascending color index; inside a run, lanes (= ascending v)
+        // write in order
+        while (true) {
+          const int kmin = __reduce_min_sync(0xffffffffu, k);
+          if (kmin == kNoShare) break;
+          const bool mine = k == kmin;
+          const uint32_t m = __ballot_sync(0xffffffffu, mine);
+          if (mine) a.col[cur[kmin] + __popc(m & lt)] = (int32_t)v;
           __syncwarp();
+          if (lane == 0) cur[kmin] += __popc(m);
+          __syncwarp();
+          if (mine) k = next_shared(rl, Lu, lv, Lv, i, j);
         }
       }
     }
     __syncwarp();
-    if (!FILL) {
-      for (int t = lane; t < Lu; t += 32) {
-        a.cnt[ru + t] = (uint32_t)cur[t];
-        a.xcnt[ru + t] = (uint32_t)xcur[t];
-      }
-    }
+    if (!FILL)
+      for (int t = lane; t < Lu; t += 32) a.cnt[ru + t] = (uint32_t)cur[t];
     __syncwarp();
   }
 }
 
 cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const size_t bytes = align16(sizeof(int32_t) * a.Lmax * kApWarps) + sizeof(int64_t) * 2 * a.Lmax * kApWarps;
+  const size_t bytes = ((sizeof(int32_t) * a.Lmax * kApWarps + 15) & ~(size_t)15) + sizeof(int64_t) * a.Lmax * kApWarps;
   auto kern = fill ? k_allpairs<true> : k_allpairs<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;

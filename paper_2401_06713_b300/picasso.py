@@ -54,7 +54,6 @@ class Stats(ctypes.Structure):
         ("L", ctypes.c_int32),
         ("base", ctypes.c_int64),
         ("nnz", ctypes.c_int64),
-        ("n_extra", ctypes.c_int64),
         ("colored", ctypes.c_int64),
         ("colors_used", ctypes.c_int64),
         ("peak_bytes", ctypes.c_int64),
@@ -109,9 +108,9 @@ _SIGS = {
     "picasso_run": [_vp, _vp, _pi32],
     "picasso_get_colors": [_vp, _vp],
     "picasso_get_round": [_vp, _vp, _vp, _vp],
-    "picasso_get_runs": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _pi64],
+    "picasso_get_runs": [_vp, ctypes.POINTER(_vp)],
     "picasso_copy_csr": [_vp, _vp, _vp],
-    "picasso_copy_runs": [_vp, _vp, _vp, _vp],
+    "picasso_copy_runs": [_vp, _vp],
     "picasso_get_stats": [_vp, ctypes.POINTER(Stats)],
     "picasso_philox_draws": [ctypes.c_uint64, _i32, _i64, ctypes.c_uint32, ctypes.c_uint32, _i32, _vp, _vp],
     "picasso_kernel_launches": [_pi64],
@@ -119,6 +118,8 @@ _SIGS = {
     "picasso_run_small_static": [_vp, _i64, _i32, ctypes.POINTER(Config), _vp, _pi32, _vp],
     "picasso_destroy": [_vp],
     "picasso_get_set_stats": [_vp, _pi64, _pi64, _pi64],
+    "picasso_save_state": [_vp, _vp, _i64, _pi64],
+    "picasso_load_state": [_vp, _vp, _i64],
     "picasso_features": [_vp, _i64, _i32, ctypes.c_uint64, _i64, ctypes.c_double, _vp, _vp, _vp],
     "picasso_mlp_param_count": [],
     "picasso_mlp_forward": [_vp, _vp, _i32, _vp, _vp],
@@ -332,15 +333,26 @@ class Picasso:
         _ck(_lib().picasso_get_set_stats(self.h, c, b, r), "picasso_get_set_stats")
         return list(c), list(b), list(r)
 
+    def save_state(self) -> bytes:
+        """Between-round checkpoint (host bytes)."""
+        need = ctypes.c_int64()
+        _ck(_lib().picasso_save_state(self.h, None, 0, ctypes.byref(need)), "picasso_save_state")
+        buf = ctypes.create_string_buffer(int(need.value))
+        _ck(_lib().picasso_save_state(self.h, buf, need.value, ctypes.byref(need)), "picasso_save_state")
+        return buf.raw[:need.value]
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _ck(_lib().picasso_load_state(self.h, buf, len(blob)), "picasso_load_state")
+
     def runs(self):
+        """Run offsets of the last build: int64 [E + 1] (run of list entry e is
+        col[runoff[e]:runoff[e+1]])."""
         st = self.stats()
-        n, L, nx = st["n_round"], st["L"], st["n_extra"]
-        dev = self.xz.device
-        runoff = torch.empty(n * L + 1, dtype=torch.int64, device=dev)
-        xoff = torch.empty(n * L + 1, dtype=torch.int64, device=dev)
-        xcol = torch.empty(max(nx, 1), dtype=torch.int32, device=dev)
-        _ck(_lib().picasso_copy_runs(self.h, _ptr(runoff), _ptr(xoff), _ptr(xcol)), "picasso_copy_runs")
-        return runoff, xoff, xcol[:nx]
+        n, L = st["n_round"], st["L"]
+        runoff = torch.empty(n * L + 1, dtype=torch.int64, device=self.xz.device)
+        _ck(_lib().picasso_copy_runs(self.h, _ptr(runoff)), "picasso_copy_runs")
+        return runoff
 
 
 def run_small_static(xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,

@@ -191,7 +191,7 @@ def test_set_stats_peak_is_max_round_structure(pc):
             p.assign_lists(P, L, base)
             p.build_conflicts()
             st = p.stats()
-            want = max(want, 8 * (st["n_round"] + 1) + 4 * st["nnz"] + 4 * st["n_extra"])
+            want = max(want, 8 * (st["n_round"] + 1) + 4 * st["nnz"])
             p.color()
             if p.carry() == 0:
                 break

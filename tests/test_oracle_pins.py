@@ -8,7 +8,8 @@ Each test fixes one part of the oracle against an independent source:
   * Floyd's list sampling: uniformity over all L-subsets (chi-square) and exact
     support;
   * the conflict graph: brute force over characters and Python sets, and the
-    closed-form expected size (Lemma 2 / list-intersection probability);
+    closed-form expected sizes (shared-color count L^2 / P per pair and the
+    list-intersection probability);
   * the coloring: L = P reduces the round to plain greedy coloring in the
     priority order (networkx.greedy_color), P >> n L^2 gives no conflicts,
     P = L = 1 gives a greedy maximal independent set, plus validity of a whole
@@ -153,23 +154,20 @@ def test_round_params_workloads(orc):
 
 # ---------------------------------------------------------------- conflict graph
 def _brute_rows(chars, lists):
+    """Row u: for each color of u's list in list order, the other vertices that
+    commute with u (character rule) and hold that color, ascending."""
     n = len(chars)
     rows = []
     for u in range(n):
-        by_k = [[] for _ in range(lists.shape[1])]
-        su = set(lists[u].tolist())
-        for v in range(n):
-            if v == u:
-                continue
-            cnt = sum(1 for a, b in zip(chars[u], chars[v]) if a and b and a != b)
-            if cnt % 2:
-                continue
-            shared = su & set(lists[v].tolist())
-            if not shared:
-                continue
-            k = list(lists[u]).index(min(shared))
-            by_k[k].append(v)
-        rows.append([v for grp in by_k for v in grp])
+        row = []
+        for c in lists[u].tolist():
+            for v in range(n):
+                if v == u or c not in set(lists[v].tolist()):
+                    continue
+                cnt = sum(1 for a, b in zip(chars[u], chars[v]) if a and b and a != b)
+                if cnt % 2 == 0:
+                    row.append(v)
+        rows.append(row)
     return rows
 
 
@@ -197,20 +195,33 @@ def test_conflict_rows_match_csr(orc):
 
 
 def test_conflict_symmetric(orc):
+    # (u, v) at color c iff (v, u) at color c; a pair appears once per shared color
     chars = synth.pauli_uniform(400, 20, seed=5)
     lists = orc.draw_lists(0, 1, np.arange(400), 50, 16)
     off, col = orc.conflict_csr(orc.encode3(chars), lists)
-    pairs = set()
+    triples = set()
     for u in range(400):
-        for v in col[off[u]:off[u + 1]]:
-            pairs.add((u, int(v)))
-    assert all((v, u) in pairs for (u, v) in pairs)
-    assert len(pairs) == len(col)
+        seg = col[off[u]:off[u + 1]].tolist()
+        per_color = [[] for _ in range(16)]
+        k, at = 0, 0
+        # runs are in list order; split the row by membership
+        for v in seg:
+            while lists[u][k] not in set(lists[v].tolist()) or (per_color[k] and per_color[k][-1] >= v):
+                k += 1
+            per_color[k].append(v)
+        for k in range(16):
+            for v in per_color[k]:
+                triples.add((u, v, int(lists[u][k])))
+    assert all((v, u, c) in triples for (u, v, c) in triples)
+    assert len(triples) == len(col)
 
 
 def test_conflict_count_closed_form(orc):
-    # E|E_c| = (#commuting pairs) * (1 - C(P-L, L) / C(P, L)) for lists that
-    # are uniform L-subsets (Sec. IV analysis: each edge is kept iff lists meet).
+    # Two uniform L-subsets of a P-palette share L^2 / P colors on average
+    # (each of u's L colors lies in v's list w.p. L/P), so the expected number
+    # of (pair, shared color) entries is 2 * (#commuting pairs) * L^2 / P, and
+    # the expected number of distinct conflict pairs is (#commuting pairs) *
+    # (1 - C(P-L, L) / C(P, L)) (Sec. III-C: an edge is kept iff lists meet).
     n, q, P, L = 2000, 20, 250, 16
     chars = synth.pauli_uniform(n, q, seed=0)
     enc = orc.encode3(chars)
@@ -220,16 +231,15 @@ def test_conflict_count_closed_form(orc):
     anti = (x @ z.T + z @ x.T) % 2
     n_comm = (int((anti == 0).sum()) - n) // 2
     p_meet = 1.0 - math.comb(P - L, L) / math.comb(P, L)
-    totals = []
     for seed in range(3):
         lists = orc.draw_lists(seed, 1, np.arange(n), P, L)
         off, col = orc.conflict_csr(enc, lists)
-        totals.append(len(col) // 2)
-    mean = n_comm * p_meet
-    sigma = math.sqrt(n_comm * p_meet * (1 - p_meet))
-    # edges sharing a vertex are positively correlated: allow a wide band
-    for t in totals:
-        assert abs(t - mean) < 8 * sigma, (t, mean, sigma)
+        entries = len(col) // 2
+        mean = n_comm * L * L / P
+        assert abs(entries - mean) < 0.03 * mean, (entries, mean)
+        distinct = sum(len(set(col[off[u]:off[u + 1]].tolist())) for u in range(n)) // 2
+        mean_d = n_comm * p_meet
+        assert abs(distinct - mean_d) < 0.03 * mean_d, (distinct, mean_d)
 
 
 # ---------------------------------------------------------------- coloring
