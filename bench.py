@@ -30,6 +30,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_DEFAULT, Q, P_W, NUM, DEN, ALPHA = 1_000_000, 64, 0.25, 1, 16, 1.5
+# DRAM bytes (read + write) per unit of work, from one ncu capture of each kernel on
+# round 1 of the n = 200,000 case of this workload (the bench's launches are too
+# large to capture); scaled here by the units each launch processes.
+MASK_DRAM_BYTES_PER_PAIR = 0.2415   # k_bucket_mask, per tested pair
+EMIT_DRAM_BYTES_PER_ENTRY = 5.03    # k_bucket_emit, per CSR run entry
 METRIC = "pair tests/s (conflict build) and colored strings/s at n=1M; colors, peak bytes"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -238,9 +243,11 @@ def run_gpu(args):
     # POPC issues at 16 lanes/clk/SM
     peak_pairs = n_sm * sm_mhz * 1e6 * 16
     achieved = st["tested_pairs"] / (st["t_pairs_ms"] / 1e3)
+    tested_per_launch = st["tested_pairs"] / max(st["pairs_launches"], 1)
     roofline = {"bound": "alu", "kernel": "k_bucket_mask", "achieved": achieved / 1e9,
                 "peak": peak_pairs / 1e9, "unit": "Gpair-tests/s", "frac": achieved / peak_pairs,
-                "traffic": None,
+                "traffic": MASK_DRAM_BYTES_PER_PAIR * tested_per_launch,
+                "traffic_note": "bytes per launch, scaled from an ncu capture of round 1 at n=200000",
                 "peak_source": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median under load) x 16 POPC/clk/SM",
                 "avg_launch_ms": st["t_pairs_ms"] / max(st["pairs_launches"], 1),
                 "tested_pairs_per_launch": st["tested_pairs"] / max(st["pairs_launches"], 1)}
@@ -250,7 +257,9 @@ def run_gpu(args):
     roofline_emit = {"bound": "hbm", "kernel": "k_bucket_emit", "achieved": emit_gbs,
                      "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                      "frac": emit_gbs / peaks["hbm_gbs"] if emit_gbs and peaks.get("hbm_gbs") else None,
-                     "bytes_per_step": st["emit_bytes"], "launches_per_step": st["emit_launches"]}
+                     "bytes_per_step": st["emit_bytes"], "launches_per_step": st["emit_launches"],
+                     "traffic": EMIT_DRAM_BYTES_PER_ENTRY * st["nnz_total"] / max(st["emit_launches"], 1)
+                     if "nnz_total" in st else None}
 
     batch = None if args.no_batch else bench_batch(rank)
     learned_form = None if args.no_learned else bench_learned(rank)

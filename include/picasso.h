@@ -137,6 +137,7 @@ typedef struct {
   int64_t emit_bytes;         /* bytes the emit passes move: mask words read,
                                  CSR written, member ids and run offsets
                                  read                                       */
+  int64_t nnz_total;          /* run entries of all builds                  */
   /* the last color step's first 64 sweeps: vertices pending at the start,
    * vertices re-evaluated, and duration in microseconds (0 for the last) */
   int32_t sweep_pending[64];

@@ -124,6 +124,7 @@ struct Ctx {
   int32_t rounds_done = 0;
   double t_assign = 0, t_build = 0, t_color = 0, t_carry = 0, t_pairs = 0, t_emit = 0;
   int64_t pairs_launches = 0, logical_pairs = 0, tested_pairs = 0, emit_launches = 0, emit_bytes = 0;
+  int64_t nnz_total = 0;
 
   const uint64_t* round_xz() const { return xz ? xz : xz_user; }
 };
@@ -491,6 +492,7 @@ int build_conflicts(Ctx* c) {
   for (int k = 0; k < c->nsets; ++k) c->logical_pairs += c->remaining[k] * (c->remaining[k] - 1) / 2;
   cleanup();
   c->nnz = nnz;
+  c->nnz_total += nnz;
   c->built = true;
 #undef TRY
 #undef TRYC
@@ -945,6 +947,7 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->t_emit_ms = c->t_emit;
   out->emit_launches = c->emit_launches;
   out->emit_bytes = c->emit_bytes;
+  out->nnz_total = c->nnz_total;
   const int ns = c->sweeps < kSweepLog ? c->sweeps : kSweepLog;
   const unsigned long long* t = reinterpret_cast<const unsigned long long*>(c->sweep_log + 8 + kSweepLog);
   for (int i = 0; i < ns; ++i) {

@@ -73,6 +73,7 @@ class Stats(ctypes.Structure):
         ("t_emit_ms", ctypes.c_double),
         ("emit_launches", ctypes.c_int64),
         ("emit_bytes", ctypes.c_int64),
+        ("nnz_total", ctypes.c_int64),
         ("sweep_pending", ctypes.c_int32 * 64),
         ("sweep_active", ctypes.c_int32 * 64),
         ("sweep_us", ctypes.c_float * 64),
