@@ -61,7 +61,10 @@ typedef enum {
   PICASSO_ERR_STATE = 8        /* call out of order for the context's state  */
 } picasso_status;
 
-/* Conflict-graph construction strategy.  Both produce the same CSR. */
+/* Conflict-graph construction strategy.  Both produce the same CSR.  AUTO
+ * tests all pairs in rounds of at most 2,048 vertices and otherwise joins
+ * through buckets, unless a bucket exceeds 2,048 members or the round has
+ * 2^21 or more colors.                                                      */
 typedef enum {
   PICASSO_CONFLICT_AUTO = 0,
   PICASSO_CONFLICT_ALLPAIRS = 1, /* every pair tested (the paper's GPU kernel) */
@@ -117,7 +120,7 @@ typedef struct {
   int32_t conflict_algo_used;
   int32_t jp_sweeps;   /* sweeps of the last color step (0: ordered pass)    */
   int32_t ordered_fallbacks; /* rounds whose ordered pass gave up (sweeps ran) */
-  int64_t max_bucket;  /* largest color bucket of the last build             */
+  int64_t max_bucket;  /* largest color bucket of the last build (0: all pairs) */
   /* cumulative since picasso_init (CUDA events on the context's stream) */
   int32_t rounds_done;
   double t_assign_ms;   /* list assignment                                   */

@@ -294,13 +294,20 @@ int assign_round(Ctx* c) {
     release(c, &len);
     return st;
   }
-  cudaError_t e = launch_list_offsets(c->gid, n, c->d_soff, c->nsets, c->d_sets, len, c->loff, tmp, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_buf, c->loff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaError_t e = cudaSuccess;
+  if (c->nsets == 1) {
+    // one list length: loff[v] = v L, no scan and no readback
+    e = launch_strided_offsets(c->loff, n, Lmax, s);
+    c->E = n * (int64_t)Lmax;
+  } else {
+    e = launch_list_offsets(c->gid, n, c->d_soff, c->nsets, c->d_sets, len, c->loff, tmp, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_buf, c->loff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) c->E = c->h_buf[0];
+  }
   release(c, &len);
   release(c, (uint8_t**)&tmp);
   CK(e);
-  c->E = c->h_buf[0];
   // with one list length (a single set) owners follow from e / L
   c->Lu = c->nsets == 1 ? Lmax : 0;
   ST(alloc(c, &c->lists, c->E));
@@ -365,26 +372,31 @@ int build_conflicts(Ctx* c) {
   TRYC(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), s));
 
   int algo = c->cfg.conflict_algo;
-  // color buckets: sizes, offsets, largest bucket
-  TRY(alloc(c, &bcount, P));
-  TRY(alloc(c, &boff, P + 1));
-  TRY(alloc(c, &dmax, 2));
-  TRY(alloc(c, &dsq, 1));
-  TRYC(cudaMemsetAsync(bcount, 0, sizeof(uint32_t) * P, s));
-  TRYC(launch_bucket_hist(c->lists, E, bcount, s));
-  TRYC(launch_bucket_stats(bcount, P, dmax, dsq, s));
-  TRYC(cudaMemcpyAsync(c->h_buf, dmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  TRYC(cudaMemcpyAsync(c->h_buf + 1, dsq, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  TRYC(cudaStreamSynchronize(s));
-  const int64_t smax = (int64_t)(*(uint32_t*)c->h_buf);
-  const int64_t bucket_pairs = c->h_buf[1];
-  c->max_bucket = smax;
-  const bool bucket_ok = smax <= kBucketCap && P < kBucketMaxP && E < (int64_t(1) << 31);
-  if (algo == PICASSO_CONFLICT_AUTO) algo = bucket_ok ? PICASSO_CONFLICT_BUCKET : PICASSO_CONFLICT_ALLPAIRS;
-  if (algo == PICASSO_CONFLICT_BUCKET && !bucket_ok) {
-    cleanup();
-    return PICASSO_ERR_UNSUPPORTED;
+  // small rounds: testing all n (n-1) pairs costs less than building buckets
+  if (algo == PICASSO_CONFLICT_AUTO && n <= kSmallRoundAllPairs) algo = PICASSO_CONFLICT_ALLPAIRS;
+  int64_t smax = 0, bucket_pairs = 0;
+  if (algo != PICASSO_CONFLICT_ALLPAIRS) {
+    // color buckets: sizes, offsets, largest bucket
+    TRY(alloc(c, &bcount, P));
+    TRY(alloc(c, &boff, P + 1));
+    TRY(alloc(c, &dmax, 2));
+    TRY(alloc(c, &dsq, 1));
+    TRYC(cudaMemsetAsync(bcount, 0, sizeof(uint32_t) * P, s));
+    TRYC(launch_bucket_hist(c->lists, E, bcount, s));
+    TRYC(launch_bucket_stats(bcount, P, dmax, dsq, s));
+    TRYC(cudaMemcpyAsync(c->h_buf, dmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    TRYC(cudaMemcpyAsync(c->h_buf + 1, dsq, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    TRYC(cudaStreamSynchronize(s));
+    smax = (int64_t)(*(uint32_t*)c->h_buf);
+    bucket_pairs = c->h_buf[1];
+    const bool bucket_ok = smax <= kBucketCap && P < kBucketMaxP && E < (int64_t(1) << 31);
+    if (algo == PICASSO_CONFLICT_AUTO) algo = bucket_ok ? PICASSO_CONFLICT_BUCKET : PICASSO_CONFLICT_ALLPAIRS;
+    if (algo == PICASSO_CONFLICT_BUCKET && !bucket_ok) {
+      cleanup();
+      return PICASSO_ERR_UNSUPPORTED;
+    }
   }
+  c->max_bucket = smax;
   c->algo_used = algo;
 
   ConflictArgs a{};
@@ -407,7 +419,7 @@ int build_conflicts(Ctx* c) {
     TRYC(cudaMemsetAsync(bcursor, 0, sizeof(uint32_t) * P, s));
     TRYC(launch_bucket_fill(c->lists, E, boff, bcursor, bmem, s));
     release(c, &bcursor);
-    TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, s));
+    TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, (int32_t)smax, s));
     // mask words: bucket c holds nwb x nwb blocks of 32 words, nwb = ceil(s_c / 32)
     TRY(alloc(c, &words, P));
     TRY(alloc(c, &moff, P + 1));
@@ -568,7 +580,17 @@ int color_round(Ctx* c) {
   a.blk = blk;
   a.blkw = blkw;
   // Ordered persistent pass; if one of its bounded waits runs out (ctl[5]),
-  // recolor the round with the sweep kernel from a fresh state.
+  // recolor the round with the sweep kernel from a fresh state.  The colors,
+  // the carry flags and their prefix sum are enqueued behind the pass, so one
+  // synchronisation reads both the pass's status and the uncolored count.
+  TRY(alloc(c, &c->flag, n));
+  TRY(alloc(c, &c->pos, n + 1));
+  auto enqueue_carry = [&]() -> cudaError_t {
+    cudaError_t e = launch_carry_flags(c->state, n, c->gid, c->d_soff, c->nsets, c->d_sets, c->color, c->flag, s);
+    if (e == cudaSuccess) e = launch_scan_u32(c->flag, n, c->pos, tmp, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_buf, c->pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    return e;
+  };
   TRYC(cudaMemsetAsync(ctl, 0, sizeof(int32_t) * kCtlWords, s));
   TRYC(launch_prio_order(c->prio, n, nbins, hist, hoff, tmp, wa, s));
   TRYC(launch_color_init(a, c->prio, ctl, s));
@@ -577,6 +599,7 @@ int color_round(Ctx* c) {
   if (!need_sweeps) {
     TRYC(launch_color_ordered(a, wa, ctl + 5, s));
     TRYC(cudaMemcpyAsync(c->sweep_log, ctl, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s));
+    TRYC(enqueue_carry());
     TRYC(cudaStreamSynchronize(s));
     need_sweeps = c->sweep_log[5] != 0;
     c->ordered_fallbacks += need_sweeps ? 1 : 0;
@@ -586,6 +609,7 @@ int color_round(Ctx* c) {
     TRYC(launch_color_init(a, c->prio, ctl, s));
     TRYC(launch_color_all(a, wa, wb, wact, ctl, s));
     TRYC(cudaMemcpyAsync(c->sweep_log, ctl, sizeof(int32_t) * kCtlWords, cudaMemcpyDeviceToHost, s));
+    TRYC(enqueue_carry());
     TRYC(cudaStreamSynchronize(s));
     sweeps = c->sweep_log[3];
     if (c->sweep_log[4] != 0 || c->sweep_log[0] != 0) {
@@ -594,13 +618,6 @@ int color_round(Ctx* c) {
     }
   }
   c->sweeps = sweeps;
-  // colors to the output; flags + positions of the uncolored
-  TRY(alloc(c, &c->flag, n));
-  TRY(alloc(c, &c->pos, n + 1));
-  TRYC(launch_carry_flags(c->state, n, c->gid, c->d_soff, c->nsets, c->d_sets, c->color, c->flag, s));
-  TRYC(launch_scan_u32(c->flag, n, c->pos, tmp, s));
-  TRYC(cudaMemcpyAsync(c->h_buf, c->pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  TRYC(cudaStreamSynchronize(s));
   c->n_remaining = c->h_buf[0];
   c->n_colored = n - c->n_remaining;
   c->colored_done = true;

@@ -22,6 +22,7 @@ constexpr uint32_t kTagPrio = 2u;
 constexpr int kMaxL = 512;           // longest list a round may draw
 constexpr int kBucketCap = 2048;     // largest color bucket of the bucket join
 constexpr int kBucketMaxP = 1 << 21; // bucket colors of one round (bucket join)
+constexpr int64_t kSmallRoundAllPairs = 2048;  // AUTO tests all pairs at or below this n
 constexpr uint32_t kFailedColor = 0x3FFFFFFFu;
 
 // Vertex state word of the coloring: bits 31..2 a bucket color, bits 1..0 the
@@ -113,6 +114,8 @@ cudaError_t launch_philox_draws(uint64_t seed, int32_t round, int64_t gid, uint3
 cudaError_t launch_list_offsets(const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
                                 const SetRound* sets, uint32_t* len, int64_t* loff, void* tmp, cudaStream_t s);
 // ent_v[e] = vertex owning list entry e.
+// loff[v] = v L for v <= n (every vertex has L entries)
+cudaError_t launch_strided_offsets(int64_t* loff, int64_t n, int32_t L, cudaStream_t s);
 cudaError_t launch_entry_owner(const int64_t* loff, int64_t n, int32_t* ent_v, cudaStream_t s);
 // Alg. 1 list assignment: lists[loff[v] ..] = sorted bucket colors, prio[v].
 cudaError_t launch_assign_lists(int32_t round, const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
@@ -149,7 +152,8 @@ struct ConflictArgs {
 cudaError_t launch_bucket_hist(const int32_t* lists, int64_t E, uint32_t* bcount, cudaStream_t s);
 cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* boff, uint32_t* bcursor,
                                int32_t* bmem, cudaStream_t s);
-cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, cudaStream_t s);
+cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, int32_t smax,
+                               cudaStream_t s);
 // out32[0] = max bucket size; out64[0] = sum over buckets of s (s - 1).
 cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out32,
                                 unsigned long long* out64, cudaStream_t s);

@@ -293,6 +293,8 @@ __global__ void __launch_bounds__(256, 4) k_color_all(ColorArgs a, int32_t* __re
 // ---------------------------------------------------------------------------
 constexpr int kMaxPolls = 1 << 20;
 
+constexpr int kOrderedGroup = 2;  // run chunks of 32 whose loads are in flight together
+
 __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
   const int64_t row = a.loff[v];
   const int L = (int)(a.loff[v + 1] - row);
@@ -304,34 +306,57 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
     const int64_t rs = a.runoff[row + k], r1 = a.runoff[row + k + 1];
     const int64_t ntot = r1 - rs;
     bool blocked = false;
-    // the run of c (the neighbours holding c) in chunks of 32; a chunk with
-    // an undecided earlier neighbour at or below c is rescanned after that
-    // neighbour moves
+    // the run of c (the neighbours holding c), kOrderedGroup chunks of 32 at a
+    // time: all column loads, then all state loads, are issued together.  A
+    // group with an undecided earlier neighbour at or below c is rescanned
+    // from that neighbour's chunk after it moves.
     for (int64_t e0 = 0; e0 < ntot && !blocked;) {
-      const int64_t e = e0 + lane;
-      bool lb = false, lw = false;
-      int32_t u = -1;
-      if (e < ntot) {
-        u = a.col[rs + e];
-        const uint64_t su = __ldcg(&a.state[u]);
-        const uint32_t pu = (uint32_t)(su >> 32);
-        if (pu < pv || (pu == pv && u < v)) {
-          const uint32_t wu = (uint32_t)su, st = wu & 3u, cu = wu >> 2;
-          lb = st == kColored && cu == c;
-          lw = st == kUndecided && cu <= c;
+      int32_t u[kOrderedGroup];
+      uint64_t su[kOrderedGroup];
+#pragma unroll
+      for (int j = 0; j < kOrderedGroup; ++j) {
+        const int64_t e = e0 + 32 * j + lane;
+        u[j] = e < ntot ? __ldg(a.col + rs + e) : -1;
+      }
+#pragma unroll
+      for (int j = 0; j < kOrderedGroup; ++j) su[j] = u[j] >= 0 ? __ldcg(&a.state[u[j]]) : 0ull;
+      bool lb = false;
+      uint32_t wm[kOrderedGroup];
+#pragma unroll
+      for (int j = 0; j < kOrderedGroup; ++j) {
+        bool lw = false;
+        if (u[j] >= 0) {
+          const uint32_t pu = (uint32_t)(su[j] >> 32);
+          if (pu < pv || (pu == pv && u[j] < v)) {
+            const uint32_t wu = (uint32_t)su[j], st = wu & 3u, cu = wu >> 2;
+            lb = lb || (st == kColored && cu == c);
+            lw = st == kUndecided && cu <= c;
+          }
         }
+        wm[j] = __ballot_sync(0xffffffffu, lw);
       }
       if (__any_sync(0xffffffffu, lb)) {
         blocked = true;
         break;
       }
-      const uint32_t wm = __ballot_sync(0xffffffffu, lw);
-      if (wm == 0u) {
-        e0 += 32;
+      int jw = -1;
+#pragma unroll
+      for (int j = kOrderedGroup - 1; j >= 0; --j)
+        if (wm[j]) jw = j;
+      if (jw < 0) {
+        e0 += 32 * kOrderedGroup;
         continue;
       }
-      // wait for the first neighbour holding us up, then rescan this chunk
-      const int32_t wu_id = __shfl_sync(0xffffffffu, u, __ffs(wm) - 1);
+      // wait for the first neighbour holding us up, then rescan from its chunk
+      uint32_t m = 0u;
+      int32_t uw = -1;
+#pragma unroll
+      for (int j = 0; j < kOrderedGroup; ++j)
+        if (j == jw) {
+          m = wm[j];
+          uw = u[j];
+        }
+      const int32_t wu_id = __shfl_sync(0xffffffffu, uw, __ffs(m) - 1);
       while (true) {
         const uint32_t w = (uint32_t)__ldcg(&a.state[wu_id]);
         if ((w & 3u) != kUndecided || (w >> 2) > c) break;
@@ -341,6 +366,7 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
         }
         __nanosleep(64);
       }
+      e0 += 32 * jw;
     }
     if (!blocked) {
       if (lane == 0) publish(a.state, v, (c << 2) | kColored);
@@ -351,7 +377,7 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
   return true;
 }
 
-__global__ void __launch_bounds__(256, 4) k_color_ordered(ColorArgs a, const int32_t* __restrict__ order,
+__global__ void __launch_bounds__(256, 8) k_color_ordered(ColorArgs a, const int32_t* __restrict__ order,
                                                           int32_t* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;

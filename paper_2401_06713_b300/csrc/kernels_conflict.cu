@@ -62,14 +62,93 @@ cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* b
   return cudaGetLastError();
 }
 
-// Ascending order inside each bucket: a shared-memory bitonic sort per bucket.
+// Ascending order inside each bucket.  Buckets of up to 512 members: one warp
+// per bucket, a bitonic network in registers (lane l holds elements
+// l*E .. l*E+E-1, E = m/32 for the padded size m); partners closer than E
+// are in the same lane, farther ones are exchanged by shuffles.  Larger
+// buckets: one CTA per bucket, the same network in shared memory.
+constexpr int kWarpSortMax = 512;
+
+template <int E>
+__device__ __forceinline__ void warp_bitonic(int32_t (&key)[E], int lane) {
+  constexpr int m = 32 * E;
+#pragma unroll
+  for (int k = 2; k <= m; k <<= 1) {
+#pragma unroll
+    for (int d = k >> 1; d > 0; d >>= 1) {
+      if (d < E) {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          if ((j & d) == 0) {
+            const int i = lane * E + j;
+            const bool up = (i & k) == 0;
+            const int32_t x = key[j], y = key[j | d];
+            const bool sw = (x > y) == up;
+            key[j] = sw ? y : x;
+            key[j | d] = sw ? x : y;
+          }
+        }
+      } else {
+        const int ld = d / E;
+        const bool lower = (lane & ld) == 0;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          const int i = lane * E + j;
+          const bool up = (i & k) == 0;
+          const int32_t y = __shfl_xor_sync(0xffffffffu, key[j], ld);
+          // the lower element keeps the smaller key when ascending
+          key[j] = (lower == up) ? min(key[j], y) : max(key[j], y);
+        }
+      }
+    }
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_bucket(int32_t* __restrict__ p, int s, int lane) {
+  int32_t key[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int i = lane * E + j;
+    key[j] = i < s ? p[i] : 0x7fffffff;
+  }
+  warp_bitonic<E>(key, lane);
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int i = lane * E + j;
+    if (i < s) p[i] = key[j];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bucket_sort_warp(const int64_t* __restrict__ boff, int64_t P,
+                                                          int32_t* __restrict__ bmem) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < P; b += gw) {
+    const int64_t o = boff[b];
+    const int s = (int)(boff[b + 1] - o);
+    if (s <= 1 || s > kWarpSortMax) continue;
+    int32_t* p = bmem + o;
+    if (s <= 32)
+      warp_sort_bucket<1>(p, s, lane);
+    else if (s <= 64)
+      warp_sort_bucket<2>(p, s, lane);
+    else if (s <= 128)
+      warp_sort_bucket<4>(p, s, lane);
+    else if (s <= 256)
+      warp_sort_bucket<8>(p, s, lane);
+    else
+      warp_sort_bucket<16>(p, s, lane);
+  }
+}
+
 __global__ void __launch_bounds__(512) k_bucket_sort(const int64_t* __restrict__ boff, int64_t P,
                                                      int32_t* __restrict__ bmem, int32_t* err) {
   __shared__ int32_t key[kBucketCap];
   for (int64_t b = blockIdx.x; b < P; b += gridDim.x) {
     const int64_t o = boff[b];
     const int s = (int)(boff[b + 1] - o);
-    if (s <= 1) continue;
+    if (s <= kWarpSortMax) continue;
     if (s > kBucketCap) {
       if (threadIdx.x == 0) atomicExch(err, 1);
       continue;
@@ -99,10 +178,17 @@ __global__ void __launch_bounds__(512) k_bucket_sort(const int64_t* __restrict__
   }
 }
 
-cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, cudaStream_t s) {
-  const unsigned blocks = (unsigned)std::min<int64_t>(P, 148 * 8);
-  k_bucket_sort<<<blocks, 256, 0, s>>>(boff, P, bmem, err);
+cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, int32_t smax,
+                               cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  const unsigned wblocks = (unsigned)std::min<int64_t>((P + 7) / 8, 148 * 16);
+  k_bucket_sort_warp<<<wblocks, 256, 0, s>>>(boff, P, bmem);
   count_launches(1);
+  if (smax > kWarpSortMax) {
+    const unsigned blocks = (unsigned)std::min<int64_t>(P, 148 * 8);
+    k_bucket_sort<<<blocks, 256, 0, s>>>(boff, P, bmem, err);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -399,16 +485,38 @@ cudaError_t launch_bucket_jblocks(const uint32_t* bcount, int64_t P, uint32_t* o
 // written in one burst of stores.
 constexpr int kEmitChunk = 16;
 
+// Rows of one staged chunk of NI partner words: lane rr keeps row rr's
+// cursor; every lane reads it by shuffle, writes its partner if its bit is
+// set, and the row's cursor advances by the word's popcount.
+template <int NI>
+__device__ __forceinline__ void emit_rows(const uint32_t* __restrict__ wbuf, const int32_t (&pv)[kEmitChunk],
+                                          int64_t& rc, int nrows, int32_t* __restrict__ col, int lane, uint32_t lt) {
+  const uint32_t lbit = 1u << lane;
+  for (int rr = 0; rr < nrows; ++rr) {
+    int32_t* dst = col + __shfl_sync(0xffffffffu, rc, rr);
+    int32_t at = 0;
+#pragma unroll
+    for (int t = 0; t < NI; ++t) {
+      const uint32_t w = wbuf[t * 32 + rr];
+      // predicated store: lane i writes partner i when bit i is set
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t@p st.global.b32 [%1], %2;\n\t}"
+          :
+          : "r"(w & lbit), "l"(dst + at + __popc(w & lt)), "r"(pv[t]));
+      at += __popc(w);
+    }
+    if (lane == rr) rc += at;
+  }
+}
+
 __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, const int64_t* __restrict__ boff,
                                                               const int32_t* __restrict__ bmem,
                                                               const int64_t* __restrict__ moff,
                                                               const int64_t* __restrict__ jboff,
                                                               int32_t* __restrict__ counter) {
-  __shared__ int64_t rcur_s[kEmitThreads / 32][32];
   __shared__ uint32_t wbuf_s[kEmitThreads / 32][kEmitChunk * 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
-  int64_t* rcur = rcur_s[wid];
   uint32_t* wbuf = wbuf_s[wid];
   const int64_t items = jboff[a.P];
   // flat / Lu as the high word of flat * ceil(2^64 / Lu): exact for flat < 2^32
@@ -434,7 +542,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
     const int nwb = (s + 31) >> 5;
     const uint32_t* rmb = a.rmask + moff[b];
     const int r = (J << 5) + lane;
-    if (r < s) rcur[lane] = a.runoff[bmem[o + r]];
+    int64_t rc = r < s ? a.runoff[bmem[o + r]] : 0;  // lane r: row r's cursor
     const int nrows = min(32, s - (J << 5));
     for (int I0 = 0; I0 < nwb; I0 += kEmitChunk) {
       const int nI = min(kEmitChunk, nwb - I0);
@@ -452,21 +560,20 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
         }
       }
       __syncwarp();
-      for (int rr = 0; rr < nrows; ++rr) {
-        int32_t* dst = a.col + rcur[rr];
-        int32_t at = 0;
-#pragma unroll
-        for (int t = 0; t < kEmitChunk; ++t) {
-          if (t < nI) {
-            const uint32_t w = wbuf[t * 32 + rr];
-            if ((w >> lane) & 1u) dst[at + __popc(w & lt)] = pv[t];
-            at += __popc(w);
-          }
-        }
-        __syncwarp();
-        if (lane == 0) rcur[rr] += at;
-        __syncwarp();
+      switch (nI) {
+#define PICASSO_EMIT_CASE(N) \
+  case N:                    \
+    emit_rows<N>(wbuf, pv, rc, nrows, a.col, lane, lt); \
+    break;
+        PICASSO_EMIT_CASE(1) PICASSO_EMIT_CASE(2) PICASSO_EMIT_CASE(3) PICASSO_EMIT_CASE(4)
+        PICASSO_EMIT_CASE(5) PICASSO_EMIT_CASE(6) PICASSO_EMIT_CASE(7) PICASSO_EMIT_CASE(8)
+        PICASSO_EMIT_CASE(9) PICASSO_EMIT_CASE(10) PICASSO_EMIT_CASE(11) PICASSO_EMIT_CASE(12)
+        PICASSO_EMIT_CASE(13) PICASSO_EMIT_CASE(14) PICASSO_EMIT_CASE(15) PICASSO_EMIT_CASE(16)
+#undef PICASSO_EMIT_CASE
+        default:
+          break;
       }
+      __syncwarp();
     }
   }
 }

@@ -69,6 +69,17 @@ cudaError_t launch_list_offsets(const int32_t* gid, int64_t n, const int64_t* so
   return launch_scan_u32(len, n, loff, tmp, s);
 }
 
+__global__ void k_strided_offsets(int64_t* __restrict__ loff, int64_t n, int32_t L) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v <= n) loff[v] = v * (int64_t)L;
+}
+
+cudaError_t launch_strided_offsets(int64_t* loff, int64_t n, int32_t L, cudaStream_t s) {
+  k_strided_offsets<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(loff, n, L);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 __global__ void k_entry_owner(const int64_t* __restrict__ loff, int64_t n, int32_t* __restrict__ ent_v) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
