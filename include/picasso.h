@@ -91,8 +91,9 @@ typedef enum {
 } picasso_color_algo;
 
 /* Conflict CSR of the current round, owned by the context and valid until
- * the next assign/build/carry or destroy.  Ids are round-local: row r is the
- * r-th uncolored vertex in ascending global id.  Rows are color-major: row u
+ * the next assign/build/carry or destroy.  Ids are round-local: vertex r is
+ * the r-th of the round's coloring order, ascending (priority, global id)
+ * (picasso_get_round maps them to global ids).  Rows are color-major: row u
  * lists, for each color c of u's list in ascending order (its "run"), the
  * neighbours v that also hold c, ascending in v.  An edge of G_c whose two
  * lists share m colors appears in m runs of each of its rows, so nnz =
@@ -211,9 +212,11 @@ int picasso_run(void* ctx, int32_t* d_color_out, int32_t* n_rounds);
 /* Copy the global color array [n] (-1 = not yet colored) to d_out.         */
 int picasso_get_colors(void* ctx, int32_t* d_out);
 
-/* Inspection of the current round, for tests and tools.
- *   d_gid   [n_l]    global ids of V_l (ascending)
- *   d_lists [n_l][L] round-local colors (add base for global), ascending
+/* Inspection of the current round, for tests and tools, indexed by the
+ * round-local id once lists are assigned (coloring order):
+ *   d_gid   [n_l]    global ids (before assignment: V_l in ascending order)
+ *   d_lists [E]      bucket colors (round-local color + the set's offset),
+ *                    ascending per vertex
  *   d_prio  [n_l]    priorities (smaller = earlier)
  * Any pointer may be NULL.                                                  */
 int picasso_get_round(void* ctx, int32_t* d_gid, int32_t* d_lists,

@@ -95,6 +95,12 @@ struct Ctx {
   int32_t* ent_v = nullptr;
   int32_t* lists = nullptr;
   uint32_t* prio = nullptr;
+  // the round in coloring order: round-local id t is the t-th vertex in
+  // ascending (priority, global id); perm[t] is its place in V_l (ascending
+  // global id), gid_r / xz_r its global id and words
+  int32_t* perm = nullptr;
+  int32_t* gid_r = nullptr;
+  uint64_t* xz_r = nullptr;
   // build
   bool built = false;
   int64_t nnz = 0, max_bucket = 0;
@@ -200,6 +206,9 @@ void free_build(Ctx* c) {
 void free_assign(Ctx* c) {
   release(c, &c->lists);
   release(c, &c->prio);
+  release(c, &c->perm);
+  release(c, &c->gid_r);
+  release(c, &c->xz_r);
   release(c, &c->loff);
   release(c, &c->ent_v);
   c->assigned = false;
@@ -285,38 +294,64 @@ int assign_round(Ctx* c) {
   const int64_t n = c->n;
   cudaStream_t s = c->s;
   CK(cudaMemcpyAsync(c->d_sets, c->sets.data(), sizeof(SetRound) * c->nsets, cudaMemcpyHostToDevice, s));
+
+  uint32_t* prio_g = nullptr;
+  uint32_t* hist = nullptr;
   uint32_t* len = nullptr;
+  int64_t* hoff = nullptr;
   void* tmp = nullptr;
-  ST(alloc(c, &c->loff, n + 1));
-  ST(alloc(c, &len, n));
-  int st = alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(n));
-  if (st != PICASSO_OK) {
+  const int nbins = prio_bins_for(n);
+  auto done = [&]() {
+    release(c, &prio_g);
+    release(c, &hist);
     release(c, &len);
+    release(c, &hoff);
+    release(c, (uint8_t**)&tmp);
+  };
+  int st = alloc(c, &prio_g, n);
+  if (st == PICASSO_OK) st = alloc(c, &hist, nbins);
+  if (st == PICASSO_OK) st = alloc(c, &hoff, nbins + 1);
+  if (st == PICASSO_OK) st = alloc(c, &len, n);
+  if (st == PICASSO_OK) st = alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(n > nbins ? n : nbins));
+  if (st == PICASSO_OK) st = alloc(c, &c->perm, n);
+  if (st == PICASSO_OK) st = alloc(c, &c->gid_r, n);
+  if (st == PICASSO_OK) st = alloc(c, &c->xz_r, 2 * n);
+  if (st == PICASSO_OK) st = alloc(c, &c->prio, n);
+  if (st == PICASSO_OK) st = alloc(c, &c->loff, n + 1);
+  if (st != PICASSO_OK) {
+    done();
     return st;
   }
-  cudaError_t e = cudaSuccess;
-  if (c->nsets == 1) {
-    // one list length: loff[v] = v L, no scan and no readback
-    e = launch_strided_offsets(c->loff, n, Lmax, s);
-    c->E = n * (int64_t)Lmax;
-  } else {
-    e = launch_list_offsets(c->gid, n, c->d_soff, c->nsets, c->d_sets, len, c->loff, tmp, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_buf, c->loff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) c->E = c->h_buf[0];
+  // Coloring order: priorities in V_l order, sorted by (priority, global id);
+  // the round's global ids, words and priorities are gathered in that order,
+  // so round-local id t is the t-th vertex to be colored.
+  cudaError_t e = launch_round_prio(c->round, c->gid, n, c->d_soff, c->nsets, c->d_sets, prio_g, s);
+  if (e == cudaSuccess) e = launch_prio_order(prio_g, n, nbins, hist, hoff, tmp, c->perm, s);
+  if (e == cudaSuccess)
+    e = launch_rank_gather(c->perm, n, c->gid, c->round_xz(), prio_g, c->gid_r, c->xz_r, c->prio, s);
+  // list offsets in that order
+  if (e == cudaSuccess) {
+    if (c->nsets == 1) {
+      // one list length: loff[t] = t L, no scan and no readback
+      e = launch_strided_offsets(c->loff, n, Lmax, s);
+      c->E = n * (int64_t)Lmax;
+    } else {
+      e = launch_list_offsets(c->gid_r, n, c->d_soff, c->nsets, c->d_sets, len, c->loff, tmp, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_buf, c->loff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) c->E = c->h_buf[0];
+    }
   }
-  release(c, &len);
-  release(c, (uint8_t**)&tmp);
+  done();
   CK(e);
   // with one list length (a single set) owners follow from e / L
   c->Lu = c->nsets == 1 ? Lmax : 0;
   ST(alloc(c, &c->lists, c->E));
-  ST(alloc(c, &c->prio, n));
   if (!c->Lu) {
     ST(alloc(c, &c->ent_v, c->E));
     CK(launch_entry_owner(c->loff, n, c->ent_v, s));
   }
-  CK(launch_assign_lists(c->round, c->gid, n, c->d_soff, c->nsets, c->d_sets, Lmax, c->loff, c->lists, c->prio,
+  CK(launch_assign_lists(c->round, c->gid_r, n, c->d_soff, c->nsets, c->d_sets, Lmax, c->loff, c->lists, c->prio,
                          s));
   c->assigned = true;
   return PICASSO_OK;
@@ -405,7 +440,7 @@ int build_conflicts(Ctx* c) {
   a.Lmax = c->Lmax;
   a.Lu = c->Lu;
   a.P = P;
-  a.xz = c->round_xz();
+  a.xz = c->xz_r;
   a.lists = c->lists;
   a.loff = c->loff;
   a.ent_v = c->ent_v;
@@ -478,10 +513,11 @@ int build_conflicts(Ctx* c) {
   TRYC(launch_row_offsets(c->runoff, c->loff, n, c->off, s));
   if (c->nsets > 1) {
     std::vector<int64_t> h(c->nsets);
-    TRYC(launch_set_csr_bytes(c->loff, c->runoff, c->gid, n, c->d_soff, c->nsets, c->d_set_bytes, s));
+    TRYC(launch_set_csr_bytes(c->loff, c->runoff, c->gid_r, n, c->d_soff, c->nsets, c->d_set_bytes, s));
     TRYC(cudaMemcpyAsync(h.data(), c->d_set_bytes, sizeof(int64_t) * c->nsets, cudaMemcpyDeviceToHost, s));
     TRYC(cudaStreamSynchronize(s));
-    for (int k = 0; k < c->nsets; ++k) c->set_peak_bytes[k] = std::max(c->set_peak_bytes[k], h[k]);
+    for (int k = 0; k < c->nsets; ++k)
+      if (c->remaining[k] > 0) c->set_peak_bytes[k] = std::max(c->set_peak_bytes[k], h[k] + 8);
   } else {
     c->set_peak_bytes[0] = std::max(c->set_peak_bytes[0], csr_bytes);
   }
@@ -516,9 +552,8 @@ int color_round(Ctx* c) {
   cudaStream_t s = c->s;
   int32_t *wa = nullptr, *wb = nullptr, *wact = nullptr, *nw = nullptr;
   uint16_t* kcur = nullptr;
-  uint32_t *rcur = nullptr, *hist = nullptr, *blkw = nullptr;
+  uint32_t *rcur = nullptr, *blkw = nullptr;
   int32_t* blk = nullptr;
-  int64_t* hoff = nullptr;
   void* tmp = nullptr;
   int st = PICASSO_OK;
   auto cleanup = [&]() {
@@ -530,8 +565,6 @@ int color_round(Ctx* c) {
     release(c, &rcur);
     release(c, &blk);
     release(c, &blkw);
-    release(c, &hist);
-    release(c, &hoff);
     release(c, (uint8_t**)&tmp);
   };
 #define TRY(expr)           \
@@ -553,7 +586,6 @@ int color_round(Ctx* c) {
     }                                             \
   } while (0)
   free_color(c);
-  const int nbins = prio_bins_for(n);
   TRY(alloc(c, &c->state, n));
   TRY(alloc(c, &kcur, n));
   TRY(alloc(c, &rcur, n));
@@ -562,10 +594,7 @@ int color_round(Ctx* c) {
   TRY(alloc(c, &wa, n));
   TRY(alloc(c, &wb, n));
   TRY(alloc(c, &wact, n));
-  TRY(alloc(c, &hist, nbins));
-  TRY(alloc(c, &hoff, nbins + 1));
-  const int64_t scan_n = n > nbins ? n : nbins;
-  TRY(alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(scan_n)));
+  TRY(alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(n)));
   TRY(alloc(c, &nw, kCtlWords));
   int32_t* ctl = nw;
   ColorArgs a{};
@@ -579,6 +608,7 @@ int color_round(Ctx* c) {
   a.rcur = rcur;
   a.blk = blk;
   a.blkw = blkw;
+  a.ranked = 1;  // round-local ids are ranks in coloring order
   // Ordered persistent pass; if one of its bounded waits runs out (ctl[5]),
   // recolor the round with the sweep kernel from a fresh state.  The colors,
   // the carry flags and their prefix sum are enqueued behind the pass, so one
@@ -586,18 +616,19 @@ int color_round(Ctx* c) {
   TRY(alloc(c, &c->flag, n));
   TRY(alloc(c, &c->pos, n + 1));
   auto enqueue_carry = [&]() -> cudaError_t {
-    cudaError_t e = launch_carry_flags(c->state, n, c->gid, c->d_soff, c->nsets, c->d_sets, c->color, c->flag, s);
+    cudaError_t e = launch_carry_flags(c->state, n, c->gid_r, c->perm, c->d_soff, c->nsets, c->d_sets, c->color,
+                                       c->flag, s);
     if (e == cudaSuccess) e = launch_scan_u32(c->flag, n, c->pos, tmp, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_buf, c->pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     return e;
   };
   TRYC(cudaMemsetAsync(ctl, 0, sizeof(int32_t) * kCtlWords, s));
-  TRYC(launch_prio_order(c->prio, n, nbins, hist, hoff, tmp, wa, s));
+  TRYC(launch_iota(wa, n, s));  // the first work list: every vertex, in coloring order
   TRYC(launch_color_init(a, c->prio, ctl, s));
   int32_t sweeps = 0;
   bool need_sweeps = c->cfg.color_algo == PICASSO_COLOR_SWEEP;
   if (!need_sweeps) {
-    TRYC(launch_color_ordered(a, wa, ctl + 5, s));
+    TRYC(launch_color_ordered(a, nullptr, ctl + 5, s));
     TRYC(cudaMemcpyAsync(c->sweep_log, ctl, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s));
     TRYC(enqueue_carry());
     TRYC(cudaStreamSynchronize(s));
@@ -892,7 +923,9 @@ int picasso_get_round(void* ctx, int32_t* d_gid, int32_t* d_lists, uint32_t* d_p
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (d_gid && c->n > 0) {
-    if (c->gid)
+    if (c->assigned)
+      CK(cudaMemcpyAsync(d_gid, c->gid_r, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->s));
+    else if (c->gid)
       CK(cudaMemcpyAsync(d_gid, c->gid, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->s));
     else
       CK(launch_iota(d_gid, c->n, c->s));

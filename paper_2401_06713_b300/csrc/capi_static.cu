@@ -232,6 +232,7 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
     ca.rcur = rcur;
     ca.blk = blk;
     ca.blkw = blkw;
+    ca.ranked = 0;  // ids in ascending global id; the order list gives the coloring order
     SCK(cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCtlWords, s));
     SCK(launch_prio_order(prio, m, prio_bins_for(m), hist, hoff, tmp, work[0], s));
     SCK(launch_color_init(ca, prio, counts, s));
@@ -249,7 +250,7 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
         if (h[4] != 0 || h[0] != 0) return PICASSO_ERR_INTERNAL;
       }
     }
-    SCK(launch_carry_flags(state, m, gid, soff, 1, dset, d_color_out, flag, s));
+    SCK(launch_carry_flags(state, m, gid, nullptr, soff, 1, dset, d_color_out, flag, s));
     SCK(launch_scan_u32(flag, m, pos, tmp, s));
     int64_t rem = 0;
     {

@@ -118,6 +118,9 @@ cudaError_t launch_list_offsets(const int32_t* gid, int64_t n, const int64_t* so
 cudaError_t launch_strided_offsets(int64_t* loff, int64_t n, int32_t L, cudaStream_t s);
 cudaError_t launch_entry_owner(const int64_t* loff, int64_t n, int32_t* ent_v, cudaStream_t s);
 // Alg. 1 list assignment: lists[loff[v] ..] = sorted bucket colors, prio[v].
+// Priorities of the round's vertices (draw 0 of the PRIO stream), no lists.
+cudaError_t launch_round_prio(int32_t round, const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
+                              const SetRound* sets, uint32_t* prio, cudaStream_t s);
 cudaError_t launch_assign_lists(int32_t round, const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
                                 const SetRound* sets, int32_t Lmax, const int64_t* loff, int32_t* lists,
                                 uint32_t* prio, cudaStream_t s);
@@ -183,6 +186,8 @@ struct ColorArgs {
   uint32_t* rcur;   // [n] resolved prefix of the current candidate's run
   int32_t* blk;     // [n] neighbour the vertex waited on last, or -1
   uint32_t* blkw;   // [n] the vertex's candidate color when it started waiting
+  int32_t ranked;   // 1: round-local ids are ranks in coloring order, so the
+                    // earlier neighbours of a run form its prefix
 };
 // Work list of all n vertices in ascending (priority, id): a counting sort on
 // the top log2(nbins) priority bits, then a sort inside each bin.  hist needs
@@ -214,8 +219,15 @@ cudaError_t launch_color_all(const ColorArgs& a, int32_t* wa, int32_t* wb, int32
                              cudaStream_t s);
 // Colors to the output (final color = base + bucket color - cofs of the
 // vertex's set, written at its batch-global id) and flags of the uncolored.
-cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* gid, const int64_t* soff,
-                               int32_t nsets, const SetRound* sets, int32_t* color, uint32_t* flag,
+// perm (may be null): flag index of round vertex v is perm[v] (the vertex's
+// place in ascending global id) instead of v.
+cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* gid, const int32_t* perm,
+                               const int64_t* soff, int32_t nsets, const SetRound* sets, int32_t* color,
+                               uint32_t* flag, cudaStream_t s);
+// Round arrays in coloring order: out[t] = in[perm[t]] for the global ids
+// (identity when gid_in is null), packed words and priorities.
+cudaError_t launch_rank_gather(const int32_t* perm, int64_t n, const int32_t* gid_in, const uint64_t* xz_in,
+                               const uint32_t* prio_in, int32_t* gid_out, uint64_t* xz_out, uint32_t* prio_out,
                                cudaStream_t s);
 cudaError_t launch_carry_gather(const uint32_t* flag, const int64_t* pos, int64_t n, const int32_t* gid,
                                 const uint64_t* xz, int32_t* gid_out, uint64_t* xz_out, cudaStream_t s);
@@ -224,6 +236,7 @@ cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff
                               cudaStream_t s);
 cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t n, uint64_t* xz_out,
                              cudaStream_t s);
+// out[k] (zeroed here) = 8 (n_k + 1) + 4 * run entries of set k's vertices.
 cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int32_t* gid, int64_t n,
                                  const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s);
 cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s);

@@ -147,9 +147,10 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
       uint32_t wu = 0;
       if (e < r1) {
         u = a.col[e];
-        const uint64_t su = __ldcg(&a.state[u]);
+        if (a.ranked && u > v) u = -1;  // past the earlier neighbours
+        const uint64_t su = u >= 0 ? __ldcg(&a.state[u]) : 0ull;
         const uint32_t pu = (uint32_t)(su >> 32);
-        if (pu < pv || (pu == pv && u < v)) {
+        if (u >= 0 && (a.ranked || pu < pv || (pu == pv && u < v))) {
           wu = (uint32_t)su;
           const uint32_t st = wu & 3u, cu = wu >> 2;
           lb = st == kColored && cu == c;
@@ -166,6 +167,8 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
         first_wait = e0 + src;
         wait_u = __shfl_sync(0xffffffffu, u, src);
       }
+      // ranked ids: the run ascends, so a later neighbour ends the prefix
+      if (a.ranked && __any_sync(0xffffffffu, e < r1 && u < 0)) break;
     }
     if (blocked) {
       ++k;
@@ -294,96 +297,155 @@ __global__ void __launch_bounds__(256, 4) k_color_all(ColorArgs a, int32_t* __re
 constexpr int kMaxPolls = 1 << 20;
 
 constexpr int kOrderedGroup = 2;  // run chunks of 32 whose loads are in flight together
+constexpr int kCandBatch = 2;     // candidates whose first run chunk is screened together
 
+// Scan the run [rs, rs + ntot) of candidate c to the end: true if an earlier
+// neighbour took c; waits (bounded) on earlier neighbours still undecided at
+// or below c.  *fail is set when a wait runs out.
+__device__ __forceinline__ bool run_blocked(const ColorArgs& a, int32_t v, uint32_t pv, uint32_t c, int64_t rs,
+                                            int64_t ntot, int lane, int& polls, bool* fail) {
+  for (int64_t e0 = 0; e0 < ntot;) {
+    int32_t u[kOrderedGroup];
+    uint64_t su[kOrderedGroup];
+    bool past = false;  // ranked ids: a later neighbour ends the prefix
+#pragma unroll
+    for (int j = 0; j < kOrderedGroup; ++j) {
+      const int64_t e = e0 + 32 * j + lane;
+      u[j] = e < ntot ? __ldg(a.col + rs + e) : -1;
+      if (a.ranked && u[j] > v) {
+        u[j] = -1;
+        past = true;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kOrderedGroup; ++j) su[j] = u[j] >= 0 ? __ldcg(&a.state[u[j]]) : 0ull;
+    bool lb = false;
+    uint32_t wm[kOrderedGroup];
+#pragma unroll
+    for (int j = 0; j < kOrderedGroup; ++j) {
+      bool lw = false;
+      if (u[j] >= 0) {
+        const uint32_t pu = (uint32_t)(su[j] >> 32);
+        if (a.ranked || pu < pv || (pu == pv && u[j] < v)) {
+          const uint32_t wu = (uint32_t)su[j], st = wu & 3u, cu = wu >> 2;
+          lb = lb || (st == kColored && cu == c);
+          lw = st == kUndecided && cu <= c;
+        }
+      }
+      wm[j] = __ballot_sync(0xffffffffu, lw);
+    }
+    if (__any_sync(0xffffffffu, lb)) return true;
+    int jw = -1;
+#pragma unroll
+    for (int j = kOrderedGroup - 1; j >= 0; --j)
+      if (wm[j]) jw = j;
+    if (jw < 0) {
+      if (__any_sync(0xffffffffu, past)) return false;
+      e0 += 32 * kOrderedGroup;
+      continue;
+    }
+    // wait for the first neighbour holding us up, then rescan from its chunk
+    uint32_t m = 0u;
+    int32_t uw = -1;
+#pragma unroll
+    for (int j = 0; j < kOrderedGroup; ++j)
+      if (j == jw) {
+        m = wm[j];
+        uw = u[j];
+      }
+    const int32_t wu_id = __shfl_sync(0xffffffffu, uw, __ffs(m) - 1);
+    while (true) {
+      const uint32_t w = (uint32_t)__ldcg(&a.state[wu_id]);
+      if ((w & 3u) != kUndecided || (w >> 2) > c) break;
+      if (++polls > kMaxPolls) {
+        *fail = true;
+        return true;
+      }
+      __nanosleep(64);
+    }
+    e0 += 32 * jw;
+  }
+  return false;
+}
+
+// One vertex.  The run offsets and colors of 32 candidates are loaded at
+// once (lane k holds candidate k's); candidates are then screened
+// kCandBatch at a time on the first 32 entries of their runs (one round of
+// column loads and one of state loads for the batch): a candidate whose first
+// chunk shows an earlier neighbour colored with it is blocked; the first one
+// not blocked that way is settled by scanning its whole run.
 __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
   const int64_t row = a.loff[v];
   const int L = (int)(a.loff[v + 1] - row);
   const uint32_t pv = (uint32_t)(__ldcg(&a.state[v]) >> 32);
   int polls = 0;
-  for (int k = 0; k < L; ++k) {
-    const uint32_t c = (uint32_t)a.lists[row + k];
-    if (k > 0 && lane == 0) publish(a.state, v, (c << 2) | kUndecided);
-    const int64_t rs = a.runoff[row + k], r1 = a.runoff[row + k + 1];
-    const int64_t ntot = r1 - rs;
-    bool blocked = false;
-    // the run of c (the neighbours holding c), kOrderedGroup chunks of 32 at a
-    // time: all column loads, then all state loads, are issued together.  A
-    // group with an undecided earlier neighbour at or below c is rescanned
-    // from that neighbour's chunk after it moves.
-    for (int64_t e0 = 0; e0 < ntot && !blocked;) {
-      int32_t u[kOrderedGroup];
-      uint64_t su[kOrderedGroup];
+  for (int kb = 0; kb < L; kb += 32) {
+    const int kl = kb + lane;
+    const int64_t my_rs = kl < L ? a.runoff[row + kl] : 0;
+    const int64_t my_re = kl < L ? a.runoff[row + kl + 1] : 0;
+    const uint32_t my_c = kl < L ? (uint32_t)a.lists[row + kl] : 0u;
+    const int kend = min(L - kb, 32);
+    for (int k0 = 0; k0 < kend; k0 += kCandBatch) {
+      int32_t u[kCandBatch];
+      uint64_t su[kCandBatch];
 #pragma unroll
-      for (int j = 0; j < kOrderedGroup; ++j) {
-        const int64_t e = e0 + 32 * j + lane;
-        u[j] = e < ntot ? __ldg(a.col + rs + e) : -1;
+      for (int b = 0; b < kCandBatch; ++b) {
+        const int64_t rs = __shfl_sync(0xffffffffu, my_rs, min(k0 + b, 31));
+        const int64_t re = __shfl_sync(0xffffffffu, my_re, min(k0 + b, 31));
+        const int64_t e = rs + lane;
+        u[b] = (k0 + b < kend && e < re) ? __ldg(a.col + e) : -1;
+        if (a.ranked && u[b] > v) u[b] = -1;
       }
 #pragma unroll
-      for (int j = 0; j < kOrderedGroup; ++j) su[j] = u[j] >= 0 ? __ldcg(&a.state[u[j]]) : 0ull;
-      bool lb = false;
-      uint32_t wm[kOrderedGroup];
+      for (int b = 0; b < kCandBatch; ++b) su[b] = u[b] >= 0 ? __ldcg(&a.state[u[b]]) : 0ull;
+      uint32_t blocked_mask = 0u;
 #pragma unroll
-      for (int j = 0; j < kOrderedGroup; ++j) {
-        bool lw = false;
-        if (u[j] >= 0) {
-          const uint32_t pu = (uint32_t)(su[j] >> 32);
-          if (pu < pv || (pu == pv && u[j] < v)) {
-            const uint32_t wu = (uint32_t)su[j], st = wu & 3u, cu = wu >> 2;
-            lb = lb || (st == kColored && cu == c);
-            lw = st == kUndecided && cu <= c;
+      for (int b = 0; b < kCandBatch; ++b) {
+        const uint32_t cb = __shfl_sync(0xffffffffu, my_c, min(k0 + b, 31));
+        bool lb = false;
+        if (u[b] >= 0) {
+          const uint32_t pu = (uint32_t)(su[b] >> 32);
+          if (a.ranked || pu < pv || (pu == pv && u[b] < v)) {
+            const uint32_t wu = (uint32_t)su[b];
+            lb = (wu & 3u) == kColored && (wu >> 2) == cb;
           }
         }
-        wm[j] = __ballot_sync(0xffffffffu, lw);
+        if (__any_sync(0xffffffffu, lb)) blocked_mask |= 1u << b;
       }
-      if (__any_sync(0xffffffffu, lb)) {
-        blocked = true;
-        break;
-      }
-      int jw = -1;
 #pragma unroll
-      for (int j = kOrderedGroup - 1; j >= 0; --j)
-        if (wm[j]) jw = j;
-      if (jw < 0) {
-        e0 += 32 * kOrderedGroup;
-        continue;
-      }
-      // wait for the first neighbour holding us up, then rescan from its chunk
-      uint32_t m = 0u;
-      int32_t uw = -1;
-#pragma unroll
-      for (int j = 0; j < kOrderedGroup; ++j)
-        if (j == jw) {
-          m = wm[j];
-          uw = u[j];
-        }
-      const int32_t wu_id = __shfl_sync(0xffffffffu, uw, __ffs(m) - 1);
-      while (true) {
-        const uint32_t w = (uint32_t)__ldcg(&a.state[wu_id]);
-        if ((w & 3u) != kUndecided || (w >> 2) > c) break;
-        if (++polls > kMaxPolls) {
+      for (int b = 0; b < kCandBatch; ++b) {
+        const int kk = k0 + b;
+        if (kk >= kend) break;
+        if ((blocked_mask >> b) & 1u) continue;
+        // candidate kb + kk is not blocked by its first chunk: settle it
+        const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
+        const int64_t rs = __shfl_sync(0xffffffffu, my_rs, kk);
+        const int64_t re = __shfl_sync(0xffffffffu, my_re, kk);
+        if (kb + kk > 0 && lane == 0) publish(a.state, v, (c << 2) | kUndecided);
+        bool fail = false;
+        const bool blk = run_blocked(a, v, pv, c, rs, re - rs, lane, polls, &fail);
+        if (fail) {
           if (lane == 0) atomicExch(err, 1);
           return false;
         }
-        __nanosleep(64);
+        if (!blk) {
+          if (lane == 0) publish(a.state, v, (c << 2) | kColored);
+          return true;
+        }
       }
-      e0 += 32 * jw;
-    }
-    if (!blocked) {
-      if (lane == 0) publish(a.state, v, (c << 2) | kColored);
-      return true;
     }
   }
   if (lane == 0) publish(a.state, v, (kFailedColor << 2) | kFailed);
   return true;
 }
 
-__global__ void __launch_bounds__(256, 8) k_color_ordered(ColorArgs a, const int32_t* __restrict__ order,
+__global__ void __launch_bounds__(256, 6) k_color_ordered(ColorArgs a, const int32_t* __restrict__ order,
                                                           int32_t* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   for (int64_t t = wid; t < a.n; t += gwarps) {
-    if (!ordered_vertex(a, __ldcg(&order[t]), lane, err)) return;
+    if (!ordered_vertex(a, order ? __ldcg(&order[t]) : (int32_t)t, lane, err)) return;
   }
 }
 
@@ -480,8 +542,9 @@ cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const
 // color of a vertex of set k is base_k + (bucket color - cofs_k), written at
 // its batch-global id.
 __global__ void k_carry_flags(const uint64_t* __restrict__ state, int64_t n, const int32_t* __restrict__ gid,
-                              const int64_t* __restrict__ soff, int nsets, const SetRound* __restrict__ sets,
-                              int32_t* __restrict__ color, uint32_t* __restrict__ flag) {
+                              const int32_t* __restrict__ perm, const int64_t* __restrict__ soff, int nsets,
+                              const SetRound* __restrict__ sets, int32_t* __restrict__ color,
+                              uint32_t* __restrict__ flag) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const uint32_t w = (uint32_t)state[v];
@@ -491,14 +554,14 @@ __global__ void k_carry_flags(const uint64_t* __restrict__ state, int64_t n, con
     const SetRound& sr = sets[nsets > 1 ? set_of(soff, nsets, g) : 0];
     color[g] = (int32_t)(sr.base + ((int64_t)(w >> 2) - sr.cofs));
   }
-  flag[v] = st == kColored ? 0u : 1u;
+  flag[perm ? perm[v] : v] = st == kColored ? 0u : 1u;
 }
 
-cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* gid, const int64_t* soff,
-                               int32_t nsets, const SetRound* sets, int32_t* color, uint32_t* flag,
-                               cudaStream_t s) {
+cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* gid, const int32_t* perm,
+                               const int64_t* soff, int32_t nsets, const SetRound* sets, int32_t* color,
+                               uint32_t* flag, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_carry_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(state, n, gid, soff, nsets, sets, color, flag);
+  k_carry_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(state, n, gid, perm, soff, nsets, sets, color, flag);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -521,36 +584,50 @@ cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff
 }
 
 // Conflict-structure bytes of every set in this round, counted like the
-// byte budget: 8 (n_k + 1) row offsets + 4 per run entry.  The round's
-// vertices are in ascending global id, so set k owns the rows
-// [lower_bound(soff[k]), lower_bound(soff[k+1])) and, through loff, a
-// contiguous range of list entries whose run offsets give its entries.
-__device__ __forceinline__ int64_t lower_bound_gid(const int32_t* __restrict__ gid, int64_t n, int64_t g) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if ((int64_t)gid[mid] < g)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
-}
-
+// byte budget: 8 (n_k + 1) row offsets + 4 per run entry, accumulated per
+// vertex (the round's vertices of a set need not be contiguous).
 __global__ void k_set_csr_bytes(const int64_t* __restrict__ loff, const int64_t* __restrict__ runoff,
                                 const int32_t* __restrict__ gid, int64_t n, const int64_t* __restrict__ soff,
-                                int nsets, int64_t* __restrict__ out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nsets) return;
-  const int64_t a = gid ? lower_bound_gid(gid, n, soff[k]) : min(soff[k], n);
-  const int64_t b = gid ? lower_bound_gid(gid, n, soff[k + 1]) : min(soff[k + 1], n);
-  out[k] = b > a ? 8 * (b - a + 1) + 4 * (runoff[loff[b]] - runoff[loff[a]]) : 0;
+                                int nsets, unsigned long long* __restrict__ out) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int64_t g = gid ? (int64_t)gid[v] : v;
+  const int k = nsets > 1 ? set_of(soff, nsets, g) : 0;
+  const int64_t row = 8 + 4 * (runoff[loff[v + 1]] - runoff[loff[v]]);
+  atomicAdd(&out[k], (unsigned long long)row);
 }
+
 
 cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int32_t* gid, int64_t n,
                                  const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s) {
   if (nsets <= 0) return cudaSuccess;
-  k_set_csr_bytes<<<(nsets + 127) / 128, 128, 0, s>>>(loff, runoff, gid, n, soff, nsets, out);
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t) * nsets, s);
+  if (e != cudaSuccess || n <= 0) return e;
+  k_set_csr_bytes<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(loff, runoff, gid, n, soff, nsets,
+                                                               (unsigned long long*)out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void k_rank_gather(const int32_t* __restrict__ perm, int64_t n, const int32_t* __restrict__ gid_in,
+                              const uint64_t* __restrict__ xz_in, const uint32_t* __restrict__ prio_in,
+                              int32_t* __restrict__ gid_out, uint64_t* __restrict__ xz_out,
+                              uint32_t* __restrict__ prio_out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int64_t i = perm[t];
+  gid_out[t] = gid_in ? gid_in[i] : (int32_t)i;
+  xz_out[2 * t] = xz_in[2 * i];
+  xz_out[2 * t + 1] = xz_in[2 * i + 1];
+  prio_out[t] = prio_in[i];
+}
+
+cudaError_t launch_rank_gather(const int32_t* perm, int64_t n, const int32_t* gid_in, const uint64_t* xz_in,
+                               const uint32_t* prio_in, int32_t* gid_out, uint64_t* xz_out, uint32_t* prio_out,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_rank_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(perm, n, gid_in, xz_in, prio_in, gid_out, xz_out,
+                                                             prio_out);
   count_launches(1);
   return cudaGetLastError();
 }

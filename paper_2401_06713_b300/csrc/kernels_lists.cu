@@ -100,6 +100,24 @@ cudaError_t launch_entry_owner(const int64_t* loff, int64_t n, int32_t* ent_v, c
 // (x*(j+1) >> 32 of the next Philox word); keep t, or j if t was already
 // kept.  Then an insertion sort; lists hold bucket colors (round-local color
 // + the set's offset cofs).  The priority is draw 0 of the PRIO stream.
+__global__ void k_round_prio(int32_t round, const int32_t* __restrict__ gid, int64_t n,
+                             const int64_t* __restrict__ soff, int nsets, const SetRound* __restrict__ sets,
+                             uint32_t* __restrict__ prio) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int64_t gg = gid ? (int64_t)gid[v] : v;
+  const int k = nsets > 1 ? set_of(soff, nsets, gg) : 0;
+  prio[v] = philox_block(sets[k].seed, round, gg - soff[k], kTagPrio, 0u).x;
+}
+
+cudaError_t launch_round_prio(int32_t round, const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
+                              const SetRound* sets, uint32_t* prio, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_round_prio<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(round, gid, n, soff, nsets, sets, prio);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 template <int LCAP>
 __global__ void k_assign_lists(int32_t round, const int32_t* __restrict__ gid, int64_t n,
                                const int64_t* __restrict__ soff, int nsets, const SetRound* __restrict__ sets,

@@ -64,21 +64,37 @@ def test_lists_and_priorities(pc, orc, n, P, L):
     with pc.Picasso(_xz(pc, chars), 8, seed=42) as p:
         p.assign_lists(P, L, 17)
         gid, lists, prio = p.round_state()
+        gid = gid.cpu().numpy().astype(np.int64)
         lists = lists.cpu().numpy().astype(np.int64)
         ref = orc.draw_lists(42, 1, np.arange(n), P, L, 0)
-        assert np.array_equal(lists, ref)
-        assert np.array_equal(_u32(prio), orc.priorities(42, 1, range(n)))
-        assert np.array_equal(gid.cpu().numpy(), np.arange(n))
+        ref_prio = orc.priorities(42, 1, range(n)).astype(np.int64)
+        # round-local id t is the t-th vertex of the coloring order
+        assert np.array_equal(np.sort(gid), np.arange(n))
+        assert np.array_equal(gid, np.lexsort((np.arange(n), ref_prio)))
+        assert np.array_equal(lists, ref[gid])
+        assert np.array_equal(_u32(prio).astype(np.int64), ref_prio[gid])
 
 
 # ------------------------------------------------------------------ conflict graph
+def _ranked(p, orc, chars, seed, P, L):
+    """Oracle inputs in the round's coloring order: the oracle's own priorities
+    give the order, checked against the context's."""
+    n = len(chars)
+    prio = orc.priorities(seed, 1, range(n)).astype(np.int64)
+    order = np.lexsort((np.arange(n), prio))
+    gid = p.round_state()[0].cpu().numpy().astype(np.int64)
+    assert np.array_equal(gid, order)
+    enc = orc.encode3(chars)[order]
+    lists = orc.draw_lists(seed, 1, order, P, L, 0)
+    return order, enc, lists
+
+
 def _check_build(pc, orc, chars, seed, P, L, algo):
     n = len(chars)
-    enc = orc.encode3(chars)
-    lists = orc.draw_lists(seed, 1, np.arange(n), P, L, 0)
-    off_r, col_r = orc.conflict_csr(enc, lists)
     with pc.Picasso(_xz(pc, chars), chars.shape[1], seed=seed, algo=algo) as p:
         p.assign_lists(P, L, 0)
+        _, enc, lists = _ranked(p, orc, chars, seed, P, L)
+        off_r, col_r = orc.conflict_csr(enc, lists)
         n_rows, nnz = p.build_conflicts()
         assert (n_rows, nnz) == (n, len(col_r))
         off, col = p.csr()
@@ -257,27 +273,23 @@ def _full_size(pc, orc, n, q, p_w, num, den, alpha, seed, samples):
         p.build_conflicts()
         off, col = p.csr()
         off = off.cpu().numpy()
-        # the oracle draws every list and priority itself
-        lists_all = orc.draw_lists(seed, 1, np.arange(n), P, L, 0)
-        prio_ref = orc.priorities(seed, 1, np.arange(n))
-        _, glists, gprio = p.round_state()
-        assert np.array_equal(glists.cpu().numpy().astype(np.int64), lists_all)
-        assert np.array_equal(_u32(gprio), prio_ref)
-        lens, ref_rows = orc.conflict_rows(enc, lists_all, rows)
+        # the oracle draws every priority and list itself; round-local ids
+        # are ranks in the coloring order
+        order, enc_r, lists_r = _ranked(p, orc, chars, seed, P, L)
+        _, glists, _ = p.round_state()
+        assert np.array_equal(glists.cpu().numpy().astype(np.int64), lists_r)
+        lens, ref_rows = orc.conflict_rows(enc_r, lists_r, rows)
         for i, u in enumerate(rows):
             got = col[off[u]:off[u + 1]].cpu().numpy()
             assert np.array_equal(got, ref_rows[i])
         p.color()
         c1 = p.colors().cpu().numpy()
-        prio = prio_ref.astype(np.uint64)
-        # first fit in priority order at every sampled vertex
+        # first fit in coloring order at every sampled vertex
         for i, u in enumerate(rows):
-            nb = ref_rows[i]
-            key_u = (int(prio[u]) << 32) | int(u)
-            earlier = [v for v in nb if ((int(prio[v]) << 32) | int(v)) < key_u]
-            taken = {int(c1[v]) for v in earlier if c1[v] >= 0}
-            want = next((int(c) for c in lists_all[u] if int(c) not in taken), -1)
-            assert int(c1[u]) == want
+            earlier = [v for v in ref_rows[i] if v < u]
+            taken = {int(c1[order[v]]) for v in earlier if c1[order[v]] >= 0}
+            want = next((int(c) for c in lists_r[u] if int(c) not in taken), -1)
+            assert int(c1[order[u]]) == want
         p.carry()
         colors, rounds = p.run()
         colors = colors.cpu().numpy()
