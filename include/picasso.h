@@ -81,8 +81,16 @@ typedef struct {
   int64_t byte_budget;   /* max bytes of one round's conflict CSR, 8 (n_l + 1)
                             + 4 nnz; 0 = no limit                            */
   int32_t color_algo;    /* picasso_color_algo                                */
-  int32_t reserved;
+  int32_t csr_form;      /* picasso_csr_form                                  */
 } picasso_config;
+
+/* Which half of G_c the conflict CSR stores.  The coloring step only reads a
+ * vertex's earlier neighbours, so EARLIER (the default) keeps each pair once,
+ * at its later endpoint, and halves the CSR; FULL keeps both directions.   */
+typedef enum {
+  PICASSO_CSR_EARLIER = 0, /* row u: neighbours ranked before u              */
+  PICASSO_CSR_FULL = 1     /* row u: all neighbours                          */
+} picasso_csr_form;
 
 /* Coloring strategy (same colors either way). */
 typedef enum {
@@ -95,10 +103,12 @@ typedef enum {
  * the r-th of the round's coloring order, ascending (priority, global id)
  * (picasso_get_round maps them to global ids).  Rows are color-major: row u
  * lists, for each color c of u's list in ascending order (its "run"), the
- * neighbours v that also hold c, ascending in v.  An edge of G_c whose two
- * lists share m colors appears in m runs of each of its rows, so nnz =
- * 2 * sum over edges of m (2|E_c| when no pair shares two colors); the run
- * of c is exactly what the coloring step needs to test color c.            */
+ * neighbours v that also hold c, ascending in v -- with cfg.csr_form EARLIER
+ * only those with v < u, with FULL all of them.  An edge of G_c whose two
+ * lists share m colors appears in m runs of its row(s), so nnz = sum over
+ * edges of m (EARLIER) or twice that (FULL); that is |E_c| (2|E_c|) when no
+ * pair shares two colors.  The run of c is what the coloring step reads to
+ * test color c.                                                             */
 typedef struct {
   const int64_t* d_off; /* [n_rows + 1]                                      */
   const int32_t* d_col; /* [nnz]                                             */

@@ -446,6 +446,7 @@ int build_conflicts(Ctx* c) {
   a.ent_v = c->ent_v;
   a.cnt = cnt;
   a.err = c->d_err;
+  a.lower = c->cfg.csr_form == PICASSO_CSR_EARLIER ? 1 : 0;
 
   if (algo == PICASSO_CONFLICT_BUCKET) {
     TRYC(launch_scan_u32(bcount, P, boff, tmp, s));
@@ -458,7 +459,7 @@ int build_conflicts(Ctx* c) {
     // mask words: bucket c holds nwb x nwb blocks of 32 words, nwb = ceil(s_c / 32)
     TRY(alloc(c, &words, P));
     TRY(alloc(c, &moff, P + 1));
-    TRYC(launch_bucket_words(bcount, P, words, s));
+    TRYC(launch_bucket_words(bcount, P, a.lower, words, s));
     TRYC(launch_scan_u32(words, P, moff, tmp, s));
     TRYC(cudaMemcpyAsync(c->h_buf, moff + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     // emit work items: the 32-row blocks of every bucket
@@ -694,7 +695,7 @@ int validate_cfg(const picasso_config* cfg) {
   if (cfg->palette_num < 1 || cfg->palette_den < 1 || cfg->palette_num > (int64_t(1) << 32) ||
       cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
       cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2 ||
-      cfg->color_algo < 0 || cfg->color_algo > 1)
+      cfg->color_algo < 0 || cfg->color_algo > 1 || cfg->csr_form < 0 || cfg->csr_form > 1)
     return PICASSO_ERR_INVALID_ARG;
   return PICASSO_OK;
 }

@@ -147,6 +147,7 @@ struct ConflictArgs {
   int32_t* col;          // [nnz]                    (fill / emit pass)
   int32_t* err;          // device error word
   uint32_t* rmask;       // bucket join: run words (mask pass -> emit)
+  int32_t lower;         // 1: rows keep only neighbours with a smaller id
 };
 
 // Buckets: members of color c are bmem[boff[c] .. boff[c+1]) ascending; a
@@ -162,7 +163,8 @@ cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out
                                 unsigned long long* out64, cudaStream_t s);
 // Bucket join: mask words per bucket (k_bucket_words + scan -> moff), the
 // mask pass (pair tests, counts, words), then the emit pass (CSR writes).
-cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, uint32_t* words, cudaStream_t s);
+// Mask words of every bucket: nwb^2 blocks of 32 words, or nwb (nwb + 1) / 2 with lower.
+cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, int32_t lower, uint32_t* words, cudaStream_t s);
 cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
                                const int64_t* moff, int32_t smax, int32_t q, cudaStream_t s);
 cudaError_t launch_bucket_jblocks(const uint32_t* bcount, int64_t P, uint32_t* out, cudaStream_t s);

@@ -239,7 +239,9 @@ cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out
 //
 // Mask words are stored block-major: the word of member row r (block R = r/32)
 // for partners of block W is at base + (R * nwb + W) * 32 + (r % 32), so each
-// 32 x 32 block is one coalesced 128-byte line.
+// 32 x 32 block is one coalesced 128-byte line.  When rows keep only their
+// smaller-id partners (lower), only blocks W <= R exist, at base +
+// (R (R + 1) / 2 + W) * 32 + (r % 32).
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -335,7 +337,11 @@ __device__ __forceinline__ uint32_t lookup(const uint4& cw, uint32_t tab_addr) {
 //     unordered pair is tested once.
 // Per-row counts go to cnt at the member's list entry (the run of this
 // bucket's color in the member's row).
-template <int QW>
+__device__ __forceinline__ int mask_block(bool lower, int R, int W, int nwb) {
+  return lower ? R * (R + 1) / 2 + W : R * nwb + W;
+}
+
+template <int QW, bool LOWER>
 __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a, const int64_t* __restrict__ boff,
                                                               const int32_t* __restrict__ bmem,
                                                               const int64_t* __restrict__ moff, int smax) {
@@ -406,10 +412,11 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       const uint32_t anti = lookup<QW>(cwj, tab_addr);
       const uint32_t rows_ok = s - ib >= 32 ? 0xffffffffu : ((1u << (s - ib)) - 1u);
       uint32_t cw = jv ? (~anti & rows_ok) : 0u;
-      if (I == J) cw &= ~(1u << lane);
-      rmb[(J * nwb + I) * 32 + lane] = cw;
+      // the diagonal block: no self pair; lower rows keep smaller partners
+      if (I == J) cw &= LOWER ? ((1u << lane) - 1u) : ~(1u << lane);
+      rmb[mask_block(LOWER, J, I, nwb) * 32 + lane] = cw;
       if (cw) atomicAdd(&cnt[j], __popc(cw));
-      if (I != J) {
+      if (!LOWER && I != J) {
         const uint32_t tr = transpose32(cw, lane);
         rmb[(I * nwb + J) * 32 + lane] = tr;
         if (tr) atomicAdd(&cnt[ib + lane], __popc(tr));
@@ -430,7 +437,8 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   smax = max(smax, 1);
   const size_t bytes = mask_smem_bytes(smax);
-  auto kern = q <= 32 ? k_bucket_mask<1> : k_bucket_mask<2>;
+  auto kern = q <= 32 ? (a.lower ? k_bucket_mask<1, true> : k_bucket_mask<1, false>)
+                      : (a.lower ? k_bucket_mask<2, true> : k_bucket_mask<2, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -445,18 +453,20 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
   return cudaGetLastError();
 }
 
-// Mask words of bucket c: nwb x nwb blocks of 32 words, nwb = ceil(s_c / 32).
-__global__ void k_bucket_words(const uint32_t* __restrict__ bcount, int64_t P, uint32_t* __restrict__ words) {
+// Mask words of bucket c: nwb x nwb blocks of 32 words (nwb (nwb + 1) / 2
+// with lower), nwb = ceil(s_c / 32).
+__global__ void k_bucket_words(const uint32_t* __restrict__ bcount, int64_t P, int32_t lower,
+                               uint32_t* __restrict__ words) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b < P) {
     const uint32_t nwb = (bcount[b] + 31u) >> 5;
-    words[b] = nwb * nwb * 32u;
+    words[b] = (lower ? nwb * (nwb + 1) / 2 : nwb * nwb) * 32u;
   }
 }
 
-cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, uint32_t* words, cudaStream_t s) {
+cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, int32_t lower, uint32_t* words, cudaStream_t s) {
   if (P <= 0) return cudaSuccess;
-  k_bucket_words<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(bcount, P, words);
+  k_bucket_words<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(bcount, P, lower, words);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -544,14 +554,16 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
     const int r = (J << 5) + lane;
     int64_t rc = r < s ? a.runoff[bmem[o + r]] : 0;  // lane r: row r's cursor
     const int nrows = min(32, s - (J << 5));
-    for (int I0 = 0; I0 < nwb; I0 += kEmitChunk) {
-      const int nI = min(kEmitChunk, nwb - I0);
+    const int nwr = a.lower ? J + 1 : nwb;  // partner blocks of these rows
+    const int blk0 = a.lower ? J * (J + 1) / 2 : J * nwb;
+    for (int I0 = 0; I0 < nwr; I0 += kEmitChunk) {
+      const int nI = min(kEmitChunk, nwr - I0);
       int32_t pv[kEmitChunk];
 #pragma unroll
       for (int t = 0; t < kEmitChunk; ++t) {
         pv[t] = 0;
         if (t < nI) {
-          wbuf[t * 32 + lane] = __ldg(rmb + (J * nwb + I0 + t) * 32 + lane);
+          wbuf[t * 32 + lane] = __ldg(rmb + (blk0 + I0 + t) * 32 + lane);
           const int pi = ((I0 + t) << 5) + lane;
           if (pi < s) {
             const int32_t f = __ldg(bmem + o + pi);
@@ -641,11 +653,12 @@ __global__ void __launch_bounds__(kApWarps * 32) k_allpairs(ConflictArgs a) {
     }
     __syncwarp();
     const uint64_t xu = a.xz[2 * u], zu = a.xz[2 * u + 1];
-    for (int64_t v0 = 0; v0 < a.n; v0 += 32) {
+    const int64_t vend = a.lower ? u : a.n;  // lower rows: partners v < u only
+    for (int64_t v0 = 0; v0 < vend; v0 += 32) {
       const int64_t v = v0 + lane;
       const int32_t* lv = nullptr;
       int Lv = 0, i = 0, j = 0, k = kNoShare;
-      if (v < a.n && v != u && commute1(xu, zu, a.xz[2 * v], a.xz[2 * v + 1])) {
+      if (v < vend && v != u && commute1(xu, zu, a.xz[2 * v], a.xz[2 * v + 1])) {
         lv = a.lists + a.loff[v];
         Lv = (int)(a.loff[v + 1] - a.loff[v]);
         k = next_shared(rl, Lu, lv, Lv, i, j);

@@ -17,6 +17,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "picasso.h")
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_INTERNAL, ERR_UNSUPPORTED, ERR_STATE = range(9)
 ALGOS = {"auto": 0, "allpairs": 1, "bucket": 2}
 COLOR_ALGOS = {"auto": 0, "sweep": 1}
+CSR_FORMS = {"earlier": 0, "full": 1}
 
 
 class PicassoError(RuntimeError):
@@ -36,7 +37,7 @@ class Config(ctypes.Structure):
         ("max_rounds", ctypes.c_int32),
         ("byte_budget", ctypes.c_int64),
         ("color_algo", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("csr_form", ctypes.c_int32),
     ]
 
 
@@ -205,7 +206,7 @@ class Picasso:
 
     def __init__(self, xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
                  algo: str = "auto", max_rounds: int = 100000, byte_budget: int = 0, stream=None,
-                 color: str = "auto", set_offsets=None, seeds=None):
+                 color: str = "auto", set_offsets=None, seeds=None, csr: str = "earlier"):
         """One set, or with ``set_offsets`` (host, nsets + 1 ints) a batch of
         independent sets stored back to back in ``xz`` (seeds default to
         seed + k)."""
@@ -224,6 +225,7 @@ class Picasso:
         cfg.max_rounds = max_rounds
         cfg.byte_budget = byte_budget
         cfg.color_algo = COLOR_ALGOS[color]
+        cfg.csr_form = CSR_FORMS[csr]
         self.cfg = cfg
         h = ctypes.c_void_p()
         if set_offsets is None:

@@ -89,29 +89,42 @@ def _ranked(p, orc, chars, seed, P, L):
     return order, enc, lists
 
 
+def _lower(off, col):
+    """Rows restricted to smaller partners (the EARLIER form of the CSR)."""
+    n = len(off) - 1
+    rows = [col[off[u]:off[u + 1]] for u in range(n)]
+    rows = [r[r < u] for u, r in enumerate(rows)]
+    lo = np.zeros(n + 1, dtype=np.int64)
+    lo[1:] = np.cumsum([len(r) for r in rows])
+    return lo, (np.concatenate(rows) if n else np.zeros(0, np.int32)).astype(np.int32)
+
+
 def _check_build(pc, orc, chars, seed, P, L, algo):
     n = len(chars)
-    with pc.Picasso(_xz(pc, chars), chars.shape[1], seed=seed, algo=algo) as p:
-        p.assign_lists(P, L, 0)
-        _, enc, lists = _ranked(p, orc, chars, seed, P, L)
-        off_r, col_r = orc.conflict_csr(enc, lists)
-        n_rows, nnz = p.build_conflicts()
-        assert (n_rows, nnz) == (n, len(col_r))
-        off, col = p.csr()
-        assert np.array_equal(off.cpu().numpy(), off_r)
-        assert np.array_equal(col.cpu().numpy(), col_r)
-        runoff = p.runs().cpu().numpy()
-        # run k of row u holds exactly the commuting neighbours that hold c_k
-        for u in range(n):
-            assert runoff[u * L] == off_r[u]
-            if u < 150:
-                for k in range(L):
-                    seg = col_r[runoff[u * L + k]:runoff[u * L + k + 1]]
-                    assert all(lists[u][k] in lists[v] for v in seg)
-                    assert np.all(np.diff(seg) > 0)
-        assert runoff[-1] == len(col_r)
-        st = p.stats()
-        assert st["conflict_algo_used"] == pc.ALGOS[algo] or algo == "auto"
+    for form in ("full", "earlier"):
+        with pc.Picasso(_xz(pc, chars), chars.shape[1], seed=seed, algo=algo, csr=form) as p:
+            p.assign_lists(P, L, 0)
+            _, enc, lists = _ranked(p, orc, chars, seed, P, L)
+            off_r, col_r = orc.conflict_csr(enc, lists)
+            if form == "earlier":
+                off_r, col_r = _lower(off_r, col_r)
+            n_rows, nnz = p.build_conflicts()
+            assert (n_rows, nnz) == (n, len(col_r))
+            off, col = p.csr()
+            assert np.array_equal(off.cpu().numpy(), off_r)
+            assert np.array_equal(col.cpu().numpy(), col_r)
+            runoff = p.runs().cpu().numpy()
+            # run k of row u holds exactly the commuting neighbours that hold c_k
+            for u in range(n):
+                assert runoff[u * L] == off_r[u]
+                if u < 150:
+                    for k in range(L):
+                        seg = col_r[runoff[u * L + k]:runoff[u * L + k + 1]]
+                        assert all(lists[u][k] in lists[v] for v in seg)
+                        assert np.all(np.diff(seg) > 0)
+            assert runoff[-1] == len(col_r)
+            st = p.stats()
+            assert st["conflict_algo_used"] == pc.ALGOS[algo] or algo == "auto"
 
 
 @pytest.mark.parametrize("algo", ["allpairs", "bucket"])
@@ -281,7 +294,7 @@ def _full_size(pc, orc, n, q, p_w, num, den, alpha, seed, samples):
         lens, ref_rows = orc.conflict_rows(enc_r, lists_r, rows)
         for i, u in enumerate(rows):
             got = col[off[u]:off[u + 1]].cpu().numpy()
-            assert np.array_equal(got, ref_rows[i])
+            assert np.array_equal(got, ref_rows[i][ref_rows[i] < u])  # the EARLIER form
         p.color()
         c1 = p.colors().cpu().numpy()
         # first fit in coloring order at every sampled vertex
