@@ -33,8 +33,8 @@ N_DEFAULT, Q, P_W, NUM, DEN, ALPHA = 1_000_000, 64, 0.25, 1, 16, 1.5
 # DRAM bytes (read + write) per unit of work, from one ncu capture of each kernel on
 # round 1 of the n = 200,000 case of this workload (the bench's launches are too
 # large to capture); scaled here by the units each launch processes.
-MASK_DRAM_BYTES_PER_PAIR = 0.2415   # k_bucket_mask, per tested pair
-EMIT_DRAM_BYTES_PER_ENTRY = 5.03    # k_bucket_emit, per CSR run entry
+MASK_DRAM_BYTES_PER_PAIR = 0.132    # k_bucket_mask, per tested pair
+EMIT_DRAM_BYTES_PER_ENTRY = 5.42   # k_bucket_emit, per CSR run entry
 METRIC = "pair tests/s (conflict build) and colored strings/s at n=1M; colors, peak bytes"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
