@@ -230,10 +230,12 @@ def run_gpu(args):
     st = stats[-1]
     # the library's counters are per context and there is one context per step
     per_step = {k: st[k] for k in ("t_assign_ms", "t_build_ms", "t_color_ms", "t_carry_ms", "t_pairs_ms",
-                                   "t_emit_ms")}
+                                   "t_emit_ms", "t_small_ms", "small_rounds", "small_stops")}
     steps_ms = ms / args.steps
     value = world * n / (steps_ms / 1e3)
-    pair_rate = st["logical_pairs"] / (st["t_build_ms"] / 1e3)
+    # the small-round engine's time includes its coloring: counted as build
+    # time here, which understates the pair rate
+    pair_rate = st["logical_pairs"] / ((st["t_build_ms"] + st["t_small_ms"]) / 1e3)
 
     peaks, peak_src = measured_peaks()
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2032.0)

@@ -82,6 +82,8 @@ typedef struct {
                             + 4 nnz; 0 = no limit                            */
   int32_t color_algo;    /* picasso_color_algo                                */
   int32_t csr_form;      /* picasso_csr_form                                  */
+  int32_t small_engine;  /* picasso_small_engine                              */
+  int32_t reserved;      /* must be 0                                         */
 } picasso_config;
 
 /* Which half of G_c the conflict CSR stores.  The coloring step only reads a
@@ -91,6 +93,18 @@ typedef enum {
   PICASSO_CSR_EARLIER = 0, /* row u: neighbours ranked before u              */
   PICASSO_CSR_FULL = 1     /* row u: all neighbours                          */
 } picasso_csr_form;
+
+/* picasso_run on a single set hands the remaining rounds to one cooperative
+ * launch (the small-round engine) once a round has at most 16384 vertices,
+ * at most 4096 palette colors and lists of at most 64 colors, under the
+ * defaults AUTO / EARLIER / AUTO coloring.  The engine runs the same rounds
+ * as picasso_round (same lists, CSR and colors) without a host round trip
+ * per round; a round it cannot finish (CSR over its buffer or the byte
+ * budget, a bounded wait that ran out) goes back to the per-round path.   */
+typedef enum {
+  PICASSO_SMALL_AUTO = 0,
+  PICASSO_SMALL_OFF = 1
+} picasso_small_engine;
 
 /* Coloring strategy (same colors either way). */
 typedef enum {
@@ -157,6 +171,9 @@ typedef struct {
   int32_t sweep_pending[64];
   int32_t sweep_active[64];
   float sweep_us[64];
+  int32_t small_rounds;       /* rounds the small-round engine ran          */
+  int32_t small_stops;        /* engine launches that handed a round back   */
+  double t_small_ms;          /* time in the small-round engine             */
 } picasso_stats;
 
 /* Fill *cfg with the defaults: seed 0, P = n/8, alpha = 2 (the paper's normal

@@ -131,6 +131,12 @@ struct Ctx {
   double t_assign = 0, t_build = 0, t_color = 0, t_carry = 0, t_pairs = 0, t_emit = 0;
   int64_t pairs_launches = 0, logical_pairs = 0, tested_pairs = 0, emit_launches = 0, emit_bytes = 0;
   int64_t nnz_total = 0;
+  // small-round engine: rounds run, launches that handed a round back, the
+  // round it handed back last (the per-round path takes that one); after a
+  // CSR overflow the engine stays off for the context
+  int32_t small_rounds = 0, small_stops = 0, small_skip_round = 0;
+  bool small_off = false;
+  double t_small = 0;
 
   const uint64_t* round_xz() const { return xz ? xz : xz_user; }
 };
@@ -691,11 +697,234 @@ int carry_round(Ctx* c) {
   return PICASSO_OK;
 }
 
+// Whether picasso_run hands the remaining rounds to the small-round engine.
+bool small_eligible(const Ctx* c) {
+  const picasso_config& cfg = c->cfg;
+  if (c->nsets != 1 || c->n < 1 || c->n > kSmallRoundsMax || cfg.small_engine != PICASSO_SMALL_AUTO) return false;
+  if (cfg.conflict_algo != PICASSO_CONFLICT_AUTO || cfg.color_algo != PICASSO_COLOR_AUTO ||
+      cfg.csr_form != PICASSO_CSR_EARLIER)
+    return false;
+  if (c->small_off || c->round == c->small_skip_round || c->round > cfg.max_rounds) return false;
+  int64_t P;
+  int32_t L;
+  params_for(cfg, c->n, &P, &L);
+  if (L > kSmallLCap || c->n * (int64_t)L > kSmallMeanBucket * P) return false;
+  // every color the engine can hand out still fits an int32 (the per-round
+  // path checks base + P each round)
+  const int64_t rounds_left = (int64_t)cfg.max_rounds - c->round + 1;
+  return c->set_base[0] + rounds_left * P <= (int64_t)0x7fffffff;
+}
+
+// The remaining rounds in one cooperative launch (kernels_small.cu); on
+// return the context stands between rounds, at the round the engine stopped
+// at (no vertex left, the round limit, or a round handed back).
+int run_small(Ctx* c) {
+  const int64_t n0 = c->n;
+  cudaStream_t s = c->s;
+  int64_t P0;
+  int32_t L0;
+  params_for(c->cfg, n0, &P0, &L0);
+  std::vector<int2> ptab((size_t)n0 + 1);
+  ptab[0] = make_int2(0, 0);
+  for (int64_t m = 1; m <= n0; ++m) {
+    int64_t P;
+    int32_t L;
+    params_for(c->cfg, m, &P, &L);
+    ptab[m] = make_int2((int)P, L);
+  }
+  // column capacity: the expected run entries of the first round if every
+  // pair commuted, n0 (n0 - 1) / 2 pairs sharing L0^2 / P0 colors on
+  // average, plus slack; a round above it goes back to the per-round path
+  const double pairs = 0.5 * (double)n0 * (double)(n0 - 1);
+  const int64_t cap = std::max<int64_t>(int64_t(1) << 22, (int64_t)(pairs * L0 * (double)L0 / (double)P0) +
+                                                               (int64_t(1) << 20));
+  constexpr int kPartCap = 2048;
+  const int64_t E0 = n0 * (int64_t)L0;
+  SmallArgs a{};
+  int2* d_ptab = nullptr;
+  int32_t *gid_a = nullptr, *gid_b = nullptr, *perm = nullptr, *gid_r = nullptr, *lists = nullptr, *col = nullptr;
+  int32_t *err = nullptr, *bmem = nullptr, *brank = nullptr, *ibkt = nullptr;
+  uint64_t* bxz = nullptr;
+  uint32_t* bitems = nullptr;
+  int64_t* iboff = nullptr;
+  uint64_t *xz_r = nullptr, *state = nullptr, *key = nullptr;
+  int64_t *loff = nullptr, *runoff = nullptr, *pos = nullptr, *part = nullptr, *ctl = nullptr, *boff = nullptr;
+  uint32_t *cnt = nullptr, *flag = nullptr, *bcnt = nullptr, *bcur = nullptr;
+  int st = PICASSO_OK;
+  auto cleanup = [&]() {
+    release(c, &d_ptab);
+    release(c, &gid_a);
+    release(c, &gid_b);
+    release(c, &perm);
+    release(c, &gid_r);
+    release(c, &lists);
+    release(c, &col);
+    release(c, &err);
+    release(c, &xz_r);
+    release(c, &state);
+    release(c, &key);
+    release(c, &loff);
+    release(c, &runoff);
+    release(c, &pos);
+    release(c, &part);
+    release(c, &ctl);
+    release(c, &cnt);
+    release(c, &flag);
+    release(c, &bcnt);
+    release(c, &bcur);
+    release(c, &boff);
+    release(c, &bmem);
+    release(c, &brank);
+    release(c, &ibkt);
+    release(c, &bxz);
+    release(c, &bitems);
+    release(c, &iboff);
+  };
+#define TRY(expr)           \
+  do {                      \
+    st = (expr);            \
+    if (st != PICASSO_OK) { \
+      cleanup();            \
+      return st;            \
+    }                       \
+  } while (0)
+#define TRYC(expr)                                \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) {                      \
+      st = map_err(_e);                           \
+      if (st == PICASSO_ERR_CUDA) c->sticky = st; \
+      cleanup();                                  \
+      return st;                                  \
+    }                                             \
+  } while (0)
+  TRY(alloc(c, &d_ptab, n0 + 1));
+  TRY(alloc(c, &gid_a, n0));
+  TRY(alloc(c, &gid_b, n0));
+  TRY(alloc(c, &perm, n0));
+  TRY(alloc(c, &gid_r, n0));
+  TRY(alloc(c, &xz_r, 2 * n0));
+  TRY(alloc(c, &lists, E0));
+  TRY(alloc(c, &loff, n0 + 1));
+  TRY(alloc(c, &cnt, E0));
+  TRY(alloc(c, &runoff, E0 + 1));
+  TRY(alloc(c, &col, cap));
+  TRY(alloc(c, &state, n0));
+  TRY(alloc(c, &flag, n0));
+  TRY(alloc(c, &pos, n0 + 1));
+  TRY(alloc(c, &key, n0));
+  TRY(alloc(c, &bcnt, P0));
+  TRY(alloc(c, &bcur, P0));
+  TRY(alloc(c, &boff, P0 + 1));
+  TRY(alloc(c, &bmem, E0));
+  TRY(alloc(c, &brank, E0));
+  TRY(alloc(c, &bxz, 2 * E0));
+  TRY(alloc(c, &bitems, P0));
+  TRY(alloc(c, &iboff, P0 + 1));
+  TRY(alloc(c, &ibkt, E0 / 32 + P0 + 1));
+  TRY(alloc(c, &part, kPartCap));
+  TRY(alloc(c, &err, 4));
+  TRY(alloc(c, &ctl, 9));
+  TRYC(cudaMemcpyAsync(d_ptab, ptab.data(), sizeof(int2) * (n0 + 1), cudaMemcpyHostToDevice, s));
+  if (c->gid)
+    TRYC(cudaMemcpyAsync(gid_a, c->gid, sizeof(int32_t) * n0, cudaMemcpyDeviceToDevice, s));
+  else
+    TRYC(launch_iota(gid_a, n0, s));
+  int64_t* h = c->h_buf;
+  std::memset(h, 0, sizeof(int64_t) * 9);
+  h[0] = n0;
+  h[3] = c->set_base[0];
+  TRYC(cudaMemcpyAsync(ctl, h, sizeof(int64_t) * 9, cudaMemcpyHostToDevice, s));
+  TRYC(cudaMemsetAsync(err, 0, sizeof(int32_t) * 4, s));
+  a.n0 = n0;
+  a.round0 = c->round;
+  a.max_rounds = c->cfg.max_rounds;
+  a.seed = c->seed[0];
+  a.ptab = d_ptab;
+  a.cap = cap;
+  a.budget = c->cfg.byte_budget;
+  a.xz = c->xz_user;
+  a.gid_a = gid_a;
+  a.gid_b = gid_b;
+  a.perm = perm;
+  a.gid_r = gid_r;
+  a.xz_r = xz_r;
+  a.lists = lists;
+  a.loff = loff;
+  a.cnt = cnt;
+  a.runoff = runoff;
+  a.col = col;
+  a.state = state;
+  a.flag = flag;
+  a.pos = pos;
+  a.color = c->color;
+  a.key = key;
+  a.bcnt = bcnt;
+  a.bcur = bcur;
+  a.boff = boff;
+  a.bmem = bmem;
+  a.brank = brank;
+  a.bxz = bxz;
+  a.bitems = bitems;
+  a.iboff = iboff;
+  a.ibkt = ibkt;
+  a.part = part;
+  a.err = err;
+  a.ctl = ctl;
+  TRYC(launch_small_rounds(a, kPartCap, s));
+  TRYC(cudaMemcpyAsync(h, ctl, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, s));
+  TRYC(cudaStreamSynchronize(s));
+  const int64_t nleft = h[0], rounds = h[1], stop = h[2], base = h[3], parity = h[4];
+  const int64_t max_nnz = h[5], sum_nnz = h[6], sum_pairs = h[7];
+  // V_l of the round the engine stopped at, and its words
+  int32_t* gid2 = nullptr;
+  uint64_t* xz2 = nullptr;
+  if (nleft > 0) {
+    TRY(alloc(c, &gid2, nleft));
+    st = alloc(c, &xz2, 2 * nleft);
+    if (st != PICASSO_OK) {
+      release(c, &gid2);
+      cleanup();
+      return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(gid2, parity ? gid_b : gid_a, sizeof(int32_t) * nleft, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = launch_gather_xz(c->xz_user, gid2, nleft, xz2, s);
+    if (e != cudaSuccess) {
+      release(c, &gid2);
+      release(c, &xz2);
+    }
+    TRYC(e);
+  }
+  release(c, &c->gid);
+  release(c, &c->xz);
+  c->gid = gid2;
+  c->xz = xz2;
+  c->n = nleft;
+  c->remaining[0] = nleft;
+  c->round += (int32_t)rounds;
+  c->rounds_done += (int32_t)rounds;
+  c->set_base[0] = base;
+  c->small_rounds += (int32_t)rounds;
+  c->nnz_total += sum_nnz;
+  c->logical_pairs += sum_pairs;
+  if (rounds > 0) c->set_peak_bytes[0] = std::max(c->set_peak_bytes[0], max_nnz);
+  if (stop == kSmallTimeout || stop == kSmallOverflow) {
+    c->small_stops += 1;
+    c->small_skip_round = c->round;
+    c->small_off = stop == kSmallOverflow;
+  }
+  cleanup();
+#undef TRY
+#undef TRYC
+  return PICASSO_OK;
+}
+
 int validate_cfg(const picasso_config* cfg) {
   if (cfg->palette_num < 1 || cfg->palette_den < 1 || cfg->palette_num > (int64_t(1) << 32) ||
       cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
       cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2 ||
-      cfg->color_algo < 0 || cfg->color_algo > 1 || cfg->csr_form < 0 || cfg->csr_form > 1)
+      cfg->color_algo < 0 || cfg->color_algo > 1 || cfg->csr_form < 0 || cfg->csr_form > 1 ||
+      cfg->small_engine < 0 || cfg->small_engine > 1 || cfg->reserved != 0)
     return PICASSO_ERR_INVALID_ARG;
   return PICASSO_OK;
 }
@@ -905,6 +1134,12 @@ int picasso_run(void* ctx, int32_t* d_color_out, int32_t* n_rounds) {
   ST(check(c));
   while (c->n > 0) {
     if (c->round > c->cfg.max_rounds) return PICASSO_ERR_INTERNAL;
+    if (small_eligible(c)) {
+      phase_begin(c);
+      ST(run_small(c));
+      CK(phase_end(c, &c->t_small));
+      continue;
+    }
     ST(picasso_round(ctx, nullptr));
   }
   if (d_color_out) ST(picasso_get_colors(ctx, d_color_out));
@@ -999,6 +1234,9 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->emit_launches = c->emit_launches;
   out->emit_bytes = c->emit_bytes;
   out->nnz_total = c->nnz_total;
+  out->small_rounds = c->small_rounds;
+  out->small_stops = c->small_stops;
+  out->t_small_ms = c->t_small;
   const int ns = c->sweeps < kSweepLog ? c->sweeps : kSweepLog;
   const unsigned long long* t = reinterpret_cast<const unsigned long long*>(c->sweep_log + 8 + kSweepLog);
   for (int i = 0; i < ns; ++i) {

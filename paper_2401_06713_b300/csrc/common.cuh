@@ -74,6 +74,37 @@ __device__ __forceinline__ uint32_t pick(const u32x4& v, uint32_t i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
+// Alg. 1 assign_rand_list_colors for one vertex: Floyd's sampling of L
+// distinct values of [0, P) (Bentley & Floyd, CACM 1987): for j = P-L .. P-1
+// draw t in [0, j] (x*(j+1) >> 32 of the next Philox word of the LIST stream
+// (seed, round, g)); keep t, or j if t was already kept.  Then an insertion
+// sort; out[0..L) = cofs + the sorted values.  L <= LCAP.
+template <int LCAP>
+__device__ __forceinline__ void draw_list(uint64_t seed, int32_t round, int64_t g, int64_t P, int L, int64_t cofs,
+                                          int32_t* __restrict__ out) {
+  uint32_t sel[LCAP];
+  u32x4 blk{0, 0, 0, 0};
+  for (int m = 0; m < L; ++m) {
+    if ((m & 3) == 0) blk = philox_block(seed, round, g, kTagList, (uint32_t)(m >> 2));
+    const uint32_t x = pick(blk, (uint32_t)(m & 3));
+    const uint64_t j = (uint64_t)(P - L + m);
+    const uint32_t t = (uint32_t)(((uint64_t)x * (j + 1)) >> 32);
+    bool seen = false;
+    for (int a = 0; a < m; ++a) seen |= (sel[a] == t);
+    sel[m] = seen ? (uint32_t)j : t;
+  }
+  for (int a = 1; a < L; ++a) {
+    const uint32_t key = sel[a];
+    int b = a - 1;
+    while (b >= 0 && sel[b] > key) {
+      sel[b + 1] = sel[b];
+      --b;
+    }
+    sel[b + 1] = key;
+  }
+  for (int a = 0; a < L; ++a) out[a] = (int32_t)(cofs + sel[a]);
+}
+
 // Symplectic commutation test for one-word strings.
 __device__ __forceinline__ bool commute1(uint64_t xu, uint64_t zu, uint64_t xv, uint64_t zv) {
   return (__popcll((xu & zv) ^ (zu & xv)) & 1) == 0;
@@ -242,6 +273,64 @@ cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t
 cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int32_t* gid, int64_t n,
                                  const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s);
 cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s);
+
+// Small-round engine (kernels_small.cu): every remaining round of a single
+// set in one cooperative launch once the round has at most kSmallRoundsMax
+// vertices and lists of at most kSmallLCap colors, and its color buckets
+// are small (mean n L / P at most kSmallMeanBucket; a bucket above
+// kSmallBucketCap stops the engine).  ctl[0..4] hold the engine's position between rounds
+// (host-initialised); the launch returns with ctl[2] = kSmallOk when no
+// vertex is left, or with the reason it stopped at the start of a round it
+// did not finish (that round's vertex list intact, none of its colors
+// written).
+constexpr int64_t kSmallRoundsMax = 16384;
+constexpr int kSmallLCap = 64;
+constexpr int kSmallBucketCap = 512;  // largest color bucket
+constexpr int kSmallMeanBucket = 320; // a round joins only if n L <= this * P
+struct SmallArgs {
+  int64_t n0;             // vertices when the engine starts
+  int32_t round0;         // number of the first round it runs
+  int32_t max_rounds;     // last round number it may run
+  uint64_t seed;          // the set's Philox key
+  const int2* ptab;       // [n0 + 1]: (P, L) of a round with m vertices
+  int64_t cap;            // CSR entries the col buffer holds
+  int64_t budget;         // byte budget of one round's CSR (0: none)
+  const uint64_t* xz;     // [N][2] all strings
+  int32_t* gid_a;         // [n0] V_l in ascending global id (ping-pong)
+  int32_t* gid_b;         // [n0]
+  int32_t* perm;          // [n0] rank -> place in V_l
+  int32_t* gid_r;         // [n0] rank -> global id
+  uint64_t* xz_r;         // [2 n0] words in rank order
+  int32_t* lists;         // [n0 * L]
+  int64_t* loff;          // [n0 + 1]
+  uint32_t* cnt;          // [n0 * L]
+  int64_t* runoff;        // [n0 * L + 1]
+  int32_t* col;           // [cap]
+  uint64_t* state;        // [n0]
+  uint32_t* flag;         // [n0] in V_l order
+  int64_t* pos;           // [n0 + 1]
+  int32_t* color;         // [N] global colors
+  uint64_t* key;          // [n0] (priority, global id) in V_l order
+  uint32_t* bcnt;         // [P0] bucket sizes
+  uint32_t* bcur;         // [P0] bucket fill cursors
+  int64_t* boff;          // [P0 + 1] bucket offsets
+  uint32_t* bitems;       // [P0] work items of a bucket, ceil(s_c / 32)
+  int64_t* iboff;         // [P0 + 1] their prefix
+  int32_t* ibkt;          // [n0 L / 32 + P0] bucket of every work item
+  int32_t* bmem;          // [n0 * L] bucket members: list-entry index,
+  int32_t* brank;         // [n0 * L]   rank,
+  uint64_t* bxz;          // [2 n0 L]   words
+  int64_t* part;          // [gridDim.x] block sums of the grid scans
+  int32_t* err;           // [4]: 0 ordered-pass poll timeout, 1 work counter, 2 bucket over the cap
+  int64_t* ctl;           // [9]: 0 n, 1 rounds done, 2 stop reason, 3 base, 4 V_l in gid_b,
+                          //      5 largest CSR bytes 8 (n + 1) + 4 nnz, 6 sum of nnz,
+                          //      7 sum of n (n - 1) / 2 (5..7 zero on entry), 8 scratch
+};
+
+// Stop reasons in ctl[2].
+constexpr int64_t kSmallOk = 0, kSmallTimeout = 1, kSmallOverflow = 2, kSmallMaxRounds = 3;
+// part_cap: words of a.part; the launch uses at most that many blocks.
+cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, cudaStream_t s);
 
 // Parameter predictor and instance features (kernels_mlp.cu).
 int mlp_param_count();

@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "color_device.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -111,11 +112,6 @@ cudaError_t launch_color_init(const ColorArgs& a, const uint32_t* prio, int32_t*
   return cudaGetLastError();
 }
 
-// Publish a new state word (the low half of the 64-bit state; the priority
-// in the high half never changes).
-__device__ __forceinline__ void publish(uint64_t* state, int32_t v, uint32_t w) {
-  __stcg(reinterpret_cast<uint32_t*>(state + v), w);
-}
 
 // ---------------------------------------------------------------------------
 // Evaluation of one vertex by one warp: advance past blocked candidates, then
@@ -283,169 +279,13 @@ __global__ void __launch_bounds__(256, 4) k_color_all(ColorArgs a, int32_t* __re
   }
 }
 
-// ---------------------------------------------------------------------------
-// Ordered persistent coloring.  `order` lists the round's vertices in exact
-// coloring order; warp w takes positions w, w + W, w + 2W, ... (W = warps in
-// the grid).  A vertex that has to wait polls the neighbour holding it up
-// instead of leaving for a later sweep.  No deadlock: the earliest unfinished
-// position's warp is working on it (all its earlier positions are done), and
-// that vertex waits only on earlier positions, which are finished; the
-// cooperative launch guarantees every warp is resident.  A poll budget
-// bounds every wait: when it runs out the kernel sets *err = 1 and the warp
-// returns; the caller then recolors the round with the sweep kernel.
-// ---------------------------------------------------------------------------
-constexpr int kMaxPolls = 1 << 20;
-
-constexpr int kOrderedGroup = 2;  // run chunks of 32 whose loads are in flight together
-constexpr int kCandBatch = 2;     // candidates whose first run chunk is screened together
-
-// Scan the run [rs, rs + ntot) of candidate c to the end: true if an earlier
-// neighbour took c; waits (bounded) on earlier neighbours still undecided at
-// or below c.  *fail is set when a wait runs out.
-__device__ __forceinline__ bool run_blocked(const ColorArgs& a, int32_t v, uint32_t pv, uint32_t c, int64_t rs,
-                                            int64_t ntot, int lane, int& polls, bool* fail) {
-  for (int64_t e0 = 0; e0 < ntot;) {
-    int32_t u[kOrderedGroup];
-    uint64_t su[kOrderedGroup];
-    bool past = false;  // ranked ids: a later neighbour ends the prefix
-#pragma unroll
-    for (int j = 0; j < kOrderedGroup; ++j) {
-      const int64_t e = e0 + 32 * j + lane;
-      u[j] = e < ntot ? __ldg(a.col + rs + e) : -1;
-      if (a.ranked && u[j] > v) {
-        u[j] = -1;
-        past = true;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kOrderedGroup; ++j) su[j] = u[j] >= 0 ? __ldcg(&a.state[u[j]]) : 0ull;
-    bool lb = false;
-    uint32_t wm[kOrderedGroup];
-#pragma unroll
-    for (int j = 0; j < kOrderedGroup; ++j) {
-      bool lw = false;
-      if (u[j] >= 0) {
-        const uint32_t pu = (uint32_t)(su[j] >> 32);
-        if (a.ranked || pu < pv || (pu == pv && u[j] < v)) {
-          const uint32_t wu = (uint32_t)su[j], st = wu & 3u, cu = wu >> 2;
-          lb = lb || (st == kColored && cu == c);
-          lw = st == kUndecided && cu <= c;
-        }
-      }
-      wm[j] = __ballot_sync(0xffffffffu, lw);
-    }
-    if (__any_sync(0xffffffffu, lb)) return true;
-    int jw = -1;
-#pragma unroll
-    for (int j = kOrderedGroup - 1; j >= 0; --j)
-      if (wm[j]) jw = j;
-    if (jw < 0) {
-      if (__any_sync(0xffffffffu, past)) return false;
-      e0 += 32 * kOrderedGroup;
-      continue;
-    }
-    // wait for the first neighbour holding us up, then rescan from its chunk
-    uint32_t m = 0u;
-    int32_t uw = -1;
-#pragma unroll
-    for (int j = 0; j < kOrderedGroup; ++j)
-      if (j == jw) {
-        m = wm[j];
-        uw = u[j];
-      }
-    const int32_t wu_id = __shfl_sync(0xffffffffu, uw, __ffs(m) - 1);
-    while (true) {
-      const uint32_t w = (uint32_t)__ldcg(&a.state[wu_id]);
-      if ((w & 3u) != kUndecided || (w >> 2) > c) break;
-      if (++polls > kMaxPolls) {
-        *fail = true;
-        return true;
-      }
-      __nanosleep(64);
-    }
-    e0 += 32 * jw;
-  }
-  return false;
-}
-
-// One vertex.  The run offsets and colors of 32 candidates are loaded at
-// once (lane k holds candidate k's); candidates are then screened
-// kCandBatch at a time on the first 32 entries of their runs (one round of
-// column loads and one of state loads for the batch): a candidate whose first
-// chunk shows an earlier neighbour colored with it is blocked; the first one
-// not blocked that way is settled by scanning its whole run.
-__device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
-  const int64_t row = a.loff[v];
-  const int L = (int)(a.loff[v + 1] - row);
-  const uint32_t pv = (uint32_t)(__ldcg(&a.state[v]) >> 32);
-  int polls = 0;
-  for (int kb = 0; kb < L; kb += 32) {
-    const int kl = kb + lane;
-    const int64_t my_rs = kl < L ? a.runoff[row + kl] : 0;
-    const int64_t my_re = kl < L ? a.runoff[row + kl + 1] : 0;
-    const uint32_t my_c = kl < L ? (uint32_t)a.lists[row + kl] : 0u;
-    const int kend = min(L - kb, 32);
-    for (int k0 = 0; k0 < kend; k0 += kCandBatch) {
-      int32_t u[kCandBatch];
-      uint64_t su[kCandBatch];
-#pragma unroll
-      for (int b = 0; b < kCandBatch; ++b) {
-        const int64_t rs = __shfl_sync(0xffffffffu, my_rs, min(k0 + b, 31));
-        const int64_t re = __shfl_sync(0xffffffffu, my_re, min(k0 + b, 31));
-        const int64_t e = rs + lane;
-        u[b] = (k0 + b < kend && e < re) ? __ldg(a.col + e) : -1;
-        if (a.ranked && u[b] > v) u[b] = -1;
-      }
-#pragma unroll
-      for (int b = 0; b < kCandBatch; ++b) su[b] = u[b] >= 0 ? __ldcg(&a.state[u[b]]) : 0ull;
-      uint32_t blocked_mask = 0u;
-#pragma unroll
-      for (int b = 0; b < kCandBatch; ++b) {
-        const uint32_t cb = __shfl_sync(0xffffffffu, my_c, min(k0 + b, 31));
-        bool lb = false;
-        if (u[b] >= 0) {
-          const uint32_t pu = (uint32_t)(su[b] >> 32);
-          if (a.ranked || pu < pv || (pu == pv && u[b] < v)) {
-            const uint32_t wu = (uint32_t)su[b];
-            lb = (wu & 3u) == kColored && (wu >> 2) == cb;
-          }
-        }
-        if (__any_sync(0xffffffffu, lb)) blocked_mask |= 1u << b;
-      }
-#pragma unroll
-      for (int b = 0; b < kCandBatch; ++b) {
-        const int kk = k0 + b;
-        if (kk >= kend) break;
-        if ((blocked_mask >> b) & 1u) continue;
-        // candidate kb + kk is not blocked by its first chunk: settle it
-        const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
-        const int64_t rs = __shfl_sync(0xffffffffu, my_rs, kk);
-        const int64_t re = __shfl_sync(0xffffffffu, my_re, kk);
-        if (kb + kk > 0 && lane == 0) publish(a.state, v, (c << 2) | kUndecided);
-        bool fail = false;
-        const bool blk = run_blocked(a, v, pv, c, rs, re - rs, lane, polls, &fail);
-        if (fail) {
-          if (lane == 0) atomicExch(err, 1);
-          return false;
-        }
-        if (!blk) {
-          if (lane == 0) publish(a.state, v, (c << 2) | kColored);
-          return true;
-        }
-      }
-    }
-  }
-  if (lane == 0) publish(a.state, v, (kFailedColor << 2) | kFailed);
-  return true;
-}
-
 __global__ void __launch_bounds__(256, 6) k_color_ordered(ColorArgs a, const int32_t* __restrict__ order,
                                                           int32_t* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   for (int64_t t = wid; t < a.n; t += gwarps) {
-    if (!ordered_vertex(a, order ? __ldcg(&order[t]) : (int32_t)t, lane, err)) return;
+    if (!ordered_vertex<false>(a, order ? __ldcg(&order[t]) : (int32_t)t, lane, err)) return;
   }
 }
 

@@ -23,6 +23,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "warp_sort.cuh"
 
 namespace picasso {
 
@@ -67,59 +68,6 @@ cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* b
 // l*E .. l*E+E-1, E = m/32 for the padded size m); partners closer than E
 // are in the same lane, farther ones are exchanged by shuffles.  Larger
 // buckets: one CTA per bucket, the same network in shared memory.
-constexpr int kWarpSortMax = 512;
-
-template <int E>
-__device__ __forceinline__ void warp_bitonic(int32_t (&key)[E], int lane) {
-  constexpr int m = 32 * E;
-#pragma unroll
-  for (int k = 2; k <= m; k <<= 1) {
-#pragma unroll
-    for (int d = k >> 1; d > 0; d >>= 1) {
-      if (d < E) {
-#pragma unroll
-        for (int j = 0; j < E; ++j) {
-          if ((j & d) == 0) {
-            const int i = lane * E + j;
-            const bool up = (i & k) == 0;
-            const int32_t x = key[j], y = key[j | d];
-            const bool sw = (x > y) == up;
-            key[j] = sw ? y : x;
-            key[j | d] = sw ? x : y;
-          }
-        }
-      } else {
-        const int ld = d / E;
-        const bool lower = (lane & ld) == 0;
-#pragma unroll
-        for (int j = 0; j < E; ++j) {
-          const int i = lane * E + j;
-          const bool up = (i & k) == 0;
-          const int32_t y = __shfl_xor_sync(0xffffffffu, key[j], ld);
-          // the lower element keeps the smaller key when ascending
-          key[j] = (lower == up) ? min(key[j], y) : max(key[j], y);
-        }
-      }
-    }
-  }
-}
-
-template <int E>
-__device__ __forceinline__ void warp_sort_bucket(int32_t* __restrict__ p, int s, int lane) {
-  int32_t key[E];
-#pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const int i = lane * E + j;
-    key[j] = i < s ? p[i] : 0x7fffffff;
-  }
-  warp_bitonic<E>(key, lane);
-#pragma unroll
-  for (int j = 0; j < E; ++j) {
-    const int i = lane * E + j;
-    if (i < s) p[i] = key[j];
-  }
-}
-
 __global__ void __launch_bounds__(256) k_bucket_sort_warp(const int64_t* __restrict__ boff, int64_t P,
                                                           int32_t* __restrict__ bmem) {
   const int lane = threadIdx.x & 31;

@@ -93,13 +93,8 @@ cudaError_t launch_entry_owner(const int64_t* loff, int64_t n, int32_t* ent_v, c
   return cudaGetLastError();
 }
 
-// Alg. 1 assign_rand_list_colors: one thread per vertex, with the P, L and
-// seed of the vertex's set; Philox is keyed by the set's seed and the
-// vertex's id within its set.  Floyd's sampling of L distinct values of
-// [0, P) (Bentley & Floyd, CACM 1987): for j = P-L .. P-1 draw t in [0, j]
-// (x*(j+1) >> 32 of the next Philox word); keep t, or j if t was already
-// kept.  Then an insertion sort; lists hold bucket colors (round-local color
-// + the set's offset cofs).  The priority is draw 0 of the PRIO stream.
+// Priority of each of the round's vertices: draw 0 of its set's PRIO stream
+// at the vertex's id within the set (the static Random order of Sec. III-B).
 __global__ void k_round_prio(int32_t round, const int32_t* __restrict__ gid, int64_t n,
                              const int64_t* __restrict__ soff, int nsets, const SetRound* __restrict__ sets,
                              uint32_t* __restrict__ prio) {
@@ -118,6 +113,11 @@ cudaError_t launch_round_prio(int32_t round, const int32_t* gid, int64_t n, cons
   return cudaGetLastError();
 }
 
+// Alg. 1 assign_rand_list_colors: one thread per vertex, with the P, L and
+// seed of the vertex's set; Philox is keyed by the set's seed and the
+// vertex's id within its set (draw_list: Floyd's sampling, sorted); lists
+// hold bucket colors (round-local color + the set's offset cofs).  The
+// priority is draw 0 of the PRIO stream.
 template <int LCAP>
 __global__ void k_assign_lists(int32_t round, const int32_t* __restrict__ gid, int64_t n,
                                const int64_t* __restrict__ soff, int nsets, const SetRound* __restrict__ sets,
@@ -129,30 +129,7 @@ __global__ void k_assign_lists(int32_t round, const int32_t* __restrict__ gid, i
   const int k = nsets > 1 ? set_of(soff, nsets, gg) : 0;
   const SetRound sr = sets[k];
   const int64_t g = gg - soff[k];  // id within the set
-  const int64_t P = sr.P;
-  const int L = sr.L;
-  uint32_t sel[LCAP];
-  u32x4 blk{0, 0, 0, 0};
-  for (int m = 0; m < L; ++m) {
-    if ((m & 3) == 0) blk = philox_block(sr.seed, round, g, kTagList, (uint32_t)(m >> 2));
-    const uint32_t x = pick(blk, (uint32_t)(m & 3));
-    const uint64_t j = (uint64_t)(P - L + m);
-    const uint32_t t = (uint32_t)(((uint64_t)x * (j + 1)) >> 32);
-    bool seen = false;
-    for (int a = 0; a < m; ++a) seen |= (sel[a] == t);
-    sel[m] = seen ? (uint32_t)j : t;
-  }
-  for (int a = 1; a < L; ++a) {
-    const uint32_t key = sel[a];
-    int b = a - 1;
-    while (b >= 0 && sel[b] > key) {
-      sel[b + 1] = sel[b];
-      --b;
-    }
-    sel[b + 1] = key;
-  }
-  int32_t* out = lists + loff[v];
-  for (int a = 0; a < L; ++a) out[a] = (int32_t)(sr.cofs + sel[a]);
+  draw_list<LCAP>(sr.seed, round, g, sr.P, sr.L, sr.cofs, lists + loff[v]);
   prio[v] = philox_block(sr.seed, round, g, kTagPrio, 0u).x;
 }
 

@@ -1,0 +1,358 @@
+// kernels_small.cu -- the small-round engine: every remaining round of a
+// single set, once it has at most kSmallRoundsMax vertices, in one cooperative
+// launch.  Late rounds are small (the uncolored set shrinks geometrically),
+// and as separate launches their cost is launch and synchronisation overhead;
+// here each round is a sequence of grid-wide phases with no host round trip.
+//
+// A round follows Alg. 1 exactly as the per-round path does:
+//   priorities (static Random order, Sec. III-B) -> ranks in ascending
+//   (priority, global id) -> lists in that order (Floyd, as draw_list) ->
+//   the EARLIER conflict CSR by a join through per-color buckets -> ordered
+//   first-fit coloring (ordered_vertex) -> colors and the uncolored set in
+//   ascending global id (carry).
+// The run of list entry (u, k) holds the vertices v < u that commute with u
+// and also hold color c = list[u][k]: exactly the members of bucket c ranked
+// before u that commute with u.  So a bucket gives every run of its color by
+// commutation tests alone: sorted by list-entry index (r L + k, ascending
+// with the rank r), member i against the members j < i.
+// (P, L) come from a table the host fills with its own rule, so both paths
+// use the same numbers.  Data the launch wrote in an earlier phase is read
+// after a grid barrier with plain or L2 loads (ld_run<true>), never through
+// the read-only path, which may hold lines from before the write.
+//
+// The engine stops, with the state of the round it could not finish intact
+// (its vertex list; no color written), when the round's CSR exceeds the
+// capacity or the byte budget, or when a bounded wait of the coloring runs
+// out; the host then continues with the per-round path.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "color_device.cuh"
+#include "common.cuh"
+#include "warp_sort.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace picasso {
+
+namespace {
+constexpr int kSmallThreads = 256;
+constexpr int kSmallWarps = kSmallThreads / 32;
+constexpr int kSmallBlocksPerSm = 2;
+// dynamic shared memory of one warp: a bucket's member words and ranks
+constexpr int kWarpSmemBytes = kSmallBucketCap * (16 + 4);
+
+// Sum of x over the block (every thread gets it).  sm: 32 words.
+__device__ __forceinline__ int64_t block_sum(int64_t x, int64_t* sm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int d = 16; d; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+  __syncthreads();
+  if (lane == 0) sm[wid] = x;
+  __syncthreads();
+  int64_t t = 0;
+  for (int w = 0; w < nw; ++w) t += sm[w];
+  return t;
+}
+
+// Exclusive scan of x over the block; *total gets the block's sum.  sm: 32 words.
+__device__ __forceinline__ int64_t block_excl(int64_t x, int64_t* sm, int64_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int64_t inc = x;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += y;
+  }
+  __syncthreads();
+  if (lane == 31) sm[wid] = inc;
+  __syncthreads();
+  int64_t before = 0, t = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int64_t y = sm[w];
+    if (w < wid) before += y;
+    t += y;
+  }
+  *total = t;
+  return before + inc - x;
+}
+
+// Exclusive scan of in[0..m) into out[0..m] (out[m] = the total) by the
+// whole grid: block b scans the b-th contiguous chunk after adding the sums
+// of the chunks before it (part: one word per block).  Contains a grid
+// barrier; every thread of the grid must call it.
+template <class TI>
+__device__ void grid_scan(cg::grid_group& grid, const TI* in, int64_t m, int64_t* out, int64_t* part, int64_t* sm) {
+  const int64_t chunk = (m + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = min(m, chunk * (int64_t)blockIdx.x), hi = min(m, lo + chunk);
+  int64_t x = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) x += (int64_t)in[i];
+  x = block_sum(x, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = x;
+  grid.sync();
+  int64_t pre = 0;
+  for (int64_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += __ldcg(part + b);
+  pre = block_sum(pre, sm);
+  for (int64_t t0 = lo; t0 < hi; t0 += blockDim.x) {
+    const int64_t i = t0 + threadIdx.x;
+    const int64_t v = i < hi ? (int64_t)in[i] : 0;
+    int64_t tot = 0;
+    const int64_t ex = block_excl(v, sm, &tot);
+    if (i < hi) out[i] = pre + ex;
+    pre += tot;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[m] = pre;
+}
+}  // namespace
+
+
+// Runs from the sorted buckets, by work items of 32 members of one bucket
+// (item = bucket c, members i0 .. i0 + 31): the warp stages the bucket's
+// ranks and words in shared memory, and lane i tests its member against the
+// members j < i (the smaller ranks).  Count (FILL false): cnt[e_i] = the
+// commuting ones; fill (FILL true): their ranks at col[runoff[e_i]..],
+// ascending.
+template <bool FILL>
+__device__ void bucket_runs(const SmallArgs& a, int32_t* R, uint64_t* X, int lane, int64_t gwarp, int64_t nwarps) {
+  const int64_t nitems = __ldcg(a.ctl + 8);
+  int64_t c = -1, b0 = 0;
+  int s = 0;
+  for (int64_t it = gwarp; it < nitems; it += nwarps) {
+    const int64_t lo = a.ibkt[it];
+    const int i0 = (int)(it - a.iboff[lo]) * 32;
+    if (lo != c) {
+      c = lo;
+      b0 = a.boff[c];
+      s = (int)(a.boff[c + 1] - b0);
+      __syncwarp();
+      for (int i = lane; i < s; i += 32) {
+        R[i] = a.brank[b0 + i];
+        X[2 * i] = a.bxz[2 * (b0 + i)];
+        X[2 * i + 1] = a.bxz[2 * (b0 + i) + 1];
+      }
+      __syncwarp();
+    }
+    const int i = i0 + lane;
+    if (i < s) {
+      const uint64_t xi = X[2 * i], zi = X[2 * i + 1];
+      const int64_t e = a.bmem[b0 + i];
+      if (!FILL) {
+        uint32_t k = 0;
+#pragma unroll 4
+        for (int j = 0; j < i; ++j) k += commute1(xi, zi, X[2 * j], X[2 * j + 1]);
+        a.cnt[e] = k;
+      } else {
+        int64_t o = a.runoff[e];
+        for (int j = 0; j < i; ++j)
+          if (commute1(xi, zi, X[2 * j], X[2 * j + 1])) a.col[o++] = R[j];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_rounds(SmallArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  __shared__ int64_t scan_s[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t* Xw = reinterpret_cast<uint64_t*>(smem_dyn + (size_t)wid * kWarpSmemBytes);
+  int32_t* Rw = reinterpret_cast<int32_t*>(Xw + 2 * kSmallBucketCap);
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
+  // per-vertex loops spread over all blocks: thread t of block b takes t G + b
+  const int64_t stid = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
+
+  while (true) {
+    const int64_t n = __ldcg(a.ctl + 0);
+    const int64_t done = __ldcg(a.ctl + 1);
+    const int32_t round = a.round0 + (int32_t)done;
+    if (n == 0 || __ldcg(a.ctl + 2) != kSmallOk) break;
+    if (round > a.max_rounds) {
+      grid.sync();
+      if (gtid == 0) a.ctl[2] = kSmallMaxRounds;
+      break;
+    }
+    const int32_t* gid = __ldcg(a.ctl + 4) ? a.gid_b : a.gid_a;
+    int32_t* gid_next = __ldcg(a.ctl + 4) ? a.gid_a : a.gid_b;
+    const int2 pl = a.ptab[n];
+    const int64_t P = pl.x;
+    const int L = pl.y;
+    const int64_t E = n * (int64_t)L;
+    const int64_t base = __ldcg(a.ctl + 3);
+
+    // (priority, global id) keys in V_l order; empty buckets
+    for (int64_t i = stid; i < n; i += gthreads) {
+      const int32_t g = gid[i];
+      a.key[i] = ((uint64_t)philox_block(a.seed, round, g, kTagPrio, 0u).x << 32) | (uint32_t)g;
+    }
+    for (int64_t c = gtid; c < P; c += gthreads) {
+      a.bcnt[c] = 0;
+      a.bcur[c] = 0;
+    }
+    if (gtid == 0) a.err[1] = 0;
+    grid.sync();
+
+    // rank of vertex i = the number of smaller keys: warp per vertex, lanes
+    // over the others; the round's arrays are written at the rank
+    for (int64_t i = gwarp; i < n; i += nwarps) {
+      const uint64_t ki = a.key[i];
+      int r = 0;
+      for (int64_t j = lane; j < n; j += 32) r += a.key[j] < ki;
+      r = __reduce_add_sync(0xffffffffu, r);
+      if (lane == 0) {
+        const int32_t g = (int32_t)(uint32_t)ki;
+        a.perm[r] = (int32_t)i;
+        a.gid_r[r] = g;
+        a.xz_r[2 * r] = a.xz[2 * (int64_t)g];
+        a.xz_r[2 * r + 1] = a.xz[2 * (int64_t)g + 1];
+      }
+    }
+    grid.sync();
+
+    // lists in rank order, list offsets, first candidates (the ranked
+    // coloring reads no priority from the state word), bucket sizes
+    for (int64_t r = stid; r < n; r += gthreads) {
+      int32_t* out = a.lists + r * L;
+      draw_list<kSmallLCap>(a.seed, round, a.gid_r[r], P, L, 0, out);
+      a.loff[r] = r * L;
+      a.state[r] = ((uint64_t)(uint32_t)out[0] << 2) | kUndecided;
+      for (int k = 0; k < L; ++k) atomicAdd(a.bcnt + out[k], 1u);
+    }
+    if (gtid == 0) a.loff[n] = E;
+    grid.sync();
+
+    // bucket offsets and work items (32 members each); a bucket above the
+    // cap stops the engine
+    for (int64_t c = gtid; c < P; c += gthreads) {
+      const uint32_t sc = a.bcnt[c];
+      a.bitems[c] = (sc + 31) / 32;
+      if (sc > (uint32_t)kSmallBucketCap) a.err[2] = 1;
+    }
+    grid_scan(grid, a.bcnt, P, a.boff, a.part, scan_s);
+    grid.sync();
+    grid_scan(grid, a.bitems, P, a.iboff, a.part, scan_s);
+    grid.sync();
+    if (__ldcg(a.err + 2) != 0) {
+      if (gtid == 0) a.ctl[2] = kSmallOverflow;
+      break;
+    }
+    // bucket members (list entries) at a slot of the bucket; item -> bucket
+    for (int64_t e = gtid; e < E; e += gthreads) {
+      const int32_t c = a.lists[e];
+      a.bmem[a.boff[c] + atomicAdd(a.bcur + c, 1u)] = (int32_t)e;
+    }
+    for (int64_t c = gtid; c < P; c += gthreads)
+      for (int64_t t = a.iboff[c]; t < a.iboff[c + 1]; ++t) a.ibkt[t] = (int32_t)c;
+    if (gtid == 0) a.ctl[8] = a.iboff[P];
+    grid.sync();
+
+    // each bucket ascending (entries r L + k ascend with the rank r), then
+    // its members' ranks and words in that order
+    for (int64_t c = gwarp; c < P; c += nwarps) {
+      const int64_t b0 = a.boff[c];
+      const int sc = (int)(a.boff[c + 1] - b0);
+      warp_sort_any(a.bmem + b0, sc, lane);
+      __syncwarp();
+      for (int i = lane; i < sc; i += 32) {
+        const int32_t r = a.bmem[b0 + i] / L;
+        a.brank[b0 + i] = r;
+        a.bxz[2 * (b0 + i)] = a.xz_r[2 * (int64_t)r];
+        a.bxz[2 * (b0 + i) + 1] = a.xz_r[2 * (int64_t)r + 1];
+      }
+    }
+    grid.sync();
+
+    bucket_runs<false>(a, Rw, Xw, lane, gwarp, nwarps);
+    grid.sync();
+    grid_scan(grid, a.cnt, E, a.runoff, a.part, scan_s);
+    grid.sync();
+    {
+      const int64_t nnz = __ldcg(a.runoff + E);
+      const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
+      if (nnz > a.cap || (a.budget > 0 && csr_bytes > a.budget)) {
+        if (gtid == 0) a.ctl[2] = kSmallOverflow;
+        break;
+      }
+      if (gtid == 0) {
+        a.ctl[5] = max(a.ctl[5], csr_bytes);
+        a.ctl[6] += nnz;
+        a.ctl[7] += n * (n - 1) / 2;
+      }
+    }
+    bucket_runs<true>(a, Rw, Xw, lane, gwarp, nwarps);
+    grid.sync();
+
+    // ordered first fit in rank order; warps take ranks from a counter
+    {
+      ColorArgs ca{};
+      ca.n = n;
+      ca.lists = a.lists;
+      ca.loff = a.loff;
+      ca.runoff = a.runoff;
+      ca.col = a.col;
+      ca.state = a.state;
+      ca.ranked = 1;
+      bool ok = true;
+      while (ok) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.err + 1, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((int64_t)t >= n || __ldcg(a.err) != 0) break;
+        ok = ordered_vertex<true>(ca, t, lane, a.err);
+      }
+    }
+    grid.sync();
+    if (__ldcg(a.err) != 0) {
+      if (gtid == 0) a.ctl[2] = kSmallTimeout;
+      break;
+    }
+
+    // carry: colors at global ids, flags in V_l order
+    for (int64_t r = gtid; r < n; r += gthreads) {
+      const uint32_t w = (uint32_t)__ldcg(a.state + r);
+      const bool colored = (w & 3u) == kColored;
+      if (colored) a.color[a.gid_r[r]] = (int32_t)(base + (int64_t)(w >> 2));
+      a.flag[a.perm[r]] = colored ? 0u : 1u;
+    }
+    grid.sync();
+    grid_scan(grid, a.flag, n, a.pos, a.part, scan_s);
+    grid.sync();
+    for (int64_t i = gtid; i < n; i += gthreads)
+      if (a.flag[i]) gid_next[a.pos[i]] = gid[i];
+    if (gtid == 0) {
+      a.ctl[0] = a.pos[n];
+      a.ctl[1] = done + 1;
+      a.ctl[3] = base + P;
+      a.ctl[4] = __ldcg(a.ctl + 4) ^ 1;
+    }
+    grid.sync();
+  }
+}
+
+size_t small_smem_bytes() { return (size_t)kSmallWarps * kWarpSmemBytes; }
+
+cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, cudaStream_t s) {
+  int dev = 0, sms = 148, per_sm = 0;
+  const size_t smem = small_smem_bytes();
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_small_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_rounds, kSmallThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  // fewer resident blocks make each grid barrier cheaper; two per SM keep
+  // 16 warps per SM for the latency-bound phases
+  int blocks = std::min(per_sm, kSmallBlocksPerSm) * sms;
+  blocks = std::min(blocks, part_cap);
+  SmallArgs args = a;
+  void* params[] = {(void*)&args};
+  e = cudaLaunchCooperativeKernel((const void*)k_small_rounds, dim3((unsigned)blocks), dim3(kSmallThreads), params,
+                                  smem, s);
+  count_launches(1);
+  return e;
+}
+
+}  // namespace picasso

@@ -1,0 +1,82 @@
+// warp_sort.cuh -- ascending sort of up to 512 int32 keys by one warp: a
+// bitonic network in registers (lane l holds elements l*E .. l*E+E-1 of the
+// padded size m = 32 E); partners closer than E are in the same lane,
+// farther ones are exchanged by shuffles.  Internal header of the CUDA
+// library (the bucket join of the per-round build and the small-round
+// engine).
+#pragma once
+
+#include <stdint.h>
+
+namespace picasso {
+
+constexpr int kWarpSortMax = 512;
+
+template <int E>
+__device__ __forceinline__ void warp_bitonic(int32_t (&key)[E], int lane) {
+  constexpr int m = 32 * E;
+#pragma unroll
+  for (int k = 2; k <= m; k <<= 1) {
+#pragma unroll
+    for (int d = k >> 1; d > 0; d >>= 1) {
+      if (d < E) {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          if ((j & d) == 0) {
+            const int i = lane * E + j;
+            const bool up = (i & k) == 0;
+            const int32_t x = key[j], y = key[j | d];
+            const bool sw = (x > y) == up;
+            key[j] = sw ? y : x;
+            key[j | d] = sw ? x : y;
+          }
+        }
+      } else {
+        const int ld = d / E;
+        const bool lower = (lane & ld) == 0;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          const int i = lane * E + j;
+          const bool up = (i & k) == 0;
+          const int32_t y = __shfl_xor_sync(0xffffffffu, key[j], ld);
+          // the lower element keeps the smaller key when ascending
+          key[j] = (lower == up) ? min(key[j], y) : max(key[j], y);
+        }
+      }
+    }
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_bucket(int32_t* __restrict__ p, int s, int lane) {
+  int32_t key[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int i = lane * E + j;
+    key[j] = i < s ? p[i] : 0x7fffffff;
+  }
+  warp_bitonic<E>(key, lane);
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int i = lane * E + j;
+    if (i < s) p[i] = key[j];
+  }
+}
+
+// Sort p[0..s) in place, s <= 512, by the warp; dispatches on the smallest
+// power-of-two E with 32 E >= s.
+__device__ __forceinline__ void warp_sort_any(int32_t* __restrict__ p, int s, int lane) {
+  if (s <= 1) return;
+  if (s <= 32)
+    warp_sort_bucket<1>(p, s, lane);
+  else if (s <= 64)
+    warp_sort_bucket<2>(p, s, lane);
+  else if (s <= 128)
+    warp_sort_bucket<4>(p, s, lane);
+  else if (s <= 256)
+    warp_sort_bucket<8>(p, s, lane);
+  else
+    warp_sort_bucket<16>(p, s, lane);
+}
+
+}  // namespace picasso

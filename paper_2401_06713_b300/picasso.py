@@ -18,6 +18,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_INTERNAL, E
 ALGOS = {"auto": 0, "allpairs": 1, "bucket": 2}
 COLOR_ALGOS = {"auto": 0, "sweep": 1}
 CSR_FORMS = {"earlier": 0, "full": 1}
+SMALL_ENGINE = {"auto": 0, "off": 1}
 
 
 class PicassoError(RuntimeError):
@@ -38,6 +39,8 @@ class Config(ctypes.Structure):
         ("byte_budget", ctypes.c_int64),
         ("color_algo", ctypes.c_int32),
         ("csr_form", ctypes.c_int32),
+        ("small_engine", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -78,6 +81,9 @@ class Stats(ctypes.Structure):
         ("sweep_pending", ctypes.c_int32 * 64),
         ("sweep_active", ctypes.c_int32 * 64),
         ("sweep_us", ctypes.c_float * 64),
+        ("small_rounds", ctypes.c_int32),
+        ("small_stops", ctypes.c_int32),
+        ("t_small_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -206,7 +212,7 @@ class Picasso:
 
     def __init__(self, xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
                  algo: str = "auto", max_rounds: int = 100000, byte_budget: int = 0, stream=None,
-                 color: str = "auto", set_offsets=None, seeds=None, csr: str = "earlier"):
+                 color: str = "auto", set_offsets=None, seeds=None, csr: str = "earlier", small: str = "auto"):
         """One set, or with ``set_offsets`` (host, nsets + 1 ints) a batch of
         independent sets stored back to back in ``xz`` (seeds default to
         seed + k)."""
@@ -226,6 +232,7 @@ class Picasso:
         cfg.byte_budget = byte_budget
         cfg.color_algo = COLOR_ALGOS[color]
         cfg.csr_form = CSR_FORMS[csr]
+        cfg.small_engine = SMALL_ENGINE[small]
         self.cfg = cfg
         h = ctypes.c_void_p()
         if set_offsets is None:
@@ -306,6 +313,14 @@ class Picasso:
         s = Stats()
         _ck(_lib().picasso_get_stats(self.h, ctypes.byref(s)), "picasso_get_stats")
         return s.as_dict()
+
+    def vertices(self) -> torch.Tensor:
+        """V_l of the current round: global ids, int32 [n_l] (ascending before
+        the lists are assigned, in coloring order after)."""
+        n = self.stats()["n_round"]
+        gid = torch.empty(max(n, 1), dtype=torch.int32, device=self.xz.device)
+        _ck(_lib().picasso_get_round(self.h, _ptr(gid), None, None), "picasso_get_round")
+        return gid[:n]
 
     def round_state(self, L: int | None = None):
         """(gid int32 [n_l], lists int32 [n_l, L] round-local, prio int32 [n_l])."""

@@ -202,10 +202,10 @@ def test_round_coloring_exact(pc, orc, algo, color):
         assert np.array_equal(got, ref)
 
 
-def _run_both(pc, orc, chars, seed, num, den, alpha, algo="auto", color="auto"):
+def _run_both(pc, orc, chars, seed, num, den, alpha, algo="auto", color="auto", small="auto"):
     ref, rounds, stats = orc.run(chars, seed, num, den, alpha)
     with pc.Picasso(_xz(pc, chars), chars.shape[1], seed=seed, palette=(num, den), alpha=alpha, algo=algo,
-                    color=color) as p:
+                    color=color, small=small) as p:
         got, r = p.run()
         got = got.cpu().numpy()
         assert r == rounds
@@ -225,15 +225,17 @@ def test_run_weighted(pc, orc, algo):
     _run_both(pc, orc, synth.pauli_weighted(4000, 48, 0.25, seed=1), 5, 1, 8, 2.0, algo)
 
 
-@pytest.mark.parametrize("color", ["auto", "sweep"])
-def test_run_throughput_law_small(pc, orc, color):
-    # the n=1M law (q=64, p=0.25, P=n/16, alpha=1.5) at a size the oracle runs
-    _run_both(pc, orc, synth.pauli_weighted(5000, 64, 0.25, seed=3), 0, 1, 16, 1.5, color=color)
+@pytest.mark.parametrize("color,small", [("auto", "auto"), ("auto", "off"), ("sweep", "auto")])
+def test_run_throughput_law_small(pc, orc, color, small):
+    # the n=1M law (q=64, p=0.25, P=n/16, alpha=1.5) at a size the oracle
+    # runs; "auto" runs every round in the small-round engine, "off" per round
+    _run_both(pc, orc, synth.pauli_weighted(5000, 64, 0.25, seed=3), 0, 1, 16, 1.5, color=color, small=small)
 
 
+@pytest.mark.parametrize("small", ["auto", "off"])
 @pytest.mark.parametrize("n", [1, 2, 31, 257])
-def test_run_edge_sizes(pc, orc, n):
-    _run_both(pc, orc, synth.pauli_uniform(n, 6, seed=n), 2, 1, 8, 2.0)
+def test_run_edge_sizes(pc, orc, n, small):
+    _run_both(pc, orc, synth.pauli_uniform(n, 6, seed=n), 2, 1, 8, 2.0, small=small)
 
 
 def test_run_all_identity(pc, orc):
