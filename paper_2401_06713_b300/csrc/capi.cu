@@ -700,19 +700,24 @@ int carry_round(Ctx* c) {
 // Whether picasso_run hands the remaining rounds to the small-round engine.
 bool small_eligible(const Ctx* c) {
   const picasso_config& cfg = c->cfg;
-  if (c->nsets != 1 || c->n < 1 || c->n > kSmallRoundsMax || cfg.small_engine != PICASSO_SMALL_AUTO) return false;
+  if (c->n < 1 || c->n > kSmallRoundsMax || cfg.small_engine != PICASSO_SMALL_AUTO) return false;
   if (cfg.conflict_algo != PICASSO_CONFLICT_AUTO || cfg.color_algo != PICASSO_COLOR_AUTO ||
       cfg.csr_form != PICASSO_CSR_EARLIER)
     return false;
   if (c->small_off || c->round == c->small_skip_round || c->round > cfg.max_rounds) return false;
-  int64_t P;
-  int32_t L;
-  params_for(cfg, c->n, &P, &L);
-  if (L > kSmallLCap || c->n * (int64_t)L > kSmallMeanBucket * P) return false;
-  // every color the engine can hand out still fits an int32 (the per-round
-  // path checks base + P each round)
   const int64_t rounds_left = (int64_t)cfg.max_rounds - c->round + 1;
-  return c->set_base[0] + rounds_left * P <= (int64_t)0x7fffffff;
+  for (int k = 0; k < c->nsets; ++k) {
+    const int64_t m = c->remaining[k];
+    if (m == 0) continue;
+    int64_t P;
+    int32_t L;
+    params_for(cfg, m, &P, &L);
+    if (L > kSmallLCap || m * (int64_t)L > kSmallMeanBucket * P) return false;
+    // every color the engine can hand out still fits an int32 (the
+    // per-round path checks base + P each round)
+    if (c->set_base[k] + rounds_left * P > (int64_t)0x7fffffff) return false;
+  }
+  return true;
 }
 
 // The remaining rounds in one cooperative launch (kernels_small.cu); on
@@ -720,30 +725,50 @@ bool small_eligible(const Ctx* c) {
 // at (no vertex left, the round limit, or a round handed back).
 int run_small(Ctx* c) {
   const int64_t n0 = c->n;
+  const int ns = c->nsets;
   cudaStream_t s = c->s;
-  int64_t P0;
-  int32_t L0;
-  params_for(c->cfg, n0, &P0, &L0);
-  std::vector<int2> ptab((size_t)n0 + 1);
+  // sizes at the start bound every later round (P and L grow with n):
+  // vertices, bucket colors, list entries, and the column capacity: the
+  // expected run entries of the first round if every pair commuted (n_k
+  // (n_k - 1) / 2 pairs per set sharing L^2 / P colors on average) plus
+  // slack; a round above it goes back to the per-round path
+  int64_t mmax = 0, P0 = 0, E0 = 0;
+  double pairs = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    const int64_t m = c->remaining[k];
+    if (m == 0) continue;
+    int64_t P;
+    int32_t L;
+    params_for(c->cfg, m, &P, &L);
+    mmax = std::max(mmax, m);
+    P0 += P;
+    E0 += m * L;
+    pairs += 0.5 * (double)m * (double)(m - 1) * L * (double)L / (double)P;
+  }
+  const int64_t cap = std::max<int64_t>(int64_t(1) << 22, (int64_t)pairs + (int64_t(1) << 20));
+  std::vector<int2> ptab((size_t)mmax + 1);
   ptab[0] = make_int2(0, 0);
-  for (int64_t m = 1; m <= n0; ++m) {
+  for (int64_t m = 1; m <= mmax; ++m) {
     int64_t P;
     int32_t L;
     params_for(c->cfg, m, &P, &L);
     ptab[m] = make_int2((int)P, L);
   }
-  // column capacity: the expected run entries of the first round if every
-  // pair commuted, n0 (n0 - 1) / 2 pairs sharing L0^2 / P0 colors on
-  // average, plus slack; a round above it goes back to the per-round path
-  const double pairs = 0.5 * (double)n0 * (double)(n0 - 1);
-  const int64_t cap = std::max<int64_t>(int64_t(1) << 22, (int64_t)(pairs * L0 * (double)L0 / (double)P0) +
-                                                               (int64_t(1) << 20));
+  // per-set words: base, remaining, peak bytes | vertex, color and entry
+  // offsets (nsets + 1 each) | seeds
+  std::vector<int64_t> hs(7 * (size_t)ns + 3, 0);
+  for (int k = 0; k < ns; ++k) {
+    hs[k] = c->set_base[k];
+    hs[ns + k] = c->remaining[k];
+    hs[2 * ns + k] = c->set_peak_bytes[k];
+    hs[6 * ns + 3 + k] = (int64_t)c->seed[k];
+  }
   constexpr int kPartCap = 2048;
-  const int64_t E0 = n0 * (int64_t)L0;
   SmallArgs a{};
   int2* d_ptab = nullptr;
+  int64_t* d_sw = nullptr;
   int32_t *gid_a = nullptr, *gid_b = nullptr, *perm = nullptr, *gid_r = nullptr, *lists = nullptr, *col = nullptr;
-  int32_t *err = nullptr, *bmem = nullptr, *brank = nullptr, *ibkt = nullptr;
+  int32_t *err = nullptr, *bmem = nullptr, *brank = nullptr, *ibkt = nullptr, *sid = nullptr, *ent_v = nullptr;
   uint64_t* bxz = nullptr;
   uint32_t* bitems = nullptr;
   int64_t* iboff = nullptr;
@@ -753,11 +778,14 @@ int run_small(Ctx* c) {
   int st = PICASSO_OK;
   auto cleanup = [&]() {
     release(c, &d_ptab);
+    release(c, &d_sw);
     release(c, &gid_a);
     release(c, &gid_b);
     release(c, &perm);
     release(c, &gid_r);
+    release(c, &sid);
     release(c, &lists);
+    release(c, &ent_v);
     release(c, &col);
     release(c, &err);
     release(c, &xz_r);
@@ -798,13 +826,16 @@ int run_small(Ctx* c) {
       return st;                                  \
     }                                             \
   } while (0)
-  TRY(alloc(c, &d_ptab, n0 + 1));
+  TRY(alloc(c, &d_ptab, mmax + 1));
+  TRY(alloc(c, &d_sw, (int64_t)hs.size()));
   TRY(alloc(c, &gid_a, n0));
   TRY(alloc(c, &gid_b, n0));
   TRY(alloc(c, &perm, n0));
   TRY(alloc(c, &gid_r, n0));
+  TRY(alloc(c, &sid, n0));
   TRY(alloc(c, &xz_r, 2 * n0));
   TRY(alloc(c, &lists, E0));
+  TRY(alloc(c, &ent_v, E0));
   TRY(alloc(c, &loff, n0 + 1));
   TRY(alloc(c, &cnt, E0));
   TRY(alloc(c, &runoff, E0 + 1));
@@ -825,7 +856,8 @@ int run_small(Ctx* c) {
   TRY(alloc(c, &part, kPartCap));
   TRY(alloc(c, &err, 4));
   TRY(alloc(c, &ctl, 9));
-  TRYC(cudaMemcpyAsync(d_ptab, ptab.data(), sizeof(int2) * (n0 + 1), cudaMemcpyHostToDevice, s));
+  TRYC(cudaMemcpyAsync(d_ptab, ptab.data(), sizeof(int2) * (mmax + 1), cudaMemcpyHostToDevice, s));
+  TRYC(cudaMemcpyAsync(d_sw, hs.data(), sizeof(int64_t) * hs.size(), cudaMemcpyHostToDevice, s));
   if (c->gid)
     TRYC(cudaMemcpyAsync(gid_a, c->gid, sizeof(int32_t) * n0, cudaMemcpyDeviceToDevice, s));
   else
@@ -833,13 +865,20 @@ int run_small(Ctx* c) {
   int64_t* h = c->h_buf;
   std::memset(h, 0, sizeof(int64_t) * 9);
   h[0] = n0;
-  h[3] = c->set_base[0];
   TRYC(cudaMemcpyAsync(ctl, h, sizeof(int64_t) * 9, cudaMemcpyHostToDevice, s));
   TRYC(cudaMemsetAsync(err, 0, sizeof(int32_t) * 4, s));
   a.n0 = n0;
   a.round0 = c->round;
   a.max_rounds = c->cfg.max_rounds;
-  a.seed = c->seed[0];
+  a.nsets = ns;
+  a.soff = c->d_soff;
+  a.sbase = d_sw;
+  a.srem = d_sw + ns;
+  a.speak = d_sw + 2 * ns;
+  a.svoff = d_sw + 3 * ns;
+  a.scof = d_sw + 4 * ns + 1;
+  a.seoff = d_sw + 5 * ns + 2;
+  a.sseed = reinterpret_cast<const uint64_t*>(d_sw + 6 * ns + 3);
   a.ptab = d_ptab;
   a.cap = cap;
   a.budget = c->cfg.byte_budget;
@@ -848,8 +887,10 @@ int run_small(Ctx* c) {
   a.gid_b = gid_b;
   a.perm = perm;
   a.gid_r = gid_r;
+  a.sid = sid;
   a.xz_r = xz_r;
   a.lists = lists;
+  a.ent_v = ent_v;
   a.loff = loff;
   a.cnt = cnt;
   a.runoff = runoff;
@@ -862,20 +903,21 @@ int run_small(Ctx* c) {
   a.bcnt = bcnt;
   a.bcur = bcur;
   a.boff = boff;
-  a.bmem = bmem;
-  a.brank = brank;
-  a.bxz = bxz;
   a.bitems = bitems;
   a.iboff = iboff;
   a.ibkt = ibkt;
+  a.bmem = bmem;
+  a.brank = brank;
+  a.bxz = bxz;
   a.part = part;
   a.err = err;
   a.ctl = ctl;
   TRYC(launch_small_rounds(a, kPartCap, s));
-  TRYC(cudaMemcpyAsync(h, ctl, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, s));
+  TRYC(cudaMemcpyAsync(h, ctl, sizeof(int64_t) * 9, cudaMemcpyDeviceToHost, s));
+  TRYC(cudaMemcpyAsync(hs.data(), d_sw, sizeof(int64_t) * 3 * ns, cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
-  const int64_t nleft = h[0], rounds = h[1], stop = h[2], base = h[3], parity = h[4];
-  const int64_t max_nnz = h[5], sum_nnz = h[6], sum_pairs = h[7];
+  const int64_t nleft = h[0], rounds = h[1], stop = h[2], parity = h[4];
+  const int64_t sum_nnz = h[6], sum_pairs = h[7];
   // V_l of the round the engine stopped at, and its words
   int32_t* gid2 = nullptr;
   uint64_t* xz2 = nullptr;
@@ -900,14 +942,16 @@ int run_small(Ctx* c) {
   c->gid = gid2;
   c->xz = xz2;
   c->n = nleft;
-  c->remaining[0] = nleft;
+  for (int k = 0; k < ns; ++k) {
+    c->set_base[k] = hs[k];
+    c->remaining[k] = hs[ns + k];
+    c->set_peak_bytes[k] = hs[2 * ns + k];
+  }
   c->round += (int32_t)rounds;
   c->rounds_done += (int32_t)rounds;
-  c->set_base[0] = base;
   c->small_rounds += (int32_t)rounds;
   c->nnz_total += sum_nnz;
   c->logical_pairs += sum_pairs;
-  if (rounds > 0) c->set_peak_bytes[0] = std::max(c->set_peak_bytes[0], max_nnz);
   if (stop == kSmallTimeout || stop == kSmallOverflow) {
     c->small_stops += 1;
     c->small_skip_round = c->round;

@@ -274,11 +274,11 @@ cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, con
                                  const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s);
 cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s);
 
-// Small-round engine (kernels_small.cu): every remaining round of a single
-// set in one cooperative launch once the round has at most kSmallRoundsMax
-// vertices and lists of at most kSmallLCap colors, and its color buckets
-// are small (mean n L / P at most kSmallMeanBucket; a bucket above
-// kSmallBucketCap stops the engine).  ctl[0..4] hold the engine's position between rounds
+// Small-round engine (kernels_small.cu): every remaining round of a context
+// (one set or a batch) in one cooperative launch once the round has at most
+// kSmallRoundsMax vertices, every set's lists at most kSmallLCap colors and
+// small color buckets (mean n_k L_k / P_k at most kSmallMeanBucket; a bucket
+// above kSmallBucketCap stops the engine).  ctl[0..4] hold the engine's position between rounds
 // (host-initialised); the launch returns with ctl[2] = kSmallOk when no
 // vertex is left, or with the reason it stopped at the start of a round it
 // did not finish (that round's vertex list intact, none of its colors
@@ -286,13 +286,21 @@ cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s);
 constexpr int64_t kSmallRoundsMax = 16384;
 constexpr int kSmallLCap = 64;
 constexpr int kSmallBucketCap = 512;  // largest color bucket
-constexpr int kSmallMeanBucket = 320; // a round joins only if n L <= this * P
+constexpr int kSmallMeanBucket = 320; // a set joins only if n L <= this * P
 struct SmallArgs {
   int64_t n0;             // vertices when the engine starts
   int32_t round0;         // number of the first round it runs
   int32_t max_rounds;     // last round number it may run
-  uint64_t seed;          // the set's Philox key
-  const int2* ptab;       // [n0 + 1]: (P, L) of a round with m vertices
+  int32_t nsets;          // sets of the context
+  const int64_t* soff;    // [nsets + 1] global id offsets of the sets
+  const uint64_t* sseed;  // [nsets] Philox keys
+  int64_t* sbase;         // [nsets] palette base of the next round (in/out)
+  int64_t* srem;          // [nsets] vertices of the set in the round (in/out)
+  int64_t* speak;         // [nsets] largest CSR bytes of one round (in/out)
+  int64_t* svoff;         // [nsets + 1] the round's offsets: vertices,
+  int64_t* scof;          // [nsets + 1]   bucket colors (sum of P),
+  int64_t* seoff;         // [nsets + 1]   list entries (sum of n L)
+  const int2* ptab;       // [max n_k + 1]: (P, L) of a set with m vertices
   int64_t cap;            // CSR entries the col buffer holds
   int64_t budget;         // byte budget of one round's CSR (0: none)
   const uint64_t* xz;     // [N][2] all strings
@@ -300,31 +308,33 @@ struct SmallArgs {
   int32_t* gid_b;         // [n0]
   int32_t* perm;          // [n0] rank -> place in V_l
   int32_t* gid_r;         // [n0] rank -> global id
+  int32_t* sid;           // [n0] rank -> set
   uint64_t* xz_r;         // [2 n0] words in rank order
-  int32_t* lists;         // [n0 * L]
+  int32_t* lists;         // [E0] (E0 = sum of n_k L_k at the start)
+  int32_t* ent_v;         // [E0] list entry -> rank
   int64_t* loff;          // [n0 + 1]
-  uint32_t* cnt;          // [n0 * L]
-  int64_t* runoff;        // [n0 * L + 1]
+  uint32_t* cnt;          // [E0]
+  int64_t* runoff;        // [E0 + 1]
   int32_t* col;           // [cap]
   uint64_t* state;        // [n0]
   uint32_t* flag;         // [n0] in V_l order
   int64_t* pos;           // [n0 + 1]
   int32_t* color;         // [N] global colors
   uint64_t* key;          // [n0] (priority, global id) in V_l order
-  uint32_t* bcnt;         // [P0] bucket sizes
+  uint32_t* bcnt;         // [P0] bucket sizes (P0 = sum of P_k at the start)
   uint32_t* bcur;         // [P0] bucket fill cursors
   int64_t* boff;          // [P0 + 1] bucket offsets
   uint32_t* bitems;       // [P0] work items of a bucket, ceil(s_c / 32)
   int64_t* iboff;         // [P0 + 1] their prefix
-  int32_t* ibkt;          // [n0 L / 32 + P0] bucket of every work item
-  int32_t* bmem;          // [n0 * L] bucket members: list-entry index,
-  int32_t* brank;         // [n0 * L]   rank,
-  uint64_t* bxz;          // [2 n0 L]   words
+  int32_t* ibkt;          // [E0 / 32 + P0 + 1] bucket of every work item
+  int32_t* bmem;          // [E0] bucket members: list-entry index,
+  int32_t* brank;         // [E0]   rank,
+  uint64_t* bxz;          // [2 E0] words
   int64_t* part;          // [gridDim.x] block sums of the grid scans
   int32_t* err;           // [4]: 0 ordered-pass poll timeout, 1 work counter, 2 bucket over the cap
-  int64_t* ctl;           // [9]: 0 n, 1 rounds done, 2 stop reason, 3 base, 4 V_l in gid_b,
-                          //      5 largest CSR bytes 8 (n + 1) + 4 nnz, 6 sum of nnz,
-                          //      7 sum of n (n - 1) / 2 (5..7 zero on entry), 8 scratch
+  int64_t* ctl;           // [9]: 0 n, 1 rounds done, 2 stop reason, 4 V_l in gid_b (0..4
+                          //      host-initialised), 6 sum of nnz, 7 sum over the sets of
+                          //      n_k (n_k - 1) / 2 (6, 7 zero on entry), 3, 5, 8 scratch
 };
 
 // Stop reasons in ctl[2].

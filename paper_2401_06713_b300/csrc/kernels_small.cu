@@ -1,6 +1,6 @@
 // kernels_small.cu -- the small-round engine: every remaining round of a
-// single set, once it has at most kSmallRoundsMax vertices, in one cooperative
-// launch.  Late rounds are small (the uncolored set shrinks geometrically),
+// context (one set, or a batch of sets advancing together), once a round has
+// at most kSmallRoundsMax vertices, in one cooperative launch.  Late rounds are small (the uncolored set shrinks geometrically),
 // and as separate launches their cost is launch and synchronisation overhead;
 // here each round is a sequence of grid-wide phases with no host round trip.
 //
@@ -15,8 +15,12 @@
 // before u that commute with u.  So a bucket gives every run of its color by
 // commutation tests alone: sorted by list-entry index (r L + k, ascending
 // with the rank r), member i against the members j < i.
-// (P, L) come from a table the host fills with its own rule, so both paths
-// use the same numbers.  Data the launch wrote in an earlier phase is read
+// (P, L) of a set come from a table the host fills with its own rule (indexed
+// by the set's vertex count), so both paths use the same numbers.  In a
+// batch, V_l in ascending global id holds the sets one after another; a
+// vertex's Philox streams are keyed by its set's seed and its id within the
+// set, its list colors carry the set's bucket-color offset (sum of the P of
+// the sets before it), and it is ranked among its own set only.  Data the launch wrote in an earlier phase is read
 // after a grid barrier with plain or L2 loads (ld_run<true>), never through
 // the read-only path, which may hold lines from before the write.
 //
@@ -105,30 +109,88 @@ __device__ void grid_scan(cg::grid_group& grid, const TI* in, int64_t m, int64_t
 }  // namespace
 
 
+// Largest k with off[k] <= x (off ascending, off[0] <= x): the set holding
+// position x when off holds the sets' offsets (empty sets are skipped).
+__device__ __forceinline__ int find_set(const int64_t* off, int nsets, int64_t x) {
+  int lo = 0, hi = nsets - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// The sets' offsets for a round from their vertex counts srem: vertices
+// (svoff), bucket colors (scof, sum of P) and list entries (seoff, sum of
+// n L).  Block 0 only; sm: 32 words.
+__device__ void set_prefixes(const SmallArgs& a, int64_t* sm) {
+  int64_t pv = 0, pc = 0, pe = 0;
+  for (int k0 = 0; k0 < a.nsets; k0 += blockDim.x) {
+    const int k = k0 + threadIdx.x;
+    int64_t nk = 0, Pk = 0, Ek = 0;
+    if (k < a.nsets) {
+      nk = a.srem[k];
+      if (nk > 0) {
+        const int2 pl = a.ptab[nk];
+        Pk = pl.x;
+        Ek = nk * pl.y;
+      }
+    }
+    int64_t tv, tc, te;
+    const int64_t xv = block_excl(nk, sm, &tv);
+    const int64_t xc = block_excl(Pk, sm, &tc);
+    const int64_t xe = block_excl(Ek, sm, &te);
+    if (k < a.nsets) {
+      a.svoff[k] = pv + xv;
+      a.scof[k] = pc + xc;
+      a.seoff[k] = pe + xe;
+    }
+    pv += tv;
+    pc += tc;
+    pe += te;
+  }
+  if (threadIdx.x == 0) {
+    a.svoff[a.nsets] = pv;
+    a.scof[a.nsets] = pc;
+    a.seoff[a.nsets] = pe;
+  }
+}
+
 // Runs from the sorted buckets, by work items of 32 members of one bucket
-// (item = bucket c, members i0 .. i0 + 31): the warp stages the bucket's
-// ranks and words in shared memory, and lane i tests its member against the
-// members j < i (the smaller ranks).  Count (FILL false): cnt[e_i] = the
-// commuting ones; fill (FILL true): their ranks at col[runoff[e_i]..],
-// ascending.
+// (item = bucket c, members i0 .. i0 + 31): lane i tests its member against
+// the members j < i (the smaller ranks), whose ranks and words the warp
+// stages in shared memory.  A warp takes a contiguous range of items, so it
+// stages a bucket's members once, as far as its items reach.  Count (FILL
+// false): cnt[e_i] = the commuting ones; fill (FILL true): their ranks at
+// col[runoff[e_i]..], ascending.
 template <bool FILL>
 __device__ void bucket_runs(const SmallArgs& a, int32_t* R, uint64_t* X, int lane, int64_t gwarp, int64_t nwarps) {
   const int64_t nitems = __ldcg(a.ctl + 8);
+  const int64_t per = (nitems + nwarps - 1) / nwarps;
+  const int64_t it0 = min(nitems, gwarp * per), it1 = min(nitems, it0 + per);
   int64_t c = -1, b0 = 0;
-  int s = 0;
-  for (int64_t it = gwarp; it < nitems; it += nwarps) {
-    const int64_t lo = a.ibkt[it];
-    const int i0 = (int)(it - a.iboff[lo]) * 32;
-    if (lo != c) {
-      c = lo;
+  int s = 0, staged = 0;
+  for (int64_t it = it0; it < it1; ++it) {
+    const int64_t cb = a.ibkt[it];
+    const int i0 = (int)(it - a.iboff[cb]) * 32;
+    if (cb != c) {
+      c = cb;
       b0 = a.boff[c];
       s = (int)(a.boff[c + 1] - b0);
+      staged = 0;
+    }
+    const int need = min(s, i0 + 32);
+    if (need > staged) {
       __syncwarp();
-      for (int i = lane; i < s; i += 32) {
+      for (int i = staged + lane; i < need; i += 32) {
         R[i] = a.brank[b0 + i];
         X[2 * i] = a.bxz[2 * (b0 + i)];
         X[2 * i + 1] = a.bxz[2 * (b0 + i) + 1];
       }
+      staged = need;
       __syncwarp();
     }
     const int i = i0 + lane;
@@ -162,6 +224,10 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
   const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
   // per-vertex loops spread over all blocks: thread t of block b takes t G + b
   const int64_t stid = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
+  const int nsets = a.nsets;
+
+  if (blockIdx.x == 0) set_prefixes(a, scan_s);
+  grid.sync();
 
   while (true) {
     const int64_t n = __ldcg(a.ctl + 0);
@@ -175,16 +241,14 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     }
     const int32_t* gid = __ldcg(a.ctl + 4) ? a.gid_b : a.gid_a;
     int32_t* gid_next = __ldcg(a.ctl + 4) ? a.gid_a : a.gid_b;
-    const int2 pl = a.ptab[n];
-    const int64_t P = pl.x;
-    const int L = pl.y;
-    const int64_t E = n * (int64_t)L;
-    const int64_t base = __ldcg(a.ctl + 3);
+    const int64_t P = a.scof[nsets];
+    const int64_t E = a.seoff[nsets];
 
     // (priority, global id) keys in V_l order; empty buckets
     for (int64_t i = stid; i < n; i += gthreads) {
+      const int k = nsets > 1 ? find_set(a.svoff, nsets, i) : 0;
       const int32_t g = gid[i];
-      a.key[i] = ((uint64_t)philox_block(a.seed, round, g, kTagPrio, 0u).x << 32) | (uint32_t)g;
+      a.key[i] = ((uint64_t)philox_block(a.sseed[k], round, g - a.soff[k], kTagPrio, 0u).x << 32) | (uint32_t)g;
     }
     for (int64_t c = gtid; c < P; c += gthreads) {
       a.bcnt[c] = 0;
@@ -193,37 +257,48 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     if (gtid == 0) a.err[1] = 0;
     grid.sync();
 
-    // rank of vertex i = the number of smaller keys: warp per vertex, lanes
-    // over the others; the round's arrays are written at the rank
+    // rank of vertex i = its set's offset + the number of smaller keys in the
+    // set: warp per vertex, lanes over the set; the round's arrays are
+    // written at the rank
     for (int64_t i = gwarp; i < n; i += nwarps) {
+      const int k = nsets > 1 ? find_set(a.svoff, nsets, i) : 0;
+      const int64_t v0 = a.svoff[k], v1 = a.svoff[k + 1];
       const uint64_t ki = a.key[i];
       int r = 0;
-      for (int64_t j = lane; j < n; j += 32) r += a.key[j] < ki;
-      r = __reduce_add_sync(0xffffffffu, r);
+      for (int64_t j = v0 + lane; j < v1; j += 32) r += a.key[j] < ki;
+      const int64_t rk = v0 + __reduce_add_sync(0xffffffffu, r);
       if (lane == 0) {
         const int32_t g = (int32_t)(uint32_t)ki;
-        a.perm[r] = (int32_t)i;
-        a.gid_r[r] = g;
-        a.xz_r[2 * r] = a.xz[2 * (int64_t)g];
-        a.xz_r[2 * r + 1] = a.xz[2 * (int64_t)g + 1];
+        a.perm[rk] = (int32_t)i;
+        a.gid_r[rk] = g;
+        a.sid[rk] = k;
+        a.xz_r[2 * rk] = a.xz[2 * (int64_t)g];
+        a.xz_r[2 * rk + 1] = a.xz[2 * (int64_t)g + 1];
       }
     }
     grid.sync();
 
-    // lists in rank order, list offsets, first candidates (the ranked
-    // coloring reads no priority from the state word), bucket sizes
+    // lists in rank order (bucket colors: + the set's offset), list offsets,
+    // entry owners, first candidates (the ranked coloring reads no priority
+    // from the state word), bucket sizes
     for (int64_t r = stid; r < n; r += gthreads) {
-      int32_t* out = a.lists + r * L;
-      draw_list<kSmallLCap>(a.seed, round, a.gid_r[r], P, L, 0, out);
-      a.loff[r] = r * L;
+      const int k = a.sid[r];
+      const int64_t v0 = a.svoff[k], nk = a.svoff[k + 1] - v0;
+      const int2 pl = a.ptab[nk];
+      const int64_t row = a.seoff[k] + (r - v0) * pl.y;
+      int32_t* out = a.lists + row;
+      draw_list<kSmallLCap>(a.sseed[k], round, a.gid_r[r] - a.soff[k], pl.x, pl.y, a.scof[k], out);
+      a.loff[r] = row;
       a.state[r] = ((uint64_t)(uint32_t)out[0] << 2) | kUndecided;
-      for (int k = 0; k < L; ++k) atomicAdd(a.bcnt + out[k], 1u);
+      for (int t = 0; t < pl.y; ++t) {
+        a.ent_v[row + t] = (int32_t)r;
+        atomicAdd(a.bcnt + out[t], 1u);
+      }
     }
     if (gtid == 0) a.loff[n] = E;
+    // bucket work items (32 members each); a bucket above the cap stops the
+    // engine
     grid.sync();
-
-    // bucket offsets and work items (32 members each); a bucket above the
-    // cap stops the engine
     for (int64_t c = gtid; c < P; c += gthreads) {
       const uint32_t sc = a.bcnt[c];
       a.bitems[c] = (sc + 31) / 32;
@@ -247,15 +322,15 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     if (gtid == 0) a.ctl[8] = a.iboff[P];
     grid.sync();
 
-    // each bucket ascending (entries r L + k ascend with the rank r), then
-    // its members' ranks and words in that order
+    // each bucket ascending (entries ascend with the rank), then its
+    // members' ranks and words in that order
     for (int64_t c = gwarp; c < P; c += nwarps) {
       const int64_t b0 = a.boff[c];
       const int sc = (int)(a.boff[c + 1] - b0);
       warp_sort_any(a.bmem + b0, sc, lane);
       __syncwarp();
       for (int i = lane; i < sc; i += 32) {
-        const int32_t r = a.bmem[b0 + i] / L;
+        const int32_t r = a.ent_v[a.bmem[b0 + i]];
         a.brank[b0 + i] = r;
         a.bxz[2 * (b0 + i)] = a.xz_r[2 * (int64_t)r];
         a.bxz[2 * (b0 + i) + 1] = a.xz_r[2 * (int64_t)r + 1];
@@ -274,11 +349,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         if (gtid == 0) a.ctl[2] = kSmallOverflow;
         break;
       }
-      if (gtid == 0) {
-        a.ctl[5] = max(a.ctl[5], csr_bytes);
-        a.ctl[6] += nnz;
-        a.ctl[7] += n * (n - 1) / 2;
-      }
+      if (gtid == 0) a.ctl[6] += nnz;
     }
     bucket_runs<true>(a, Rw, Xw, lane, gwarp, nwarps);
     grid.sync();
@@ -308,11 +379,15 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       break;
     }
 
-    // carry: colors at global ids, flags in V_l order
+    // carry: colors at global ids (final color = the set's base + bucket
+    // color - the set's offset), flags in V_l order
     for (int64_t r = gtid; r < n; r += gthreads) {
       const uint32_t w = (uint32_t)__ldcg(a.state + r);
       const bool colored = (w & 3u) == kColored;
-      if (colored) a.color[a.gid_r[r]] = (int32_t)(base + (int64_t)(w >> 2));
+      if (colored) {
+        const int k = a.sid[r];
+        a.color[a.gid_r[r]] = (int32_t)(a.sbase[k] + ((int64_t)(w >> 2) - a.scof[k]));
+      }
       a.flag[a.perm[r]] = colored ? 0u : 1u;
     }
     grid.sync();
@@ -320,11 +395,30 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     grid.sync();
     for (int64_t i = gtid; i < n; i += gthreads)
       if (a.flag[i]) gid_next[a.pos[i]] = gid[i];
-    if (gtid == 0) {
-      a.ctl[0] = a.pos[n];
-      a.ctl[1] = done + 1;
-      a.ctl[3] = base + P;
-      a.ctl[4] = __ldcg(a.ctl + 4) ^ 1;
+    if (blockIdx.x == 0) {
+      // per set: next palette base, largest CSR bytes of a round, vertices
+      // left; then the next round's offsets
+      int64_t pairs = 0;
+      for (int k = threadIdx.x; k < nsets; k += blockDim.x) {
+        const int64_t v0 = a.svoff[k], v1 = a.svoff[k + 1];
+        const int64_t nk = v1 - v0;
+        if (nk > 0) {
+          const int64_t nnzk = a.runoff[a.seoff[k + 1]] - a.runoff[a.seoff[k]];
+          a.sbase[k] += a.scof[k + 1] - a.scof[k];
+          a.speak[k] = max(a.speak[k], 8 * (nk + 1) + 4 * nnzk);
+          pairs += nk * (nk - 1) / 2;
+        }
+        a.srem[k] = a.pos[v1] - a.pos[v0];
+      }
+      pairs = block_sum(pairs, scan_s);
+      if (threadIdx.x == 0) {
+        a.ctl[0] = a.pos[n];
+        a.ctl[1] = done + 1;
+        a.ctl[4] = __ldcg(a.ctl + 4) ^ 1;
+        a.ctl[7] += pairs;
+      }
+      __syncthreads();
+      set_prefixes(a, scan_s);
     }
     grid.sync();
   }

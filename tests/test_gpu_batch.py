@@ -33,24 +33,72 @@ def _batch(sets):
     return padded, offs, q
 
 
-def _run_batch(pc, sets, seeds, palette=(1, 8), alpha=2.0, algo="auto", color="auto"):
+def _run_batch(pc, sets, seeds, palette=(1, 8), alpha=2.0, algo="auto", color="auto", small="auto", stats=False):
     padded, offs, q = _batch(sets)
     xz = pc.pack(torch.from_numpy(padded).cuda())
     with pc.Picasso(xz, q, palette=palette, alpha=alpha, algo=algo, color=color, set_offsets=offs,
-                    seeds=seeds) as p:
+                    seeds=seeds, small=small) as p:
         colors, rounds = p.run()
+        if stats:
+            st = p.stats()
+            st["set_stats"] = p.set_stats()
+            return colors.cpu().numpy(), offs, rounds, st
         return colors.cpu().numpy(), offs, rounds
 
 
-def test_batch_matches_oracle_per_set(pc, orc):
+@pytest.mark.parametrize("small", ["auto", "off"])
+def test_batch_matches_oracle_per_set(pc, orc, small):
+    # "auto": the whole run in the small-round engine (the union has under
+    # 16384 vertices); "off": every round through the per-round path
     specs = [(700, 16, 0.3), (1, 24, 0.2), (2500, 64, 0.25), (1200, 32, 0.45), (33, 48, 0.1), (2048, 20, 0.5)]
     sets = [(synth.pauli_weighted(n, q, p, seed=11, stream=i), q) for i, (n, q, p) in enumerate(specs)]
     seeds = [100 + i for i in range(len(sets))]
-    colors, offs, rounds = _run_batch(pc, sets, seeds)
+    colors, offs, rounds, st = _run_batch(pc, sets, seeds, small=small, stats=True)
+    used, peak, left = st["set_stats"]
     for k, (c, q) in enumerate(sets):
-        ref, r, _ = orc.run(c, seeds[k], 1, 8, 2.0)
+        ref, r, ostats = orc.run(c, seeds[k], 1, 8, 2.0)
         assert np.array_equal(colors[offs[k]:offs[k + 1]], ref), k
         assert r <= rounds
+        assert used[k] == int(ostats[:, 1].sum()) and left[k] == 0, k
+        # the largest conflict CSR of the set in one round, EARLIER form:
+        # 8 (n_l + 1) + 4 nnz_l / 2 of the oracle's two-sided rows
+        assert peak[k] == max(8 * (int(m) + 1) + 4 * (int(z) // 2) for m, z in ostats[:, [0, 4]]), k
+    assert (st["small_rounds"] == rounds) if small == "auto" else (st["small_rounds"] == 0)
+
+
+def test_batch_engine_hands_over_and_matches_per_round(pc):
+    # union above 16384 at first: the per-round path runs the first rounds,
+    # the engine the rest; everything equals the per-round-only run
+    specs = synth.batch_specs(10, seed=4, n_lo=1000, n_hi=20000)
+    sets = [(synth.pauli_weighted(n, q, p, seed=4, stream=i + 1), q) for i, (n, q, p) in enumerate(specs)]
+    seeds = [50 + i for i in range(len(sets))]
+    a, offs, ra, sa = _run_batch(pc, sets, seeds, small="auto", stats=True)
+    b, _, rb, sb = _run_batch(pc, sets, seeds, small="off", stats=True)
+    assert sum(n for n, _, _ in specs) > 16384
+    assert ra == rb and np.array_equal(a, b)
+    assert sa["set_stats"] == sb["set_stats"]
+    assert sa["nnz_total"] == sb["nnz_total"] and sa["logical_pairs"] == sb["logical_pairs"]
+    assert 0 < sa["small_rounds"] < ra and sb["small_rounds"] == 0
+
+
+def test_batch_engine_empty_and_single_sets(pc, orc):
+    # an empty set between others and sets of one string
+    c0 = synth.pauli_weighted(300, 24, 0.3, seed=2)
+    c2 = synth.pauli_weighted(500, 24, 0.3, seed=3)
+    c3 = synth.pauli_weighted(1, 24, 0.3, seed=4)
+    padded = np.concatenate([c0, c2, c3])
+    offs = [0, 300, 300, 800, 801]
+    seeds = [5, 6, 7, 8]
+    xz = pc.pack(torch.from_numpy(padded).cuda())
+    with pc.Picasso(xz, 24, set_offsets=offs, seeds=seeds) as p:
+        colors, _ = p.run()
+        colors = colors.cpu().numpy()
+        used, _, left = p.set_stats()
+        assert p.stats()["small_rounds"] > 0
+    for k, c in ((0, c0), (2, c2), (3, c3)):
+        ref, _, _ = orc.run(c, seeds[k], 1, 8, 2.0)
+        assert np.array_equal(colors[offs[k]:offs[k + 1]], ref), k
+    assert used[1] == 0 and left == [0, 0, 0, 0]
 
 
 @pytest.mark.parametrize("algo,color", [("allpairs", "auto"), ("bucket", "sweep")])
