@@ -559,7 +559,7 @@ int color_round(Ctx* c) {
   cudaStream_t s = c->s;
   int32_t *wa = nullptr, *wb = nullptr, *wact = nullptr, *nw = nullptr;
   uint16_t* kcur = nullptr;
-  uint32_t *rcur = nullptr, *blkw = nullptr;
+  uint32_t *rcur = nullptr, *blkw = nullptr, *clist = nullptr;
   int32_t* blk = nullptr;
   void* tmp = nullptr;
   int st = PICASSO_OK;
@@ -572,6 +572,7 @@ int color_round(Ctx* c) {
     release(c, &rcur);
     release(c, &blk);
     release(c, &blkw);
+    release(c, &clist);
     release(c, (uint8_t**)&tmp);
   };
 #define TRY(expr)           \
@@ -616,6 +617,10 @@ int color_round(Ctx* c) {
   a.blk = blk;
   a.blkw = blkw;
   a.ranked = 1;  // round-local ids are ranks in coloring order
+  TRY(alloc(c, &clist, 8 * c->Ptot));
+  TRYC(cudaMemsetAsync(clist, 0, sizeof(uint32_t) * 8 * c->Ptot, s));
+  a.clist = clist;
+  a.xz = c->xz_r;
   // Ordered persistent pass; if one of its bounded waits runs out (ctl[5]),
   // recolor the round with the sweep kernel from a fresh state.  The colors,
   // the carry flags and their prefix sum are enqueued behind the pass, so one
@@ -774,10 +779,11 @@ int run_small(Ctx* c) {
   int64_t* iboff = nullptr;
   uint64_t *xz_r = nullptr, *state = nullptr, *key = nullptr;
   int64_t *loff = nullptr, *runoff = nullptr, *pos = nullptr, *part = nullptr, *ctl = nullptr, *boff = nullptr;
-  uint32_t *cnt = nullptr, *flag = nullptr, *bcnt = nullptr, *bcur = nullptr;
+  uint32_t *cnt = nullptr, *flag = nullptr, *bcnt = nullptr, *bcur = nullptr, *clist = nullptr;
   int st = PICASSO_OK;
   auto cleanup = [&]() {
     release(c, &d_ptab);
+    release(c, &clist);
     release(c, &d_sw);
     release(c, &gid_a);
     release(c, &gid_b);
@@ -845,6 +851,7 @@ int run_small(Ctx* c) {
   TRY(alloc(c, &pos, n0 + 1));
   TRY(alloc(c, &key, n0));
   TRY(alloc(c, &bcnt, P0));
+  TRY(alloc(c, &clist, 8 * P0));
   TRY(alloc(c, &bcur, P0));
   TRY(alloc(c, &boff, P0 + 1));
   TRY(alloc(c, &bmem, E0));
@@ -902,6 +909,7 @@ int run_small(Ctx* c) {
   a.key = key;
   a.bcnt = bcnt;
   a.bcur = bcur;
+  a.clist = clist;
   a.boff = boff;
   a.bitems = bitems;
   a.iboff = iboff;

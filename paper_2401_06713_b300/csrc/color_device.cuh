@@ -38,7 +38,8 @@ __device__ __forceinline__ T ld_run(const T* p) {
   if (FRESH) return *p;
   return __ldg(p);
 }
-constexpr int kCandBatch = 2;     // candidates whose first run chunk is screened together
+constexpr int kListBatch = 4;     // candidates checked against their colored lists together
+constexpr int kClistSlots = 7;    // colored vertices a list word records per color
 
 // Scan the run [rs, rs + ntot) of candidate c to the end: true if an earlier
 // neighbour took c; waits (bounded) on earlier neighbours still undecided at
@@ -111,16 +112,26 @@ __device__ __forceinline__ bool run_blocked(const ColorArgs& a, int32_t v, uint3
 }
 
 // One vertex.  The run offsets and colors of 32 candidates are loaded at
-// once (lane k holds candidate k's); candidates are then screened
-// kCandBatch at a time on the first 32 entries of their runs (one round of
-// column loads and one of state loads for the batch): a candidate whose first
-// chunk shows an earlier neighbour colored with it is blocked; the first one
-// not blocked that way is settled by scanning its whole run.
+// once (lane k holds candidate k's).  With colored lists (a.clist), four
+// candidates at a time are first checked against the vertices already
+// colored with them: eight lanes per candidate read the candidate's list
+// word (a count and the ranks of its first kClistSlots colored vertices) and
+// test commutation with those ranked before v.  A hit proves the candidate
+// blocked (that vertex is an earlier neighbour holding the color); nothing
+// else is concluded from the list.  Every candidate not proven blocked, in
+// list order, is settled by scanning its whole run (run_blocked), which is
+// exact; the first one no earlier neighbour can take is v's color.
 template <bool FRESH>
 __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
   const int64_t row = ld_run<FRESH>(a.loff + v);
   const int L = (int)(ld_run<FRESH>(a.loff + v + 1) - row);
   const uint32_t pv = (uint32_t)(__ldcg(&a.state[v]) >> 32);
+  const bool lists = a.clist != nullptr;
+  uint64_t xv = 0, zv = 0;
+  if (lists) {
+    xv = ld_run<FRESH>(a.xz + 2 * (int64_t)v);
+    zv = ld_run<FRESH>(a.xz + 2 * (int64_t)v + 1);
+  }
   int polls = 0;
   for (int kb = 0; kb < L; kb += 32) {
     const int kl = kb + lane;
@@ -128,39 +139,27 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
     const int64_t my_re = kl < L ? ld_run<FRESH>(a.runoff + row + kl + 1) : 0;
     const uint32_t my_c = kl < L ? (uint32_t)ld_run<FRESH>(a.lists + row + kl) : 0u;
     const int kend = min(L - kb, 32);
-    for (int k0 = 0; k0 < kend; k0 += kCandBatch) {
-      int32_t u[kCandBatch];
-      uint64_t su[kCandBatch];
-#pragma unroll
-      for (int b = 0; b < kCandBatch; ++b) {
-        const int64_t rs = __shfl_sync(0xffffffffu, my_rs, min(k0 + b, 31));
-        const int64_t re = __shfl_sync(0xffffffffu, my_re, min(k0 + b, 31));
-        const int64_t e = rs + lane;
-        u[b] = (k0 + b < kend && e < re) ? ld_run<FRESH>(a.col + e) : -1;
-        if (a.ranked && u[b] > v) u[b] = -1;
-      }
-#pragma unroll
-      for (int b = 0; b < kCandBatch; ++b) su[b] = u[b] >= 0 ? __ldcg(&a.state[u[b]]) : 0ull;
-      uint32_t blocked_mask = 0u;
-#pragma unroll
-      for (int b = 0; b < kCandBatch; ++b) {
-        const uint32_t cb = __shfl_sync(0xffffffffu, my_c, min(k0 + b, 31));
+    for (int k0 = 0; k0 < kend; k0 += kListBatch) {
+      uint32_t proven = 0u;  // bit b: candidate k0 + b is blocked
+      if (lists) {
+        const int kq = k0 + (lane >> 3), w = lane & 7;
+        const uint32_t cq = __shfl_sync(0xffffffffu, my_c, min(kq, 31));
+        const uint32_t word = (kq < kend && w > 0) ? __ldcg(a.clist + (size_t)cq * 8 + w) : 0u;
         bool lb = false;
-        if (u[b] >= 0) {
-          const uint32_t pu = (uint32_t)(su[b] >> 32);
-          if (a.ranked || pu < pv || (pu == pv && u[b] < v)) {
-            const uint32_t wu = (uint32_t)su[b];
-            lb = (wu & 3u) == kColored && (wu >> 2) == cb;
-          }
+        if (word != 0u && (int32_t)(word - 1) < v) {
+          const int64_t u = (int64_t)(word - 1);
+          lb = commute1(xv, zv, ld_run<FRESH>(a.xz + 2 * u), ld_run<FRESH>(a.xz + 2 * u + 1));
         }
-        if (__any_sync(0xffffffffu, lb)) blocked_mask |= 1u << b;
-      }
+        const uint32_t bm = __ballot_sync(0xffffffffu, lb);
 #pragma unroll
-      for (int b = 0; b < kCandBatch; ++b) {
+        for (int b = 0; b < kListBatch; ++b)
+          if ((bm >> (8 * b)) & 0xFFu) proven |= 1u << b;
+      }
+#pragma unroll 1
+      for (int b = 0; b < kListBatch; ++b) {
         const int kk = k0 + b;
         if (kk >= kend) break;
-        if ((blocked_mask >> b) & 1u) continue;
-        // candidate kb + kk is not blocked by its first chunk: settle it
+        if ((proven >> b) & 1u) continue;
         const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
         const int64_t rs = __shfl_sync(0xffffffffu, my_rs, kk);
         const int64_t re = __shfl_sync(0xffffffffu, my_re, kk);
@@ -172,7 +171,13 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
           return false;
         }
         if (!blk) {
-          if (lane == 0) publish(a.state, v, (c << 2) | kColored);
+          if (lane == 0) {
+            if (lists) {
+              const uint32_t slot = atomicAdd(a.clist + (size_t)c * 8, 1u);
+              if (slot < (uint32_t)kClistSlots) __stcg(a.clist + (size_t)c * 8 + 1 + slot, (uint32_t)v + 1u);
+            }
+            publish(a.state, v, (c << 2) | kColored);
+          }
           return true;
         }
       }

@@ -221,6 +221,11 @@ struct ColorArgs {
   uint32_t* blkw;   // [n] the vertex's candidate color when it started waiting
   int32_t ranked;   // 1: round-local ids are ranks in coloring order, so the
                     // earlier neighbours of a run form its prefix
+  // colored lists (ranked coloring only; null: off): per bucket color c, 8
+  // words at 8 c, zero at the start of the round: word 0 counts the vertices
+  // colored c, words 1..7 hold rank + 1 of the first seven of them
+  uint32_t* clist;
+  const uint64_t* xz;  // [n][2] words in rank order (with clist)
 };
 // Work list of all n vertices in ascending (priority, id): a counting sort on
 // the top log2(nbins) priority bits, then a sort inside each bin.  hist needs
@@ -323,6 +328,7 @@ struct SmallArgs {
   uint64_t* key;          // [n0] (priority, global id) in V_l order
   uint32_t* bcnt;         // [P0] bucket sizes (P0 = sum of P_k at the start)
   uint32_t* bcur;         // [P0] bucket fill cursors
+  uint32_t* clist;        // [8 P0] colored lists of the ordered coloring
   int64_t* boff;          // [P0 + 1] bucket offsets
   uint32_t* bitems;       // [P0] work items of a bucket, ceil(s_c / 32)
   int64_t* iboff;         // [P0 + 1] their prefix

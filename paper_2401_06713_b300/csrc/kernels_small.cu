@@ -193,19 +193,31 @@ __device__ void bucket_runs(const SmallArgs& a, int32_t* R, uint64_t* X, int lan
       staged = need;
       __syncwarp();
     }
+    // members j < i: the warp loops to the item's last member (a uniform
+    // bound), each lane counting only its own j < i.  The symplectic form
+    // folded to one 32-bit word: parity of x_i & z_j ^ z_i & x_j over both
+    // halves.
     const int i = i0 + lane;
-    if (i < s) {
-      const uint64_t xi = X[2 * i], zi = X[2 * i + 1];
-      const int64_t e = a.bmem[b0 + i];
-      if (!FILL) {
-        uint32_t k = 0;
+    const int jend = need;
+    const uint4* X4 = reinterpret_cast<const uint4*>(X);
+    const uint4 wi = X4[min(i, s - 1)];
+    const bool active = i < s;
+    const int ilim = active ? i : 0;  // lanes past the bucket test nothing
+    if (!FILL) {
+      uint32_t anti = 0;
 #pragma unroll 4
-        for (int j = 0; j < i; ++j) k += commute1(xi, zi, X[2 * j], X[2 * j + 1]);
-        a.cnt[e] = k;
-      } else {
-        int64_t o = a.runoff[e];
-        for (int j = 0; j < i; ++j)
-          if (commute1(xi, zi, X[2 * j], X[2 * j + 1])) a.col[o++] = R[j];
+      for (int j = 0; j < jend; ++j) {
+        const uint4 w = X4[j];
+        const uint32_t d = (wi.x & w.z) ^ (wi.z & w.x) ^ (wi.y & w.w) ^ (wi.w & w.y);
+        anti += (j < ilim) ? (__popc(d) & 1u) : 0u;
+      }
+      if (active) a.cnt[a.bmem[b0 + i]] = (uint32_t)i - anti;
+    } else {
+      int64_t o = active ? a.runoff[a.bmem[b0 + i]] : 0;
+      for (int j = 0; j < jend; ++j) {
+        const uint4 w = X4[j];
+        const uint32_t d = (wi.x & w.z) ^ (wi.z & w.x) ^ (wi.y & w.w) ^ (wi.w & w.y);
+        if (j < ilim && (__popc(d) & 1u) == 0u) a.col[o++] = R[j];
       }
     }
   }
@@ -254,6 +266,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       a.bcnt[c] = 0;
       a.bcur[c] = 0;
     }
+    for (int64_t t = gtid; t < 8 * P; t += gthreads) a.clist[t] = 0;
     if (gtid == 0) a.err[1] = 0;
     grid.sync();
 
@@ -364,6 +377,8 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       ca.col = a.col;
       ca.state = a.state;
       ca.ranked = 1;
+      ca.clist = a.clist;
+      ca.xz = a.xz_r;
       bool ok = true;
       while (ok) {
         int t = 0;
