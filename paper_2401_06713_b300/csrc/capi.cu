@@ -617,8 +617,8 @@ int color_round(Ctx* c) {
   a.blk = blk;
   a.blkw = blkw;
   a.ranked = 1;  // round-local ids are ranks in coloring order
-  TRY(alloc(c, &clist, 8 * c->Ptot));
-  TRYC(cudaMemsetAsync(clist, 0, sizeof(uint32_t) * 8 * c->Ptot, s));
+  TRY(alloc(c, &clist, kClistWords * c->Ptot));
+  TRYC(cudaMemsetAsync(clist, 0, sizeof(uint32_t) * kClistWords * c->Ptot, s));
   a.clist = clist;
   a.xz = c->xz_r;
   // Ordered persistent pass; if one of its bounded waits runs out (ctl[5]),
@@ -851,7 +851,7 @@ int run_small(Ctx* c) {
   TRY(alloc(c, &pos, n0 + 1));
   TRY(alloc(c, &key, n0));
   TRY(alloc(c, &bcnt, P0));
-  TRY(alloc(c, &clist, 8 * P0));
+  TRY(alloc(c, &clist, kClistWords * P0));
   TRY(alloc(c, &bcur, P0));
   TRY(alloc(c, &boff, P0 + 1));
   TRY(alloc(c, &bmem, E0));

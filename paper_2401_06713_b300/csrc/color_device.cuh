@@ -38,8 +38,8 @@ __device__ __forceinline__ T ld_run(const T* p) {
   if (FRESH) return *p;
   return __ldg(p);
 }
-constexpr int kListBatch = 4;     // candidates checked against their colored lists together
-constexpr int kClistSlots = 7;    // colored vertices a list word records per color
+constexpr int kListBatch = 32 / kClistWords;   // candidates checked against their lists together
+constexpr int kClistSlots = kClistWords - 1;   // colored vertices a list records per color
 
 // Scan the run [rs, rs + ntot) of candidate c to the end: true if an earlier
 // neighbour took c; waits (bounded) on earlier neighbours still undecided at
@@ -112,11 +112,11 @@ __device__ __forceinline__ bool run_blocked(const ColorArgs& a, int32_t v, uint3
 }
 
 // One vertex.  The run offsets and colors of 32 candidates are loaded at
-// once (lane k holds candidate k's).  With colored lists (a.clist), four
-// candidates at a time are first checked against the vertices already
-// colored with them: eight lanes per candidate read the candidate's list
-// word (a count and the ranks of its first kClistSlots colored vertices) and
-// test commutation with those ranked before v.  A hit proves the candidate
+// once (lane k holds candidate k's).  With colored lists (a.clist),
+// kListBatch candidates at a time are first checked against the vertices
+// already colored with them: kClistWords lanes per candidate read the
+// candidate's list (a count and the ranks of its first kClistSlots colored
+// vertices) and test commutation with those ranked before v.  A hit proves the candidate
 // blocked (that vertex is an earlier neighbour holding the color); nothing
 // else is concluded from the list.  Every candidate not proven blocked, in
 // list order, is settled by scanning its whole run (run_blocked), which is
@@ -142,9 +142,9 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
     for (int k0 = 0; k0 < kend; k0 += kListBatch) {
       uint32_t proven = 0u;  // bit b: candidate k0 + b is blocked
       if (lists) {
-        const int kq = k0 + (lane >> 3), w = lane & 7;
+        const int kq = k0 + lane / kClistWords, w = lane % kClistWords;
         const uint32_t cq = __shfl_sync(0xffffffffu, my_c, min(kq, 31));
-        const uint32_t word = (kq < kend && w > 0) ? __ldcg(a.clist + (size_t)cq * 8 + w) : 0u;
+        const uint32_t word = (kq < kend && w > 0) ? __ldcg(a.clist + (size_t)cq * kClistWords + w) : 0u;
         bool lb = false;
         if (word != 0u && (int32_t)(word - 1) < v) {
           const int64_t u = (int64_t)(word - 1);
@@ -153,7 +153,7 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
         const uint32_t bm = __ballot_sync(0xffffffffu, lb);
 #pragma unroll
         for (int b = 0; b < kListBatch; ++b)
-          if ((bm >> (8 * b)) & 0xFFu) proven |= 1u << b;
+          if ((bm >> (kClistWords * b)) & ((1u << kClistWords) - 1u)) proven |= 1u << b;
       }
 #pragma unroll 1
       for (int b = 0; b < kListBatch; ++b) {
@@ -173,8 +173,9 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
         if (!blk) {
           if (lane == 0) {
             if (lists) {
-              const uint32_t slot = atomicAdd(a.clist + (size_t)c * 8, 1u);
-              if (slot < (uint32_t)kClistSlots) __stcg(a.clist + (size_t)c * 8 + 1 + slot, (uint32_t)v + 1u);
+              const uint32_t slot = atomicAdd(a.clist + (size_t)c * kClistWords, 1u);
+              if (slot < (uint32_t)kClistSlots)
+                __stcg(a.clist + (size_t)c * kClistWords + 1 + slot, (uint32_t)v + 1u);
             }
             publish(a.state, v, (c << 2) | kColored);
           }

@@ -22,6 +22,7 @@ constexpr uint32_t kTagPrio = 2u;
 constexpr int kMaxL = 512;           // longest list a round may draw
 constexpr int kBucketCap = 2048;     // largest color bucket of the bucket join
 constexpr int kBucketMaxP = 1 << 21; // bucket colors of one round (bucket join)
+constexpr int kClistWords = 8;       // colored-list words per color (ordered coloring)
 constexpr int64_t kSmallRoundAllPairs = 2048;  // AUTO tests all pairs at or below this n
 constexpr uint32_t kFailedColor = 0x3FFFFFFFu;
 
@@ -221,9 +222,10 @@ struct ColorArgs {
   uint32_t* blkw;   // [n] the vertex's candidate color when it started waiting
   int32_t ranked;   // 1: round-local ids are ranks in coloring order, so the
                     // earlier neighbours of a run form its prefix
-  // colored lists (ranked coloring only; null: off): per bucket color c, 8
-  // words at 8 c, zero at the start of the round: word 0 counts the vertices
-  // colored c, words 1..7 hold rank + 1 of the first seven of them
+  // colored lists (ranked coloring only; null: off): per bucket color c,
+  // kClistWords words at kClistWords c, zero at the start of the round:
+  // word 0 counts the vertices colored c, the others hold rank + 1 of the
+  // first of them
   uint32_t* clist;
   const uint64_t* xz;  // [n][2] words in rank order (with clist)
 };
@@ -328,7 +330,7 @@ struct SmallArgs {
   uint64_t* key;          // [n0] (priority, global id) in V_l order
   uint32_t* bcnt;         // [P0] bucket sizes (P0 = sum of P_k at the start)
   uint32_t* bcur;         // [P0] bucket fill cursors
-  uint32_t* clist;        // [8 P0] colored lists of the ordered coloring
+  uint32_t* clist;        // [kClistWords P0] colored lists of the ordered coloring
   int64_t* boff;          // [P0 + 1] bucket offsets
   uint32_t* bitems;       // [P0] work items of a bucket, ceil(s_c / 32)
   int64_t* iboff;         // [P0 + 1] their prefix

@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       a.bcnt[c] = 0;
       a.bcur[c] = 0;
     }
-    for (int64_t t = gtid; t < 8 * P; t += gthreads) a.clist[t] = 0;
+    for (int64_t t = gtid; t < kClistWords * P; t += gthreads) a.clist[t] = 0;
     if (gtid == 0) a.err[1] = 0;
     grid.sync();
 
