@@ -371,7 +371,7 @@ int build_conflicts(Ctx* c) {
   uint32_t *words = nullptr, *rmask = nullptr;
   unsigned long long* dsq = nullptr;
   int64_t *boff = nullptr, *moff = nullptr, *jboff = nullptr;
-  int32_t* bmem = nullptr;
+  int32_t *bmem = nullptr, *ibkt = nullptr;
   void* tmp = nullptr;
   int st = PICASSO_OK;
   auto cleanup = [&]() {
@@ -385,6 +385,7 @@ int build_conflicts(Ctx* c) {
     release(c, &words);
     release(c, &moff);
     release(c, &jboff);
+    release(c, &ibkt);
     release(c, &rmask);
     release(c, (uint8_t**)&tmp);
   };
@@ -472,8 +473,11 @@ int build_conflicts(Ctx* c) {
     TRY(alloc(c, &jboff, P + 1));
     TRYC(launch_bucket_jblocks(bcount, P, words, s));
     TRYC(launch_scan_u32(words, P, jboff, tmp, s));
+    TRYC(cudaMemcpyAsync(c->h_buf + 3, jboff + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TRYC(cudaStreamSynchronize(s));
     const int64_t nwords = c->h_buf[0];
+    TRY(alloc(c, &ibkt, c->h_buf[3]));
+    TRYC(launch_item_bucket(jboff, P, ibkt, s));
     release(c, &words);
     TRY(alloc(c, &rmask, nwords));
     a.rmask = rmask;
@@ -512,7 +516,7 @@ int build_conflicts(Ctx* c) {
   a.col = c->col;
   TRYC(cudaEventRecord(c->ev[4], s));
   if (algo == PICASSO_CONFLICT_BUCKET) {
-    TRYC(launch_bucket_emit(a, boff, bmem, moff, jboff, c->d_err + 2, s));
+    TRYC(launch_bucket_emit(a, boff, bmem, moff, jboff, ibkt, c->d_err + 2, s));
   } else {
     TRYC(launch_allpairs(a, true, s));
   }

@@ -202,7 +202,10 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
 cudaError_t launch_bucket_jblocks(const uint32_t* bcount, int64_t P, uint32_t* out, cudaStream_t s);
 // jboff [P+1]: prefix of ceil(s_c / 32); counter: one device int32 (reset here)
 cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
-                               const int64_t* moff, const int64_t* jboff, int32_t* counter, cudaStream_t s);
+                               const int64_t* moff, const int64_t* jboff, const int32_t* ibkt, int32_t* counter,
+                               cudaStream_t s);
+// ibkt [jboff[P]]: the bucket of every emit work item.
+cudaError_t launch_item_bucket(const int64_t* jboff, int64_t P, int32_t* ibkt, cudaStream_t s);
 cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s);
 // off[u] = runoff[loff[u]], u <= n.
 cudaError_t launch_row_offsets(const int64_t* runoff, const int64_t* loff, int64_t n, int64_t* off,

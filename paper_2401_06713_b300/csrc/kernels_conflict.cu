@@ -432,6 +432,20 @@ cudaError_t launch_bucket_jblocks(const uint32_t* bcount, int64_t P, uint32_t* o
   return cudaGetLastError();
 }
 
+// ibkt[t] = the bucket of work item t, for t in [jboff[b], jboff[b + 1]).
+__global__ void k_item_bucket(const int64_t* __restrict__ jboff, int64_t P, int32_t* __restrict__ ibkt) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= P) return;
+  for (int64_t t = jboff[b]; t < jboff[b + 1]; ++t) ibkt[t] = (int32_t)b;
+}
+
+cudaError_t launch_item_bucket(const int64_t* jboff, int64_t P, int32_t* ibkt, cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  k_item_bucket<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(jboff, P, ibkt);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // Emit pass: the mask words become CSR runs.  Work items are the 32-row
 // blocks of all buckets (jboff = prefix of ceil(s_c / 32)); every warp takes
 // items from a global counter, so no warp waits for another.  For an item the
@@ -471,6 +485,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
                                                               const int32_t* __restrict__ bmem,
                                                               const int64_t* __restrict__ moff,
                                                               const int64_t* __restrict__ jboff,
+                                                              const int32_t* __restrict__ ibkt,
                                                               int32_t* __restrict__ counter) {
   __shared__ uint32_t wbuf_s[kEmitThreads / 32][kEmitChunk * 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -479,21 +494,15 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
   const int64_t items = jboff[a.P];
   // flat / Lu as the high word of flat * ceil(2^64 / Lu): exact for flat < 2^32
   const uint64_t invL = a.Lu > 1 ? ~0ull / (uint64_t)a.Lu + 1ull : 0ull;
-  while (true) {
-    int64_t item = 0;
-    if (lane == 0) item = atomicAdd(counter, 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= items) break;
-    // bucket of the item: the last b with jboff[b] <= item
-    int64_t lo = 0, hi = a.P - 1;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if (jboff[mid] <= item)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    const int64_t b = lo;
+  int64_t item = 0;
+  if (lane == 0) item = atomicAdd(counter, 1);
+  item = __shfl_sync(0xffffffffu, item, 0);
+  while (item < items) {
+    // the next item's id is fetched now and used at the end, so the atomic's
+    // latency hides behind this item's stores
+    int64_t next = 0;
+    if (lane == 0) next = atomicAdd(counter, 1);
+    const int64_t b = ibkt[item];
     const int J = (int)(item - jboff[b]);
     const int64_t o = boff[b];
     const int s = (int)(boff[b + 1] - o);
@@ -535,11 +544,12 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
       }
       __syncwarp();
     }
+    item = __shfl_sync(0xffffffffu, next, 0);
   }
 }
 
 cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
-                               const int64_t* jboff, int32_t* counter, cudaStream_t s) {
+                               const int64_t* jboff, const int32_t* ibkt, int32_t* counter, cudaStream_t s) {
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
@@ -549,7 +559,8 @@ cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_bucket_emit<<<(unsigned)(sms * max(per_sm, 1)), kEmitThreads, 0, s>>>(a, boff, bmem, moff, jboff, counter);
+  k_bucket_emit<<<(unsigned)(sms * max(per_sm, 1)), kEmitThreads, 0, s>>>(a, boff, bmem, moff, jboff, ibkt,
+                                                                         counter);
   count_launches(1);
   return cudaGetLastError();
 }
