@@ -244,10 +244,14 @@ def run_gpu(args):
     # pair-test kernel: one POPC per tested pair (parity of popc(lo ^ hi));
     # POPC issues at 16 lanes/clk/SM
     peak_pairs = n_sm * sm_mhz * 1e6 * 16
-    achieved = st["tested_pairs"] / (st["t_pairs_ms"] / 1e3)
+    # (a run small enough for the small-round engine alone has no per-round
+    # pair-test launches: no figure then)
+    achieved = st["tested_pairs"] / (st["t_pairs_ms"] / 1e3) if st["t_pairs_ms"] > 0 else None
     tested_per_launch = st["tested_pairs"] / max(st["pairs_launches"], 1)
-    roofline = {"bound": "alu", "kernel": "k_bucket_mask", "achieved": achieved / 1e9,
-                "peak": peak_pairs / 1e9, "unit": "Gpair-tests/s", "frac": achieved / peak_pairs,
+    roofline = {"bound": "alu", "kernel": "k_bucket_mask",
+                "achieved": achieved / 1e9 if achieved else None,
+                "peak": peak_pairs / 1e9, "unit": "Gpair-tests/s",
+                "frac": achieved / peak_pairs if achieved else None,
                 "traffic": MASK_DRAM_BYTES_PER_PAIR * tested_per_launch,
                 "traffic_note": "bytes per launch, scaled from an ncu capture of round 1 at n=200000",
                 "peak_source": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median under load) x 16 POPC/clk/SM",
