@@ -348,7 +348,8 @@ int picasso_philox_draws(uint64_t seed, int32_t round, int64_t gid,
                          uint32_t* d_out, void* stream);
 
 /* Return cached pool memory of the current device to the driver, keeping at
- * most keep_bytes reserved.  Synchronises the device.                      */
+ * most keep_bytes reserved, and free the pinned host read-back buffers that
+ * destroyed contexts left for reuse.  Synchronises the device.             */
 int picasso_trim_memory(int64_t keep_bytes);
 
 /* Process-wide count of kernels this library has launched (all contexts). */

@@ -55,6 +55,37 @@ cudaError_t pool_for(int dev, cudaMemPool_t* out) {
   *out = g_pool[dev];
   return cudaSuccess;
 }
+
+// Pinned read-back buffers of 16 words, kept for reuse across contexts:
+// pinning host memory costs far more than a round, and a context needs
+// only one.  picasso_trim_memory returns them.
+std::mutex g_pin_mu;
+std::vector<int64_t*> g_pin_free;
+constexpr size_t kPinWords = 16;
+
+cudaError_t pinned_get(int64_t** out) {
+  {
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    if (!g_pin_free.empty()) {
+      *out = g_pin_free.back();
+      g_pin_free.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaMallocHost((void**)out, sizeof(int64_t) * kPinWords);
+}
+
+void pinned_put(int64_t* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
+void pinned_trim() {
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  for (int64_t* p : g_pin_free) cudaFreeHost(p);
+  g_pin_free.clear();
+}
 }  // namespace
 
 namespace {
@@ -1020,7 +1051,7 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
     c->seed[k] = h_seeds ? h_seeds[k] : cfg->seed + (uint64_t)k;
     c->remaining[k] = h_soff[k + 1] - h_soff[k];
   }
-  e = cudaMallocHost((void**)&c->h_buf, sizeof(int64_t) * 16);
+  e = pinned_get(&c->h_buf);
   if (e != cudaSuccess) {
     delete c;
     return map_err(e);
@@ -1047,7 +1078,7 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
     release(c, &c->d_set_bytes);
     for (int i = 0; i < 6; ++i)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
-    cudaFreeHost(c->h_buf);
+    pinned_put(c->h_buf);
     delete c;
     return st;
   }
@@ -1481,6 +1512,7 @@ int picasso_mlp_to_bf16(const float* d_src, uint16_t* d_dst, int32_t count, void
 
 int picasso_trim_memory(int64_t keep_bytes) {
   if (keep_bytes < 0) return PICASSO_ERR_INVALID_ARG;
+  pinned_trim();
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return map_err(e);
@@ -1519,7 +1551,7 @@ int picasso_destroy(void* ctx) {
   cudaStreamSynchronize(c->s);
   for (int i = 0; i < 6; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
-  if (c->h_buf) cudaFreeHost(c->h_buf);
+  pinned_put(c->h_buf);
   delete c;
   return PICASSO_OK;
 }
