@@ -139,6 +139,12 @@ struct Ctx {
   int64_t* off = nullptr;
   int32_t* col = nullptr;
   int64_t* runoff = nullptr;
+  // direct layout (fused pass): entry e's run is col[rstart[e] ..
+  // rstart[e] + rcnt[e]); off and runoff are made on request (canonical_csr)
+  bool direct = false;
+  int64_t* rstart = nullptr;
+  uint32_t* rcnt = nullptr;
+  double commute_ratio = 0.6;  // nnz / bucket pair bound of the last fused build
   // color
   bool colored_done = false;
   int64_t n_colored = 0, n_remaining = 0;
@@ -236,6 +242,9 @@ void free_build(Ctx* c) {
   release(c, &c->off);
   release(c, &c->col);
   release(c, &c->runoff);
+  release(c, &c->rstart);
+  release(c, &c->rcnt);
+  c->direct = false;
   c->built = false;
   c->nnz = 0;
 }
@@ -494,6 +503,75 @@ int build_conflicts(Ctx* c) {
     TRYC(launch_bucket_fill(c->lists, E, boff, bcursor, bmem, s));
     release(c, &bcursor);
     TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, (int32_t)smax, s));
+    if (a.lower && c->cfg.byte_budget == 0 && smax <= kFusedMax) {
+      // fused mask + emit: the runs of a bucket go to one region claimed from
+      // a cursor.  The column buffer is sized from the bucket pair bound and
+      // the last fused build's commuting ratio; if the runs need more, the
+      // pass ran to the end counting (nothing written past the buffer) and
+      // runs once more with the exact size.
+      const int64_t bound = bucket_pairs / 2;
+      int64_t cap = std::min<int64_t>(bound, (int64_t)(c->commute_ratio * 1.08 * (double)bound) + (int64_t(1) << 20));
+      cap = std::max<int64_t>(cap, 1);
+      // the cursor: the context's error block, words 2..3 (8-byte aligned)
+      unsigned long long* cur = reinterpret_cast<unsigned long long*>(c->d_err + 2);
+      TRY(alloc(c, &c->rstart, E));
+      TRY(alloc(c, &c->col, cap));
+      a.rstart = c->rstart;
+      a.col = c->col;
+      a.cursor = cur;
+      a.cap = cap;
+      int64_t nnz = 0;
+      float ms = 0.f;
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        TRYC(cudaMemsetAsync(cur, 0, sizeof(unsigned long long), s));
+        TRYC(cudaEventRecord(c->ev[2], s));
+        TRYC(launch_bucket_fused(a, boff, bmem, (int32_t)smax, c->q, s));
+        TRYC(cudaEventRecord(c->ev[3], s));
+        TRYC(cudaMemcpyAsync(c->h_buf, cur, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        TRYC(cudaStreamSynchronize(s));
+        nnz = c->h_buf[0];
+        ms += (float)elapsed(c, 2, 3);
+        if (nnz <= a.cap) break;
+        release(c, &c->col);
+        TRY(alloc(c, &c->col, nnz));
+        a.col = c->col;
+        a.cap = nnz;
+      }
+      if (nnz > a.cap) {
+        cleanup();
+        return PICASSO_ERR_INTERNAL;
+      }
+      c->commute_ratio = bound > 0 ? (double)nnz / (double)bound : c->commute_ratio;
+      c->rcnt = cnt;  // the run lengths stay with the context
+      cnt = nullptr;
+      c->direct = true;
+      const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
+      if (c->nsets > 1) {
+        std::vector<int64_t> h(c->nsets);
+        TRYC(launch_set_csr_bytes(c->loff, nullptr, c->rcnt, c->gid_r, n, c->d_soff, c->nsets, c->d_set_bytes, s));
+        TRYC(cudaMemcpyAsync(h.data(), c->d_set_bytes, sizeof(int64_t) * c->nsets, cudaMemcpyDeviceToHost, s));
+        TRYC(cudaStreamSynchronize(s));
+        for (int k = 0; k < c->nsets; ++k)
+          if (c->remaining[k] > 0) c->set_peak_bytes[k] = std::max(c->set_peak_bytes[k], h[k] + 8);
+      } else {
+        c->set_peak_bytes[0] = std::max(c->set_peak_bytes[0], csr_bytes);
+      }
+      // one kernel both tests the pairs and writes the runs: its time counts
+      // for the pair tests and for the CSR writes (member words, entry ids,
+      // run starts and lengths, the runs)
+      c->t_pairs += ms;
+      c->pairs_launches += 1;
+      c->tested_pairs += bucket_pairs / 2;
+      c->t_emit += ms;
+      c->emit_launches += 1;
+      c->emit_bytes += 4 * nnz + 16 * E + 4 * E + 12 * E;
+      for (int k = 0; k < c->nsets; ++k) c->logical_pairs += c->remaining[k] * (c->remaining[k] - 1) / 2;
+      cleanup();
+      c->nnz = nnz;
+      c->nnz_total += nnz;
+      c->built = true;
+      return PICASSO_OK;
+    }
     // mask words: bucket c holds nwb x nwb blocks of 32 words, nwb = ceil(s_c / 32)
     TRY(alloc(c, &words, P));
     TRY(alloc(c, &moff, P + 1));
@@ -555,7 +633,7 @@ int build_conflicts(Ctx* c) {
   TRYC(launch_row_offsets(c->runoff, c->loff, n, c->off, s));
   if (c->nsets > 1) {
     std::vector<int64_t> h(c->nsets);
-    TRYC(launch_set_csr_bytes(c->loff, c->runoff, c->gid_r, n, c->d_soff, c->nsets, c->d_set_bytes, s));
+    TRYC(launch_set_csr_bytes(c->loff, c->runoff, nullptr, c->gid_r, n, c->d_soff, c->nsets, c->d_set_bytes, s));
     TRYC(cudaMemcpyAsync(h.data(), c->d_set_bytes, sizeof(int64_t) * c->nsets, cudaMemcpyDeviceToHost, s));
     TRYC(cudaStreamSynchronize(s));
     for (int k = 0; k < c->nsets; ++k)
@@ -586,6 +664,44 @@ int build_conflicts(Ctx* c) {
   c->built = true;
 #undef TRY
 #undef TRYC
+  return PICASSO_OK;
+}
+
+// The canonical CSR of a direct-layout build: run offsets by entry (a scan of
+// the run lengths), row offsets, and the runs moved to row order.  The
+// context keeps the canonical form afterwards.
+int canonical_csr(Ctx* c) {
+  if (!c->built || !c->direct) return PICASSO_OK;
+  const int64_t n = c->n, E = c->E;
+  cudaStream_t s = c->s;
+  void* tmp = nullptr;
+  int32_t* colc = nullptr;
+  auto fail = [&](int st) {
+    release(c, (uint8_t**)&tmp);
+    release(c, &colc);
+    release(c, &c->runoff);
+    release(c, &c->off);
+    return st;
+  };
+  int st = alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(E));
+  if (st == PICASSO_OK) st = alloc(c, &c->runoff, E + 1);
+  if (st == PICASSO_OK) st = alloc(c, &c->off, n + 1);
+  if (st == PICASSO_OK) st = alloc(c, &colc, c->nnz);
+  if (st != PICASSO_OK) return fail(st);
+  cudaError_t e = launch_scan_u32(c->rcnt, E, c->runoff, tmp, s);
+  if (e == cudaSuccess) e = launch_row_offsets(c->runoff, c->loff, n, c->off, s);
+  if (e == cudaSuccess) e = launch_runs_to_rows(c->rstart, c->rcnt, c->runoff, E, c->col, colc, s);
+  if (e != cudaSuccess) {
+    st = map_err(e);
+    if (st == PICASSO_ERR_CUDA) c->sticky = st;
+    return fail(st);
+  }
+  release(c, (uint8_t**)&tmp);
+  release(c, &c->col);
+  c->col = colc;
+  release(c, &c->rstart);
+  release(c, &c->rcnt);
+  c->direct = false;
   return PICASSO_OK;
 }
 
@@ -645,6 +761,8 @@ int color_round(Ctx* c) {
   a.lists = c->lists;
   a.loff = c->loff;
   a.runoff = c->runoff;
+  a.rstart = c->rstart;
+  a.rcnt = c->direct ? c->rcnt : nullptr;
   a.col = c->col;
   a.state = c->state;
   a.kcur = kcur;
@@ -1169,6 +1287,7 @@ int picasso_build_conflicts(void* ctx, picasso_csr* out) {
   ST(build_conflicts(c));
   CK(phase_end(c, &c->t_build));
   if (out) {
+    ST(canonical_csr(c));
     out->d_off = c->off;
     out->d_col = c->col;
     out->n_rows = c->n;
@@ -1265,6 +1384,7 @@ int picasso_get_runs(void* ctx, const int64_t** d_runoff) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (!c->built) return PICASSO_ERR_STATE;
+  ST(canonical_csr(c));
   if (d_runoff) *d_runoff = c->runoff;
   return PICASSO_OK;
 }
@@ -1273,6 +1393,7 @@ int picasso_copy_csr(void* ctx, int64_t* d_off, int32_t* d_col) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (!c->built) return PICASSO_ERR_STATE;
+  ST(canonical_csr(c));
   if (d_off) CK(cudaMemcpyAsync(d_off, c->off, sizeof(int64_t) * (c->n + 1), cudaMemcpyDeviceToDevice, c->s));
   if (d_col && c->nnz > 0)
     CK(cudaMemcpyAsync(d_col, c->col, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToDevice, c->s));
@@ -1283,6 +1404,7 @@ int picasso_copy_runs(void* ctx, int64_t* d_runoff) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (!c->built) return PICASSO_ERR_STATE;
+  ST(canonical_csr(c));
   if (d_runoff)
     CK(cudaMemcpyAsync(d_runoff, c->runoff, sizeof(int64_t) * (c->E + 1), cudaMemcpyDeviceToDevice, c->s));
   return PICASSO_OK;

@@ -135,8 +135,16 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
   int polls = 0;
   for (int kb = 0; kb < L; kb += 32) {
     const int kl = kb + lane;
-    const int64_t my_rs = kl < L ? ld_run<FRESH>(a.runoff + row + kl) : 0;
-    const int64_t my_re = kl < L ? ld_run<FRESH>(a.runoff + row + kl + 1) : 0;
+    int64_t my_rs = 0, my_re = 0;
+    if (kl < L) {
+      if (a.rcnt) {
+        my_rs = ld_run<FRESH>(a.rstart + row + kl);
+        my_re = my_rs + ld_run<FRESH>(a.rcnt + row + kl);
+      } else {
+        my_rs = ld_run<FRESH>(a.runoff + row + kl);
+        my_re = ld_run<FRESH>(a.runoff + row + kl + 1);
+      }
+    }
     const uint32_t my_c = kl < L ? (uint32_t)ld_run<FRESH>(a.lists + row + kl) : 0u;
     const int kend = min(L - kb, 32);
     for (int k0 = 0; k0 < kend; k0 += kListBatch) {

@@ -180,6 +180,13 @@ struct ConflictArgs {
   int32_t* err;          // device error word
   uint32_t* rmask;       // bucket join: run words (mask pass -> emit)
   int32_t lower;         // 1: rows keep only neighbours with a smaller id
+  // direct layout (the fused mask + emit pass): entry e's run is
+  // col[rstart[e] .. rstart[e] + cnt[e]), each bucket's runs one contiguous
+  // region claimed from *cursor; regions that would pass cap are not written
+  // (the cursor still counts, so it ends at the exact nnz)
+  int64_t* rstart;                // [E]
+  unsigned long long* cursor;     // one word, zero on entry
+  int64_t cap;                    // entries col holds
 };
 
 // Buckets: members of color c are bmem[boff[c] .. boff[c+1]) ascending; a
@@ -199,6 +206,12 @@ cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out
 cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, int32_t lower, uint32_t* words, cudaStream_t s);
 cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
                                const int64_t* moff, int32_t smax, int32_t q, cudaStream_t s);
+// The fused pass (EARLIER form, buckets of at most kFusedMax members): the
+// mask blocks stay in shared memory and every bucket's runs are written at
+// once, in the direct layout (a.rstart, a.cnt, a.col, a.cursor, a.cap).
+constexpr int kFusedMax = 512;
+cudaError_t launch_bucket_fused(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, int32_t smax,
+                                int32_t q, cudaStream_t s);
 cudaError_t launch_bucket_jblocks(const uint32_t* bcount, int64_t P, uint32_t* out, cudaStream_t s);
 // jboff [P+1]: prefix of ceil(s_c / 32); counter: one device int32 (reset here)
 cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
@@ -216,7 +229,9 @@ struct ColorArgs {
   int64_t n;
   const int32_t* lists;
   const int64_t* loff;
-  const int64_t* runoff;
+  const int64_t* runoff;   // [E+1] canonical layout: run of entry e ends at runoff[e+1]
+  const int64_t* rstart;   // direct layout (rcnt set): run of e is rstart[e] .. + rcnt[e]
+  const uint32_t* rcnt;
   const int32_t* col;
   uint64_t* state;  // [n] priority << 32 | state word
   uint16_t* kcur;   // [n] index of the current candidate in the list
@@ -279,9 +294,13 @@ cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff
                               cudaStream_t s);
 cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t n, uint64_t* xz_out,
                              cudaStream_t s);
-// out[k] (zeroed here) = 8 (n_k + 1) + 4 * run entries of set k's vertices.
-cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int32_t* gid, int64_t n,
-                                 const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s);
+// out[k] (zeroed here) = 8 n_k + 4 * run entries of set k's vertices; the
+// entries from runoff (canonical layout) or, if it is null, from cnt.
+cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const uint32_t* cnt, const int32_t* gid,
+                                 int64_t n, const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s);
+// Direct layout -> canonical rows: dst[runoff[e] + t] = src[rstart[e] + t].
+cudaError_t launch_runs_to_rows(const int64_t* rstart, const uint32_t* rcnt, const int64_t* runoff, int64_t E,
+                                const int32_t* src, int32_t* dst, cudaStream_t s);
 cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s);
 
 // Small-round engine (kernels_small.cu): every remaining round of a context

@@ -20,6 +20,8 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include <algorithm>
+
 #include "color_device.cuh"
 
 namespace cg = cooperative_groups;
@@ -131,7 +133,8 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
       return;
     }
     const uint32_t c = (uint32_t)a.lists[row + k];
-    const int64_t rs = a.runoff[row + k], r1 = a.runoff[row + k + 1];
+    const int64_t rs = a.rcnt ? a.rstart[row + k] : a.runoff[row + k];
+    const int64_t r1 = a.rcnt ? rs + a.rcnt[row + k] : a.runoff[row + k + 1];
     bool blocked = false;
     int64_t first_wait = -1;
     int32_t wait_u = -1;
@@ -427,24 +430,52 @@ cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff
 // byte budget: 8 (n_k + 1) row offsets + 4 per run entry, accumulated per
 // vertex (the round's vertices of a set need not be contiguous).
 __global__ void k_set_csr_bytes(const int64_t* __restrict__ loff, const int64_t* __restrict__ runoff,
-                                const int32_t* __restrict__ gid, int64_t n, const int64_t* __restrict__ soff,
-                                int nsets, unsigned long long* __restrict__ out) {
+                                const uint32_t* __restrict__ cnt, const int32_t* __restrict__ gid, int64_t n,
+                                const int64_t* __restrict__ soff, int nsets, unsigned long long* __restrict__ out) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const int64_t g = gid ? (int64_t)gid[v] : v;
   const int k = nsets > 1 ? set_of(soff, nsets, g) : 0;
-  const int64_t row = 8 + 4 * (runoff[loff[v + 1]] - runoff[loff[v]]);
-  atomicAdd(&out[k], (unsigned long long)row);
+  int64_t entries = 0;
+  if (runoff) {
+    entries = runoff[loff[v + 1]] - runoff[loff[v]];
+  } else {
+    for (int64_t e = loff[v]; e < loff[v + 1]; ++e) entries += cnt[e];
+  }
+  atomicAdd(&out[k], (unsigned long long)(8 + 4 * entries));
 }
 
 
-cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const int32_t* gid, int64_t n,
-                                 const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s) {
+cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const uint32_t* cnt, const int32_t* gid,
+                                 int64_t n, const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s) {
   if (nsets <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t) * nsets, s);
   if (e != cudaSuccess || n <= 0) return e;
-  k_set_csr_bytes<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(loff, runoff, gid, n, soff, nsets,
+  k_set_csr_bytes<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(loff, runoff, cnt, gid, n, soff, nsets,
                                                                (unsigned long long*)out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Warp per list entry: its run moves from the direct layout to its place in
+// the canonical rows.
+__global__ void k_runs_to_rows(const int64_t* __restrict__ rstart, const uint32_t* __restrict__ rcnt,
+                               const int64_t* __restrict__ runoff, int64_t E, const int32_t* __restrict__ src,
+                               int32_t* __restrict__ dst) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < E; e += nw) {
+    const int64_t s0 = rstart[e], d0 = runoff[e];
+    const uint32_t m = rcnt[e];
+    for (uint32_t t = lane; t < m; t += 32) dst[d0 + t] = src[s0 + t];
+  }
+}
+
+cudaError_t launch_runs_to_rows(const int64_t* rstart, const uint32_t* rcnt, const int64_t* runoff, int64_t E,
+                                const int32_t* src, int32_t* dst, cudaStream_t s) {
+  if (E <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((E + 7) / 8, 148 * 16);
+  k_runs_to_rows<<<(unsigned)blocks, 256, 0, s>>>(rstart, rcnt, runoff, E, src, dst);
   count_launches(1);
   return cudaGetLastError();
 }

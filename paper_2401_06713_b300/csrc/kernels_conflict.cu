@@ -206,6 +206,14 @@ __host__ __device__ inline size_t mask_smem_bytes(int smax) {
          sizeof(uint32_t) * ((size_t)nwb * 128 + 64 + (size_t)kMaskWarps * kTabWords);
 }
 
+// The fused pass adds, per member, its vertex id and run offset, and the
+// bucket's lower mask blocks (nwb (nwb + 1) / 2 blocks of 32 words).
+__host__ __device__ inline size_t fused_smem_bytes(int smax) {
+  const int nwb = (smax + 31) >> 5;
+  return mask_smem_bytes(smax) + align16(sizeof(int32_t) * smax) + align16(sizeof(uint32_t) * smax) +
+         sizeof(uint32_t) * 32 * (size_t)(nwb * (nwb + 1) / 2);
+}
+
 // 32 x 32 bit transpose across the warp: on entry lane r holds row r (bit k =
 // M[r][k]); on exit lane k holds column k (bit r = M[r][k]).  Five butterfly
 // stages exchange ever smaller off-diagonal sub-blocks.
@@ -289,7 +297,33 @@ __device__ __forceinline__ int mask_block(bool lower, int R, int W, int nwb) {
   return lower ? R * (R + 1) / 2 + W : R * nwb + W;
 }
 
-template <int QW, bool LOWER>
+constexpr int kEmitChunk = 16;
+
+// Rows of one staged chunk of NI partner words: lane rr keeps row rr's
+// cursor; every lane reads it by shuffle, writes its partner if its bit is
+// set, and the row's cursor advances by the word's popcount.
+template <int NI>
+__device__ __forceinline__ void emit_rows(const uint32_t* __restrict__ wbuf, const int32_t (&pv)[kEmitChunk],
+                                          int64_t& rc, int nrows, int32_t* __restrict__ col, int lane, uint32_t lt) {
+  const uint32_t lbit = 1u << lane;
+  for (int rr = 0; rr < nrows; ++rr) {
+    int32_t* dst = col + __shfl_sync(0xffffffffu, rc, rr);
+    int32_t at = 0;
+#pragma unroll
+    for (int t = 0; t < NI; ++t) {
+      const uint32_t w = wbuf[t * 32 + rr];
+      // predicated store: lane i writes partner i when bit i is set
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t@p st.global.b32 [%1], %2;\n\t}"
+          :
+          : "r"(w & lbit), "l"(dst + at + __popc(w & lt)), "r"(pv[t]));
+      at += __popc(w);
+    }
+    if (lane == rr) rc += at;
+  }
+}
+
+template <int QW, bool LOWER, bool FUSED>
 __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a, const int64_t* __restrict__ boff,
                                                               const int32_t* __restrict__ bmem,
                                                               const int64_t* __restrict__ moff, int smax) {
@@ -301,6 +335,22 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   p += align16(sizeof(int32_t) * smax);
   int32_t* cnt = (int32_t*)p;
   p += align16(sizeof(int32_t) * smax);
+  // fused pass: members' vertex ids, run offsets inside the bucket, mask blocks
+  int32_t* pid = nullptr;
+  uint32_t* roff = nullptr;
+  uint32_t* mw = nullptr;
+  if (FUSED) {
+    pid = (int32_t*)p;
+    p += align16(sizeof(int32_t) * smax);
+    roff = (uint32_t*)p;
+    p += align16(sizeof(uint32_t) * smax);
+    const int nwbm = (smax + 31) >> 5;
+    mw = (uint32_t*)p;
+    p += sizeof(uint32_t) * 32 * (size_t)(nwbm * (nwbm + 1) / 2);
+  }
+  __shared__ unsigned long long base_s;
+  __shared__ uint32_t wsum_s[kMaskWarps];
+  __shared__ int rb_next;
   // 256-byte aligned region: bit columns, then per-warp tables (table bases
   // need a zero low byte)
   {
@@ -321,6 +371,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       w4[i] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
       sfl[i] = flat;
       cnt[i] = 0;
+      if (FUSED) pid[i] = (int32_t)v;
     }
     __syncthreads();
     const int nwb = (s + 31) >> 5;
@@ -335,7 +386,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     const uint32_t tab_addr = (uint32_t)__cvta_generic_to_shared(tab);
     __syncthreads();
 
-    uint32_t* rmb = a.rmask + moff[b];
+    uint32_t* rmb = FUSED ? nullptr : a.rmask + moff[b];
     const int nblk = nwb * (nwb + 1) / 2;
     const int q0 = (int)((int64_t)nblk * wid / kMaskWarps), q1 = (int)((int64_t)nblk * (wid + 1) / kMaskWarps);
     int I = 0, J = 0;
@@ -362,7 +413,10 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       uint32_t cw = jv ? (~anti & rows_ok) : 0u;
       // the diagonal block: no self pair; lower rows keep smaller partners
       if (I == J) cw &= LOWER ? ((1u << lane) - 1u) : ~(1u << lane);
-      rmb[mask_block(LOWER, J, I, nwb) * 32 + lane] = cw;
+      if (FUSED)
+        mw[mask_block(true, J, I, nwb) * 32 + lane] = cw;
+      else
+        rmb[mask_block(LOWER, J, I, nwb) * 32 + lane] = cw;
       if (cw) atomicAdd(&cnt[j], __popc(cw));
       if (!LOWER && I != J) {
         const uint32_t tr = transpose32(cw, lane);
@@ -376,6 +430,65 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     }
     __syncthreads();
     for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
+    if (FUSED) {
+      // run offsets inside the bucket: each thread scans two consecutive rows
+      const int i0 = 2 * threadIdx.x;
+      const uint32_t c0 = i0 < s ? (uint32_t)cnt[i0] : 0u, c1 = i0 + 1 < s ? (uint32_t)cnt[i0 + 1] : 0u;
+      uint32_t inc = c0 + c1;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+      }
+      if (lane == 31) wsum_s[wid] = inc;
+      __syncthreads();
+      uint32_t before = 0, total = 0;
+      for (int w = 0; w < kMaskWarps; ++w) {
+        if (w < wid) before += wsum_s[w];
+        total += wsum_s[w];
+      }
+      const uint32_t ex = before + inc - (c0 + c1);
+      if (i0 < s) roff[i0] = ex;
+      if (i0 + 1 < s) roff[i0 + 1] = ex + c0;
+      if (threadIdx.x == 0) {
+        base_s = atomicAdd(a.cursor, (unsigned long long)total);
+        rb_next = 0;
+      }
+      __syncthreads();
+      const int64_t base = (int64_t)base_s;
+      if (base + (int64_t)total <= a.cap) {
+        for (int i = threadIdx.x; i < s; i += kMaskThreads) a.rstart[sfl[i]] = base + roff[i];
+        // runs: warps take row blocks from a shared counter, largest first;
+        // a block's rows are written one after the other as in the emit
+        // pass (partner ids of the block's partner blocks in registers)
+        const uint32_t lt = lanemask_lt();
+        while (true) {
+          int R = 0;
+          if (lane == 0) R = nwb - 1 - atomicAdd(&rb_next, 1);
+          R = __shfl_sync(0xffffffffu, R, 0);
+          if (R < 0) break;
+          const int nrows = min(32, s - (R << 5));
+          int32_t pv[kEmitChunk];
+#pragma unroll
+          for (int t = 0; t < kEmitChunk; ++t) pv[t] = t <= R ? pid[(t << 5) + lane] : 0;
+          int64_t rc = lane < nrows ? base + roff[(R << 5) + lane] : 0;
+          const uint32_t* wb = mw + (R * (R + 1) / 2) * 32;
+          switch (R + 1) {
+#define PICASSO_FUSED_CASE(N) \
+  case N:                     \
+    emit_rows<N>(wb, pv, rc, nrows, a.col, lane, lt); \
+    break;
+            PICASSO_FUSED_CASE(1) PICASSO_FUSED_CASE(2) PICASSO_FUSED_CASE(3) PICASSO_FUSED_CASE(4)
+            PICASSO_FUSED_CASE(5) PICASSO_FUSED_CASE(6) PICASSO_FUSED_CASE(7) PICASSO_FUSED_CASE(8)
+            PICASSO_FUSED_CASE(9) PICASSO_FUSED_CASE(10) PICASSO_FUSED_CASE(11) PICASSO_FUSED_CASE(12)
+            PICASSO_FUSED_CASE(13) PICASSO_FUSED_CASE(14) PICASSO_FUSED_CASE(15) PICASSO_FUSED_CASE(16)
+#undef PICASSO_FUSED_CASE
+            default:
+              break;
+          }
+        }
+      }
+    }
     __syncthreads();
   }
 }
@@ -385,8 +498,8 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   smax = max(smax, 1);
   const size_t bytes = mask_smem_bytes(smax);
-  auto kern = q <= 32 ? (a.lower ? k_bucket_mask<1, true> : k_bucket_mask<1, false>)
-                      : (a.lower ? k_bucket_mask<2, true> : k_bucket_mask<2, false>);
+  auto kern = q <= 32 ? (a.lower ? k_bucket_mask<1, true, false> : k_bucket_mask<1, false, false>)
+                      : (a.lower ? k_bucket_mask<2, true, false> : k_bucket_mask<2, false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -397,6 +510,27 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
   kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, moff, smax);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_fused(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, int32_t smax,
+                                int32_t q, cudaStream_t s) {
+  if (a.P <= 0 || a.n <= 0) return cudaSuccess;
+  if (smax > kFusedMax || !a.lower) return cudaErrorInvalidValue;
+  smax = max(smax, 1);
+  const size_t bytes = fused_smem_bytes(smax);
+  auto kern = q <= 32 ? k_bucket_mask<1, true, true> : k_bucket_mask<2, true, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMaskThreads, bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
+  kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, nullptr, smax);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -455,32 +589,6 @@ cudaError_t launch_item_bucket(const int64_t* jboff, int64_t P, int32_t* ibkt, c
 // consecutive positions (lane i writes partner i at the row's cursor plus the
 // set bits below i), so each run comes out in ascending partner order and is
 // written in one burst of stores.
-constexpr int kEmitChunk = 16;
-
-// Rows of one staged chunk of NI partner words: lane rr keeps row rr's
-// cursor; every lane reads it by shuffle, writes its partner if its bit is
-// set, and the row's cursor advances by the word's popcount.
-template <int NI>
-__device__ __forceinline__ void emit_rows(const uint32_t* __restrict__ wbuf, const int32_t (&pv)[kEmitChunk],
-                                          int64_t& rc, int nrows, int32_t* __restrict__ col, int lane, uint32_t lt) {
-  const uint32_t lbit = 1u << lane;
-  for (int rr = 0; rr < nrows; ++rr) {
-    int32_t* dst = col + __shfl_sync(0xffffffffu, rc, rr);
-    int32_t at = 0;
-#pragma unroll
-    for (int t = 0; t < NI; ++t) {
-      const uint32_t w = wbuf[t * 32 + rr];
-      // predicated store: lane i writes partner i when bit i is set
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t@p st.global.b32 [%1], %2;\n\t}"
-          :
-          : "r"(w & lbit), "l"(dst + at + __popc(w & lt)), "r"(pv[t]));
-      at += __popc(w);
-    }
-    if (lane == rr) rc += at;
-  }
-}
-
 __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, const int64_t* __restrict__ boff,
                                                               const int32_t* __restrict__ bmem,
                                                               const int64_t* __restrict__ moff,

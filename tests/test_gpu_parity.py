@@ -244,6 +244,18 @@ def test_run_all_identity(pc, orc):
     _run_both(pc, orc, chars, 1, 1, 8, 2.0)
 
 
+def test_run_all_commuting_bucket_path(pc, orc):
+    # Z/I strings all commute, so every pair of a bucket is an edge: the fused
+    # build's first column estimate (from the default commuting ratio) is too
+    # small and it reruns with the exact size; per round the CSR is checked
+    # against the oracle through the canonical form
+    g = np.random.default_rng(12)
+    chars = (g.integers(0, 2, size=(4000, 16)) * 3).astype(np.uint8)  # 0 = I, 3 = Z
+    _run_both(pc, orc, chars, 3, 1, 8, 2.0, small="off")
+    P, L = orc.round_params(4000, 1, 8, 2.0)
+    _check_build(pc, orc, chars, 3, P, L, "auto")
+
+
 def test_run_aggressive_small(pc, orc):
     # the paper's aggressive mode (P = 3%, alpha = 30) on a small set
     _run_both(pc, orc, synth.pauli_weighted(1500, 24, 0.3, seed=8), 4, 3, 100, 30.0)
