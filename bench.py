@@ -30,11 +30,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_DEFAULT, Q, P_W, NUM, DEN, ALPHA = 1_000_000, 64, 0.25, 1, 16, 1.5
-# DRAM bytes (read + write) per unit of work, from one ncu capture of each kernel on
-# round 1 of the n = 200,000 case of this workload (the bench's launches are too
-# large to capture); scaled here by the units each launch processes.
-MASK_DRAM_BYTES_PER_PAIR = 0.132    # k_bucket_mask, per tested pair
-EMIT_DRAM_BYTES_PER_ENTRY = 5.42   # k_bucket_emit, per CSR run entry
+# DRAM bytes (read + write) per algorithmic byte of the fused build pass
+# (k_bucket_mask<.., fused>: pair tests and CSR runs in one kernel), from one ncu
+# capture of round 1 of the n = 200,000 case of this workload (the bench's
+# launches are too large to capture): 1.428 GB measured / 1.337 GB algorithmic.
+FUSED_DRAM_PER_ALG_BYTE = 1.068
 METRIC = "pair tests/s (conflict build) and colored strings/s at n=1M; colors, peak bytes"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -241,31 +241,32 @@ def run_gpu(args):
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2032.0)
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    # pair-test kernel: one POPC per tested pair (parity of popc(lo ^ hi));
-    # POPC issues at 16 lanes/clk/SM
-    peak_pairs = n_sm * sm_mhz * 1e6 * 16
-    # (a run small enough for the small-round engine alone has no per-round
-    # pair-test launches: no figure then)
-    achieved = st["tested_pairs"] / (st["t_pairs_ms"] / 1e3) if st["t_pairs_ms"] > 0 else None
-    tested_per_launch = st["tested_pairs"] / max(st["pairs_launches"], 1)
-    roofline = {"bound": "alu", "kernel": "k_bucket_mask",
-                "achieved": achieved / 1e9 if achieved else None,
-                "peak": peak_pairs / 1e9, "unit": "Gpair-tests/s",
-                "frac": achieved / peak_pairs if achieved else None,
-                "traffic": MASK_DRAM_BYTES_PER_PAIR * tested_per_launch,
+    # The dominant kernel is the fused build pass: it tests every pair of a
+    # color bucket and writes the bucket's conflict runs.  Primary roofline:
+    # its algorithmic bytes (CSR runs 4 B per entry; per list entry the member
+    # words 16 B, the entry id 4 B, run start and length 12 B) per launch over
+    # its event time, against the measured HBM copy peak.  Secondary: its pair
+    # tests against one POPC per pair (16 lanes/clk/SM).  A run small enough
+    # for the small-round engine alone has no per-round build: no figures then.
+    launches_b = max(st["emit_launches"], 1)
+    avg_ms = st["t_emit_ms"] / launches_b
+    bytes_launch = st["emit_bytes"] / launches_b
+    gbs = bytes_launch / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
+    roofline = {"bound": "hbm", "kernel": "k_bucket_mask<fused> (pair tests + CSR runs)",
+                "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"] if gbs and peaks.get("hbm_gbs") else None,
+                "traffic": FUSED_DRAM_PER_ALG_BYTE * bytes_launch if gbs else None,
                 "traffic_note": "bytes per launch, scaled from an ncu capture of round 1 at n=200000",
-                "peak_source": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median under load) x 16 POPC/clk/SM",
-                "avg_launch_ms": st["t_pairs_ms"] / max(st["pairs_launches"], 1),
-                "tested_pairs_per_launch": st["tested_pairs"] / max(st["pairs_launches"], 1)}
-
-    # CSR emit pass: streams the mask words and writes the conflict CSR
-    emit_gbs = st["emit_bytes"] / (st["t_emit_ms"] / 1e3) / 1e9 if st["t_emit_ms"] > 0 else None
-    roofline_emit = {"bound": "hbm", "kernel": "k_bucket_emit", "achieved": emit_gbs,
-                     "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                     "frac": emit_gbs / peaks["hbm_gbs"] if emit_gbs and peaks.get("hbm_gbs") else None,
-                     "bytes_per_step": st["emit_bytes"], "launches_per_step": st["emit_launches"],
-                     "traffic": EMIT_DRAM_BYTES_PER_ENTRY * st["nnz_total"] / max(st["emit_launches"], 1)
-                     if "nnz_total" in st else None}
+                "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": bytes_launch,
+                "launches_per_step": st["emit_launches"]}
+    peak_pairs = n_sm * sm_mhz * 1e6 * 16
+    achieved = st["tested_pairs"] / (st["t_pairs_ms"] / 1e3) if st["t_pairs_ms"] > 0 else None
+    roofline_pairs = {"bound": "alu", "kernel": "k_bucket_mask<fused> (pair tests)",
+                      "achieved": achieved / 1e9 if achieved else None,
+                      "peak": peak_pairs / 1e9, "unit": "Gpair-tests/s",
+                      "frac": achieved / peak_pairs if achieved else None,
+                      "peak_source": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median under load) x 16 POPC/clk/SM",
+                      "tested_pairs_per_launch": st["tested_pairs"] / max(st["pairs_launches"], 1)}
 
     batch = None if args.no_batch else bench_batch(rank)
     learned_form = None if args.no_learned else bench_learned(rank)
@@ -290,7 +291,7 @@ def run_gpu(args):
         "pair_tests_per_s": pair_rate, "colors": int(len(np.unique(colors_np))),
         "colors_sum_P": st["colors_used"], "rounds": rounds,
         "peak_bytes": st["peak_bytes"], "breakdown_ms_per_step": per_step,
-        "roofline": roofline, "roofline_emit": roofline_emit, "cpu_baseline": cpu, "batch": batch, "learned": learned_form,
+        "roofline": roofline, "roofline_pairs": roofline_pairs, "cpu_baseline": cpu, "batch": batch, "learned": learned_form,
         "e2e": {"value": world * n / (ms_e2e / args.steps / 1e3), "unit": "strings/s",
                 "h2d_bytes_per_step": n * Q, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": launches, "clocks": clocks, "wall_s": t_wall,

@@ -153,18 +153,21 @@ typedef struct {
   double t_color_ms;    /* coloring sweeps + color write-back                */
   double t_carry_ms;    /* compaction of the uncolored vertices              */
   double t_pairs_ms;    /* the pair-test kernels alone (bucket join: mask
-                           pass; all pairs: count and fill)                 */
+                           pass, or the fused pass; all pairs: count and
+                           fill)                                            */
   int64_t pairs_launches;     /* launches of the pair-test kernels           */
   int64_t logical_pairs;      /* sum over builds of n_l (n_l - 1) / 2        */
   int64_t tested_pairs;       /* pair tests of the pair-test kernels: per
                                  build, bucket join sum_c s_c (s_c - 1) / 2
                                  (the mask pass tests each unordered pair of
                                  a bucket once), all pairs 2 n (n - 1)      */
-  double t_emit_ms;           /* bucket join's emit pass (CSR writes)        */
+  double t_emit_ms;           /* bucket join's emit pass (CSR writes); with the
+                                 fused pass, that same kernel's time        */
   int64_t emit_launches;
   int64_t emit_bytes;         /* bytes the emit passes move: mask words read,
                                  CSR written, member ids and run offsets
-                                 read                                       */
+                                 read; fused pass: CSR written, member words,
+                                 ids, run starts and lengths                */
   int64_t nnz_total;          /* run entries of all builds                  */
   /* the last color step's first 64 sweeps: vertices pending at the start,
    * vertices re-evaluated, and duration in microseconds (0 for the last) */
@@ -216,7 +219,14 @@ int picasso_assign_lists(void* ctx, int64_t P, int32_t L, int64_t base);
 
 /* Alg. 1 conflict-graph construction (Sec. III-A, Alg. 3's count / offsets /
  * fill structure).  Synchronises to size the CSR; returns ERR_BUDGET, before
- * allocating, if the CSR would exceed cfg.byte_budget.                     */
+ * allocating, if the CSR would exceed cfg.byte_budget.
+ * With the EARLIER form, no byte budget and color buckets of at most 512
+ * members, one fused pass tests the pairs and writes the runs, each bucket's
+ * runs as one contiguous region (the library's direct layout, read by
+ * picasso_color).  The canonical row-major CSR described by picasso_csr is
+ * made from it when asked for: by a non-NULL out here, or by
+ * picasso_get_runs / picasso_copy_csr / picasso_copy_runs (which then
+ * allocate it and synchronise).  out may be NULL.                          */
 int picasso_build_conflicts(void* ctx, picasso_csr* out);
 
 /* Alg. 1 coloring of the unconflicted vertices and of G_c (Sec. III-B static
@@ -251,7 +261,8 @@ int picasso_get_round(void* ctx, int32_t* d_gid, int32_t* d_lists,
 
 /* Run structure of the last build: d_runoff [E + 1] int64 (E = the round's
  * list entries; with one list length L, entry u*L+k) where the run of row
- * u's k-th color is col[runoff[e] .. runoff[e+1]).  Owned by the context.  */
+ * u's k-th color is col[runoff[e] .. runoff[e+1]) of the canonical CSR.
+ * Owned by the context.                                                    */
 int picasso_get_runs(void* ctx, const int64_t** d_runoff);
 
 /* Copy the last build's CSR into caller-owned device buffers: d_off
