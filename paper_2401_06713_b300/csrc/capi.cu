@@ -411,7 +411,8 @@ int build_conflicts(Ctx* c) {
   uint32_t *words = nullptr, *rmask = nullptr;
   unsigned long long* dsq = nullptr;
   int64_t *boff = nullptr, *moff = nullptr, *jboff = nullptr;
-  int32_t *bmem = nullptr, *ibkt = nullptr;
+  int32_t *bmem = nullptr, *ibkt = nullptr, *bpid = nullptr;
+  uint4* bxz = nullptr;
   void* tmp = nullptr;
   int st = PICASSO_OK;
   auto cleanup = [&]() {
@@ -426,6 +427,8 @@ int build_conflicts(Ctx* c) {
     release(c, &moff);
     release(c, &jboff);
     release(c, &ibkt);
+    release(c, &bxz);
+    release(c, &bpid);
     release(c, &rmask);
     release(c, (uint8_t**)&tmp);
   };
@@ -515,6 +518,11 @@ int build_conflicts(Ctx* c) {
       // the cursor: the context's error block, words 2..3 (8-byte aligned)
       unsigned long long* cur = reinterpret_cast<unsigned long long*>(c->d_err + 2);
       TRY(alloc(c, &c->rstart, E));
+      TRY(alloc(c, &bxz, E));
+      TRY(alloc(c, &bpid, E));
+      TRYC(launch_bucket_gather(a, bmem, bxz, bpid, s));
+      a.bxz = bxz;
+      a.bpid = bpid;
       TRY(alloc(c, &c->col, cap));
       a.rstart = c->rstart;
       a.col = c->col;

@@ -187,6 +187,8 @@ struct ConflictArgs {
   int64_t* rstart;                // [E]
   unsigned long long* cursor;     // one word, zero on entry
   int64_t cap;                    // entries col holds
+  const uint4* bxz;               // [E] member words in bucket-slot order (x lo, x hi, z lo, z hi)
+  const int32_t* bpid;            // [E] member vertex ids in bucket-slot order
 };
 
 // Buckets: members of color c are bmem[boff[c] .. boff[c+1]) ascending; a
@@ -212,6 +214,9 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
 constexpr int kFusedMax = 512;
 cudaError_t launch_bucket_fused(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, int32_t smax,
                                 int32_t q, cudaStream_t s);
+// bxz[p], bpid[p]: words and vertex id of the member at bucket slot p < E.
+cudaError_t launch_bucket_gather(const ConflictArgs& a, const int32_t* bmem, uint4* bxz, int32_t* bpid,
+                                 cudaStream_t s);
 cudaError_t launch_bucket_jblocks(const uint32_t* bcount, int64_t P, uint32_t* out, cudaStream_t s);
 // jboff [P+1]: prefix of ceil(s_c / 32); counter: one device int32 (reset here)
 cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,

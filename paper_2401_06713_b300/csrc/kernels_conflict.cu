@@ -211,8 +211,22 @@ __host__ __device__ inline size_t mask_smem_bytes(int smax) {
 __host__ __device__ inline size_t fused_smem_bytes(int smax) {
   const int nwb = (smax + 31) >> 5;
   return mask_smem_bytes(smax) + align16(sizeof(int32_t) * smax) + align16(sizeof(uint32_t) * smax) +
-         sizeof(uint32_t) * 32 * (size_t)(nwb * (nwb + 1) / 2);
+         sizeof(uint32_t) * 32 * (size_t)(nwb * (nwb + 1) / 2) +
+         // the other buffer of member words, entry ids and vertex ids
+         align16(sizeof(uint4) * smax) + 2 * align16(sizeof(int32_t) * smax);
 }
+
+// Asynchronous global -> shared copies (the next bucket's members).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // 32 x 32 bit transpose across the warp: on entry lane r holds row r (bit k =
 // M[r][k]); on exit lane k holds column k (bit r = M[r][k]).  Five butterfly
@@ -339,6 +353,8 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   int32_t* pid = nullptr;
   uint32_t* roff = nullptr;
   uint32_t* mw = nullptr;
+  uint4* w4b = nullptr;
+  int32_t *sflb = nullptr, *pidb = nullptr;
   if (FUSED) {
     pid = (int32_t*)p;
     p += align16(sizeof(int32_t) * smax);
@@ -347,6 +363,12 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     const int nwbm = (smax + 31) >> 5;
     mw = (uint32_t*)p;
     p += sizeof(uint32_t) * 32 * (size_t)(nwbm * (nwbm + 1) / 2);
+    w4b = (uint4*)p;
+    p += align16(sizeof(uint4) * smax);
+    sflb = (int32_t*)p;
+    p += align16(sizeof(int32_t) * smax);
+    pidb = (int32_t*)p;
+    p += align16(sizeof(int32_t) * smax);
   }
   __shared__ unsigned long long base_s;
   __shared__ uint32_t wsum_s[kMaskWarps];
@@ -360,18 +382,71 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   uint32_t* colw = (uint32_t*)p;  // [nwb][2 QW][32]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
-  for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
-    const int64_t o = boff[b];
-    const int s = (int)(boff[b + 1] - o);
-    if (s == 0) continue;
+  // fused pass: a bucket's members (words, entry ids, vertex ids, gathered in
+  // slot order beforehand) are copied asynchronously into one of two buffers
+  // while the previous bucket's runs are written
+  auto fetch = [&](int64_t o, int s, uint4* w4x, int32_t* sflx, int32_t* pidx) {
     for (int i = threadIdx.x; i < s; i += kMaskThreads) {
-      const int32_t flat = bmem[o + i];
-      const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
-      const uint64_t x = a.xz[2 * v], z = a.xz[2 * v + 1];
-      w4[i] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
-      sfl[i] = flat;
-      cnt[i] = 0;
-      if (FUSED) pid[i] = (int32_t)v;
+      cp_async16(w4x + i, a.bxz + o + i);
+      cp_async4(sflx + i, bmem + o + i);
+      cp_async4(pidx + i, a.bpid + o + i);
+    }
+    cp_async_commit();
+  };
+  auto swap_buffers = [&]() {
+    uint4* t4 = w4;
+    w4 = w4b;
+    w4b = t4;
+    int32_t* t = sfl;
+    sfl = sflb;
+    sflb = t;
+    t = pid;
+    pid = pidb;
+    pidb = t;
+  };
+  int64_t o_nx = 0;
+  int s_nx = 0;
+  if (FUSED && blockIdx.x < a.P) {
+    o_nx = boff[blockIdx.x];
+    s_nx = (int)(boff[blockIdx.x + 1] - o_nx);
+    fetch(o_nx, s_nx, w4, sfl, pid);
+  }
+  for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
+    int64_t o;
+    int s;
+    int64_t o2 = 0;
+    int s2 = 0;
+    if (FUSED) {
+      const int64_t b2 = b + gridDim.x;
+      if (b2 < a.P) {
+        o2 = boff[b2];
+        s2 = (int)(boff[b2 + 1] - o2);
+      }
+      o = o_nx;
+      s = s_nx;
+      // w4 / sfl / pid hold this bucket (the last fetch went there)
+      cp_async_wait_all();
+      __syncthreads();
+      if (s == 0) {
+        fetch(o2, s2, w4b, sflb, pidb);
+        swap_buffers();
+        o_nx = o2;
+        s_nx = s2;
+        continue;
+      }
+      for (int i = threadIdx.x; i < s; i += kMaskThreads) cnt[i] = 0;
+    } else {
+      o = boff[b];
+      s = (int)(boff[b + 1] - o);
+      if (s == 0) continue;
+      for (int i = threadIdx.x; i < s; i += kMaskThreads) {
+        const int32_t flat = bmem[o + i];
+        const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
+        const uint64_t x = a.xz[2 * v], z = a.xz[2 * v + 1];
+        w4[i] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
+        sfl[i] = flat;
+        cnt[i] = 0;
+      }
     }
     __syncthreads();
     const int nwb = (s + 31) >> 5;
@@ -428,6 +503,9 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
         J = I;
       }
     }
+    // the next bucket's members go to the other buffer while this one's runs
+    // are written
+    if (FUSED) fetch(o2, s2, w4b, sflb, pidb);
     __syncthreads();
     for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
     if (FUSED) {
@@ -490,7 +568,13 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       }
     }
     __syncthreads();
+    if (FUSED) {
+      swap_buffers();
+      o_nx = o2;
+      s_nx = s2;
+    }
   }
+  if (FUSED) cp_async_wait_all();
 }
 
 cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
@@ -510,6 +594,25 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
   kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, moff, smax);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void k_bucket_gather(ConflictArgs a, const int32_t* __restrict__ bmem, uint4* __restrict__ bxz,
+                                int32_t* __restrict__ bpid) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.E) return;
+  const int32_t flat = bmem[p];
+  const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
+  const uint64_t x = a.xz[2 * v], z = a.xz[2 * v + 1];
+  bxz[p] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
+  bpid[p] = (int32_t)v;
+}
+
+cudaError_t launch_bucket_gather(const ConflictArgs& a, const int32_t* bmem, uint4* bxz, int32_t* bpid,
+                                 cudaStream_t s) {
+  if (a.E <= 0) return cudaSuccess;
+  k_bucket_gather<<<(unsigned)((a.E + 255) / 256), 256, 0, s>>>(a, bmem, bxz, bpid);
   count_launches(1);
   return cudaGetLastError();
 }
