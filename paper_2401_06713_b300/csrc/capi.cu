@@ -132,6 +132,7 @@ struct Ctx {
   int32_t* perm = nullptr;
   int32_t* gid_r = nullptr;
   uint64_t* xz_r = nullptr;
+  uint32_t* bcount = nullptr;  // [P] bucket sizes, when assign counted them
   // build
   bool built = false;
   int64_t nnz = 0, max_bucket = 0;
@@ -250,6 +251,7 @@ void free_build(Ctx* c) {
 }
 
 void free_assign(Ctx* c) {
+  release(c, &c->bcount);
   release(c, &c->lists);
   release(c, &c->prio);
   release(c, &c->perm);
@@ -397,8 +399,17 @@ int assign_round(Ctx* c) {
     ST(alloc(c, &c->ent_v, c->E));
     CK(launch_entry_owner(c->loff, n, c->ent_v, s));
   }
+  // bucket sizes counted as the lists are drawn when the build will join
+  // through buckets (lists of at most 32 colors)
+  const int algo = c->cfg.conflict_algo;
+  const bool buckets = Lmax <= 32 && c->Ptot < kBucketMaxP && algo != PICASSO_CONFLICT_ALLPAIRS &&
+                       !(algo == PICASSO_CONFLICT_AUTO && n <= kSmallRoundAllPairs);
+  if (buckets) {
+    ST(alloc(c, &c->bcount, c->Ptot));
+    CK(cudaMemsetAsync(c->bcount, 0, sizeof(uint32_t) * c->Ptot, s));
+  }
   CK(launch_assign_lists(c->round, c->gid_r, n, c->d_soff, c->nsets, c->d_sets, Lmax, c->loff, c->lists, c->prio,
-                         s));
+                         c->bcount, s));
   c->assigned = true;
   return PICASSO_OK;
 }
@@ -462,12 +473,17 @@ int build_conflicts(Ctx* c) {
   int64_t smax = 0, bucket_pairs = 0;
   if (algo != PICASSO_CONFLICT_ALLPAIRS) {
     // color buckets: sizes, offsets, largest bucket
-    TRY(alloc(c, &bcount, P));
     TRY(alloc(c, &boff, P + 1));
     TRY(alloc(c, &dmax, 2));
     TRY(alloc(c, &dsq, 1));
-    TRYC(cudaMemsetAsync(bcount, 0, sizeof(uint32_t) * P, s));
-    TRYC(launch_bucket_hist(c->lists, E, bcount, s));
+    if (c->bcount) {
+      bcount = c->bcount;  // counted while the lists were drawn
+      c->bcount = nullptr;
+    } else {
+      TRY(alloc(c, &bcount, P));
+      TRYC(cudaMemsetAsync(bcount, 0, sizeof(uint32_t) * P, s));
+      TRYC(launch_bucket_hist(c->lists, E, bcount, s));
+    }
     TRYC(launch_bucket_stats(bcount, P, dmax, dsq, s));
     TRYC(cudaMemcpyAsync(c->h_buf, dmax, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     TRYC(cudaMemcpyAsync(c->h_buf + 1, dsq, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));

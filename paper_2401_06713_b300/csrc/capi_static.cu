@@ -195,7 +195,7 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
     SCK(cudaMemcpyAsync(dset, &sr, sizeof(sr), cudaMemcpyHostToDevice, s));
     SCK(launch_list_offsets(gid, m, soff, 1, dset, len, loff, tmp, s));
     SCK(launch_entry_owner(loff, m, ent_v, s));
-    SCK(launch_assign_lists(round, gid, m, soff, 1, dset, L, loff, lists, prio, s));
+    SCK(launch_assign_lists(round, gid, m, soff, 1, dset, L, loff, lists, prio, nullptr, s));
 
     ConflictArgs a{};
     a.n = m;

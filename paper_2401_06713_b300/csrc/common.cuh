@@ -106,6 +106,56 @@ __device__ __forceinline__ void draw_list(uint64_t seed, int32_t round, int64_t 
   for (int a = 0; a < L; ++a) out[a] = (int32_t)(cofs + sel[a]);
 }
 
+// draw_list for L <= 32 with the picks in registers: the same draws as
+// draw_list (Floyd's sampling on the same Philox words), every loop unrolled
+// so no pick leaves registers, then ascending order by a 32-wide bitonic
+// network (unused slots hold the maximum and sort last).  With bcount, the
+// bucket color of every pick is also counted.
+__device__ __forceinline__ void draw_list32(uint64_t seed, int32_t round, int64_t g, int64_t P, int L, int64_t cofs,
+                                            int32_t* __restrict__ out, uint32_t* __restrict__ bcount) {
+  uint32_t sel[32];
+  u32x4 blk{0, 0, 0, 0};
+#pragma unroll
+  for (int m = 0; m < 32; ++m) {
+    sel[m] = 0xFFFFFFFFu;
+    if (m < L) {
+      if ((m & 3) == 0) blk = philox_block(seed, round, g, kTagList, (uint32_t)(m >> 2));
+      const uint32_t x = pick(blk, (uint32_t)(m & 3));
+      const uint64_t j = (uint64_t)(P - L + m);
+      const uint32_t t = (uint32_t)(((uint64_t)x * (j + 1)) >> 32);
+      bool seen = false;
+#pragma unroll
+      for (int a = 0; a < m; ++a) seen |= (sel[a] == t);
+      sel[m] = seen ? (uint32_t)j : t;
+    }
+  }
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int d = k >> 1; d > 0; d >>= 1) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int l = i ^ d;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const uint32_t x = sel[i], y = sel[l];
+          const bool sw = (x > y) == up;
+          sel[i] = sw ? y : x;
+          sel[l] = sw ? x : y;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 32; ++a) {
+    if (a < L) {
+      const int32_t c = (int32_t)(cofs + sel[a]);
+      out[a] = c;
+      if (bcount) atomicAdd(bcount + c, 1u);
+    }
+  }
+}
+
 // Symplectic commutation test for one-word strings.
 __device__ __forceinline__ bool commute1(uint64_t xu, uint64_t zu, uint64_t xv, uint64_t zv) {
   return (__popcll((xu & zv) ^ (zu & xv)) & 1) == 0;
@@ -153,9 +203,11 @@ cudaError_t launch_entry_owner(const int64_t* loff, int64_t n, int32_t* ent_v, c
 // Priorities of the round's vertices (draw 0 of the PRIO stream), no lists.
 cudaError_t launch_round_prio(int32_t round, const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
                               const SetRound* sets, uint32_t* prio, cudaStream_t s);
+// bcount (may be null; used when every list has at most 32 colors): bucket
+// sizes, counted as the lists are drawn (zeroed by the caller).
 cudaError_t launch_assign_lists(int32_t round, const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
                                 const SetRound* sets, int32_t Lmax, const int64_t* loff, int32_t* lists,
-                                uint32_t* prio, cudaStream_t s);
+                                uint32_t* prio, uint32_t* bcount, cudaStream_t s);
 
 // Exclusive scan of n uint32 counts into out[n+1] (int64); tmp needs
 // scan_tmp_bytes(n) bytes.

@@ -122,28 +122,31 @@ template <int LCAP>
 __global__ void k_assign_lists(int32_t round, const int32_t* __restrict__ gid, int64_t n,
                                const int64_t* __restrict__ soff, int nsets, const SetRound* __restrict__ sets,
                                const int64_t* __restrict__ loff, int32_t* __restrict__ lists,
-                               uint32_t* __restrict__ prio) {
+                               uint32_t* __restrict__ prio, uint32_t* __restrict__ bcount) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const int64_t gg = gid ? (int64_t)gid[v] : v;
   const int k = nsets > 1 ? set_of(soff, nsets, gg) : 0;
   const SetRound sr = sets[k];
   const int64_t g = gg - soff[k];  // id within the set
-  draw_list<LCAP>(sr.seed, round, g, sr.P, sr.L, sr.cofs, lists + loff[v]);
+  if (LCAP == 32)
+    draw_list32(sr.seed, round, g, sr.P, sr.L, sr.cofs, lists + loff[v], bcount);
+  else
+    draw_list<LCAP>(sr.seed, round, g, sr.P, sr.L, sr.cofs, lists + loff[v]);
   prio[v] = philox_block(sr.seed, round, g, kTagPrio, 0u).x;
 }
 
 cudaError_t launch_assign_lists(int32_t round, const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets,
                                 const SetRound* sets, int32_t Lmax, const int64_t* loff, int32_t* lists,
-                                uint32_t* prio, cudaStream_t s) {
+                                uint32_t* prio, uint32_t* bcount, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n + 127) / 128);
   if (Lmax <= 32) {
-    k_assign_lists<32><<<blocks, 128, 0, s>>>(round, gid, n, soff, nsets, sets, loff, lists, prio);
+    k_assign_lists<32><<<blocks, 128, 0, s>>>(round, gid, n, soff, nsets, sets, loff, lists, prio, bcount);
   } else if (Lmax <= 128) {
-    k_assign_lists<128><<<blocks, 128, 0, s>>>(round, gid, n, soff, nsets, sets, loff, lists, prio);
+    k_assign_lists<128><<<blocks, 128, 0, s>>>(round, gid, n, soff, nsets, sets, loff, lists, prio, nullptr);
   } else {
-    k_assign_lists<kMaxL><<<blocks, 128, 0, s>>>(round, gid, n, soff, nsets, sets, loff, lists, prio);
+    k_assign_lists<kMaxL><<<blocks, 128, 0, s>>>(round, gid, n, soff, nsets, sets, loff, lists, prio, nullptr);
   }
   count_launches(1);
   return cudaGetLastError();
