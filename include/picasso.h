@@ -83,8 +83,24 @@ typedef struct {
   int32_t color_algo;    /* picasso_color_algo                                */
   int32_t csr_form;      /* picasso_csr_form                                  */
   int32_t small_engine;  /* picasso_small_engine                              */
-  int32_t reserved;      /* must be 0                                         */
+  int32_t budget_mode;   /* picasso_budget_mode                               */
 } picasso_config;
+
+/* What picasso_round / picasso_run do with a round whose conflict CSR would
+ * exceed cfg.byte_budget (single-set contexts; the explicit steps always
+ * return PICASSO_ERR_BUDGET):
+ *   FAIL  return PICASSO_ERR_BUDGET before allocating the CSR (Alg. 3 sizes
+ *         the CSR first, too);
+ *   CHUNK color the round in chunks of its coloring order, each chunk's CSR
+ *         rows (8 bytes per row + 8, 4 per run entry) within the budget:
+ *         emit the chunk's rows, color them, free them, next chunk.  In the
+ *         EARLIER form a row lists only earlier neighbours, so the colors are
+ *         those of the unchunked round.  ERR_BUDGET only if one vertex's rows
+ *         alone exceed the budget.                                        */
+typedef enum {
+  PICASSO_BUDGET_FAIL = 0,
+  PICASSO_BUDGET_CHUNK = 1
+} picasso_budget_mode;
 
 /* Which half of G_c the conflict CSR stores.  The coloring step only reads a
  * vertex's earlier neighbours, so EARLIER (the default) keeps each pair once,
@@ -177,6 +193,8 @@ typedef struct {
   int32_t small_rounds;       /* rounds the small-round engine ran          */
   int32_t small_stops;        /* engine launches that handed a round back   */
   double t_small_ms;          /* time in the small-round engine             */
+  int32_t round_chunks;       /* chunks of the rounds colored by chunk      */
+  int32_t pad_;
 } picasso_stats;
 
 /* Fill *cfg with the defaults: seed 0, P = n/8, alpha = 2 (the paper's normal

@@ -143,6 +143,13 @@ struct Ctx {
   // direct layout (fused pass): entry e's run is col[rstart[e] ..
   // rstart[e] + rcnt[e]); off and runoff are made on request (canonical_csr)
   bool direct = false;
+  // a round over the byte budget in chunk mode: the count pass's buckets and
+  // masks kept for the chunked emit (the runs of one chunk at a time)
+  bool chunk_pending = false;
+  int64_t *ck_boff = nullptr, *ck_moff = nullptr, *ck_jboff = nullptr;
+  int32_t *ck_bmem = nullptr, *ck_ibkt = nullptr;
+  uint32_t* ck_rmask = nullptr;
+  int32_t round_chunks = 0;  // chunks of all chunked rounds
   int64_t* rstart = nullptr;
   uint32_t* rcnt = nullptr;
   double commute_ratio = 0.6;  // nnz / bucket pair bound of the last fused build
@@ -246,6 +253,13 @@ void free_build(Ctx* c) {
   release(c, &c->rstart);
   release(c, &c->rcnt);
   c->direct = false;
+  release(c, &c->ck_boff);
+  release(c, &c->ck_moff);
+  release(c, &c->ck_jboff);
+  release(c, &c->ck_bmem);
+  release(c, &c->ck_ibkt);
+  release(c, &c->ck_rmask);
+  c->chunk_pending = false;
   c->built = false;
   c->nnz = 0;
 }
@@ -414,7 +428,7 @@ int assign_round(Ctx* c) {
   return PICASSO_OK;
 }
 
-int build_conflicts(Ctx* c) {
+int build_conflicts(Ctx* c, bool chunk_ok) {
   const int64_t n = c->n, P = c->Ptot, E = c->E;
   cudaStream_t s = c->s;
 
@@ -469,7 +483,10 @@ int build_conflicts(Ctx* c) {
 
   int algo = c->cfg.conflict_algo;
   // small rounds: testing all n (n-1) pairs costs less than building buckets
-  if (algo == PICASSO_CONFLICT_AUTO && n <= kSmallRoundAllPairs) algo = PICASSO_CONFLICT_ALLPAIRS;
+  // (chunk mode keeps small rounds on the bucket join, which can emit by chunk)
+  const bool chunking = chunk_ok && c->cfg.byte_budget > 0 && c->cfg.budget_mode == PICASSO_BUDGET_CHUNK &&
+                        c->nsets == 1;
+  if (algo == PICASSO_CONFLICT_AUTO && n <= kSmallRoundAllPairs && !chunking) algo = PICASSO_CONFLICT_ALLPAIRS;
   int64_t smax = 0, bucket_pairs = 0;
   if (algo != PICASSO_CONFLICT_ALLPAIRS) {
     // color buckets: sizes, offsets, largest bucket
@@ -639,6 +656,27 @@ int build_conflicts(Ctx* c) {
   }
   const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
   if (c->cfg.byte_budget > 0 && csr_bytes > c->cfg.byte_budget) {
+    if (chunking && algo == PICASSO_CONFLICT_BUCKET) {
+      // the round goes by chunks of coloring order (color_chunked)
+      c->ck_boff = boff;
+      c->ck_moff = moff;
+      c->ck_jboff = jboff;
+      c->ck_bmem = bmem;
+      c->ck_ibkt = ibkt;
+      c->ck_rmask = rmask;
+      boff = moff = jboff = nullptr;
+      bmem = ibkt = nullptr;
+      rmask = nullptr;
+      c->t_pairs += elapsed(c, 2, 3);
+      c->pairs_launches += 1;
+      c->tested_pairs += tested / 2;
+      c->logical_pairs += c->remaining[0] * (c->remaining[0] - 1) / 2;
+      cleanup();
+      c->nnz = nnz;
+      c->nnz_total += nnz;
+      c->chunk_pending = true;
+      return PICASSO_OK;
+    }
     cleanup();
     release(c, &c->runoff);
     return PICASSO_ERR_BUDGET;
@@ -649,7 +687,7 @@ int build_conflicts(Ctx* c) {
   a.col = c->col;
   TRYC(cudaEventRecord(c->ev[4], s));
   if (algo == PICASSO_CONFLICT_BUCKET) {
-    TRYC(launch_bucket_emit(a, boff, bmem, moff, jboff, ibkt, c->d_err + 2, s));
+    TRYC(launch_bucket_emit(a, boff, bmem, moff, jboff, ibkt, c->d_err + 2, 0, n, 0, s));
   } else {
     TRYC(launch_allpairs(a, true, s));
   }
@@ -1148,12 +1186,150 @@ int run_small(Ctx* c) {
   return PICASSO_OK;
 }
 
+// A round whose CSR exceeds the byte budget (chunk mode): the vertices in
+// coloring order are cut into chunks whose own CSR rows fit the budget (8
+// bytes per row + 1, 4 per run entry); chunk by chunk the rows are emitted
+// and colored, earlier chunks' colors already final.  In the EARLIER form a
+// row only lists earlier neighbours, so each chunk's coloring is exact.
+int color_chunked(Ctx* c) {
+  const int64_t n = c->n;
+  const int64_t budget = c->cfg.byte_budget;
+  cudaStream_t s = c->s;
+  uint16_t* kcur = nullptr;
+  uint32_t *rcur = nullptr, *blkw = nullptr, *clist = nullptr;
+  int32_t *blk = nullptr, *ctl = nullptr, *colk = nullptr;
+  void* tmp = nullptr;
+  int st = PICASSO_OK;
+  auto cleanup = [&]() {
+    release(c, &kcur);
+    release(c, &rcur);
+    release(c, &blkw);
+    release(c, &clist);
+    release(c, &blk);
+    release(c, &ctl);
+    release(c, &colk);
+    release(c, (uint8_t**)&tmp);
+  };
+#define TRY(expr)           \
+  do {                      \
+    st = (expr);            \
+    if (st != PICASSO_OK) { \
+      cleanup();            \
+      return st;            \
+    }                       \
+  } while (0)
+#define TRYC(expr)                                \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) {                      \
+      st = map_err(_e);                           \
+      if (st == PICASSO_ERR_CUDA) c->sticky = st; \
+      cleanup();                                  \
+      return st;                                  \
+    }                                             \
+  } while (0)
+  // row offsets give every chunk's bytes: rows [lo, hi) take
+  // 8 (hi - lo + 1) + 4 (off[hi] - off[lo])
+  TRY(alloc(c, &c->off, n + 1));
+  TRYC(launch_row_offsets(c->runoff, c->loff, n, c->off, s));
+  std::vector<int64_t> off((size_t)n + 1);
+  TRYC(cudaMemcpyAsync(off.data(), c->off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaStreamSynchronize(s));
+  free_color(c);
+  TRY(alloc(c, &c->state, n));
+  TRY(alloc(c, &kcur, n));
+  TRY(alloc(c, &rcur, n));
+  TRY(alloc(c, &blk, n));
+  TRY(alloc(c, &blkw, n));
+  TRY(alloc(c, &ctl, kCtlWords));
+  TRY(alloc(c, &clist, kClistWords * c->Ptot));
+  TRY(alloc(c, &c->flag, n));
+  TRY(alloc(c, &c->pos, n + 1));
+  TRY(alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(n)));
+  TRYC(cudaMemsetAsync(clist, 0, sizeof(uint32_t) * kClistWords * c->Ptot, s));
+  TRYC(cudaMemsetAsync(ctl, 0, sizeof(int32_t) * kCtlWords, s));
+  ColorArgs a{};
+  a.n = n;
+  a.lists = c->lists;
+  a.loff = c->loff;
+  a.runoff = c->runoff;
+  a.state = c->state;
+  a.kcur = kcur;
+  a.rcur = rcur;
+  a.blk = blk;
+  a.blkw = blkw;
+  a.ranked = 1;
+  a.clist = clist;
+  a.xz = c->xz_r;
+  TRYC(launch_color_init(a, c->prio, ctl, s));
+  ConflictArgs ca{};
+  ca.n = n;
+  ca.E = c->E;
+  ca.Lmax = c->Lmax;
+  ca.Lu = c->Lu;
+  ca.P = c->Ptot;
+  ca.xz = c->xz_r;
+  ca.lists = c->lists;
+  ca.loff = c->loff;
+  ca.ent_v = c->ent_v;
+  ca.err = c->d_err;
+  ca.lower = 1;
+  ca.rmask = c->ck_rmask;
+  ca.runoff = c->runoff;
+  int64_t lo = 0;
+  int64_t peak = 0;
+  int32_t chunks = 0;
+  while (lo < n) {
+    int64_t hi = lo;
+    while (hi < n && 8 * (hi + 1 - lo + 1) + 4 * (off[hi + 1] - off[lo]) <= budget) ++hi;
+    if (hi == lo) {
+      // one vertex's rows alone exceed the budget
+      cleanup();
+      return PICASSO_ERR_BUDGET;
+    }
+    const int64_t cnnz = off[hi] - off[lo];
+    TRY(alloc(c, &colk, cnnz));
+    ca.col = colk;
+    TRYC(launch_bucket_emit(ca, c->ck_boff, c->ck_bmem, c->ck_moff, c->ck_jboff, c->ck_ibkt, c->d_err + 2, lo, hi,
+                            off[lo], s));
+    a.col = colk;
+    a.cbase = off[lo];
+    a.v0 = lo;
+    a.n = hi - lo;
+    TRYC(launch_color_ordered(a, nullptr, ctl + 5, s));
+    TRYC(cudaMemcpyAsync(c->h_buf, ctl + 5, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    TRYC(cudaStreamSynchronize(s));
+    if (*(int32_t*)c->h_buf != 0) {
+      cleanup();
+      return PICASSO_ERR_TIMEOUT;
+    }
+    release(c, &colk);
+    peak = std::max(peak, 8 * (hi - lo + 1) + 4 * cnnz);
+    ++chunks;
+    lo = hi;
+  }
+  c->set_peak_bytes[0] = std::max(c->set_peak_bytes[0], peak);
+  c->round_chunks += chunks;
+  TRYC(launch_carry_flags(c->state, n, c->gid_r, c->perm, c->d_soff, c->nsets, c->d_sets, c->color, c->flag, s));
+  TRYC(launch_scan_u32(c->flag, n, c->pos, tmp, s));
+  TRYC(cudaMemcpyAsync(c->h_buf, c->pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaStreamSynchronize(s));
+  c->sweeps = 0;
+  c->n_remaining = c->h_buf[0];
+  c->n_colored = n - c->n_remaining;
+  c->colored_done = true;
+  cleanup();
+#undef TRY
+#undef TRYC
+  return PICASSO_OK;
+}
+
 int validate_cfg(const picasso_config* cfg) {
   if (cfg->palette_num < 1 || cfg->palette_den < 1 || cfg->palette_num > (int64_t(1) << 32) ||
       cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
       cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2 ||
       cfg->color_algo < 0 || cfg->color_algo > 1 || cfg->csr_form < 0 || cfg->csr_form > 1 ||
-      cfg->small_engine < 0 || cfg->small_engine > 1 || cfg->reserved != 0)
+      cfg->small_engine < 0 || cfg->small_engine > 1 || cfg->budget_mode < 0 || cfg->budget_mode > 1)
     return PICASSO_ERR_INVALID_ARG;
   return PICASSO_OK;
 }
@@ -1308,7 +1484,7 @@ int picasso_build_conflicts(void* ctx, picasso_csr* out) {
   free_color(c);
   free_build(c);
   phase_begin(c);
-  ST(build_conflicts(c));
+  ST(build_conflicts(c, false));
   CK(phase_end(c, &c->t_build));
   if (out) {
     ST(canonical_csr(c));
@@ -1354,8 +1530,18 @@ int picasso_round(void* ctx, int64_t* n_remaining) {
   phase_begin(c);
   ST(assign_round(c));
   CK(phase_end(c, &c->t_assign));
-  ST(picasso_build_conflicts(ctx, nullptr));
-  ST(picasso_color(ctx, nullptr));
+  free_color(c);
+  free_build(c);
+  phase_begin(c);
+  ST(build_conflicts(c, true));
+  CK(phase_end(c, &c->t_build));
+  if (c->chunk_pending) {
+    phase_begin(c);
+    ST(color_chunked(c));
+    CK(phase_end(c, &c->t_color));
+  } else {
+    ST(picasso_color(ctx, nullptr));
+  }
   return picasso_carry(ctx, n_remaining);
 }
 
@@ -1470,6 +1656,7 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->small_rounds = c->small_rounds;
   out->small_stops = c->small_stops;
   out->t_small_ms = c->t_small;
+  out->round_chunks = c->round_chunks;
   const int ns = c->sweeps < kSweepLog ? c->sweeps : kSweepLog;
   const unsigned long long* t = reinterpret_cast<const unsigned long long*>(c->sweep_log + 8 + kSweepLog);
   for (int i = 0; i < ns; ++i) {

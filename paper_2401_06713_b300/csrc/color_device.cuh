@@ -141,8 +141,8 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
         my_rs = ld_run<FRESH>(a.rstart + row + kl);
         my_re = my_rs + ld_run<FRESH>(a.rcnt + row + kl);
       } else {
-        my_rs = ld_run<FRESH>(a.runoff + row + kl);
-        my_re = ld_run<FRESH>(a.runoff + row + kl + 1);
+        my_rs = ld_run<FRESH>(a.runoff + row + kl) - a.cbase;
+        my_re = ld_run<FRESH>(a.runoff + row + kl + 1) - a.cbase;
       }
     }
     const uint32_t my_c = kl < L ? (uint32_t)ld_run<FRESH>(a.lists + row + kl) : 0u;

@@ -271,9 +271,11 @@ cudaError_t launch_bucket_gather(const ConflictArgs& a, const int32_t* bmem, uin
                                  cudaStream_t s);
 cudaError_t launch_bucket_jblocks(const uint32_t* bcount, int64_t P, uint32_t* out, cudaStream_t s);
 // jboff [P+1]: prefix of ceil(s_c / 32); counter: one device int32 (reset here)
+// Rows of vertices in [lo, hi) only (a chunk of the round), written at
+// runoff - base.
 cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
                                const int64_t* moff, const int64_t* jboff, const int32_t* ibkt, int32_t* counter,
-                               cudaStream_t s);
+                               int64_t lo, int64_t hi, int64_t base, cudaStream_t s);
 // ibkt [jboff[P]]: the bucket of every emit work item.
 cudaError_t launch_item_bucket(const int64_t* jboff, int64_t P, int32_t* ibkt, cudaStream_t s);
 cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s);
@@ -287,6 +289,8 @@ struct ColorArgs {
   const int32_t* lists;
   const int64_t* loff;
   const int64_t* runoff;   // [E+1] canonical layout: run of entry e ends at runoff[e+1]
+  int64_t cbase;           // canonical layout: run offsets are col indices + cbase
+  int64_t v0;              // ordered pass: position t is vertex v0 + t (a chunk of the round)
   const int64_t* rstart;   // direct layout (rcnt set): run of e is rstart[e] .. + rcnt[e]
   const uint32_t* rcnt;
   const int32_t* col;

@@ -133,8 +133,8 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
       return;
     }
     const uint32_t c = (uint32_t)a.lists[row + k];
-    const int64_t rs = a.rcnt ? a.rstart[row + k] : a.runoff[row + k];
-    const int64_t r1 = a.rcnt ? rs + a.rcnt[row + k] : a.runoff[row + k + 1];
+    const int64_t rs = a.rcnt ? a.rstart[row + k] : a.runoff[row + k] - a.cbase;
+    const int64_t r1 = a.rcnt ? rs + a.rcnt[row + k] : a.runoff[row + k + 1] - a.cbase;
     bool blocked = false;
     int64_t first_wait = -1;
     int32_t wait_u = -1;
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256, 6) k_color_ordered(ColorArgs a, const int
   const int64_t gwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   for (int64_t t = wid; t < a.n; t += gwarps) {
-    if (!ordered_vertex<false>(a, order ? __ldcg(&order[t]) : (int32_t)t, lane, err)) return;
+    if (!ordered_vertex<false>(a, order ? __ldcg(&order[t]) : (int32_t)(a.v0 + t), lane, err)) return;
   }
 }
 

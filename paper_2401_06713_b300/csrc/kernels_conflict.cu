@@ -318,9 +318,11 @@ constexpr int kEmitChunk = 16;
 // set, and the row's cursor advances by the word's popcount.
 template <int NI>
 __device__ __forceinline__ void emit_rows(const uint32_t* __restrict__ wbuf, const int32_t (&pv)[kEmitChunk],
-                                          int64_t& rc, int nrows, int32_t* __restrict__ col, int lane, uint32_t lt) {
+                                          int64_t& rc, int nrows, int32_t* __restrict__ col, int lane, uint32_t lt,
+                                          uint32_t rows = 0xffffffffu) {
   const uint32_t lbit = 1u << lane;
   for (int rr = 0; rr < nrows; ++rr) {
+    if (!((rows >> rr) & 1u)) continue;
     int32_t* dst = col + __shfl_sync(0xffffffffu, rc, rr);
     int32_t at = 0;
 #pragma unroll
@@ -697,7 +699,8 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
                                                               const int64_t* __restrict__ moff,
                                                               const int64_t* __restrict__ jboff,
                                                               const int32_t* __restrict__ ibkt,
-                                                              int32_t* __restrict__ counter) {
+                                                              int32_t* __restrict__ counter, int64_t lo,
+                                                              int64_t hi, int64_t base) {
   __shared__ uint32_t wbuf_s[kEmitThreads / 32][kEmitChunk * 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
@@ -720,7 +723,16 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
     const int nwb = (s + 31) >> 5;
     const uint32_t* rmb = a.rmask + moff[b];
     const int r = (J << 5) + lane;
-    int64_t rc = r < s ? a.runoff[bmem[o + r]] : 0;  // lane r: row r's cursor
+    // lane r: row r's cursor; rows of vertices outside [lo, hi) are skipped
+    bool in = false;
+    int64_t rc = 0;
+    if (r < s) {
+      const int32_t f = bmem[o + r];
+      const int64_t vr = a.Lu > 1 ? (int64_t)__umul64hi((uint64_t)f, invL) : a.Lu == 1 ? f : a.ent_v[f];
+      in = vr >= lo && vr < hi;
+      rc = a.runoff[f] - base;
+    }
+    const uint32_t rows_in = __ballot_sync(0xffffffffu, in);
     const int nrows = min(32, s - (J << 5));
     const int nwr = a.lower ? J + 1 : nwb;  // partner blocks of these rows
     const int blk0 = a.lower ? J * (J + 1) / 2 : J * nwb;
@@ -743,7 +755,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
       switch (nI) {
 #define PICASSO_EMIT_CASE(N) \
   case N:                    \
-    emit_rows<N>(wbuf, pv, rc, nrows, a.col, lane, lt); \
+    emit_rows<N>(wbuf, pv, rc, nrows, a.col, lane, lt, rows_in); \
     break;
         PICASSO_EMIT_CASE(1) PICASSO_EMIT_CASE(2) PICASSO_EMIT_CASE(3) PICASSO_EMIT_CASE(4)
         PICASSO_EMIT_CASE(5) PICASSO_EMIT_CASE(6) PICASSO_EMIT_CASE(7) PICASSO_EMIT_CASE(8)
@@ -760,7 +772,8 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
 }
 
 cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
-                               const int64_t* jboff, const int32_t* ibkt, int32_t* counter, cudaStream_t s) {
+                               const int64_t* jboff, const int32_t* ibkt, int32_t* counter, int64_t lo, int64_t hi,
+                               int64_t base, cudaStream_t s) {
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
@@ -771,7 +784,7 @@ cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   k_bucket_emit<<<(unsigned)(sms * max(per_sm, 1)), kEmitThreads, 0, s>>>(a, boff, bmem, moff, jboff, ibkt,
-                                                                         counter);
+                                                                         counter, lo, hi, base);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -19,6 +19,7 @@ ALGOS = {"auto": 0, "allpairs": 1, "bucket": 2}
 COLOR_ALGOS = {"auto": 0, "sweep": 1}
 CSR_FORMS = {"earlier": 0, "full": 1}
 SMALL_ENGINE = {"auto": 0, "off": 1}
+BUDGET_MODES = {"fail": 0, "chunk": 1}
 
 
 class PicassoError(RuntimeError):
@@ -40,7 +41,7 @@ class Config(ctypes.Structure):
         ("color_algo", ctypes.c_int32),
         ("csr_form", ctypes.c_int32),
         ("small_engine", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("budget_mode", ctypes.c_int32),
     ]
 
 
@@ -84,6 +85,8 @@ class Stats(ctypes.Structure):
         ("small_rounds", ctypes.c_int32),
         ("small_stops", ctypes.c_int32),
         ("t_small_ms", ctypes.c_double),
+        ("round_chunks", ctypes.c_int32),
+        ("pad_", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -212,7 +215,8 @@ class Picasso:
 
     def __init__(self, xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
                  algo: str = "auto", max_rounds: int = 100000, byte_budget: int = 0, stream=None,
-                 color: str = "auto", set_offsets=None, seeds=None, csr: str = "earlier", small: str = "auto"):
+                 color: str = "auto", set_offsets=None, seeds=None, csr: str = "earlier", small: str = "auto",
+                 budget_mode: str = "fail"):
         """One set, or with ``set_offsets`` (host, nsets + 1 ints) a batch of
         independent sets stored back to back in ``xz`` (seeds default to
         seed + k)."""
@@ -233,6 +237,7 @@ class Picasso:
         cfg.color_algo = COLOR_ALGOS[color]
         cfg.csr_form = CSR_FORMS[csr]
         cfg.small_engine = SMALL_ENGINE[small]
+        cfg.budget_mode = BUDGET_MODES[budget_mode]
         self.cfg = cfg
         h = ctypes.c_void_p()
         if set_offsets is None:

@@ -1,0 +1,84 @@
+"""Rounds over the byte budget colored in chunks of coloring order
+(budget_mode="chunk") against the CPU oracle.
+
+Integer work, bit-exact: a chunked run colors exactly as the oracle's
+unchunked run, and no chunk's CSR passes the budget."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2401_06713_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_2401_06713_b300 import build, picasso
+
+    build.build()
+    assert torch.cuda.is_available()
+    return picasso
+
+
+def _xz(pc, chars):
+    return pc.pack(torch.from_numpy(np.ascontiguousarray(chars)).cuda())
+
+
+def _round1_bytes(ostats):
+    # EARLIER CSR of round 1: 8 (n + 1) + 4 nnz, nnz half the oracle's two-sided rows
+    n, nnz = int(ostats[0, 0]), int(ostats[0, 4]) // 2
+    return 8 * (n + 1) + 4 * nnz
+
+
+@pytest.mark.parametrize("n,q,pw,num,den,alpha,seed,parts", [
+    (5000, 40, 0.3, 1, 8, 2.0, 6, 3),      # about three chunks in round 1
+    (12000, 64, 0.25, 1, 16, 1.5, 2, 7),   # the n=1M law at a smaller size, many chunks
+    (3000, 24, 0.5, 1, 4, 3.0, 9, 2),      # long lists
+])
+def test_chunked_run_matches_oracle(pc, orc, n, q, pw, num, den, alpha, seed, parts):
+    chars = synth.pauli_weighted(n, q, pw, seed=seed)
+    ref, rounds, ostats = orc.run(chars, seed, num, den, alpha)
+    budget = _round1_bytes(ostats) // parts
+    with pc.Picasso(_xz(pc, chars), q, seed=seed, palette=(num, den), alpha=alpha, byte_budget=budget,
+                    budget_mode="chunk") as p:
+        got, r = p.run()
+        st = p.stats()
+        used, peak, left = p.set_stats()
+    assert r == rounds and np.array_equal(got.cpu().numpy(), ref)
+    assert st["colors_used"] == int(ostats[:, 1].sum())
+    assert st["round_chunks"] >= parts
+    assert 0 < peak[0] <= budget and left == [0]
+
+
+def test_fail_mode_and_single_row_limit(pc, orc):
+    chars = synth.pauli_weighted(4000, 40, 0.3, seed=3)
+    _, _, ostats = orc.run(chars, 3, 1, 8, 2.0)
+    budget = _round1_bytes(ostats) // 3
+    xz = _xz(pc, chars)
+    # FAIL (the default): the first round over budget stops the run
+    with pc.Picasso(xz, 40, seed=3, byte_budget=budget) as p:
+        with pytest.raises(pc.PicassoError) as e:
+            p.run()
+        assert e.value.status == pc.ERR_BUDGET
+    # CHUNK with a budget below one vertex's rows: nothing to cut
+    with pc.Picasso(xz, 40, seed=3, byte_budget=64, budget_mode="chunk") as p:
+        with pytest.raises(pc.PicassoError) as e:
+            p.run()
+        assert e.value.status == pc.ERR_BUDGET
+
+
+def test_chunked_round_steps_equal_unchunked(pc):
+    # one round through picasso_round: same colors and uncolored set as the
+    # unchunked round
+    chars = synth.pauli_weighted(20000, 64, 0.25, seed=4)
+    xz = _xz(pc, chars)
+    out = {}
+    for mode, budget in (("fail", 0), ("chunk", 2_000_000)):
+        with pc.Picasso(xz, 64, seed=4, palette=(1, 16), alpha=1.5, byte_budget=budget, budget_mode=mode) as p:
+            left = p.round()
+            st = p.stats()
+            out[mode] = (left, p.colors().cpu().numpy(), p.vertices().cpu().numpy(), st["round_chunks"])
+    assert out["chunk"][0] == out["fail"][0]
+    assert np.array_equal(out["chunk"][1], out["fail"][1]) and np.array_equal(out["chunk"][2], out["fail"][2])
+    assert out["chunk"][3] > 1 and out["fail"][3] == 0
