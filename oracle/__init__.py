@@ -94,6 +94,16 @@ def lib():
         L.orc_run.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
                               ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _i64p, _i64p]
         L.orc_run.restype = ctypes.c_int32
+        L.orc_run_colorer.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
+                                      ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, _i64p, _i64p]
+        L.orc_run_colorer.restype = ctypes.c_int32
+        L.orc_color_dynamic.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, _i64p, _i64p,
+                                        ctypes.c_int32, _i64p, _i32p, _i64p]
+        L.orc_color_dynamic.restype = ctypes.c_int64
+        L.orc_color_dynamic_par.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, _i64p, _i64p,
+                                            ctypes.c_int32, _i64p, _i32p, _i64p, _i64p]
+        L.orc_color_dynamic_par.restype = ctypes.c_int64
         L.orc_feature_counts.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
                                          _i64p]
         _lib = L
@@ -230,16 +240,41 @@ def color_greedy(seed: int, rnd: int, gids, lists, off, col, P: int, base: int) 
     return out[:n]
 
 
+def color_dynamic(seed: int, rnd: int, gids, lists, off, col, parallel: bool = False):
+    """Alg. 2 on the two-sided rows (off, col) of G_c: sequential (parallel
+    False) or its parallel rule.  Returns (colors int64 [n] or -1, steps)."""
+    gids = np.ascontiguousarray(np.asarray(gids, dtype=np.int64))
+    lists = np.ascontiguousarray(lists, dtype=np.int64)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = len(gids)
+    L = lists.shape[1] if lists.ndim == 2 else 0
+    out = np.zeros(max(n, 1), dtype=np.int64)
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.int32)
+    steps = ctypes.c_int64(0)
+    if parallel:
+        lib().orc_color_dynamic_par(seed, rnd, n, _p(gids, _i64p), _p(lists, _i64p), L, _p(off, _i64p),
+                                    _p(col, _i32p), _p(out, _i64p), ctypes.byref(steps))
+    else:
+        lib().orc_color_dynamic(seed, rnd, n, _p(gids, _i64p), _p(lists, _i64p), L, _p(off, _i64p),
+                                _p(col, _i32p), _p(out, _i64p))
+    return out[:n], int(steps.value)
+
+
 def run(chars: np.ndarray, seed: int, num: int, den: int, alpha: float, max_rounds: int = 4096,
-        threads: int | None = None):
+        threads: int | None = None, colorer: str = "static"):
     """Alg. 1 end to end.  Returns (color int64 [N], rounds, stats [rounds][6])
-    with stats columns (n, P, L, base, nnz, colored)."""
+    with stats columns (n, P, L, base, nnz, colored).  colorer: "static"
+    (Random order, first fit), "dynamic" (Alg. 2) or "dynamic_par" (Alg. 2's
+    parallel rule)."""
     chars = np.ascontiguousarray(chars, dtype=np.uint8)
     N, q = chars.shape
     color = np.zeros(max(N, 1), dtype=np.int64)
     stats = np.zeros((max_rounds, 6), dtype=np.int64)
-    r = lib().orc_run(_p(chars, _u8p), N, q, seed, num, den, alpha, max_rounds, threads or default_threads(),
-                      _p(color, _i64p), _p(stats, _i64p))
+    which = {"static": 0, "dynamic": 1, "dynamic_par": 2}[colorer]
+    r = lib().orc_run_colorer(_p(chars, _u8p), N, q, seed, num, den, alpha, max_rounds,
+                              threads or default_threads(), which, _p(color, _i64p), _p(stats, _i64p))
     if r < 0:
         raise RuntimeError("oracle run hit max_rounds")
     return color[:N], int(r), stats[:r].copy()

@@ -402,6 +402,192 @@ int64_t orc_color_greedy(uint64_t seed, int32_t round, int64_t n,
   return colored;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Alg. 2: dynamic greedy list coloring of G_c (Sec. III-B "dynamic vertex   */
+/* order scheme").  Vertices sit in buckets by the size of their remaining   */
+/* list; the lowest bucket is served first; the chosen vertex takes a color  */
+/* drawn uniformly from its remaining list, and that color leaves the lists  */
+/* of its uncolored neighbours (a list that becomes empty leaves the vertex  */
+/* uncolored).  Readings: "a vertex chosen uniformly at random from the      */
+/* lowest bucket" is the bucket's vertex of smallest (priority, gid), the    */
+/* priority being the round's Philox priority (for iid priorities, a uniform */
+/* pick); "a color chosen uniformly at random" is the remaining list's entry */
+/* at floor(x * size / 2^32), x = word 0 of the Philox stream (seed, round,  */
+/* gid, tag 4), one draw per vertex.                                         */
+/* ------------------------------------------------------------------------ */
+static int64_t orc_dyn_pick(uint64_t seed, int32_t round, int64_t gid, const int64_t* rem, int32_t L,
+                            const int8_t* alive) {
+  int32_t size = 0;
+  for (int32_t k = 0; k < L; ++k) size += alive[k];
+  uint32_t x = orc_draw_u32(seed, round, gid, 4u, 0u);
+  int32_t idx = (int32_t)(((uint64_t)x * (uint64_t)size) >> 32);
+  for (int32_t k = 0; k < L; ++k) {
+    if (!alive[k]) continue;
+    if (idx == 0) return rem[k];
+    --idx;
+  }
+  return -1;
+}
+
+/* remove color c from u's remaining list; returns 1 if it was there */
+static int orc_dyn_remove(const int64_t* list_u, int8_t* alive_u, int32_t L, int64_t c) {
+  for (int32_t k = 0; k < L; ++k)
+    if (alive_u[k] && list_u[k] == c) {
+      alive_u[k] = 0;
+      return 1;
+    }
+  return 0;
+}
+
+typedef struct {
+  int32_t size;
+  uint64_t key; /* priority << 32 | gid */
+  int64_t v;
+} orc_dyn_entry;
+
+static int orc_dyn_less(const orc_dyn_entry* a, const orc_dyn_entry* b) {
+  if (a->size != b->size) return a->size < b->size;
+  return a->key < b->key;
+}
+
+/* Sequential Alg. 2.  off/col: the two-sided per-color rows of G_c (any
+ * neighbour order; repeats harmless).  color_local[n]: color or -1.
+ * Returns the colored count.  The "lowest bucket, then smallest key" choice
+ * is served by a binary heap of (size, key) entries; an entry whose size is
+ * stale or whose vertex is done is skipped when popped.                    */
+int64_t orc_color_dynamic(uint64_t seed, int32_t round, int64_t n, const int64_t* gids, const int64_t* lists,
+                          int32_t L, const int64_t* off, const int32_t* col, int64_t* color_local) {
+  int8_t* alive = (int8_t*)malloc((size_t)(n * L + 1));
+  int32_t* size = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  int8_t* done = (int8_t*)malloc((size_t)(n + 1));
+  int64_t cap = n + 1 + 64;
+  orc_dyn_entry* heap = (orc_dyn_entry*)malloc(sizeof(orc_dyn_entry) * (size_t)cap);
+  int64_t hn = 0;
+#define ORC_PUSH(E)                                                                            \
+  do {                                                                                         \
+    if (hn == cap) {                                                                           \
+      cap *= 2;                                                                                \
+      heap = (orc_dyn_entry*)realloc(heap, sizeof(orc_dyn_entry) * (size_t)cap);               \
+    }                                                                                          \
+    int64_t i_ = hn++;                                                                         \
+    heap[i_] = (E);                                                                            \
+    while (i_ > 0 && orc_dyn_less(&heap[i_], &heap[(i_ - 1) / 2])) {                           \
+      orc_dyn_entry t_ = heap[i_];                                                             \
+      heap[i_] = heap[(i_ - 1) / 2];                                                           \
+      heap[(i_ - 1) / 2] = t_;                                                                 \
+      i_ = (i_ - 1) / 2;                                                                       \
+    }                                                                                          \
+  } while (0)
+  for (int64_t v = 0; v < n; ++v) {
+    for (int32_t k = 0; k < L; ++k) alive[v * L + k] = 1;
+    size[v] = L;
+    done[v] = 0;
+    color_local[v] = -1;
+    orc_dyn_entry e = {L, ((uint64_t)orc_priority(seed, round, gids[v]) << 32) | (uint32_t)gids[v], v};
+    ORC_PUSH(e);
+  }
+  int64_t colored = 0;
+  while (hn > 0) {
+    orc_dyn_entry top = heap[0];
+    heap[0] = heap[--hn];
+    for (int64_t i = 0;;) {
+      int64_t l = 2 * i + 1, r = l + 1, m = i;
+      if (l < hn && orc_dyn_less(&heap[l], &heap[m])) m = l;
+      if (r < hn && orc_dyn_less(&heap[r], &heap[m])) m = r;
+      if (m == i) break;
+      orc_dyn_entry t = heap[i];
+      heap[i] = heap[m];
+      heap[m] = t;
+      i = m;
+    }
+    const int64_t v = top.v;
+    if (done[v] || top.size != size[v]) continue;
+    done[v] = 1;
+    const int64_t c = orc_dyn_pick(seed, round, gids[v], lists + v * L, L, alive + v * L);
+    color_local[v] = c;
+    ++colored;
+    for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+      const int64_t u = col[e];
+      if (done[u]) continue;
+      if (!orc_dyn_remove(lists + u * L, alive + u * L, L, c)) continue;
+      if (--size[u] == 0) {
+        done[u] = 1; /* no color left: stays uncolored */
+        continue;
+      }
+      orc_dyn_entry eu = {size[u], ((uint64_t)orc_priority(seed, round, gids[u]) << 32) | (uint32_t)gids[u], u};
+      ORC_PUSH(eu);
+    }
+  }
+#undef ORC_PUSH
+  free(alive);
+  free(size);
+  free(done);
+  free(heap);
+  return colored;
+}
+
+/* The parallel form of Alg. 2's rule (what the GPU computes): in each step
+ * every uncolored vertex with a nonempty list whose (size, priority, gid) is
+ * smaller than that of each such neighbour takes its color (the same draw as
+ * above), then all those colors leave the neighbours' lists; a vertex whose
+ * list empties is left uncolored at the start of the next step.  Returns the
+ * colored count; *steps gets the number of steps.                          */
+int64_t orc_color_dynamic_par(uint64_t seed, int32_t round, int64_t n, const int64_t* gids, const int64_t* lists,
+                              int32_t L, const int64_t* off, const int32_t* col, int64_t* color_local,
+                              int64_t* steps) {
+  int8_t* alive = (int8_t*)malloc((size_t)(n * L + 1));
+  int32_t* size = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  int8_t* state = (int8_t*)malloc((size_t)(n + 1)); /* 0 active, 1 colored, 2 left uncolored */
+  uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n + 1));
+  int8_t* pick = (int8_t*)malloc((size_t)(n + 1));
+  for (int64_t v = 0; v < n; ++v) {
+    for (int32_t k = 0; k < L; ++k) alive[v * L + k] = 1;
+    size[v] = L;
+    state[v] = 0;
+    color_local[v] = -1;
+    key[v] = ((uint64_t)orc_priority(seed, round, gids[v]) << 32) | (uint32_t)gids[v];
+  }
+  int64_t colored = 0, t = 0, active = n;
+  while (active > 0) {
+    ++t;
+    for (int64_t v = 0; v < n; ++v)
+      if (state[v] == 0 && size[v] == 0) state[v] = 2;
+    for (int64_t v = 0; v < n; ++v) {
+      pick[v] = 0;
+      if (state[v] != 0) continue;
+      int ok = 1;
+      for (int64_t e = off[v]; e < off[v + 1] && ok; ++e) {
+        const int64_t u = col[e];
+        if (state[u] != 0) continue;
+        if (size[u] < size[v] || (size[u] == size[v] && key[u] < key[v])) ok = 0;
+      }
+      pick[v] = (int8_t)ok;
+    }
+    for (int64_t v = 0; v < n; ++v) {
+      if (!pick[v]) continue;
+      color_local[v] = orc_dyn_pick(seed, round, gids[v], lists + v * L, L, alive + v * L);
+      state[v] = 1;
+      ++colored;
+    }
+    for (int64_t v = 0; v < n; ++v) {
+      if (!pick[v]) continue;
+      for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+        const int64_t u = col[e];
+        if (state[u] == 0 && orc_dyn_remove(lists + u * L, alive + u * L, L, color_local[v])) --size[u];
+      }
+    }
+    active = 0;
+    for (int64_t v = 0; v < n; ++v) active += state[v] == 0;
+  }
+  if (steps) *steps = t;
+  free(alive);
+  free(size);
+  free(state);
+  free(key);
+  free(pick);
+  return colored;
+}
+
 /* Round parameters (Table I; Sec. VI "P a percentage of |V|, L = alpha
  * log|V|, the same percentage and alpha in every iteration").              */
 void orc_round_params(int64_t n, int64_t num, int64_t den, double alpha,
@@ -422,9 +608,21 @@ void orc_round_params(int64_t n, int64_t num, int64_t den, double alpha,
 /* (n, P, L, base, nnz, colored) go to stats[6 * r] for r < max_rounds.      */
 /* Returns the number of rounds run, or -1 if max_rounds was hit first.      */
 /* ------------------------------------------------------------------------ */
+int32_t orc_run_colorer(const uint8_t* chars, int64_t N, int32_t q, uint64_t seed, int64_t num, int64_t den,
+                        double alpha, int32_t max_rounds, int32_t threads, int32_t colorer, int64_t* color,
+                        int64_t* stats);
+
 int32_t orc_run(const uint8_t* chars, int64_t N, int32_t q, uint64_t seed,
                 int64_t num, int64_t den, double alpha, int32_t max_rounds,
                 int32_t threads, int64_t* color, int64_t* stats) {
+  return orc_run_colorer(chars, N, q, seed, num, den, alpha, max_rounds, threads, 0, color, stats);
+}
+
+/* colorer: 0 static Random order with first fit (the default), 1 Alg. 2
+ * sequential, 2 Alg. 2's parallel rule.                                    */
+int32_t orc_run_colorer(const uint8_t* chars, int64_t N, int32_t q, uint64_t seed, int64_t num, int64_t den,
+                        double alpha, int32_t max_rounds, int32_t threads, int32_t colorer, int64_t* color,
+                        int64_t* stats) {
   int32_t w3 = orc_words3(q);
   uint32_t* enc_all = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(N * w3 + 1));
   orc_encode3(chars, N, q, enc_all);
@@ -456,7 +654,9 @@ int32_t orc_run(const uint8_t* chars, int64_t N, int32_t q, uint64_t seed,
     orc_conflict_fill(n, enc, w3, lists, L, lens, off, col, threads);
     int64_t* cl = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
     int64_t colored =
-        orc_color_greedy(seed, round, n, gids, lists, L, off, col, P, base, cl);
+        colorer == 1   ? orc_color_dynamic(seed, round, n, gids, lists, L, off, col, cl)
+        : colorer == 2 ? orc_color_dynamic_par(seed, round, n, gids, lists, L, off, col, cl, NULL)
+                       : orc_color_greedy(seed, round, n, gids, lists, L, off, col, P, base, cl);
     if (stats) {
       int64_t* s = stats + 6 * (round - 1);
       s[0] = n;

@@ -331,3 +331,94 @@ def test_run_valid_workload_small(orc):
 def test_run_valid_weighted(orc):
     chars = synth.pauli_weighted(700, 48, 0.25, seed=2)
     _check_valid_run(orc, chars, 5, 1, 16, 1.5)
+
+
+# ------------------------------------------------------------ Alg. 2 (dynamic)
+def _dyn_case(orc, n, q, P, L, seed, chars=None):
+    if chars is None:
+        chars = synth.pauli_uniform(n, q, seed=seed)
+    gids = np.arange(n)
+    lists = orc.draw_lists(seed, 1, gids, P, L)
+    off, col = orc.conflict_csr(orc.encode3(chars), lists)
+    return chars, gids, lists, off, col
+
+
+@pytest.mark.parametrize("parallel", [False, True])
+def test_dynamic_single_color_is_greedy_mis(orc, parallel):
+    # P = L = 1: every list has one color, so the lowest bucket is always the
+    # whole active set and both forms of Alg. 2 reduce to the maximal
+    # independent set of G', greedy in priority order (the parallel rule is
+    # the local-minimum iteration, whose fixed point is that same set)
+    n = 90
+    chars, gids, lists, off, col = _dyn_case(orc, n, 6, 1, 1, 7)
+    color, _ = orc.color_dynamic(7, 1, gids, lists, off, col, parallel=parallel)
+    chosen = set(np.nonzero(color >= 0)[0].tolist())
+    prio = orc.priorities(7, 1, gids).astype(np.uint64)
+    mis = []
+    for v in sorted(range(n), key=lambda v: (int(prio[v]), v)):
+        if all(not orc.commute_chars(chars[v], chars[u]) for u in mis):
+            mis.append(v)
+    assert chosen == set(mis)
+
+
+@pytest.mark.parametrize("parallel", [False, True])
+def test_dynamic_without_conflicts_takes_the_drawn_color(orc, parallel):
+    # no pair commutes (each string anticommutes with every other: the
+    # anticommuting set {X I.., Z I.., Y I..} extended by singles), so G_c has
+    # no edge and every vertex takes the entry floor(x L / 2^32) of its list,
+    # x = word 0 of its Philox stream with tag 4
+    chars = np.array([[1, 0], [3, 0], [2, 0]], dtype=np.uint8)
+    n = 3
+    gids = np.arange(n) + 40
+    P, L = 50, 7
+    lists = orc.draw_lists(11, 2, gids, P, L)
+    off, col = orc.conflict_csr(orc.encode3(chars), lists)
+    assert off[-1] == 0
+    color, _ = orc.color_dynamic(11, 2, gids, lists, off, col, parallel=parallel)
+    for v in range(n):
+        x = orc.draw_u32(11, 2, int(gids[v]), 4, 0)
+        assert color[v] == lists[v][(x * L) >> 32]
+
+
+@pytest.mark.parametrize("parallel", [False, True])
+def test_dynamic_complete_graph_full_palette(orc, parallel):
+    # identical strings all commute: G' is complete.  With L = P every list is
+    # the whole palette, each coloring removes one color from every other
+    # list, so exactly min(n, P) vertices are colored, all with distinct colors
+    for n, P in ((12, 5), (6, 9)):
+        chars = np.zeros((n, 4), dtype=np.uint8)
+        gids = np.arange(n)
+        lists = orc.draw_lists(2, 1, gids, P, P)
+        off, col = orc.conflict_csr(orc.encode3(chars), lists)
+        color, _ = orc.color_dynamic(2, 1, gids, lists, off, col, parallel=parallel)
+        got = color[color >= 0]
+        assert len(got) == min(n, P) and len(set(got.tolist())) == len(got)
+
+
+@pytest.mark.parametrize("parallel", [False, True])
+def test_dynamic_valid_and_blocked(orc, parallel):
+    # a proper list coloring of G_c, and a vertex is left uncolored only when
+    # every color of its list went to a conflict neighbour
+    n, P, L = 400, 30, 5
+    chars, gids, lists, off, col = _dyn_case(orc, n, 8, P, L, 5)
+    color, steps = orc.color_dynamic(5, 1, gids, lists, off, col, parallel=parallel)
+    assert (steps > 0) == parallel
+    for v in range(n):
+        nb = col[off[v]:off[v + 1]]
+        taken = set(int(color[u]) for u in nb if color[u] >= 0)
+        if color[v] >= 0:
+            assert color[v] in lists[v] and color[v] not in taken
+        else:
+            assert set(lists[v].tolist()) <= taken
+
+
+def test_dynamic_colors_more_than_static(orc):
+    # Sec. III-B: the dynamic order (most constrained first) leaves fewer
+    # vertices uncolored than the static Random order on the same round
+    n, P, L = 3000, 375, 16
+    chars, gids, lists, off, col = _dyn_case(orc, n, 24, P, L, 1)
+    static = orc.color_greedy(1, 1, gids, lists, off, col, P, 0)
+    dyn, _ = orc.color_dynamic(1, 1, gids, lists, off, col)
+    par, _ = orc.color_dynamic(1, 1, gids, lists, off, col, parallel=True)
+    s, d, p = int((static >= 0).sum()), int((dyn >= 0).sum()), int((par >= 0).sum())
+    assert d > s and p > s
