@@ -271,6 +271,7 @@ def run_gpu(args):
     batch = None if args.no_batch else bench_batch(rank)
     learned_form = None if args.no_learned else bench_learned(rank)
     chunked = None if args.no_chunked else bench_chunked(rank, codes, colors_np)
+    dynamic = None if args.no_dynamic else bench_dynamic(rank, codes, st)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -292,7 +293,7 @@ def run_gpu(args):
         "pair_tests_per_s": pair_rate, "colors": int(len(np.unique(colors_np))),
         "colors_sum_P": st["colors_used"], "rounds": rounds,
         "peak_bytes": st["peak_bytes"], "breakdown_ms_per_step": per_step,
-        "roofline": roofline, "roofline_pairs": roofline_pairs, "chunked": chunked, "cpu_baseline": cpu, "batch": batch, "learned": learned_form,
+        "roofline": roofline, "roofline_pairs": roofline_pairs, "chunked": chunked, "dynamic": dynamic, "cpu_baseline": cpu, "batch": batch, "learned": learned_form,
         "e2e": {"value": world * n / (ms_e2e / args.steps / 1e3), "unit": "strings/s",
                 "h2d_bytes_per_step": n * Q, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": launches, "clocks": clocks, "wall_s": t_wall,
@@ -357,6 +358,31 @@ def bench_batch(rank, nsets=256):
                         f"P=n/8, alpha=2", "strings": offs[-1], "batched_ms": tb, "sequential_ms": ts,
             "batched_strings_per_s": offs[-1] / (tb / 1e3), "sequential_strings_per_s": offs[-1] / (ts / 1e3),
             "speedup": ts / tb, "identical_colors": same}
+
+
+def bench_dynamic(rank, codes, st_static):
+    """The benchmark workload colored with Alg. 2's dynamic order (parallel
+    rule) instead of the static Random order: time, colors and rounds."""
+    import torch
+
+    from paper_2401_06713_b300 import picasso
+
+    def run():
+        xz = picasso.pack(codes)
+        with picasso.Picasso(xz, Q, seed=rank, palette=(NUM, DEN), alpha=ALPHA, color="dynamic") as p:
+            _, r = p.run()
+            return r, p.stats()
+
+    run()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    r, st = run()
+    ev[1].record()
+    torch.cuda.synchronize()
+    return {"workload": "the benchmark workload, color_algo DYNAMIC (Alg. 2, parallel rule)",
+            "ms": ev[0].elapsed_time(ev[1]), "rounds": r, "colors_sum_P": st["colors_used"],
+            "static_colors_sum_P": st_static["colors_used"], "peak_bytes": st["peak_bytes"]}
 
 
 def bench_chunked(rank, codes, ref_colors, budget=2_000_000_000):
@@ -499,6 +525,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-chunked", action="store_true")
+    ap.add_argument("--no-dynamic", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -122,10 +122,19 @@ typedef enum {
   PICASSO_SMALL_OFF = 1
 } picasso_small_engine;
 
-/* Coloring strategy (same colors either way). */
+/* Coloring strategy (AUTO and SWEEP give the same colors). */
 typedef enum {
   PICASSO_COLOR_AUTO = 0,  /* ordered persistent pass; sweeps if it gives up */
-  PICASSO_COLOR_SWEEP = 1  /* dependency sweeps only                         */
+  PICASSO_COLOR_SWEEP = 1, /* dependency sweeps only                         */
+  PICASSO_COLOR_DYNAMIC = 2 /* Alg. 2's dynamic order (most constrained
+                               first), parallel rule: each step colors every
+                               uncolored vertex whose (remaining list size,
+                               priority) is below all its uncolored
+                               neighbours', with a color drawn from its
+                               remaining list, and strikes those colors from
+                               the neighbours' lists.  Not the static order's
+                               colors; lists of at most 64; the build keeps
+                               both directions of every pair (FULL).      */
 } picasso_color_algo;
 
 /* Conflict CSR of the current round, owned by the context and valid until

@@ -485,7 +485,7 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
   // small rounds: testing all n (n-1) pairs costs less than building buckets
   // (chunk mode keeps small rounds on the bucket join, which can emit by chunk)
   const bool chunking = chunk_ok && c->cfg.byte_budget > 0 && c->cfg.budget_mode == PICASSO_BUDGET_CHUNK &&
-                        c->nsets == 1;
+                        c->nsets == 1 && c->cfg.color_algo != PICASSO_COLOR_DYNAMIC;
   if (algo == PICASSO_CONFLICT_AUTO && n <= kSmallRoundAllPairs && !chunking) algo = PICASSO_CONFLICT_ALLPAIRS;
   int64_t smax = 0, bucket_pairs = 0;
   if (algo != PICASSO_CONFLICT_ALLPAIRS) {
@@ -529,7 +529,9 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
   a.ent_v = c->ent_v;
   a.cnt = cnt;
   a.err = c->d_err;
-  a.lower = c->cfg.csr_form == PICASSO_CSR_EARLIER ? 1 : 0;
+  // Alg. 2's dynamic order strikes colors from later neighbours' lists too:
+  // it needs both directions of every pair
+  a.lower = c->cfg.csr_form == PICASSO_CSR_EARLIER && c->cfg.color_algo != PICASSO_COLOR_DYNAMIC ? 1 : 0;
 
   if (algo == PICASSO_CONFLICT_BUCKET) {
     TRYC(launch_scan_u32(bcount, P, boff, tmp, s));
@@ -767,7 +769,112 @@ int canonical_csr(Ctx* c) {
   return PICASSO_OK;
 }
 
+// Alg. 2's dynamic order (parallel rule, kernels_dynamic.cu): steps until no
+// uncolored vertex with a nonempty list is left; one read-back per step.
+int color_dynamic(Ctx* c) {
+  const int64_t n = c->n;
+  cudaStream_t s = c->s;
+  if (c->Lmax > 64) return PICASSO_ERR_UNSUPPORTED;
+  ST(canonical_csr(c));
+  uint64_t* mask = nullptr;
+  int32_t *state = nullptr, *colorl = nullptr, *ctl = nullptr, *wa = nullptr, *wb = nullptr, *sel = nullptr,
+          *fin = nullptr, *blk = nullptr, *stamp = nullptr, *bstep = nullptr, *parts = nullptr;
+  void* tmp = nullptr;
+  int st = PICASSO_OK;
+  auto cleanup = [&]() {
+    release(c, &mask);
+    release(c, &state);
+    release(c, &colorl);
+    release(c, &ctl);
+    release(c, &wa);
+    release(c, &wb);
+    release(c, &sel);
+    release(c, &fin);
+    release(c, &blk);
+    release(c, &stamp);
+    release(c, &bstep);
+    release(c, &parts);
+    release(c, (uint8_t**)&tmp);
+  };
+#define TRY(expr)           \
+  do {                      \
+    st = (expr);            \
+    if (st != PICASSO_OK) { \
+      cleanup();            \
+      return st;            \
+    }                       \
+  } while (0)
+#define TRYC(expr)                                \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) {                      \
+      st = map_err(_e);                           \
+      if (st == PICASSO_ERR_CUDA) c->sticky = st; \
+      cleanup();                                  \
+      return st;                                  \
+    }                                             \
+  } while (0)
+  free_color(c);
+  TRY(alloc(c, &mask, n));
+  TRY(alloc(c, &state, n));
+  TRY(alloc(c, &colorl, n));
+  TRY(alloc(c, &ctl, 8));
+  TRY(alloc(c, &wa, n));
+  TRY(alloc(c, &wb, n));
+  TRY(alloc(c, &sel, n));
+  TRY(alloc(c, &fin, n));
+  TRY(alloc(c, &blk, n));
+  TRY(alloc(c, &stamp, n));
+  TRY(alloc(c, &bstep, n));
+  TRY(alloc(c, &parts, n));
+  TRY(alloc(c, &c->state, n));
+  TRY(alloc(c, &c->flag, n));
+  TRY(alloc(c, &c->pos, n + 1));
+  TRY(alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(n)));
+  DynArgs d{};
+  d.n = n;
+  d.round = c->round;
+  d.nsets = c->nsets;
+  d.soff = c->d_soff;
+  d.sets = c->d_sets;
+  d.gid = c->gid_r;
+  d.loff = c->loff;
+  d.lists = c->lists;
+  d.runoff = c->runoff;
+  d.col = c->col;
+  d.mask = mask;
+  d.state = state;
+  d.color = colorl;
+  d.wa = wa;
+  d.wb = wb;
+  d.sel = sel;
+  d.fin = fin;
+  d.blk = blk;
+  d.stamp = stamp;
+  d.bstep = bstep;
+  d.parts = parts;
+  d.ctl = ctl;
+  TRYC(launch_dyn_init(d, s));
+  TRYC(launch_dyn_all(d, s));
+  TRYC(launch_dyn_finish(d, c->state, s));
+  TRYC(launch_carry_flags(c->state, n, c->gid_r, c->perm, c->d_soff, c->nsets, c->d_sets, c->color, c->flag, s));
+  TRYC(launch_scan_u32(c->flag, n, c->pos, tmp, s));
+  TRYC(cudaMemcpyAsync(c->h_buf, c->pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaMemcpyAsync(c->h_buf + 1, ctl + 6, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaStreamSynchronize(s));
+  const int32_t steps = *(const int32_t*)(c->h_buf + 1);
+  c->sweeps = steps;
+  c->n_remaining = c->h_buf[0];
+  c->n_colored = n - c->n_remaining;
+  c->colored_done = true;
+  cleanup();
+#undef TRY
+#undef TRYC
+  return PICASSO_OK;
+}
+
 int color_round(Ctx* c) {
+  if (c->cfg.color_algo == PICASSO_COLOR_DYNAMIC) return color_dynamic(c);
   const int64_t n = c->n;
   cudaStream_t s = c->s;
   int32_t *wa = nullptr, *wb = nullptr, *wact = nullptr, *nw = nullptr;
@@ -1328,7 +1435,7 @@ int validate_cfg(const picasso_config* cfg) {
   if (cfg->palette_num < 1 || cfg->palette_den < 1 || cfg->palette_num > (int64_t(1) << 32) ||
       cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
       cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2 ||
-      cfg->color_algo < 0 || cfg->color_algo > 1 || cfg->csr_form < 0 || cfg->csr_form > 1 ||
+      cfg->color_algo < 0 || cfg->color_algo > 2 || cfg->csr_form < 0 || cfg->csr_form > 1 ||
       cfg->small_engine < 0 || cfg->small_engine > 1 || cfg->budget_mode < 0 || cfg->budget_mode > 1)
     return PICASSO_ERR_INVALID_ARG;
   return PICASSO_OK;

@@ -19,6 +19,7 @@ namespace picasso {
 
 constexpr uint32_t kTagList = 1u;
 constexpr uint32_t kTagPrio = 2u;
+constexpr uint32_t kTagDynamic = 4u;  // Alg. 2's color draw
 constexpr int kMaxL = 512;           // longest list a round may draw
 constexpr int kBucketCap = 2048;     // largest color bucket of the bucket join
 constexpr int kBucketMaxP = 1 << 21; // bucket colors of one round (bucket join)
@@ -432,6 +433,39 @@ struct SmallArgs {
 constexpr int64_t kSmallOk = 0, kSmallTimeout = 1, kSmallOverflow = 2, kSmallMaxRounds = 3;
 // part_cap: words of a.part; the launch uses at most that many blocks.
 cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, cudaStream_t s);
+
+// Alg. 2's dynamic order, parallel rule (kernels_dynamic.cu).  Rows are the
+// two-sided canonical ones; lists of at most 64 colors.
+struct DynArgs {
+  int64_t n;
+  int32_t round;
+  int32_t nsets;
+  const int64_t* soff;
+  const SetRound* sets;
+  const int32_t* gid;     // [n] global id of each round-local id
+  const int64_t* loff;
+  const int32_t* lists;
+  const int64_t* runoff;  // [E + 1]
+  const int32_t* col;
+  uint64_t* mask;         // [n] remaining list entries; 0 once finished
+  int32_t* state;         // [n] 0 uncolored, 1 colored, 2 left uncolored
+  int32_t* color;         // [n] bucket color taken
+  int32_t* wa;            // [n] work lists: vertices to examine (by step parity)
+  int32_t* wb;            // [n]
+  int32_t* sel;           // [n] the step's local minima
+  int32_t* fin;           // [n] the step's lists struck empty
+  int32_t* blk;           // [n] a smaller uncolored neighbour (blocked vertices)
+  int32_t* stamp;         // [n] last step + 1 the vertex was put on a work list
+  int32_t* bstep;         // [n] last step + 1 the vertex was found blocked
+  int32_t* parts;         // [n] parts of the vertex's examination finished
+  int32_t* ctl;           // [8] list lengths, sel and fin lengths (by parity), steps
+};
+// masks of full lists, state 0, wa = all vertices, ctl = {n, 0, ...}
+cudaError_t launch_dyn_init(const DynArgs& d, cudaStream_t s);
+// every step of the round in one cooperative launch; ctl[6] = steps on exit
+cudaError_t launch_dyn_all(const DynArgs& d, cudaStream_t s);
+// the state words the carry reads (colored: bucket color, else failed)
+cudaError_t launch_dyn_finish(const DynArgs& d, uint64_t* words, cudaStream_t s);
 
 // Parameter predictor and instance features (kernels_mlp.cu).
 int mlp_param_count();

@@ -16,7 +16,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "picasso.h")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_BUDGET, ERR_TIMEOUT, ERR_INTERNAL, ERR_UNSUPPORTED, ERR_STATE = range(9)
 ALGOS = {"auto": 0, "allpairs": 1, "bucket": 2}
-COLOR_ALGOS = {"auto": 0, "sweep": 1}
+COLOR_ALGOS = {"auto": 0, "sweep": 1, "dynamic": 2}
 CSR_FORMS = {"earlier": 0, "full": 1}
 SMALL_ENGINE = {"auto": 0, "off": 1}
 BUDGET_MODES = {"fail": 0, "chunk": 1}

@@ -1,0 +1,83 @@
+"""Alg. 2's dynamic order on the GPU (color="dynamic", the parallel rule)
+against the CPU oracle's parallel rule, bit for bit, and its quality against
+the static order."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2401_06713_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_2401_06713_b300 import build, picasso
+
+    build.build()
+    assert torch.cuda.is_available()
+    return picasso
+
+
+def _xz(pc, chars):
+    return pc.pack(torch.from_numpy(np.ascontiguousarray(chars)).cuda())
+
+
+@pytest.mark.parametrize("n,q,P,L,seed", [(2500, 24, 312, 16, 3), (700, 10, 40, 40, 8), (5000, 40, 300, 7, 1)])
+def test_dynamic_round_matches_oracle(pc, orc, n, q, P, L, seed):
+    chars = synth.pauli_uniform(n, q, seed=seed)
+    gids = np.arange(n)
+    lists = orc.draw_lists(seed, 1, gids, P, L)
+    off, col = orc.conflict_csr(orc.encode3(chars), lists)
+    ref, steps = orc.color_dynamic(seed, 1, gids, lists, off, col, parallel=True)
+    with pc.Picasso(_xz(pc, chars), q, seed=seed, color="dynamic") as p:
+        p.assign_lists(P, L, 0)
+        p.build_conflicts()
+        k = p.color()
+        assert k == int((ref >= 0).sum())
+        p.carry()
+        got = p.colors().cpu().numpy()
+        assert p.stats()["jp_sweeps"] == steps
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("algo", ["auto", "allpairs"])
+def test_dynamic_run_matches_oracle(pc, orc, algo):
+    chars = synth.pauli_weighted(4000, 48, 0.3, seed=12)
+    ref, rounds, ostats = orc.run(chars, 4, 1, 8, 2.0, colorer="dynamic_par")
+    with pc.Picasso(_xz(pc, chars), 48, seed=4, palette=(1, 8), alpha=2.0, color="dynamic", algo=algo) as p:
+        got, r = p.run()
+        st = p.stats()
+    assert r == rounds and np.array_equal(got.cpu().numpy(), ref)
+    assert st["colors_used"] == int(ostats[:, 1].sum()) and st["small_rounds"] == 0
+
+
+def test_dynamic_batch_matches_oracle(pc, orc):
+    specs = [(900, 16, 0.3), (1600, 40, 0.25), (40, 24, 0.5)]
+    sets = [synth.pauli_weighted(n, q, p, seed=2, stream=i) for i, (n, q, p) in enumerate(specs)]
+    offs = [0]
+    for c in sets:
+        offs.append(offs[-1] + len(c))
+    pad = np.zeros((offs[-1], 40), dtype=np.uint8)
+    for k, c in enumerate(sets):
+        pad[offs[k]:offs[k + 1], :c.shape[1]] = c
+    seeds = [31, 32, 33]
+    with pc.Picasso(_xz(pc, pad), 40, set_offsets=offs, seeds=seeds, color="dynamic") as p:
+        got, _ = p.run()
+        got = got.cpu().numpy()
+    for k, c in enumerate(sets):
+        ref, _, _ = orc.run(c, seeds[k], 1, 8, 2.0, colorer="dynamic_par")
+        assert np.array_equal(got[offs[k]:offs[k + 1]], ref), k
+
+
+def test_dynamic_fewer_colors_than_static(pc):
+    # Sec. III-B: coloring the most constrained vertex first leaves fewer
+    # vertices per round, so the run needs fewer rounds' palettes
+    chars = synth.pauli_weighted(20000, 64, 0.25, seed=5)
+    xz = _xz(pc, chars)
+    used = {}
+    for color in ("auto", "dynamic"):
+        with pc.Picasso(xz, 64, seed=5, palette=(1, 16), alpha=1.5, color=color) as p:
+            p.run()
+            used[color] = p.stats()["colors_used"]
+    assert used["dynamic"] < used["auto"]
