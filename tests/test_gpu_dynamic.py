@@ -41,11 +41,15 @@ def test_dynamic_round_matches_oracle(pc, orc, n, q, P, L, seed):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("algo", ["auto", "allpairs"])
-def test_dynamic_run_matches_oracle(pc, orc, algo):
-    chars = synth.pauli_weighted(4000, 48, 0.3, seed=12)
-    ref, rounds, ostats = orc.run(chars, 4, 1, 8, 2.0, colorer="dynamic_par")
-    with pc.Picasso(_xz(pc, chars), 48, seed=4, palette=(1, 8), alpha=2.0, color="dynamic", algo=algo) as p:
+@pytest.mark.parametrize("n,q,pw,num,den,alpha,algo", [
+    (4000, 48, 0.3, 1, 8, 2.0, "auto"),
+    (4000, 48, 0.3, 1, 8, 2.0, "allpairs"),
+    (8000, 64, 0.25, 1, 16, 1.5, "auto"),   # the n=1M law at a smaller size: dense conflicts
+])
+def test_dynamic_run_matches_oracle(pc, orc, n, q, pw, num, den, alpha, algo):
+    chars = synth.pauli_weighted(n, q, pw, seed=12)
+    ref, rounds, ostats = orc.run(chars, 4, num, den, alpha, colorer="dynamic_par")
+    with pc.Picasso(_xz(pc, chars), q, seed=4, palette=(num, den), alpha=alpha, color="dynamic", algo=algo) as p:
         got, r = p.run()
         st = p.stats()
     assert r == rounds and np.array_equal(got.cpu().numpy(), ref)
