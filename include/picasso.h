@@ -21,10 +21,12 @@
  *     when picasso_init ran; h_* are host pointers.  The caller owns every
  *     buffer it passes in; the context owns (and frees in picasso_destroy)
  *     every buffer it hands out.
- *   - Strings are packed as symplectic words: for q <= 64 qubits each string
- *     is two uint64 words [x, z]; qubit i sets bit i of x for X and Y, bit i
- *     of z for Z and Y.  Two strings commute iff popcount((x_u & z_v) ^
- *     (z_u & x_v)) is even.
+ *   - Strings are packed as symplectic words: a string of q <= 1024 qubits
+ *     is 2W uint64 words [x_0 .. x_{W-1}, z_0 .. z_{W-1}], W = ceil(q / 64)
+ *     (for q <= 64 the two words [x, z]); qubit i sets bit i % 64 of x_{i/64}
+ *     for X and Y, of z_{i/64} for Z and Y.  Two strings commute iff the
+ *     popcount of the XOR over w of (x_u,w & z_v,w) ^ (z_u,w & x_v,w) is
+ *     even.  Every d_xz below is [n][2W] in this layout.
  *   - Character codes are 0=I 1=X 2=Y 3=Z.
  *   - Random numbers are Philox4x32-10 (Salmon et al., SC'11).  Draw i of the
  *     stream (seed, round, gid, tag) is word i%4 of the block with counter
@@ -211,19 +213,24 @@ typedef struct {
 int picasso_config_default(picasso_config* cfg);
 
 /* Pack n strings of q character codes (row-major uint8 [n][q]) into
- * symplectic words d_xz [n][2] (q <= 64).  Sec. III-A encodes characters in
- * bits; this is the product's two-word form of that idea.  Asynchronous.   */
+ * symplectic words d_xz [n][2W], W = ceil(q / 64) (1 <= q <= 1024; more is
+ * PICASSO_ERR_UNSUPPORTED).  Sec. III-A encodes characters in bits; this is
+ * the product's word form of that idea.  Asynchronous.                     */
 int picasso_pack(const uint8_t* d_codes, int64_t n, int32_t q, uint64_t* d_xz,
                  void* stream);
 
-/* Create a context over d_xz [n][2] (read-only, must outlive the context;
- * 1 <= n < 2^30, 1 <= q <= 64).  stream is a cudaStream_t (NULL = legacy
- * default stream).  Round 1 starts with V_1 = all n strings, all colors -1. */
+/* Create a context over d_xz [n][2W] (read-only, must outlive the context;
+ * 1 <= n < 2^30, 1 <= q <= 1024, W = ceil(q / 64)).  stream is a
+ * cudaStream_t (NULL = legacy default stream).  Round 1 starts with V_1 =
+ * all n strings, all colors -1.  Strings of q > 64 (Sec. VII's larger
+ * systems) take the same rounds; their conflict pass forms each pair's
+ * symplectic product over all words (no fused run writes), and the
+ * small-round engine is not used for them.                                 */
 int picasso_init(void** ctx, const picasso_config* cfg, const uint64_t* d_xz,
                  int64_t n, int32_t q, void* stream);
 
 /* A batch of independent string sets in one context (one launch per step
- * for the whole batch).  d_xz [N][2] holds the sets back to back; set k is
+ * for the whole batch).  d_xz [N][2W] holds the sets back to back; set k is
  * the global ids h_set_offsets[k] .. h_set_offsets[k+1] (host array of
  * nsets + 1 entries, h_set_offsets[0] = 0, N = h_set_offsets[nsets] < 2^30).
  * Set k is colored exactly as picasso_init on its own strings with seed

@@ -97,6 +97,7 @@ struct Ctx {
   cudaMemPool_t pool = nullptr;
   int64_t N = 0;
   int32_t q = 0;
+  int32_t qw = 1;  // 64-bit words per part of a string: ceil(q / 64); a string is 2 qw words
   const uint64_t* xz_user = nullptr;
 
   // the sets of the batch (one for a plain context)
@@ -377,7 +378,7 @@ int assign_round(Ctx* c) {
   if (st == PICASSO_OK) st = alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(n > nbins ? n : nbins));
   if (st == PICASSO_OK) st = alloc(c, &c->perm, n);
   if (st == PICASSO_OK) st = alloc(c, &c->gid_r, n);
-  if (st == PICASSO_OK) st = alloc(c, &c->xz_r, 2 * n);
+  if (st == PICASSO_OK) st = alloc(c, &c->xz_r, 2 * (int64_t)c->qw * n);
   if (st == PICASSO_OK) st = alloc(c, &c->prio, n);
   if (st == PICASSO_OK) st = alloc(c, &c->loff, n + 1);
   if (st != PICASSO_OK) {
@@ -390,7 +391,7 @@ int assign_round(Ctx* c) {
   cudaError_t e = launch_round_prio(c->round, c->gid, n, c->d_soff, c->nsets, c->d_sets, prio_g, s);
   if (e == cudaSuccess) e = launch_prio_order(prio_g, n, nbins, hist, hoff, tmp, c->perm, s);
   if (e == cudaSuccess)
-    e = launch_rank_gather(c->perm, n, c->gid, c->round_xz(), prio_g, c->gid_r, c->xz_r, c->prio, s);
+    e = launch_rank_gather(c->perm, n, c->gid, c->round_xz(), prio_g, c->gid_r, c->xz_r, c->prio, 2 * c->qw, s);
   // list offsets in that order
   if (e == cudaSuccess) {
     if (c->nsets == 1) {
@@ -507,7 +508,8 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
     TRYC(cudaStreamSynchronize(s));
     smax = (int64_t)(*(uint32_t*)c->h_buf);
     bucket_pairs = c->h_buf[1];
-    const bool bucket_ok = smax <= kBucketCap && P < kBucketMaxP && E < (int64_t(1) << 31);
+    const bool bucket_ok = smax <= kBucketCap && P < kBucketMaxP && E < (int64_t(1) << 31) &&
+                           (c->qw == 1 || wide_mask_fits(smax, c->qw));
     if (algo == PICASSO_CONFLICT_AUTO) algo = bucket_ok ? PICASSO_CONFLICT_BUCKET : PICASSO_CONFLICT_ALLPAIRS;
     if (algo == PICASSO_CONFLICT_BUCKET && !bucket_ok) {
       cleanup();
@@ -524,6 +526,7 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
   a.Lu = c->Lu;
   a.P = P;
   a.xz = c->xz_r;
+  a.qw = c->qw;
   a.lists = c->lists;
   a.loff = c->loff;
   a.ent_v = c->ent_v;
@@ -541,7 +544,7 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
     TRYC(launch_bucket_fill(c->lists, E, boff, bcursor, bmem, s));
     release(c, &bcursor);
     TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, (int32_t)smax, s));
-    if (a.lower && c->cfg.byte_budget == 0 && smax <= kFusedMax) {
+    if (a.lower && c->cfg.byte_budget == 0 && smax <= kFusedMax && c->qw == 1) {
       // fused mask + emit: the runs of a bucket go to one region claimed from
       // a cursor.  The column buffer is sized from the bucket pair bound and
       // the last fused build's commuting ratio; if the runs need more, the
@@ -943,6 +946,7 @@ int color_round(Ctx* c) {
   TRYC(cudaMemsetAsync(clist, 0, sizeof(uint32_t) * kClistWords * c->Ptot, s));
   a.clist = clist;
   a.xz = c->xz_r;
+  a.qw = c->qw;
   // Ordered persistent pass; if one of its bounded waits runs out (ctl[5]),
   // recolor the round with the sweep kernel from a fresh state.  The colors,
   // the carry flags and their prefix sum are enqueued behind the pass, so one
@@ -998,8 +1002,8 @@ int carry_round(Ctx* c) {
   uint64_t* xz2 = nullptr;
   if (m > 0) {
     ST(alloc(c, &gid2, m));
-    ST(alloc(c, &xz2, 2 * m));
-    CK(launch_carry_gather(c->flag, c->pos, c->n, c->gid, c->round_xz(), gid2, xz2, c->s));
+    ST(alloc(c, &xz2, 2 * (int64_t)c->qw * m));
+    CK(launch_carry_gather(c->flag, c->pos, c->n, c->gid, c->round_xz(), gid2, xz2, 2 * c->qw, c->s));
   }
   release(c, &c->gid);
   release(c, &c->xz);
@@ -1027,7 +1031,7 @@ int carry_round(Ctx* c) {
 // Whether picasso_run hands the remaining rounds to the small-round engine.
 bool small_eligible(const Ctx* c) {
   const picasso_config& cfg = c->cfg;
-  if (c->n < 1 || c->n > kSmallRoundsMax || cfg.small_engine != PICASSO_SMALL_AUTO) return false;
+  if (c->n < 1 || c->n > kSmallRoundsMax || cfg.small_engine != PICASSO_SMALL_AUTO || c->qw != 1) return false;
   if (cfg.conflict_algo != PICASSO_CONFLICT_AUTO || cfg.color_algo != PICASSO_COLOR_AUTO ||
       cfg.csr_form != PICASSO_CSR_EARLIER)
     return false;
@@ -1253,14 +1257,14 @@ int run_small(Ctx* c) {
   uint64_t* xz2 = nullptr;
   if (nleft > 0) {
     TRY(alloc(c, &gid2, nleft));
-    st = alloc(c, &xz2, 2 * nleft);
+    st = alloc(c, &xz2, 2 * (int64_t)c->qw * nleft);
     if (st != PICASSO_OK) {
       release(c, &gid2);
       cleanup();
       return st;
     }
     cudaError_t e = cudaMemcpyAsync(gid2, parity ? gid_b : gid_a, sizeof(int32_t) * nleft, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = launch_gather_xz(c->xz_user, gid2, nleft, xz2, s);
+    if (e == cudaSuccess) e = launch_gather_xz(c->xz_user, gid2, nleft, xz2, 2 * c->qw, s);
     if (e != cudaSuccess) {
       release(c, &gid2);
       release(c, &xz2);
@@ -1368,6 +1372,7 @@ int color_chunked(Ctx* c) {
   a.ranked = 1;
   a.clist = clist;
   a.xz = c->xz_r;
+  a.qw = c->qw;
   TRYC(launch_color_init(a, c->prio, ctl, s));
   ConflictArgs ca{};
   ca.n = n;
@@ -1376,6 +1381,7 @@ int color_chunked(Ctx* c) {
   ca.Lu = c->Lu;
   ca.P = c->Ptot;
   ca.xz = c->xz_r;
+  ca.qw = c->qw;
   ca.lists = c->lists;
   ca.loff = c->loff;
   ca.ent_v = c->ent_v;
@@ -1449,7 +1455,7 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
   if (h_soff[0] != 0 || n < 1 || n >= (int64_t(1) << 30) || q < 1) return PICASSO_ERR_INVALID_ARG;
   for (int k = 0; k < nsets; ++k)
     if (h_soff[k + 1] < h_soff[k]) return PICASSO_ERR_INVALID_ARG;
-  if (q > 64) return PICASSO_ERR_UNSUPPORTED;
+  if (q > kMaxQ) return PICASSO_ERR_UNSUPPORTED;
   ST(validate_cfg(cfg));
   Ctx* c = new (std::nothrow) Ctx();
   if (!c) return PICASSO_ERR_OOM;
@@ -1463,6 +1469,7 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
   }
   c->N = n;
   c->q = q;
+  c->qw = (q + 63) / 64;
   c->xz_user = d_xz;
   c->n = n;
   c->nsets = nsets;
@@ -1530,7 +1537,7 @@ int picasso_config_default(picasso_config* cfg) {
 }
 
 int picasso_pack(const uint8_t* d_codes, int64_t n, int32_t q, uint64_t* d_xz, void* stream) {
-  if (n < 0 || q < 1 || q > 64) return q > 64 ? PICASSO_ERR_UNSUPPORTED : PICASSO_ERR_INVALID_ARG;
+  if (n < 0 || q < 1 || q > kMaxQ) return q > kMaxQ ? PICASSO_ERR_UNSUPPORTED : PICASSO_ERR_INVALID_ARG;
   if (n > 0 && (!d_codes || !d_xz)) return PICASSO_ERR_INVALID_ARG;
   return map_err(launch_pack(d_codes, n, q, d_xz, (cudaStream_t)stream));
 }
@@ -1878,13 +1885,13 @@ int picasso_load_state(void* ctx, const void* h_buf, int64_t bytes) {
   uint64_t* xz2 = nullptr;
   if (n > 0) {
     ST(alloc(c, &gid2, n));
-    int st = alloc(c, &xz2, 2 * n);
+    int st = alloc(c, &xz2, 2 * (int64_t)c->qw * n);
     if (st != PICASSO_OK) {
       release(c, &gid2);
       return st;
     }
     CK(cudaMemcpyAsync(gid2, gid, 4 * n, cudaMemcpyHostToDevice, c->s));
-    CK(launch_gather_xz(c->xz_user, gid2, n, xz2, c->s));
+    CK(launch_gather_xz(c->xz_user, gid2, n, xz2, 2 * c->qw, c->s));
   }
   CK(cudaMemcpyAsync(c->color, color, 4 * N, cudaMemcpyHostToDevice, c->s));
   CK(cudaStreamSynchronize(c->s));
@@ -1917,7 +1924,7 @@ int picasso_features(const uint64_t* d_xz, int64_t n, int32_t q, uint64_t seed, 
   if (!d_xz || !d_counts || !d_feat || n < 1 || n >= (int64_t(1) << 31) || q < 1 || samples < 0 ||
       !(budget_bytes > 0.0) || !std::isfinite(budget_bytes))
     return PICASSO_ERR_INVALID_ARG;
-  if (q > 64) return PICASSO_ERR_UNSUPPORTED;
+  if (q > kMaxQ) return PICASSO_ERR_UNSUPPORTED;
   return map_err(launch_features(d_xz, n, q, seed, samples, std::log2(budget_bytes),
                                  reinterpret_cast<unsigned long long*>(d_counts), d_feat, (cudaStream_t)stream));
 }

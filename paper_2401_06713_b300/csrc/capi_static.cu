@@ -258,7 +258,7 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
       if (st != PICASSO_OK) return st;
     }
     if (rem > 0) {
-      SCK(launch_carry_gather(flag, pos, m, gid, xz, gid_buf[cur], xz_buf[cur], s));
+      SCK(launch_carry_gather(flag, pos, m, gid, xz, gid_buf[cur], xz_buf[cur], 2, s));
       gid = gid_buf[cur];
       xz = xz_buf[cur];
       cur = 1 - cur;

@@ -127,8 +127,9 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
   const int L = (int)(ld_run<FRESH>(a.loff + v + 1) - row);
   const uint32_t pv = (uint32_t)(__ldcg(&a.state[v]) >> 32);
   const bool lists = a.clist != nullptr;
+  const bool wide = a.qw > 1;  // strings of more than one word per part
   uint64_t xv = 0, zv = 0;
-  if (lists) {
+  if (lists && !wide) {
     xv = ld_run<FRESH>(a.xz + 2 * (int64_t)v);
     zv = ld_run<FRESH>(a.xz + 2 * (int64_t)v + 1);
   }
@@ -156,7 +157,10 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
         bool lb = false;
         if (word != 0u && (int32_t)(word - 1) < v) {
           const int64_t u = (int64_t)(word - 1);
-          lb = commute1(xv, zv, ld_run<FRESH>(a.xz + 2 * u), ld_run<FRESH>(a.xz + 2 * u + 1));
+          if (wide)
+            lb = commuteW(a.xz + 2 * a.qw * (int64_t)v, a.xz + 2 * a.qw * u, a.qw);
+          else
+            lb = commute1(xv, zv, ld_run<FRESH>(a.xz + 2 * u), ld_run<FRESH>(a.xz + 2 * u + 1));
         }
         const uint32_t bm = __ballot_sync(0xffffffffu, lb);
 #pragma unroll

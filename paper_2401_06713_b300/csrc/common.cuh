@@ -162,6 +162,21 @@ __device__ __forceinline__ bool commute1(uint64_t xu, uint64_t zu, uint64_t xv, 
   return (__popcll((xu & zv) ^ (zu & xv)) & 1) == 0;
 }
 
+// The same for strings of W words per part (a string is x_0 .. x_{W-1},
+// z_0 .. z_{W-1}): the symplectic form is a sum over the words, so the
+// words' terms are XORed and one parity taken.
+__device__ __forceinline__ bool commuteW(const uint64_t* __restrict__ u, const uint64_t* __restrict__ v, int W) {
+  uint64_t acc = 0;
+  for (int w = 0; w < W; ++w) acc ^= (u[w] & v[W + w]) ^ (u[W + w] & v[w]);
+  return (__popcll(acc) & 1) == 0;
+}
+
+constexpr int kMaxQ = 1024;  // qubits of a string: at most 16 words per part
+constexpr size_t kWideMaskSmem = 200 * 1024;  // shared memory of the wide mask pass
+// whether the mask pass for strings of qw > 1 words per part holds a bucket
+// of smax members in shared memory
+bool wide_mask_fits(int64_t smax, int32_t qw);
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -223,7 +238,8 @@ struct ConflictArgs {
   int32_t Lu;            // L of every vertex when all lists have one length
                          // (loff[v] = v * Lu; ent_v unused), else 0
   int64_t P;             // bucket colors of the round (sum of the sets' P)
-  const uint64_t* xz;    // [n][2]
+  const uint64_t* xz;    // [n][2 qw]: x words, then z words
+  int32_t qw;            // 64-bit words per part: ceil(q / 64)
   const int32_t* lists;  // [E] bucket colors, ascending within each vertex
   const int64_t* loff;   // [n+1]
   const int32_t* ent_v;  // [E] vertex of each list entry
@@ -307,7 +323,8 @@ struct ColorArgs {
   // word 0 counts the vertices colored c, the others hold rank + 1 of the
   // first of them
   uint32_t* clist;
-  const uint64_t* xz;  // [n][2] words in rank order (with clist)
+  const uint64_t* xz;  // [n][2 qw] words in rank order (with clist)
+  int32_t qw;          // 64-bit words per part
 };
 // Work list of all n vertices in ascending (priority, id): a counting sort on
 // the top log2(nbins) priority bits, then a sort inside each bin.  hist needs
@@ -348,13 +365,13 @@ cudaError_t launch_carry_flags(const uint64_t* state, int64_t n, const int32_t* 
 // (identity when gid_in is null), packed words and priorities.
 cudaError_t launch_rank_gather(const int32_t* perm, int64_t n, const int32_t* gid_in, const uint64_t* xz_in,
                                const uint32_t* prio_in, int32_t* gid_out, uint64_t* xz_out, uint32_t* prio_out,
-                               cudaStream_t s);
+                               int32_t S, cudaStream_t s);
 cudaError_t launch_carry_gather(const uint32_t* flag, const int64_t* pos, int64_t n, const int32_t* gid,
-                                const uint64_t* xz, int32_t* gid_out, uint64_t* xz_out, cudaStream_t s);
+                                const uint64_t* xz, int32_t* gid_out, uint64_t* xz_out, int32_t S, cudaStream_t s);
 // Remaining vertices per set after a carry: hist[k] += 1 for each gid.
 cudaError_t launch_set_counts(const int32_t* gid, int64_t n, const int64_t* soff, int32_t nsets, uint32_t* hist,
                               cudaStream_t s);
-cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t n, uint64_t* xz_out,
+cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t n, uint64_t* xz_out, int32_t S,
                              cudaStream_t s);
 // out[k] (zeroed here) = 8 n_k + 4 * run entries of set k's vertices; the
 // entries from runoff (canonical layout) or, if it is null, from cnt.

@@ -483,22 +483,21 @@ cudaError_t launch_runs_to_rows(const int64_t* rstart, const uint32_t* rcnt, con
 __global__ void k_rank_gather(const int32_t* __restrict__ perm, int64_t n, const int32_t* __restrict__ gid_in,
                               const uint64_t* __restrict__ xz_in, const uint32_t* __restrict__ prio_in,
                               int32_t* __restrict__ gid_out, uint64_t* __restrict__ xz_out,
-                              uint32_t* __restrict__ prio_out) {
+                              uint32_t* __restrict__ prio_out, int32_t S) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int64_t i = perm[t];
   gid_out[t] = gid_in ? gid_in[i] : (int32_t)i;
-  xz_out[2 * t] = xz_in[2 * i];
-  xz_out[2 * t + 1] = xz_in[2 * i + 1];
+  for (int w = 0; w < S; ++w) xz_out[S * t + w] = xz_in[S * i + w];
   prio_out[t] = prio_in[i];
 }
 
 cudaError_t launch_rank_gather(const int32_t* perm, int64_t n, const int32_t* gid_in, const uint64_t* xz_in,
                                const uint32_t* prio_in, int32_t* gid_out, uint64_t* xz_out, uint32_t* prio_out,
-                               cudaStream_t s) {
+                               int32_t S, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_rank_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(perm, n, gid_in, xz_in, prio_in, gid_out, xz_out,
-                                                             prio_out);
+                                                             prio_out, S);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -506,36 +505,34 @@ cudaError_t launch_rank_gather(const int32_t* perm, int64_t n, const int32_t* gi
 // Stable compaction of the flagged vertices (ascending global id is kept).
 __global__ void k_carry_gather(const uint32_t* __restrict__ flag, const int64_t* __restrict__ pos, int64_t n,
                                const int32_t* __restrict__ gid, const uint64_t* __restrict__ xz,
-                               int32_t* __restrict__ gid_out, uint64_t* __restrict__ xz_out) {
+                               int32_t* __restrict__ gid_out, uint64_t* __restrict__ xz_out, int32_t S) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n || !flag[v]) return;
   const int64_t p = pos[v];
   gid_out[p] = gid ? gid[v] : (int32_t)v;
-  xz_out[2 * p] = xz[2 * v];
-  xz_out[2 * p + 1] = xz[2 * v + 1];
+  for (int w = 0; w < S; ++w) xz_out[S * p + w] = xz[S * v + w];
 }
 
 cudaError_t launch_carry_gather(const uint32_t* flag, const int64_t* pos, int64_t n, const int32_t* gid,
-                                const uint64_t* xz, int32_t* gid_out, uint64_t* xz_out, cudaStream_t s) {
+                                const uint64_t* xz, int32_t* gid_out, uint64_t* xz_out, int32_t S, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_carry_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(flag, pos, n, gid, xz, gid_out, xz_out);
+  k_carry_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(flag, pos, n, gid, xz, gid_out, xz_out, S);
   count_launches(1);
   return cudaGetLastError();
 }
 
 __global__ void k_gather_xz(const uint64_t* __restrict__ xz_all, const int32_t* __restrict__ gid, int64_t n,
-                            uint64_t* __restrict__ xz_out) {
+                            uint64_t* __restrict__ xz_out, int32_t S) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const int64_t g = gid[v];
-  xz_out[2 * v] = xz_all[2 * g];
-  xz_out[2 * v + 1] = xz_all[2 * g + 1];
+  for (int w = 0; w < S; ++w) xz_out[S * v + w] = xz_all[S * g + w];
 }
 
-cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t n, uint64_t* xz_out,
+cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t n, uint64_t* xz_out, int32_t S,
                              cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_gather_xz<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xz_all, gid, n, xz_out);
+  k_gather_xz<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xz_all, gid, n, xz_out, S);
   count_launches(1);
   return cudaGetLastError();
 }

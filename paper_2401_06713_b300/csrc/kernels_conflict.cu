@@ -579,10 +579,119 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   if (FUSED) cp_async_wait_all();
 }
 
+// Mask pass for strings of more than one word per part (q > 64): the
+// outputs of the unfused k_bucket_mask (mask blocks and per-entry counts)
+// from a direct symplectic form per pair.  Block (I, J >= I) of the upper
+// triangle goes to one warp; lane j keeps partner J*32+j's words in
+// registers and every row I*32+r of the block is read from shared memory
+// as a broadcast, so a warp forms 32 pairs per row.  WM >= qw words per part.
+template <int WM, bool LOWER>
+__global__ void __launch_bounds__(kMaskThreads) k_bucket_mask_wide(ConflictArgs a, const int64_t* __restrict__ boff,
+                                                                   const int32_t* __restrict__ bmem,
+                                                                   const int64_t* __restrict__ moff, int smax) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int W = a.qw, S = 2 * W;
+  uint64_t* wv = reinterpret_cast<uint64_t*>(smem_raw);  // [smax][S] member words
+  int32_t* sfl = reinterpret_cast<int32_t*>(wv + (size_t)smax * S);
+  int32_t* cnt = sfl + smax;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
+    const int64_t o = boff[b];
+    const int s = (int)(boff[b + 1] - o);
+    if (s == 0) continue;
+    for (int i = threadIdx.x; i < s; i += kMaskThreads) {
+      sfl[i] = bmem[o + i];
+      cnt[i] = 0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < s * S; t += kMaskThreads) {
+      const int i = t / S, w = t - i * S;
+      const int32_t flat = sfl[i];
+      const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
+      wv[t] = a.xz[(int64_t)S * v + w];
+    }
+    __syncthreads();
+    const int nwb = (s + 31) >> 5;
+    const int nblk = nwb * (nwb + 1) / 2;
+    uint32_t* rmb = a.rmask + moff[b];
+    for (int qb = wid; qb < nblk; qb += kMaskWarps) {
+      int I = 0, rem = qb;
+      while (rem >= nwb - I) {
+        rem -= nwb - I;
+        ++I;
+      }
+      const int J = I + rem;
+      const int ib = I << 5, j = (J << 5) + lane;
+      const bool jv = j < s;
+      uint64_t px[WM], pz[WM];
+#pragma unroll
+      for (int w = 0; w < WM; ++w) {
+        px[w] = (jv && w < W) ? wv[(size_t)j * S + w] : 0ull;
+        pz[w] = (jv && w < W) ? wv[(size_t)j * S + W + w] : 0ull;
+      }
+      const int nr = min(32, s - ib);
+      uint32_t anti = 0u;
+      for (int r = 0; r < nr; ++r) {
+        const uint64_t* rw = wv + (size_t)(ib + r) * S;
+        uint64_t acc = 0ull;
+#pragma unroll
+        for (int w = 0; w < WM; ++w)
+          if (w < W) acc ^= (rw[w] & pz[w]) ^ (rw[W + w] & px[w]);
+        anti |= (uint32_t)(__popcll(acc) & 1) << r;
+      }
+      const uint32_t rows_ok = nr >= 32 ? 0xffffffffu : ((1u << nr) - 1u);
+      uint32_t cw = jv ? (~anti & rows_ok) : 0u;
+      // the diagonal block: no self pair; lower rows keep smaller partners
+      if (I == J) cw &= LOWER ? ((1u << lane) - 1u) : ~(1u << lane);
+      rmb[mask_block(LOWER, J, I, nwb) * 32 + lane] = cw;
+      if (cw) atomicAdd(&cnt[j], __popc(cw));
+      if (!LOWER && I != J) {
+        const uint32_t tr = transpose32(cw, lane);
+        rmb[(I * nwb + J) * 32 + lane] = tr;
+        if (tr) atomicAdd(&cnt[ib + lane], __popc(tr));
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
+    __syncthreads();
+  }
+}
+
+size_t wide_mask_smem_bytes(int64_t smax, int32_t qw) { return (size_t)smax * (16 * (size_t)qw + 8); }
+
+bool wide_mask_fits(int64_t smax, int32_t qw) { return wide_mask_smem_bytes(smax, qw) <= kWideMaskSmem; }
+
+template <int WM>
+static cudaError_t launch_mask_wide(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
+                                    const int64_t* moff, int32_t smax, cudaStream_t s) {
+  const size_t bytes = wide_mask_smem_bytes(smax, a.qw);
+  if (bytes > kWideMaskSmem) return cudaErrorInvalidValue;
+  auto kern = a.lower ? k_bucket_mask_wide<WM, true> : k_bucket_mask_wide<WM, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMaskThreads, bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
+  kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, moff, smax);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
                                int32_t smax, int32_t q, cudaStream_t s) {
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   smax = max(smax, 1);
+  if (a.qw > 1) {
+    if (a.qw <= 2) return launch_mask_wide<2>(a, boff, bmem, moff, smax, s);
+    if (a.qw <= 4) return launch_mask_wide<4>(a, boff, bmem, moff, smax, s);
+    if (a.qw <= 8) return launch_mask_wide<8>(a, boff, bmem, moff, smax, s);
+    if (a.qw <= 16) return launch_mask_wide<16>(a, boff, bmem, moff, smax, s);
+    return cudaErrorInvalidValue;
+  }
   const size_t bytes = mask_smem_bytes(smax);
   auto kern = q <= 32 ? (a.lower ? k_bucket_mask<1, true, false> : k_bucket_mask<1, false, false>)
                       : (a.lower ? k_bucket_mask<2, true, false> : k_bucket_mask<2, false, false>);
@@ -835,13 +944,17 @@ __global__ void __launch_bounds__(kApWarps * 32) k_allpairs(ConflictArgs a) {
       cur[t] = FILL ? a.runoff[ru + t] : 0;
     }
     __syncwarp();
-    const uint64_t xu = a.xz[2 * u], zu = a.xz[2 * u + 1];
+    const bool wide = a.qw > 1;
+    const uint64_t xu = wide ? 0 : a.xz[2 * u], zu = wide ? 0 : a.xz[2 * u + 1];
     const int64_t vend = a.lower ? u : a.n;  // lower rows: partners v < u only
     for (int64_t v0 = 0; v0 < vend; v0 += 32) {
       const int64_t v = v0 + lane;
       const int32_t* lv = nullptr;
       int Lv = 0, i = 0, j = 0, k = kNoShare;
-      if (v < vend && v != u && commute1(xu, zu, a.xz[2 * v], a.xz[2 * v + 1])) {
+      const bool cm = v < vend && v != u &&
+                      (wide ? commuteW(a.xz + 2 * a.qw * u, a.xz + 2 * a.qw * v, a.qw)
+                            : commute1(xu, zu, a.xz[2 * v], a.xz[2 * v + 1]));
+      if (cm) {
         lv = a.lists + a.loff[v];
         Lv = (int)(a.loff[v + 1] - a.loff[v]);
         k = next_shared(rl, Lu, lv, Lv, i, j);

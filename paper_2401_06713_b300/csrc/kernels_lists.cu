@@ -25,8 +25,35 @@ __global__ void k_pack(const uint8_t* __restrict__ codes, int64_t n, int32_t q, 
   xz[2 * (row0 + threadIdx.x) + 1] = z;
 }
 
+// Strings of more than 64 qubits: W = ceil(q / 64) words per part, the
+// string's words x_0 .. x_{W-1}, z_0 .. z_{W-1}; word w holds qubits
+// 64 w .. 64 w + 63.  One thread per (string, word).
+__global__ void k_pack_wide(const uint8_t* __restrict__ codes, int64_t n, int32_t q, uint64_t* __restrict__ xz) {
+  const int W = (q + 63) >> 6;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * W) return;
+  const int64_t v = t / W;
+  const int w = (int)(t - v * W);
+  const uint8_t* s = codes + v * q + 64 * w;
+  const int m = min(64, q - 64 * w);
+  uint64_t x = 0, z = 0;
+  for (int i = 0; i < m; ++i) {
+    const uint32_t c = s[i];
+    x |= (uint64_t)(c == 1u || c == 2u) << i;
+    z |= (uint64_t)(c == 3u || c == 2u) << i;
+  }
+  xz[2 * W * v + w] = x;
+  xz[2 * W * v + W + w] = z;
+}
+
 cudaError_t launch_pack(const uint8_t* codes, int64_t n, int32_t q, uint64_t* xz, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  if (q > 64) {
+    const int64_t t = n * ((q + 63) / 64);
+    k_pack_wide<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(codes, n, q, xz);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   const int64_t blocks = (n + 255) / 256;
   k_pack<<<(unsigned)blocks, 256, 0, s>>>(codes, n, q, xz);
   count_launches(1);

@@ -194,19 +194,21 @@ __global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict
 // all strings; counts[1] = commuting pairs among `samples` pairs of distinct
 // strings drawn by Philox (tag 3, counter = pair index, round 0): first
 // string floor(r.x n / 2^32), second floor(r.y (n-1) / 2^32), moved up by one
-// when not below the first.
-__global__ void k_feature_counts(const uint64_t* __restrict__ xz, int64_t n, uint64_t seed, int64_t samples,
-                                 unsigned long long* __restrict__ counts) {
+// when not below the first.  Strings of W words per part.
+__global__ void k_feature_counts(const uint64_t* __restrict__ xz, int64_t n, int32_t W, uint64_t seed,
+                                 int64_t samples, unsigned long long* __restrict__ counts) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t S = 2 * W;
   unsigned long long wsum = 0, csum = 0;
-  for (int64_t v = tid; v < n; v += stride) wsum += __popcll(xz[2 * v] | xz[2 * v + 1]);
+  for (int64_t v = tid; v < n; v += stride)
+    for (int k = 0; k < W; ++k) wsum += __popcll(xz[S * v + k] | xz[S * v + W + k]);
   for (int64_t p = tid; p < samples; p += stride) {
     const u32x4 r = philox_block(seed, 0, p, 3u, 0u);
     const int64_t u = (int64_t)(((uint64_t)r.x * (uint64_t)n) >> 32);
     int64_t w = (int64_t)(((uint64_t)r.y * (uint64_t)(n - 1)) >> 32);
     if (w >= u) ++w;
-    csum += commute1(xz[2 * u], xz[2 * u + 1], xz[2 * w], xz[2 * w + 1]) ? 1ull : 0ull;
+    csum += commuteW(xz + S * u, xz + S * w, W) ? 1ull : 0ull;
   }
   for (int d = 16; d; d >>= 1) {
     wsum += __shfl_xor_sync(0xffffffffu, wsum, d);
@@ -275,7 +277,7 @@ cudaError_t launch_features(const uint64_t* xz, int64_t n, int32_t q, uint64_t s
   if (e != cudaSuccess) return e;
   if (n < 2) samples = 0;
   if (n > 0) {
-    k_feature_counts<<<148 * 4, 256, 0, s>>>(xz, n, seed, samples, counts);
+    k_feature_counts<<<148 * 4, 256, 0, s>>>(xz, n, (q + 63) / 64, seed, samples, counts);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       ca.ranked = 1;
       ca.clist = a.clist;
       ca.xz = a.xz_r;
+      ca.qw = 1;
       bool ok = true;
       while (ok) {
         int t = 0;

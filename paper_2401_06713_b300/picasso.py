@@ -181,13 +181,19 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def words_per_part(q: int) -> int:
+    """64-bit words per part (x or z) of a packed string of q qubits."""
+    return (q + 63) // 64
+
+
 def pack(codes: torch.Tensor, stream=None) -> torch.Tensor:
     """uint8 codes [n, q] (0=I 1=X 2=Y 3=Z) on the GPU -> symplectic words
-    int64 [n, 2] (bit patterns of uint64 x, z)."""
+    int64 [n, 2W] (bit patterns of uint64 x_0 .. x_{W-1}, z_0 .. z_{W-1};
+    W = ceil(q / 64))."""
     assert codes.is_cuda and codes.dtype == torch.uint8 and codes.dim() == 2
     codes = codes.contiguous()
     n, q = codes.shape
-    xz = torch.empty((n, 2), dtype=torch.int64, device=codes.device)
+    xz = torch.empty((n, 2 * words_per_part(q)), dtype=torch.int64, device=codes.device)
     _ck(_lib().picasso_pack(_ptr(codes), n, q, _ptr(xz), _stream(stream)), "picasso_pack")
     return xz
 
@@ -211,7 +217,8 @@ def philox_draws(seed: int, rnd: int, gid: int, tag: int, i0: int, count: int, d
 
 
 class Picasso:
-    """A context over packed strings ``xz`` (int64 [n, 2] on the GPU)."""
+    """A context over packed strings ``xz`` (int64 [n, 2W] on the GPU, W =
+    ceil(q / 64))."""
 
     def __init__(self, xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
                  algo: str = "auto", max_rounds: int = 100000, byte_budget: int = 0, stream=None,
@@ -220,7 +227,7 @@ class Picasso:
         """One set, or with ``set_offsets`` (host, nsets + 1 ints) a batch of
         independent sets stored back to back in ``xz`` (seeds default to
         seed + k)."""
-        assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2
+        assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2 * words_per_part(q)
         self.xz = xz.contiguous()
         self.n = int(xz.shape[0])
         self.q = q
@@ -410,7 +417,7 @@ def color_strings(codes: torch.Tensor, seed: int = 0, palette=(1, 8), alpha: flo
 def features(xz: torch.Tensor, q: int, seed: int, budget_bytes: float, samples: int = 1 << 16, stream=None):
     """Regressor inputs of one set (Sec. V): (counts int64 [2], feat float32 [5])
     on the GPU; see picasso_features."""
-    assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2
+    assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2 * words_per_part(q)
     xz = xz.contiguous()
     counts = torch.empty(2, dtype=torch.int64, device=xz.device)
     feat = torch.empty(5, dtype=torch.float32, device=xz.device)

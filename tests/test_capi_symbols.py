@@ -31,5 +31,6 @@ def test_strerror_and_defaults_without_gpu():
     # argument validation happens before any device work
     h = ctypes.c_void_p()
     assert lib.picasso_init(ctypes.byref(h), ctypes.byref(cfg), None, 10, 8, None) == picasso.ERR_INVALID_ARG
-    assert lib.picasso_pack(None, 5, 65, None, None) == picasso.ERR_UNSUPPORTED
+    assert lib.picasso_pack(None, 5, 1025, None, None) == picasso.ERR_UNSUPPORTED
+    assert lib.picasso_pack(None, 5, 65, None, None) == picasso.ERR_INVALID_ARG
     assert lib.picasso_destroy(None) == picasso.ERR_INVALID_ARG
