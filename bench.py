@@ -272,6 +272,7 @@ def run_gpu(args):
     learned_form = None if args.no_learned else bench_learned(rank)
     chunked = None if args.no_chunked else bench_chunked(rank, codes, colors_np)
     dynamic = None if args.no_dynamic else bench_dynamic(rank, codes, st)
+    wide = None if args.no_wide else bench_wide(rank, n)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -293,7 +294,7 @@ def run_gpu(args):
         "pair_tests_per_s": pair_rate, "colors": int(len(np.unique(colors_np))),
         "colors_sum_P": st["colors_used"], "rounds": rounds,
         "peak_bytes": st["peak_bytes"], "breakdown_ms_per_step": per_step,
-        "roofline": roofline, "roofline_pairs": roofline_pairs, "chunked": chunked, "dynamic": dynamic, "cpu_baseline": cpu, "batch": batch, "learned": learned_form,
+        "roofline": roofline, "roofline_pairs": roofline_pairs, "chunked": chunked, "dynamic": dynamic, "wide": wide, "cpu_baseline": cpu, "batch": batch, "learned": learned_form,
         "e2e": {"value": world * n / (ms_e2e / args.steps / 1e3), "unit": "strings/s",
                 "h2d_bytes_per_step": n * Q, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": launches, "clocks": clocks, "wall_s": t_wall,
@@ -383,6 +384,38 @@ def bench_dynamic(rank, codes, st_static):
     return {"workload": "the benchmark workload, color_algo DYNAMIC (Alg. 2, parallel rule)",
             "ms": ev[0].elapsed_time(ev[1]), "rounds": r, "colors_sum_P": st["colors_used"],
             "static_colors_sum_P": st_static["colors_used"], "peak_bytes": st["peak_bytes"]}
+
+
+def bench_wide(rank, n, q=128, p_w=0.125):
+    """Strings of twice the qubits at the same mean weight (q = 128, weight
+    p = 0.125: 16 non-identity positions, as the benchmark workload's q = 64,
+    p = 0.25), same palette law: whole-run time, rounds, colors and the wide
+    mask pass's pair-test rate."""
+    import torch
+
+    from paper_2401_06713_b300 import picasso, synth
+
+    codes = torch.from_numpy(synth.pauli_weighted(n, q, p_w, seed=rank)).cuda()
+
+    def run():
+        xz = picasso.pack(codes)
+        with picasso.Picasso(xz, q, seed=rank, palette=(NUM, DEN), alpha=ALPHA) as p:
+            _, r = p.run()
+            return r, p.stats()
+
+    run()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    r, st = run()
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    return {"workload": f"n={n} q={q} p={p_w} P=n/{DEN} alpha={ALPHA} (2 words per part)",
+            "ms": ms, "strings_per_s": n / (ms / 1e3), "rounds": r, "colors_sum_P": st["colors_used"],
+            "t_build_ms": st["t_build_ms"], "t_color_ms": st["t_color_ms"],
+            "pair_tests_per_s": st["tested_pairs"] / (st["t_pairs_ms"] / 1e3) if st["t_pairs_ms"] > 0 else None,
+            "peak_bytes": st["peak_bytes"]}
 
 
 def bench_chunked(rank, codes, ref_colors, budget=2_000_000_000):
@@ -526,6 +559,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-chunked", action="store_true")
     ap.add_argument("--no-dynamic", action="store_true")
+    ap.add_argument("--no-wide", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
