@@ -271,6 +271,7 @@ def run_gpu(args):
     batch = None if args.no_batch else bench_batch(rank)
     learned_form = None if args.no_learned else bench_learned(rank)
     chunked = None if args.no_chunked else bench_chunked(rank, codes, colors_np)
+    host_csr = None if args.no_host else bench_host(rank, codes, colors_np)
     dynamic = None if args.no_dynamic else bench_dynamic(rank, codes, st)
     wide = None if args.no_wide else bench_wide(rank, n)
 
@@ -294,7 +295,7 @@ def run_gpu(args):
         "pair_tests_per_s": pair_rate, "colors": int(len(np.unique(colors_np))),
         "colors_sum_P": st["colors_used"], "rounds": rounds,
         "peak_bytes": st["peak_bytes"], "breakdown_ms_per_step": per_step,
-        "roofline": roofline, "roofline_pairs": roofline_pairs, "chunked": chunked, "dynamic": dynamic, "wide": wide, "cpu_baseline": cpu, "batch": batch, "learned": learned_form,
+        "roofline": roofline, "roofline_pairs": roofline_pairs, "chunked": chunked, "host_csr": host_csr, "dynamic": dynamic, "wide": wide, "cpu_baseline": cpu, "batch": batch, "learned": learned_form,
         "e2e": {"value": world * n / (ms_e2e / args.steps / 1e3), "unit": "strings/s",
                 "h2d_bytes_per_step": n * Q, "d2h_bytes_per_step": 4 * n},
         "gpu_launches": launches, "clocks": clocks, "wall_s": t_wall,
@@ -447,6 +448,35 @@ def bench_chunked(rank, codes, ref_colors, budget=2_000_000_000):
             "identical_colors": bool(np.array_equal(c.cpu().numpy(), ref_colors))}
 
 
+def bench_host(rank, codes, ref_colors, budget=2_000_000_000):
+    """The benchmark workload under a 2 GB byte budget in host mode (Alg. 3's
+    fallback): rounds over the budget keep their columns in mapped pinned host
+    memory, written and read in place.  Same colors as the device run."""
+    import numpy as np
+    import torch
+
+    from paper_2401_06713_b300 import picasso
+
+    def run():
+        xz = picasso.pack(codes)
+        with picasso.Picasso(xz, Q, seed=rank, palette=(NUM, DEN), alpha=ALPHA, byte_budget=budget,
+                             budget_mode="host") as p:
+            c, _ = p.run()
+            return c, p.stats()
+
+    run()  # the host buffer is pinned once and kept for later contexts
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    c, st = run()
+    ev[1].record()
+    torch.cuda.synchronize()
+    return {"workload": f"the benchmark workload, byte budget {budget} bytes, budget_mode host",
+            "ms": ev[0].elapsed_time(ev[1]), "host_csr_rounds": st["host_csr_rounds"],
+            "t_build_ms": st["t_build_ms"], "t_color_ms": st["t_color_ms"], "peak_bytes": st["peak_bytes"],
+            "identical_colors": bool(np.array_equal(c.cpu().numpy(), ref_colors))}
+
+
 def bench_learned(rank, count=16):
     """The learned-parameter form on held-out n = 200,000, q = 56 sets, each
     with its own byte budget: the committed regressor's pick (features, MLP
@@ -560,6 +590,7 @@ def main():
     ap.add_argument("--no-chunked", action="store_true")
     ap.add_argument("--no-dynamic", action="store_true")
     ap.add_argument("--no-wide", action="store_true")
+    ap.add_argument("--no-host", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

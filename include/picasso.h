@@ -98,10 +98,18 @@ typedef struct {
  *         emit the chunk's rows, color them, free them, next chunk.  In the
  *         EARLIER form a row lists only earlier neighbours, so the colors are
  *         those of the unchunked round.  ERR_BUDGET only if one vertex's rows
- *         alone exceed the budget.                                        */
+ *         alone exceed the budget.
+ *   HOST  Alg. 3's fallback: the round's columns go to pinned host memory
+ *         (mapped, so the emit pass writes them and the coloring reads them
+ *         in place; row and run offsets stay on the device).  The host
+ *         buffer grows to the largest such round; picasso_destroy keeps it
+ *         for later contexts (picasso_trim_memory frees it).  Colors are
+ *         those of the device round; picasso_build_conflicts then hands out
+ *         d_col as a mapped host pointer (valid on the device, UVA).       */
 typedef enum {
   PICASSO_BUDGET_FAIL = 0,
-  PICASSO_BUDGET_CHUNK = 1
+  PICASSO_BUDGET_CHUNK = 1,
+  PICASSO_BUDGET_HOST = 2
 } picasso_budget_mode;
 
 /* Which half of G_c the conflict CSR stores.  The coloring step only reads a
@@ -205,7 +213,7 @@ typedef struct {
   int32_t small_stops;        /* engine launches that handed a round back   */
   double t_small_ms;          /* time in the small-round engine             */
   int32_t round_chunks;       /* chunks of the rounds colored by chunk      */
-  int32_t pad_;
+  int32_t host_csr_rounds;    /* rounds whose columns went to host memory   */
 } picasso_stats;
 
 /* Fill *cfg with the defaults: seed 0, P = n/8, alpha = 2 (the paper's normal

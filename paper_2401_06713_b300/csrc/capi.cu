@@ -81,10 +81,48 @@ void pinned_put(int64_t* p) {
   g_pin_free.push_back(p);
 }
 
+// Host CSR buffers (budget mode HOST): mapped pinned memory, kept across
+// contexts for the same reason; a request takes the largest cached buffer
+// if it is big enough.
+std::vector<std::pair<int32_t*, int64_t>> g_hcol_free;
+
+cudaError_t hostcol_get(int64_t need, int32_t** out, int64_t* cap) {
+  {
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    auto best = g_hcol_free.end();
+    for (auto it = g_hcol_free.begin(); it != g_hcol_free.end(); ++it)
+      if (it->second >= need && (best == g_hcol_free.end() || it->second < best->second)) best = it;
+    if (best != g_hcol_free.end()) {
+      *out = best->first;
+      *cap = best->second;
+      g_hcol_free.erase(best);
+      return cudaSuccess;
+    }
+  }
+  *out = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaHostAlloc((void**)out, sizeof(int32_t) * (size_t)std::max<int64_t>(need, 1),
+                                cudaHostAllocMapped | cudaHostAllocPortable);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return e;
+  }
+  *cap = need;
+  return cudaSuccess;
+}
+
+void hostcol_put(int32_t* p, int64_t cap) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  g_hcol_free.emplace_back(p, cap);
+}
+
 void pinned_trim() {
   std::lock_guard<std::mutex> lock(g_pin_mu);
   for (int64_t* p : g_pin_free) cudaFreeHost(p);
   g_pin_free.clear();
+  for (auto& b : g_hcol_free) cudaFreeHost(b.first);
+  g_hcol_free.clear();
 }
 }  // namespace
 
@@ -151,6 +189,12 @@ struct Ctx {
   int32_t *ck_bmem = nullptr, *ck_ibkt = nullptr;
   uint32_t* ck_rmask = nullptr;
   int32_t round_chunks = 0;  // chunks of all chunked rounds
+  // host CSR (budget mode HOST): the columns of a round over the budget live
+  // in mapped pinned host memory, kept for the next such round
+  int32_t* hcol = nullptr;
+  int64_t hcol_cap = 0;
+  bool col_host = false;  // c->col points into hcol
+  int32_t host_rounds = 0;
   int64_t* rstart = nullptr;
   uint32_t* rcnt = nullptr;
   double commute_ratio = 0.6;  // nnz / bucket pair bound of the last fused build
@@ -249,7 +293,12 @@ void free_color(Ctx* c) {
 
 void free_build(Ctx* c) {
   release(c, &c->off);
-  release(c, &c->col);
+  if (c->col_host) {
+    c->col = nullptr;  // hcol stays with the context
+    c->col_host = false;
+  } else {
+    release(c, &c->col);
+  }
   release(c, &c->runoff);
   release(c, &c->rstart);
   release(c, &c->rcnt);
@@ -682,12 +731,30 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
       c->chunk_pending = true;
       return PICASSO_OK;
     }
-    cleanup();
-    release(c, &c->runoff);
-    return PICASSO_ERR_BUDGET;
+    if (c->cfg.budget_mode != PICASSO_BUDGET_HOST) {
+      cleanup();
+      release(c, &c->runoff);
+      return PICASSO_ERR_BUDGET;
+    }
+    // Alg. 3: a conflict graph the device cannot hold goes to host memory.
+    // The columns are written to mapped pinned host memory by the emit
+    // pass and read from there by the coloring (the row and run offsets
+    // stay on the device).
+    if (c->hcol_cap < nnz) {
+      TRYC(cudaStreamSynchronize(s));
+      hostcol_put(c->hcol, c->hcol_cap);
+      c->hcol = nullptr;
+      c->hcol_cap = 0;
+      TRYC(hostcol_get(nnz, &c->hcol, &c->hcol_cap));
+    }
+    int32_t* dcol = nullptr;
+    TRYC(cudaHostGetDevicePointer((void**)&dcol, c->hcol, 0));
+    c->col = dcol;
+    c->col_host = true;
+    c->host_rounds += 1;
   }
   TRY(alloc(c, &c->off, n + 1));
-  TRY(alloc(c, &c->col, nnz));
+  if (!c->col_host) TRY(alloc(c, &c->col, nnz));
   a.runoff = c->runoff;
   a.col = c->col;
   TRYC(cudaEventRecord(c->ev[4], s));
@@ -1442,7 +1509,7 @@ int validate_cfg(const picasso_config* cfg) {
       cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
       cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2 ||
       cfg->color_algo < 0 || cfg->color_algo > 2 || cfg->csr_form < 0 || cfg->csr_form > 1 ||
-      cfg->small_engine < 0 || cfg->small_engine > 1 || cfg->budget_mode < 0 || cfg->budget_mode > 1)
+      cfg->small_engine < 0 || cfg->small_engine > 1 || cfg->budget_mode < 0 || cfg->budget_mode > 2)
     return PICASSO_ERR_INVALID_ARG;
   return PICASSO_OK;
 }
@@ -1720,7 +1787,7 @@ int picasso_copy_csr(void* ctx, int64_t* d_off, int32_t* d_col) {
   ST(canonical_csr(c));
   if (d_off) CK(cudaMemcpyAsync(d_off, c->off, sizeof(int64_t) * (c->n + 1), cudaMemcpyDeviceToDevice, c->s));
   if (d_col && c->nnz > 0)
-    CK(cudaMemcpyAsync(d_col, c->col, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToDevice, c->s));
+    CK(cudaMemcpyAsync(d_col, c->col, sizeof(int32_t) * c->nnz, cudaMemcpyDefault, c->s));
   return PICASSO_OK;
 }
 
@@ -1771,6 +1838,7 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->small_stops = c->small_stops;
   out->t_small_ms = c->t_small;
   out->round_chunks = c->round_chunks;
+  out->host_csr_rounds = c->host_rounds;
   const int ns = c->sweeps < kSweepLog ? c->sweeps : kSweepLog;
   const unsigned long long* t = reinterpret_cast<const unsigned long long*>(c->sweep_log + 8 + kSweepLog);
   for (int i = 0; i < ns; ++i) {
@@ -1996,6 +2064,7 @@ int picasso_destroy(void* ctx) {
   release(c, &c->d_hist);
   release(c, &c->d_set_bytes);
   cudaStreamSynchronize(c->s);
+  hostcol_put(c->hcol, c->hcol_cap);
   for (int i = 0; i < 6; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   pinned_put(c->h_buf);

@@ -19,7 +19,7 @@ ALGOS = {"auto": 0, "allpairs": 1, "bucket": 2}
 COLOR_ALGOS = {"auto": 0, "sweep": 1, "dynamic": 2}
 CSR_FORMS = {"earlier": 0, "full": 1}
 SMALL_ENGINE = {"auto": 0, "off": 1}
-BUDGET_MODES = {"fail": 0, "chunk": 1}
+BUDGET_MODES = {"fail": 0, "chunk": 1, "host": 2}
 
 
 class PicassoError(RuntimeError):
@@ -86,7 +86,7 @@ class Stats(ctypes.Structure):
         ("small_stops", ctypes.c_int32),
         ("t_small_ms", ctypes.c_double),
         ("round_chunks", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("host_csr_rounds", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -1,8 +1,10 @@
-"""Rounds over the byte budget colored in chunks of coloring order
-(budget_mode="chunk") against the CPU oracle.
+"""Rounds over the byte budget, colored in chunks of coloring order
+(budget_mode="chunk") or with their columns in host memory (budget_mode=
+"host", Alg. 3's fallback), against the CPU oracle.
 
-Integer work, bit-exact: a chunked run colors exactly as the oracle's
-unchunked run, and no chunk's CSR passes the budget."""
+Integer work, bit-exact: either way a run colors exactly as the oracle's
+unrestricted run; no chunk's CSR passes the budget, and the host CSR equals
+the device one."""
 import numpy as np
 import pytest
 import torch
@@ -82,3 +84,52 @@ def test_chunked_round_steps_equal_unchunked(pc):
     assert out["chunk"][0] == out["fail"][0]
     assert np.array_equal(out["chunk"][1], out["fail"][1]) and np.array_equal(out["chunk"][2], out["fail"][2])
     assert out["chunk"][3] > 1 and out["fail"][3] == 0
+
+
+@pytest.mark.parametrize("n,q,pw,num,den,alpha,seed,parts", [
+    (5000, 40, 0.3, 1, 8, 2.0, 6, 3),
+    (12000, 64, 0.25, 1, 16, 1.5, 2, 7),
+])
+def test_host_csr_run_matches_oracle(pc, orc, n, q, pw, num, den, alpha, seed, parts):
+    # Alg. 3's fallback: rounds over the budget keep their columns in host
+    # memory; the colors are those of the device rounds
+    chars = synth.pauli_weighted(n, q, pw, seed=seed)
+    ref, rounds, ostats = orc.run(chars, seed, num, den, alpha)
+    budget = _round1_bytes(ostats) // parts
+    with pc.Picasso(_xz(pc, chars), q, seed=seed, palette=(num, den), alpha=alpha, byte_budget=budget,
+                    budget_mode="host") as p:
+        got, r = p.run()
+        st = p.stats()
+    assert r == rounds and np.array_equal(got.cpu().numpy(), ref)
+    assert st["colors_used"] == int(ostats[:, 1].sum())
+    assert st["host_csr_rounds"] >= 1 and st["round_chunks"] == 0
+
+
+@pytest.mark.parametrize("form", ["earlier", "full"])
+def test_host_csr_equals_device_csr(pc, form):
+    chars = synth.pauli_weighted(8000, 48, 0.25, seed=7)
+    xz = _xz(pc, chars)
+    out = {}
+    for mode, budget in (("fail", 0), ("host", 100_000)):
+        with pc.Picasso(xz, 48, seed=7, palette=(1, 8), alpha=2.0, csr=form, byte_budget=budget,
+                        budget_mode=mode) as p:
+            p.assign_lists(*p.round_params())
+            p.build_conflicts()
+            off, col = p.csr()
+            k = p.color()
+            out[mode] = (off.cpu().numpy(), col.cpu().numpy(), k, p.colors().cpu().numpy(),
+                         p.stats()["host_csr_rounds"])
+    assert np.array_equal(out["host"][0], out["fail"][0]) and np.array_equal(out["host"][1], out["fail"][1])
+    assert out["host"][2] == out["fail"][2] and np.array_equal(out["host"][3], out["fail"][3])
+    assert out["host"][4] == 1 and out["fail"][4] == 0
+
+
+def test_host_csr_dynamic_order(pc, orc):
+    chars = synth.pauli_weighted(4000, 48, 0.3, seed=12)
+    ref, rounds, ostats = orc.run(chars, 4, 1, 8, 2.0, colorer="dynamic_par")
+    budget = 8 * 4001 + 4 * int(ostats[0, 4]) // 4
+    with pc.Picasso(_xz(pc, chars), 48, seed=4, palette=(1, 8), alpha=2.0, color="dynamic", byte_budget=budget,
+                    budget_mode="host") as p:
+        got, r = p.run()
+        assert p.stats()["host_csr_rounds"] >= 1
+    assert r == rounds and np.array_equal(got.cpu().numpy(), ref)
