@@ -368,6 +368,13 @@ int picasso_features(const uint64_t* d_xz, int64_t n, int32_t q,
                      uint64_t seed, int64_t samples, double budget_bytes,
                      int64_t* d_counts, float* d_feat, void* stream);
 
+/* The same features for the weighted objective of Eq. ml, min over (P, alpha)
+ * of beta C + (1 - beta) |E_c|: d_feat[4] = 4 beta - 2 in place of the
+ * budget term (0 <= beta <= 1; the other four and d_counts as above).      */
+int picasso_features_beta(const uint64_t* d_xz, int64_t n, int32_t q,
+                          uint64_t seed, int64_t samples, double beta,
+                          int64_t* d_counts, float* d_feat, void* stream);
+
 int32_t picasso_mlp_param_count(void);
 
 /* d_y[b][0..1] = MLP(d_w, d_x[b][0..4]) for b < batch (fp32 in and out). */

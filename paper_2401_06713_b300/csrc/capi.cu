@@ -1997,6 +1997,16 @@ int picasso_features(const uint64_t* d_xz, int64_t n, int32_t q, uint64_t seed, 
                                  reinterpret_cast<unsigned long long*>(d_counts), d_feat, (cudaStream_t)stream));
 }
 
+int picasso_features_beta(const uint64_t* d_xz, int64_t n, int32_t q, uint64_t seed, int64_t samples, double beta,
+                          int64_t* d_counts, float* d_feat, void* stream) {
+  if (!d_xz || !d_counts || !d_feat || n < 1 || n >= (int64_t(1) << 31) || q < 1 || samples < 0 ||
+      !(beta >= 0.0 && beta <= 1.0))
+    return PICASSO_ERR_INVALID_ARG;
+  if (q > kMaxQ) return PICASSO_ERR_UNSUPPORTED;
+  return map_err(launch_features(d_xz, n, q, seed, samples, 0.0, reinterpret_cast<unsigned long long*>(d_counts),
+                                 d_feat, (cudaStream_t)stream, beta));
+}
+
 int32_t picasso_mlp_param_count(void) { return mlp_param_count(); }
 
 int picasso_mlp_forward(const uint16_t* d_w, const float* d_x, int32_t batch, float* d_y, void* stream) {

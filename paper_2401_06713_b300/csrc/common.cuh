@@ -492,8 +492,11 @@ cudaError_t launch_mlp_backward(const void* w, const float* x, const float* t, f
 cudaError_t launch_mlp_adamw(float* master, void* w, const float* g, float* m, float* v, float lr, float b1,
                              float b2, float eps, float wd, int step, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* a, void* b, int n, cudaStream_t s);
+// feat[4] is log2(budget / n) / 4 - 3 (log2_budget given), or 4 beta - 2
+// when beta >= 0 (the weighted objective of Eq. ml)
 cudaError_t launch_features(const uint64_t* xz, int64_t n, int32_t q, uint64_t seed, int64_t samples,
-                            double log2_budget, unsigned long long* counts, float* feat, cudaStream_t s);
+                            double log2_budget, unsigned long long* counts, float* feat, cudaStream_t s,
+                            double beta = -1.0);
 cudaError_t launch_fill_i32(int32_t* out, int64_t n, int32_t v, cudaStream_t s);
 
 }  // namespace picasso

@@ -227,14 +227,14 @@ __global__ void k_feature_counts(const uint64_t* __restrict__ xz, int64_t n, int
 // L = alpha ln n, so size and budget enter on the log scales that count is
 // linear in.
 __global__ void k_feature_final(const unsigned long long* __restrict__ counts, int64_t n, int32_t q, int64_t samples,
-                                double log2_budget, float* __restrict__ feat) {
+                                double log2_budget, double beta, float* __restrict__ feat) {
   if (threadIdx.x != 0) return;
   const double dn = (double)n;
   feat[0] = (float)(n > 1 ? log2(log(dn)) - 3.0 : -3.0);
   feat[1] = (float)((double)q / 64.0);
   feat[2] = (float)((double)counts[0] / (dn * (double)q));
   feat[3] = samples > 0 ? (float)((double)counts[1] / (double)samples) : 1.0f;
-  feat[4] = (float)((log2_budget - log2(dn)) / 4.0 - 3.0);
+  feat[4] = beta >= 0.0 ? (float)(4.0 * beta - 2.0) : (float)((log2_budget - log2(dn)) / 4.0 - 3.0);
 }
 
 int mlp_param_count() { return kParams; }
@@ -272,7 +272,8 @@ cudaError_t launch_to_bf16(const float* a, void* b, int n, cudaStream_t s) {
 }
 
 cudaError_t launch_features(const uint64_t* xz, int64_t n, int32_t q, uint64_t seed, int64_t samples,
-                            double log2_budget, unsigned long long* counts, float* feat, cudaStream_t s) {
+                            double log2_budget, unsigned long long* counts, float* feat, cudaStream_t s,
+                            double beta) {
   cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   if (n < 2) samples = 0;
@@ -281,7 +282,7 @@ cudaError_t launch_features(const uint64_t* xz, int64_t n, int32_t q, uint64_t s
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  k_feature_final<<<1, 32, 0, s>>>(counts, n, q, samples, log2_budget, feat);
+  k_feature_final<<<1, 32, 0, s>>>(counts, n, q, samples, log2_budget, beta, feat);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -19,6 +19,15 @@ features to that pair.  Here:
   a non-finite or out-of-range output falls back to the paper's normal mode
   P/n = 1/8, alpha = 2 (Sec. VI).
 
+A second network of the same shape takes Eq. ml as the paper states it: the
+weight beta (an input in place of the budget term) trades colors against
+conflict edges, min beta C / C_min + (1 - beta) B / B_min over the grid,
+where B is the largest round's conflict CSR bytes (8 per row + 4 per entry,
+the size |E_c| sets) and each term is divided by its smallest value on the
+instance's grid, so that beta weighs relative excesses of two quantities of
+very different scale.  Labels for beta in {0.1, ..., 0.9} come from the
+same unconstrained grid runs.
+
 Every arithmetic step of the path (features, MLP, optimizer, the runs) is a
 library kernel; the host loop only orders the calls and keeps the records.
 """
@@ -37,6 +46,8 @@ GRID_ALPHA = (1.0, 1.5, 2.0, 3.0)
 DEFAULT = (8, 2.0)
 T_SHIFT = (3.5, 2.0)  # targets: log2(den) - 3.5, alpha - 2
 WEIGHTS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "regressor_weights.npz")
+BETA_WEIGHTS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "regressor_beta_weights.npz")
+BETAS = tuple(round(0.1 * k, 1) for k in range(1, 10))
 
 
 def targets(den: int, alpha: float):
@@ -179,6 +190,32 @@ def run_learned(reg: "Regressor", xz: torch.Tensor, q: int, seed: int, budget: f
     return den, alpha, None, None, tries
 
 
+def grid_full(xz: torch.Tensor, q: int, seed: int):
+    """Every grid point run without a budget: {(den, alpha): (colors, peak
+    conflict bytes)}."""
+    return {(d, a): run_config(xz, q, seed, d, a, None)[:2] for d in GRID_DEN for a in GRID_ALPHA}
+
+
+def beta_objective(grid, beta: float):
+    """Eq. ml on one instance's grid, each term over its smallest value:
+    {(den, alpha): beta C / C_min + (1 - beta) B / B_min}."""
+    cmin = min(c for c, _ in grid.values())
+    bmin = min(b for _, b in grid.values())
+    return {k: beta * c / cmin + (1.0 - beta) * b / bmin for k, (c, b) in grid.items()}
+
+
+def beta_label(grid, beta: float):
+    """Grid point minimising the weighted objective (ties: fewer colors)."""
+    j = beta_objective(grid, beta)
+    return min(j, key=lambda k: (j[k], grid[k][0], k))
+
+
+def predict_beta(reg: "Regressor", xz: torch.Tensor, q: int, seed: int, beta: float, samples: int = 1 << 16):
+    """The beta network's pick for one set: (den, alpha, fell_back)."""
+    _, f = picasso.features_beta(xz, q, seed, beta, samples)
+    return reg.predict(f)[0]
+
+
 def instance(spec, device="cuda"):
     """(xz on the GPU, q, budget) of a ``synth.learned_specs`` entry."""
     n, q, p, budget, seed, stream = spec
@@ -233,6 +270,56 @@ def evaluate(reg: Regressor, specs, seed_base: int, samples: int = 1 << 16, log=
     return rows
 
 
+def label_set_beta(specs, seed_base: int = 0, samples: int = 1 << 16, log=None):
+    """Features [N * len(BETAS), 5] (GPU, one row per instance and beta) and
+    the matching grid labels."""
+    feats, labels = [], []
+    for i, spec in enumerate(specs):
+        xz, q, _ = instance(spec)
+        grid = grid_full(xz, q, seed_base + i)
+        for beta in BETAS:
+            _, f = picasso.features_beta(xz, q, seed_base + i, beta, samples)
+            feats.append(f)
+            labels.append(beta_label(grid, beta))
+        if log and (i % 100 == 0 or i == len(specs) - 1):
+            log(f"labelled {i + 1}/{len(specs)}")
+        del xz
+    return torch.stack(feats), labels
+
+
+def evaluate_beta(reg: Regressor, specs, seed_base: int, samples: int = 1 << 16, log=None):
+    """Per held-out instance and beta: the objective of the regressor's pick,
+    of the default and of the grid's best (1 + its relative excess)."""
+    rows = []
+    for i, spec in enumerate(specs):
+        xz, q, _ = instance(spec)
+        seed = seed_base + i
+        grid = grid_full(xz, q, seed)
+        for beta in BETAS:
+            den, alpha, fell_back = predict_beta(reg, xz, q, seed, beta, samples)
+            j = beta_objective(grid, beta)
+            best = beta_label(grid, beta)
+            rows.append({"n": spec[0], "q": spec[1], "p": spec[2], "beta": beta, "pick": (den, alpha),
+                         "fell_back": fell_back, "best": best, "j_pick": j[(den, alpha)], "j_best": j[best],
+                         "j_default": j[DEFAULT]})
+        if log and (i % 10 == 0 or i == len(specs) - 1):
+            log(f"evaluated {i + 1}/{len(specs)}")
+        del xz
+    return rows
+
+
+def summarize_beta(rows):
+    r_pick = [r["j_pick"] / r["j_best"] for r in rows]
+    r_def = [r["j_default"] / r["j_best"] for r in rows]
+    return {"cases": len(rows),
+            "learned": {"picked_best": sum(1 for r in rows if tuple(r["pick"]) == tuple(r["best"])),
+                        "within_5pct_of_best": sum(1 for x in r_pick if x <= 1.05),
+                        "mean_objective_over_best": float(np.mean(r_pick)),
+                        "fallbacks": sum(1 for r in rows if r["fell_back"])},
+            "default": {"within_5pct_of_best": sum(1 for x in r_def if x <= 1.05),
+                        "mean_objective_over_best": float(np.mean(r_def))}}
+
+
 def summarize(rows):
     out = {"instances": len(rows)}
     ok = [r for r in rows if r["best_fits"]]
@@ -276,11 +363,15 @@ def main(argv=None):
     ap.add_argument("--out", default=WEIGHTS_PATH)
     ap.add_argument("--report", default=None, help="JSON report path")
     ap.add_argument("--weights", default=None, help="evaluate these weights; no labelling or training")
+    ap.add_argument("--objective", choices=("memory", "beta"), default="memory",
+                    help="memory: fewest colors within the byte budget; beta: Eq. ml weighted by beta")
     args = ap.parse_args(argv)
 
     def log(msg):
         print(f"[{time.strftime('%H:%M:%S')}] {msg}", flush=True)
 
+    if args.objective == "beta":
+        return main_beta(args, log)
     if args.weights:
         reg = Regressor.load(args.weights)
         eval_specs = synth.learned_specs(args.eval, args.seed + 1, n_lo=args.eval_n, n_hi=args.eval_n,
@@ -321,6 +412,45 @@ def main(argv=None):
                     "eval_s": time.time() - t2, "loss_history": hist, "train_pick_accuracy": train_acc,
                     "eval_workload": f"n={args.eval_n} q={args.eval_q} p~U[0.1,0.5] budget n*2^U[9,15]"})
     log(json.dumps({k: v for k, v in summary.items() if k != "loss_history"}))
+    if args.report:
+        with open(args.report, "w") as fh:
+            json.dump({"summary": summary, "rows": rows}, fh, indent=1, default=str)
+
+
+def main_beta(args, log):
+    """Label, train and evaluate the beta network (Eq. ml as stated)."""
+    import json
+    import time
+
+    out = args.out if args.out != WEIGHTS_PATH else BETA_WEIGHTS_PATH
+    eval_specs = synth.learned_specs(args.eval, args.seed + 1, n_lo=args.eval_n, n_hi=args.eval_n, qs=(args.eval_q,))
+    if args.weights:
+        reg = Regressor.load(args.weights)
+        summary = summarize_beta(evaluate_beta(reg, eval_specs, seed_base=10 ** 6, log=log))
+        log(json.dumps(summary))
+        return
+    t0 = time.time()
+    feats, labels = label_set_beta(synth.learned_specs(args.train, args.seed), seed_base=0, log=log)
+    t = torch.tensor([targets(d, a) for d, a in labels], dtype=torch.float32, device="cuda")
+    t_label = time.time() - t0
+    log(f"labels done in {t_label:.1f} s: " + json.dumps({f"{d},{a}": labels.count((d, a)) for d, a in set(labels)}))
+    reg = Regressor(seed=args.seed)
+    t1 = time.time()
+    hist = reg.fit(feats, t, args.steps, lr=args.lr, log_every=max(1, args.steps // 20))
+    torch.cuda.synchronize()
+    t_train = time.time() - t1
+    picks = reg.predict(feats)
+    train_acc = sum(1 for (d, a, _), lab in zip(picks, labels) if (d, a) == lab) / len(labels)
+    log(f"trained {args.steps} steps in {t_train:.2f} s; loss {hist[0][1]:.4f} -> {hist[-1][1]:.4f}; "
+        f"train pick accuracy {train_acc:.3f}")
+    reg.save(out, train=args.train, steps=args.steps, seed=args.seed, objective="beta")
+    t2 = time.time()
+    rows = evaluate_beta(reg, eval_specs, seed_base=10 ** 6, log=log)
+    summary = summarize_beta(rows)
+    summary.update({"train_instances": args.train, "label_s": t_label, "train_s": t_train,
+                    "eval_s": time.time() - t2, "train_pick_accuracy": train_acc,
+                    "eval_workload": f"n={args.eval_n} q={args.eval_q} p~U[0.1,0.5], beta in {list(BETAS)}"})
+    log(json.dumps(summary))
     if args.report:
         with open(args.report, "w") as fh:
             json.dump({"summary": summary, "rows": rows}, fh, indent=1, default=str)

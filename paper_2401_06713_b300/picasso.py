@@ -132,6 +132,7 @@ _SIGS = {
     "picasso_save_state": [_vp, _vp, _i64, _pi64],
     "picasso_load_state": [_vp, _vp, _i64],
     "picasso_features": [_vp, _i64, _i32, ctypes.c_uint64, _i64, ctypes.c_double, _vp, _vp, _vp],
+    "picasso_features_beta": [_vp, _i64, _i32, ctypes.c_uint64, _i64, ctypes.c_double, _vp, _vp, _vp],
     "picasso_mlp_param_count": [],
     "picasso_mlp_forward": [_vp, _vp, _i32, _vp, _vp],
     "picasso_mlp_backward": [_vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _i32, _vp, _vp, _vp],
@@ -423,6 +424,18 @@ def features(xz: torch.Tensor, q: int, seed: int, budget_bytes: float, samples: 
     feat = torch.empty(5, dtype=torch.float32, device=xz.device)
     _ck(_lib().picasso_features(_ptr(xz), int(xz.shape[0]), q, seed, samples, float(budget_bytes), _ptr(counts),
                                 _ptr(feat), _stream(stream)), "picasso_features")
+    return counts, feat
+
+
+def features_beta(xz: torch.Tensor, q: int, seed: int, beta: float, samples: int = 1 << 16, stream=None):
+    """Regressor inputs for the weighted objective of Eq. ml (feature 4 =
+    4 beta - 2); see picasso_features_beta."""
+    assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2 * words_per_part(q)
+    xz = xz.contiguous()
+    counts = torch.empty(2, dtype=torch.int64, device=xz.device)
+    feat = torch.empty(5, dtype=torch.float32, device=xz.device)
+    _ck(_lib().picasso_features_beta(_ptr(xz), int(xz.shape[0]), q, seed, samples, float(beta), _ptr(counts),
+                                     _ptr(feat), _stream(stream)), "picasso_features_beta")
     return counts, feat
 
 

@@ -239,3 +239,53 @@ def test_learned_gain_over_defaults(pc):
     assert best_fits >= 6
     assert learned_near >= 0.6 * best_fits and np.mean(ratios) <= 1.05
     assert learned_near > default_near and best_fits >= default_fits
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.3, 1.0])
+def test_features_beta(pc, orc, beta):
+    # Eq. ml's weight in place of the budget term; the other inputs as before
+    chars = synth.pauli_weighted(3000, 40, 0.3, seed=8)
+    xz = pc.pack(torch.from_numpy(chars).cuda())
+    counts, feat = pc.features_beta(xz, 40, seed=9, beta=beta, samples=5000)
+    assert tuple(counts.cpu().tolist()) == orc.feature_counts(chars, 9, 5000)
+    ref = orc.features(chars, 9, 5000, 1e6)
+    got = feat.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got[:4], ref[:4], rtol=1e-6, atol=1e-6)
+    assert got[4] == np.float32(4.0 * beta - 2.0)
+    with pytest.raises(pc.PicassoError):
+        pc.features_beta(xz, 40, seed=9, beta=1.5)
+
+
+def test_beta_objective_labels():
+    # the grid label of Eq. ml: each term over its smallest grid value
+    from paper_2401_06713_b300 import learned
+
+    grid = {(4, 1.0): (100, 50), (8, 1.0): (80, 100), (16, 2.0): (60, 400)}
+    assert learned.beta_label(grid, 0.1) == (4, 1.0)   # bytes dominate
+    assert learned.beta_label(grid, 0.9) == (8, 1.0)
+    assert learned.beta_label(grid, 0.99) == (16, 2.0)  # colors dominate
+    j = learned.beta_objective(grid, 0.5)
+    assert j[(4, 1.0)] == pytest.approx(0.5 * 100 / 60 + 0.5 * 1.0)
+
+
+def test_beta_regressor_gain_over_defaults(pc):
+    """The committed beta network (trained on the GPU on 1,500 instances with
+    n in [1e3, 5e4], nine beta values each) on fresh held-out n = 200,000,
+    q = 56 sets: its pick's objective is the grid's best or close to it for
+    every beta, the paper's normal mode is far from it."""
+    from paper_2401_06713_b300 import learned
+
+    reg = learned.Regressor.load(learned.BETA_WEIGHTS_PATH)
+    specs = synth.learned_specs(4, 4242, n_lo=200000, n_hi=200000, qs=(56,))
+    picks, defaults = [], []
+    for i, spec in enumerate(specs):
+        xz, q, _ = learned.instance(spec)
+        grid = learned.grid_full(xz, q, 7000 + i)
+        for beta in (0.2, 0.5, 0.6, 0.8, 0.9):
+            d, a, _ = learned.predict_beta(reg, xz, q, 7000 + i, beta)
+            j = learned.beta_objective(grid, beta)
+            best = min(j.values())
+            picks.append(j[(d, a)] / best)
+            defaults.append(j[learned.DEFAULT] / best)
+    assert np.mean(picks) <= 1.02 and max(picks) <= 1.1
+    assert np.mean(defaults) > 1.5
