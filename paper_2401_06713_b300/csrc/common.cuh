@@ -172,7 +172,9 @@ __device__ __forceinline__ bool commuteW(const uint64_t* __restrict__ u, const u
 }
 
 constexpr int kMaxQ = 1024;  // qubits of a string: at most 16 words per part
-constexpr size_t kWideMaskSmem = 200 * 1024;  // shared memory of the wide mask pass
+constexpr size_t kWideMaskSmem = 200 * 1024;  // shared memory of the direct wide mask pass
+constexpr int kWideTabSlices = 4;             // words per part the table pass serves (q <= 256)
+constexpr size_t kWideTabSmem = 225 * 1024;   // shared memory of the table pass
 // whether the mask pass for strings of qw > 1 words per part holds a bucket
 // of smax members in shared memory
 bool wide_mask_fits(int64_t smax, int32_t qw);

@@ -657,9 +657,141 @@ __global__ void __launch_bounds__(kMaskThreads) k_bucket_mask_wide(ConflictArgs 
   }
 }
 
+// Wide mask pass with nibble tables, for strings of 2 to kWideTabSlices
+// words per part.  The symplectic form is a sum over 64-qubit slices, so a
+// 32 x 32 anticommutation block is the XOR over slices of the q <= 64
+// lookups: a warp keeps one table set per slice for its current row block
+// (the bit columns of the block's rows, transposed in the warp), and each
+// partner word group costs the lookups of the one-word pass.  Members' words
+// are staged slice-major as (x lo, x hi, z lo, z hi).  Same outputs as the
+// unfused k_bucket_mask.
+template <bool LOWER>
+__global__ void __launch_bounds__(kMaskThreads) k_bucket_mask_wtab(ConflictArgs a, const int64_t* __restrict__ boff,
+                                                                   const int32_t* __restrict__ bmem,
+                                                                   const int64_t* __restrict__ moff, int smax) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int W = a.qw, S = 2 * W;
+  uint8_t* p = smem_raw;
+  uint4* wv4 = (uint4*)p;  // [W][smax]
+  p += align16(sizeof(uint4) * (size_t)W * smax);
+  int32_t* sfl = (int32_t*)p;
+  p += align16(sizeof(int32_t) * smax);
+  int32_t* cnt = (int32_t*)p;
+  p += align16(sizeof(int32_t) * smax);
+  {
+    const uint32_t ad = (uint32_t)__cvta_generic_to_shared(p);
+    p += (256u - (ad & 255u)) & 255u;  // table bases need a zero low byte
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // per warp: W table sets, then the bit columns of one slice [4][32]
+  uint32_t* tab = (uint32_t*)p + (size_t)wid * (W * kTabWords + 128);
+  uint32_t* colw = tab + W * kTabWords;
+  const uint32_t tab_addr = (uint32_t)__cvta_generic_to_shared(tab);
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
+    const int64_t o = boff[b];
+    const int s = (int)(boff[b + 1] - o);
+    if (s == 0) continue;
+    for (int i = threadIdx.x; i < s; i += kMaskThreads) {
+      sfl[i] = bmem[o + i];
+      cnt[i] = 0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < s * W; t += kMaskThreads) {
+      const int i = t / W, k = t - i * W;
+      const int32_t flat = sfl[i];
+      const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
+      const uint64_t x = a.xz[(int64_t)S * v + k], z = a.xz[(int64_t)S * v + W + k];
+      wv4[(size_t)k * smax + i] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
+    }
+    __syncthreads();
+    const int nwb = (s + 31) >> 5;
+    const int nblk = nwb * (nwb + 1) / 2;
+    uint32_t* rmb = a.rmask + moff[b];
+    // a contiguous range of upper-triangle blocks (I, J >= I) per warp, so a
+    // row block's tables serve several partner blocks
+    const int q0 = (int)((int64_t)nblk * wid / kMaskWarps), q1 = (int)((int64_t)nblk * (wid + 1) / kMaskWarps);
+    int I = 0, J = 0;
+    {
+      int rem = q0;
+      while (rem >= nwb - I) {
+        rem -= nwb - I;
+        ++I;
+      }
+      J = I + rem;
+    }
+    int tab_I = -1;
+    for (int q = q0; q < q1; ++q) {
+      if (tab_I != I) {
+        const int r = (I << 5) + lane;
+        for (int k = 0; k < W; ++k) {
+          const uint4 w = r < s ? wv4[(size_t)k * smax + r] : zero4;
+#pragma unroll
+          for (int g = 0; g < 4; ++g) colw[g * 32 + lane] = transpose32(word_of<2>(w, g), lane);
+          build_tables<2>(colw, tab + k * kTabWords, lane);
+        }
+        tab_I = I;
+      }
+      const int ib = I << 5;
+      const int j = (J << 5) + lane;
+      const bool jv = j < s;
+      uint32_t anti = 0u;
+      for (int k = 0; k < W; ++k) {
+        const uint4 cwj = jv ? wv4[(size_t)k * smax + j] : zero4;
+        anti ^= lookup<2>(cwj, tab_addr + (uint32_t)(k * kTabWords * 4));
+      }
+      const int nr = min(32, s - ib);
+      const uint32_t rows_ok = nr >= 32 ? 0xffffffffu : ((1u << nr) - 1u);
+      uint32_t cw = jv ? (~anti & rows_ok) : 0u;
+      // the diagonal block: no self pair; lower rows keep smaller partners
+      if (I == J) cw &= LOWER ? ((1u << lane) - 1u) : ~(1u << lane);
+      rmb[mask_block(LOWER, J, I, nwb) * 32 + lane] = cw;
+      if (cw) atomicAdd(&cnt[j], __popc(cw));
+      if (!LOWER && I != J) {
+        const uint32_t tr = transpose32(cw, lane);
+        rmb[(I * nwb + J) * 32 + lane] = tr;
+        if (tr) atomicAdd(&cnt[ib + lane], __popc(tr));
+      }
+      if (++J == nwb) {
+        ++I;
+        J = I;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
+    __syncthreads();
+  }
+}
+
+size_t wtab_mask_smem_bytes(int64_t smax, int32_t qw) {
+  return align16(sizeof(uint4) * (size_t)qw * smax) + 2 * align16(sizeof(int32_t) * smax) + 256 +
+         sizeof(uint32_t) * (size_t)kMaskWarps * (qw * kTabWords + 128);
+}
+
 size_t wide_mask_smem_bytes(int64_t smax, int32_t qw) { return (size_t)smax * (16 * (size_t)qw + 8); }
 
-bool wide_mask_fits(int64_t smax, int32_t qw) { return wide_mask_smem_bytes(smax, qw) <= kWideMaskSmem; }
+bool wide_mask_fits(int64_t smax, int32_t qw) {
+  if (qw <= kWideTabSlices && wtab_mask_smem_bytes(smax, qw) <= kWideTabSmem) return true;
+  return wide_mask_smem_bytes(smax, qw) <= kWideMaskSmem;
+}
+
+static cudaError_t launch_mask_wtab(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
+                                    const int64_t* moff, int32_t smax, cudaStream_t s) {
+  const size_t bytes = wtab_mask_smem_bytes(smax, a.qw);
+  auto kern = a.lower ? k_bucket_mask_wtab<true> : k_bucket_mask_wtab<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMaskThreads, bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
+  kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, moff, smax);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 template <int WM>
 static cudaError_t launch_mask_wide(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
@@ -686,6 +818,8 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   smax = max(smax, 1);
   if (a.qw > 1) {
+    if (a.qw <= kWideTabSlices && wtab_mask_smem_bytes(smax, a.qw) <= kWideTabSmem)
+      return launch_mask_wtab(a, boff, bmem, moff, smax, s);
     if (a.qw <= 2) return launch_mask_wide<2>(a, boff, bmem, moff, smax, s);
     if (a.qw <= 4) return launch_mask_wide<4>(a, boff, bmem, moff, smax, s);
     if (a.qw <= 8) return launch_mask_wide<8>(a, boff, bmem, moff, smax, s);
