@@ -133,3 +133,25 @@ def test_host_csr_dynamic_order(pc, orc):
         got, r = p.run()
         assert p.stats()["host_csr_rounds"] >= 1
     assert r == rounds and np.array_equal(got.cpu().numpy(), ref)
+
+
+def test_host_csr_batch(pc, orc):
+    # a batch context: rounds whose combined CSR passes the budget keep their
+    # columns in host memory; every set colors as the oracle's own run
+    specs = [(3000, 40, 0.3), (2500, 48, 0.25), (60, 24, 0.5)]
+    sets = [synth.pauli_weighted(n, q, p, seed=3, stream=i) for i, (n, q, p) in enumerate(specs)]
+    offs = [0]
+    for c in sets:
+        offs.append(offs[-1] + len(c))
+    pad = np.zeros((offs[-1], 48), dtype=np.uint8)
+    for k, c in enumerate(sets):
+        pad[offs[k]:offs[k + 1], :c.shape[1]] = c
+    seeds = [41, 42, 43]
+    with pc.Picasso(_xz(pc, pad), 48, set_offsets=offs, seeds=seeds, byte_budget=200_000,
+                    budget_mode="host") as p:
+        got, _ = p.run()
+        got = got.cpu().numpy()
+        assert p.stats()["host_csr_rounds"] >= 1
+    for k, c in enumerate(sets):
+        ref, _, _ = orc.run(c, seeds[k], 1, 8, 2.0)
+        assert np.array_equal(got[offs[k]:offs[k + 1]], ref), k

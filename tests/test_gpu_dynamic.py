@@ -85,3 +85,22 @@ def test_dynamic_fewer_colors_than_static(pc):
             p.run()
             used[color] = p.stats()["colors_used"]
     assert used["dynamic"] < used["auto"]
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 257])
+def test_dynamic_edge_sizes(pc, orc, n):
+    chars = synth.pauli_uniform(n, 6, seed=n)
+    ref, rounds, _ = orc.run(chars, 2, 1, 8, 2.0, colorer="dynamic_par")
+    with pc.Picasso(_xz(pc, chars), 6, seed=2, color="dynamic") as p:
+        got, r = p.run()
+    assert r == rounds and np.array_equal(got.cpu().numpy(), ref)
+
+
+def test_dynamic_all_identity(pc, orc):
+    # every pair commutes: each round's conflict graph joins every two
+    # vertices that share a list color
+    chars = np.zeros((600, 12), dtype=np.uint8)
+    ref, rounds, _ = orc.run(chars, 5, 1, 4, 2.0, colorer="dynamic_par")
+    with pc.Picasso(_xz(pc, chars), 12, seed=5, palette=(1, 4), color="dynamic") as p:
+        got, r = p.run()
+    assert r == rounds and np.array_equal(got.cpu().numpy(), ref)

@@ -163,3 +163,8 @@ def test_features_wide(pc, orc, q):
     chars = synth.pauli_weighted(3000, q, 0.1, seed=q)
     counts, _ = pc.features(_xz(pc, chars), q, seed=9, budget_bytes=1e8, samples=20000)
     assert tuple(counts.cpu().numpy().tolist()) == orc.feature_counts(chars, 9, 20000)
+
+
+@pytest.mark.parametrize("n", [1, 2, 33])
+def test_run_wide_edge_sizes(pc, orc, n):
+    _run_both(pc, orc, synth.pauli_uniform(n, 100, seed=n), 2, 1, 8, 2.0)
