@@ -122,8 +122,8 @@ typedef enum {
 
 /* picasso_run on a single set hands the remaining rounds to one cooperative
  * launch (the small-round engine) once a round has at most 16384 vertices,
- * at most 4096 palette colors and lists of at most 64 colors, under the
- * defaults AUTO / EARLIER / AUTO coloring.  The engine runs the same rounds
+ * at most 4096 palette colors and lists of at most 64 colors, for strings
+ * of at most 64 qubits, under the defaults AUTO / EARLIER / AUTO coloring.  The engine runs the same rounds
  * as picasso_round (same lists, CSR and colors) without a host round trip
  * per round; a round it cannot finish (CSR over its buffer or the byte
  * budget, a bounded wait that ran out) goes back to the per-round path.   */
