@@ -848,7 +848,8 @@ int color_dynamic(Ctx* c) {
   ST(canonical_csr(c));
   uint64_t* mask = nullptr;
   int32_t *state = nullptr, *colorl = nullptr, *ctl = nullptr, *wa = nullptr, *wb = nullptr, *sel = nullptr,
-          *fin = nullptr, *blk = nullptr, *stamp = nullptr, *bstep = nullptr, *parts = nullptr;
+          *fin = nullptr, *blk = nullptr, *stamp = nullptr, *bstep = nullptr, *parts = nullptr,
+          *lng = nullptr;
   void* tmp = nullptr;
   int st = PICASSO_OK;
   auto cleanup = [&]() {
@@ -864,6 +865,7 @@ int color_dynamic(Ctx* c) {
     release(c, &stamp);
     release(c, &bstep);
     release(c, &parts);
+    release(c, &lng);
     release(c, (uint8_t**)&tmp);
   };
 #define TRY(expr)           \
@@ -897,6 +899,7 @@ int color_dynamic(Ctx* c) {
   TRY(alloc(c, &stamp, n));
   TRY(alloc(c, &bstep, n));
   TRY(alloc(c, &parts, n));
+  TRY(alloc(c, &lng, n));
   TRY(alloc(c, &c->state, n));
   TRY(alloc(c, &c->flag, n));
   TRY(alloc(c, &c->pos, n + 1));
@@ -923,6 +926,7 @@ int color_dynamic(Ctx* c) {
   d.stamp = stamp;
   d.bstep = bstep;
   d.parts = parts;
+  d.lng = lng;
   d.ctl = ctl;
   TRYC(launch_dyn_init(d, s));
   TRYC(launch_dyn_all(d, s));

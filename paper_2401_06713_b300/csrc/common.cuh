@@ -477,7 +477,8 @@ struct DynArgs {
   int32_t* stamp;         // [n] last step + 1 the vertex was put on a work list
   int32_t* bstep;         // [n] last step + 1 the vertex was found blocked
   int32_t* parts;         // [n] parts of the vertex's examination finished
-  int32_t* ctl;           // [8] list lengths, sel and fin lengths (by parity), steps
+  int32_t* lng;           // [n] the step's vertices whose row heads decided nothing
+  int32_t* ctl;           // [8] list lengths, sel and fin lengths (by parity), steps, long list
 };
 // masks of full lists, state 0, wa = all vertices, ctl = {n, 0, ...}
 cudaError_t launch_dyn_init(const DynArgs& d, cudaStream_t s);

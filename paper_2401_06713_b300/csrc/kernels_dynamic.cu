@@ -61,29 +61,38 @@ __device__ __forceinline__ void push_next(const DynArgs& d, int32_t v, int32_t s
 }
 
 constexpr int kScanChunks = 4;   // 32-entry chunks of a row scan in flight per warp
-constexpr int kMaxParts = 16;    // warps sharing one vertex's scan or strike
+constexpr int kMaxParts = 16;    // warps sharing one vertex's strike or drain
+constexpr int kMaxLongParts = 64;                  // warps sharing one long row scan
+constexpr int64_t kHeadEntries = 64 * kScanChunks;  // row entries the first pass scans
 
 // Warps per item when `items` items share the grid's nw warps.
-__device__ __forceinline__ int64_t parts_for(int64_t items, int64_t nw) {
+__device__ __forceinline__ int64_t parts_for(int64_t items, int64_t nw, int64_t cap = kMaxParts) {
   if (items >= nw) return 1;
   const int64_t g = nw / items;
-  return g < kMaxParts ? g : kMaxParts;
+  return g < cap ? g : cap;
 }
 
 // Part j of G of examining vertex v at a step (one warp per part).  A vertex
 // is active while its mask is nonzero (colored vertices and emptied lists
-// have mask 0).  The part scans chunks j, j + G, ... of v's rows (chunks of
-// 32 x kScanChunks entries, the next chunk's ids loaded while the current
-// one's masks arrive) for an active neighbour smaller in (size, rank); on
-// finding one it records it in blk[v] (the chunk's largest such neighbour in
-// that order) and marks v blocked for this step (bstep[v] = stamp).  The
-// part that finishes last appends v to sel when no part found a blocker.
+// have mask 0).  The part scans chunks j, j + G, ... of v's row entries from
+// `skip` on, at most `limit` of them (chunks of 32 x kScanChunks entries,
+// the next chunk's ids loaded while the current one's masks arrive), for an
+// active neighbour smaller in (size, rank); on finding one it records it in
+// blk[v] (the chunk's largest such neighbour in that order) and marks v
+// blocked for this step (bstep[v] = stamp).
+//   First pass (G = 1, skip 0, limit kHeadEntries): no blocker and nothing
+//   left to scan makes v a local minimum (to sel); no blocker with entries
+//   left puts v on the long list (lng).
+//   Second pass (the long list, skip kHeadEntries, G parts): the part that
+//   finishes last appends v to sel when no part found a blocker.
 __device__ __forceinline__ void dyn_examine(const DynArgs& d, int32_t v, int64_t j, int64_t G, int lane,
-                                            int32_t stamp, int32_t* slen) {
+                                            int32_t stamp, int32_t* slen, int64_t skip, int64_t limit,
+                                            int32_t* llen) {
   const uint64_t m = __ldcg(d.mask + v);
   if (m == 0) return;  // finished (all parts see the same)
   const int cnt = __popcll(m);
-  const int64_t rs = d.runoff[d.loff[v]], re = d.runoff[d.loff[v + 1]];
+  const int64_t r0 = d.runoff[d.loff[v]], rend = d.runoff[d.loff[v + 1]];
+  const int64_t rs = r0 + skip, re = min(rend, rs + limit);
   constexpr int64_t CH = 32 * kScanChunks;
   bool found = false;
   int32_t u[kScanChunks], un[kScanChunks];
@@ -130,6 +139,15 @@ __device__ __forceinline__ void dyn_examine(const DynArgs& d, int32_t v, int64_t
     for (int k = 0; k < kScanChunks; ++k) u[k] = un[k];
   }
   if (lane != 0) return;
+  if (llen != nullptr) {  // first pass
+    if (!found) {
+      if (re < rend)
+        d.lng[atomicAdd(llen, 1)] = v;
+      else
+        d.sel[atomicAdd(slen, 1)] = v;
+    }
+    return;
+  }
   if (G == 1) {
     if (!found) d.sel[atomicAdd(slen, 1)] = v;
     return;
@@ -191,14 +209,18 @@ __device__ __forceinline__ void dyn_apply(const DynArgs& d, int32_t v, int64_t j
 // other active vertex is still blocked by its recorded neighbour (which is
 // still active, and whose size only shrinks), so the steps take the same
 // local minima as examining every vertex at every step.  Per step:
-//   S  examine the work list: local minima to sel, blocked ones record blk;
+//   S  examine the work list: local minima to sel, blocked ones record blk
+//      (a list longer than a quarter of the grid's warps: a first pass over
+//      each row's head, then, after a barrier, the rows still undecided split
+//      over all warps; a shorter one: several warps per row from the start);
 //   A  the minima take colors and strike them; lists struck empty to fin;
 //      neighbours whose size crossed their blocker's to the next list;
 //   D  the minima's masks to 0; the waiters of each finished vertex (sel and
 //      fin), neighbours w with blk[w] = that vertex, to the next list;
 // with a grid barrier after each.  Short lists spread each item over up to
 // kMaxParts warps.  ctl: [0..1] work list lengths (by step parity), [2..3]
-// sel lengths, [4..5] fin lengths, [6] steps that colored a vertex.  The
+// sel lengths, [4..5] fin lengths, [6] steps that colored a vertex, [7]
+// long list length.  The
 // smallest active vertex is never blocked, so it is on the work list while
 // any vertex is active; every step finishes it, so the list is empty after
 // at most n + 1 steps.
@@ -215,10 +237,24 @@ __global__ void k_dyn_all(DynArgs d) {
     const int32_t stamp = (int32_t)(step + 1);
     const int64_t m = __ldcg(ctl + p);
     if (m == 0) break;
-    // S
-    {
+    constexpr int64_t kAll = (int64_t)1 << 62;
+    if (4 * m > nw) {
+      // S, long work list: first pass, one warp per vertex over its row head
+      for (int64_t i = gw; i < m; i += nw)
+        dyn_examine(d, __ldcg(cur + i), 0, 1, lane, stamp, ctl + 2 + p, 0, kHeadEntries, ctl + 7);
+      grid.sync();
+      // second pass: the rows still undecided, split over the warps
+      const int64_t nl = __ldcg(ctl + 7);
+      if (nl > 0) {
+        const int64_t G = parts_for(nl, nw, kMaxLongParts);
+        for (int64_t w = gw; w < nl * G; w += nw)
+          dyn_examine(d, __ldcg(d.lng + w / G), w % G, G, lane, stamp, ctl + 2 + p, kHeadEntries, kAll, nullptr);
+      }
+    } else {
+      // S, short work list: at least four warps per vertex, whole rows
       const int64_t G = parts_for(m, nw);
-      for (int64_t w = gw; w < m * G; w += nw) dyn_examine(d, __ldcg(cur + w / G), w % G, G, lane, stamp, ctl + 2 + p);
+      for (int64_t w = gw; w < m * G; w += nw)
+        dyn_examine(d, __ldcg(cur + w / G), w % G, G, lane, stamp, ctl + 2 + p, 0, kAll, nullptr);
     }
     grid.sync();
     // A
@@ -248,6 +284,7 @@ __global__ void k_dyn_all(DynArgs d) {
       ctl[p] = 0;          // read by S of this step only
       ctl[2 + 1 - p] = 0;  // the next step's sel and fin
       ctl[4 + 1 - p] = 0;
+      ctl[7] = 0;          // read after the first pass of this step's S only
       if (ns > 0) ctl[6] += 1;
     }
     grid.sync();
