@@ -55,23 +55,68 @@ def workload(n):
 
 
 class Clocks:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """SM clock, power and clock-event reasons sampled while the timed region
+    runs: the driver's NVML library (through ctypes, reads only) every 5 ms
+    from a thread, else nvidia-smi every 50 ms."""
+
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
 
     def __init__(self, index):
         self.index = index
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.rows = []  # (sm_mhz, max_mhz, power_w, reason bits)
+        self.nvml = None
         self.p = None
+        self.f = None
+        self.stop = None
+        self.thread = None
+
+    def _poll(self, lib, h):
+        import ctypes
+
+        clk, mx, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))  # 1 = SM clock
+        try:
+            reasons = lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            reasons = lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0
+                    and lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw)) == 0
+                    and reasons(h, ctypes.byref(rs)) == 0):
+                self.rows.append((float(clk.value), float(mx.value), pw.value / 1000.0, int(rs.value)))
+            self.stop.wait(0.005)
 
     def __enter__(self):
         try:
+            import ctypes
+            import threading
+
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            h = ctypes.c_void_p()
+            if lib.nvmlInit_v2() != 0 or lib.nvmlDeviceGetHandleByIndex_v2(self.index, ctypes.byref(h)) != 0:
+                raise OSError("NVML")
+            self.nvml = lib
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, args=(lib, h), daemon=True)
+            self.thread.start()
+            return self
+        except Exception:
+            self.nvml = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={SMI_FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
         return self
 
     def __exit__(self, *a):
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
+            self.nvml.nvmlShutdown()
         if self.p is not None:
             self.p.terminate()
             try:
@@ -80,24 +125,28 @@ class Clocks:
                 self.p.kill()
 
     def summary(self):
-        self.f.flush()
-        rows = []
-        with open(self.f.name) as fh:
-            for line in fh:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        os.unlink(self.f.name)
+        rows = list(self.rows)
+        source = "nvml, 5 ms"
+        if self.f is not None:
+            source = "nvidia-smi, 50 ms"
+            self.f.flush()
+            with open(self.f.name) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                        bits = sum(v for (_, v), x in zip(self.REASONS, parts[5:9]) if x.lower() == "active")
+                        pw = float(parts[3]) if parts[3].replace(".", "").isdigit() else None
+                        mx = float(parts[2]) if parts[2].replace(".", "").isdigit() else None
+                        rows.append((float(parts[1]), mx, pw, bits))
+            os.unlink(self.f.name)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
-                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+        mx = [r[1] for r in rows if r[1] is not None]
+        pw = [r[2] for r in rows if r[2] is not None]
+        reasons = sorted({name for r in rows for name, bit in self.REASONS if r[3] & bit})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "source": source,
+                "power_w_max": max(pw) if pw else None}
 
 
 def measured_peaks():
