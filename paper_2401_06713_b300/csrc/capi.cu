@@ -13,6 +13,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 using namespace picasso;
@@ -195,6 +197,7 @@ struct Ctx {
   int64_t hcol_cap = 0;
   bool col_host = false;  // c->col points into hcol
   int32_t host_rounds = 0;
+  bool nvtx_open = false;  // an NVTX phase range is pushed
   int64_t* rstart = nullptr;
   uint32_t* rcnt = nullptr;
   double commute_ratio = 0.6;  // nnz / bucket pair bound of the last fused build
@@ -334,10 +337,20 @@ int check(Ctx* c) {
   return PICASSO_OK;
 }
 
-void phase_begin(Ctx* c) { cudaEventRecord(c->ev[0], c->s); }
+// Phase timers: CUDA events on the context's stream, and an NVTX range of
+// the phase's name for profilers (a range left open by an error return is
+// closed by the next phase).
+void phase_begin(Ctx* c, const char* name) {
+  if (c->nvtx_open) nvtxRangePop();
+  nvtxRangePushA(name);
+  c->nvtx_open = true;
+  cudaEventRecord(c->ev[0], c->s);
+}
 
 // Records the end event, waits for it and adds the elapsed time to *acc.
 cudaError_t phase_end(Ctx* c, double* acc) {
+  if (c->nvtx_open) nvtxRangePop();
+  c->nvtx_open = false;
   cudaError_t e = cudaEventRecord(c->ev[1], c->s);
   if (e == cudaSuccess) e = cudaEventSynchronize(c->ev[1]);
   float ms = 0.f;
@@ -1656,7 +1669,7 @@ int picasso_assign_lists(void* ctx, int64_t P, int32_t L, int64_t base) {
   sr.P = P;
   sr.L = L;
   sr.base = base;
-  phase_begin(c);
+  phase_begin(c, "assign");
   ST(assign_round(c));
   CK(phase_end(c, &c->t_assign));
   return PICASSO_OK;
@@ -1668,7 +1681,7 @@ int picasso_build_conflicts(void* ctx, picasso_csr* out) {
   if (!c->assigned) return PICASSO_ERR_STATE;
   free_color(c);
   free_build(c);
-  phase_begin(c);
+  phase_begin(c, "build");
   ST(build_conflicts(c, false));
   CK(phase_end(c, &c->t_build));
   if (out) {
@@ -1685,7 +1698,7 @@ int picasso_color(void* ctx, int64_t* n_colored) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (!c->built) return PICASSO_ERR_STATE;
-  phase_begin(c);
+  phase_begin(c, "color");
   ST(color_round(c));
   CK(phase_end(c, &c->t_color));
   if (n_colored) *n_colored = c->n_colored;
@@ -1696,7 +1709,7 @@ int picasso_carry(void* ctx, int64_t* n_remaining) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
   if (!c->colored_done) return PICASSO_ERR_STATE;
-  phase_begin(c);
+  phase_begin(c, "carry");
   ST(carry_round(c));
   CK(phase_end(c, &c->t_carry));
   c->rounds_done += 1;
@@ -1712,16 +1725,16 @@ int picasso_round(void* ctx, int64_t* n_remaining) {
     return PICASSO_OK;
   }
   plan_round(c);
-  phase_begin(c);
+  phase_begin(c, "assign");
   ST(assign_round(c));
   CK(phase_end(c, &c->t_assign));
   free_color(c);
   free_build(c);
-  phase_begin(c);
+  phase_begin(c, "build");
   ST(build_conflicts(c, true));
   CK(phase_end(c, &c->t_build));
   if (c->chunk_pending) {
-    phase_begin(c);
+    phase_begin(c, "color");
     ST(color_chunked(c));
     CK(phase_end(c, &c->t_color));
   } else {
@@ -1736,7 +1749,7 @@ int picasso_run(void* ctx, int32_t* d_color_out, int32_t* n_rounds) {
   while (c->n > 0) {
     if (c->round > c->cfg.max_rounds) return PICASSO_ERR_INTERNAL;
     if (small_eligible(c)) {
-      phase_begin(c);
+      phase_begin(c, "small");
       ST(run_small(c));
       CK(phase_end(c, &c->t_small));
       continue;
