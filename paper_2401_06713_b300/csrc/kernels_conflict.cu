@@ -210,10 +210,10 @@ __host__ __device__ inline size_t mask_smem_bytes(int smax) {
 // bucket's lower mask blocks (nwb (nwb + 1) / 2 blocks of 32 words).
 __host__ __device__ inline size_t fused_smem_bytes(int smax) {
   const int nwb = (smax + 31) >> 5;
+  // (the next bucket's staging lies in the bit columns and tables:
+  // 24 smax <= 12,288 bytes <= the tables' 16,384)
   return mask_smem_bytes(smax) + align16(sizeof(int32_t) * smax) + align16(sizeof(uint32_t) * smax) +
-         sizeof(uint32_t) * 32 * (size_t)(nwb * (nwb + 1) / 2) +
-         // the other buffer of member words, entry ids and vertex ids
-         align16(sizeof(uint4) * smax) + 2 * align16(sizeof(int32_t) * smax);
+         sizeof(uint32_t) * 32 * (size_t)(nwb * (nwb + 1) / 2);
 }
 
 // Asynchronous global -> shared copies (the next bucket's members).
@@ -355,8 +355,6 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   int32_t* pid = nullptr;
   uint32_t* roff = nullptr;
   uint32_t* mw = nullptr;
-  uint4* w4b = nullptr;
-  int32_t *sflb = nullptr, *pidb = nullptr;
   if (FUSED) {
     pid = (int32_t*)p;
     p += align16(sizeof(int32_t) * smax);
@@ -365,12 +363,6 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     const int nwbm = (smax + 31) >> 5;
     mw = (uint32_t*)p;
     p += sizeof(uint32_t) * 32 * (size_t)(nwbm * (nwbm + 1) / 2);
-    w4b = (uint4*)p;
-    p += align16(sizeof(uint4) * smax);
-    sflb = (int32_t*)p;
-    p += align16(sizeof(int32_t) * smax);
-    pidb = (int32_t*)p;
-    p += align16(sizeof(int32_t) * smax);
   }
   __shared__ unsigned long long base_s;
   __shared__ uint32_t wsum_s[kMaskWarps];
@@ -385,33 +377,28 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
   // fused pass: a bucket's members (words, entry ids, vertex ids, gathered in
-  // slot order beforehand) are copied asynchronously into one of two buffers
-  // while the previous bucket's runs are written
-  auto fetch = [&](int64_t o, int s, uint4* w4x, int32_t* sflx, int32_t* pidx) {
+  // slot order beforehand) are copied asynchronously into a staging area
+  // while the previous bucket's runs are written.  The staging area lies in
+  // the bit columns and tables, which only the mask phase uses: the copy
+  // starts after the mask phase and is moved into place before the next one.
+  static_assert(24 * kFusedMax <= kMaskWarps * kTabWords * 4, "staging must fit in the tables");
+  uint4* w4s = (uint4*)colw;
+  int32_t* sfls = (int32_t*)(w4s + smax);
+  int32_t* pids = sfls + smax;
+  auto fetch = [&](int64_t o, int s) {
     for (int i = threadIdx.x; i < s; i += kMaskThreads) {
-      cp_async16(w4x + i, a.bxz + o + i);
-      cp_async4(sflx + i, bmem + o + i);
-      cp_async4(pidx + i, a.bpid + o + i);
+      cp_async16(w4s + i, a.bxz + o + i);
+      cp_async4(sfls + i, bmem + o + i);
+      cp_async4(pids + i, a.bpid + o + i);
     }
     cp_async_commit();
-  };
-  auto swap_buffers = [&]() {
-    uint4* t4 = w4;
-    w4 = w4b;
-    w4b = t4;
-    int32_t* t = sfl;
-    sfl = sflb;
-    sflb = t;
-    t = pid;
-    pid = pidb;
-    pidb = t;
   };
   int64_t o_nx = 0;
   int s_nx = 0;
   if (FUSED && blockIdx.x < a.P) {
     o_nx = boff[blockIdx.x];
     s_nx = (int)(boff[blockIdx.x + 1] - o_nx);
-    fetch(o_nx, s_nx, w4, sfl, pid);
+    fetch(o_nx, s_nx);
   }
   for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
     int64_t o;
@@ -426,17 +413,21 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       }
       o = o_nx;
       s = s_nx;
-      // w4 / sfl / pid hold this bucket (the last fetch went there)
+      // the staging area holds this bucket (the last fetch went there)
       cp_async_wait_all();
       __syncthreads();
       if (s == 0) {
-        fetch(o2, s2, w4b, sflb, pidb);
-        swap_buffers();
+        fetch(o2, s2);
         o_nx = o2;
         s_nx = s2;
         continue;
       }
-      for (int i = threadIdx.x; i < s; i += kMaskThreads) cnt[i] = 0;
+      for (int i = threadIdx.x; i < s; i += kMaskThreads) {
+        w4[i] = w4s[i];
+        sfl[i] = sfls[i];
+        pid[i] = pids[i];
+        cnt[i] = 0;
+      }
     } else {
       o = boff[b];
       s = (int)(boff[b + 1] - o);
@@ -505,10 +496,10 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
         J = I;
       }
     }
-    // the next bucket's members go to the other buffer while this one's runs
-    // are written
-    if (FUSED) fetch(o2, s2, w4b, sflb, pidb);
     __syncthreads();
+    // the next bucket's members go to the staging area (the bit columns and
+    // tables are done with) while this one's runs are written
+    if (FUSED) fetch(o2, s2);
     for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
     if (FUSED) {
       // run offsets inside the bucket: each thread scans two consecutive rows
@@ -571,7 +562,6 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     }
     __syncthreads();
     if (FUSED) {
-      swap_buffers();
       o_nx = o2;
       s_nx = s2;
     }
