@@ -33,8 +33,8 @@ N_DEFAULT, Q, P_W, NUM, DEN, ALPHA = 1_000_000, 64, 0.25, 1, 16, 1.5
 # DRAM bytes (read + write) per algorithmic byte of the fused build pass
 # (k_bucket_mask<.., fused>: pair tests and CSR runs in one kernel), from one ncu
 # capture of round 1 of the n = 200,000 case of this workload (the bench's
-# launches are too large to capture): 1.494 GB measured / 1.337 GB algorithmic.
-FUSED_DRAM_PER_ALG_BYTE = 1.117
+# launches are too large to capture): 1.496 GB measured / 1.337 GB algorithmic.
+FUSED_DRAM_PER_ALG_BYTE = 1.119
 METRIC = "pair tests/s (conflict build) and colored strings/s at n=1M; colors, peak bytes"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
