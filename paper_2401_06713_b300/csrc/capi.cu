@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -1603,6 +1604,18 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
 }
 
 }  // namespace
+
+namespace picasso {
+int64_t debug_grid(int64_t blocks) {
+  static const int64_t div = [] {
+    const char* e = std::getenv("PICASSO_GRID_DIVISOR");
+    const long long d = e ? std::atoll(e) : 1;
+    return (int64_t)(d > 1 ? d : 1);
+  }();
+  const int64_t b = blocks / div;
+  return b > 0 ? b : 1;
+}
+}  // namespace picasso
 
 extern "C" {
 

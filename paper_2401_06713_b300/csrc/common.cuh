@@ -200,6 +200,11 @@ __device__ __forceinline__ int set_of(const int64_t* __restrict__ soff, int nset
 
 // Process-wide launch counter (capi.cu); every launcher adds its launches.
 void count_launches(int k);
+// Grid of the persistent and grid-stride kernels: the launcher's choice,
+// divided by the PICASSO_GRID_DIVISOR environment variable when it is set
+// (a debugging aid: every such kernel gives the same output at any grid
+// size, so runs at different divisors must agree bit for bit).
+int64_t debug_grid(int64_t blocks);
 
 // ---------------------------------------------------------------------------
 // Launchers (host functions defined in the kernel .cu files).

@@ -302,6 +302,7 @@ cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32
   int64_t blocks = (int64_t)per_sm * sms;
   const int64_t want = (a.n + 7) / 8;
   if (want < blocks) blocks = want > 0 ? want : 1;
+  blocks = debug_grid(blocks);
   ColorArgs args = a;
   void* params[] = {(void*)&args, (void*)&order, (void*)&err};
   e = cudaLaunchCooperativeKernel((const void*)k_color_ordered, dim3((unsigned)blocks), dim3(256), params, 0, s);
@@ -320,6 +321,7 @@ cudaError_t launch_color_all(const ColorArgs& a, int32_t* wa, int32_t* wb, int32
   int64_t blocks = (int64_t)per_sm * sms;
   const int64_t want = (a.n + 7) / 8;  // one warp per vertex at most
   if (want < blocks) blocks = want > 0 ? want : 1;
+  blocks = debug_grid(blocks);
   ColorArgs args = a;
   int32_t max_sweeps = (int32_t)(a.n + 4 < 0x7fffffff ? a.n + 4 : 0x7fffffff);
   void* params[] = {(void*)&args, (void*)&wa, (void*)&wb, (void*)&wact, (void*)&ctl, (void*)&max_sweeps};

@@ -777,7 +777,7 @@ static cudaError_t launch_mask_wtab(const ConflictArgs& a, const int64_t* boff, 
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
+  const int64_t blocks = debug_grid(std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1)));
   kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, moff, smax);
   count_launches(1);
   return cudaGetLastError();
@@ -797,7 +797,7 @@ static cudaError_t launch_mask_wide(const ConflictArgs& a, const int64_t* boff, 
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
+  const int64_t blocks = debug_grid(std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1)));
   kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, moff, smax);
   count_launches(1);
   return cudaGetLastError();
@@ -827,7 +827,7 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
+  const int64_t blocks = debug_grid(std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1)));
   kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, moff, smax);
   count_launches(1);
   return cudaGetLastError();
@@ -867,7 +867,7 @@ cudaError_t launch_bucket_fused(const ConflictArgs& a, const int64_t* boff, cons
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t blocks = std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1));
+  const int64_t blocks = debug_grid(std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1)));
   kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, nullptr, smax);
   count_launches(1);
   return cudaGetLastError();
@@ -1016,7 +1016,7 @@ cudaError_t launch_bucket_emit(const ConflictArgs& a, const int64_t* boff, const
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_bucket_emit<<<(unsigned)(sms * max(per_sm, 1)), kEmitThreads, 0, s>>>(a, boff, bmem, moff, jboff, ibkt,
+  k_bucket_emit<<<(unsigned)debug_grid(sms * max(per_sm, 1)), kEmitThreads, 0, s>>>(a, boff, bmem, moff, jboff, ibkt,
                                                                          counter, lo, hi, base);
   count_launches(1);
   return cudaGetLastError();
@@ -1117,7 +1117,7 @@ cudaError_t launch_allpairs(const ConflictArgs& a, bool fill, cudaStream_t s) {
   auto kern = fill ? k_allpairs<true> : k_allpairs<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = std::min<int64_t>((a.n + kApWarps - 1) / kApWarps, 148 * 8);
+  const int64_t blocks = debug_grid(std::min<int64_t>((a.n + kApWarps - 1) / kApWarps, 148 * 8));
   kern<<<(unsigned)blocks, kApWarps * 32, bytes, s>>>(a);
   count_launches(1);
   return cudaGetLastError();

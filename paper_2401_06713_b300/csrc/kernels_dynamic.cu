@@ -332,6 +332,7 @@ cudaError_t launch_dyn_all(const DynArgs& d, cudaStream_t s) {
   int64_t blocks = (int64_t)std::min(per_sm, 4) * sms;
   const int64_t want = (d.n + 7) / 8;
   if (want < blocks) blocks = want > 0 ? want : 1;
+  blocks = debug_grid(blocks);
   DynArgs args = d;
   void* params[] = {(void*)&args};
   e = cudaLaunchCooperativeKernel((const void*)k_dyn_all, dim3((unsigned)blocks), dim3(256), params, 0, s);

@@ -457,6 +457,7 @@ cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, cudaStream_t s
   // 16 warps per SM for the latency-bound phases
   int blocks = std::min(per_sm, kSmallBlocksPerSm) * sms;
   blocks = std::min(blocks, part_cap);
+  blocks = (int)debug_grid(blocks);
   SmallArgs args = a;
   void* params[] = {(void*)&args};
   e = cudaLaunchCooperativeKernel((const void*)k_small_rounds, dim3((unsigned)blocks), dim3(kSmallThreads), params,
