@@ -345,6 +345,7 @@ def run_gpu(args):
 
     batch = None if args.no_batch else bench_batch(rank)
     learned_form = None if args.no_learned else bench_learned(rank)
+    learned_beta = None if args.no_learned else bench_learned_beta(rank)
     chunked = None if args.no_chunked else bench_chunked(rank, codes, colors_np)
     host_csr = None if args.no_host else bench_host(rank, codes, colors_np)
     dynamic = None if args.no_dynamic else bench_dynamic(rank, codes, st)
@@ -370,7 +371,7 @@ def run_gpu(args):
         "pair_tests_per_s": pair_rate, "colors": int(len(np.unique(colors_np))),
         "colors_sum_P": st["colors_used"], "rounds": rounds,
         "peak_bytes": st["peak_bytes"], "breakdown_ms_per_step": per_step,
-        "roofline": roofline, "roofline_pairs": roofline_pairs, "chunked": chunked, "host_csr": host_csr, "dynamic": dynamic, "wide": wide, "cpu_baseline": cpu, "batch": batch, "learned": learned_form,
+        "roofline": roofline, "roofline_pairs": roofline_pairs, "chunked": chunked, "host_csr": host_csr, "dynamic": dynamic, "wide": wide, "cpu_baseline": cpu, "batch": batch, "learned": learned_form, "learned_beta": learned_beta,
         "e2e": {"value": world * n / (ms_e2e / args.steps / 1e3), "unit": "strings/s",
                 "h2d_bytes_per_step": n * Q, "d2h_bytes_per_step": 4 * n,
                 "overlap": "each step's upload on a copy stream during the previous step"},
@@ -595,6 +596,26 @@ def bench_learned(rank, count=16):
             "default_mean_peak_over_budget": float(np.mean([r[5] for r in rows])),
             "learned_ms_per_set": 1e3 * t_learned / count,
             "learned_mean_attempts": float(np.mean([r[6] for r in rows]))}
+
+
+def bench_learned_beta(rank, count=4):
+    """The beta network (Eq. ml as stated) on fresh held-out n = 200,000,
+    q = 56 sets: for each set and each beta in 0.1 .. 0.9, the objective of
+    its pick against the grid's best and against the paper's normal mode."""
+    import time
+
+    from paper_2401_06713_b300 import learned, synth
+
+    reg = learned.Regressor.load(learned.BETA_WEIGHTS_PATH)
+    specs = synth.learned_specs(count, 95001 + rank, n_lo=200000, n_hi=200000, qs=(56,))
+    t0 = time.perf_counter()
+    rows = learned.evaluate_beta(reg, specs, seed_base=3 * 10 ** 6)
+    summary = learned.summarize_beta(rows)
+    return {"workload": f"{count} held-out sets x 9 betas, n=200000 q=56 p~U[0.1,0.5]",
+            "cases": summary["cases"], "picked_best": summary["learned"]["picked_best"],
+            "mean_objective_over_best": summary["learned"]["mean_objective_over_best"],
+            "default_mean_objective_over_best": summary["default"]["mean_objective_over_best"],
+            "wall_s": time.perf_counter() - t0}
 
 
 def round_sizes_from(colors, st):
