@@ -48,6 +48,25 @@ def dist_env():
     return rank, world, local
 
 
+def allmax(x, world, device):
+    """Max of x over the ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms_per_step):
+    """Units all ranks processed per second: every rank colors its own set of
+    units_per_rank strings per step (weak scaling), the step time is the max
+    over ranks."""
+    return world * units_per_rank / (ms_per_step / 1e3)
+
+
 def workload(n):
     return {"workload": f"picasso n={n} q={Q} p={P_W} P=n/{DEN} alpha={ALPHA}", "n": n, "q": Q,
             "weight_p": P_W, "palette": f"{NUM}/{DEN}", "alpha": ALPHA, "seed": "rank",
@@ -289,17 +308,8 @@ def run_gpu(args):
     barrier()
     ms_e2e = e0.elapsed_time(e1)
 
-    def allmax(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms = allmax(ms)
-    ms_e2e = allmax(ms_e2e)
+    ms = allmax(ms, world, "cuda")
+    ms_e2e = allmax(ms_e2e, world, "cuda")
     colors_np = colors.cpu().numpy()
     assert (colors_np >= 0).all(), "uncolored vertices after a full run"
     st = stats[-1]
@@ -307,7 +317,7 @@ def run_gpu(args):
     per_step = {k: st[k] for k in ("t_assign_ms", "t_build_ms", "t_color_ms", "t_carry_ms", "t_pairs_ms",
                                    "t_emit_ms", "t_small_ms", "small_rounds", "small_stops")}
     steps_ms = ms / args.steps
-    value = world * n / (steps_ms / 1e3)
+    value = whole_job_rate(n, world, steps_ms)
     # the small-round engine's time includes its coloring: counted as build
     # time here, which understates the pair rate
     pair_rate = st["logical_pairs"] / ((st["t_build_ms"] + st["t_small_ms"]) / 1e3)
@@ -372,7 +382,7 @@ def run_gpu(args):
         "colors_sum_P": st["colors_used"], "rounds": rounds,
         "peak_bytes": st["peak_bytes"], "breakdown_ms_per_step": per_step,
         "roofline": roofline, "roofline_pairs": roofline_pairs, "chunked": chunked, "host_csr": host_csr, "dynamic": dynamic, "wide": wide, "cpu_baseline": cpu, "batch": batch, "learned": learned_form, "learned_beta": learned_beta,
-        "e2e": {"value": world * n / (ms_e2e / args.steps / 1e3), "unit": "strings/s",
+        "e2e": {"value": whole_job_rate(n, world, ms_e2e / args.steps), "unit": "strings/s",
                 "h2d_bytes_per_step": n * Q, "d2h_bytes_per_step": 4 * n,
                 "overlap": "each step's upload on a copy stream during the previous step"},
         "gpu_launches": launches, "clocks": clocks, "wall_s": t_wall,
