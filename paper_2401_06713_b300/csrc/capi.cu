@@ -606,8 +606,16 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
     TRYC(cudaMemsetAsync(bcursor, 0, sizeof(uint32_t) * P, s));
     TRYC(launch_bucket_fill(c->lists, E, boff, bcursor, bmem, s));
     release(c, &bcursor);
-    TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, (int32_t)smax, s));
-    if (a.lower && c->cfg.byte_budget == 0 && smax <= kFusedMax && c->qw == 1) {
+    const bool fused = a.lower && c->cfg.byte_budget == 0 && smax <= kFusedMax && c->qw == 1;
+    if (fused) {
+      // sorted buckets, and the members' words and vertex ids in slot order
+      TRY(alloc(c, &bxz, E));
+      TRY(alloc(c, &bpid, E));
+      TRYC(launch_bucket_sort_gather(boff, P, bmem, (int32_t)smax, a, bxz, bpid, s));
+    } else {
+      TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, (int32_t)smax, s));
+    }
+    if (fused) {
       // fused mask + emit: the runs of a bucket go to one region claimed from
       // a cursor.  The column buffer is sized from the bucket pair bound and
       // the last fused build's commuting ratio; if the runs need more, the
@@ -619,9 +627,6 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
       // the cursor: the context's error block, words 2..3 (8-byte aligned)
       unsigned long long* cur = reinterpret_cast<unsigned long long*>(c->d_err + 2);
       TRY(alloc(c, &c->rstart, E));
-      TRY(alloc(c, &bxz, E));
-      TRY(alloc(c, &bpid, E));
-      TRYC(launch_bucket_gather(a, bmem, bxz, bpid, s));
       a.bxz = bxz;
       a.bpid = bpid;
       TRY(alloc(c, &c->col, cap));

@@ -68,16 +68,23 @@ cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* b
 // l*E .. l*E+E-1, E = m/32 for the padded size m); partners closer than E
 // are in the same lane, farther ones are exchanged by shuffles.  Larger
 // buckets: one CTA per bucket, the same network in shared memory.
+// GATHER (the fused pass, buckets of at most kWarpSortMax members): the
+// same warp then writes the sorted members' words and vertex ids in slot
+// order (bxz, bpid), as k_bucket_gather would.
+template <bool GATHER>
 __global__ void __launch_bounds__(256) k_bucket_sort_warp(const int64_t* __restrict__ boff, int64_t P,
-                                                          int32_t* __restrict__ bmem) {
+                                                          int32_t* __restrict__ bmem, ConflictArgs a,
+                                                          uint4* __restrict__ bxz, int32_t* __restrict__ bpid) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < P; b += gw) {
     const int64_t o = boff[b];
     const int s = (int)(boff[b + 1] - o);
-    if (s <= 1 || s > kWarpSortMax) continue;
+    if (s > kWarpSortMax) continue;
     int32_t* p = bmem + o;
-    if (s <= 32)
+    if (s <= 1)
+      ;
+    else if (s <= 32)
       warp_sort_bucket<1>(p, s, lane);
     else if (s <= 64)
       warp_sort_bucket<2>(p, s, lane);
@@ -87,6 +94,16 @@ __global__ void __launch_bounds__(256) k_bucket_sort_warp(const int64_t* __restr
       warp_sort_bucket<8>(p, s, lane);
     else
       warp_sort_bucket<16>(p, s, lane);
+    if (GATHER) {
+      __syncwarp();
+      for (int i = lane; i < s; i += 32) {
+        const int32_t flat = p[i];
+        const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
+        const uint64_t x = a.xz[2 * v], z = a.xz[2 * v + 1];
+        bxz[o + i] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
+        bpid[o + i] = (int32_t)v;
+      }
+    }
   }
 }
 
@@ -130,13 +147,23 @@ cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, in
                                cudaStream_t s) {
   if (P <= 0) return cudaSuccess;
   const unsigned wblocks = (unsigned)std::min<int64_t>((P + 7) / 8, 148 * 16);
-  k_bucket_sort_warp<<<wblocks, 256, 0, s>>>(boff, P, bmem);
+  k_bucket_sort_warp<false><<<wblocks, 256, 0, s>>>(boff, P, bmem, ConflictArgs{}, nullptr, nullptr);
   count_launches(1);
   if (smax > kWarpSortMax) {
     const unsigned blocks = (unsigned)std::min<int64_t>(P, 148 * 8);
     k_bucket_sort<<<blocks, 256, 0, s>>>(boff, P, bmem, err);
     count_launches(1);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_sort_gather(const int64_t* boff, int64_t P, int32_t* bmem, int32_t smax,
+                                      const ConflictArgs& a, uint4* bxz, int32_t* bpid, cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  if (smax > kWarpSortMax) return cudaErrorInvalidValue;
+  const unsigned wblocks = (unsigned)std::min<int64_t>((P + 7) / 8, 148 * 16);
+  k_bucket_sort_warp<true><<<wblocks, 256, 0, s>>>(boff, P, bmem, a, bxz, bpid);
+  count_launches(1);
   return cudaGetLastError();
 }
 
