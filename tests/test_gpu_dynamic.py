@@ -104,3 +104,54 @@ def test_dynamic_all_identity(pc, orc):
     with pc.Picasso(_xz(pc, chars), 12, seed=5, palette=(1, 4), color="dynamic") as p:
         got, r = p.run()
     assert r == rounds and np.array_equal(got.cpu().numpy(), ref)
+
+
+def test_dynamic_full_size_n1m(pc, orc):
+    """The n = 1M throughput workload in the dynamic order, checked through
+    properties that hold at any size (the rule's result at a vertex depends
+    on the whole round, so no row-local replay): round 1 at sampled
+    vertices, every colored one holds a color of its list that no conflict
+    neighbour holds, and every uncolored one had each list color taken by a
+    conflict neighbour holding it (Alg. 2 leaves a vertex only when its list
+    is empty); the whole run colors everything, each class a clique."""
+    n, q, seed = 1_000_000, 64, 0
+    chars = synth.pauli_weighted(n, q, 0.25, seed=seed)
+    enc = orc.encode3(chars)
+    P, L = orc.round_params(n, 1, 16, 1.5)
+    prio = orc.priorities(seed, 1, range(n)).astype(np.int64)
+    order = np.lexsort((np.arange(n), prio))
+    lists_r = orc.draw_lists(seed, 1, order, P, L, 0)
+    with pc.Picasso(_xz(pc, chars), q, seed=seed, palette=(1, 16), alpha=1.5, color="dynamic") as p:
+        p.assign_lists(P, L, 0)
+        p.build_conflicts()
+        p.color()
+        c1 = p.colors().cpu().numpy()
+        rng = np.random.default_rng(5)
+        ranks = np.arange(n)
+        colored = ranks[c1[order] >= 0]
+        failed = ranks[c1[order] < 0]
+        rows = np.sort(np.concatenate([rng.choice(colored, 12, replace=False), rng.choice(failed, 12, replace=False)]))
+        _, ref_rows = orc.conflict_rows(enc[order], lists_r, rows)
+        for i, u in enumerate(rows):
+            nb = np.asarray(ref_rows[i], dtype=np.int64)
+            nb_colors = c1[order[nb]]
+            cu = int(c1[order[u]])
+            if cu >= 0:
+                assert cu in lists_r[u] and not (nb_colors == cu).any()
+            else:
+                for c in lists_r[u]:
+                    assert (nb_colors == c).any(), (u, c)
+        p.carry()
+        colors, _ = p.run()
+        colors = colors.cpu().numpy()
+    assert (colors >= 0).all()
+    order_c = np.argsort(colors, kind="stable")
+    cs = colors[order_c]
+    d = 1
+    while True:
+        same = cs[d:] == cs[:-d]
+        if not same.any():
+            break
+        a, b = order_c[:-d][same], order_c[d:][same]
+        assert ((np.bitwise_count(np.bitwise_and(enc[a], enc[b])).sum(axis=1) % 2) == 1).all()
+        d += 1
