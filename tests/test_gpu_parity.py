@@ -333,3 +333,9 @@ def test_full_size_n100k(pc, orc):
 def test_full_size_n1m(pc, orc):
     # n=1,000,000, q=64, p=0.25, P=n/16, alpha=1.5 (the throughput workload)
     _full_size(pc, orc, 1_000_000, 64, 0.25, 1, 16, 1.5, 0, 24)
+
+
+def test_full_size_wide_n200k(pc, orc):
+    # n=200,000 strings of 128 qubits (two words per part, the table pass),
+    # p=0.125, P=n/16, alpha=1.5
+    _full_size(pc, orc, 200_000, 128, 0.125, 1, 16, 1.5, 3, 40)
