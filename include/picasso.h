@@ -123,7 +123,7 @@ typedef enum {
 /* picasso_run on a single set hands the remaining rounds to one cooperative
  * launch (the small-round engine) once a round has at most 16384 vertices,
  * at most 4096 palette colors and lists of at most 64 colors, for strings
- * of at most 64 qubits, under the defaults AUTO / EARLIER / AUTO coloring.  The engine runs the same rounds
+ * of at most 128 qubits, under the defaults AUTO / EARLIER / AUTO coloring.  The engine runs the same rounds
  * as picasso_round (same lists, CSR and colors) without a host round trip
  * per round; a round it cannot finish (CSR over its buffer or the byte
  * budget, a bounded wait that ran out) goes back to the per-round path.   */
@@ -232,8 +232,8 @@ int picasso_pack(const uint8_t* d_codes, int64_t n, int32_t q, uint64_t* d_xz,
  * cudaStream_t (NULL = legacy default stream).  Round 1 starts with V_1 =
  * all n strings, all colors -1.  Strings of q > 64 (Sec. VII's larger
  * systems) take the same rounds; their conflict pass forms each pair's
- * symplectic product over all words (no fused run writes), and the
- * small-round engine is not used for them.                                 */
+ * symplectic product over all words (no fused run writes); the small-round
+ * engine takes strings of up to 128 qubits.                                */
 int picasso_init(void** ctx, const picasso_config* cfg, const uint64_t* d_xz,
                  int64_t n, int32_t q, void* stream);
 

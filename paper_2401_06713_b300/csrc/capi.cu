@@ -1121,7 +1121,7 @@ int carry_round(Ctx* c) {
 // Whether picasso_run hands the remaining rounds to the small-round engine.
 bool small_eligible(const Ctx* c) {
   const picasso_config& cfg = c->cfg;
-  if (c->n < 1 || c->n > kSmallRoundsMax || cfg.small_engine != PICASSO_SMALL_AUTO || c->qw != 1) return false;
+  if (c->n < 1 || c->n > kSmallRoundsMax || cfg.small_engine != PICASSO_SMALL_AUTO || c->qw > 2) return false;
   if (cfg.conflict_algo != PICASSO_CONFLICT_AUTO || cfg.color_algo != PICASSO_COLOR_AUTO ||
       cfg.csr_form != PICASSO_CSR_EARLIER)
     return false;
@@ -1255,7 +1255,7 @@ int run_small(Ctx* c) {
   TRY(alloc(c, &perm, n0));
   TRY(alloc(c, &gid_r, n0));
   TRY(alloc(c, &sid, n0));
-  TRY(alloc(c, &xz_r, 2 * n0));
+  TRY(alloc(c, &xz_r, 2 * (int64_t)c->qw * n0));
   TRY(alloc(c, &lists, E0));
   TRY(alloc(c, &ent_v, E0));
   TRY(alloc(c, &loff, n0 + 1));
@@ -1272,7 +1272,7 @@ int run_small(Ctx* c) {
   TRY(alloc(c, &boff, P0 + 1));
   TRY(alloc(c, &bmem, E0));
   TRY(alloc(c, &brank, E0));
-  TRY(alloc(c, &bxz, 2 * E0));
+  TRY(alloc(c, &bxz, 2 * (int64_t)c->qw * E0));
   TRY(alloc(c, &bitems, P0));
   TRY(alloc(c, &iboff, P0 + 1));
   TRY(alloc(c, &ibkt, E0 / 32 + P0 + 1));
@@ -1312,6 +1312,7 @@ int run_small(Ctx* c) {
   a.gid_r = gid_r;
   a.sid = sid;
   a.xz_r = xz_r;
+  a.qw = c->qw;
   a.lists = lists;
   a.ent_v = ent_v;
   a.loff = loff;

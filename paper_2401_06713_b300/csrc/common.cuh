@@ -410,6 +410,7 @@ struct SmallArgs {
   int64_t n0;             // vertices when the engine starts
   int32_t round0;         // number of the first round it runs
   int32_t max_rounds;     // last round number it may run
+  int32_t qw;             // 64-bit words per part of a string (1 or 2)
   int32_t nsets;          // sets of the context
   const int64_t* soff;    // [nsets + 1] global id offsets of the sets
   const uint64_t* sseed;  // [nsets] Philox keys

@@ -44,8 +44,10 @@ namespace {
 constexpr int kSmallThreads = 256;
 constexpr int kSmallWarps = kSmallThreads / 32;
 constexpr int kSmallBlocksPerSm = 2;
-// dynamic shared memory of one warp: a bucket's member words and ranks
-constexpr int kWarpSmemBytes = kSmallBucketCap * (16 + 4);
+// dynamic shared memory of one warp: a bucket's member words (W words per
+// part) and ranks
+template <int W>
+__host__ __device__ constexpr int warp_smem_bytes() { return kSmallBucketCap * (16 * W + 4); }
 
 // Sum of x over the block (every thread gets it).  sm: 32 words.
 __device__ __forceinline__ int64_t block_sum(int64_t x, int64_t* sm) {
@@ -166,7 +168,7 @@ __device__ void set_prefixes(const SmallArgs& a, int64_t* sm) {
 // stages a bucket's members once, as far as its items reach.  Count (FILL
 // false): cnt[e_i] = the commuting ones; fill (FILL true): their ranks at
 // col[runoff[e_i]..], ascending.
-template <bool FILL>
+template <int W, bool FILL>
 __device__ void bucket_runs(const SmallArgs& a, int32_t* R, uint64_t* X, int lane, int64_t gwarp, int64_t nwarps) {
   const int64_t nitems = __ldcg(a.ctl + 8);
   const int64_t per = (nitems + nwarps - 1) / nwarps;
@@ -187,8 +189,8 @@ __device__ void bucket_runs(const SmallArgs& a, int32_t* R, uint64_t* X, int lan
       __syncwarp();
       for (int i = staged + lane; i < need; i += 32) {
         R[i] = a.brank[b0 + i];
-        X[2 * i] = a.bxz[2 * (b0 + i)];
-        X[2 * i + 1] = a.bxz[2 * (b0 + i) + 1];
+#pragma unroll
+        for (int k = 0; k < 2 * W; ++k) X[2 * W * i + k] = a.bxz[2 * W * (b0 + i) + k];
       }
       staged = need;
       __syncwarp();
@@ -199,38 +201,63 @@ __device__ void bucket_runs(const SmallArgs& a, int32_t* R, uint64_t* X, int lan
     // halves.
     const int i = i0 + lane;
     const int jend = need;
-    const uint4* X4 = reinterpret_cast<const uint4*>(X);
-    const uint4 wi = X4[min(i, s - 1)];
     const bool active = i < s;
     const int ilim = active ? i : 0;  // lanes past the bucket test nothing
-    if (!FILL) {
-      uint32_t anti = 0;
+    if constexpr (W == 1) {
+      const uint4* X4 = reinterpret_cast<const uint4*>(X);
+      const uint4 wi = X4[min(i, s - 1)];
+      if (!FILL) {
+        uint32_t anti = 0;
 #pragma unroll 4
-      for (int j = 0; j < jend; ++j) {
-        const uint4 w = X4[j];
-        const uint32_t d = (wi.x & w.z) ^ (wi.z & w.x) ^ (wi.y & w.w) ^ (wi.w & w.y);
-        anti += (j < ilim) ? (__popc(d) & 1u) : 0u;
+        for (int j = 0; j < jend; ++j) {
+          const uint4 w = X4[j];
+          const uint32_t d = (wi.x & w.z) ^ (wi.z & w.x) ^ (wi.y & w.w) ^ (wi.w & w.y);
+          anti += (j < ilim) ? (__popc(d) & 1u) : 0u;
+        }
+        if (active) a.cnt[a.bmem[b0 + i]] = (uint32_t)i - anti;
+      } else {
+        int64_t o = active ? a.runoff[a.bmem[b0 + i]] : 0;
+        for (int j = 0; j < jend; ++j) {
+          const uint4 w = X4[j];
+          const uint32_t d = (wi.x & w.z) ^ (wi.z & w.x) ^ (wi.y & w.w) ^ (wi.w & w.y);
+          if (j < ilim && (__popc(d) & 1u) == 0u) a.col[o++] = R[j];
+        }
       }
-      if (active) a.cnt[a.bmem[b0 + i]] = (uint32_t)i - anti;
     } else {
-      int64_t o = active ? a.runoff[a.bmem[b0 + i]] : 0;
-      for (int j = 0; j < jend; ++j) {
-        const uint4 w = X4[j];
-        const uint32_t d = (wi.x & w.z) ^ (wi.z & w.x) ^ (wi.y & w.w) ^ (wi.w & w.y);
-        if (j < ilim && (__popc(d) & 1u) == 0u) a.col[o++] = R[j];
+      // W words per part: the member's 32-bit halves, x part then z part
+      const uint32_t* X32 = reinterpret_cast<const uint32_t*>(X);
+      uint32_t wi[4 * W];
+#pragma unroll
+      for (int k = 0; k < 4 * W; ++k) wi[k] = X32[4 * W * min(i, s - 1) + k];
+      auto odd = [&](int j) {
+        const uint32_t* w = X32 + 4 * W * j;
+        uint32_t d = 0u;
+#pragma unroll
+        for (int h = 0; h < 2 * W; ++h) d ^= (wi[h] & w[2 * W + h]) ^ (wi[2 * W + h] & w[h]);
+        return __popc(d) & 1u;
+      };
+      if (!FILL) {
+        uint32_t anti = 0;
+        for (int j = 0; j < jend; ++j) anti += (j < ilim) ? odd(j) : 0u;
+        if (active) a.cnt[a.bmem[b0 + i]] = (uint32_t)i - anti;
+      } else {
+        int64_t o = active ? a.runoff[a.bmem[b0 + i]] : 0;
+        for (int j = 0; j < jend; ++j)
+          if (j < ilim && odd(j) == 0u) a.col[o++] = R[j];
       }
     }
   }
   __syncwarp();
 }
 
+template <int W>
 __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_rounds(SmallArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ int64_t scan_s[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint64_t* Xw = reinterpret_cast<uint64_t*>(smem_dyn + (size_t)wid * kWarpSmemBytes);
-  int32_t* Rw = reinterpret_cast<int32_t*>(Xw + 2 * kSmallBucketCap);
+  uint64_t* Xw = reinterpret_cast<uint64_t*>(smem_dyn + (size_t)wid * warp_smem_bytes<W>());
+  int32_t* Rw = reinterpret_cast<int32_t*>(Xw + 2 * W * kSmallBucketCap);
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
@@ -285,8 +312,8 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         a.perm[rk] = (int32_t)i;
         a.gid_r[rk] = g;
         a.sid[rk] = k;
-        a.xz_r[2 * rk] = a.xz[2 * (int64_t)g];
-        a.xz_r[2 * rk + 1] = a.xz[2 * (int64_t)g + 1];
+#pragma unroll
+        for (int k = 0; k < 2 * W; ++k) a.xz_r[2 * W * rk + k] = a.xz[2 * W * (int64_t)g + k];
       }
     }
     grid.sync();
@@ -345,13 +372,13 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       for (int i = lane; i < sc; i += 32) {
         const int32_t r = a.ent_v[a.bmem[b0 + i]];
         a.brank[b0 + i] = r;
-        a.bxz[2 * (b0 + i)] = a.xz_r[2 * (int64_t)r];
-        a.bxz[2 * (b0 + i) + 1] = a.xz_r[2 * (int64_t)r + 1];
+#pragma unroll
+        for (int k = 0; k < 2 * W; ++k) a.bxz[2 * W * (b0 + i) + k] = a.xz_r[2 * W * (int64_t)r + k];
       }
     }
     grid.sync();
 
-    bucket_runs<false>(a, Rw, Xw, lane, gwarp, nwarps);
+    bucket_runs<W, false>(a, Rw, Xw, lane, gwarp, nwarps);
     grid.sync();
     grid_scan(grid, a.cnt, E, a.runoff, a.part, scan_s);
     grid.sync();
@@ -364,7 +391,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       }
       if (gtid == 0) a.ctl[6] += nnz;
     }
-    bucket_runs<true>(a, Rw, Xw, lane, gwarp, nwarps);
+    bucket_runs<W, true>(a, Rw, Xw, lane, gwarp, nwarps);
     grid.sync();
 
     // ordered first fit in rank order; warps take ranks from a counter
@@ -379,7 +406,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       ca.ranked = 1;
       ca.clist = a.clist;
       ca.xz = a.xz_r;
-      ca.qw = 1;
+      ca.qw = W;
       bool ok = true;
       while (ok) {
         int t = 0;
@@ -440,17 +467,21 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
   }
 }
 
-size_t small_smem_bytes() { return (size_t)kSmallWarps * kWarpSmemBytes; }
+size_t small_smem_bytes(int32_t qw) {
+  return (size_t)kSmallWarps * (qw == 2 ? warp_smem_bytes<2>() : warp_smem_bytes<1>());
+}
 
 cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, cudaStream_t s) {
   int dev = 0, sms = 148, per_sm = 0;
-  const size_t smem = small_smem_bytes();
+  if (a.qw != 1 && a.qw != 2) return cudaErrorInvalidValue;
+  const size_t smem = small_smem_bytes(a.qw);
+  auto kern = a.qw == 2 ? k_small_rounds<2> : k_small_rounds<1>;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_small_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_rounds, kSmallThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmallThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   // fewer resident blocks make each grid barrier cheaper; two per SM keep
@@ -460,7 +491,7 @@ cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, cudaStream_t s
   blocks = (int)debug_grid(blocks);
   SmallArgs args = a;
   void* params[] = {(void*)&args};
-  e = cudaLaunchCooperativeKernel((const void*)k_small_rounds, dim3((unsigned)blocks), dim3(kSmallThreads), params,
+  e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)blocks), dim3(kSmallThreads), params,
                                   smem, s);
   count_launches(1);
   return e;
