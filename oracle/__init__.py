@@ -14,6 +14,8 @@ Function map (paper passage each follows):
   encode3/commute3  Sec. III-A, inverse one-hot code + AND + popcount parity
   conflict_*        Alg. 1 construct_conflict_graph (color-major rows: per
                     list color, the commuting vertices holding it)
+  conflict_edges    Sec. III-A's G_c with each edge once (commute and lists
+                    meet)
   color_greedy      Sec. III-B static order, first available list color
   round_params      Table I / Sec. VI parameter rule
   run               Alg. 1, all rounds
@@ -83,6 +85,11 @@ def lib():
         L.orc_conflict_nnz.restype = ctypes.c_int64
         L.orc_conflict_fill.argtypes = [ctypes.c_int64, _u32p, ctypes.c_int32, _i64p, ctypes.c_int32, _i64p,
                                         _i64p, _i32p, ctypes.c_int32]
+        L.orc_conflict_collect.argtypes = [ctypes.c_int64, _u32p, ctypes.c_int32, _i64p, ctypes.c_int32, _i64p,
+                                           ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _i64p,
+                                           ctypes.POINTER(_i32p)]
+        L.orc_conflict_collect.restype = ctypes.c_int64
+        L.orc_free.argtypes = [ctypes.c_void_p]
         L.orc_color_greedy.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, _i64p, _i64p,
                                        ctypes.c_int32, _i64p, _i32p, ctypes.c_int64, ctypes.c_int64, _i64p]
         L.orc_color_greedy.restype = ctypes.c_int64
@@ -189,40 +196,43 @@ def round_params(n: int, num: int, den: int, alpha: float):
     return int(P.value), int(L.value)
 
 
-def conflict_csr(enc: np.ndarray, lists: np.ndarray, threads: int | None = None):
-    """Whole conflict CSR (off int64 [n+1], col int32) of one round."""
+def _collect(enc: np.ndarray, lists: np.ndarray, rows, edges: int, threads: int | None):
     enc = np.ascontiguousarray(enc, dtype=np.uint32)
     lists = np.ascontiguousarray(lists, dtype=np.int64)
     n, w3 = enc.shape
     L = lists.shape[1]
-    threads = threads or default_threads()
-    lens = np.zeros(n + 1, dtype=np.int64)
-    nnz = lib().orc_conflict_nnz(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(lens, _i64p), threads)
-    off = np.zeros(n + 1, dtype=np.int64)
-    col = np.zeros(max(nnz, 1), dtype=np.int32)
-    lib().orc_conflict_fill(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(lens, _i64p), _p(off, _i64p),
-                            _p(col, _i32p), threads)
-    return off, col[:nnz]
+    if rows is None:
+        m, rp = n, None
+    else:
+        rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+        m, rp = len(rows), _p(rows, _i64p)
+    off = np.zeros(m + 1, dtype=np.int64)
+    colp = _i32p()
+    nnz = lib().orc_conflict_collect(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, rp, m, edges,
+                                     threads or default_threads(), _p(off, _i64p), ctypes.byref(colp))
+    col = np.ctypeslib.as_array(colp, shape=(max(nnz, 1),))[:nnz].copy()
+    lib().orc_free(ctypes.cast(colp, ctypes.c_void_p))
+    return off, col
+
+
+def conflict_csr(enc: np.ndarray, lists: np.ndarray, threads: int | None = None):
+    """Whole conflict CSR (off int64 [n+1], col int32) of one round, in the
+    color-major layout (a neighbour once per shared color)."""
+    return _collect(enc, lists, None, 0, threads)
+
+
+def conflict_edges(enc: np.ndarray, lists: np.ndarray, threads: int | None = None):
+    """The paper's G_c with each edge once: (off int64 [n+1], col int32), row
+    u holding the partners v > u (ascending) that commute with u and share a
+    list color with it."""
+    return _collect(enc, lists, None, 1, threads)
 
 
 def conflict_rows(enc: np.ndarray, lists: np.ndarray, rows, threads: int | None = None):
     """Selected rows: returns (lens int64 [m], list of int32 arrays)."""
-    enc = np.ascontiguousarray(enc, dtype=np.uint32)
-    lists = np.ascontiguousarray(lists, dtype=np.int64)
-    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
-    n, w3 = enc.shape
-    L = lists.shape[1]
-    m = len(rows)
-    threads = threads or default_threads()
-    lens = np.zeros(m + 1, dtype=np.int64)
-    lib().orc_conflict_rows(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(rows, _i64p), m, _p(lens, _i64p),
-                            None, None, threads)
-    off = np.zeros(m + 1, dtype=np.int64)
-    off[1:] = np.cumsum(lens[:m])
-    col = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
-    lib().orc_conflict_rows(n, _p(enc, _u32p), w3, _p(lists, _i64p), L, _p(rows, _i64p), m, None,
-                            _p(off, _i64p), _p(col, _i32p), threads)
-    return lens[:m], [col[off[i]:off[i + 1]].copy() for i in range(m)]
+    off, col = _collect(enc, lists, rows, 0, threads)
+    m = len(off) - 1
+    return np.diff(off), [col[off[i]:off[i + 1]].copy() for i in range(m)]
 
 
 def color_greedy(seed: int, rnd: int, gids, lists, off, col, P: int, base: int) -> np.ndarray:

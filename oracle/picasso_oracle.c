@@ -183,14 +183,8 @@ void orc_encode3(const uint8_t* chars, int64_t n, int32_t q, uint32_t* enc) {
   }
 }
 
-static int orc_popcount32(uint32_t x) {
-  int c = 0;
-  while (x) {
-    c += (int)(x & 1u);
-    x >>= 1;
-  }
-  return c;
-}
+/* Number of one bits of x (the compiler's population count builtin). */
+static int orc_popcount32(uint32_t x) { return __builtin_popcount(x); }
 
 /* AND the codes and count ones: the count's parity is the parity of the
  * number of mismatching non-identity positions.  Returns 1 if they commute. */
@@ -224,50 +218,95 @@ int64_t orc_min_shared(const int64_t* a, const int64_t* b, int32_t L) {
 /* ------------------------------------------------------------------------ */
 
 /* One row in color-major order.  enc: [n][w3] codes of the round's vertices
- * (round-local ids), lists: [n][L] sorted global colors.  cnt: scratch
- * [L+1].  Row u lists, for each color c_k of u's list (ascending k), every
+ * (round-local ids), lists: [n][L] sorted colors, all in [cmin, cmin +
+ * ncol).  Row u lists, for each color c_k of u's list (ascending k), every
  * other vertex v that commutes with u and also holds c_k, ascending in v; a
  * neighbour sharing m colors with u therefore appears in m of u's runs.
  * Writes the row into out (may be NULL to count) and returns its length.
- * The first pass counts per color index, the second lays the row out.     */
-int64_t orc_conflict_row(int64_t u, int64_t n, const uint32_t* enc, int32_t w3,
-                         const int64_t* lists, int32_t L, int64_t* cnt,
-                         int32_t* out) {
-  for (int32_t k = 0; k <= L; ++k) cnt[k] = 0;
+ * Scratch (per calling thread): idx [ncol] all zero on entry and on return
+ * (idx[c - cmin] = k + 1 while c is u's k-th color); cnt [L + 1]; hit_k /
+ * hit_v a growable list of the row's (k, v) hits in the order found
+ * (ascending v), which a counting sort by k turns into the runs.           */
+typedef struct {
+  int32_t* idx;
+  int64_t cmin, ncol;
+  int64_t* cnt;
+  int32_t* hit_k;
+  int32_t* hit_v;
+  int64_t cap;
+} orc_row_scratch;
+
+static void orc_hit(orc_row_scratch* sc, int64_t len, int32_t k, int64_t v) {
+  if (len == sc->cap) {
+    sc->cap = sc->cap ? 2 * sc->cap : 1024;
+    sc->hit_k = (int32_t*)realloc(sc->hit_k, sizeof(int32_t) * (size_t)sc->cap);
+    sc->hit_v = (int32_t*)realloc(sc->hit_v, sizeof(int32_t) * (size_t)sc->cap);
+  }
+  sc->hit_k[len] = k;
+  sc->hit_v[len] = (int32_t)v;
+}
+
+/* The row's (k, v) hits into the scratch list, in ascending v; sc->cnt[k+1]
+ * counts the hits of u's k-th color.  Returns the count.                   */
+static int64_t orc_conflict_hits(int64_t u, int64_t n, const uint32_t* enc, int32_t w3,
+                                 const int64_t* lists, int32_t L, orc_row_scratch* sc) {
+  const int64_t* a = lists + u * L;
+  for (int32_t k = 0; k < L; ++k) sc->idx[a[k] - sc->cmin] = k + 1;
+  for (int32_t k = 0; k <= L; ++k) sc->cnt[k] = 0;
   int64_t len = 0;
-  for (int pass = 0; pass < (out ? 2 : 1); ++pass) {
-    if (pass == 1) {
-      int64_t run = 0;
-      for (int32_t k = 0; k < L; ++k) {
-        int64_t c = cnt[k + 1];
-        cnt[k + 1] = run;
-        run += c;
-      }
-    }
-    for (int64_t v = 0; v < n; ++v) {
-      if (v == u) continue;
-      if (!orc_commute3(enc + u * w3, enc + v * w3, w3)) continue;
-      const int64_t* a = lists + u * L;
-      const int64_t* b = lists + v * L;
-      int32_t i = 0, j = 0;
-      while (i < L && j < L) {
-        if (a[i] == b[j]) {
-          if (pass == 0) {
-            cnt[i + 1]++;
-            ++len;
-          } else {
-            out[cnt[i + 1]++] = (int32_t)v;
-          }
-          ++i;
-          ++j;
-        } else if (a[i] < b[j]) {
-          ++i;
-        } else {
-          ++j;
-        }
-      }
+  for (int64_t v = 0; v < n; ++v) {
+    if (v == u) continue;
+    if (!orc_commute3(enc + u * w3, enc + v * w3, w3)) continue;
+    const int64_t* b = lists + v * L;
+    for (int32_t j = 0; j < L; ++j) {
+      int32_t k1 = sc->idx[b[j] - sc->cmin]; /* b[j] is u's color k1 - 1 */
+      if (k1 == 0) continue;
+      sc->cnt[k1]++;
+      orc_hit(sc, len++, k1 - 1, v);
     }
   }
+  for (int32_t k = 0; k < L; ++k) sc->idx[a[k] - sc->cmin] = 0;
+  return len;
+}
+
+/* Lays the hits out as runs in ascending k (a counting sort by k; inside a
+ * run the hits keep their ascending v).                                    */
+static void orc_conflict_layout(orc_row_scratch* sc, int64_t len, int32_t L, int32_t* out) {
+  int64_t run = 0;
+  for (int32_t k = 1; k <= L; ++k) {
+    int64_t c = sc->cnt[k];
+    sc->cnt[k] = run;
+    run += c;
+  }
+  for (int64_t h = 0; h < len; ++h) out[sc->cnt[sc->hit_k[h] + 1]++] = sc->hit_v[h];
+}
+
+int64_t orc_conflict_row(int64_t u, int64_t n, const uint32_t* enc, int32_t w3,
+                         const int64_t* lists, int32_t L, orc_row_scratch* sc,
+                         int32_t* out) {
+  int64_t len = orc_conflict_hits(u, n, enc, w3, lists, L, sc);
+  if (out) orc_conflict_layout(sc, len, L, out);
+  return len;
+}
+
+/* The paper's conflict graph G_c with each edge once (Sec. III-A: u and v
+ * are adjacent iff they commute and their lists share a color): the
+ * partners v > u of u, ascending, into the scratch hit list (hit_v).
+ * Returns the count.                                                       */
+static int64_t orc_edge_row(int64_t u, int64_t n, const uint32_t* enc, int32_t w3,
+                            const int64_t* lists, int32_t L, orc_row_scratch* sc) {
+  const int64_t* a = lists + u * L;
+  for (int32_t k = 0; k < L; ++k) sc->idx[a[k] - sc->cmin] = k + 1;
+  int64_t len = 0;
+  for (int64_t v = u + 1; v < n; ++v) {
+    if (!orc_commute3(enc + u * w3, enc + v * w3, w3)) continue;
+    const int64_t* b = lists + v * L;
+    int meet = 0;
+    for (int32_t j = 0; j < L; ++j)
+      if (sc->idx[b[j] - sc->cmin]) meet = 1;
+    if (meet) orc_hit(sc, len++, 0, v);
+  }
+  for (int32_t k = 0; k < L; ++k) sc->idx[a[k] - sc->cmin] = 0;
   return len;
 }
 
@@ -278,27 +317,59 @@ typedef struct {
   const int64_t* lists;
   int32_t L;
   const int64_t* rows; /* NULL: rows 0..count-1 themselves */
+  int64_t cmin, ncol;  /* every list color lies in [cmin, cmin + ncol) */
   int64_t* lens;
   const int64_t* off;
   int32_t* col;
+  int32_t** rowbuf; /* non-NULL: each row into its own malloc'd buffer */
+  int32_t edges;    /* 1: the deduplicated edge rows of orc_edge_row instead */
 } orc_rows_job;
 
 static void* orc_rows_worker(void* arg) {
   orc_rows_job* j = (orc_rows_job*)arg;
-  int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)(j->L + 2));
+  orc_row_scratch sc;
+  memset(&sc, 0, sizeof(sc));
+  sc.cmin = j->cmin;
+  sc.ncol = j->ncol;
+  sc.idx = (int32_t*)calloc((size_t)(j->ncol > 0 ? j->ncol : 1), sizeof(int32_t));
+  sc.cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)(j->L + 2));
   for (int64_t i = j->r0; i < j->r1; i += j->stride) {
     int64_t u = j->rows ? j->rows[i] : i;
+    if (j->rowbuf) {
+      /* the row goes to the scratch hit list first, then to a buffer of its own */
+      int64_t len = j->edges ? orc_edge_row(u, j->n, j->enc, j->w3, j->lists, j->L, &sc)
+                             : orc_conflict_hits(u, j->n, j->enc, j->w3, j->lists, j->L, &sc);
+      int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(len > 0 ? len : 1));
+      if (j->edges)
+        memcpy(tmp, sc.hit_v, sizeof(int32_t) * (size_t)len);
+      else
+        orc_conflict_layout(&sc, len, j->L, tmp);
+      j->rowbuf[i] = tmp;
+      j->lens[i] = len;
+      continue;
+    }
     int32_t* dst = j->col ? j->col + j->off[i] : NULL;
-    int64_t len = orc_conflict_row(u, j->n, j->enc, j->w3, j->lists, j->L, cnt, dst);
+    int64_t len = orc_conflict_row(u, j->n, j->enc, j->w3, j->lists, j->L, &sc, dst);
     if (j->lens) j->lens[i] = len;
   }
-  free(cnt);
+  free(sc.idx);
+  free(sc.cnt);
+  free(sc.hit_k);
+  free(sc.hit_v);
   return NULL;
 }
 
 static void orc_run_rows(orc_rows_job proto, int64_t count, int32_t threads) {
   if (threads < 1) threads = 1;
   if (threads > 256) threads = 256;
+  const int64_t E = proto.n * proto.L;
+  int64_t lo = E > 0 ? proto.lists[0] : 0, hi = E > 0 ? proto.lists[0] : -1;
+  for (int64_t e = 1; e < E; ++e) {
+    if (proto.lists[e] < lo) lo = proto.lists[e];
+    if (proto.lists[e] > hi) hi = proto.lists[e];
+  }
+  proto.cmin = lo;
+  proto.ncol = hi - lo + 1;
   pthread_t tid[256];
   orc_rows_job jobs[256];
   for (int32_t t = 0; t < threads; ++t) {
@@ -349,6 +420,43 @@ void orc_conflict_fill(int64_t n, const uint32_t* enc, int32_t w3,
   for (int64_t u = 0; u < n; ++u) off[u + 1] = off[u] + lens[u];
   orc_conflict_rows(n, enc, w3, lists, L, NULL, n, NULL, off, col, threads);
 }
+
+/* Rows rows[0..m) (NULL: all n rows) in one pass: off[m+1] receives the
+ * offsets and *col a malloc'd array of the concatenated rows (release it
+ * with orc_free).  edges = 0: the color-major rows of orc_conflict_row;
+ * edges = 1: the deduplicated rows of orc_edge_row (partners v > u).
+ * Returns the total length.                                               */
+int64_t orc_conflict_collect(int64_t n, const uint32_t* enc, int32_t w3, const int64_t* lists, int32_t L,
+                             const int64_t* rows, int64_t m, int32_t edges, int32_t threads, int64_t* off,
+                             int32_t** col) {
+  int32_t** rowbuf = (int32_t**)malloc(sizeof(int32_t*) * (size_t)(m > 0 ? m : 1));
+  int64_t* lens = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+  orc_rows_job p;
+  memset(&p, 0, sizeof(p));
+  p.n = n;
+  p.enc = enc;
+  p.w3 = w3;
+  p.lists = lists;
+  p.L = L;
+  p.rows = rows;
+  p.lens = lens;
+  p.rowbuf = rowbuf;
+  p.edges = edges;
+  orc_run_rows(p, m, threads);
+  off[0] = 0;
+  for (int64_t i = 0; i < m; ++i) off[i + 1] = off[i] + lens[i];
+  int32_t* out = (int32_t*)malloc(sizeof(int32_t) * (size_t)(off[m] > 0 ? off[m] : 1));
+  for (int64_t i = 0; i < m; ++i) {
+    memcpy(out + off[i], rowbuf[i], sizeof(int32_t) * (size_t)lens[i]);
+    free(rowbuf[i]);
+  }
+  free(rowbuf);
+  free(lens);
+  *col = out;
+  return off[m];
+}
+
+void orc_free(void* p) { free(p); }
 
 /* ------------------------------------------------------------------------ */
 /* Coloring of the conflict graph: static Random order, first fit (Sec.      */
@@ -647,11 +755,9 @@ int32_t orc_run_colorer(const uint8_t* chars, int64_t N, int32_t q, uint64_t see
       memcpy(enc + v * w3, enc_all + gids[v] * w3, sizeof(uint32_t) * (size_t)w3);
       orc_draw_list(seed, round, gids[v], P, L, base, lists + v * L);
     }
-    int64_t* lens = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
     int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
-    int64_t nnz = orc_conflict_nnz(n, enc, w3, lists, L, lens, threads);
-    int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz + 1));
-    orc_conflict_fill(n, enc, w3, lists, L, lens, off, col, threads);
+    int32_t* col = NULL;
+    int64_t nnz = orc_conflict_collect(n, enc, w3, lists, L, NULL, n, 0, threads, off, &col);
     int64_t* cl = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
     int64_t colored =
         colorer == 1   ? orc_color_dynamic(seed, round, n, gids, lists, L, off, col, cl)
@@ -679,7 +785,6 @@ int32_t orc_run_colorer(const uint8_t* chars, int64_t N, int32_t q, uint64_t see
     ++round;
     free(enc);
     free(lists);
-    free(lens);
     free(off);
     free(col);
     free(cl);

@@ -242,6 +242,58 @@ def test_conflict_count_closed_form(orc):
         assert abs(distinct - mean_d) < 0.03 * mean_d, (distinct, mean_d)
 
 
+def _brute_edges(chars, lists):
+    """G_c with each edge once: pairs u < v that commute (character rule) and
+    whose lists share at least one color (Python sets)."""
+    n = len(chars)
+    sets = [set(l.tolist()) for l in lists]
+    out = []
+    for u in range(n):
+        for v in range(u + 1, n):
+            cnt = sum(1 for a, b in zip(chars[u], chars[v]) if a and b and a != b)
+            if cnt % 2 == 0 and sets[u] & sets[v]:
+                out.append((u, v))
+    return out
+
+
+@pytest.mark.parametrize("n,q,P,L", [(1, 5, 3, 2), (2, 3, 2, 1), (37, 6, 9, 3), (64, 20, 12, 4), (50, 3, 5, 5),
+                                     (90, 8, 40, 2)])
+def test_conflict_edges_brute_force(orc, n, q, P, L):
+    chars = synth.pauli_uniform(n, q, seed=n * 5 + q)
+    lists = orc.draw_lists(6, 1, np.arange(n), P, L)
+    off, col = orc.conflict_edges(orc.encode3(chars), lists)
+    got = [(u, int(v)) for u in range(n) for v in col[off[u]:off[u + 1]]]
+    assert got == _brute_edges(chars, lists)
+
+
+def test_conflict_edges_are_the_distinct_pairs_of_the_runs(orc):
+    # the color-major rows list a pair once per shared color; their distinct
+    # pairs are exactly the edge set
+    chars = synth.pauli_weighted(500, 24, 0.3, seed=2)
+    lists = orc.draw_lists(3, 1, np.arange(500), 60, 9)
+    enc = orc.encode3(chars)
+    off, col = orc.conflict_csr(enc, lists)
+    eo, ec = orc.conflict_edges(enc, lists)
+    runs = {(min(u, int(v)), max(u, int(v))) for u in range(500) for v in col[off[u]:off[u + 1]]}
+    edges = {(u, int(v)) for u in range(500) for v in ec[eo[u]:eo[u + 1]]}
+    assert runs == edges and len(edges) == len(ec)
+
+
+def test_conflict_edges_closed_form(orc):
+    # E|E_c| = (#commuting pairs) * (1 - C(P-L, L) / C(P, L)) on the n = 2,000
+    # uniform workload (Sec. III-C: a commuting pair is kept iff its lists meet)
+    n, q, P, L = 2000, 20, 250, 16
+    chars = synth.pauli_uniform(n, q, seed=0)
+    x = ((chars == 1) | (chars == 2)).astype(np.int64)
+    z = ((chars == 3) | (chars == 2)).astype(np.int64)
+    n_comm = (int((((x @ z.T + z @ x.T) % 2) == 0).sum()) - n) // 2
+    mean = n_comm * (1.0 - math.comb(P - L, L) / math.comb(P, L))
+    enc = orc.encode3(chars)
+    for seed in range(3):
+        _, col = orc.conflict_edges(enc, orc.draw_lists(seed, 1, np.arange(n), P, L))
+        assert abs(len(col) - mean) < 0.03 * mean, (len(col), mean)
+
+
 # ---------------------------------------------------------------- coloring
 def test_full_palette_is_plain_greedy(orc):
     # L = P: every list is the whole palette, so the conflict graph is G' and
