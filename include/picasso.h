@@ -86,6 +86,13 @@ typedef struct {
   int32_t csr_form;      /* picasso_csr_form                                  */
   int32_t small_engine;  /* picasso_small_engine                              */
   int32_t budget_mode;   /* picasso_budget_mode                               */
+  int32_t wait_polls;    /* bounded device waits (the ordered coloring waiting
+                            on an earlier neighbour, per-round pass and small-
+                            round engine): polls of one wait before the kernel
+                            gives up, reports it and the round is recolored by
+                            the sweep kernel (per-round path) or handed back to
+                            the per-round path (engine); same colors either
+                            way.  0 = 1,048,576; 1 <= wait_polls <= 2^30    */
 } picasso_config;
 
 /* What picasso_round / picasso_run do with a round whose conflict CSR would
@@ -415,6 +422,11 @@ int picasso_trim_memory(int64_t keep_bytes);
 /* Process-wide count of kernels this library has launched (all contexts). */
 int picasso_kernel_launches(int64_t* out);
 
+/* Process-wide count of the memory requests this library has made: memory
+ * pool creations, device allocations from its pool, and pinned or mapped
+ * host allocations (all contexts).  The paper has no counterpart.          */
+int picasso_memory_requests(int64_t* out);
+
 /* Whole run of Alg. 1 (as picasso_init + picasso_run + picasso_get_colors,
  * same colors) for a small set, with no device allocation at all.  The paper
  * has no counterpart: this entry point exists for callers that cannot call
@@ -424,10 +436,23 @@ int picasso_kernel_launches(int64_t* out);
  * static device array of about 12.1 MB; once this function has run on a GPU,
  * that GPU holds the array until the process exits.
  *   d_xz        [n][2] packed strings (caller-owned, read-only)
- *   d_color_out [n] int32, receives the global colors (caller-owned)
+ *   d_color_out [n] int32, receives the global colors (caller-owned); it is
+ *               set to -1 first and each round writes its colors as it ends,
+ *               so a call that fails in a later round (for example
+ *               PICASSO_ERR_UNSUPPORTED from that round's size check, or
+ *               PICASSO_ERR_BUDGET) leaves the earlier rounds' colors there
+ *               and -1 for the rest
  *   n_rounds    may be NULL
+ * Fields of cfg it reads: seed, palette_num, palette_den, alpha, max_rounds,
+ * color_algo (AUTO and SWEEP give the same colors; DYNAMIC returns
+ * PICASSO_ERR_UNSUPPORTED), byte_budget with budget_mode FAIL (a round whose
+ * CSR in cfg.csr_form would exceed it returns PICASSO_ERR_BUDGET; another
+ * budget_mode with a nonzero budget returns PICASSO_ERR_UNSUPPORTED), and
+ * wait_polls.  conflict_algo and small_engine do not change colors and are
+ * not read: every round tests all pairs.
  * Limits: 1 <= n <= 2048, q <= 64, round-1 list size L <= 32, and at most
- * 2,621,440 run entries in any round;
+ * 2,621,440 run entries in any round, counted with both directions of every
+ * pair (the array's conflict rows hold both, whatever cfg.csr_form says);
  * beyond them it returns PICASSO_ERR_UNSUPPORTED without touching the GPU
  * (the size checks of later rounds run after that round's count pass).
  * The first call on a device looks up the array's device address with that

@@ -22,6 +22,10 @@ using namespace picasso;
 
 namespace {
 std::atomic<long long> g_launches{0};
+// memory requests of the library: pool creations, device allocations from
+// the pool, pinned and mapped host allocations
+std::atomic<long long> g_mem_requests{0};
+void count_request() { g_mem_requests.fetch_add(1, std::memory_order_relaxed); }
 }
 
 namespace picasso {
@@ -45,6 +49,7 @@ cudaError_t pool_for(int dev, cudaMemPool_t* out) {
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = dev;
     cudaMemPool_t pool = nullptr;
+    count_request();
     cudaError_t e = cudaMemPoolCreate(&pool, &props);
     if (e != cudaSuccess) return e;
     uint64_t thr = ~0ull;
@@ -75,6 +80,7 @@ cudaError_t pinned_get(int64_t** out) {
       return cudaSuccess;
     }
   }
+  count_request();
   return cudaMallocHost((void**)out, sizeof(int64_t) * kPinWords);
 }
 
@@ -104,6 +110,7 @@ cudaError_t hostcol_get(int64_t need, int32_t** out, int64_t* cap) {
   }
   *out = nullptr;
   *cap = 0;
+  count_request();
   cudaError_t e = cudaHostAlloc((void**)out, sizeof(int32_t) * (size_t)std::max<int64_t>(need, 1),
                                 cudaHostAllocMapped | cudaHostAllocPortable);
   if (e != cudaSuccess) {
@@ -133,6 +140,8 @@ namespace {
 
 struct Ctx {
   picasso_config cfg{};
+  // polls of one bounded device wait (cfg.wait_polls, 0 = the default)
+  int32_t max_polls() const { return cfg.wait_polls > 0 ? cfg.wait_polls : kMaxPolls; }
   cudaStream_t s = nullptr;
   int dev = 0;
   cudaMemPool_t pool = nullptr;
@@ -264,6 +273,7 @@ template <class T>
 int alloc(Ctx* c, T** p, int64_t count) {
   *p = nullptr;
   const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+  count_request();
   cudaError_t e = cudaMallocFromPoolAsync((void**)p, bytes, c->pool, c->s);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -678,7 +688,8 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
       c->tested_pairs += bucket_pairs / 2;
       c->t_emit += ms;
       c->emit_launches += 1;
-      c->emit_bytes += 4 * nnz + 16 * E + 4 * E + 12 * E;
+      // per list entry: member words 16, entry and vertex ids 8, run start 8 and length 4
+      c->emit_bytes += 4 * nnz + 36 * E;
       for (int k = 0; k < c->nsets; ++k) c->logical_pairs += c->remaining[k] * (c->remaining[k] - 1) / 2;
       cleanup();
       c->nnz = nnz;
@@ -1037,6 +1048,7 @@ int color_round(Ctx* c) {
   a.clist = clist;
   a.xz = c->xz_r;
   a.qw = c->qw;
+  a.max_polls = c->max_polls();
   // Ordered persistent pass; if one of its bounded waits runs out (ctl[5]),
   // recolor the round with the sweep kernel from a fresh state.  The colors,
   // the carry flags and their prefix sum are enqueued behind the pass, so one
@@ -1313,6 +1325,7 @@ int run_small(Ctx* c) {
   a.sid = sid;
   a.xz_r = xz_r;
   a.qw = c->qw;
+  a.max_polls = c->max_polls();
   a.lists = lists;
   a.ent_v = ent_v;
   a.loff = loff;
@@ -1464,6 +1477,7 @@ int color_chunked(Ctx* c) {
   a.clist = clist;
   a.xz = c->xz_r;
   a.qw = c->qw;
+  a.max_polls = c->max_polls();
   TRYC(launch_color_init(a, c->prio, ctl, s));
   ConflictArgs ca{};
   ca.n = n;
@@ -1533,7 +1547,8 @@ int validate_cfg(const picasso_config* cfg) {
       cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
       cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->conflict_algo < 0 || cfg->conflict_algo > 2 ||
       cfg->color_algo < 0 || cfg->color_algo > 2 || cfg->csr_form < 0 || cfg->csr_form > 1 ||
-      cfg->small_engine < 0 || cfg->small_engine > 1 || cfg->budget_mode < 0 || cfg->budget_mode > 2)
+      cfg->small_engine < 0 || cfg->small_engine > 1 || cfg->budget_mode < 0 || cfg->budget_mode > 2 ||
+      cfg->wait_polls < 0 || cfg->wait_polls > (1 << 30))
     return PICASSO_ERR_INVALID_ARG;
   return PICASSO_OK;
 }
@@ -2091,6 +2106,12 @@ int picasso_trim_memory(int64_t keep_bytes) {
 int picasso_kernel_launches(int64_t* out) {
   if (!out) return PICASSO_ERR_INVALID_ARG;
   *out = (int64_t)g_launches.load();
+  return PICASSO_OK;
+}
+
+int picasso_memory_requests(int64_t* out) {
+  if (!out) return PICASSO_ERR_INVALID_ARG;
+  *out = (int64_t)g_mem_requests.load();
   return PICASSO_OK;
 }
 

@@ -124,8 +124,14 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
   if (q > 64 || n > kStaticMaxN) return PICASSO_ERR_UNSUPPORTED;
   if (cfg->palette_num < 1 || cfg->palette_den < 1 || cfg->palette_num > (int64_t(1) << 32) ||
       cfg->palette_den > (int64_t(1) << 32) || !(cfg->alpha > 0.0) || !std::isfinite(cfg->alpha) ||
-      cfg->max_rounds < 1)
+      cfg->max_rounds < 1 || cfg->byte_budget < 0 || cfg->color_algo < 0 || cfg->color_algo > 2 ||
+      cfg->csr_form < 0 || cfg->csr_form > 1 || cfg->budget_mode < 0 || cfg->budget_mode > 2 ||
+      cfg->wait_polls < 0 || cfg->wait_polls > (1 << 30))
     return PICASSO_ERR_INVALID_ARG;
+  // Alg. 2's dynamic order and the budget fallbacks (chunks, host CSR) are
+  // not built here
+  if (cfg->color_algo == PICASSO_COLOR_DYNAMIC) return PICASSO_ERR_UNSUPPORTED;
+  if (cfg->byte_budget > 0 && cfg->budget_mode != PICASSO_BUDGET_FAIL) return PICASSO_ERR_UNSUPPORTED;
   {
     int64_t P;
     int32_t L;
@@ -217,6 +223,10 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
       if (st != PICASSO_OK) return st;
     }
     if (nnz > kStaticMaxNnz) return PICASSO_ERR_UNSUPPORTED;
+    // the byte budget counts the CSR picasso_run would build: both directions
+    // (FULL) or each pair once (EARLIER, half of the two-sided count here)
+    const int64_t csr_nnz = cfg->csr_form == PICASSO_CSR_FULL ? nnz : nnz / 2;
+    if (cfg->byte_budget > 0 && 8 * (m + 1) + 4 * csr_nnz > cfg->byte_budget) return PICASSO_ERR_BUDGET;
     a.runoff = runoff;
     a.col = col;
     SCK(launch_allpairs(a, true, s));
@@ -233,15 +243,17 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
     ca.blk = blk;
     ca.blkw = blkw;
     ca.ranked = 0;  // ids in ascending global id; the order list gives the coloring order
+    ca.max_polls = cfg->wait_polls > 0 ? cfg->wait_polls : kMaxPolls;
     SCK(cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCtlWords, s));
     SCK(launch_prio_order(prio, m, prio_bins_for(m), hist, hoff, tmp, work[0], s));
     SCK(launch_color_init(ca, prio, counts, s));
-    SCK(launch_color_ordered(ca, work[0], counts + 5, s));
+    const bool sweep_only = cfg->color_algo == PICASSO_COLOR_SWEEP;
+    if (!sweep_only) SCK(launch_color_ordered(ca, work[0], counts + 5, s));
     {
       int32_t h[8];
       SCK(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, s));
       SCK(cudaStreamSynchronize(s));
-      if (h[5] != 0) {  // a bounded wait ran out: recolor with the sweep kernel
+      if (sweep_only || h[5] != 0) {  // SWEEP, or a bounded wait ran out: the sweep kernel
         SCK(cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCtlWords, s));
         SCK(launch_color_init(ca, prio, counts, s));
         SCK(launch_color_all(ca, work[0], work[1], wact, counts, s));

@@ -21,10 +21,10 @@ __device__ __forceinline__ void publish(uint64_t* state, int32_t v, uint32_t w) 
 // position's warp is working on it (all its earlier positions are done), and
 // that vertex waits only on earlier positions, which are finished; the
 // cooperative launch guarantees every warp is resident.  A poll budget
-// bounds every wait: when it runs out the kernel sets *err = 1 and the warp
-// returns; the caller then recolors the round with the sweep kernel.
+// bounds every wait (a.max_polls polls; the context's wait_polls, by default
+// kMaxPolls): when it runs out the kernel sets *err = 1 and the warp returns;
+// the caller then recolors the round with the sweep kernel.
 // ---------------------------------------------------------------------------
-constexpr int kMaxPolls = 1 << 20;
 
 constexpr int kOrderedGroup = 2;  // run chunks of 32 whose loads are in flight together
 
@@ -100,7 +100,7 @@ __device__ __forceinline__ bool run_blocked(const ColorArgs& a, int32_t v, uint3
     while (true) {
       const uint32_t w = (uint32_t)__ldcg(&a.state[wu_id]);
       if ((w & 3u) != kUndecided || (w >> 2) > c) break;
-      if (++polls > kMaxPolls) {
+      if (++polls > a.max_polls) {
         *fail = true;
         return true;
       }

@@ -21,6 +21,7 @@ constexpr uint32_t kTagList = 1u;
 constexpr uint32_t kTagPrio = 2u;
 constexpr uint32_t kTagDynamic = 4u;  // Alg. 2's color draw
 constexpr int kMaxL = 512;           // longest list a round may draw
+constexpr int kMaxPolls = 1 << 20;   // default polls of one bounded device wait
 constexpr int kBucketCap = 2048;     // largest color bucket of the bucket join
 constexpr int kBucketMaxP = 1 << 21; // bucket colors of one round (bucket join)
 constexpr int kClistWords = 8;       // colored-list words per color (ordered coloring)
@@ -336,6 +337,7 @@ struct ColorArgs {
   uint32_t* clist;
   const uint64_t* xz;  // [n][2 qw] words in rank order (with clist)
   int32_t qw;          // 64-bit words per part
+  int32_t max_polls;   // polls of one bounded wait before the kernel gives up
 };
 // Work list of all n vertices in ascending (priority, id): a counting sort on
 // the top log2(nbins) priority bits, then a sort inside each bin.  hist needs
@@ -456,6 +458,7 @@ struct SmallArgs {
   int64_t* ctl;           // [9]: 0 n, 1 rounds done, 2 stop reason, 4 V_l in gid_b (0..4
                           //      host-initialised), 6 sum of nnz, 7 sum over the sets of
                           //      n_k (n_k - 1) / 2 (6, 7 zero on entry), 3, 5, 8 scratch
+  int32_t max_polls;      // polls of one bounded wait before the engine gives up
 };
 
 // Stop reasons in ctl[2].

@@ -407,6 +407,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       ca.clist = a.clist;
       ca.xz = a.xz_r;
       ca.qw = W;
+      ca.max_polls = a.max_polls;
       bool ok = true;
       while (ok) {
         int t = 0;

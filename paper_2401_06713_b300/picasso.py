@@ -42,6 +42,7 @@ class Config(ctypes.Structure):
         ("csr_form", ctypes.c_int32),
         ("small_engine", ctypes.c_int32),
         ("budget_mode", ctypes.c_int32),
+        ("wait_polls", ctypes.c_int32),
     ]
 
 
@@ -125,6 +126,7 @@ _SIGS = {
     "picasso_get_stats": [_vp, ctypes.POINTER(Stats)],
     "picasso_philox_draws": [ctypes.c_uint64, _i32, _i64, ctypes.c_uint32, ctypes.c_uint32, _i32, _vp, _vp],
     "picasso_kernel_launches": [_pi64],
+    "picasso_memory_requests": [_pi64],
     "picasso_trim_memory": [_i64],
     "picasso_run_small_static": [_vp, _i64, _i32, ctypes.POINTER(Config), _vp, _pi32, _vp],
     "picasso_destroy": [_vp],
@@ -206,6 +208,14 @@ def kernel_launches() -> int:
     return int(k.value)
 
 
+def memory_requests() -> int:
+    """Process-wide count of libpicasso's memory requests (pool creations,
+    device allocations from its pool, pinned and mapped host allocations)."""
+    k = ctypes.c_int64()
+    _ck(_lib().picasso_memory_requests(ctypes.byref(k)), "picasso_memory_requests")
+    return int(k.value)
+
+
 def trim_memory(keep_bytes: int = 0):
     """Return the library's cached device memory (current device) to the driver."""
     _ck(_lib().picasso_trim_memory(keep_bytes), "picasso_trim_memory")
@@ -224,7 +234,7 @@ class Picasso:
     def __init__(self, xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
                  algo: str = "auto", max_rounds: int = 100000, byte_budget: int = 0, stream=None,
                  color: str = "auto", set_offsets=None, seeds=None, csr: str = "earlier", small: str = "auto",
-                 budget_mode: str = "fail"):
+                 budget_mode: str = "fail", wait_polls: int = 0):
         """One set, or with ``set_offsets`` (host, nsets + 1 ints) a batch of
         independent sets stored back to back in ``xz`` (seeds default to
         seed + k)."""
@@ -246,6 +256,7 @@ class Picasso:
         cfg.csr_form = CSR_FORMS[csr]
         cfg.small_engine = SMALL_ENGINE[small]
         cfg.budget_mode = BUDGET_MODES[budget_mode]
+        cfg.wait_polls = wait_polls
         self.cfg = cfg
         h = ctypes.c_void_p()
         if set_offsets is None:
@@ -387,7 +398,8 @@ class Picasso:
 
 
 def run_small_static(xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
-                     max_rounds: int = 100000, out: torch.Tensor | None = None, stream=None):
+                     max_rounds: int = 100000, out: torch.Tensor | None = None, stream=None, color: str = "auto",
+                     byte_budget: int = 0, csr: str = "earlier", wait_polls: int = 0):
     """Whole run for a small set (n <= 2048) that allocates no device memory
     inside the library; see picasso_run_small_static.  Returns (colors, rounds)."""
     assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2
@@ -401,6 +413,10 @@ def run_small_static(xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), al
     cfg.palette_num, cfg.palette_den = palette
     cfg.alpha = alpha
     cfg.max_rounds = max_rounds
+    cfg.color_algo = COLOR_ALGOS[color]
+    cfg.byte_budget = byte_budget
+    cfg.csr_form = CSR_FORMS[csr]
+    cfg.wait_polls = wait_polls
     r = ctypes.c_int32()
     _ck(_lib().picasso_run_small_static(_ptr(xz), n, q, ctypes.byref(cfg), _ptr(out), ctypes.byref(r),
                                         _stream(stream)), "picasso_run_small_static")

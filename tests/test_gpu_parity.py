@@ -170,6 +170,65 @@ def test_conflict_weighted_mid(pc, orc):
     _check_build(pc, orc, synth.pauli_weighted(n, 48, 0.25, seed=4), 7, P, L, "auto")
 
 
+@pytest.mark.parametrize("P,lo,hi", [(500, 440, 480), (450, 500, 512)])
+def test_conflict_fused_large_buckets(pc, orc, P, lo, hi):
+    # the fused build pass at the bucket sizes of the n = 1M workload (mean
+    # n L / P = 408) and up to its limit of 512 members (mean 453, largest
+    # 511): n = 12,000 strings of the weighted law, L = 17; whole CSRs of
+    # both forms (EARLIER through the fused pass, FULL through the two-pass
+    # build) element by element against the oracle
+    n, L, seed = 12000, 17, 7
+    chars = synth.pauli_weighted(n, 64, 0.25, seed=21)
+    _check_build(pc, orc, chars, seed, P, L, "bucket")
+    with pc.Picasso(_xz(pc, chars), 64, seed=seed) as p:
+        p.assign_lists(P, L, 0)
+        _, nnz = p.build_conflicts()
+        st = p.stats()
+        assert lo <= st["max_bucket"] <= hi
+        # only the fused pass counts 4 bytes per run entry + 36 per list entry
+        assert st["emit_launches"] == 1 and st["emit_bytes"] == 4 * nnz + 36 * n * L
+
+
+@pytest.mark.parametrize("P,palette,alpha", [(450, (3, 80), 1.8)])
+@pytest.mark.parametrize("small", ["off", "auto"])
+def test_run_fused_large_buckets(pc, orc, P, palette, alpha, small):
+    # whole runs whose every per-round build has buckets of about 450 members
+    n = 12000
+    assert orc.round_params(n, *palette, alpha) == (P, 17)
+    _run_both(pc, orc, synth.pauli_weighted(n, 64, 0.25, seed=21), 7, *palette, alpha, small=small)
+
+
+def _pair_keys(off, col):
+    """Distinct unordered pairs {u, v} of a CSR, as sorted keys min * n + max."""
+    n = len(off) - 1
+    u = np.repeat(np.arange(n, dtype=np.int64), np.diff(off))
+    v = col.astype(np.int64)
+    return np.unique(np.minimum(u, v) * n + np.maximum(u, v))
+
+
+@pytest.mark.parametrize("case", ["n2000_q20", "n12000_q64_large_buckets"])
+@pytest.mark.parametrize("form", ["earlier", "full"])
+def test_conflict_edges_deduplicated(pc, orc, case, form):
+    # the paper's G_c has each edge once (Sec. III-A: u, v adjacent iff they
+    # commute and their lists meet); the CSR lists a pair once per shared
+    # color, so its distinct pairs must be exactly the oracle's edge set
+    if case == "n2000_q20":
+        chars, q, seed, P, L = synth.pauli_uniform(2000, 20, seed=0), 20, 0, 250, 16
+    else:
+        chars, q, seed, P, L = synth.pauli_weighted(12000, 64, 0.25, seed=21), 64, 7, 500, 17
+    n = len(chars)
+    with pc.Picasso(_xz(pc, chars), q, seed=seed, csr=form) as p:
+        p.assign_lists(P, L, 0)
+        p.build_conflicts()
+        off, col = p.csr()
+        _, enc, lists = _ranked(p, orc, chars, seed, P, L)
+        got = _pair_keys(off.cpu().numpy(), col.cpu().numpy())
+    eo, ec = orc.conflict_edges(enc, lists)
+    ref = np.repeat(np.arange(n, dtype=np.int64), np.diff(eo)) * n + ec.astype(np.int64)
+    assert np.all(np.diff(ref) > 0)  # the oracle's rows are ascending, rows in order
+    assert np.array_equal(got, ref)
+
+
 def test_budget_rejects_before_allocation(pc):
     chars = synth.pauli_uniform(2000, 20, seed=0)
     with pc.Picasso(_xz(pc, chars), 20, seed=0, byte_budget=1000) as p:
@@ -287,6 +346,15 @@ def _check_cliques(enc, colors):
         d += 1
 
 
+def _sampled_rows(col, off, rows):
+    """Rows `rows` of a device CSR, gathered on the device and copied once."""
+    lens = off[rows + 1] - off[rows]
+    starts = np.repeat(off[rows] - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)
+    idx = torch.from_numpy(starts + np.arange(lens.sum(), dtype=np.int64)).cuda()
+    flat = col[idx].cpu().numpy()
+    return np.split(flat, np.cumsum(lens)[:-1])
+
+
 def _full_size(pc, orc, n, q, p_w, num, den, alpha, seed, samples):
     chars = synth.pauli_weighted(n, q, p_w, seed=seed)
     enc = _enc_np(orc, chars)
@@ -306,16 +374,19 @@ def _full_size(pc, orc, n, q, p_w, num, den, alpha, seed, samples):
         _, glists, _ = p.round_state()
         assert np.array_equal(glists.cpu().numpy().astype(np.int64), lists_r)
         lens, ref_rows = orc.conflict_rows(enc_r, lists_r, rows)
+        got_rows = _sampled_rows(col, off, rows)
+        del col
         for i, u in enumerate(rows):
-            got = col[off[u]:off[u + 1]].cpu().numpy()
-            assert np.array_equal(got, ref_rows[i][ref_rows[i] < u])  # the EARLIER form
+            assert np.array_equal(got_rows[i], ref_rows[i][ref_rows[i] < u])  # the EARLIER form
         p.color()
         c1 = p.colors().cpu().numpy()
         # first fit in coloring order at every sampled vertex
         for i, u in enumerate(rows):
-            earlier = [v for v in ref_rows[i] if v < u]
-            taken = {int(c1[order[v]]) for v in earlier if c1[order[v]] >= 0}
-            want = next((int(c) for c in lists_r[u] if int(c) not in taken), -1)
+            earlier = got_rows[i]
+            cn = c1[order[earlier]]
+            taken = np.unique(cn[cn >= 0])
+            free = lists_r[u][~np.isin(lists_r[u], taken)]
+            want = int(free[0]) if len(free) else -1
             assert int(c1[order[u]]) == want
         p.carry()
         colors, rounds = p.run()
@@ -331,8 +402,16 @@ def test_full_size_n100k(pc, orc):
 
 
 def test_full_size_n1m(pc, orc):
-    # n=1,000,000, q=64, p=0.25, P=n/16, alpha=1.5 (the throughput workload)
-    _full_size(pc, orc, 1_000_000, 64, 0.25, 1, 16, 1.5, 0, 24)
+    # n=1,000,000, q=64, p=0.25, P=n/16, alpha=1.5 (the throughput workload):
+    # the exact round-1 conflict rows of a seeded 20,000-vertex sample
+    _full_size(pc, orc, 1_000_000, 64, 0.25, 1, 16, 1.5, 0, 20_000)
+
+
+@pytest.mark.slow
+def test_run_n100k_whole(pc, orc):
+    # n=100,000, q=48, p=0.25, P=n/8, alpha=2: every round and every color
+    # of the GPU run against the oracle's whole run
+    _run_both(pc, orc, synth.pauli_weighted(100_000, 48, 0.25, seed=0), 0, 1, 8, 2.0)
 
 
 def test_full_size_wide_n200k(pc, orc):
