@@ -211,6 +211,18 @@ struct Ctx {
   int64_t* rstart = nullptr;
   uint32_t* rcnt = nullptr;
   double commute_ratio = 0.6;  // nnz / bucket pair bound of the last fused build
+  // bit layout (the bit pass): G_c as every bucket's lower blocks of pair
+  // bits (rmask at moff), each entry's row address (rbits, rpbase), the run
+  // lengths in rcnt and the members in slot order (bt_bmem entries, bt_bpid
+  // vertex ids); the canonical CSR is made from them on request
+  bool bits = false;
+  bool bits_off = false;  // the run layout instead (PICASSO_RUN_LAYOUT=1 at load)
+  int64_t* rbits = nullptr;
+  int32_t* rpbase = nullptr;
+  uint32_t* bt_rmask = nullptr;
+  uint32_t* bt_bcount = nullptr;
+  int64_t *bt_boff = nullptr, *bt_moff = nullptr;
+  int32_t *bt_bmem = nullptr, *bt_bpid = nullptr;
   // color
   bool colored_done = false;
   int64_t n_colored = 0, n_remaining = 0;
@@ -317,6 +329,15 @@ void free_build(Ctx* c) {
   release(c, &c->rstart);
   release(c, &c->rcnt);
   c->direct = false;
+  release(c, &c->rbits);
+  release(c, &c->rpbase);
+  release(c, &c->bt_rmask);
+  release(c, &c->bt_bcount);
+  release(c, &c->bt_boff);
+  release(c, &c->bt_moff);
+  release(c, &c->bt_bmem);
+  release(c, &c->bt_bpid);
+  c->bits = false;
   release(c, &c->ck_boff);
   release(c, &c->ck_moff);
   release(c, &c->ck_jboff);
@@ -625,6 +646,76 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
     } else {
       TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, (int32_t)smax, s));
     }
+    if (fused && !c->bits_off) {
+      // the bit pass: every bucket's lower blocks of pair bits, no run
+      // written.  The blocks' words are allocated from a bound, so nothing
+      // is read back before the pass: a bucket of s members has
+      // 16 nwb (nwb + 1) <= (s + 31)(s + 63) / 64 words, nwb = ceil(s / 32),
+      // and sum s = E, sum s^2 = bucket_pairs + E.
+      TRY(alloc(c, &words, P));
+      TRY(alloc(c, &moff, P + 1));
+      TRYC(launch_bucket_words(bcount, P, 1, words, s));
+      TRYC(launch_scan_u32(words, P, moff, tmp, s));
+      release(c, &words);
+      const int64_t wcap = (bucket_pairs + E + 94 * E + 1953 * P) / 64 + 64;
+      TRY(alloc(c, &rmask, wcap));
+      TRY(alloc(c, &c->rbits, E));
+      TRY(alloc(c, &c->rpbase, E));
+      a.bxz = bxz;
+      a.bpid = bpid;
+      a.rmask = rmask;
+      a.rbits = c->rbits;
+      a.rpbase = c->rpbase;
+      TRYC(cudaEventRecord(c->ev[2], s));
+      TRYC(launch_bucket_bits(a, boff, bmem, moff, (int32_t)smax, c->q, s));
+      TRYC(cudaEventRecord(c->ev[3], s));
+      int64_t* dn = reinterpret_cast<int64_t*>(c->d_err + 2);  // the context's error block, words 2..3
+      TRYC(launch_sum_u32(cnt, E, dn, s));
+      TRYC(cudaMemcpyAsync(c->h_buf, dn, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      TRYC(cudaMemcpyAsync(c->h_buf + 1, moff + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      TRYC(cudaStreamSynchronize(s));
+      const int64_t nnz = c->h_buf[0], mwords = c->h_buf[1];
+      const float ms = (float)elapsed(c, 2, 3);
+      c->rcnt = cnt;
+      cnt = nullptr;
+      c->bt_rmask = rmask;
+      c->bt_bcount = bcount;
+      c->bt_boff = boff;
+      c->bt_moff = moff;
+      c->bt_bmem = bmem;
+      c->bt_bpid = bpid;
+      rmask = nullptr;
+      bcount = nullptr;
+      boff = moff = nullptr;
+      bmem = bpid = nullptr;
+      c->bits = true;
+      const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
+      if (c->nsets > 1) {
+        std::vector<int64_t> h(c->nsets);
+        TRYC(launch_set_csr_bytes(c->loff, nullptr, c->rcnt, c->gid_r, n, c->d_soff, c->nsets, c->d_set_bytes, s));
+        TRYC(cudaMemcpyAsync(h.data(), c->d_set_bytes, sizeof(int64_t) * c->nsets, cudaMemcpyDeviceToHost, s));
+        TRYC(cudaStreamSynchronize(s));
+        for (int k = 0; k < c->nsets; ++k)
+          if (c->remaining[k] > 0) c->set_peak_bytes[k] = std::max(c->set_peak_bytes[k], h[k] + 8);
+      } else {
+        c->set_peak_bytes[0] = std::max(c->set_peak_bytes[0], csr_bytes);
+      }
+      // the pass tests the pairs and writes G_c: member words and entry ids
+      // read (20 bytes per list entry), the bit blocks (4 bytes per word),
+      // run lengths, row addresses and bucket starts (16 bytes per entry)
+      c->t_pairs += ms;
+      c->pairs_launches += 1;
+      c->tested_pairs += bucket_pairs / 2;
+      c->t_emit += ms;
+      c->emit_launches += 1;
+      c->emit_bytes += 36 * E + 4 * mwords;
+      for (int k = 0; k < c->nsets; ++k) c->logical_pairs += c->remaining[k] * (c->remaining[k] - 1) / 2;
+      cleanup();
+      c->nnz = nnz;
+      c->nnz_total += nnz;
+      c->built = true;
+      return PICASSO_OK;
+    }
     if (fused) {
       // fused mask + emit: the runs of a bucket go to one region claimed from
       // a cursor.  The column buffer is sized from the bucket pair bound and
@@ -834,7 +925,10 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
 // The canonical CSR of a direct-layout build: run offsets by entry (a scan of
 // the run lengths), row offsets, and the runs moved to row order.  The
 // context keeps the canonical form afterwards.
+int canonical_bits(Ctx* c);
+
 int canonical_csr(Ctx* c) {
+  if (c->built && c->bits) return canonical_bits(c);
   if (!c->built || !c->direct) return PICASSO_OK;
   const int64_t n = c->n, E = c->E;
   cudaStream_t s = c->s;
@@ -866,6 +960,80 @@ int canonical_csr(Ctx* c) {
   release(c, &c->rstart);
   release(c, &c->rcnt);
   c->direct = false;
+  return PICASSO_OK;
+}
+
+// The canonical CSR of a bit-layout build: run offsets (a scan of the run
+// lengths), row offsets, and the emit pass over the bit blocks, which writes
+// every row's runs in ascending partner order.  The bit layout is released.
+int canonical_bits(Ctx* c) {
+  const int64_t n = c->n, E = c->E, P = c->Ptot;
+  cudaStream_t s = c->s;
+  void* tmp = nullptr;
+  uint32_t* words = nullptr;
+  int64_t* jboff = nullptr;
+  int32_t* ibkt = nullptr;
+  auto fail = [&](int st) {
+    release(c, (uint8_t**)&tmp);
+    release(c, &words);
+    release(c, &jboff);
+    release(c, &ibkt);
+    release(c, &c->runoff);
+    release(c, &c->off);
+    release(c, &c->col);
+    return st;
+  };
+  int st = alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(E > P ? E : P));
+  if (st == PICASSO_OK) st = alloc(c, &c->runoff, E + 1);
+  if (st == PICASSO_OK) st = alloc(c, &c->off, n + 1);
+  if (st == PICASSO_OK) st = alloc(c, &c->col, c->nnz);
+  if (st == PICASSO_OK) st = alloc(c, &words, P);
+  if (st == PICASSO_OK) st = alloc(c, &jboff, P + 1);
+  if (st != PICASSO_OK) return fail(st);
+  cudaError_t e = launch_scan_u32(c->rcnt, E, c->runoff, tmp, s);
+  if (e == cudaSuccess) e = launch_row_offsets(c->runoff, c->loff, n, c->off, s);
+  if (e == cudaSuccess) e = launch_bucket_jblocks(c->bt_bcount, P, words, s);
+  if (e == cudaSuccess) e = launch_scan_u32(words, P, jboff, tmp, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_buf, jboff + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    st = alloc(c, &ibkt, c->h_buf[0] > 0 ? c->h_buf[0] : 1);
+    if (st != PICASSO_OK) return fail(st);
+    e = launch_item_bucket(jboff, P, ibkt, s);
+  }
+  if (e == cudaSuccess) {
+    ConflictArgs a{};
+    a.n = n;
+    a.E = E;
+    a.Lu = c->Lu;
+    a.P = P;
+    a.loff = c->loff;
+    a.ent_v = c->ent_v;
+    a.runoff = c->runoff;
+    a.col = c->col;
+    a.rmask = c->bt_rmask;
+    a.lower = 1;
+    e = launch_bucket_emit(a, c->bt_boff, c->bt_bmem, c->bt_moff, jboff, ibkt, c->d_err + 2, 0, n, 0, s);
+  }
+  if (e != cudaSuccess) {
+    st = map_err(e);
+    if (st == PICASSO_ERR_CUDA) c->sticky = st;
+    return fail(st);
+  }
+  release(c, (uint8_t**)&tmp);
+  release(c, &words);
+  release(c, &jboff);
+  release(c, &ibkt);
+  release(c, &c->rbits);
+  release(c, &c->rpbase);
+  release(c, &c->bt_rmask);
+  release(c, &c->bt_bcount);
+  release(c, &c->bt_boff);
+  release(c, &c->bt_moff);
+  release(c, &c->bt_bmem);
+  release(c, &c->bt_bpid);
+  release(c, &c->rcnt);
+  c->bits = false;
   return PICASSO_OK;
 }
 
@@ -1035,7 +1203,13 @@ int color_round(Ctx* c) {
   a.loff = c->loff;
   a.runoff = c->runoff;
   a.rstart = c->rstart;
-  a.rcnt = c->direct ? c->rcnt : nullptr;
+  a.rcnt = c->direct || c->bits ? c->rcnt : nullptr;
+  if (c->bits) {
+    a.rbits = c->rbits;
+    a.rpbase = c->rpbase;
+    a.rmask = c->bt_rmask;
+    a.bpid = c->bt_bpid;
+  }
   a.col = c->col;
   a.state = c->state;
   a.kcur = kcur;
@@ -1577,6 +1751,7 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
   c->q = q;
   c->qw = (q + 63) / 64;
   c->xz_user = d_xz;
+  c->bits_off = run_layout_env();
   c->n = n;
   c->nsets = nsets;
   c->soff.assign(h_soff, h_soff + nsets + 1);
@@ -1627,6 +1802,13 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
 }  // namespace
 
 namespace picasso {
+bool run_layout_env() {
+  static const bool on = [] {
+    const char* e = std::getenv("PICASSO_RUN_LAYOUT");
+    return e && std::atoi(e) == 1;
+  }();
+  return on;
+}
 int64_t debug_grid(int64_t blocks) {
   static const int64_t div = [] {
     const char* e = std::getenv("PICASSO_GRID_DIVISOR");

@@ -111,6 +111,79 @@ __device__ __forceinline__ bool run_blocked(const ColorArgs& a, int32_t v, uint3
   return false;
 }
 
+// The same scan over a run in the bit layout: row words of partner blocks
+// W = 0 .. slot / 32 (every partner is a member at a smaller slot, ranked
+// before v), kBitsGroup words at a time; lane t holds partner slot 32 W + t,
+// whose vertex id is loaded together with the word, so a group costs one
+// level of loads for the words and ids and one for the partners' states.
+constexpr int kBitsGroup = 4;
+template <bool FRESH>
+__device__ __forceinline__ bool bits_blocked(const ColorArgs& a, uint32_t c, int64_t rb, int32_t pb, int lane,
+                                             int& polls, bool* fail) {
+  const int slot = (int)(rb >> 48);
+  const int64_t w0 = rb & ((int64_t(1) << 48) - 1);
+  const int nW = (slot >> 5) + 1;
+  for (int W0 = 0; W0 < nW;) {
+    uint32_t wd[kBitsGroup];
+    int32_t u[kBitsGroup];
+#pragma unroll
+    for (int j = 0; j < kBitsGroup; ++j) {
+      const int W = W0 + j;
+      const int t = (W << 5) + lane;
+      wd[j] = W < nW ? ld_run<FRESH>(a.rmask + w0 + 32 * (int64_t)W) : 0u;
+      u[j] = t < slot ? ld_run<FRESH>(a.bpid + pb + t) : -1;
+    }
+    uint64_t su[kBitsGroup];
+#pragma unroll
+    for (int j = 0; j < kBitsGroup; ++j) {
+      if (!((wd[j] >> lane) & 1u)) u[j] = -1;
+      su[j] = u[j] >= 0 ? __ldcg(&a.state[u[j]]) : 0ull;
+    }
+    bool lb = false;
+    uint32_t wm[kBitsGroup];
+#pragma unroll
+    for (int j = 0; j < kBitsGroup; ++j) {
+      bool lw = false;
+      if (u[j] >= 0) {
+        const uint32_t wu = (uint32_t)su[j], st = wu & 3u, cu = wu >> 2;
+        lb = lb || (st == kColored && cu == c);
+        lw = st == kUndecided && cu <= c;
+      }
+      wm[j] = __ballot_sync(0xffffffffu, lw);
+    }
+    if (__any_sync(0xffffffffu, lb)) return true;
+    int jw = -1;
+#pragma unroll
+    for (int j = kBitsGroup - 1; j >= 0; --j)
+      if (wm[j]) jw = j;
+    if (jw < 0) {
+      W0 += kBitsGroup;
+      continue;
+    }
+    // wait for the first partner holding us up, then rescan from its word
+    uint32_t m = 0u;
+    int32_t uw = -1;
+#pragma unroll
+    for (int j = 0; j < kBitsGroup; ++j)
+      if (j == jw) {
+        m = wm[j];
+        uw = u[j];
+      }
+    const int32_t wu_id = __shfl_sync(0xffffffffu, uw, __ffs(m) - 1);
+    while (true) {
+      const uint32_t w = (uint32_t)__ldcg(&a.state[wu_id]);
+      if ((w & 3u) != kUndecided || (w >> 2) > c) break;
+      if (++polls > a.max_polls) {
+        *fail = true;
+        return true;
+      }
+      __nanosleep(64);
+    }
+    W0 += jw;
+  }
+  return false;
+}
+
 // One vertex.  The run offsets and colors of 32 candidates are loaded at
 // once (lane k holds candidate k's).  With colored lists (a.clist),
 // kListBatch candidates at a time are first checked against the vertices
@@ -137,8 +210,14 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
   for (int kb = 0; kb < L; kb += 32) {
     const int kl = kb + lane;
     int64_t my_rs = 0, my_re = 0;
+    int32_t my_pb = 0;
     if (kl < L) {
-      if (a.rcnt) {
+      if (a.rbits) {
+        // bit layout: rs = the row address, re - rs = the run length
+        my_rs = ld_run<FRESH>(a.rbits + row + kl);
+        my_pb = ld_run<FRESH>(a.rpbase + row + kl);
+        my_re = ld_run<FRESH>(a.rcnt + row + kl);
+      } else if (a.rcnt) {
         my_rs = ld_run<FRESH>(a.rstart + row + kl);
         my_re = my_rs + ld_run<FRESH>(a.rcnt + row + kl);
       } else {
@@ -177,7 +256,13 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
         const int64_t re = __shfl_sync(0xffffffffu, my_re, kk);
         if (kb + kk > 0 && lane == 0) publish(a.state, v, (c << 2) | kUndecided);
         bool fail = false;
-        const bool blk = run_blocked<FRESH>(a, v, pv, c, rs, re - rs, lane, polls, &fail);
+        bool blk;
+        if (a.rbits) {
+          const int32_t pb = __shfl_sync(0xffffffffu, my_pb, kk);
+          blk = re != 0 && bits_blocked<FRESH>(a, c, rs, pb, lane, polls, &fail);
+        } else {
+          blk = run_blocked<FRESH>(a, v, pv, c, rs, re - rs, lane, polls, &fail);
+        }
         if (fail) {
           if (lane == 0) atomicExch(err, 1);
           return false;

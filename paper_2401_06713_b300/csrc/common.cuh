@@ -206,6 +206,9 @@ void count_launches(int k);
 // (a debugging aid: every such kernel gives the same output at any grid
 // size, so runs at different divisors must agree bit for bit).
 int64_t debug_grid(int64_t blocks);
+// PICASSO_RUN_LAYOUT=1 at load: per-round builds write the run layout (the
+// fused pass) instead of the bit layout.
+bool run_layout_env();
 
 // ---------------------------------------------------------------------------
 // Launchers (host functions defined in the kernel .cu files).
@@ -237,6 +240,8 @@ cudaError_t launch_assign_lists(int32_t round, const int32_t* gid, int64_t n, co
 // scan_tmp_bytes(n) bytes.
 size_t scan_tmp_bytes(int64_t n);
 cudaError_t launch_scan_u32(const uint32_t* in, int64_t n, int64_t* out, void* tmp, cudaStream_t s);
+// *out = sum of the n counts (out zeroed first).
+cudaError_t launch_sum_u32(const uint32_t* in, int64_t n, int64_t* out, cudaStream_t s);
 
 // Conflict build.  Run k of row v is runoff[loff[v] + k] .. runoff[loff[v]+k+1].
 struct ConflictArgs {
@@ -266,6 +271,12 @@ struct ConflictArgs {
   int64_t cap;                    // entries col holds
   const uint4* bxz;               // [E] member words in bucket-slot order (x lo, x hi, z lo, z hi)
   const int32_t* bpid;            // [E] member vertex ids in bucket-slot order
+  // bit layout (launch_bucket_bits): entry e, member i of bucket b, has
+  // rbits[e] = (moff[b] + word offset of row i's block-0 word) | i << 48 and
+  // rpbase[e] = boff[b]; row i's word for partner block W is at
+  // rmask[(rbits[e] & (2^48 - 1)) + 32 W], bit t of it = partner slot 32 W + t
+  int64_t* rbits;                 // [E]
+  int32_t* rpbase;                // [E]
 };
 
 // Buckets: members of color c are bmem[boff[c] .. boff[c+1]) ascending; a
@@ -291,6 +302,13 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
 constexpr int kFusedMax = 512;
 cudaError_t launch_bucket_fused(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, int32_t smax,
                                 int32_t q, cudaStream_t s);
+// The bit pass (EARLIER form, buckets of at most kFusedMax members, one word
+// per part): pair tests as in the fused pass from the gathered members
+// (a.bxz), the lower blocks to a.rmask + moff[b], run lengths to a.cnt and
+// each entry's row address to a.rbits / a.rpbase.  No run is written: the
+// coloring reads the bits, the canonical CSR is made from them on request.
+cudaError_t launch_bucket_bits(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
+                               int32_t smax, int32_t q, cudaStream_t s);
 // bxz[p], bpid[p]: words and vertex id of the member at bucket slot p < E.
 // The warp sort of every bucket (all of at most 512 members) and, by the
 // same warp, the gather of launch_bucket_gather (fused pass).
@@ -322,6 +340,15 @@ struct ColorArgs {
   int64_t v0;              // ordered pass: position t is vertex v0 + t (a chunk of the round)
   const int64_t* rstart;   // direct layout (rcnt set): run of e is rstart[e] .. + rcnt[e]
   const uint32_t* rcnt;
+  // bit layout (rbits set; ConflictArgs gives the encoding): the run of
+  // entry e is the set bits of its row words rmask[(rbits[e] & (2^48 - 1))
+  // + 32 W], W <= slot / 32, slot = rbits[e] >> 48; bit t of word W is the
+  // member at bucket slot 32 W + t, vertex bpid[rpbase[e] + 32 W + t];
+  // rcnt[e] holds the run's length
+  const int64_t* rbits;
+  const int32_t* rpbase;
+  const uint32_t* rmask;
+  const int32_t* bpid;
   const int32_t* col;
   uint64_t* state;  // [n] priority << 32 | state word
   uint16_t* kcur;   // [n] index of the current candidate in the list

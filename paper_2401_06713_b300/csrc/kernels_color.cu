@@ -133,13 +133,47 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
       return;
     }
     const uint32_t c = (uint32_t)a.lists[row + k];
-    const int64_t rs = a.rcnt ? a.rstart[row + k] : a.runoff[row + k] - a.cbase;
-    const int64_t r1 = a.rcnt ? rs + a.rcnt[row + k] : a.runoff[row + k + 1] - a.cbase;
     bool blocked = false;
     int64_t first_wait = -1;
     int32_t wait_u = -1;
+    int64_t rs = 0, r1 = 0;
+    if (a.rbits) {
+      // bit layout: cur counts resolved partner slots; every partner is
+      // ranked before v
+      const int64_t rb = a.rbits[row + k];
+      const int32_t pb = a.rpbase[row + k];
+      const int slot = (int)(rb >> 48);
+      const int64_t w0 = rb & ((int64_t(1) << 48) - 1);
+      r1 = a.rcnt[row + k] ? slot : 0;
+      for (int64_t W = cur >> 5; (W << 5) < r1; ++W) {
+        const int64_t t = (W << 5) + lane;
+        const uint32_t wd = a.rmask[w0 + 32 * W];
+        int32_t u = -1;
+        if (t < slot && ((wd >> lane) & 1u)) u = a.bpid[pb + t];
+        bool lb = false, lw = false;
+        if (u >= 0) {
+          const uint32_t wu = (uint32_t)__ldcg(&a.state[u]);
+          const uint32_t st = wu & 3u, cu = wu >> 2;
+          lb = st == kColored && cu == c;
+          lw = st == kUndecided && cu <= c;
+        }
+        if (__any_sync(0xffffffffu, lb)) {
+          blocked = true;
+          break;
+        }
+        const uint32_t wm = __ballot_sync(0xffffffffu, lw);
+        if (wm && first_wait < 0) {
+          const int src = __ffs(wm) - 1;
+          first_wait = (W << 5) + src;
+          wait_u = __shfl_sync(0xffffffffu, u, src);
+        }
+      }
+    } else {
+      rs = a.rcnt ? a.rstart[row + k] : a.runoff[row + k] - a.cbase;
+      r1 = a.rcnt ? rs + a.rcnt[row + k] : a.runoff[row + k + 1] - a.cbase;
+    }
     // the run of c: the neighbours that hold c
-    for (int64_t e0 = rs + cur; e0 < r1; e0 += 32) {
+    for (int64_t e0 = rs + cur; !a.rbits && e0 < r1; e0 += 32) {
       const int64_t e = e0 + lane;
       bool lb = false, lw = false;
       int32_t u = -1;

@@ -222,6 +222,7 @@ namespace {
 
 constexpr int kMaskThreads = 256;
 constexpr int kMaskWarps = kMaskThreads / 32;
+constexpr int kMaskPlain = 0, kMaskRuns = 1, kMaskBits = 2;  // k_bucket_mask modes
 constexpr int kTabWords = 32 * 16;  // one warp's tables: 32 chunks x 16 entries
 constexpr int kEmitThreads = 256;
 
@@ -366,10 +367,17 @@ __device__ __forceinline__ void emit_rows(const uint32_t* __restrict__ wbuf, con
   }
 }
 
-template <int QW, bool LOWER, bool FUSED>
+// MODE: kMaskPlain (members read through bmem and the strings; blocks and
+// counts to HBM), kMaskRuns (members gathered in slot order and prefetched;
+// blocks kept in shared memory and every bucket's runs written at once, the
+// direct run layout) or kMaskBits (members gathered and prefetched; the lower
+// blocks, counts and each entry's row address go to HBM: the bit layout).
+template <int QW, bool LOWER, int MODE>
 __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a, const int64_t* __restrict__ boff,
                                                               const int32_t* __restrict__ bmem,
                                                               const int64_t* __restrict__ moff, int smax) {
+  constexpr bool FUSED = MODE == kMaskRuns;       // runs written from shared memory
+  constexpr bool STAGED = MODE != kMaskPlain;     // gathered, prefetched members
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* p = smem_raw;
   uint4* w4 = (uint4*)p;
@@ -416,13 +424,13 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     for (int i = threadIdx.x; i < s; i += kMaskThreads) {
       cp_async16(w4s + i, a.bxz + o + i);
       cp_async4(sfls + i, bmem + o + i);
-      cp_async4(pids + i, a.bpid + o + i);
+      if (FUSED) cp_async4(pids + i, a.bpid + o + i);
     }
     cp_async_commit();
   };
   int64_t o_nx = 0;
   int s_nx = 0;
-  if (FUSED && blockIdx.x < a.P) {
+  if (STAGED && blockIdx.x < a.P) {
     o_nx = boff[blockIdx.x];
     s_nx = (int)(boff[blockIdx.x + 1] - o_nx);
     fetch(o_nx, s_nx);
@@ -432,7 +440,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     int s;
     int64_t o2 = 0;
     int s2 = 0;
-    if (FUSED) {
+    if (STAGED) {
       const int64_t b2 = b + gridDim.x;
       if (b2 < a.P) {
         o2 = boff[b2];
@@ -452,7 +460,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       for (int i = threadIdx.x; i < s; i += kMaskThreads) {
         w4[i] = w4s[i];
         sfl[i] = sfls[i];
-        pid[i] = pids[i];
+        if (FUSED) pid[i] = pids[i];
         cnt[i] = 0;
       }
     } else {
@@ -526,8 +534,19 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     __syncthreads();
     // the next bucket's members go to the staging area (the bit columns and
     // tables are done with) while this one's runs are written
-    if (FUSED) fetch(o2, s2);
+    if (STAGED) fetch(o2, s2);
     for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
+    if (MODE == kMaskBits) {
+      // entry of member i: the address of its row's word for partner block 0
+      // (the word for block W lies 32 W words further) with i in the top 16
+      // bits, and the bucket's first slot
+      for (int i = threadIdx.x; i < s; i += kMaskThreads) {
+        const int R = i >> 5;
+        const int64_t w0 = moff[b] + (int64_t)(R * (R + 1) / 2) * 32 + (i & 31);
+        a.rbits[sfl[i]] = w0 | ((int64_t)i << 48);
+        a.rpbase[sfl[i]] = (int32_t)o;
+      }
+    }
     if (FUSED) {
       // run offsets inside the bucket: each thread scans two consecutive rows
       const int i0 = 2 * threadIdx.x;
@@ -588,12 +607,12 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       }
     }
     __syncthreads();
-    if (FUSED) {
+    if (STAGED) {
       o_nx = o2;
       s_nx = s2;
     }
   }
-  if (FUSED) cp_async_wait_all();
+  if (STAGED) cp_async_wait_all();
 }
 
 // Mask pass for strings of more than one word per part (q > 64): the
@@ -830,6 +849,27 @@ static cudaError_t launch_mask_wide(const ConflictArgs& a, const int64_t* boff, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_bucket_bits(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
+                               int32_t smax, int32_t q, cudaStream_t s) {
+  if (a.P <= 0 || a.n <= 0) return cudaSuccess;
+  if (smax > kFusedMax || !a.lower || a.qw != 1) return cudaErrorInvalidValue;
+  smax = max(smax, 1);
+  const size_t bytes = mask_smem_bytes(smax);
+  auto kern = q <= 32 ? k_bucket_mask<1, true, kMaskBits> : k_bucket_mask<2, true, kMaskBits>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMaskThreads, bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = debug_grid(std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1)));
+  kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, moff, smax);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
                                int32_t smax, int32_t q, cudaStream_t s) {
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
@@ -844,8 +884,8 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
     return cudaErrorInvalidValue;
   }
   const size_t bytes = mask_smem_bytes(smax);
-  auto kern = q <= 32 ? (a.lower ? k_bucket_mask<1, true, false> : k_bucket_mask<1, false, false>)
-                      : (a.lower ? k_bucket_mask<2, true, false> : k_bucket_mask<2, false, false>);
+  auto kern = q <= 32 ? (a.lower ? k_bucket_mask<1, true, kMaskPlain> : k_bucket_mask<1, false, kMaskPlain>)
+                      : (a.lower ? k_bucket_mask<2, true, kMaskPlain> : k_bucket_mask<2, false, kMaskPlain>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -885,7 +925,7 @@ cudaError_t launch_bucket_fused(const ConflictArgs& a, const int64_t* boff, cons
   if (smax > kFusedMax || !a.lower) return cudaErrorInvalidValue;
   smax = max(smax, 1);
   const size_t bytes = fused_smem_bytes(smax);
-  auto kern = q <= 32 ? k_bucket_mask<1, true, true> : k_bucket_mask<2, true, true>;
+  auto kern = q <= 32 ? k_bucket_mask<1, true, kMaskRuns> : k_bucket_mask<2, true, kMaskRuns>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

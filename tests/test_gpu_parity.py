@@ -185,8 +185,14 @@ def test_conflict_fused_large_buckets(pc, orc, P, lo, hi):
         _, nnz = p.build_conflicts()
         st = p.stats()
         assert lo <= st["max_bucket"] <= hi
-        # only the fused pass counts 4 bytes per run entry + 36 per list entry
-        assert st["emit_launches"] == 1 and st["emit_bytes"] == 4 * nnz + 36 * n * L
+        # the bit pass (the per-round default for buckets of at most 512
+        # members) counts 36 bytes per list entry and 4 per word of the
+        # buckets' lower blocks: 32 nwb (nwb + 1) / 2 words, nwb = ceil(s / 32)
+        _, lists, _ = p.round_state()
+        sizes = np.bincount(lists.cpu().numpy().ravel(), minlength=P).astype(np.int64)
+        nwb = (sizes + 31) // 32
+        words = int((16 * nwb * (nwb + 1)).sum())
+        assert st["emit_launches"] == 1 and st["emit_bytes"] == 4 * words + 36 * n * L
 
 
 @pytest.mark.parametrize("P,palette,alpha", [(450, (3, 80), 1.8)])
