@@ -30,11 +30,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_DEFAULT, Q, P_W, NUM, DEN, ALPHA = 1_000_000, 64, 0.25, 1, 16, 1.5
-# DRAM bytes (read + write) per algorithmic byte of the fused build pass
-# (k_bucket_mask<.., fused>: pair tests and CSR runs in one kernel), from one ncu
-# capture of round 1 of the n = 200,000 case of this workload (the bench's
-# launches are too large to capture): 1.496 GB measured / 1.337 GB algorithmic.
-FUSED_DRAM_PER_ALG_BYTE = 1.119
+# DRAM bytes (read + write) per algorithmic byte of the bit pass
+# (k_bucket_mask<.., bits>: every color bucket's pair tests, its lower blocks of
+# pair bits to HBM), from one ncu capture of round 1 of the n = 200,000 case of
+# this workload (the bench's launches are too large to capture).
+BITS_DRAM_PER_ALG_BYTE = None
 METRIC = "pair tests/s (conflict build) and colored strings/s at n=1M; colors, peak bytes"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -326,32 +326,35 @@ def run_gpu(args):
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2032.0)
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    # The dominant kernel is the fused build pass: it tests every pair of a
-    # color bucket and writes the bucket's conflict runs.  Primary roofline:
-    # its algorithmic bytes (CSR runs 4 B per entry; per list entry the member
-    # words 16 B, entry and vertex ids 8 B, run start and length 12 B) per launch over
-    # its event time, against the measured HBM copy peak.  Secondary: its pair
-    # tests against one POPC per pair (16 lanes/clk/SM).  A run small enough
-    # for the small-round engine alone has no per-round build: no figures then.
-    launches_b = max(st["emit_launches"], 1)
-    avg_ms = st["t_emit_ms"] / launches_b
-    bytes_launch = st["emit_bytes"] / launches_b
-    gbs = bytes_launch / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
-    roofline = {"bound": "hbm", "kernel": "k_bucket_mask<fused> (pair tests + CSR runs)",
-                "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": gbs / peaks["hbm_gbs"] if gbs and peaks.get("hbm_gbs") else None,
-                "traffic": FUSED_DRAM_PER_ALG_BYTE * bytes_launch if gbs else None,
-                "traffic_note": "bytes per launch, scaled from an ncu capture of round 1 at n=200000",
-                "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": bytes_launch,
-                "launches_per_step": st["emit_launches"]}
+    # The dominant kernel is the bit pass of the conflict build: it tests every
+    # pair of a color bucket (nibble tables over the symplectic words) and
+    # writes G_c as the bucket's lower blocks of pair bits.  It is bound by the
+    # pair tests, not by HBM: primary roofline = its pair tests per launch over
+    # its event time against one POPC per pair (16 lanes/clk/SM at the clock
+    # measured under load).  Secondary: its algorithmic bytes (per list entry
+    # 16 B member words, 4 B entry id, 4 B run length, 12 B row address and
+    # bucket start; 4 B per word of bit blocks) against the HBM copy peak.  A
+    # run small enough for the small-round engine alone has no per-round
+    # build: no figures then.
+    launches_b = max(st["pairs_launches"], 1)
+    avg_ms = st["t_pairs_ms"] / launches_b
+    pairs_launch = st["tested_pairs"] / launches_b
     peak_pairs = n_sm * sm_mhz * 1e6 * 16
-    achieved = st["tested_pairs"] / (st["t_pairs_ms"] / 1e3) if st["t_pairs_ms"] > 0 else None
-    roofline_pairs = {"bound": "alu", "kernel": "k_bucket_mask<fused> (pair tests)",
-                      "achieved": achieved / 1e9 if achieved else None,
-                      "peak": peak_pairs / 1e9, "unit": "Gpair-tests/s",
-                      "frac": achieved / peak_pairs if achieved else None,
-                      "peak_source": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median under load) x 16 POPC/clk/SM",
-                      "tested_pairs_per_launch": st["tested_pairs"] / max(st["pairs_launches"], 1)}
+    achieved = pairs_launch / (avg_ms / 1e3) if avg_ms > 0 else None
+    bytes_launch = st["emit_bytes"] / max(st["emit_launches"], 1)
+    roofline = {"bound": "alu", "kernel": "k_bucket_mask<bits> (pair tests; G_c as bucket bit blocks)",
+                "achieved": achieved / 1e9 if achieved else None, "peak": peak_pairs / 1e9,
+                "unit": "Gpair-tests/s", "frac": achieved / peak_pairs if achieved else None,
+                "peak_source": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median under load) x 16 POPC/clk/SM",
+                "traffic": BITS_DRAM_PER_ALG_BYTE * bytes_launch if (achieved and BITS_DRAM_PER_ALG_BYTE) else None,
+                "traffic_note": "DRAM bytes per launch, scaled from an ncu capture of round 1 at n=200000",
+                "avg_launch_ms": avg_ms, "tested_pairs_per_launch": pairs_launch,
+                "launches_per_step": st["pairs_launches"]}
+    gbs = bytes_launch / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
+    roofline_hbm = {"bound": "hbm", "kernel": "k_bucket_mask<bits>", "achieved": gbs,
+                    "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": gbs / peaks["hbm_gbs"] if gbs and peaks.get("hbm_gbs") else None,
+                    "algorithmic_bytes_per_launch": bytes_launch}
 
     batch = None if args.no_batch else bench_batch(rank)
     learned_form = None if args.no_learned else bench_learned(rank)
@@ -382,7 +385,7 @@ def run_gpu(args):
         "pair_tests_per_s": pair_rate, "colors": int(len(np.unique(colors_np))),
         "colors_sum_P": st["colors_used"], "rounds": rounds,
         "peak_bytes": st["peak_bytes"], "breakdown_ms_per_step": per_step,
-        "roofline": roofline, "roofline_pairs": roofline_pairs, "chunked": chunked, "host_csr": host_csr, "dynamic": dynamic, "wide": wide, "cpu_baseline": cpu, "cpu_runs": cpu_runs, "batch": batch, "learned": learned_form, "learned_beta": learned_beta,
+        "roofline": roofline, "roofline_hbm": roofline_hbm, "chunked": chunked, "host_csr": host_csr, "dynamic": dynamic, "wide": wide, "cpu_baseline": cpu, "cpu_runs": cpu_runs, "batch": batch, "learned": learned_form, "learned_beta": learned_beta,
         "e2e": {"value": whole_job_rate(n, world, ms_e2e / args.steps), "unit": "strings/s",
                 "h2d_bytes_per_step": n * Q, "d2h_bytes_per_step": 4 * n,
                 "overlap": "each step's upload on a copy stream during the previous step"},

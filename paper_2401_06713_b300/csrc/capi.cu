@@ -1013,6 +1013,7 @@ int canonical_bits(Ctx* c) {
     a.col = c->col;
     a.rmask = c->bt_rmask;
     a.lower = 1;
+    a.rowmajor = 1;
     e = launch_bucket_emit(a, c->bt_boff, c->bt_bmem, c->bt_moff, jboff, ibkt, c->d_err + 2, 0, n, 0, s);
   }
   if (e != cudaSuccess) {
@@ -1209,6 +1210,7 @@ int color_round(Ctx* c) {
     a.rpbase = c->rpbase;
     a.rmask = c->bt_rmask;
     a.bpid = c->bt_bpid;
+    a.rstride = 1;  // a row's words are consecutive
   }
   a.col = c->col;
   a.state = c->state;
@@ -1217,9 +1219,16 @@ int color_round(Ctx* c) {
   a.blk = blk;
   a.blkw = blkw;
   a.ranked = 1;  // round-local ids are ranks in coloring order
-  TRY(alloc(c, &clist, kClistWords * c->Ptot));
-  TRYC(cudaMemsetAsync(clist, 0, sizeof(uint32_t) * kClistWords * c->Ptot, s));
-  a.clist = clist;
+  if (c->bits) {
+    // the ordered pass of the bit layout reads the buckets' masks
+    TRY(alloc(c, &clist, 32 * c->Ptot));
+    TRYC(cudaMemsetAsync(clist, 0, sizeof(uint32_t) * 32 * c->Ptot, s));
+    a.cmask = clist;
+  } else {
+    TRY(alloc(c, &clist, kClistWords * c->Ptot));
+    TRYC(cudaMemsetAsync(clist, 0, sizeof(uint32_t) * kClistWords * c->Ptot, s));
+    a.clist = clist;
+  }
   a.xz = c->xz_r;
   a.qw = c->qw;
   a.max_polls = c->max_polls();
@@ -1524,7 +1533,11 @@ int run_small(Ctx* c) {
   a.part = part;
   a.err = err;
   a.ctl = ctl;
-  TRYC(launch_small_rounds(a, kPartCap, s));
+  // rounds of at most small_cluster_maxn() vertices run in one cluster
+  static int cl_blocks[3] = {-1, -1, -1};
+  if (cl_blocks[c->qw] < 0) cl_blocks[c->qw] = small_cluster_blocks(c->qw);
+  a.handoff = small_cluster_maxn();
+  TRYC(launch_small_rounds(a, kPartCap, a.handoff > 0 ? cl_blocks[c->qw] : 0, s));
   TRYC(cudaMemcpyAsync(h, ctl, sizeof(int64_t) * 9, cudaMemcpyDeviceToHost, s));
   TRYC(cudaMemcpyAsync(hs.data(), d_sw, sizeof(int64_t) * 3 * ns, cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
@@ -1802,6 +1815,13 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
 }  // namespace
 
 namespace picasso {
+int64_t small_cluster_maxn() {
+  static const int64_t v = [] {
+    const char* e = std::getenv("PICASSO_CLUSTER_MAXN");
+    return e ? (int64_t)std::atoll(e) : kSmallClusterMaxN;
+  }();
+  return v;
+}
 bool run_layout_env() {
   static const bool on = [] {
     const char* e = std::getenv("PICASSO_RUN_LAYOUT");

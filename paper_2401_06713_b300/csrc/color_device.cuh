@@ -130,7 +130,7 @@ __device__ __forceinline__ bool bits_blocked(const ColorArgs& a, uint32_t c, int
     for (int j = 0; j < kBitsGroup; ++j) {
       const int W = W0 + j;
       const int t = (W << 5) + lane;
-      wd[j] = W < nW ? ld_run<FRESH>(a.rmask + w0 + 32 * (int64_t)W) : 0u;
+      wd[j] = W < nW ? ld_run<FRESH>(a.rmask + w0 + a.rstride * (int64_t)W) : 0u;
       u[j] = t < slot ? ld_run<FRESH>(a.bpid + pb + t) : -1;
     }
     uint64_t su[kBitsGroup];
@@ -285,5 +285,117 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
   return true;
 }
 
+
+// ---------------------------------------------------------------------------
+// Mask coloring (bit layout).  Bucket c keeps two 512-bit masks over its
+// member slots: colored (the member took c) and resolved (the member will
+// never take c: it passed c or took another color).  For vertex v and its
+// candidate c with row bits r (the earlier members of bucket c that commute
+// with v):
+//   r & colored != 0                 c is taken by an earlier neighbour;
+//   r & ~(colored | resolved) == 0   no earlier neighbour can still take c:
+//                                    v takes c (first fit);
+//   otherwise                        v waits (bounded) for those members.
+// A vertex publishes its passes (resolved bits) before it waits and, once
+// decided, its color (colored bit) and every other list color (resolved),
+// so each bit only ever changes from 0 to 1 and a decision taken from any
+// value read is final.  Candidates are examined kMaskCands at a time: lanes
+// 16 h .. 16 h + 15 hold words 0..15 of one candidate's row and masks.
+// ---------------------------------------------------------------------------
+constexpr int kMaskCands = 8;
+
+// Mark list entries [from, to) of v (row = loff[v]) except `skip`: resolved.
+__device__ __forceinline__ void mask_resolve(const ColorArgs& a, int64_t row, int from, int to, int skip, int lane) {
+  for (int t = from + lane; t < to; t += 32) {
+    if (t == skip) continue;
+    const uint32_t c = (uint32_t)__ldg(a.lists + row + t);
+    const int slot = (int)(__ldg(a.rbits + row + t) >> 48);
+    atomicOr(a.cmask + (size_t)c * 32 + 16 + (slot >> 5), 1u << (slot & 31));
+  }
+}
+
+__device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
+  const int64_t row = __ldg(a.loff + v);
+  const int L = (int)(__ldg(a.loff + v + 1) - row);
+  const int64_t lo48 = (int64_t(1) << 48) - 1;
+  const int h = lane >> 4, W = lane & 15;
+  int polls = 0;
+  int kdone = 0;  // entries [0, kdone) passed and marked resolved
+  for (int kb = 0; kb < L; kb += 32) {
+    const int kl = kb + lane;
+    uint32_t my_c = 0u;
+    int64_t my_rb = 0;
+    if (kl < L) {
+      my_c = (uint32_t)__ldg(a.lists + row + kl);
+      my_rb = __ldg(a.rbits + row + kl);
+    }
+    const int kend = min(L - kb, 32);
+    for (int k0 = 0; k0 < kend; k0 += kMaskCands) {
+      uint32_t rw[kMaskCands / 2], cw[kMaskCands / 2], sw[kMaskCands / 2];
+#pragma unroll
+      for (int p = 0; p < kMaskCands / 2; ++p) {
+        const int kk = k0 + 2 * p + h;
+        const uint32_t c = __shfl_sync(0xffffffffu, my_c, min(kk, 31));
+        const int64_t rb = __shfl_sync(0xffffffffu, my_rb, min(kk, 31));
+        const bool act = kk < kend && W <= (int)(rb >> 53);  // W <= slot / 32
+        rw[p] = act ? __ldg(a.rmask + (rb & lo48) + (int64_t)a.rstride * W) : 0u;
+        cw[p] = act ? __ldcg(a.cmask + (size_t)c * 32 + W) : 0u;
+        sw[p] = act ? __ldcg(a.cmask + (size_t)c * 32 + 16 + W) : 0u;
+      }
+      uint32_t blockedm = 0u, pendm = 0u;  // bit j: candidate k0 + j
+#pragma unroll
+      for (int p = 0; p < kMaskCands / 2; ++p) {
+        const uint32_t bb = __ballot_sync(0xffffffffu, (rw[p] & cw[p]) != 0u);
+        const uint32_t pp = __ballot_sync(0xffffffffu, (rw[p] & ~(cw[p] | sw[p])) != 0u);
+        blockedm |= ((bb & 0xffffu) ? 1u : 0u) << (2 * p) | ((bb >> 16) ? 1u : 0u) << (2 * p + 1);
+        pendm |= ((pp & 0xffffu) ? 1u : 0u) << (2 * p) | ((pp >> 16) ? 1u : 0u) << (2 * p + 1);
+      }
+#pragma unroll 1
+      for (int j = 0; j < kMaskCands; ++j) {
+        const int kk = k0 + j;
+        if (kk >= kend) break;
+        if ((blockedm >> j) & 1u) continue;
+        // earlier candidates are passed: say so before waiting or deciding
+        mask_resolve(a, row, kdone, kb + kk, -1, lane);
+        kdone = kb + kk;
+        bool blocked = false;
+        if ((pendm >> j) & 1u) {
+          // wait for the earlier neighbours that may still take c
+          const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
+          const int64_t rb = __shfl_sync(0xffffffffu, my_rb, kk);
+          const bool act = lane < 16 && lane <= (int)(rb >> 53);
+          const uint32_t r = act ? __ldg(a.rmask + (rb & lo48) + (int64_t)a.rstride * lane) : 0u;
+          while (true) {
+            const uint32_t cc = act ? __ldcg(a.cmask + (size_t)c * 32 + lane) : 0u;
+            const uint32_t ss = act ? __ldcg(a.cmask + (size_t)c * 32 + 16 + lane) : 0u;
+            if (__any_sync(0xffffffffu, (r & cc) != 0u)) {
+              blocked = true;
+              break;
+            }
+            if (!__any_sync(0xffffffffu, (r & ~(cc | ss)) != 0u)) break;
+            if (++polls > a.max_polls) {
+              if (lane == 0) atomicExch(err, 1);
+              return false;
+            }
+            __nanosleep(64);
+          }
+        }
+        if (blocked) continue;
+        // v takes c: colored bit, every other list color resolved
+        const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
+        const int slot = (int)(__shfl_sync(0xffffffffu, my_rb, kk) >> 48);
+        mask_resolve(a, row, kdone, L, kb + kk, lane);
+        if (lane == 0) {
+          atomicOr(a.cmask + (size_t)c * 32 + (slot >> 5), 1u << (slot & 31));
+          publish(a.state, v, (c << 2) | kColored);
+        }
+        return true;
+      }
+    }
+  }
+  mask_resolve(a, row, kdone, L, -1, lane);
+  if (lane == 0) publish(a.state, v, (kFailedColor << 2) | kFailed);
+  return true;
+}
 
 }  // namespace picasso

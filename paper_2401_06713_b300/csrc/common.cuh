@@ -209,6 +209,9 @@ int64_t debug_grid(int64_t blocks);
 // PICASSO_RUN_LAYOUT=1 at load: per-round builds write the run layout (the
 // fused pass) instead of the bit layout.
 bool run_layout_env();
+// Rounds of at most this many vertices go to the engine's cluster launch
+// (kSmallClusterMaxN; PICASSO_CLUSTER_MAXN at load, 0: never).
+int64_t small_cluster_maxn();
 
 // ---------------------------------------------------------------------------
 // Launchers (host functions defined in the kernel .cu files).
@@ -271,12 +274,15 @@ struct ConflictArgs {
   int64_t cap;                    // entries col holds
   const uint4* bxz;               // [E] member words in bucket-slot order (x lo, x hi, z lo, z hi)
   const int32_t* bpid;            // [E] member vertex ids in bucket-slot order
-  // bit layout (launch_bucket_bits): entry e, member i of bucket b, has
-  // rbits[e] = (moff[b] + word offset of row i's block-0 word) | i << 48 and
-  // rpbase[e] = boff[b]; row i's word for partner block W is at
-  // rmask[(rbits[e] & (2^48 - 1)) + 32 W], bit t of it = partner slot 32 W + t
+  // bit layout (launch_bucket_bits): bucket b's lower blocks are stored
+  // row-major at rmask + moff[b]: row i (block R = i / 32) has R + 1 words,
+  // word W's bit t = partner slot 32 W + t (< i) commutes with i.  Entry e,
+  // member i of bucket b, has rbits[e] = (moff[b] + 16 R (R + 1) + (i % 32)
+  // (R + 1)) | i << 48, the address of row i, and rpbase[e] = boff[b]
   int64_t* rbits;                 // [E]
   int32_t* rpbase;                // [E]
+  int32_t rowmajor;               // emit pass: a.rmask holds the bit layout's row-major
+                                  // rows (row r of block R at 16 R (R + 1) + r (R + 1))
 };
 
 // Buckets: members of color c are bmem[boff[c] .. boff[c+1]) ascending; a
@@ -349,6 +355,11 @@ struct ColorArgs {
   const int32_t* rpbase;
   const uint32_t* rmask;
   const int32_t* bpid;
+  int32_t rstride;      // bit layout: words between a row's word W and W + 1
+  // mask coloring (bit layout; null: off): per bucket color c, 32 words at
+  // 32 c, zero at the start of the round: words 0..15 mark the members
+  // (by slot) colored c, words 16..31 those that will never take c
+  uint32_t* cmask;
   const int32_t* col;
   uint64_t* state;  // [n] priority << 32 | state word
   uint16_t* kcur;   // [n] index of the current candidate in the list
@@ -486,12 +497,20 @@ struct SmallArgs {
                           //      host-initialised), 6 sum of nnz, 7 sum over the sets of
                           //      n_k (n_k - 1) / 2 (6, 7 zero on entry), 3, 5, 8 scratch
   int32_t max_polls;      // polls of one bounded wait before the engine gives up
+  int64_t handoff;        // grid launch: stop (kSmallHandoff) at a round of at most
+                          // this many vertices, for the cluster launch
 };
 
 // Stop reasons in ctl[2].
-constexpr int64_t kSmallOk = 0, kSmallTimeout = 1, kSmallOverflow = 2, kSmallMaxRounds = 3;
-// part_cap: words of a.part; the launch uses at most that many blocks.
-cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, cudaStream_t s);
+constexpr int64_t kSmallOk = 0, kSmallTimeout = 1, kSmallOverflow = 2, kSmallMaxRounds = 3, kSmallHandoff = 4;
+// Rounds of at most this many vertices run in one thread-block cluster.
+constexpr int64_t kSmallClusterMaxN = 2048;
+// part_cap: words of a.part; the launch uses at most that many blocks.  The
+// grid launch runs the rounds above a.handoff vertices, then (cluster_blocks
+// > 0) one cluster of cluster_blocks blocks the rest, back to back on s.
+cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_blocks, cudaStream_t s);
+// Blocks of the largest cluster the engine can launch (16, 8, 4 or 2), 0 if none.
+int small_cluster_blocks(int32_t qw);
 
 // Alg. 2's dynamic order, parallel rule (kernels_dynamic.cu).  Rows are the
 // two-sided canonical ones; lists of at most 64 colors.

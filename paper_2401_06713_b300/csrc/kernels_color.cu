@@ -147,7 +147,7 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
       r1 = a.rcnt[row + k] ? slot : 0;
       for (int64_t W = cur >> 5; (W << 5) < r1; ++W) {
         const int64_t t = (W << 5) + lane;
-        const uint32_t wd = a.rmask[w0 + 32 * W];
+        const uint32_t wd = a.rmask[w0 + a.rstride * W];
         int32_t u = -1;
         if (t < slot && ((wd >> lane) & 1u)) u = a.bpid[pb + t];
         bool lb = false, lw = false;
@@ -326,11 +326,24 @@ __global__ void __launch_bounds__(256, 6) k_color_ordered(ColorArgs a, const int
   }
 }
 
+// The ordered pass of the bit layout with the buckets' masks (mask_vertex);
+// vertices in rank order (ranked ids), one warp each.
+__global__ void __launch_bounds__(256, 6) k_color_masks(ColorArgs a, int32_t* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t t = wid; t < a.n; t += gwarps) {
+    if (!mask_vertex(a, (int32_t)(a.v0 + t), lane, err)) return;
+  }
+}
+
 cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32_t* err, cudaStream_t s) {
   int dev = 0, sms = 148, per_sm = 0;
+  const bool masks = a.cmask != nullptr;
+  const void* kern = masks ? (const void*)k_color_masks : (const void*)k_color_ordered;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_color_ordered, 256, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   int64_t blocks = (int64_t)per_sm * sms;
@@ -338,8 +351,13 @@ cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32
   if (want < blocks) blocks = want > 0 ? want : 1;
   blocks = debug_grid(blocks);
   ColorArgs args = a;
-  void* params[] = {(void*)&args, (void*)&order, (void*)&err};
-  e = cudaLaunchCooperativeKernel((const void*)k_color_ordered, dim3((unsigned)blocks), dim3(256), params, 0, s);
+  if (masks) {
+    void* params[] = {(void*)&args, (void*)&err};
+    e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)blocks), dim3(256), params, 0, s);
+  } else {
+    void* params[] = {(void*)&args, (void*)&order, (void*)&err};
+    e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)blocks), dim3(256), params, 0, s);
+  }
   count_launches(1);
   return e;
 }

@@ -234,6 +234,15 @@ __host__ __device__ inline size_t mask_smem_bytes(int smax) {
          sizeof(uint32_t) * ((size_t)nwb * 128 + 64 + (size_t)kMaskWarps * kTabWords);
 }
 
+// The bit pass keeps a bucket's lower blocks row-major in shared memory: row
+// r of block R at rm_pad_off(R) + r ((R + 1) | 1) + W (odd row strides, so a
+// warp's 32 rows hit 32 banks), then copies them to HBM row-major without
+// the padding: row r of block R at 16 R (R + 1) + r (R + 1).
+__host__ __device__ inline int rm_pad_off(int R) { return 32 * (R * (R + 1) / 2 + R / 2); }
+__host__ __device__ inline size_t bits_smem_bytes(int smax) {
+  return mask_smem_bytes(smax) + sizeof(uint32_t) * (size_t)rm_pad_off((smax + 31) >> 5);
+}
+
 // The fused pass adds, per member, its vertex id and run offset, and the
 // bucket's lower mask blocks (nwb (nwb + 1) / 2 blocks of 32 words).
 __host__ __device__ inline size_t fused_smem_bytes(int smax) {
@@ -390,6 +399,11 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   int32_t* pid = nullptr;
   uint32_t* roff = nullptr;
   uint32_t* mw = nullptr;
+  uint32_t* mwp = nullptr;
+  if (MODE == kMaskBits) {
+    mwp = (uint32_t*)p;
+    p += sizeof(uint32_t) * (size_t)rm_pad_off((smax + 31) >> 5);
+  }
   if (FUSED) {
     pid = (int32_t*)p;
     p += align16(sizeof(int32_t) * smax);
@@ -518,6 +532,8 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       if (I == J) cw &= LOWER ? ((1u << lane) - 1u) : ~(1u << lane);
       if (FUSED)
         mw[mask_block(true, J, I, nwb) * 32 + lane] = cw;
+      else if (MODE == kMaskBits)
+        mwp[rm_pad_off(J) + lane * ((J + 1) | 1) + I] = cw;
       else
         rmb[mask_block(LOWER, J, I, nwb) * 32 + lane] = cw;
       if (cw) atomicAdd(&cnt[j], __popc(cw));
@@ -537,14 +553,24 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     if (STAGED) fetch(o2, s2);
     for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
     if (MODE == kMaskBits) {
-      // entry of member i: the address of its row's word for partner block 0
-      // (the word for block W lies 32 W words further) with i in the top 16
-      // bits, and the bucket's first slot
+      // entry of member i: the address of its row's first word (the row's
+      // R + 1 words are consecutive) with i in the top 16 bits, and the
+      // bucket's first slot
       for (int i = threadIdx.x; i < s; i += kMaskThreads) {
         const int R = i >> 5;
-        const int64_t w0 = moff[b] + (int64_t)(R * (R + 1) / 2) * 32 + (i & 31);
+        const int64_t w0 = moff[b] + 16 * R * (R + 1) + (i & 31) * (R + 1);
         a.rbits[sfl[i]] = w0 | ((int64_t)i << 48);
         a.rpbase[sfl[i]] = (int32_t)o;
+      }
+      // the rows to HBM, row-major: warp per row block, 32 words a step
+      for (int R = wid; R < nwb; R += kMaskWarps) {
+        const uint32_t d = (uint32_t)(R + 1), m = (65536u + d - 1u) / d, sp = d | 1u;
+        const uint32_t* src = mwp + rm_pad_off(R);
+        uint32_t* dst = rmb + 16 * R * (R + 1);
+        for (uint32_t o = lane; o < 32u * d; o += 32u) {
+          const uint32_t r = (o * m) >> 16, w = o - r * d;  // o = r d + w, exact for o < 4096 / d
+          dst[o] = src[r * sp + w];
+        }
       }
     }
     if (FUSED) {
@@ -854,7 +880,7 @@ cudaError_t launch_bucket_bits(const ConflictArgs& a, const int64_t* boff, const
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   if (smax > kFusedMax || !a.lower || a.qw != 1) return cudaErrorInvalidValue;
   smax = max(smax, 1);
-  const size_t bytes = mask_smem_bytes(smax);
+  const size_t bytes = bits_smem_bytes(smax);
   auto kern = q <= 32 ? k_bucket_mask<1, true, kMaskBits> : k_bucket_mask<2, true, kMaskBits>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
@@ -1043,7 +1069,8 @@ __global__ void __launch_bounds__(kEmitThreads) k_bucket_emit(ConflictArgs a, co
       for (int t = 0; t < kEmitChunk; ++t) {
         pv[t] = 0;
         if (t < nI) {
-          wbuf[t * 32 + lane] = __ldg(rmb + (blk0 + I0 + t) * 32 + lane);
+          wbuf[t * 32 + lane] = a.rowmajor ? __ldg(rmb + 16 * J * (J + 1) + lane * (J + 1) + I0 + t)
+                                           : __ldg(rmb + (blk0 + I0 + t) * 32 + lane);
           const int pi = ((I0 + t) << 5) + lane;
           if (pi < s) {
             const int32_t f = __ldg(bmem + o + pi);

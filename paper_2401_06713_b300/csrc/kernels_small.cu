@@ -82,19 +82,32 @@ __device__ __forceinline__ int64_t block_excl(int64_t x, int64_t* sm, int64_t* t
   return before + inc - x;
 }
 
+// Barrier of every thread of the launch: the cooperative grid's, or, when
+// the launch is one thread-block cluster (CL), the cluster's hardware
+// barrier (release / acquire at cluster scope, which covers global memory
+// written by the cluster's blocks).
+template <bool CL>
+__device__ __forceinline__ void engine_sync() {
+  if constexpr (CL) {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  } else {
+    cg::this_grid().sync();
+  }
+}
+
 // Exclusive scan of in[0..m) into out[0..m] (out[m] = the total) by the
 // whole grid: block b scans the b-th contiguous chunk after adding the sums
 // of the chunks before it (part: one word per block).  Contains a grid
 // barrier; every thread of the grid must call it.
-template <class TI>
-__device__ void grid_scan(cg::grid_group& grid, const TI* in, int64_t m, int64_t* out, int64_t* part, int64_t* sm) {
+template <bool CL, class TI>
+__device__ void grid_scan(const TI* in, int64_t m, int64_t* out, int64_t* part, int64_t* sm) {
   const int64_t chunk = (m + gridDim.x - 1) / gridDim.x;
   const int64_t lo = min(m, chunk * (int64_t)blockIdx.x), hi = min(m, lo + chunk);
   int64_t x = 0;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) x += (int64_t)in[i];
   x = block_sum(x, sm);
   if (threadIdx.x == 0) part[blockIdx.x] = x;
-  grid.sync();
+  engine_sync<CL>();
   int64_t pre = 0;
   for (int64_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += __ldcg(part + b);
   pre = block_sum(pre, sm);
@@ -250,9 +263,8 @@ __device__ void bucket_runs(const SmallArgs& a, int32_t* R, uint64_t* X, int lan
   __syncwarp();
 }
 
-template <int W>
+template <int W, bool CL>
 __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_rounds(SmallArgs a) {
-  cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ int64_t scan_s[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -265,8 +277,10 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
   const int64_t stid = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
   const int nsets = a.nsets;
 
+  // the cluster launch takes over from a grid launch that handed off
+  if (CL && gtid == 0 && a.ctl[2] == kSmallHandoff) a.ctl[2] = kSmallOk;
   if (blockIdx.x == 0) set_prefixes(a, scan_s);
-  grid.sync();
+  engine_sync<CL>();
 
   while (true) {
     const int64_t n = __ldcg(a.ctl + 0);
@@ -274,8 +288,14 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     const int32_t round = a.round0 + (int32_t)done;
     if (n == 0 || __ldcg(a.ctl + 2) != kSmallOk) break;
     if (round > a.max_rounds) {
-      grid.sync();
+      engine_sync<CL>();
       if (gtid == 0) a.ctl[2] = kSmallMaxRounds;
+      break;
+    }
+    if (!CL && n <= a.handoff) {
+      // small enough for one cluster: its barriers cost far less
+      engine_sync<CL>();
+      if (gtid == 0) a.ctl[2] = kSmallHandoff;
       break;
     }
     const int32_t* gid = __ldcg(a.ctl + 4) ? a.gid_b : a.gid_a;
@@ -295,7 +315,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     }
     for (int64_t t = gtid; t < kClistWords * P; t += gthreads) a.clist[t] = 0;
     if (gtid == 0) a.err[1] = 0;
-    grid.sync();
+    engine_sync<CL>();
 
     // rank of vertex i = its set's offset + the number of smaller keys in the
     // set: warp per vertex, lanes over the set; the round's arrays are
@@ -316,7 +336,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         for (int k = 0; k < 2 * W; ++k) a.xz_r[2 * W * rk + k] = a.xz[2 * W * (int64_t)g + k];
       }
     }
-    grid.sync();
+    engine_sync<CL>();
 
     // lists in rank order (bucket colors: + the set's offset), list offsets,
     // entry owners, first candidates (the ranked coloring reads no priority
@@ -338,16 +358,16 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     if (gtid == 0) a.loff[n] = E;
     // bucket work items (32 members each); a bucket above the cap stops the
     // engine
-    grid.sync();
+    engine_sync<CL>();
     for (int64_t c = gtid; c < P; c += gthreads) {
       const uint32_t sc = a.bcnt[c];
       a.bitems[c] = (sc + 31) / 32;
       if (sc > (uint32_t)kSmallBucketCap) a.err[2] = 1;
     }
-    grid_scan(grid, a.bcnt, P, a.boff, a.part, scan_s);
-    grid.sync();
-    grid_scan(grid, a.bitems, P, a.iboff, a.part, scan_s);
-    grid.sync();
+    grid_scan<CL>(a.bcnt, P, a.boff, a.part, scan_s);
+    engine_sync<CL>();
+    grid_scan<CL>(a.bitems, P, a.iboff, a.part, scan_s);
+    engine_sync<CL>();
     if (__ldcg(a.err + 2) != 0) {
       if (gtid == 0) a.ctl[2] = kSmallOverflow;
       break;
@@ -360,7 +380,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     for (int64_t c = gtid; c < P; c += gthreads)
       for (int64_t t = a.iboff[c]; t < a.iboff[c + 1]; ++t) a.ibkt[t] = (int32_t)c;
     if (gtid == 0) a.ctl[8] = a.iboff[P];
-    grid.sync();
+    engine_sync<CL>();
 
     // each bucket ascending (entries ascend with the rank), then its
     // members' ranks and words in that order
@@ -376,12 +396,12 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         for (int k = 0; k < 2 * W; ++k) a.bxz[2 * W * (b0 + i) + k] = a.xz_r[2 * W * (int64_t)r + k];
       }
     }
-    grid.sync();
+    engine_sync<CL>();
 
     bucket_runs<W, false>(a, Rw, Xw, lane, gwarp, nwarps);
-    grid.sync();
-    grid_scan(grid, a.cnt, E, a.runoff, a.part, scan_s);
-    grid.sync();
+    engine_sync<CL>();
+    grid_scan<CL>(a.cnt, E, a.runoff, a.part, scan_s);
+    engine_sync<CL>();
     {
       const int64_t nnz = __ldcg(a.runoff + E);
       const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
@@ -392,7 +412,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       if (gtid == 0) a.ctl[6] += nnz;
     }
     bucket_runs<W, true>(a, Rw, Xw, lane, gwarp, nwarps);
-    grid.sync();
+    engine_sync<CL>();
 
     // ordered first fit in rank order; warps take ranks from a counter
     {
@@ -417,7 +437,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         ok = ordered_vertex<true>(ca, t, lane, a.err);
       }
     }
-    grid.sync();
+    engine_sync<CL>();
     if (__ldcg(a.err) != 0) {
       if (gtid == 0) a.ctl[2] = kSmallTimeout;
       break;
@@ -434,9 +454,9 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       }
       a.flag[a.perm[r]] = colored ? 0u : 1u;
     }
-    grid.sync();
-    grid_scan(grid, a.flag, n, a.pos, a.part, scan_s);
-    grid.sync();
+    engine_sync<CL>();
+    grid_scan<CL>(a.flag, n, a.pos, a.part, scan_s);
+    engine_sync<CL>();
     for (int64_t i = gtid; i < n; i += gthreads)
       if (a.flag[i]) gid_next[a.pos[i]] = gid[i];
     if (blockIdx.x == 0) {
@@ -464,7 +484,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       __syncthreads();
       set_prefixes(a, scan_s);
     }
-    grid.sync();
+    engine_sync<CL>();
   }
 }
 
@@ -472,30 +492,85 @@ size_t small_smem_bytes(int32_t qw) {
   return (size_t)kSmallWarps * (qw == 2 ? warp_smem_bytes<2>() : warp_smem_bytes<1>());
 }
 
-cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, cudaStream_t s) {
+// The grid launch (cooperative, up to kSmallBlocksPerSm blocks per SM) runs
+// the rounds above a.handoff vertices; the cluster launch (one cluster of
+// cluster_blocks blocks) runs the rest.  `cluster_blocks` 0: no cluster
+// launch (the grid launch runs every round).
+cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_blocks, cudaStream_t s) {
   int dev = 0, sms = 148, per_sm = 0;
   if (a.qw != 1 && a.qw != 2) return cudaErrorInvalidValue;
   const size_t smem = small_smem_bytes(a.qw);
-  auto kern = a.qw == 2 ? k_small_rounds<2> : k_small_rounds<1>;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmallThreads, smem);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-  // fewer resident blocks make each grid barrier cheaper; two per SM keep
-  // 16 warps per SM for the latency-bound phases
-  int blocks = std::min(per_sm, kSmallBlocksPerSm) * sms;
-  blocks = std::min(blocks, part_cap);
-  blocks = (int)debug_grid(blocks);
   SmallArgs args = a;
-  void* params[] = {(void*)&args};
-  e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)blocks), dim3(kSmallThreads), params,
-                                  smem, s);
+  if (cluster_blocks <= 0) args.handoff = 0;
+  const bool grid_rounds = cluster_blocks <= 0 || a.n0 > args.handoff;
+  if (grid_rounds) {
+    auto kern = a.qw == 2 ? k_small_rounds<2, false> : k_small_rounds<1, false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmallThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    // fewer resident blocks make each grid barrier cheaper; two per SM keep
+    // 16 warps per SM for the latency-bound phases
+    int blocks = std::min(per_sm, kSmallBlocksPerSm) * sms;
+    blocks = std::min(blocks, part_cap);
+    blocks = (int)debug_grid(blocks);
+    void* params[] = {(void*)&args};
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)blocks), dim3(kSmallThreads), params,
+                                    smem, s);
+    count_launches(1);
+    if (e != cudaSuccess) return e;
+  }
+  if (cluster_blocks <= 0) return cudaSuccess;
+  auto kern = a.qw == 2 ? k_small_rounds<2, true> : k_small_rounds<1, true>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && cluster_blocks > 8)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)std::min(cluster_blocks, part_cap);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(attr[0].val.clusterDim.x);
+  cfg.blockDim = dim3(kSmallThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, args);
   count_launches(1);
   return e;
+}
+
+// Largest cluster (16, 8, 4, 2 blocks) the engine's cluster launch can have
+// resident on this device, 0 if none.
+int small_cluster_blocks(int32_t qw) {
+  if (qw != 1 && qw != 2) return 0;
+  const size_t smem = small_smem_bytes(qw);
+  auto kern = qw == 2 ? k_small_rounds<2, true> : k_small_rounds<1, true>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+  for (int k = 16; k >= 2; k >>= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)k;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(k);
+    cfg.blockDim = dim3(kSmallThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc >= 1) return k;
+    cudaGetLastError();
+  }
+  return 0;
 }
 
 }  // namespace picasso
