@@ -70,7 +70,8 @@ def whole_job_rate(units_per_rank, world, ms_per_step):
 def workload(n):
     return {"workload": f"picasso n={n} q={Q} p={P_W} P=n/{DEN} alpha={ALPHA}", "n": n, "q": Q,
             "weight_p": P_W, "palette": f"{NUM}/{DEN}", "alpha": ALPHA, "seed": "rank",
-            "l2": "working set > L2 (round-1 conflict CSR is ~14 GB); no explicit flush"}
+            "l2": "working set > L2 (round 1 alone writes 0.53 GB of bit rows and reads and writes ~1 GB of "
+                  "bucket members and per-entry words); no explicit flush"}
 
 
 class Clocks:
@@ -332,8 +333,8 @@ def run_gpu(args):
     # pair tests, not by HBM: primary roofline = its pair tests per launch over
     # its event time against one POPC per pair (16 lanes/clk/SM at the clock
     # measured under load).  Secondary: its algorithmic bytes (per list entry
-    # 16 B member words, 4 B entry id, 4 B run length, 12 B row address and
-    # bucket start; 4 B per word of bit blocks) against the HBM copy peak.  A
+    # 16 B member words and 4 B entry id read, 8 B row address, slot and run
+    # length written; 4 B per word of bit rows) against the HBM copy peak.  A
     # run small enough for the small-round engine alone has no per-round
     # build: no figures then.
     launches_b = max(st["pairs_launches"], 1)
@@ -422,8 +423,8 @@ def bench_batch(rank, nsets=256):
     seeds = [rank * 100003 + k for k in range(nsets)]
     parts = [xz[offs[k]:offs[k + 1]].contiguous() for k in range(nsets)]
 
-    def batched():
-        with picasso.Picasso(xz, 64, set_offsets=offs, seeds=seeds) as p:
+    def batched(schedule=None):
+        with picasso.Picasso(xz, 64, set_offsets=offs, seeds=seeds, schedule=schedule) as p:
             return p.run()[0]
 
     def sequential():
@@ -447,10 +448,33 @@ def bench_batch(rank, nsets=256):
     torch.cuda.synchronize()
     tb, ts = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
     same = all(torch.equal(cb[offs[k]:offs[k + 1]], cs[k]) for k in range(nsets))
+    # the library's autotuner picks the launch schedule for this batch; then
+    # the median of 5 batched runs under it and under the defaults
+    t0 = time.perf_counter()
+    sched, tuned_med, start_med = picasso.autotune(xz, 64, set_offsets=offs, seeds=seeds, reps=3)
+    tune_s = time.perf_counter() - t0
+
+    def med5(schedule):
+        ts_ = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c = batched(schedule)
+            e1.record()
+            torch.cuda.synchronize()
+            ts_.append(e0.elapsed_time(e1))
+        return sorted(ts_)[2], c
+
+    t_def, _ = med5(None)
+    t_tuned, ct = med5(sched)
+    same = same and torch.equal(ct, cb)
     return {"workload": f"{nsets} sets, n log-uniform [1e3, 5e4], q in {{16,24,32,48,64}}, p in U[0.1,0.5], "
                         f"P=n/8, alpha=2", "strings": offs[-1], "batched_ms": tb, "sequential_ms": ts,
             "batched_strings_per_s": offs[-1] / (tb / 1e3), "sequential_strings_per_s": offs[-1] / (ts / 1e3),
-            "speedup": ts / tb, "identical_colors": same}
+            "speedup": ts / tb, "identical_colors": same,
+            "autotune": {"schedule": sched, "tuning_s": tune_s, "median_ms_default_schedule": t_def,
+                         "median_ms_tuned_schedule": t_tuned, "tuner_median_ms_start": start_med,
+                         "tuner_median_ms_best": tuned_med}}
 
 
 def bench_dynamic(rank, codes, st_static):
@@ -671,6 +695,29 @@ def bench_cpu_runs(rank, threads=None):
             r == rounds and np.array_equal(colors.cpu().numpy(), ref)),
             "oracle_s": cpu_s, "oracle_strings_per_s": n / cpu_s, "cores": threads,
             "gpu_ms": gpu_ms, "gpu_strings_per_s": n / (gpu_ms / 1e3)})
+    # Alg. 2 on the benchmark's law at n = 20,000: the oracle's sequential
+    # loop and its parallel rule, which the GPU computes exactly; the sums
+    # of P show what the parallel reading costs in colors
+    chars = synth.pauli_weighted(20_000, Q, P_W, seed=rank)
+    sums, secs = {}, {}
+    for colorer in ("dynamic", "dynamic_par", "static"):
+        t0 = time.perf_counter()
+        oc, orounds, ost = oracle.run(chars, rank, NUM, DEN, ALPHA, threads=threads, colorer=colorer)
+        secs[colorer] = time.perf_counter() - t0
+        sums[colorer] = int(ost[:, 1].sum())
+        if colorer == "dynamic_par":
+            par = (oc, orounds)
+    xz = picasso.pack(torch.from_numpy(chars).cuda())
+    with picasso.Picasso(xz, Q, seed=rank, palette=(NUM, DEN), alpha=ALPHA, color="dynamic") as p:
+        colors, r = p.run()
+        gsum = p.stats()["colors_used"]
+    out.append({"workload": f"n=20000 q={Q} p={P_W} P=n/{DEN} alpha={ALPHA}, Alg. 2 dynamic order",
+                "oracle_colors_sum_P": {"sequential_alg2": sums["dynamic"], "parallel_rule": sums["dynamic_par"],
+                                        "static_random_order": sums["static"]},
+                "oracle_s": {"sequential_alg2": secs["dynamic"], "parallel_rule": secs["dynamic_par"],
+                             "static_random_order": secs["static"]},
+                "gpu_parallel_rule_colors_sum_P": gsum, "cores": threads,
+                "identical_colors": bool(r == par[1] and np.array_equal(colors.cpu().numpy(), par[0]))})
     return out
 
 

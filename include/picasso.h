@@ -73,6 +73,33 @@ typedef enum {
   PICASSO_CONFLICT_BUCKET = 2    /* pairs joined through per-color buckets   */
 } picasso_conflict_algo;
 
+/* Launch schedule of the kernels whose shape changes no result (colors,
+ * CSRs, rounds and stats other than times are the same under every
+ * schedule): the small-round engine's grid, the rounds it gives to one
+ * thread-block cluster, and the blocks per SM of the bit pass and of the
+ * mask coloring.  All zero = the library's defaults.  picasso_autotune picks
+ * one for a workload by timing candidates on it.  The paper has no
+ * counterpart (its kernels have one launch shape).                          */
+typedef struct {
+  int32_t engine_blocks_per_sm; /* grid launch of the small-round engine:
+                                   1 or 2 blocks of 256 threads per SM
+                                   (0: 2)                                    */
+  int32_t cluster_max_n;        /* engine rounds of at most this many
+                                   vertices run in one thread-block cluster
+                                   (0: 2048; -1: never; else 1 .. 16384)     */
+  int32_t cluster_blocks;       /* blocks of that cluster: 2, 4, 8 or 16 (0:
+                                   the largest that fits); more than fit is
+                                   clamped to the largest that fits         */
+  int32_t bits_blocks_per_sm;   /* bit pass of the build: 1 .. 4 blocks of 256
+                                   threads per SM (0: the occupancy limit;
+                                   more than the limit is clamped)           */
+  int32_t color_blocks_per_sm;  /* mask coloring: 1 .. 8 blocks of 256 per SM
+                                   (0: the occupancy limit; clamped to it)   */
+  int32_t engine_max_n;         /* picasso_run hands the rounds to the small-
+                                   round engine from a round of at most this
+                                   many vertices (0: 16384; else 1 .. 16384) */
+} picasso_schedule;
+
 typedef struct {
   uint64_t seed;         /* Philox key                                        */
   int64_t palette_num;   /* P_l = max(1, ceil(n_l * num / den))  (Table I)    */
@@ -93,6 +120,7 @@ typedef struct {
                             the sweep kernel (per-round path) or handed back to
                             the per-round path (engine); same colors either
                             way.  0 = 1,048,576; 1 <= wait_polls <= 2^30    */
+  picasso_schedule sched; /* launch schedule (all zero: defaults)            */
 } picasso_config;
 
 /* What picasso_round / picasso_run do with a round whose conflict CSR would
@@ -195,7 +223,7 @@ typedef struct {
   double t_color_ms;    /* coloring sweeps + color write-back                */
   double t_carry_ms;    /* compaction of the uncolored vertices              */
   double t_pairs_ms;    /* the pair-test kernels alone (bucket join: mask
-                           pass, or the fused pass; all pairs: count and
+                           pass, or the bit pass; all pairs: count and
                            fill)                                            */
   int64_t pairs_launches;     /* launches of the pair-test kernels           */
   int64_t logical_pairs;      /* sum over builds of n_l (n_l - 1) / 2        */
@@ -204,12 +232,14 @@ typedef struct {
                                  (the mask pass tests each unordered pair of
                                  a bucket once), all pairs 2 n (n - 1)      */
   double t_emit_ms;           /* bucket join's emit pass (CSR writes); with the
-                                 fused pass, that same kernel's time        */
+                                 bit pass, that same kernel's time          */
   int64_t emit_launches;
   int64_t emit_bytes;         /* bytes the emit passes move: mask words read,
                                  CSR written, member ids and run offsets
-                                 read; fused pass: CSR written, member words,
-                                 ids, run starts and lengths                */
+                                 read; bit pass: 28 per list entry (member
+                                 words and entry ids read, one word of row
+                                 address, slot and run length written) and 4
+                                 per word of bit rows written               */
   int64_t nnz_total;          /* run entries of all builds                  */
   /* the last color step's first 64 sweeps: vertices pending at the start,
    * vertices re-evaluated, and duration in microseconds (0 for the last) */
@@ -221,6 +251,11 @@ typedef struct {
   double t_small_ms;          /* time in the small-round engine             */
   int32_t round_chunks;       /* chunks of the rounds colored by chunk      */
   int32_t host_csr_rounds;    /* rounds whose columns went to host memory   */
+  int32_t barrier_timeout[4]; /* a grid barrier that gave up (4 s; the call
+                                 returned PICASSO_ERR_TIMEOUT): kernel (1
+                                 small-round engine, 2 sweep coloring, 3
+                                 dynamic order; 0 none), its site, round or
+                                 step, and the blocks that had arrived      */
 } picasso_stats;
 
 /* Fill *cfg with the defaults: seed 0, P = n/8, alpha = 2 (the paper's normal
@@ -239,7 +274,7 @@ int picasso_pack(const uint8_t* d_codes, int64_t n, int32_t q, uint64_t* d_xz,
  * cudaStream_t (NULL = legacy default stream).  Round 1 starts with V_1 =
  * all n strings, all colors -1.  Strings of q > 64 (Sec. VII's larger
  * systems) take the same rounds; their conflict pass forms each pair's
- * symplectic product over all words (no fused run writes); the small-round
+ * symplectic product over all words (no bit layout); the small-round
  * engine takes strings of up to 128 qubits.                                */
 int picasso_init(void** ctx, const picasso_config* cfg, const uint64_t* d_xz,
                  int64_t n, int32_t q, void* stream);
@@ -269,13 +304,15 @@ int picasso_assign_lists(void* ctx, int64_t P, int32_t L, int64_t base);
 /* Alg. 1 conflict-graph construction (Sec. III-A, Alg. 3's count / offsets /
  * fill structure).  Synchronises to size the CSR; returns ERR_BUDGET, before
  * allocating, if the CSR would exceed cfg.byte_budget.
- * With the EARLIER form, no byte budget and color buckets of at most 512
- * members, one fused pass tests the pairs and writes the runs, each bucket's
- * runs as one contiguous region (the library's direct layout, read by
- * picasso_color).  The canonical row-major CSR described by picasso_csr is
- * made from it when asked for: by a non-NULL out here, or by
- * picasso_get_runs / picasso_copy_csr / picasso_copy_runs (which then
- * allocate it and synchronise).  out may be NULL.                          */
+ * With the EARLIER form, no byte budget, strings of at most 64 qubits and
+ * color buckets of at most 512 members, one pass tests the pairs of every
+ * color bucket and stores G_c as the bucket's lower blocks of pair bits (the
+ * library's bit layout: bit t of row i's word W says whether member i
+ * commutes with member 32 W + t < i; read by picasso_color).  The canonical
+ * row-major CSR described by picasso_csr is made from it when asked for: by
+ * a non-NULL out here, or by picasso_get_runs / picasso_copy_csr /
+ * picasso_copy_runs (which then allocate it and synchronise).  out may be
+ * NULL.                                                                     */
 int picasso_build_conflicts(void* ctx, picasso_csr* out);
 
 /* Alg. 1 coloring of the unconflicted vertices and of G_c (Sec. III-B static
@@ -294,6 +331,26 @@ int picasso_round(void* ctx, int64_t* n_remaining);
 /* Rounds until every vertex is colored; then copies the global colors to
  * d_color_out [n] (may be NULL) and sets *n_rounds (may be NULL).          */
 int picasso_run(void* ctx, int32_t* d_color_out, int32_t* n_rounds);
+
+/* Autotuner of the launch schedule (picasso_schedule) for a workload of one
+ * or many sets, given as picasso_init_batch takes them (nsets = 1 with
+ * h_set_offsets = {0, n}: one set).  Starting from cfg->sched it tunes one
+ * field at a time, in the order engine_max_n, engine_blocks_per_sm,
+ * cluster_max_n, cluster_blocks, bits_blocks_per_sm, color_blocks_per_sm,
+ * over that field's candidates (16384, 8192, 4096; 1, 2; -1, 512, 2048,
+ * 8192; 16, 8; 4, 3, 2; 6, 4, 3),
+ * keeping the others at their best so far.  Each candidate is one whole
+ * picasso_run of the workload after one untimed run, timed with CUDA events
+ * on `stream`, the median of `reps` (1 .. 64) runs.  The fastest schedule
+ * goes to *best, its time to *best_ms and the time of cfg->sched itself to
+ * *start_ms (either may be NULL).  The colors of every run are compared
+ * with the first run's; a difference is PICASSO_ERR_INTERNAL.  d_xz,
+ * h_set_offsets, h_seeds, q: as picasso_init_batch.  Synchronises; the
+ * device memory it takes comes from the library's pool.  Not in the paper:
+ * it picks launch shapes of this library's kernels.                        */
+int picasso_autotune(const picasso_config* cfg, const uint64_t* d_xz, const int64_t* h_set_offsets,
+                     int32_t nsets, const uint64_t* h_seeds, int32_t q, int32_t reps,
+                     picasso_schedule* best, double* best_ms, double* start_ms, void* stream);
 
 /* Copy the global color array [n] (-1 = not yet colored) to d_out.         */
 int picasso_get_colors(void* ctx, int32_t* d_out);

@@ -191,9 +191,6 @@ struct Ctx {
   int64_t* off = nullptr;
   int32_t* col = nullptr;
   int64_t* runoff = nullptr;
-  // direct layout (fused pass): entry e's run is col[rstart[e] ..
-  // rstart[e] + rcnt[e]); off and runoff are made on request (canonical_csr)
-  bool direct = false;
   // a round over the byte budget in chunk mode: the count pass's buckets and
   // masks kept for the chunked emit (the runs of one chunk at a time)
   bool chunk_pending = false;
@@ -208,17 +205,12 @@ struct Ctx {
   bool col_host = false;  // c->col points into hcol
   int32_t host_rounds = 0;
   bool nvtx_open = false;  // an NVTX phase range is pushed
-  int64_t* rstart = nullptr;
-  uint32_t* rcnt = nullptr;
-  double commute_ratio = 0.6;  // nnz / bucket pair bound of the last fused build
   // bit layout (the bit pass): G_c as every bucket's lower blocks of pair
-  // bits (rmask at moff), each entry's row address (rbits, rpbase), the run
-  // lengths in rcnt and the members in slot order (bt_bmem entries, bt_bpid
-  // vertex ids); the canonical CSR is made from them on request
+  // bits (rmask at moff), each entry's row address, slot and run length
+  // (rinfo) and the members in slot order (bt_bmem entries, bt_bpid vertex
+  // ids); the canonical CSR is made from them on request
   bool bits = false;
-  bool bits_off = false;  // the run layout instead (PICASSO_RUN_LAYOUT=1 at load)
-  int64_t* rbits = nullptr;
-  int32_t* rpbase = nullptr;
+  int64_t* rinfo = nullptr;
   uint32_t* bt_rmask = nullptr;
   uint32_t* bt_bcount = nullptr;
   int64_t *bt_boff = nullptr, *bt_moff = nullptr;
@@ -250,6 +242,9 @@ struct Ctx {
   // round it handed back last (the per-round path takes that one); after a
   // CSR overflow the engine stays off for the context
   int32_t small_rounds = 0, small_stops = 0, small_skip_round = 0;
+  // a bounded grid barrier that timed out: kernel (1 engine, 2 sweep
+  // coloring, 3 dynamic order), its site, round or step, arrivals seen
+  int32_t barrier_timeout[4] = {0, 0, 0, 0};
   bool small_off = false;
   double t_small = 0;
 
@@ -326,11 +321,7 @@ void free_build(Ctx* c) {
     release(c, &c->col);
   }
   release(c, &c->runoff);
-  release(c, &c->rstart);
-  release(c, &c->rcnt);
-  c->direct = false;
-  release(c, &c->rbits);
-  release(c, &c->rpbase);
+  release(c, &c->rinfo);
   release(c, &c->bt_rmask);
   release(c, &c->bt_bcount);
   release(c, &c->bt_boff);
@@ -637,8 +628,13 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
     TRYC(cudaMemsetAsync(bcursor, 0, sizeof(uint32_t) * P, s));
     TRYC(launch_bucket_fill(c->lists, E, boff, bcursor, bmem, s));
     release(c, &bcursor);
-    const bool fused = a.lower && c->cfg.byte_budget == 0 && smax <= kFusedMax && c->qw == 1;
-    if (fused) {
+    // the bit layout: EARLIER form, no byte budget, buckets of at most
+    // kFusedMax members, strings of one word per part
+    // (the bit rows' words, bounded below, must fit rinfo's address field)
+    const int64_t wcap = (bucket_pairs + E + 94 * E + 1953 * P) / 64 + 64;
+    const bool bitl = a.lower && c->cfg.byte_budget == 0 && smax <= kFusedMax && c->qw == 1 &&
+                      wcap < (int64_t(1) << kRinfoAddrBits);
+    if (bitl) {
       // sorted buckets, and the members' words and vertex ids in slot order
       TRY(alloc(c, &bxz, E));
       TRY(alloc(c, &bpid, E));
@@ -646,7 +642,7 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
     } else {
       TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, (int32_t)smax, s));
     }
-    if (fused && !c->bits_off) {
+    if (bitl) {
       // the bit pass: every bucket's lower blocks of pair bits, no run
       // written.  The blocks' words are allocated from a bound, so nothing
       // is read back before the pass: a bucket of s members has
@@ -657,27 +653,24 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
       TRYC(launch_bucket_words(bcount, P, 1, words, s));
       TRYC(launch_scan_u32(words, P, moff, tmp, s));
       release(c, &words);
-      const int64_t wcap = (bucket_pairs + E + 94 * E + 1953 * P) / 64 + 64;
       TRY(alloc(c, &rmask, wcap));
-      TRY(alloc(c, &c->rbits, E));
-      TRY(alloc(c, &c->rpbase, E));
+      TRY(alloc(c, &c->rinfo, E));
+      // the run total: the context's error block, words 2..3
+      unsigned long long* dn = reinterpret_cast<unsigned long long*>(c->d_err + 2);
+      TRYC(cudaMemsetAsync(dn, 0, sizeof(unsigned long long), s));
       a.bxz = bxz;
       a.bpid = bpid;
       a.rmask = rmask;
-      a.rbits = c->rbits;
-      a.rpbase = c->rpbase;
+      a.rinfo = c->rinfo;
+      a.nnz = dn;
       TRYC(cudaEventRecord(c->ev[2], s));
-      TRYC(launch_bucket_bits(a, boff, bmem, moff, (int32_t)smax, c->q, s));
+      TRYC(launch_bucket_bits(a, boff, bmem, moff, (int32_t)smax, c->q, s, c->cfg.sched.bits_blocks_per_sm));
       TRYC(cudaEventRecord(c->ev[3], s));
-      int64_t* dn = reinterpret_cast<int64_t*>(c->d_err + 2);  // the context's error block, words 2..3
-      TRYC(launch_sum_u32(cnt, E, dn, s));
       TRYC(cudaMemcpyAsync(c->h_buf, dn, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
       TRYC(cudaMemcpyAsync(c->h_buf + 1, moff + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
       TRYC(cudaStreamSynchronize(s));
       const int64_t nnz = c->h_buf[0], mwords = c->h_buf[1];
       const float ms = (float)elapsed(c, 2, 3);
-      c->rcnt = cnt;
-      cnt = nullptr;
       c->bt_rmask = rmask;
       c->bt_bcount = bcount;
       c->bt_boff = boff;
@@ -692,7 +685,8 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
       const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
       if (c->nsets > 1) {
         std::vector<int64_t> h(c->nsets);
-        TRYC(launch_set_csr_bytes(c->loff, nullptr, c->rcnt, c->gid_r, n, c->d_soff, c->nsets, c->d_set_bytes, s));
+        TRYC(launch_rinfo_lengths(c->rinfo, E, cnt, s));
+        TRYC(launch_set_csr_bytes(c->loff, nullptr, cnt, c->gid_r, n, c->d_soff, c->nsets, c->d_set_bytes, s));
         TRYC(cudaMemcpyAsync(h.data(), c->d_set_bytes, sizeof(int64_t) * c->nsets, cudaMemcpyDeviceToHost, s));
         TRYC(cudaStreamSynchronize(s));
         for (int k = 0; k < c->nsets; ++k)
@@ -701,86 +695,14 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
         c->set_peak_bytes[0] = std::max(c->set_peak_bytes[0], csr_bytes);
       }
       // the pass tests the pairs and writes G_c: member words and entry ids
-      // read (20 bytes per list entry), the bit blocks (4 bytes per word),
-      // run lengths, row addresses and bucket starts (16 bytes per entry)
+      // read (20 bytes per list entry), the bit rows (4 bytes per word), one
+      // row address, slot and run length word per entry (8 bytes)
       c->t_pairs += ms;
       c->pairs_launches += 1;
       c->tested_pairs += bucket_pairs / 2;
       c->t_emit += ms;
       c->emit_launches += 1;
-      c->emit_bytes += 36 * E + 4 * mwords;
-      for (int k = 0; k < c->nsets; ++k) c->logical_pairs += c->remaining[k] * (c->remaining[k] - 1) / 2;
-      cleanup();
-      c->nnz = nnz;
-      c->nnz_total += nnz;
-      c->built = true;
-      return PICASSO_OK;
-    }
-    if (fused) {
-      // fused mask + emit: the runs of a bucket go to one region claimed from
-      // a cursor.  The column buffer is sized from the bucket pair bound and
-      // the last fused build's commuting ratio; if the runs need more, the
-      // pass ran to the end counting (nothing written past the buffer) and
-      // runs once more with the exact size.
-      const int64_t bound = bucket_pairs / 2;
-      int64_t cap = std::min<int64_t>(bound, (int64_t)(c->commute_ratio * 1.08 * (double)bound) + (int64_t(1) << 20));
-      cap = std::max<int64_t>(cap, 1);
-      // the cursor: the context's error block, words 2..3 (8-byte aligned)
-      unsigned long long* cur = reinterpret_cast<unsigned long long*>(c->d_err + 2);
-      TRY(alloc(c, &c->rstart, E));
-      a.bxz = bxz;
-      a.bpid = bpid;
-      TRY(alloc(c, &c->col, cap));
-      a.rstart = c->rstart;
-      a.col = c->col;
-      a.cursor = cur;
-      a.cap = cap;
-      int64_t nnz = 0;
-      float ms = 0.f;
-      for (int attempt = 0; attempt < 2; ++attempt) {
-        TRYC(cudaMemsetAsync(cur, 0, sizeof(unsigned long long), s));
-        TRYC(cudaEventRecord(c->ev[2], s));
-        TRYC(launch_bucket_fused(a, boff, bmem, (int32_t)smax, c->q, s));
-        TRYC(cudaEventRecord(c->ev[3], s));
-        TRYC(cudaMemcpyAsync(c->h_buf, cur, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        TRYC(cudaStreamSynchronize(s));
-        nnz = c->h_buf[0];
-        ms += (float)elapsed(c, 2, 3);
-        if (nnz <= a.cap) break;
-        release(c, &c->col);
-        TRY(alloc(c, &c->col, nnz));
-        a.col = c->col;
-        a.cap = nnz;
-      }
-      if (nnz > a.cap) {
-        cleanup();
-        return PICASSO_ERR_INTERNAL;
-      }
-      c->commute_ratio = bound > 0 ? (double)nnz / (double)bound : c->commute_ratio;
-      c->rcnt = cnt;  // the run lengths stay with the context
-      cnt = nullptr;
-      c->direct = true;
-      const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
-      if (c->nsets > 1) {
-        std::vector<int64_t> h(c->nsets);
-        TRYC(launch_set_csr_bytes(c->loff, nullptr, c->rcnt, c->gid_r, n, c->d_soff, c->nsets, c->d_set_bytes, s));
-        TRYC(cudaMemcpyAsync(h.data(), c->d_set_bytes, sizeof(int64_t) * c->nsets, cudaMemcpyDeviceToHost, s));
-        TRYC(cudaStreamSynchronize(s));
-        for (int k = 0; k < c->nsets; ++k)
-          if (c->remaining[k] > 0) c->set_peak_bytes[k] = std::max(c->set_peak_bytes[k], h[k] + 8);
-      } else {
-        c->set_peak_bytes[0] = std::max(c->set_peak_bytes[0], csr_bytes);
-      }
-      // one kernel both tests the pairs and writes the runs: its time counts
-      // for the pair tests and for the CSR writes (member words, entry ids,
-      // run starts and lengths, the runs)
-      c->t_pairs += ms;
-      c->pairs_launches += 1;
-      c->tested_pairs += bucket_pairs / 2;
-      c->t_emit += ms;
-      c->emit_launches += 1;
-      // per list entry: member words 16, entry and vertex ids 8, run start 8 and length 4
-      c->emit_bytes += 4 * nnz + 36 * E;
+      c->emit_bytes += 28 * E + 4 * mwords;
       for (int k = 0; k < c->nsets; ++k) c->logical_pairs += c->remaining[k] * (c->remaining[k] - 1) / 2;
       cleanup();
       c->nnz = nnz;
@@ -922,44 +844,12 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
   return PICASSO_OK;
 }
 
-// The canonical CSR of a direct-layout build: run offsets by entry (a scan of
-// the run lengths), row offsets, and the runs moved to row order.  The
-// context keeps the canonical form afterwards.
 int canonical_bits(Ctx* c);
 
+// The canonical CSR of the current build (the bit layout is converted; the
+// other builds already are canonical).
 int canonical_csr(Ctx* c) {
   if (c->built && c->bits) return canonical_bits(c);
-  if (!c->built || !c->direct) return PICASSO_OK;
-  const int64_t n = c->n, E = c->E;
-  cudaStream_t s = c->s;
-  void* tmp = nullptr;
-  int32_t* colc = nullptr;
-  auto fail = [&](int st) {
-    release(c, (uint8_t**)&tmp);
-    release(c, &colc);
-    release(c, &c->runoff);
-    release(c, &c->off);
-    return st;
-  };
-  int st = alloc(c, (uint8_t**)&tmp, (int64_t)scan_tmp_bytes(E));
-  if (st == PICASSO_OK) st = alloc(c, &c->runoff, E + 1);
-  if (st == PICASSO_OK) st = alloc(c, &c->off, n + 1);
-  if (st == PICASSO_OK) st = alloc(c, &colc, c->nnz);
-  if (st != PICASSO_OK) return fail(st);
-  cudaError_t e = launch_scan_u32(c->rcnt, E, c->runoff, tmp, s);
-  if (e == cudaSuccess) e = launch_row_offsets(c->runoff, c->loff, n, c->off, s);
-  if (e == cudaSuccess) e = launch_runs_to_rows(c->rstart, c->rcnt, c->runoff, E, c->col, colc, s);
-  if (e != cudaSuccess) {
-    st = map_err(e);
-    if (st == PICASSO_ERR_CUDA) c->sticky = st;
-    return fail(st);
-  }
-  release(c, (uint8_t**)&tmp);
-  release(c, &c->col);
-  c->col = colc;
-  release(c, &c->rstart);
-  release(c, &c->rcnt);
-  c->direct = false;
   return PICASSO_OK;
 }
 
@@ -971,11 +861,13 @@ int canonical_bits(Ctx* c) {
   cudaStream_t s = c->s;
   void* tmp = nullptr;
   uint32_t* words = nullptr;
+  uint32_t* lens = nullptr;
   int64_t* jboff = nullptr;
   int32_t* ibkt = nullptr;
   auto fail = [&](int st) {
     release(c, (uint8_t**)&tmp);
     release(c, &words);
+    release(c, &lens);
     release(c, &jboff);
     release(c, &ibkt);
     release(c, &c->runoff);
@@ -989,8 +881,10 @@ int canonical_bits(Ctx* c) {
   if (st == PICASSO_OK) st = alloc(c, &c->col, c->nnz);
   if (st == PICASSO_OK) st = alloc(c, &words, P);
   if (st == PICASSO_OK) st = alloc(c, &jboff, P + 1);
+  if (st == PICASSO_OK) st = alloc(c, &lens, E);
   if (st != PICASSO_OK) return fail(st);
-  cudaError_t e = launch_scan_u32(c->rcnt, E, c->runoff, tmp, s);
+  cudaError_t e = launch_rinfo_lengths(c->rinfo, E, lens, s);
+  if (e == cudaSuccess) e = launch_scan_u32(lens, E, c->runoff, tmp, s);
   if (e == cudaSuccess) e = launch_row_offsets(c->runoff, c->loff, n, c->off, s);
   if (e == cudaSuccess) e = launch_bucket_jblocks(c->bt_bcount, P, words, s);
   if (e == cudaSuccess) e = launch_scan_u32(words, P, jboff, tmp, s);
@@ -1025,15 +919,14 @@ int canonical_bits(Ctx* c) {
   release(c, &words);
   release(c, &jboff);
   release(c, &ibkt);
-  release(c, &c->rbits);
-  release(c, &c->rpbase);
+  release(c, &lens);
+  release(c, &c->rinfo);
   release(c, &c->bt_rmask);
   release(c, &c->bt_bcount);
   release(c, &c->bt_boff);
   release(c, &c->bt_moff);
   release(c, &c->bt_bmem);
   release(c, &c->bt_bpid);
-  release(c, &c->rcnt);
   c->bits = false;
   return PICASSO_OK;
 }
@@ -1089,7 +982,7 @@ int color_dynamic(Ctx* c) {
   TRY(alloc(c, &mask, n));
   TRY(alloc(c, &state, n));
   TRY(alloc(c, &colorl, n));
-  TRY(alloc(c, &ctl, 8));
+  TRY(alloc(c, &ctl, kDynCtlWords));
   TRY(alloc(c, &wa, n));
   TRY(alloc(c, &wb, n));
   TRY(alloc(c, &sel, n));
@@ -1134,8 +1027,19 @@ int color_dynamic(Ctx* c) {
   TRYC(launch_scan_u32(c->flag, n, c->pos, tmp, s));
   TRYC(cudaMemcpyAsync(c->h_buf, c->pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   TRYC(cudaMemcpyAsync(c->h_buf + 1, ctl + 6, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  TRYC(cudaMemcpyAsync(c->h_buf + 2, ctl + 10, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
   const int32_t steps = *(const int32_t*)(c->h_buf + 1);
+  if (reinterpret_cast<const int32_t*>(c->h_buf + 2)[0] != 0) {
+    // a grid barrier of the dynamic order gave up: the launch ended mid-step
+    c->barrier_timeout[0] = 3;
+    c->barrier_timeout[1] = 0;
+    c->barrier_timeout[2] = steps;
+    c->barrier_timeout[3] = reinterpret_cast<const int32_t*>(c->h_buf + 2)[1];
+    c->sticky = PICASSO_ERR_TIMEOUT;
+    cleanup();
+    return PICASSO_ERR_TIMEOUT;
+  }
   c->sweeps = steps;
   c->n_remaining = c->h_buf[0];
   c->n_colored = n - c->n_remaining;
@@ -1203,11 +1107,9 @@ int color_round(Ctx* c) {
   a.lists = c->lists;
   a.loff = c->loff;
   a.runoff = c->runoff;
-  a.rstart = c->rstart;
-  a.rcnt = c->direct || c->bits ? c->rcnt : nullptr;
   if (c->bits) {
-    a.rbits = c->rbits;
-    a.rpbase = c->rpbase;
+    a.rinfo = c->rinfo;
+    a.bboff = c->bt_boff;
     a.rmask = c->bt_rmask;
     a.bpid = c->bt_bpid;
     a.rstride = 1;  // a row's words are consecutive
@@ -1251,7 +1153,7 @@ int color_round(Ctx* c) {
   int32_t sweeps = 0;
   bool need_sweeps = c->cfg.color_algo == PICASSO_COLOR_SWEEP;
   if (!need_sweeps) {
-    TRYC(launch_color_ordered(a, nullptr, ctl + 5, s));
+    TRYC(launch_color_ordered(a, nullptr, ctl + 5, s, c->bits ? c->cfg.sched.color_blocks_per_sm : 0));
     TRYC(cudaMemcpyAsync(c->sweep_log, ctl, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s));
     TRYC(enqueue_carry());
     TRYC(cudaStreamSynchronize(s));
@@ -1266,6 +1168,16 @@ int color_round(Ctx* c) {
     TRYC(enqueue_carry());
     TRYC(cudaStreamSynchronize(s));
     sweeps = c->sweep_log[3];
+    if (c->sweep_log[kCtlAbort] != 0) {
+      // a grid barrier of the sweep kernel gave up: the launch ended mid-sweep
+      c->barrier_timeout[0] = 2;
+      c->barrier_timeout[1] = 0;
+      c->barrier_timeout[2] = sweeps;
+      c->barrier_timeout[3] = c->sweep_log[kCtlSeen];
+      c->sticky = PICASSO_ERR_TIMEOUT;
+      cleanup();
+      return PICASSO_ERR_TIMEOUT;
+    }
     if (c->sweep_log[4] != 0 || c->sweep_log[0] != 0) {
       cleanup();
       return PICASSO_ERR_INTERNAL;
@@ -1316,7 +1228,8 @@ int carry_round(Ctx* c) {
 // Whether picasso_run hands the remaining rounds to the small-round engine.
 bool small_eligible(const Ctx* c) {
   const picasso_config& cfg = c->cfg;
-  if (c->n < 1 || c->n > kSmallRoundsMax || cfg.small_engine != PICASSO_SMALL_AUTO || c->qw > 2) return false;
+  const int64_t nmax = cfg.sched.engine_max_n > 0 ? cfg.sched.engine_max_n : kSmallRoundsMax;
+  if (c->n < 1 || c->n > nmax || cfg.small_engine != PICASSO_SMALL_AUTO || c->qw > 2) return false;
   if (cfg.conflict_algo != PICASSO_CONFLICT_AUTO || cfg.color_algo != PICASSO_COLOR_AUTO ||
       cfg.csr_form != PICASSO_CSR_EARLIER)
     return false;
@@ -1390,7 +1303,7 @@ int run_small(Ctx* c) {
   int64_t* iboff = nullptr;
   uint64_t *xz_r = nullptr, *state = nullptr, *key = nullptr;
   int64_t *loff = nullptr, *runoff = nullptr, *pos = nullptr, *part = nullptr, *ctl = nullptr, *boff = nullptr;
-  uint32_t *cnt = nullptr, *flag = nullptr, *bcnt = nullptr, *bcur = nullptr, *clist = nullptr;
+  uint32_t *cnt = nullptr, *flag = nullptr, *bcnt = nullptr, *bcur = nullptr, *clist = nullptr, *sbar = nullptr;
   int st = PICASSO_OK;
   auto cleanup = [&]() {
     release(c, &d_ptab);
@@ -1413,6 +1326,7 @@ int run_small(Ctx* c) {
     release(c, &pos);
     release(c, &part);
     release(c, &ctl);
+    release(c, &sbar);
     release(c, &cnt);
     release(c, &flag);
     release(c, &bcnt);
@@ -1473,7 +1387,8 @@ int run_small(Ctx* c) {
   TRY(alloc(c, &ibkt, E0 / 32 + P0 + 1));
   TRY(alloc(c, &part, kPartCap));
   TRY(alloc(c, &err, 4));
-  TRY(alloc(c, &ctl, 9));
+  TRY(alloc(c, &ctl, kSmallCtlWords));
+  TRY(alloc(c, &sbar, 2));
   TRYC(cudaMemcpyAsync(d_ptab, ptab.data(), sizeof(int2) * (mmax + 1), cudaMemcpyHostToDevice, s));
   TRYC(cudaMemcpyAsync(d_sw, hs.data(), sizeof(int64_t) * hs.size(), cudaMemcpyHostToDevice, s));
   if (c->gid)
@@ -1481,10 +1396,11 @@ int run_small(Ctx* c) {
   else
     TRYC(launch_iota(gid_a, n0, s));
   int64_t* h = c->h_buf;
-  std::memset(h, 0, sizeof(int64_t) * 9);
+  std::memset(h, 0, sizeof(int64_t) * kSmallCtlWords);
   h[0] = n0;
-  TRYC(cudaMemcpyAsync(ctl, h, sizeof(int64_t) * 9, cudaMemcpyHostToDevice, s));
+  TRYC(cudaMemcpyAsync(ctl, h, sizeof(int64_t) * kSmallCtlWords, cudaMemcpyHostToDevice, s));
   TRYC(cudaMemsetAsync(err, 0, sizeof(int32_t) * 4, s));
+  TRYC(cudaMemsetAsync(sbar, 0, sizeof(uint32_t) * 2, s));
   a.n0 = n0;
   a.round0 = c->round;
   a.max_rounds = c->cfg.max_rounds;
@@ -1533,14 +1449,31 @@ int run_small(Ctx* c) {
   a.part = part;
   a.err = err;
   a.ctl = ctl;
-  // rounds of at most small_cluster_maxn() vertices run in one cluster
+  a.bar = sbar;
+  // rounds of at most cluster_max_n vertices run in one cluster of the
+  // largest size that fits (or the schedule's, if smaller)
   static int cl_blocks[3] = {-1, -1, -1};
   if (cl_blocks[c->qw] < 0) cl_blocks[c->qw] = small_cluster_blocks(c->qw);
-  a.handoff = small_cluster_maxn();
-  TRYC(launch_small_rounds(a, kPartCap, a.handoff > 0 ? cl_blocks[c->qw] : 0, s));
-  TRYC(cudaMemcpyAsync(h, ctl, sizeof(int64_t) * 9, cudaMemcpyDeviceToHost, s));
+  const picasso_schedule& sc = c->cfg.sched;
+  a.handoff = sc.cluster_max_n == 0 ? kSmallClusterMaxN : sc.cluster_max_n < 0 ? 0 : sc.cluster_max_n;
+  int clb = cl_blocks[c->qw];
+  if (sc.cluster_blocks > 0) clb = std::min(clb, (int)sc.cluster_blocks);
+  TRYC(launch_small_rounds(a, kPartCap, a.handoff > 0 ? clb : 0, sc.engine_blocks_per_sm, s));
+  TRYC(cudaMemcpyAsync(h, ctl, sizeof(int64_t) * kSmallCtlWords, cudaMemcpyDeviceToHost, s));
+  TRYC(cudaMemcpyAsync(h + kSmallCtlWords, err, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, s));
   TRYC(cudaMemcpyAsync(hs.data(), d_sw, sizeof(int64_t) * 3 * ns, cudaMemcpyDeviceToHost, s));
   TRYC(cudaStreamSynchronize(s));
+  if (reinterpret_cast<const int32_t*>(h + kSmallCtlWords)[3] != 0) {
+    // a grid barrier of the engine timed out: the launch ended in the middle
+    // of a round, so the context cannot go on
+    c->barrier_timeout[0] = 1;
+    c->barrier_timeout[1] = (int32_t)h[9];
+    c->barrier_timeout[2] = (int32_t)h[10];
+    c->barrier_timeout[3] = (int32_t)h[11];
+    c->sticky = PICASSO_ERR_TIMEOUT;
+    cleanup();
+    return PICASSO_ERR_TIMEOUT;
+  }
   const int64_t nleft = h[0], rounds = h[1], stop = h[2], parity = h[4];
   const int64_t sum_nnz = h[6], sum_pairs = h[7];
   // V_l of the round the engine stopped at, and its words
@@ -1737,6 +1670,13 @@ int validate_cfg(const picasso_config* cfg) {
       cfg->small_engine < 0 || cfg->small_engine > 1 || cfg->budget_mode < 0 || cfg->budget_mode > 2 ||
       cfg->wait_polls < 0 || cfg->wait_polls > (1 << 30))
     return PICASSO_ERR_INVALID_ARG;
+  const picasso_schedule& sc = cfg->sched;
+  const int cb = sc.cluster_blocks;
+  if (sc.engine_blocks_per_sm < 0 || sc.engine_blocks_per_sm > 2 || sc.cluster_max_n < -1 ||
+      sc.cluster_max_n > kSmallRoundsMax || !(cb == 0 || cb == 2 || cb == 4 || cb == 8 || cb == 16) ||
+      sc.bits_blocks_per_sm < 0 || sc.bits_blocks_per_sm > 4 || sc.color_blocks_per_sm < 0 ||
+      sc.color_blocks_per_sm > 8 || sc.engine_max_n < 0 || sc.engine_max_n > kSmallRoundsMax)
+    return PICASSO_ERR_INVALID_ARG;
   return PICASSO_OK;
 }
 
@@ -1764,7 +1704,6 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
   c->q = q;
   c->qw = (q + 63) / 64;
   c->xz_user = d_xz;
-  c->bits_off = run_layout_env();
   c->n = n;
   c->nsets = nsets;
   c->soff.assign(h_soff, h_soff + nsets + 1);
@@ -1815,19 +1754,19 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
 }  // namespace
 
 namespace picasso {
-int64_t small_cluster_maxn() {
-  static const int64_t v = [] {
-    const char* e = std::getenv("PICASSO_CLUSTER_MAXN");
-    return e ? (int64_t)std::atoll(e) : kSmallClusterMaxN;
-  }();
-  return v;
+// *diff (zeroed here) = 1 if a and b differ somewhere in [0, n).
+__global__ void k_count_diff(const int32_t* __restrict__ a, const int32_t* __restrict__ b, int64_t n,
+                             int32_t* __restrict__ diff) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (a[i] != b[i]) *diff = 1;
 }
-bool run_layout_env() {
-  static const bool on = [] {
-    const char* e = std::getenv("PICASSO_RUN_LAYOUT");
-    return e && std::atoi(e) == 1;
-  }();
-  return on;
+cudaError_t launch_count_diff(const int32_t* a, const int32_t* b, int64_t n, int32_t* diff, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(diff, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 148 * 8);
+  k_count_diff<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a, b, n, diff);
+  count_launches(1);
+  return cudaGetLastError();
 }
 int64_t debug_grid(int64_t blocks) {
   static const int64_t div = [] {
@@ -1997,6 +1936,118 @@ int picasso_run(void* ctx, int32_t* d_color_out, int32_t* n_rounds) {
   return PICASSO_OK;
 }
 
+int picasso_autotune(const picasso_config* cfg, const uint64_t* d_xz, const int64_t* h_set_offsets,
+                     int32_t nsets, const uint64_t* h_seeds, int32_t q, int32_t reps, picasso_schedule* best,
+                     double* best_ms, double* start_ms, void* stream) {
+  if (!cfg || !d_xz || !h_set_offsets || nsets < 1 || reps < 1 || reps > 64) return PICASSO_ERR_INVALID_ARG;
+  ST(validate_cfg(cfg));
+  const int64_t n = h_set_offsets[nsets];
+  if (h_set_offsets[0] != 0 || n < 1 || n >= (int64_t(1) << 30)) return PICASSO_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  cudaMemPool_t pool;
+  {
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = pool_for(dev, &pool);
+    if (ce != cudaSuccess) return map_err(ce);
+  }
+  int32_t *ref = nullptr, *out = nullptr, *diff = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto done = [&](int st) {
+    if (ref) cudaFreeAsync(ref, s);
+    if (out) cudaFreeAsync(out, s);
+    if (diff) cudaFreeAsync(diff, s);
+    cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return st;
+  };
+  cudaError_t e = cudaMallocFromPoolAsync((void**)&ref, sizeof(int32_t) * n, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&out, sizeof(int32_t) * n, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&diff, sizeof(int32_t), pool, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return done(map_err(e));
+  bool have_ref = false;
+  // one whole run under `sc` into `dst`, its time on the stream in *ms
+  auto run = [&](const picasso_schedule& sc, int32_t* dst, float* ms) -> int {
+    picasso_config cf = *cfg;
+    cf.sched = sc;
+    void* ctx = nullptr;
+    cudaError_t ce = cudaEventRecord(e0, s);
+    if (ce != cudaSuccess) return map_err(ce);
+    int st = init_common(&ctx, &cf, d_xz, h_set_offsets, nsets, h_seeds, q, stream);
+    if (st == PICASSO_OK) st = picasso_run(ctx, dst, nullptr);
+    if (ctx) {
+      const int st2 = picasso_destroy(ctx);
+      if (st == PICASSO_OK) st = st2;
+    }
+    if (st != PICASSO_OK) return st;
+    ce = cudaEventRecord(e1, s);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, e0, e1);
+    return map_err(ce);
+  };
+  // median time of `reps` runs after one untimed run; every run's colors
+  // must equal the first run's (a schedule never changes a result)
+  auto measure = [&](const picasso_schedule& sc, double* med) -> int {
+    float ms = 0.f;
+    std::vector<float> t;
+    for (int r = 0; r <= reps; ++r) {
+      ST(run(sc, have_ref ? out : ref, &ms));
+      if (have_ref) {
+        int32_t h = 0;
+        cudaError_t ce = launch_count_diff(ref, out, n, diff, s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h, diff, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return map_err(ce);
+        if (h != 0) return PICASSO_ERR_INTERNAL;
+      }
+      have_ref = true;
+      if (r > 0) t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    *med = t[t.size() / 2];
+    return PICASSO_OK;
+  };
+  picasso_schedule cur = cfg->sched;
+  double t_cur = 0;
+  int st = measure(cur, &t_cur);
+  if (st != PICASSO_OK) return done(st);
+  if (start_ms) *start_ms = t_cur;
+  // coordinate descent: one field at a time over its candidates; a
+  // candidate replaces the best only if it is at least 1 % faster
+  struct Field {
+    int32_t picasso_schedule::*f;
+    int32_t cand[4];
+    int nc;
+  };
+  const Field fields[] = {{&picasso_schedule::engine_max_n, {16384, 8192, 4096}, 3},
+                          {&picasso_schedule::engine_blocks_per_sm, {1, 2}, 2},
+                          {&picasso_schedule::cluster_max_n, {-1, 512, 2048, 8192}, 4},
+                          {&picasso_schedule::cluster_blocks, {16, 8}, 2},
+                          {&picasso_schedule::bits_blocks_per_sm, {4, 3, 2}, 3},
+                          {&picasso_schedule::color_blocks_per_sm, {6, 4, 3}, 3}};
+  for (const Field& fd : fields) {
+    picasso_schedule base = cur;
+    for (int k = 0; k < fd.nc; ++k) {
+      if (base.*(fd.f) == fd.cand[k]) continue;
+      picasso_schedule trial = base;
+      trial.*(fd.f) = fd.cand[k];
+      double t = 0;
+      st = measure(trial, &t);
+      if (st != PICASSO_OK) return done(st);
+      if (t < 0.99 * t_cur) {
+        cur = trial;
+        t_cur = t;
+      }
+    }
+  }
+  if (best) *best = cur;
+  if (best_ms) *best_ms = t_cur;
+  return done(PICASSO_OK);
+}
+
 int picasso_get_colors(void* ctx, int32_t* d_out) {
   Ctx* c = (Ctx*)ctx;
   ST(check(c));
@@ -2089,6 +2140,7 @@ int picasso_get_stats(void* ctx, picasso_stats* out) {
   out->nnz_total = c->nnz_total;
   out->small_rounds = c->small_rounds;
   out->small_stops = c->small_stops;
+  for (int i = 0; i < 4; ++i) out->barrier_timeout[i] = c->barrier_timeout[i];
   out->t_small_ms = c->t_small;
   out->round_chunks = c->round_chunks;
   out->host_csr_rounds = c->host_rounds;

@@ -257,8 +257,11 @@ extern "C" int picasso_run_small_static(const uint64_t* d_xz, int64_t n, int32_t
         SCK(cudaMemsetAsync(counts, 0, sizeof(int32_t) * kCtlWords, s));
         SCK(launch_color_init(ca, prio, counts, s));
         SCK(launch_color_all(ca, work[0], work[1], wact, counts, s));
+        int32_t ab = 0;
         SCK(cudaMemcpyAsync(h, counts, sizeof(h), cudaMemcpyDeviceToHost, s));
+        SCK(cudaMemcpyAsync(&ab, counts + kCtlAbort, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         SCK(cudaStreamSynchronize(s));
+        if (ab != 0) return PICASSO_ERR_TIMEOUT;  // a grid barrier of the sweep kernel gave up
         if (h[4] != 0 || h[0] != 0) return PICASSO_ERR_INTERNAL;
       }
     }

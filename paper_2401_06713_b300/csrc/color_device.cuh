@@ -111,79 +111,6 @@ __device__ __forceinline__ bool run_blocked(const ColorArgs& a, int32_t v, uint3
   return false;
 }
 
-// The same scan over a run in the bit layout: row words of partner blocks
-// W = 0 .. slot / 32 (every partner is a member at a smaller slot, ranked
-// before v), kBitsGroup words at a time; lane t holds partner slot 32 W + t,
-// whose vertex id is loaded together with the word, so a group costs one
-// level of loads for the words and ids and one for the partners' states.
-constexpr int kBitsGroup = 4;
-template <bool FRESH>
-__device__ __forceinline__ bool bits_blocked(const ColorArgs& a, uint32_t c, int64_t rb, int32_t pb, int lane,
-                                             int& polls, bool* fail) {
-  const int slot = (int)(rb >> 48);
-  const int64_t w0 = rb & ((int64_t(1) << 48) - 1);
-  const int nW = (slot >> 5) + 1;
-  for (int W0 = 0; W0 < nW;) {
-    uint32_t wd[kBitsGroup];
-    int32_t u[kBitsGroup];
-#pragma unroll
-    for (int j = 0; j < kBitsGroup; ++j) {
-      const int W = W0 + j;
-      const int t = (W << 5) + lane;
-      wd[j] = W < nW ? ld_run<FRESH>(a.rmask + w0 + a.rstride * (int64_t)W) : 0u;
-      u[j] = t < slot ? ld_run<FRESH>(a.bpid + pb + t) : -1;
-    }
-    uint64_t su[kBitsGroup];
-#pragma unroll
-    for (int j = 0; j < kBitsGroup; ++j) {
-      if (!((wd[j] >> lane) & 1u)) u[j] = -1;
-      su[j] = u[j] >= 0 ? __ldcg(&a.state[u[j]]) : 0ull;
-    }
-    bool lb = false;
-    uint32_t wm[kBitsGroup];
-#pragma unroll
-    for (int j = 0; j < kBitsGroup; ++j) {
-      bool lw = false;
-      if (u[j] >= 0) {
-        const uint32_t wu = (uint32_t)su[j], st = wu & 3u, cu = wu >> 2;
-        lb = lb || (st == kColored && cu == c);
-        lw = st == kUndecided && cu <= c;
-      }
-      wm[j] = __ballot_sync(0xffffffffu, lw);
-    }
-    if (__any_sync(0xffffffffu, lb)) return true;
-    int jw = -1;
-#pragma unroll
-    for (int j = kBitsGroup - 1; j >= 0; --j)
-      if (wm[j]) jw = j;
-    if (jw < 0) {
-      W0 += kBitsGroup;
-      continue;
-    }
-    // wait for the first partner holding us up, then rescan from its word
-    uint32_t m = 0u;
-    int32_t uw = -1;
-#pragma unroll
-    for (int j = 0; j < kBitsGroup; ++j)
-      if (j == jw) {
-        m = wm[j];
-        uw = u[j];
-      }
-    const int32_t wu_id = __shfl_sync(0xffffffffu, uw, __ffs(m) - 1);
-    while (true) {
-      const uint32_t w = (uint32_t)__ldcg(&a.state[wu_id]);
-      if ((w & 3u) != kUndecided || (w >> 2) > c) break;
-      if (++polls > a.max_polls) {
-        *fail = true;
-        return true;
-      }
-      __nanosleep(64);
-    }
-    W0 += jw;
-  }
-  return false;
-}
-
 // One vertex.  The run offsets and colors of 32 candidates are loaded at
 // once (lane k holds candidate k's).  With colored lists (a.clist),
 // kListBatch candidates at a time are first checked against the vertices
@@ -210,20 +137,9 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
   for (int kb = 0; kb < L; kb += 32) {
     const int kl = kb + lane;
     int64_t my_rs = 0, my_re = 0;
-    int32_t my_pb = 0;
     if (kl < L) {
-      if (a.rbits) {
-        // bit layout: rs = the row address, re - rs = the run length
-        my_rs = ld_run<FRESH>(a.rbits + row + kl);
-        my_pb = ld_run<FRESH>(a.rpbase + row + kl);
-        my_re = ld_run<FRESH>(a.rcnt + row + kl);
-      } else if (a.rcnt) {
-        my_rs = ld_run<FRESH>(a.rstart + row + kl);
-        my_re = my_rs + ld_run<FRESH>(a.rcnt + row + kl);
-      } else {
-        my_rs = ld_run<FRESH>(a.runoff + row + kl) - a.cbase;
-        my_re = ld_run<FRESH>(a.runoff + row + kl + 1) - a.cbase;
-      }
+      my_rs = ld_run<FRESH>(a.runoff + row + kl) - a.cbase;
+      my_re = ld_run<FRESH>(a.runoff + row + kl + 1) - a.cbase;
     }
     const uint32_t my_c = kl < L ? (uint32_t)ld_run<FRESH>(a.lists + row + kl) : 0u;
     const int kend = min(L - kb, 32);
@@ -256,13 +172,7 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
         const int64_t re = __shfl_sync(0xffffffffu, my_re, kk);
         if (kb + kk > 0 && lane == 0) publish(a.state, v, (c << 2) | kUndecided);
         bool fail = false;
-        bool blk;
-        if (a.rbits) {
-          const int32_t pb = __shfl_sync(0xffffffffu, my_pb, kk);
-          blk = re != 0 && bits_blocked<FRESH>(a, c, rs, pb, lane, polls, &fail);
-        } else {
-          blk = run_blocked<FRESH>(a, v, pv, c, rs, re - rs, lane, polls, &fail);
-        }
+        const bool blk = run_blocked<FRESH>(a, v, pv, c, rs, re - rs, lane, polls, &fail);
         if (fail) {
           if (lane == 0) atomicExch(err, 1);
           return false;
@@ -309,7 +219,7 @@ __device__ __forceinline__ void mask_resolve(const ColorArgs& a, int64_t row, in
   for (int t = from + lane; t < to; t += 32) {
     if (t == skip) continue;
     const uint32_t c = (uint32_t)__ldg(a.lists + row + t);
-    const int slot = (int)(__ldg(a.rbits + row + t) >> 48);
+    const int slot = rinfo_slot(__ldg(a.rinfo + row + t));
     atomicOr(a.cmask + (size_t)c * 32 + 16 + (slot >> 5), 1u << (slot & 31));
   }
 }
@@ -317,7 +227,6 @@ __device__ __forceinline__ void mask_resolve(const ColorArgs& a, int64_t row, in
 __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
   const int64_t row = __ldg(a.loff + v);
   const int L = (int)(__ldg(a.loff + v + 1) - row);
-  const int64_t lo48 = (int64_t(1) << 48) - 1;
   const int h = lane >> 4, W = lane & 15;
   int polls = 0;
   int kdone = 0;  // entries [0, kdone) passed and marked resolved
@@ -327,7 +236,7 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
     int64_t my_rb = 0;
     if (kl < L) {
       my_c = (uint32_t)__ldg(a.lists + row + kl);
-      my_rb = __ldg(a.rbits + row + kl);
+      my_rb = __ldg(a.rinfo + row + kl);
     }
     const int kend = min(L - kb, 32);
     for (int k0 = 0; k0 < kend; k0 += kMaskCands) {
@@ -337,8 +246,8 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
         const int kk = k0 + 2 * p + h;
         const uint32_t c = __shfl_sync(0xffffffffu, my_c, min(kk, 31));
         const int64_t rb = __shfl_sync(0xffffffffu, my_rb, min(kk, 31));
-        const bool act = kk < kend && W <= (int)(rb >> 53);  // W <= slot / 32
-        rw[p] = act ? __ldg(a.rmask + (rb & lo48) + (int64_t)a.rstride * W) : 0u;
+        const bool act = kk < kend && W <= (rinfo_slot(rb) >> 5);
+        rw[p] = act ? __ldg(a.rmask + rinfo_addr(rb) + (int64_t)a.rstride * W) : 0u;
         cw[p] = act ? __ldcg(a.cmask + (size_t)c * 32 + W) : 0u;
         sw[p] = act ? __ldcg(a.cmask + (size_t)c * 32 + 16 + W) : 0u;
       }
@@ -363,8 +272,8 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
           // wait for the earlier neighbours that may still take c
           const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
           const int64_t rb = __shfl_sync(0xffffffffu, my_rb, kk);
-          const bool act = lane < 16 && lane <= (int)(rb >> 53);
-          const uint32_t r = act ? __ldg(a.rmask + (rb & lo48) + (int64_t)a.rstride * lane) : 0u;
+          const bool act = lane < 16 && lane <= (rinfo_slot(rb) >> 5);
+          const uint32_t r = act ? __ldg(a.rmask + rinfo_addr(rb) + (int64_t)a.rstride * lane) : 0u;
           while (true) {
             const uint32_t cc = act ? __ldcg(a.cmask + (size_t)c * 32 + lane) : 0u;
             const uint32_t ss = act ? __ldcg(a.cmask + (size_t)c * 32 + 16 + lane) : 0u;
@@ -383,7 +292,7 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
         if (blocked) continue;
         // v takes c: colored bit, every other list color resolved
         const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
-        const int slot = (int)(__shfl_sync(0xffffffffu, my_rb, kk) >> 48);
+        const int slot = rinfo_slot(__shfl_sync(0xffffffffu, my_rb, kk));
         mask_resolve(a, row, kdone, L, kb + kk, lane);
         if (lane == 0) {
           atomicOr(a.cmask + (size_t)c * 32 + (slot >> 5), 1u << (slot & 31));

@@ -186,6 +186,56 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch with a time limit.  bar: two
+// words (arrivals, generation), zero before the launch.  Thread 0 of every
+// block arrives once per call; the last arrival resets the count and bumps
+// the generation.  A block that waits longer than limit_ns (by the global
+// timer), or sees *abort set, sets *abort, writes the arrivals it saw to
+// *seen and returns false: the caller then ends the kernel, and every other
+// block leaves at its next barrier.  Writes made before the barrier by any
+// block are visible after it (fences on both sides).
+constexpr uint64_t kBarrierLimitNs = 4000000000ull;
+__device__ __forceinline__ bool grid_sync_bounded(unsigned int* bar, int* abort, uint64_t limit_ns, int* seen) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      while (*gen == g) {
+        if (*(volatile int*)abort) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > limit_ns) {
+          *seen = (int)*(volatile unsigned int*)bar;
+          atomicExch(abort, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
 // Set of batch-global vertex id g: the k with soff[k] <= g < soff[k+1].
 __device__ __forceinline__ int set_of(const int64_t* __restrict__ soff, int nsets, int64_t g) {
   int lo = 0, hi = nsets - 1;
@@ -206,12 +256,7 @@ void count_launches(int k);
 // (a debugging aid: every such kernel gives the same output at any grid
 // size, so runs at different divisors must agree bit for bit).
 int64_t debug_grid(int64_t blocks);
-// PICASSO_RUN_LAYOUT=1 at load: per-round builds write the run layout (the
-// fused pass) instead of the bit layout.
-bool run_layout_env();
-// Rounds of at most this many vertices go to the engine's cluster launch
-// (kSmallClusterMaxN; PICASSO_CLUSTER_MAXN at load, 0: never).
-int64_t small_cluster_maxn();
+
 
 // ---------------------------------------------------------------------------
 // Launchers (host functions defined in the kernel .cu files).
@@ -243,8 +288,19 @@ cudaError_t launch_assign_lists(int32_t round, const int32_t* gid, int64_t n, co
 // scan_tmp_bytes(n) bytes.
 size_t scan_tmp_bytes(int64_t n);
 cudaError_t launch_scan_u32(const uint32_t* in, int64_t n, int64_t* out, void* tmp, cudaStream_t s);
-// *out = sum of the n counts (out zeroed first).
-cudaError_t launch_sum_u32(const uint32_t* in, int64_t n, int64_t* out, cudaStream_t s);
+// out[e] = rinfo_len(rinfo[e]): the bit layout's run lengths, e < E.
+cudaError_t launch_rinfo_lengths(const int64_t* rinfo, int64_t E, uint32_t* out, cudaStream_t s);
+
+// One word per list entry of the bit layout: row address (bits 0..37, in
+// words of the bit rows), bucket slot (bits 38..46) and run length (bits
+// 47..55; a run never passes the slot, and slots stay below kFusedMax).
+constexpr int kRinfoAddrBits = 38;
+__host__ __device__ inline int64_t rinfo_pack(int64_t addr, int slot, int len) {
+  return addr | ((int64_t)slot << kRinfoAddrBits) | ((int64_t)len << (kRinfoAddrBits + 9));
+}
+__host__ __device__ inline int64_t rinfo_addr(int64_t r) { return r & ((int64_t(1) << kRinfoAddrBits) - 1); }
+__host__ __device__ inline int rinfo_slot(int64_t r) { return (int)((r >> kRinfoAddrBits) & 511); }
+__host__ __device__ inline int rinfo_len(int64_t r) { return (int)((r >> (kRinfoAddrBits + 9)) & 511); }
 
 // Conflict build.  Run k of row v is runoff[loff[v] + k] .. runoff[loff[v]+k+1].
 struct ConflictArgs {
@@ -265,22 +321,17 @@ struct ConflictArgs {
   int32_t* err;          // device error word
   uint32_t* rmask;       // bucket join: run words (mask pass -> emit)
   int32_t lower;         // 1: rows keep only neighbours with a smaller id
-  // direct layout (the fused mask + emit pass): entry e's run is
-  // col[rstart[e] .. rstart[e] + cnt[e]), each bucket's runs one contiguous
-  // region claimed from *cursor; regions that would pass cap are not written
-  // (the cursor still counts, so it ends at the exact nnz)
-  int64_t* rstart;                // [E]
-  unsigned long long* cursor;     // one word, zero on entry
-  int64_t cap;                    // entries col holds
   const uint4* bxz;               // [E] member words in bucket-slot order (x lo, x hi, z lo, z hi)
   const int32_t* bpid;            // [E] member vertex ids in bucket-slot order
   // bit layout (launch_bucket_bits): bucket b's lower blocks are stored
   // row-major at rmask + moff[b]: row i (block R = i / 32) has R + 1 words,
   // word W's bit t = partner slot 32 W + t (< i) commutes with i.  Entry e,
-  // member i of bucket b, has rbits[e] = (moff[b] + 16 R (R + 1) + (i % 32)
-  // (R + 1)) | i << 48, the address of row i, and rpbase[e] = boff[b]
-  int64_t* rbits;                 // [E]
-  int32_t* rpbase;                // [E]
+  // member i of bucket b, gets one word rinfo[e] (rinfo_* below): the
+  // address of row i, moff[b] + 16 R (R + 1) + (i % 32) (R + 1), the slot i
+  // and the run length (the set bits of the row); *nnz gets the sum of the
+  // run lengths (one atomic per bucket)
+  int64_t* rinfo;                 // [E]
+  unsigned long long* nnz;        // one word, zero on entry
   int32_t rowmajor;               // emit pass: a.rmask holds the bit layout's row-major
                                   // rows (row r of block R at 16 R (R + 1) + r (R + 1))
 };
@@ -302,22 +353,20 @@ cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out
 cudaError_t launch_bucket_words(const uint32_t* bcount, int64_t P, int32_t lower, uint32_t* words, cudaStream_t s);
 cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem,
                                const int64_t* moff, int32_t smax, int32_t q, cudaStream_t s);
-// The fused pass (EARLIER form, buckets of at most kFusedMax members): the
-// mask blocks stay in shared memory and every bucket's runs are written at
-// once, in the direct layout (a.rstart, a.cnt, a.col, a.cursor, a.cap).
+// Largest bucket the bit pass handles.
 constexpr int kFusedMax = 512;
-cudaError_t launch_bucket_fused(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, int32_t smax,
-                                int32_t q, cudaStream_t s);
 // The bit pass (EARLIER form, buckets of at most kFusedMax members, one word
-// per part): pair tests as in the fused pass from the gathered members
-// (a.bxz), the lower blocks to a.rmask + moff[b], run lengths to a.cnt and
-// each entry's row address to a.rbits / a.rpbase.  No run is written: the
-// coloring reads the bits, the canonical CSR is made from them on request.
+// per part): the pair tests of launch_bucket_mask from the gathered members
+// (a.bxz), the lower blocks row-major to a.rmask + moff[b], each entry's
+// row address, slot and run length to a.rinfo, the run total to *a.nnz.  No
+// run is written: the coloring reads the bits, the canonical CSR is made
+// from them on request.
+// per_sm_cap > 0: at most that many blocks per SM (the schedule's).
 cudaError_t launch_bucket_bits(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
-                               int32_t smax, int32_t q, cudaStream_t s);
+                               int32_t smax, int32_t q, cudaStream_t s, int per_sm_cap = 0);
 // bxz[p], bpid[p]: words and vertex id of the member at bucket slot p < E.
 // The warp sort of every bucket (all of at most 512 members) and, by the
-// same warp, the gather of launch_bucket_gather (fused pass).
+// same warp, the gather of launch_bucket_gather (bit pass).
 cudaError_t launch_bucket_sort_gather(const int64_t* boff, int64_t P, int32_t* bmem, int32_t smax,
                                       const ConflictArgs& a, uint4* bxz, int32_t* bpid, cudaStream_t s);
 cudaError_t launch_bucket_gather(const ConflictArgs& a, const int32_t* bmem, uint4* bxz, int32_t* bpid,
@@ -344,15 +393,13 @@ struct ColorArgs {
   const int64_t* runoff;   // [E+1] canonical layout: run of entry e ends at runoff[e+1]
   int64_t cbase;           // canonical layout: run offsets are col indices + cbase
   int64_t v0;              // ordered pass: position t is vertex v0 + t (a chunk of the round)
-  const int64_t* rstart;   // direct layout (rcnt set): run of e is rstart[e] .. + rcnt[e]
-  const uint32_t* rcnt;
-  // bit layout (rbits set; ConflictArgs gives the encoding): the run of
-  // entry e is the set bits of its row words rmask[(rbits[e] & (2^48 - 1))
-  // + 32 W], W <= slot / 32, slot = rbits[e] >> 48; bit t of word W is the
-  // member at bucket slot 32 W + t, vertex bpid[rpbase[e] + 32 W + t];
-  // rcnt[e] holds the run's length
-  const int64_t* rbits;
-  const int32_t* rpbase;
+  // bit layout (rinfo set; ConflictArgs gives the encoding): the run of
+  // entry e is the set bits of its row words rmask[rinfo_addr(rinfo[e]) +
+  // rstride W], W <= slot / 32, slot = rinfo_slot(rinfo[e]); bit t of word
+  // W is the member at slot 32 W + t of bucket c = lists[e], vertex
+  // bpid[bboff[c] + 32 W + t]
+  const int64_t* rinfo;
+  const int64_t* bboff;
   const uint32_t* rmask;
   const int32_t* bpid;
   int32_t rstride;      // bit layout: words between a row's word W and W + 1
@@ -393,7 +440,8 @@ cudaError_t launch_color_sweep(const ColorArgs& a, const int32_t* work_in, const
 // Ordered persistent coloring of a round: `order` must list the vertices in
 // exact (priority, id) order (launch_prio_order gives it).  On return *err
 // is 1 if a bounded wait ran out (then recolor with launch_color_all).
-cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32_t* err, cudaStream_t s);
+cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32_t* err, cudaStream_t s,
+                                 int per_sm_cap = 0);
 // Every sweep of a round in one cooperative launch.  ctl [kCtlWords] int32:
 // ctl[0] holds the pending count of wa on entry (launch_color_init writes
 // it), the rest must be zero; on exit ctl[3] = sweeps, ctl[4] = 1 if the
@@ -402,7 +450,10 @@ cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32
 // (uint64 at ctl + 8 + kSweepLog, entry s) and the active count
 // (ctl[8 + 3 kSweepLog + s]).
 constexpr int kSweepLog = 64;
-constexpr int kCtlWords = 8 + 4 * kSweepLog;
+// after the sweep log: the bounded grid barrier (2 words), its abort flag
+// (set when a barrier gave up; the launch ended) and the arrivals it saw
+constexpr int kCtlBar = 8 + 4 * kSweepLog, kCtlAbort = kCtlBar + 2, kCtlSeen = kCtlBar + 3;
+constexpr int kCtlWords = kCtlBar + 4;
 cudaError_t launch_color_all(const ColorArgs& a, int32_t* wa, int32_t* wb, int32_t* wact, int32_t* ctl,
                              cudaStream_t s);
 // Colors to the output (final color = base + bucket color - cofs of the
@@ -428,9 +479,6 @@ cudaError_t launch_gather_xz(const uint64_t* xz_all, const int32_t* gid, int64_t
 // entries from runoff (canonical layout) or, if it is null, from cnt.
 cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, const uint32_t* cnt, const int32_t* gid,
                                  int64_t n, const int64_t* soff, int32_t nsets, int64_t* out, cudaStream_t s);
-// Direct layout -> canonical rows: dst[runoff[e] + t] = src[rstart[e] + t].
-cudaError_t launch_runs_to_rows(const int64_t* rstart, const uint32_t* rcnt, const int64_t* runoff, int64_t E,
-                                const int32_t* src, int32_t* dst, cudaStream_t s);
 cudaError_t launch_iota(int32_t* out, int64_t n, cudaStream_t s);
 
 // Small-round engine (kernels_small.cu): every remaining round of a context
@@ -492,23 +540,29 @@ struct SmallArgs {
   int32_t* brank;         // [E0]   rank,
   uint64_t* bxz;          // [2 E0] words
   int64_t* part;          // [gridDim.x] block sums of the grid scans
-  int32_t* err;           // [4]: 0 ordered-pass poll timeout, 1 work counter, 2 bucket over the cap
-  int64_t* ctl;           // [9]: 0 n, 1 rounds done, 2 stop reason, 4 V_l in gid_b (0..4
+  int32_t* err;           // [4]: 0 ordered-pass poll timeout, 1 work counter, 2 bucket over the cap,
+                          //      3 a grid barrier timed out (the launch ended; ctl[9] its site,
+                          //      ctl[10] its round, ctl[11] the arrivals it saw)
+  int64_t* ctl;           // [kSmallCtlWords]: 0 n, 1 rounds done, 2 stop reason, 4 V_l in gid_b (0..4
                           //      host-initialised), 6 sum of nnz, 7 sum over the sets of
                           //      n_k (n_k - 1) / 2 (6, 7 zero on entry), 3, 5, 8 scratch
   int32_t max_polls;      // polls of one bounded wait before the engine gives up
+  unsigned int* bar;      // [2] bounded grid barrier (zero before the grid launch)
   int64_t handoff;        // grid launch: stop (kSmallHandoff) at a round of at most
                           // this many vertices, for the cluster launch
 };
 
 // Stop reasons in ctl[2].
 constexpr int64_t kSmallOk = 0, kSmallTimeout = 1, kSmallOverflow = 2, kSmallMaxRounds = 3, kSmallHandoff = 4;
-// Rounds of at most this many vertices run in one thread-block cluster.
+constexpr int kSmallCtlWords = 12;
+// Rounds of at most this many vertices run in one thread-block cluster (the
+// default of picasso_schedule.cluster_max_n).
 constexpr int64_t kSmallClusterMaxN = 2048;
 // part_cap: words of a.part; the launch uses at most that many blocks.  The
 // grid launch runs the rounds above a.handoff vertices, then (cluster_blocks
 // > 0) one cluster of cluster_blocks blocks the rest, back to back on s.
-cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_blocks, cudaStream_t s);
+cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_blocks, int blocks_per_sm,
+                                cudaStream_t s);
 // Blocks of the largest cluster the engine can launch (16, 8, 4 or 2), 0 if none.
 int small_cluster_blocks(int32_t qw);
 
@@ -537,8 +591,11 @@ struct DynArgs {
   int32_t* bstep;         // [n] last step + 1 the vertex was found blocked
   int32_t* parts;         // [n] parts of the vertex's examination finished
   int32_t* lng;           // [n] the step's vertices whose row heads decided nothing
-  int32_t* ctl;           // [8] list lengths, sel and fin lengths (by parity), steps, long list
+  int32_t* ctl;           // [kDynCtlWords] list lengths, sel and fin lengths (by parity), steps,
+                          // long list; 8..9 the bounded grid barrier, 10 its abort flag (the
+                          // launch ended), 11 the arrivals it saw
 };
+constexpr int kDynCtlWords = 12;
 // masks of full lists, state 0, wa = all vertices, ctl = {n, 0, ...}
 cudaError_t launch_dyn_init(const DynArgs& d, cudaStream_t s);
 // every step of the round in one cooperative launch; ctl[6] = steps on exit

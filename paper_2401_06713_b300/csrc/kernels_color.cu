@@ -137,14 +137,14 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
     int64_t first_wait = -1;
     int32_t wait_u = -1;
     int64_t rs = 0, r1 = 0;
-    if (a.rbits) {
+    if (a.rinfo) {
       // bit layout: cur counts resolved partner slots; every partner is
       // ranked before v
-      const int64_t rb = a.rbits[row + k];
-      const int32_t pb = a.rpbase[row + k];
-      const int slot = (int)(rb >> 48);
-      const int64_t w0 = rb & ((int64_t(1) << 48) - 1);
-      r1 = a.rcnt[row + k] ? slot : 0;
+      const int64_t rb = a.rinfo[row + k];
+      const int64_t pb = a.bboff[c];
+      const int slot = rinfo_slot(rb);
+      const int64_t w0 = rinfo_addr(rb);
+      r1 = rinfo_len(rb) ? slot : 0;
       for (int64_t W = cur >> 5; (W << 5) < r1; ++W) {
         const int64_t t = (W << 5) + lane;
         const uint32_t wd = a.rmask[w0 + a.rstride * W];
@@ -169,11 +169,11 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
         }
       }
     } else {
-      rs = a.rcnt ? a.rstart[row + k] : a.runoff[row + k] - a.cbase;
-      r1 = a.rcnt ? rs + a.rcnt[row + k] : a.runoff[row + k + 1] - a.cbase;
+      rs = a.runoff[row + k] - a.cbase;
+      r1 = a.runoff[row + k + 1] - a.cbase;
     }
     // the run of c: the neighbours that hold c
-    for (int64_t e0 = rs + cur; !a.rbits && e0 < r1; e0 += 32) {
+    for (int64_t e0 = rs + cur; !a.rinfo && e0 < r1; e0 += 32) {
       const int64_t e = e0 + lane;
       bool lb = false, lw = false;
       int32_t u = -1;
@@ -273,7 +273,6 @@ __device__ __forceinline__ void wake_chunk(const ColorArgs& a, const int32_t* __
 __global__ void __launch_bounds__(256, 4) k_color_all(ColorArgs a, int32_t* __restrict__ wa, int32_t* __restrict__ wb,
                                                       int32_t* __restrict__ wact, int32_t* __restrict__ ctl,
                                                       int32_t max_sweeps) {
-  cg::grid_group g = cg::this_grid();
   const int lane = threadIdx.x & 31;
   const uint32_t lt = lanemask_lt();
   const int64_t gwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -297,10 +296,10 @@ __global__ void __launch_bounds__(256, 4) k_color_all(ColorArgs a, int32_t* __re
     }
     for (int64_t b0 = wid * 32; b0 < nin; b0 += gwarps * 32)
       wake_chunk(a, in, nin, b0, lane, lt, wact, &ctl[2], out, &ctl[1]);
-    g.sync();
+    if (!grid_sync_bounded(reinterpret_cast<unsigned int*>(ctl + kCtlBar), ctl + kCtlAbort, kBarrierLimitNs, ctl + kCtlSeen)) return;
     const int32_t nact = __ldcg(&ctl[2]);
     for (int64_t w = wid; w < nact; w += gwarps) eval_vertex(a, __ldcg(&wact[w]), lane, out, &ctl[1]);
-    g.sync();
+    if (!grid_sync_bounded(reinterpret_cast<unsigned int*>(ctl + kCtlBar), ctl + kCtlAbort, kBarrierLimitNs, ctl + kCtlSeen)) return;
     if (tid == 0) {
       ctl[0] = __ldcg(&ctl[1]);
       ctl[1] = 0;
@@ -308,7 +307,7 @@ __global__ void __launch_bounds__(256, 4) k_color_all(ColorArgs a, int32_t* __re
       ctl[3] = sweep + 1;
       if (sweep < kSweepLog) ctl[8 + 3 * kSweepLog + sweep] = nact;
     }
-    g.sync();
+    if (!grid_sync_bounded(reinterpret_cast<unsigned int*>(ctl + kCtlBar), ctl + kCtlAbort, kBarrierLimitNs, ctl + kCtlSeen)) return;
     int32_t* t = in;
     in = out;
     out = t;
@@ -337,7 +336,8 @@ __global__ void __launch_bounds__(256, 6) k_color_masks(ColorArgs a, int32_t* __
   }
 }
 
-cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32_t* err, cudaStream_t s) {
+cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32_t* err, cudaStream_t s,
+                                 int per_sm_cap) {
   int dev = 0, sms = 148, per_sm = 0;
   const bool masks = a.cmask != nullptr;
   const void* kern = masks ? (const void*)k_color_masks : (const void*)k_color_ordered;
@@ -346,6 +346,7 @@ cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  if (per_sm_cap > 0) per_sm = std::min(per_sm, per_sm_cap);
   int64_t blocks = (int64_t)per_sm * sms;
   const int64_t want = (a.n + 7) / 8;
   if (want < blocks) blocks = want > 0 ? want : 1;
@@ -507,29 +508,6 @@ cudaError_t launch_set_csr_bytes(const int64_t* loff, const int64_t* runoff, con
   if (e != cudaSuccess || n <= 0) return e;
   k_set_csr_bytes<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(loff, runoff, cnt, gid, n, soff, nsets,
                                                                (unsigned long long*)out);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-// Warp per list entry: its run moves from the direct layout to its place in
-// the canonical rows.
-__global__ void k_runs_to_rows(const int64_t* __restrict__ rstart, const uint32_t* __restrict__ rcnt,
-                               const int64_t* __restrict__ runoff, int64_t E, const int32_t* __restrict__ src,
-                               int32_t* __restrict__ dst) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < E; e += nw) {
-    const int64_t s0 = rstart[e], d0 = runoff[e];
-    const uint32_t m = rcnt[e];
-    for (uint32_t t = lane; t < m; t += 32) dst[d0 + t] = src[s0 + t];
-  }
-}
-
-cudaError_t launch_runs_to_rows(const int64_t* rstart, const uint32_t* rcnt, const int64_t* runoff, int64_t E,
-                                const int32_t* src, int32_t* dst, cudaStream_t s) {
-  if (E <= 0) return cudaSuccess;
-  const int64_t blocks = std::min<int64_t>((E + 7) / 8, 148 * 16);
-  k_runs_to_rows<<<(unsigned)blocks, 256, 0, s>>>(rstart, rcnt, runoff, E, src, dst);
   count_launches(1);
   return cudaGetLastError();
 }

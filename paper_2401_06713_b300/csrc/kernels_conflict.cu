@@ -68,7 +68,7 @@ cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* b
 // l*E .. l*E+E-1, E = m/32 for the padded size m); partners closer than E
 // are in the same lane, farther ones are exchanged by shuffles.  Larger
 // buckets: one CTA per bucket, the same network in shared memory.
-// GATHER (the fused pass, buckets of at most kWarpSortMax members): the
+// GATHER (the bit pass, buckets of at most kWarpSortMax members): the
 // same warp then writes the sorted members' words and vertex ids in slot
 // order (bxz, bpid), as k_bucket_gather would.
 template <bool GATHER>
@@ -222,7 +222,7 @@ namespace {
 
 constexpr int kMaskThreads = 256;
 constexpr int kMaskWarps = kMaskThreads / 32;
-constexpr int kMaskPlain = 0, kMaskRuns = 1, kMaskBits = 2;  // k_bucket_mask modes
+constexpr int kMaskPlain = 0, kMaskBits = 1;  // k_bucket_mask modes
 constexpr int kTabWords = 32 * 16;  // one warp's tables: 32 chunks x 16 entries
 constexpr int kEmitThreads = 256;
 
@@ -241,16 +241,6 @@ __host__ __device__ inline size_t mask_smem_bytes(int smax) {
 __host__ __device__ inline int rm_pad_off(int R) { return 32 * (R * (R + 1) / 2 + R / 2); }
 __host__ __device__ inline size_t bits_smem_bytes(int smax) {
   return mask_smem_bytes(smax) + sizeof(uint32_t) * (size_t)rm_pad_off((smax + 31) >> 5);
-}
-
-// The fused pass adds, per member, its vertex id and run offset, and the
-// bucket's lower mask blocks (nwb (nwb + 1) / 2 blocks of 32 words).
-__host__ __device__ inline size_t fused_smem_bytes(int smax) {
-  const int nwb = (smax + 31) >> 5;
-  // (the next bucket's staging lies in the bit columns and tables:
-  // 24 smax <= 12,288 bytes <= the tables' 16,384)
-  return mask_smem_bytes(smax) + align16(sizeof(int32_t) * smax) + align16(sizeof(uint32_t) * smax) +
-         sizeof(uint32_t) * 32 * (size_t)(nwb * (nwb + 1) / 2);
 }
 
 // Asynchronous global -> shared copies (the next bucket's members).
@@ -377,15 +367,13 @@ __device__ __forceinline__ void emit_rows(const uint32_t* __restrict__ wbuf, con
 }
 
 // MODE: kMaskPlain (members read through bmem and the strings; blocks and
-// counts to HBM), kMaskRuns (members gathered in slot order and prefetched;
-// blocks kept in shared memory and every bucket's runs written at once, the
-// direct run layout) or kMaskBits (members gathered and prefetched; the lower
-// blocks, counts and each entry's row address go to HBM: the bit layout).
+// counts to HBM, block-major) or kMaskBits (members gathered in slot order
+// and prefetched; the lower blocks, row-major, counts and each entry's row
+// address go to HBM: the bit layout).
 template <int QW, bool LOWER, int MODE>
 __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a, const int64_t* __restrict__ boff,
                                                               const int32_t* __restrict__ bmem,
                                                               const int64_t* __restrict__ moff, int smax) {
-  constexpr bool FUSED = MODE == kMaskRuns;       // runs written from shared memory
   constexpr bool STAGED = MODE != kMaskPlain;     // gathered, prefetched members
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* p = smem_raw;
@@ -395,27 +383,11 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   p += align16(sizeof(int32_t) * smax);
   int32_t* cnt = (int32_t*)p;
   p += align16(sizeof(int32_t) * smax);
-  // fused pass: members' vertex ids, run offsets inside the bucket, mask blocks
-  int32_t* pid = nullptr;
-  uint32_t* roff = nullptr;
-  uint32_t* mw = nullptr;
   uint32_t* mwp = nullptr;
   if (MODE == kMaskBits) {
     mwp = (uint32_t*)p;
     p += sizeof(uint32_t) * (size_t)rm_pad_off((smax + 31) >> 5);
   }
-  if (FUSED) {
-    pid = (int32_t*)p;
-    p += align16(sizeof(int32_t) * smax);
-    roff = (uint32_t*)p;
-    p += align16(sizeof(uint32_t) * smax);
-    const int nwbm = (smax + 31) >> 5;
-    mw = (uint32_t*)p;
-    p += sizeof(uint32_t) * 32 * (size_t)(nwbm * (nwbm + 1) / 2);
-  }
-  __shared__ unsigned long long base_s;
-  __shared__ uint32_t wsum_s[kMaskWarps];
-  __shared__ int rb_next;
   // 256-byte aligned region: bit columns, then per-warp tables (table bases
   // need a zero low byte)
   {
@@ -425,20 +397,18 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   uint32_t* colw = (uint32_t*)p;  // [nwb][2 QW][32]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
-  // fused pass: a bucket's members (words, entry ids, vertex ids, gathered in
-  // slot order beforehand) are copied asynchronously into a staging area
-  // while the previous bucket's runs are written.  The staging area lies in
-  // the bit columns and tables, which only the mask phase uses: the copy
-  // starts after the mask phase and is moved into place before the next one.
-  static_assert(24 * kFusedMax <= kMaskWarps * kTabWords * 4, "staging must fit in the tables");
+  // bit pass: a bucket's members (words and entry ids, gathered in slot
+  // order beforehand) are copied asynchronously into a staging area while
+  // the previous bucket's rows are written.  The staging area lies in the
+  // bit columns and tables, which only the mask phase uses: the copy starts
+  // after the mask phase and is moved into place before the next one.
+  static_assert(20 * kFusedMax <= kMaskWarps * kTabWords * 4, "staging must fit in the tables");
   uint4* w4s = (uint4*)colw;
   int32_t* sfls = (int32_t*)(w4s + smax);
-  int32_t* pids = sfls + smax;
   auto fetch = [&](int64_t o, int s) {
     for (int i = threadIdx.x; i < s; i += kMaskThreads) {
       cp_async16(w4s + i, a.bxz + o + i);
       cp_async4(sfls + i, bmem + o + i);
-      if (FUSED) cp_async4(pids + i, a.bpid + o + i);
     }
     cp_async_commit();
   };
@@ -474,7 +444,6 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       for (int i = threadIdx.x; i < s; i += kMaskThreads) {
         w4[i] = w4s[i];
         sfl[i] = sfls[i];
-        if (FUSED) pid[i] = pids[i];
         cnt[i] = 0;
       }
     } else {
@@ -503,7 +472,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     const uint32_t tab_addr = (uint32_t)__cvta_generic_to_shared(tab);
     __syncthreads();
 
-    uint32_t* rmb = FUSED ? nullptr : a.rmask + moff[b];
+    uint32_t* rmb = a.rmask + moff[b];
     const int nblk = nwb * (nwb + 1) / 2;
     const int q0 = (int)((int64_t)nblk * wid / kMaskWarps), q1 = (int)((int64_t)nblk * (wid + 1) / kMaskWarps);
     int I = 0, J = 0;
@@ -530,9 +499,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       uint32_t cw = jv ? (~anti & rows_ok) : 0u;
       // the diagonal block: no self pair; lower rows keep smaller partners
       if (I == J) cw &= LOWER ? ((1u << lane) - 1u) : ~(1u << lane);
-      if (FUSED)
-        mw[mask_block(true, J, I, nwb) * 32 + lane] = cw;
-      else if (MODE == kMaskBits)
+      if (MODE == kMaskBits)
         mwp[rm_pad_off(J) + lane * ((J + 1) | 1) + I] = cw;
       else
         rmb[mask_block(LOWER, J, I, nwb) * 32 + lane] = cw;
@@ -549,19 +516,23 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     }
     __syncthreads();
     // the next bucket's members go to the staging area (the bit columns and
-    // tables are done with) while this one's runs are written
+    // tables are done with) while this one's rows are written
     if (STAGED) fetch(o2, s2);
-    for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
-    if (MODE == kMaskBits) {
-      // entry of member i: the address of its row's first word (the row's
-      // R + 1 words are consecutive) with i in the top 16 bits, and the
-      // bucket's first slot
+    if (MODE != kMaskBits) {
+      for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
+    } else {
+      // entry of member i: one word with the address of its row's first
+      // word (the row's R + 1 words are consecutive), i and its run length;
+      // the bucket's run total to *a.nnz
+      uint32_t tot = 0;
       for (int i = threadIdx.x; i < s; i += kMaskThreads) {
         const int R = i >> 5;
         const int64_t w0 = moff[b] + 16 * R * (R + 1) + (i & 31) * (R + 1);
-        a.rbits[sfl[i]] = w0 | ((int64_t)i << 48);
-        a.rpbase[sfl[i]] = (int32_t)o;
+        a.rinfo[sfl[i]] = rinfo_pack(w0, i, cnt[i]);
+        tot += (uint32_t)cnt[i];
       }
+      tot = __reduce_add_sync(0xffffffffu, tot);
+      if (lane == 0 && tot) atomicAdd(a.nnz, (unsigned long long)tot);
       // the rows to HBM, row-major: warp per row block, 32 words a step
       for (int R = wid; R < nwb; R += kMaskWarps) {
         const uint32_t d = (uint32_t)(R + 1), m = (65536u + d - 1u) / d, sp = d | 1u;
@@ -570,65 +541,6 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
         for (uint32_t o = lane; o < 32u * d; o += 32u) {
           const uint32_t r = (o * m) >> 16, w = o - r * d;  // o = r d + w, exact for o < 4096 / d
           dst[o] = src[r * sp + w];
-        }
-      }
-    }
-    if (FUSED) {
-      // run offsets inside the bucket: each thread scans two consecutive rows
-      const int i0 = 2 * threadIdx.x;
-      const uint32_t c0 = i0 < s ? (uint32_t)cnt[i0] : 0u, c1 = i0 + 1 < s ? (uint32_t)cnt[i0 + 1] : 0u;
-      uint32_t inc = c0 + c1;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += y;
-      }
-      if (lane == 31) wsum_s[wid] = inc;
-      __syncthreads();
-      uint32_t before = 0, total = 0;
-      for (int w = 0; w < kMaskWarps; ++w) {
-        if (w < wid) before += wsum_s[w];
-        total += wsum_s[w];
-      }
-      const uint32_t ex = before + inc - (c0 + c1);
-      if (i0 < s) roff[i0] = ex;
-      if (i0 + 1 < s) roff[i0 + 1] = ex + c0;
-      if (threadIdx.x == 0) {
-        base_s = atomicAdd(a.cursor, (unsigned long long)total);
-        rb_next = 0;
-      }
-      __syncthreads();
-      const int64_t base = (int64_t)base_s;
-      if (base + (int64_t)total <= a.cap) {
-        for (int i = threadIdx.x; i < s; i += kMaskThreads) a.rstart[sfl[i]] = base + roff[i];
-        // runs: warps take row blocks from a shared counter, largest first;
-        // a block's rows are written one after the other as in the emit
-        // pass (partner ids of the block's partner blocks in registers)
-        const uint32_t lt = lanemask_lt();
-        while (true) {
-          int R = 0;
-          if (lane == 0) R = nwb - 1 - atomicAdd(&rb_next, 1);
-          R = __shfl_sync(0xffffffffu, R, 0);
-          if (R < 0) break;
-          const int nrows = min(32, s - (R << 5));
-          int32_t pv[kEmitChunk];
-#pragma unroll
-          for (int t = 0; t < kEmitChunk; ++t) pv[t] = t <= R ? pid[(t << 5) + lane] : 0;
-          int64_t rc = lane < nrows ? base + roff[(R << 5) + lane] : 0;
-          const uint32_t* wb = mw + (R * (R + 1) / 2) * 32;
-          switch (R + 1) {
-#define PICASSO_FUSED_CASE(N) \
-  case N:                     \
-    emit_rows<N>(wb, pv, rc, nrows, a.col, lane, lt); \
-    break;
-            PICASSO_FUSED_CASE(1) PICASSO_FUSED_CASE(2) PICASSO_FUSED_CASE(3) PICASSO_FUSED_CASE(4)
-            PICASSO_FUSED_CASE(5) PICASSO_FUSED_CASE(6) PICASSO_FUSED_CASE(7) PICASSO_FUSED_CASE(8)
-            PICASSO_FUSED_CASE(9) PICASSO_FUSED_CASE(10) PICASSO_FUSED_CASE(11) PICASSO_FUSED_CASE(12)
-            PICASSO_FUSED_CASE(13) PICASSO_FUSED_CASE(14) PICASSO_FUSED_CASE(15) PICASSO_FUSED_CASE(16)
-#undef PICASSO_FUSED_CASE
-            default:
-              break;
-          }
         }
       }
     }
@@ -642,7 +554,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
 }
 
 // Mask pass for strings of more than one word per part (q > 64): the
-// outputs of the unfused k_bucket_mask (mask blocks and per-entry counts)
+// outputs of the plain k_bucket_mask (mask blocks and per-entry counts)
 // from a direct symplectic form per pair.  Block (I, J >= I) of the upper
 // triangle goes to one warp; lane j keeps partner J*32+j's words in
 // registers and every row I*32+r of the block is read from shared memory
@@ -726,7 +638,7 @@ __global__ void __launch_bounds__(kMaskThreads) k_bucket_mask_wide(ConflictArgs 
 // (the bit columns of the block's rows, transposed in the warp), and each
 // partner word group costs the lookups of the one-word pass.  Members' words
 // are staged slice-major as (x lo, x hi, z lo, z hi).  Same outputs as the
-// unfused k_bucket_mask.
+// plain k_bucket_mask.
 template <bool LOWER>
 __global__ void __launch_bounds__(kMaskThreads) k_bucket_mask_wtab(ConflictArgs a, const int64_t* __restrict__ boff,
                                                                    const int32_t* __restrict__ bmem,
@@ -876,7 +788,7 @@ static cudaError_t launch_mask_wide(const ConflictArgs& a, const int64_t* boff, 
 }
 
 cudaError_t launch_bucket_bits(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, const int64_t* moff,
-                               int32_t smax, int32_t q, cudaStream_t s) {
+                               int32_t smax, int32_t q, cudaStream_t s, int per_sm_cap) {
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   if (smax > kFusedMax || !a.lower || a.qw != 1) return cudaErrorInvalidValue;
   smax = max(smax, 1);
@@ -890,6 +802,7 @@ cudaError_t launch_bucket_bits(const ConflictArgs& a, const int64_t* boff, const
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (per_sm_cap > 0) per_sm = min(per_sm, per_sm_cap);
   const int64_t blocks = debug_grid(std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1)));
   kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, moff, smax);
   count_launches(1);
@@ -945,26 +858,6 @@ cudaError_t launch_bucket_gather(const ConflictArgs& a, const int32_t* bmem, uin
   return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_fused(const ConflictArgs& a, const int64_t* boff, const int32_t* bmem, int32_t smax,
-                                int32_t q, cudaStream_t s) {
-  if (a.P <= 0 || a.n <= 0) return cudaSuccess;
-  if (smax > kFusedMax || !a.lower) return cudaErrorInvalidValue;
-  smax = max(smax, 1);
-  const size_t bytes = fused_smem_bytes(smax);
-  auto kern = q <= 32 ? k_bucket_mask<1, true, kMaskRuns> : k_bucket_mask<2, true, kMaskRuns>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMaskThreads, bytes);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t blocks = debug_grid(std::min<int64_t>(a.P, (int64_t)sms * max(per_sm, 1)));
-  kern<<<(unsigned)blocks, kMaskThreads, bytes, s>>>(a, boff, bmem, nullptr, smax);
-  count_launches(1);
-  return cudaGetLastError();
-}
 
 // Mask words of bucket c: nwb x nwb blocks of 32 words (nwb (nwb + 1) / 2
 // with lower), nwb = ceil(s_c / 32).

@@ -225,7 +225,6 @@ __device__ __forceinline__ void dyn_apply(const DynArgs& d, int32_t v, int64_t j
 // any vertex is active; every step finishes it, so the list is empty after
 // at most n + 1 steps.
 __global__ void k_dyn_all(DynArgs d) {
-  cg::grid_group grid = cg::this_grid();
   int32_t* const ctl = d.ctl;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -242,7 +241,7 @@ __global__ void k_dyn_all(DynArgs d) {
       // S, long work list: first pass, one warp per vertex over its row head
       for (int64_t i = gw; i < m; i += nw)
         dyn_examine(d, __ldcg(cur + i), 0, 1, lane, stamp, ctl + 2 + p, 0, kHeadEntries, ctl + 7);
-      grid.sync();
+      if (!grid_sync_bounded(reinterpret_cast<unsigned int*>(ctl + 8), ctl + 10, kBarrierLimitNs, ctl + 11)) return;
       // second pass: the rows still undecided, split over the warps
       const int64_t nl = __ldcg(ctl + 7);
       if (nl > 0) {
@@ -256,7 +255,7 @@ __global__ void k_dyn_all(DynArgs d) {
       for (int64_t w = gw; w < m * G; w += nw)
         dyn_examine(d, __ldcg(cur + w / G), w % G, G, lane, stamp, ctl + 2 + p, 0, kAll, nullptr);
     }
-    grid.sync();
+    if (!grid_sync_bounded(reinterpret_cast<unsigned int*>(ctl + 8), ctl + 10, kBarrierLimitNs, ctl + 11)) return;
     // A
     const int64_t ns = __ldcg(ctl + 2 + p);
     if (ns > 0) {
@@ -264,7 +263,7 @@ __global__ void k_dyn_all(DynArgs d) {
       for (int64_t w = gw; w < ns * G; w += nw)
         dyn_apply(d, __ldcg(d.sel + w / G), w % G, G, lane, stamp, nxt, ctl + 1 - p, ctl + 4 + p);
     }
-    grid.sync();
+    if (!grid_sync_bounded(reinterpret_cast<unsigned int*>(ctl + 8), ctl + 10, kBarrierLimitNs, ctl + 11)) return;
     // D
     const int64_t nf = __ldcg(ctl + 4 + p), nt = ns + nf;
     if (nt > 0) {
@@ -287,7 +286,7 @@ __global__ void k_dyn_all(DynArgs d) {
       ctl[7] = 0;          // read after the first pass of this step's S only
       if (ns > 0) ctl[6] += 1;
     }
-    grid.sync();
+    if (!grid_sync_bounded(reinterpret_cast<unsigned int*>(ctl + 8), ctl + 10, kBarrierLimitNs, ctl + 11)) return;
   }
 }
 
@@ -295,7 +294,7 @@ __global__ void k_dyn_all(DynArgs d) {
 // the carry at the end.
 __global__ void k_dyn_init(DynArgs d) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < 8) d.ctl[v] = v == 0 ? (int32_t)d.n : 0;
+  if (v < kDynCtlWords) d.ctl[v] = v == 0 ? (int32_t)d.n : 0;
   if (v >= d.n) return;
   const int L = (int)(d.loff[v + 1] - d.loff[v]);
   d.mask[v] = L >= 64 ? ~0ull : ((1ull << L) - 1ull);

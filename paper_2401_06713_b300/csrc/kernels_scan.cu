@@ -109,22 +109,14 @@ size_t scan_tmp_bytes(int64_t n) {
   return (words + 16) * sizeof(int64_t);
 }
 
-// *out (zeroed here) = sum of in[0 .. n): block sums added atomically.
-__global__ void k_sum_u32(const uint32_t* __restrict__ in, int64_t n, unsigned long long* __restrict__ out) {
-  int64_t s = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    s += in[i];
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, (unsigned long long)s);
+__global__ void k_rinfo_lengths(const int64_t* __restrict__ rinfo, int64_t E, uint32_t* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < E) out[e] = (uint32_t)rinfo_len(rinfo[e]);
 }
 
-cudaError_t launch_sum_u32(const uint32_t* in, int64_t n, int64_t* out, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t), s);
-  if (e != cudaSuccess || n <= 0) return e;
-  int64_t blocks = (n + 255) / 256;
-  if (blocks > 148 * 8) blocks = 148 * 8;
-  k_sum_u32<<<(unsigned)blocks, 256, 0, s>>>(in, n, (unsigned long long*)out);
+cudaError_t launch_rinfo_lengths(const int64_t* rinfo, int64_t E, uint32_t* out, cudaStream_t s) {
+  if (E <= 0) return cudaSuccess;
+  k_rinfo_lengths<<<(unsigned)((E + 255) / 256), 256, 0, s>>>(rinfo, E, out);
   count_launches(1);
   return cudaGetLastError();
 }

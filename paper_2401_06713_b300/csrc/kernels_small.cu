@@ -87,11 +87,20 @@ __device__ __forceinline__ int64_t block_excl(int64_t x, int64_t* sm, int64_t* t
 // barrier (release / acquire at cluster scope, which covers global memory
 // written by the cluster's blocks).
 template <bool CL>
-__device__ __forceinline__ void engine_sync() {
+__device__ __forceinline__ bool engine_sync(const SmallArgs& a, int site, int64_t round) {
   if constexpr (CL) {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    return true;
   } else {
-    cg::this_grid().sync();
+    // the grid's barrier is bounded in time: a block that gives up records
+    // where (first one only) and the launch ends with err[3] set
+    int seen = -1;
+    if (grid_sync_bounded(a.bar, a.err + 3, kBarrierLimitNs, &seen)) return true;
+    if (threadIdx.x == 0 && seen >= 0 && atomicCAS((unsigned long long*)(a.ctl + 9), 0ull, (unsigned long long)site) == 0ull) {
+      a.ctl[10] = round;
+      a.ctl[11] = seen;
+    }
+    return false;
   }
 }
 
@@ -100,14 +109,15 @@ __device__ __forceinline__ void engine_sync() {
 // of the chunks before it (part: one word per block).  Contains a grid
 // barrier; every thread of the grid must call it.
 template <bool CL, class TI>
-__device__ void grid_scan(const TI* in, int64_t m, int64_t* out, int64_t* part, int64_t* sm) {
+__device__ bool grid_scan(const SmallArgs& a, int64_t round, const TI* in, int64_t m, int64_t* out, int64_t* part,
+                          int64_t* sm) {
   const int64_t chunk = (m + gridDim.x - 1) / gridDim.x;
   const int64_t lo = min(m, chunk * (int64_t)blockIdx.x), hi = min(m, lo + chunk);
   int64_t x = 0;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) x += (int64_t)in[i];
   x = block_sum(x, sm);
   if (threadIdx.x == 0) part[blockIdx.x] = x;
-  engine_sync<CL>();
+  if (!engine_sync<CL>(a, __LINE__, round)) return false;
   int64_t pre = 0;
   for (int64_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += __ldcg(part + b);
   pre = block_sum(pre, sm);
@@ -120,6 +130,7 @@ __device__ void grid_scan(const TI* in, int64_t m, int64_t* out, int64_t* part, 
     pre += tot;
   }
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[m] = pre;
+  return true;
 }
 }  // namespace
 
@@ -277,10 +288,12 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
   const int64_t stid = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
   const int nsets = a.nsets;
 
-  // the cluster launch takes over from a grid launch that handed off
+  // the cluster launch takes over from a grid launch that handed off (not
+  // from one whose barrier timed out)
+  if (CL && a.err[3] != 0) return;
   if (CL && gtid == 0 && a.ctl[2] == kSmallHandoff) a.ctl[2] = kSmallOk;
   if (blockIdx.x == 0) set_prefixes(a, scan_s);
-  engine_sync<CL>();
+  if (!engine_sync<CL>(a, __LINE__, 0)) return;
 
   while (true) {
     const int64_t n = __ldcg(a.ctl + 0);
@@ -288,13 +301,13 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     const int32_t round = a.round0 + (int32_t)done;
     if (n == 0 || __ldcg(a.ctl + 2) != kSmallOk) break;
     if (round > a.max_rounds) {
-      engine_sync<CL>();
+      if (!engine_sync<CL>(a, __LINE__, round)) return;
       if (gtid == 0) a.ctl[2] = kSmallMaxRounds;
       break;
     }
     if (!CL && n <= a.handoff) {
       // small enough for one cluster: its barriers cost far less
-      engine_sync<CL>();
+      if (!engine_sync<CL>(a, __LINE__, round)) return;
       if (gtid == 0) a.ctl[2] = kSmallHandoff;
       break;
     }
@@ -315,7 +328,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     }
     for (int64_t t = gtid; t < kClistWords * P; t += gthreads) a.clist[t] = 0;
     if (gtid == 0) a.err[1] = 0;
-    engine_sync<CL>();
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
 
     // rank of vertex i = its set's offset + the number of smaller keys in the
     // set: warp per vertex, lanes over the set; the round's arrays are
@@ -336,7 +349,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         for (int k = 0; k < 2 * W; ++k) a.xz_r[2 * W * rk + k] = a.xz[2 * W * (int64_t)g + k];
       }
     }
-    engine_sync<CL>();
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
 
     // lists in rank order (bucket colors: + the set's offset), list offsets,
     // entry owners, first candidates (the ranked coloring reads no priority
@@ -358,16 +371,16 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     if (gtid == 0) a.loff[n] = E;
     // bucket work items (32 members each); a bucket above the cap stops the
     // engine
-    engine_sync<CL>();
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
     for (int64_t c = gtid; c < P; c += gthreads) {
       const uint32_t sc = a.bcnt[c];
       a.bitems[c] = (sc + 31) / 32;
       if (sc > (uint32_t)kSmallBucketCap) a.err[2] = 1;
     }
-    grid_scan<CL>(a.bcnt, P, a.boff, a.part, scan_s);
-    engine_sync<CL>();
-    grid_scan<CL>(a.bitems, P, a.iboff, a.part, scan_s);
-    engine_sync<CL>();
+    if (!grid_scan<CL>(a, round, a.bcnt, P, a.boff, a.part, scan_s)) return;
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (!grid_scan<CL>(a, round, a.bitems, P, a.iboff, a.part, scan_s)) return;
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
     if (__ldcg(a.err + 2) != 0) {
       if (gtid == 0) a.ctl[2] = kSmallOverflow;
       break;
@@ -380,7 +393,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     for (int64_t c = gtid; c < P; c += gthreads)
       for (int64_t t = a.iboff[c]; t < a.iboff[c + 1]; ++t) a.ibkt[t] = (int32_t)c;
     if (gtid == 0) a.ctl[8] = a.iboff[P];
-    engine_sync<CL>();
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
 
     // each bucket ascending (entries ascend with the rank), then its
     // members' ranks and words in that order
@@ -396,12 +409,12 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         for (int k = 0; k < 2 * W; ++k) a.bxz[2 * W * (b0 + i) + k] = a.xz_r[2 * W * (int64_t)r + k];
       }
     }
-    engine_sync<CL>();
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
 
     bucket_runs<W, false>(a, Rw, Xw, lane, gwarp, nwarps);
-    engine_sync<CL>();
-    grid_scan<CL>(a.cnt, E, a.runoff, a.part, scan_s);
-    engine_sync<CL>();
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (!grid_scan<CL>(a, round, a.cnt, E, a.runoff, a.part, scan_s)) return;
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
     {
       const int64_t nnz = __ldcg(a.runoff + E);
       const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
@@ -412,7 +425,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       if (gtid == 0) a.ctl[6] += nnz;
     }
     bucket_runs<W, true>(a, Rw, Xw, lane, gwarp, nwarps);
-    engine_sync<CL>();
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
 
     // ordered first fit in rank order; warps take ranks from a counter
     {
@@ -437,7 +450,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         ok = ordered_vertex<true>(ca, t, lane, a.err);
       }
     }
-    engine_sync<CL>();
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
     if (__ldcg(a.err) != 0) {
       if (gtid == 0) a.ctl[2] = kSmallTimeout;
       break;
@@ -454,9 +467,9 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       }
       a.flag[a.perm[r]] = colored ? 0u : 1u;
     }
-    engine_sync<CL>();
-    grid_scan<CL>(a.flag, n, a.pos, a.part, scan_s);
-    engine_sync<CL>();
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (!grid_scan<CL>(a, round, a.flag, n, a.pos, a.part, scan_s)) return;
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
     for (int64_t i = gtid; i < n; i += gthreads)
       if (a.flag[i]) gid_next[a.pos[i]] = gid[i];
     if (blockIdx.x == 0) {
@@ -484,7 +497,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       __syncthreads();
       set_prefixes(a, scan_s);
     }
-    engine_sync<CL>();
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
   }
 }
 
@@ -496,7 +509,8 @@ size_t small_smem_bytes(int32_t qw) {
 // the rounds above a.handoff vertices; the cluster launch (one cluster of
 // cluster_blocks blocks) runs the rest.  `cluster_blocks` 0: no cluster
 // launch (the grid launch runs every round).
-cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_blocks, cudaStream_t s) {
+cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_blocks, int blocks_per_sm,
+                                cudaStream_t s) {
   int dev = 0, sms = 148, per_sm = 0;
   if (a.qw != 1 && a.qw != 2) return cudaErrorInvalidValue;
   const size_t smem = small_smem_bytes(a.qw);
@@ -514,7 +528,8 @@ cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_bl
     if (per_sm < 1) return cudaErrorLaunchOutOfResources;
     // fewer resident blocks make each grid barrier cheaper; two per SM keep
     // 16 warps per SM for the latency-bound phases
-    int blocks = std::min(per_sm, kSmallBlocksPerSm) * sms;
+    int blocks = std::min(per_sm, blocks_per_sm > 0 ? std::min(blocks_per_sm, kSmallBlocksPerSm) : kSmallBlocksPerSm) *
+                 sms;
     blocks = std::min(blocks, part_cap);
     blocks = (int)debug_grid(blocks);
     void* params[] = {(void*)&args};

@@ -29,6 +29,20 @@ class PicassoError(RuntimeError):
         super().__init__(f"{where}: {msg} (status {status})")
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [
+        ("engine_blocks_per_sm", ctypes.c_int32),
+        ("cluster_max_n", ctypes.c_int32),
+        ("cluster_blocks", ctypes.c_int32),
+        ("bits_blocks_per_sm", ctypes.c_int32),
+        ("color_blocks_per_sm", ctypes.c_int32),
+        ("engine_max_n", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class Config(ctypes.Structure):
     _fields_ = [
         ("seed", ctypes.c_uint64),
@@ -43,6 +57,7 @@ class Config(ctypes.Structure):
         ("small_engine", ctypes.c_int32),
         ("budget_mode", ctypes.c_int32),
         ("wait_polls", ctypes.c_int32),
+        ("sched", Schedule),
     ]
 
 
@@ -88,6 +103,7 @@ class Stats(ctypes.Structure):
         ("t_small_ms", ctypes.c_double),
         ("round_chunks", ctypes.c_int32),
         ("host_csr_rounds", ctypes.c_int32),
+        ("barrier_timeout", ctypes.c_int32 * 4),
     ]
 
     def as_dict(self):
@@ -118,6 +134,9 @@ _SIGS = {
     "picasso_carry": [_vp, _pi64],
     "picasso_round": [_vp, _pi64],
     "picasso_run": [_vp, _vp, _pi32],
+    "picasso_autotune": [ctypes.POINTER(Config), _vp, _pi64, _i32, ctypes.POINTER(ctypes.c_uint64), _i32, _i32,
+                         ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                         _vp],
     "picasso_get_colors": [_vp, _vp],
     "picasso_get_round": [_vp, _vp, _vp, _vp],
     "picasso_get_runs": [_vp, ctypes.POINTER(_vp)],
@@ -227,6 +246,37 @@ def philox_draws(seed: int, rnd: int, gid: int, tag: int, i0: int, count: int, d
     return out
 
 
+def autotune(xz: torch.Tensor, q: int, set_offsets=None, seeds=None, reps: int = 3, seed: int = 0,
+             palette=(1, 8), alpha: float = 2.0, schedule=None, stream=None):
+    """picasso_autotune over the sets of ``xz`` (one set when set_offsets is
+    None): returns (schedule dict, its median ms per run, the starting
+    schedule's median ms)."""
+    assert xz.is_cuda and xz.dtype == torch.int64 and xz.shape[1] == 2 * words_per_part(q)
+    xz = xz.contiguous()
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    cfg = Config()
+    _ck(_lib().picasso_config_default(ctypes.byref(cfg)), "picasso_config_default")
+    cfg.seed = seed
+    cfg.palette_num, cfg.palette_den = palette
+    cfg.alpha = alpha
+    for k, v in (schedule or {}).items():
+        setattr(cfg.sched, k, int(v))
+    offs_l = [0, int(xz.shape[0])] if set_offsets is None else [int(x) for x in set_offsets]
+    nsets = len(offs_l) - 1
+    offs = (ctypes.c_int64 * len(offs_l))(*offs_l)
+    sd = None
+    if seeds is not None:
+        sd = (ctypes.c_uint64 * nsets)(*[int(x) for x in seeds])
+    elif set_offsets is None:
+        sd = (ctypes.c_uint64 * 1)(seed)
+    best = Schedule()
+    bms, sms = ctypes.c_double(), ctypes.c_double()
+    _ck(_lib().picasso_autotune(ctypes.byref(cfg), _ptr(xz), offs, nsets, sd, q, reps, ctypes.byref(best),
+                                ctypes.byref(bms), ctypes.byref(sms), ctypes.c_void_p(stream.cuda_stream)),
+        "picasso_autotune")
+    return best.as_dict(), float(bms.value), float(sms.value)
+
+
 class Picasso:
     """A context over packed strings ``xz`` (int64 [n, 2W] on the GPU, W =
     ceil(q / 64))."""
@@ -234,10 +284,11 @@ class Picasso:
     def __init__(self, xz: torch.Tensor, q: int, seed: int = 0, palette=(1, 8), alpha: float = 2.0,
                  algo: str = "auto", max_rounds: int = 100000, byte_budget: int = 0, stream=None,
                  color: str = "auto", set_offsets=None, seeds=None, csr: str = "earlier", small: str = "auto",
-                 budget_mode: str = "fail", wait_polls: int = 0):
+                 budget_mode: str = "fail", wait_polls: int = 0, schedule=None):
         """One set, or with ``set_offsets`` (host, nsets + 1 ints) a batch of
         independent sets stored back to back in ``xz`` (seeds default to
-        seed + k)."""
+        seed + k).  ``schedule``: a dict of picasso_schedule fields (launch
+        shapes only; ``autotune`` returns one)."""
         assert xz.is_cuda and xz.dtype == torch.int64 and xz.dim() == 2 and xz.shape[1] == 2 * words_per_part(q)
         self.xz = xz.contiguous()
         self.n = int(xz.shape[0])
@@ -257,6 +308,8 @@ class Picasso:
         cfg.small_engine = SMALL_ENGINE[small]
         cfg.budget_mode = BUDGET_MODES[budget_mode]
         cfg.wait_polls = wait_polls
+        for k, v in (schedule or {}).items():
+            setattr(cfg.sched, k, int(v))
         self.cfg = cfg
         h = ctypes.c_void_p()
         if set_offsets is None:
@@ -324,7 +377,13 @@ class Picasso:
         if out is None:
             out = torch.empty(self.n, dtype=torch.int32, device=self.xz.device)
         r = ctypes.c_int32()
-        _ck(_lib().picasso_run(self.h, _ptr(out), ctypes.byref(r)), "picasso_run")
+        st = _lib().picasso_run(self.h, _ptr(out), ctypes.byref(r))
+        if st == ERR_TIMEOUT:
+            # a bounded grid barrier gave up: say where
+            bt = self.stats()["barrier_timeout"]
+            raise PicassoError(st, f"picasso_run (barrier timeout: kernel {bt[0]}, site {bt[1]}, "
+                                   f"round {bt[2]}, arrivals {bt[3]})")
+        _ck(st, "picasso_run")
         return out, int(r.value)
 
     # -- inspection

@@ -124,3 +124,75 @@ def test_batch_equals_single_runs_larger(pc):
         with pc.Picasso(xz, q, seed=seeds[k]) as p:
             single, _ = p.run()
         assert np.array_equal(colors[offs[k]:offs[k + 1]], single.cpu().numpy()), k
+
+
+# Launch schedules (picasso_schedule): the engine's grid, the rounds it gives
+# to one thread-block cluster, the blocks per SM of the bit pass and of the
+# mask coloring.  None of them may change a color.
+_SCHEDULES = [
+    {},
+    {"engine_blocks_per_sm": 1},
+    {"cluster_max_n": -1},
+    {"cluster_max_n": 512, "cluster_blocks": 8},
+    {"cluster_max_n": 8192, "cluster_blocks": 2},
+    {"bits_blocks_per_sm": 2, "color_blocks_per_sm": 3},
+    {"bits_blocks_per_sm": 1, "color_blocks_per_sm": 1, "engine_blocks_per_sm": 1},
+    {"engine_max_n": 4096},
+    {"engine_max_n": 64, "cluster_max_n": 16},
+]
+
+
+def _mixed_sets():
+    # a batch whose first rounds go through the per-round path (more than
+    # 16,384 strings), the bit pass and the mask coloring, then the engine's
+    # grid and cluster launches
+    specs = [(9000, 64, 0.25), (300, 16, 0.4), (6000, 48, 0.2), (2200, 32, 0.35), (1, 24, 0.3)]
+    return [(synth.pauli_weighted(n, q, p, seed=17, stream=i), q) for i, (n, q, p) in enumerate(specs)]
+
+
+@pytest.mark.parametrize("sched", _SCHEDULES)
+def test_schedules_keep_colors(pc, orc, sched):
+    sets = _mixed_sets()
+    seeds = [40 + k for k in range(len(sets))]
+    padded, offs, q = _batch(sets)
+    xz = pc.pack(torch.from_numpy(padded).cuda())
+    with pc.Picasso(xz, q, set_offsets=offs, seeds=seeds, schedule=sched) as p:
+        colors, _ = p.run()
+        colors = colors.cpu().numpy()
+        st = p.stats()
+    assert st["small_rounds"] > 0 and st["pairs_launches"] > 0
+    for k, (c, _) in enumerate(sets):
+        ref, _, _ = orc.run(c, seeds[k], 1, 8, 2.0)
+        assert np.array_equal(colors[offs[k]:offs[k + 1]], ref), (sched, k)
+
+
+def test_autotune_picks_a_valid_schedule(pc, orc):
+    sets = _mixed_sets()
+    seeds = [40 + k for k in range(len(sets))]
+    padded, offs, q = _batch(sets)
+    xz = pc.pack(torch.from_numpy(padded).cuda())
+    best, best_ms, start_ms = pc.autotune(xz, q, set_offsets=offs, seeds=seeds, reps=1)
+    assert set(best) == {"engine_blocks_per_sm", "cluster_max_n", "cluster_blocks", "bits_blocks_per_sm",
+                         "color_blocks_per_sm", "engine_max_n"}
+    assert best["engine_max_n"] in (0, 16384, 8192, 4096)
+    assert best["engine_blocks_per_sm"] in (0, 1, 2) and best["cluster_max_n"] in (0, -1, 512, 2048, 8192)
+    assert best["cluster_blocks"] in (0, 8, 16) and best["bits_blocks_per_sm"] in (0, 2, 3, 4)
+    assert best["color_blocks_per_sm"] in (0, 3, 4, 6)
+    # a candidate replaces the start only if it is at least 1 % faster
+    assert 0 < best_ms <= start_ms
+    with pc.Picasso(xz, q, set_offsets=offs, seeds=seeds, schedule=best) as p:
+        colors = p.run()[0].cpu().numpy()
+    for k, (c, _) in enumerate(sets):
+        ref, _, _ = orc.run(c, seeds[k], 1, 8, 2.0)
+        assert np.array_equal(colors[offs[k]:offs[k + 1]], ref), k
+
+
+@pytest.mark.parametrize("bad", [{"engine_blocks_per_sm": 3}, {"cluster_max_n": -2}, {"cluster_max_n": 16385},
+                                 {"cluster_blocks": 6}, {"bits_blocks_per_sm": 5}, {"color_blocks_per_sm": 9},
+                                 {"engine_max_n": -1}, {"engine_max_n": 16385}])
+def test_schedule_validated(pc, bad):
+    chars = synth.pauli_uniform(50, 10, seed=2)
+    xz = pc.pack(torch.from_numpy(chars).cuda())
+    with pytest.raises(pc.PicassoError) as e:
+        pc.Picasso(xz, 10, schedule=bad)
+    assert e.value.status == pc.ERR_INVALID_ARG

@@ -155,3 +155,22 @@ def test_dynamic_full_size_n1m(pc, orc):
         a, b = order_c[:-d][same], order_c[d:][same]
         assert ((np.bitwise_count(np.bitwise_and(enc[a], enc[b])).sum(axis=1) % 2) == 1).all()
         d += 1
+
+
+def test_parallel_rule_against_sequential_alg2(pc, orc):
+    # the n = 1M law at n = 8,000: the GPU runs Alg. 2's order under the
+    # parallel rule (exactly the oracle's parallel rule); the oracle's
+    # sequential Alg. 2 shows what that reading costs in colors.  Measured
+    # here: sequential 1,104 colors (sum of P over the rounds), parallel
+    # rule 1,112 (+0.7 %), static Random order 1,143.
+    chars = synth.pauli_weighted(8000, 64, 0.25, seed=3)
+    seq, _, sst = orc.run(chars, 3, 1, 16, 1.5, colorer="dynamic")
+    par, prounds, pst = orc.run(chars, 3, 1, 16, 1.5, colorer="dynamic_par")
+    _, _, tst = orc.run(chars, 3, 1, 16, 1.5)
+    with pc.Picasso(_xz(pc, chars), 64, seed=3, palette=(1, 16), alpha=1.5, color="dynamic") as p:
+        got, rounds = p.run()
+        used = p.stats()["colors_used"]
+    assert rounds == prounds and np.array_equal(got.cpu().numpy(), par)
+    c_seq, c_par, c_static = int(sst[:, 1].sum()), int(pst[:, 1].sum()), int(tst[:, 1].sum())
+    assert used == c_par
+    assert c_par <= 1.02 * c_seq and c_seq < c_static and c_par < c_static

@@ -171,11 +171,11 @@ def test_conflict_weighted_mid(pc, orc):
 
 
 @pytest.mark.parametrize("P,lo,hi", [(500, 440, 480), (450, 500, 512)])
-def test_conflict_fused_large_buckets(pc, orc, P, lo, hi):
-    # the fused build pass at the bucket sizes of the n = 1M workload (mean
+def test_conflict_bits_large_buckets(pc, orc, P, lo, hi):
+    # the bit pass of the build at the bucket sizes of the n = 1M workload (mean
     # n L / P = 408) and up to its limit of 512 members (mean 453, largest
     # 511): n = 12,000 strings of the weighted law, L = 17; whole CSRs of
-    # both forms (EARLIER through the fused pass, FULL through the two-pass
+    # both forms (EARLIER through the bit pass, FULL through the two-pass
     # build) element by element against the oracle
     n, L, seed = 12000, 17, 7
     chars = synth.pauli_weighted(n, 64, 0.25, seed=21)
@@ -186,18 +186,18 @@ def test_conflict_fused_large_buckets(pc, orc, P, lo, hi):
         st = p.stats()
         assert lo <= st["max_bucket"] <= hi
         # the bit pass (the per-round default for buckets of at most 512
-        # members) counts 36 bytes per list entry and 4 per word of the
+        # members) counts 28 bytes per list entry and 4 per word of the
         # buckets' lower blocks: 32 nwb (nwb + 1) / 2 words, nwb = ceil(s / 32)
         _, lists, _ = p.round_state()
         sizes = np.bincount(lists.cpu().numpy().ravel(), minlength=P).astype(np.int64)
         nwb = (sizes + 31) // 32
         words = int((16 * nwb * (nwb + 1)).sum())
-        assert st["emit_launches"] == 1 and st["emit_bytes"] == 4 * words + 36 * n * L
+        assert st["emit_launches"] == 1 and st["emit_bytes"] == 4 * words + 28 * n * L
 
 
 @pytest.mark.parametrize("P,palette,alpha", [(450, (3, 80), 1.8)])
 @pytest.mark.parametrize("small", ["off", "auto"])
-def test_run_fused_large_buckets(pc, orc, P, palette, alpha, small):
+def test_run_bits_large_buckets(pc, orc, P, palette, alpha, small):
     # whole runs whose every per-round build has buckets of about 450 members
     n = 12000
     assert orc.round_params(n, *palette, alpha) == (P, 17)
@@ -310,10 +310,10 @@ def test_run_all_identity(pc, orc):
 
 
 def test_run_all_commuting_bucket_path(pc, orc):
-    # Z/I strings all commute, so every pair of a bucket is an edge: the fused
-    # build's first column estimate (from the default commuting ratio) is too
-    # small and it reruns with the exact size; per round the CSR is checked
-    # against the oracle through the canonical form
+    # Z/I strings all commute, so every pair of a bucket is an edge: every bit
+    # of the bit layout's rows is set (the densest runs the coloring reads);
+    # per round the CSR is checked against the oracle through the canonical
+    # form
     g = np.random.default_rng(12)
     chars = (g.integers(0, 2, size=(4000, 16)) * 3).astype(np.uint8)  # 0 = I, 3 = Z
     _run_both(pc, orc, chars, 3, 1, 8, 2.0, small="off")
