@@ -232,8 +232,15 @@ struct Ctx {
   std::unordered_map<void*, size_t> sizes;
   int64_t cur_bytes = 0, peak_bytes = 0;
 
-  // timing (CUDA events on s): ev[0..1] phase, ev[2..5] pair kernels
-  cudaEvent_t ev[6] = {};
+  // timing (CUDA events on s): ev[2..5] pair kernels; phase p (assign,
+  // build, color, carry, small) ev[6 + 2p] .. ev[7 + 2p], read when the
+  // phase comes again or the stats are asked for (no synchronisation of its
+  // own: the elapsed time of events long complete)
+  static constexpr int kEvents = 16;
+  cudaEvent_t ev[kEvents] = {};
+  double* phase_acc[5] = {};
+  bool phase_pending[5] = {};
+  int phase_cur = -1;
   int32_t rounds_done = 0;
   double t_assign = 0, t_build = 0, t_color = 0, t_carry = 0, t_pairs = 0, t_emit = 0;
   int64_t pairs_launches = 0, logical_pairs = 0, tested_pairs = 0, emit_launches = 0, emit_bytes = 0;
@@ -363,25 +370,53 @@ int check(Ctx* c) {
 // Phase timers: CUDA events on the context's stream, and an NVTX range of
 // the phase's name for profilers (a range left open by an error return is
 // closed by the next phase).
+int phase_index(const char* name) {
+  static const char* names[5] = {"assign", "build", "color", "carry", "small"};
+  for (int i = 0; i < 5; ++i)
+    if (std::strcmp(name, names[i]) == 0) return i;
+  return 0;
+}
+
+// Fold phase p's pending time into its accumulator (waits for its end
+// event, which in the normal flow completed long before).
+cudaError_t phase_resolve(Ctx* c, int p) {
+  if (!c->phase_pending[p]) return cudaSuccess;
+  c->phase_pending[p] = false;
+  cudaError_t e = cudaEventSynchronize(c->ev[7 + 2 * p]);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev[6 + 2 * p], c->ev[7 + 2 * p]);
+  if (e == cudaSuccess) *c->phase_acc[p] += ms;
+  return e;
+}
+
+cudaError_t phase_resolve_all(Ctx* c) {
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < 5; ++p) {
+    const cudaError_t e2 = phase_resolve(c, p);
+    if (e == cudaSuccess) e = e2;
+  }
+  return e;
+}
+
 void phase_begin(Ctx* c, const char* name) {
   if (c->nvtx_open) nvtxRangePop();
   nvtxRangePushA(name);
   c->nvtx_open = true;
-  cudaEventRecord(c->ev[0], c->s);
+  const int p = phase_index(name);
+  phase_resolve(c, p);  // its events are about to be reused
+  c->phase_cur = p;
+  cudaEventRecord(c->ev[6 + 2 * p], c->s);
 }
-
-// Records the end event, waits for it and adds the elapsed time to *acc.
 cudaError_t phase_end(Ctx* c, double* acc) {
   if (c->nvtx_open) nvtxRangePop();
   c->nvtx_open = false;
-  cudaError_t e = cudaEventRecord(c->ev[1], c->s);
-  if (e == cudaSuccess) e = cudaEventSynchronize(c->ev[1]);
-  float ms = 0.f;
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
-  if (e == cudaSuccess) *acc += ms;
+  const int p = c->phase_cur < 0 ? 0 : c->phase_cur;
+  cudaError_t e = cudaEventRecord(c->ev[7 + 2 * p], c->s);
+  c->phase_acc[p] = acc;
+  c->phase_pending[p] = e == cudaSuccess;
+  c->phase_cur = -1;
   return e;
 }
-
 double elapsed(Ctx* c, int a, int b) {
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) return 0.0;
@@ -1112,7 +1147,6 @@ int color_round(Ctx* c) {
     a.bboff = c->bt_boff;
     a.rmask = c->bt_rmask;
     a.bpid = c->bt_bpid;
-    a.rstride = 1;  // a row's words are consecutive
   }
   a.col = c->col;
   a.state = c->state;
@@ -1257,12 +1291,8 @@ int run_small(Ctx* c) {
   const int ns = c->nsets;
   cudaStream_t s = c->s;
   // sizes at the start bound every later round (P and L grow with n):
-  // vertices, bucket colors, list entries, and the column capacity: the
-  // expected run entries of the first round if every pair commuted (n_k
-  // (n_k - 1) / 2 pairs per set sharing L^2 / P colors on average) plus
-  // slack; a round above it goes back to the per-round path
+  // vertices, bucket colors, list entries, and the words of the bit rows
   int64_t mmax = 0, P0 = 0, E0 = 0;
-  double pairs = 0.0;
   for (int k = 0; k < ns; ++k) {
     const int64_t m = c->remaining[k];
     if (m == 0) continue;
@@ -1272,9 +1302,11 @@ int run_small(Ctx* c) {
     mmax = std::max(mmax, m);
     P0 += P;
     E0 += m * L;
-    pairs += 0.5 * (double)m * (double)(m - 1) * L * (double)L / (double)P;
   }
-  const int64_t cap = std::max<int64_t>(int64_t(1) << 22, (int64_t)pairs + (int64_t(1) << 20));
+  // the bit rows of a round: a bucket of s <= kSmallBucketCap members has
+  // 16 nwb (nwb + 1) <= 9.5 s + 32 words (nwb = ceil(s / 32)); a round's
+  // buckets hold at most E0 entries over at most P0 colors
+  const int64_t wcap = 10 * E0 + 32 * P0 + 1024;
   std::vector<int2> ptab((size_t)mmax + 1);
   ptab[0] = make_int2(0, 0);
   for (int64_t m = 1; m <= mmax; ++m) {
@@ -1296,18 +1328,20 @@ int run_small(Ctx* c) {
   SmallArgs a{};
   int2* d_ptab = nullptr;
   int64_t* d_sw = nullptr;
-  int32_t *gid_a = nullptr, *gid_b = nullptr, *perm = nullptr, *gid_r = nullptr, *lists = nullptr, *col = nullptr;
+  int32_t *gid_a = nullptr, *gid_b = nullptr, *perm = nullptr, *gid_r = nullptr, *lists = nullptr;
   int32_t *err = nullptr, *bmem = nullptr, *brank = nullptr, *ibkt = nullptr, *sid = nullptr, *ent_v = nullptr;
   uint64_t* bxz = nullptr;
   uint32_t* bitems = nullptr;
   int64_t* iboff = nullptr;
   uint64_t *xz_r = nullptr, *state = nullptr, *key = nullptr;
-  int64_t *loff = nullptr, *runoff = nullptr, *pos = nullptr, *part = nullptr, *ctl = nullptr, *boff = nullptr;
-  uint32_t *cnt = nullptr, *flag = nullptr, *bcnt = nullptr, *bcur = nullptr, *clist = nullptr, *sbar = nullptr;
+  int64_t *loff = nullptr, *rinfo = nullptr, *pos = nullptr, *part = nullptr, *ctl = nullptr, *boff = nullptr;
+  int64_t *moff = nullptr, *snnz = nullptr;
+  uint32_t *rmask = nullptr, *bwords = nullptr, *flag = nullptr, *bcnt = nullptr, *bcur = nullptr, *cmask = nullptr,
+           *sbar = nullptr;
   int st = PICASSO_OK;
   auto cleanup = [&]() {
     release(c, &d_ptab);
-    release(c, &clist);
+    release(c, &cmask);
     release(c, &d_sw);
     release(c, &gid_a);
     release(c, &gid_b);
@@ -1316,18 +1350,20 @@ int run_small(Ctx* c) {
     release(c, &sid);
     release(c, &lists);
     release(c, &ent_v);
-    release(c, &col);
+    release(c, &rmask);
+    release(c, &bwords);
+    release(c, &moff);
+    release(c, &snnz);
     release(c, &err);
     release(c, &xz_r);
     release(c, &state);
     release(c, &key);
     release(c, &loff);
-    release(c, &runoff);
+    release(c, &rinfo);
     release(c, &pos);
     release(c, &part);
     release(c, &ctl);
     release(c, &sbar);
-    release(c, &cnt);
     release(c, &flag);
     release(c, &bcnt);
     release(c, &bcur);
@@ -1368,15 +1404,17 @@ int run_small(Ctx* c) {
   TRY(alloc(c, &lists, E0));
   TRY(alloc(c, &ent_v, E0));
   TRY(alloc(c, &loff, n0 + 1));
-  TRY(alloc(c, &cnt, E0));
-  TRY(alloc(c, &runoff, E0 + 1));
-  TRY(alloc(c, &col, cap));
+  TRY(alloc(c, &rinfo, E0));
+  TRY(alloc(c, &rmask, wcap));
+  TRY(alloc(c, &bwords, P0));
+  TRY(alloc(c, &moff, P0 + 1));
+  TRY(alloc(c, &snnz, ns));
   TRY(alloc(c, &state, n0));
   TRY(alloc(c, &flag, n0));
   TRY(alloc(c, &pos, n0 + 1));
   TRY(alloc(c, &key, n0));
   TRY(alloc(c, &bcnt, P0));
-  TRY(alloc(c, &clist, kClistWords * P0));
+  TRY(alloc(c, &cmask, 32 * P0));
   TRY(alloc(c, &bcur, P0));
   TRY(alloc(c, &boff, P0 + 1));
   TRY(alloc(c, &bmem, E0));
@@ -1414,7 +1452,7 @@ int run_small(Ctx* c) {
   a.seoff = d_sw + 5 * ns + 2;
   a.sseed = reinterpret_cast<const uint64_t*>(d_sw + 6 * ns + 3);
   a.ptab = d_ptab;
-  a.cap = cap;
+  a.wcap = wcap;
   a.budget = c->cfg.byte_budget;
   a.xz = c->xz_user;
   a.gid_a = gid_a;
@@ -1428,9 +1466,11 @@ int run_small(Ctx* c) {
   a.lists = lists;
   a.ent_v = ent_v;
   a.loff = loff;
-  a.cnt = cnt;
-  a.runoff = runoff;
-  a.col = col;
+  a.rinfo = rinfo;
+  a.rmask = rmask;
+  a.bwords = bwords;
+  a.moff = moff;
+  a.snnz = snnz;
   a.state = state;
   a.flag = flag;
   a.pos = pos;
@@ -1438,7 +1478,7 @@ int run_small(Ctx* c) {
   a.key = key;
   a.bcnt = bcnt;
   a.bcur = bcur;
-  a.clist = clist;
+  a.cmask = cmask;
   a.boff = boff;
   a.bitems = bitems;
   a.iboff = iboff;
@@ -1722,7 +1762,7 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
     return map_err(e);
   }
   int st = PICASSO_OK;
-  for (int i = 0; i < 6 && st == PICASSO_OK; ++i) st = map_err(cudaEventCreate(&c->ev[i]));
+  for (int i = 0; i < Ctx::kEvents && st == PICASSO_OK; ++i) st = map_err(cudaEventCreate(&c->ev[i]));
   if (st == PICASSO_OK) st = alloc(c, &c->color, n);
   if (st == PICASSO_OK) st = alloc(c, &c->d_err, 4);
   if (st == PICASSO_OK) st = alloc(c, &c->d_soff, nsets + 1);
@@ -1741,7 +1781,7 @@ int init_common(void** out, const picasso_config* cfg, const uint64_t* d_xz, con
     release(c, &c->d_sets);
     release(c, &c->d_hist);
     release(c, &c->d_set_bytes);
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < Ctx::kEvents; ++i)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     pinned_put(c->h_buf);
     delete c;
@@ -2108,6 +2148,7 @@ int picasso_copy_runs(void* ctx, int64_t* d_runoff) {
 int picasso_get_stats(void* ctx, picasso_stats* out) {
   Ctx* c = (Ctx*)ctx;
   if (!c || !out) return PICASSO_ERR_INVALID_ARG;
+  phase_resolve_all(c);
   std::memset(out, 0, sizeof(*out));
   out->round = c->round;
   out->n_total = c->N;
@@ -2386,7 +2427,7 @@ int picasso_destroy(void* ctx) {
   release(c, &c->d_set_bytes);
   cudaStreamSynchronize(c->s);
   hostcol_put(c->hcol, c->hcol_cap);
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < Ctx::kEvents; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   pinned_put(c->h_buf);
   delete c;

@@ -215,18 +215,29 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
 constexpr int kMaskCands = 8;
 
 // Mark list entries [from, to) of v (row = loff[v]) except `skip`: resolved.
-__device__ __forceinline__ void mask_resolve(const ColorArgs& a, int64_t row, int from, int to, int skip, int lane) {
-  for (int t = from + lane; t < to; t += 32) {
-    if (t == skip) continue;
-    const uint32_t c = (uint32_t)__ldg(a.lists + row + t);
-    const int slot = rinfo_slot(__ldg(a.rinfo + row + t));
+// Entries kb .. kb + 31 come from the lanes' registers (lane t holds entry
+// kb + t's color c and packed word rb), the others (lists of more than 32
+// colors) from memory.
+template <bool FRESH>
+__device__ __forceinline__ void mask_resolve(const ColorArgs& a, int64_t row, int from, int to, int skip, int lane,
+                                             int kb, uint32_t c, int64_t rb) {
+  const int t = kb + lane;
+  if (t >= from && t < to && t != skip) {
+    const int slot = rinfo_slot(rb);
     atomicOr(a.cmask + (size_t)c * 32 + 16 + (slot >> 5), 1u << (slot & 31));
+  }
+  for (int u = from + lane; u < to; u += 32) {
+    if (u == skip || (u >= kb && u < kb + 32)) continue;
+    const uint32_t cu = (uint32_t)ld_run<FRESH>(a.lists + row + u);
+    const int slot = rinfo_slot(ld_run<FRESH>(a.rinfo + row + u));
+    atomicOr(a.cmask + (size_t)cu * 32 + 16 + (slot >> 5), 1u << (slot & 31));
   }
 }
 
+template <bool FRESH>
 __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
-  const int64_t row = __ldg(a.loff + v);
-  const int L = (int)(__ldg(a.loff + v + 1) - row);
+  const int64_t row = ld_run<FRESH>(a.loff + v);
+  const int L = (int)(ld_run<FRESH>(a.loff + v + 1) - row);
   const int h = lane >> 4, W = lane & 15;
   int polls = 0;
   int kdone = 0;  // entries [0, kdone) passed and marked resolved
@@ -235,8 +246,8 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
     uint32_t my_c = 0u;
     int64_t my_rb = 0;
     if (kl < L) {
-      my_c = (uint32_t)__ldg(a.lists + row + kl);
-      my_rb = __ldg(a.rinfo + row + kl);
+      my_c = (uint32_t)ld_run<FRESH>(a.lists + row + kl);
+      my_rb = ld_run<FRESH>(a.rinfo + row + kl);
     }
     const int kend = min(L - kb, 32);
     for (int k0 = 0; k0 < kend; k0 += kMaskCands) {
@@ -247,7 +258,7 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
         const uint32_t c = __shfl_sync(0xffffffffu, my_c, min(kk, 31));
         const int64_t rb = __shfl_sync(0xffffffffu, my_rb, min(kk, 31));
         const bool act = kk < kend && W <= (rinfo_slot(rb) >> 5);
-        rw[p] = act ? __ldg(a.rmask + rinfo_addr(rb) + (int64_t)a.rstride * W) : 0u;
+        rw[p] = act ? ld_run<FRESH>(a.rmask + rinfo_addr(rb) + W) : 0u;
         cw[p] = act ? __ldcg(a.cmask + (size_t)c * 32 + W) : 0u;
         sw[p] = act ? __ldcg(a.cmask + (size_t)c * 32 + 16 + W) : 0u;
       }
@@ -265,7 +276,7 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
         if (kk >= kend) break;
         if ((blockedm >> j) & 1u) continue;
         // earlier candidates are passed: say so before waiting or deciding
-        mask_resolve(a, row, kdone, kb + kk, -1, lane);
+        mask_resolve<FRESH>(a, row, kdone, kb + kk, -1, lane, kb, my_c, my_rb);
         kdone = kb + kk;
         bool blocked = false;
         if ((pendm >> j) & 1u) {
@@ -273,7 +284,7 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
           const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
           const int64_t rb = __shfl_sync(0xffffffffu, my_rb, kk);
           const bool act = lane < 16 && lane <= (rinfo_slot(rb) >> 5);
-          const uint32_t r = act ? __ldg(a.rmask + rinfo_addr(rb) + (int64_t)a.rstride * lane) : 0u;
+          const uint32_t r = act ? ld_run<FRESH>(a.rmask + rinfo_addr(rb) + lane) : 0u;
           while (true) {
             const uint32_t cc = act ? __ldcg(a.cmask + (size_t)c * 32 + lane) : 0u;
             const uint32_t ss = act ? __ldcg(a.cmask + (size_t)c * 32 + 16 + lane) : 0u;
@@ -293,7 +304,7 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
         // v takes c: colored bit, every other list color resolved
         const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
         const int slot = rinfo_slot(__shfl_sync(0xffffffffu, my_rb, kk));
-        mask_resolve(a, row, kdone, L, kb + kk, lane);
+        mask_resolve<FRESH>(a, row, kdone, L, kb + kk, lane, kb, my_c, my_rb);
         if (lane == 0) {
           atomicOr(a.cmask + (size_t)c * 32 + (slot >> 5), 1u << (slot & 31));
           publish(a.state, v, (c << 2) | kColored);
@@ -301,8 +312,12 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
         return true;
       }
     }
+    if (kb + 32 >= L) {
+      // every candidate taken: v fails and will never take any of them
+      mask_resolve<FRESH>(a, row, kdone, L, -1, lane, kb, my_c, my_rb);
+      break;
+    }
   }
-  mask_resolve(a, row, kdone, L, -1, lane);
   if (lane == 0) publish(a.state, v, (kFailedColor << 2) | kFailed);
   return true;
 }

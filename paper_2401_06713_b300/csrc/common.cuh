@@ -192,41 +192,41 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Grid-wide barrier of a cooperative launch with a time limit.  bar: two
-// words (arrivals, generation), zero before the launch.  Thread 0 of every
-// block arrives once per call; the last arrival resets the count and bumps
-// the generation.  A block that waits longer than limit_ns (by the global
-// timer), or sees *abort set, sets *abort, writes the arrivals it saw to
-// *seen and returns false: the caller then ends the kernel, and every other
-// block leaves at its next barrier.  Writes made before the barrier by any
-// block are visible after it (fences on both sides).
+// Grid-wide barrier of a cooperative launch with a time limit.  bar: one
+// word, zero before the launch (two are reserved).  Thread 0 of every block
+// adds to it once per call: block 0 adds 2^31 - (blocks - 1), the others
+// add 1, so the word's top bit flips exactly when the last block arrives
+// and its other bits come back to where they were.  A block waits until the
+// top bit differs from the value it found; one that waits longer than
+// limit_ns (by the global timer), or sees *abort set, sets *abort, writes
+// the arrivals it saw to *seen and returns false: the caller then ends the
+// kernel, and every other block leaves at its next barrier.  Writes made
+// before the barrier by any block are visible after it (fences on both
+// sides).
 constexpr uint64_t kBarrierLimitNs = 4000000000ull;
 __device__ __forceinline__ bool grid_sync_bounded(unsigned int* bar, int* abort, uint64_t limit_ns, int* seen) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned int* gen = bar + 1;
-    const unsigned int g = *gen;
+    const unsigned int inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    volatile unsigned int* vb = bar;
     __threadfence();
-    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const uint64_t t0 = global_ns();
-      while (*gen == g) {
-        if (*(volatile int*)abort) {
-          ok = 0;
-          break;
-        }
-        if (global_ns() - t0 > limit_ns) {
-          *seen = (int)*(volatile unsigned int*)bar;
-          atomicExch(abort, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
+    const unsigned int old = atomicAdd(bar, inc);
+    // spin (an L2 round trip per poll); the clock and the abort flag every
+    // 64 polls
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1; ((old ^ *vb) & 0x80000000u) == 0u; ++it) {
+      if ((it & 63u) != 0u) continue;
+      if (*(volatile int*)abort) {
+        ok = 0;
+        break;
+      }
+      if (global_ns() - t0 > limit_ns) {
+        *seen = (int)(*vb & 0x7fffffffu);
+        atomicExch(abort, 1);
+        ok = 0;
+        break;
       }
     }
     __threadfence();
@@ -395,14 +395,13 @@ struct ColorArgs {
   int64_t v0;              // ordered pass: position t is vertex v0 + t (a chunk of the round)
   // bit layout (rinfo set; ConflictArgs gives the encoding): the run of
   // entry e is the set bits of its row words rmask[rinfo_addr(rinfo[e]) +
-  // rstride W], W <= slot / 32, slot = rinfo_slot(rinfo[e]); bit t of word
+  // W], W <= slot / 32, slot = rinfo_slot(rinfo[e]); bit t of word
   // W is the member at slot 32 W + t of bucket c = lists[e], vertex
   // bpid[bboff[c] + 32 W + t]
   const int64_t* rinfo;
   const int64_t* bboff;
   const uint32_t* rmask;
   const int32_t* bpid;
-  int32_t rstride;      // bit layout: words between a row's word W and W + 1
   // mask coloring (bit layout; null: off): per bucket color c, 32 words at
   // 32 c, zero at the start of the round: words 0..15 mark the members
   // (by slot) colored c, words 16..31 those that will never take c
@@ -509,7 +508,6 @@ struct SmallArgs {
   int64_t* scof;          // [nsets + 1]   bucket colors (sum of P),
   int64_t* seoff;         // [nsets + 1]   list entries (sum of n L)
   const int2* ptab;       // [max n_k + 1]: (P, L) of a set with m vertices
-  int64_t cap;            // CSR entries the col buffer holds
   int64_t budget;         // byte budget of one round's CSR (0: none)
   const uint64_t* xz;     // [N][2] all strings
   int32_t* gid_a;         // [n0] V_l in ascending global id (ping-pong)
@@ -521,9 +519,13 @@ struct SmallArgs {
   int32_t* lists;         // [E0] (E0 = sum of n_k L_k at the start)
   int32_t* ent_v;         // [E0] list entry -> rank
   int64_t* loff;          // [n0 + 1]
-  uint32_t* cnt;          // [E0]
-  int64_t* runoff;        // [E0 + 1]
-  int32_t* col;           // [cap]
+  int64_t* rinfo;         // [E0] packed word of every list entry (bit layout)
+  uint32_t* rmask;        // [wcap] the buckets' bit rows
+  int64_t wcap;           // words rmask holds
+  uint32_t* bwords;       // [P0] words of a bucket's rows
+  int64_t* moff;          // [P0 + 1] their prefix
+  int64_t* snnz;          // [nsets] run entries of every set in the round
+  uint32_t* cmask;        // [32 P0] the buckets' color masks of the mask coloring
   uint64_t* state;        // [n0]
   uint32_t* flag;         // [n0] in V_l order
   int64_t* pos;           // [n0 + 1]
@@ -531,7 +533,6 @@ struct SmallArgs {
   uint64_t* key;          // [n0] (priority, global id) in V_l order
   uint32_t* bcnt;         // [P0] bucket sizes (P0 = sum of P_k at the start)
   uint32_t* bcur;         // [P0] bucket fill cursors
-  uint32_t* clist;        // [kClistWords P0] colored lists of the ordered coloring
   int64_t* boff;          // [P0 + 1] bucket offsets
   uint32_t* bitems;       // [P0] work items of a bucket, ceil(s_c / 32)
   int64_t* iboff;         // [P0 + 1] their prefix
@@ -545,7 +546,8 @@ struct SmallArgs {
                           //      ctl[10] its round, ctl[11] the arrivals it saw)
   int64_t* ctl;           // [kSmallCtlWords]: 0 n, 1 rounds done, 2 stop reason, 4 V_l in gid_b (0..4
                           //      host-initialised), 6 sum of nnz, 7 sum over the sets of
-                          //      n_k (n_k - 1) / 2 (6, 7 zero on entry), 3, 5, 8 scratch
+                          //      n_k (n_k - 1) / 2 (6, 7 zero on entry), 3 the round's run
+                          //      entries, 5, 8 scratch
   int32_t max_polls;      // polls of one bounded wait before the engine gives up
   unsigned int* bar;      // [2] bounded grid barrier (zero before the grid launch)
   int64_t handoff;        // grid launch: stop (kSmallHandoff) at a round of at most

@@ -147,7 +147,7 @@ __device__ __forceinline__ void eval_vertex(const ColorArgs& a, int32_t v, int l
       r1 = rinfo_len(rb) ? slot : 0;
       for (int64_t W = cur >> 5; (W << 5) < r1; ++W) {
         const int64_t t = (W << 5) + lane;
-        const uint32_t wd = a.rmask[w0 + a.rstride * W];
+        const uint32_t wd = a.rmask[w0 + W];
         int32_t u = -1;
         if (t < slot && ((wd >> lane) & 1u)) u = a.bpid[pb + t];
         bool lb = false, lw = false;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(256, 6) k_color_masks(ColorArgs a, int32_t* __
   const int64_t gwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   for (int64_t t = wid; t < a.n; t += gwarps) {
-    if (!mask_vertex(a, (int32_t)(a.v0 + t), lane, err)) return;
+    if (!mask_vertex<false>(a, (int32_t)(a.v0 + t), lane, err)) return;
   }
 }
 

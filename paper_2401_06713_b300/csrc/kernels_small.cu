@@ -7,14 +7,14 @@
 // A round follows Alg. 1 exactly as the per-round path does:
 //   priorities (static Random order, Sec. III-B) -> ranks in ascending
 //   (priority, global id) -> lists in that order (Floyd, as draw_list) ->
-//   the EARLIER conflict CSR by a join through per-color buckets -> ordered
-//   first-fit coloring (ordered_vertex) -> colors and the uncolored set in
-//   ascending global id (carry).
+//   G_c in the bit layout by a join through per-color buckets -> ordered
+//   first-fit coloring over the buckets' color masks (mask_vertex) -> colors
+//   and the uncolored set in ascending global id (carry).
 // The run of list entry (u, k) holds the vertices v < u that commute with u
 // and also hold color c = list[u][k]: exactly the members of bucket c ranked
 // before u that commute with u.  So a bucket gives every run of its color by
 // commutation tests alone: sorted by list-entry index (r L + k, ascending
-// with the rank r), member i against the members j < i.
+// with the rank r), member i against the members j < i, one bit each.
 // (P, L) of a set come from a table the host fills with its own rule (indexed
 // by the set's vertex count), so both paths use the same numbers.  In a
 // batch, V_l in ascending global id holds the sets one after another; a
@@ -185,20 +185,22 @@ __device__ void set_prefixes(const SmallArgs& a, int64_t* sm) {
   }
 }
 
-// Runs from the sorted buckets, by work items of 32 members of one bucket
-// (item = bucket c, members i0 .. i0 + 31): lane i tests its member against
-// the members j < i (the smaller ranks), whose ranks and words the warp
-// stages in shared memory.  A warp takes a contiguous range of items, so it
-// stages a bucket's members once, as far as its items reach.  Count (FILL
-// false): cnt[e_i] = the commuting ones; fill (FILL true): their ranks at
-// col[runoff[e_i]..], ascending.
-template <int W, bool FILL>
-__device__ void bucket_runs(const SmallArgs& a, int32_t* R, uint64_t* X, int lane, int64_t gwarp, int64_t nwarps) {
+// The bit layout from the sorted buckets, by work items of 32 members of
+// one bucket (item = bucket c, members i0 .. i0 + 31 = row block R): lane i
+// tests its member against the members j < i (the smaller ranks), whose
+// ranks and words the warp stages in shared memory, and writes its row of
+// R + 1 words (bit t of word W: member 32 W + t commutes with i) at
+// moff[c] + 16 R (R + 1) + (i % 32)(R + 1), and its entry's packed word
+// (row address, slot, run length).  A warp takes a contiguous range of
+// items, so it stages a bucket's members once, as far as its items reach.
+// The run total goes to the set's count snnz and to the round's, ctl[3].
+template <int W>
+__device__ void bucket_bits(const SmallArgs& a, int32_t* R, uint64_t* X, int lane, int64_t gwarp, int64_t nwarps) {
   const int64_t nitems = __ldcg(a.ctl + 8);
   const int64_t per = (nitems + nwarps - 1) / nwarps;
   const int64_t it0 = min(nitems, gwarp * per), it1 = min(nitems, it0 + per);
   int64_t c = -1, b0 = 0;
-  int s = 0, staged = 0;
+  int s = 0, staged = 0, set = 0;
   for (int64_t it = it0; it < it1; ++it) {
     const int64_t cb = a.ibkt[it];
     const int i0 = (int)(it - a.iboff[cb]) * 32;
@@ -207,6 +209,7 @@ __device__ void bucket_runs(const SmallArgs& a, int32_t* R, uint64_t* X, int lan
       b0 = a.boff[c];
       s = (int)(a.boff[c + 1] - b0);
       staged = 0;
+      set = a.nsets > 1 ? find_set(a.scof, a.nsets, c) : 0;
     }
     const int need = min(s, i0 + 32);
     if (need > staged) {
@@ -219,56 +222,36 @@ __device__ void bucket_runs(const SmallArgs& a, int32_t* R, uint64_t* X, int lan
       staged = need;
       __syncwarp();
     }
-    // members j < i: the warp loops to the item's last member (a uniform
-    // bound), each lane counting only its own j < i.  The symplectic form
-    // folded to one 32-bit word: parity of x_i & z_j ^ z_i & x_j over both
-    // halves.
     const int i = i0 + lane;
-    const int jend = need;
     const bool active = i < s;
+    const int Rb = i0 >> 5;  // this item's row block
+    int64_t addr = a.moff[c] + 16 * (int64_t)Rb * (Rb + 1) + (int64_t)lane * (Rb + 1);
     const int ilim = active ? i : 0;  // lanes past the bucket test nothing
-    if constexpr (W == 1) {
-      const uint4* X4 = reinterpret_cast<const uint4*>(X);
-      const uint4 wi = X4[min(i, s - 1)];
-      if (!FILL) {
-        uint32_t anti = 0;
-#pragma unroll 4
-        for (int j = 0; j < jend; ++j) {
-          const uint4 w = X4[j];
-          const uint32_t d = (wi.x & w.z) ^ (wi.z & w.x) ^ (wi.y & w.w) ^ (wi.w & w.y);
-          anti += (j < ilim) ? (__popc(d) & 1u) : 0u;
-        }
-        if (active) a.cnt[a.bmem[b0 + i]] = (uint32_t)i - anti;
-      } else {
-        int64_t o = active ? a.runoff[a.bmem[b0 + i]] : 0;
-        for (int j = 0; j < jend; ++j) {
-          const uint4 w = X4[j];
-          const uint32_t d = (wi.x & w.z) ^ (wi.z & w.x) ^ (wi.y & w.w) ^ (wi.w & w.y);
-          if (j < ilim && (__popc(d) & 1u) == 0u) a.col[o++] = R[j];
-        }
-      }
-    } else {
-      // W words per part: the member's 32-bit halves, x part then z part
-      const uint32_t* X32 = reinterpret_cast<const uint32_t*>(X);
-      uint32_t wi[4 * W];
+    uint32_t tot = 0;
+    // the symplectic form folded to one 32-bit word: parity of
+    // x_i & z_j ^ z_i & x_j over all halves
+    const uint32_t* X32 = reinterpret_cast<const uint32_t*>(X);
+    uint32_t wi[4 * W];
 #pragma unroll
-      for (int k = 0; k < 4 * W; ++k) wi[k] = X32[4 * W * min(i, s - 1) + k];
-      auto odd = [&](int j) {
+    for (int k = 0; k < 4 * W; ++k) wi[k] = X32[4 * W * min(i, max(s - 1, 0)) + k];
+    for (int Wb = 0; Wb <= Rb; ++Wb) {
+      uint32_t word = 0u;
+      const int jend = min(32 * Wb + 32, i0 + 32);
+      for (int j = 32 * Wb; j < jend; ++j) {
         const uint32_t* w = X32 + 4 * W * j;
         uint32_t d = 0u;
 #pragma unroll
         for (int h = 0; h < 2 * W; ++h) d ^= (wi[h] & w[2 * W + h]) ^ (wi[2 * W + h] & w[h]);
-        return __popc(d) & 1u;
-      };
-      if (!FILL) {
-        uint32_t anti = 0;
-        for (int j = 0; j < jend; ++j) anti += (j < ilim) ? odd(j) : 0u;
-        if (active) a.cnt[a.bmem[b0 + i]] = (uint32_t)i - anti;
-      } else {
-        int64_t o = active ? a.runoff[a.bmem[b0 + i]] : 0;
-        for (int j = 0; j < jend; ++j)
-          if (j < ilim && odd(j) == 0u) a.col[o++] = R[j];
+        if (j < ilim && (__popc(d) & 1u) == 0u) word |= 1u << (j - 32 * Wb);
       }
+      if (active) a.rmask[addr + Wb] = word;
+      tot += __popc(word);
+    }
+    if (active) a.rinfo[a.bmem[b0 + i]] = rinfo_pack(addr, i, (int)tot);
+    const uint32_t wsum = __reduce_add_sync(0xffffffffu, tot);
+    if (lane == 0 && wsum) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.snnz + set), (unsigned long long)wsum);
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.ctl + 3), (unsigned long long)wsum);
     }
   }
   __syncwarp();
@@ -326,7 +309,11 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       a.bcnt[c] = 0;
       a.bcur[c] = 0;
     }
-    for (int64_t t = gtid; t < kClistWords * P; t += gthreads) a.clist[t] = 0;
+    // the buckets' color masks of the mask coloring start empty; the
+    // round's run counts at zero
+    for (int64_t t = gtid; t < 32 * P; t += gthreads) a.cmask[t] = 0u;
+    for (int64_t k = gtid; k < nsets; k += gthreads) a.snnz[k] = 0;
+    if (gtid == 0) a.ctl[3] = 0;
     if (gtid == 0) a.err[1] = 0;
     if (!engine_sync<CL>(a, __LINE__, round)) return;
 
@@ -374,14 +361,18 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     if (!engine_sync<CL>(a, __LINE__, round)) return;
     for (int64_t c = gtid; c < P; c += gthreads) {
       const uint32_t sc = a.bcnt[c];
-      a.bitems[c] = (sc + 31) / 32;
+      const uint32_t nwb = (sc + 31) / 32;
+      a.bitems[c] = nwb;
+      a.bwords[c] = 16u * nwb * (nwb + 1u);  // the bucket's lower blocks, row-major
       if (sc > (uint32_t)kSmallBucketCap) a.err[2] = 1;
     }
     if (!grid_scan<CL>(a, round, a.bcnt, P, a.boff, a.part, scan_s)) return;
     if (!engine_sync<CL>(a, __LINE__, round)) return;
     if (!grid_scan<CL>(a, round, a.bitems, P, a.iboff, a.part, scan_s)) return;
     if (!engine_sync<CL>(a, __LINE__, round)) return;
-    if (__ldcg(a.err + 2) != 0) {
+    if (!grid_scan<CL>(a, round, a.bwords, P, a.moff, a.part, scan_s)) return;
+    if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (__ldcg(a.err + 2) != 0 || __ldcg(a.moff + P) > a.wcap) {
       if (gtid == 0) a.ctl[2] = kSmallOverflow;
       break;
     }
@@ -411,21 +402,21 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     }
     if (!engine_sync<CL>(a, __LINE__, round)) return;
 
-    bucket_runs<W, false>(a, Rw, Xw, lane, gwarp, nwarps);
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
-    if (!grid_scan<CL>(a, round, a.cnt, E, a.runoff, a.part, scan_s)) return;
+    bucket_bits<W>(a, Rw, Xw, lane, gwarp, nwarps);
     if (!engine_sync<CL>(a, __LINE__, round)) return;
     {
-      const int64_t nnz = __ldcg(a.runoff + E);
+      // the round's CSR, counted as the byte budget counts it (8 bytes per
+      // row and one, 4 per run entry): over the budget, the round goes back
+      const int64_t nnz = __ldcg(a.ctl + 3);
       const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
-      if (nnz > a.cap || (a.budget > 0 && csr_bytes > a.budget)) {
+      if (a.budget > 0 && csr_bytes > a.budget) {
+        if (!engine_sync<CL>(a, __LINE__, round)) return;
         if (gtid == 0) a.ctl[2] = kSmallOverflow;
         break;
       }
-      if (gtid == 0) a.ctl[6] += nnz;
     }
-    bucket_runs<W, true>(a, Rw, Xw, lane, gwarp, nwarps);
     if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (gtid == 0) a.ctl[6] += __ldcg(a.ctl + 3);
 
     // ordered first fit in rank order; warps take ranks from a counter
     {
@@ -433,13 +424,11 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       ca.n = n;
       ca.lists = a.lists;
       ca.loff = a.loff;
-      ca.runoff = a.runoff;
-      ca.col = a.col;
       ca.state = a.state;
       ca.ranked = 1;
-      ca.clist = a.clist;
-      ca.xz = a.xz_r;
-      ca.qw = W;
+      ca.rinfo = a.rinfo;
+      ca.rmask = a.rmask;
+      ca.cmask = a.cmask;
       ca.max_polls = a.max_polls;
       bool ok = true;
       while (ok) {
@@ -447,7 +436,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         if (lane == 0) t = atomicAdd(a.err + 1, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if ((int64_t)t >= n || __ldcg(a.err) != 0) break;
-        ok = ordered_vertex<true>(ca, t, lane, a.err);
+        ok = mask_vertex<true>(ca, t, lane, a.err);
       }
     }
     if (!engine_sync<CL>(a, __LINE__, round)) return;
@@ -480,7 +469,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         const int64_t v0 = a.svoff[k], v1 = a.svoff[k + 1];
         const int64_t nk = v1 - v0;
         if (nk > 0) {
-          const int64_t nnzk = a.runoff[a.seoff[k + 1]] - a.runoff[a.seoff[k]];
+          const int64_t nnzk = a.snnz[k];
           a.sbase[k] += a.scof[k + 1] - a.scof[k];
           a.speak[k] = max(a.speak[k], 8 * (nk + 1) + 4 * nnzk);
           pairs += nk * (nk - 1) / 2;
