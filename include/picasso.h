@@ -332,6 +332,18 @@ int picasso_round(void* ctx, int64_t* n_remaining);
  * d_color_out [n] (may be NULL) and sets *n_rounds (may be NULL).          */
 int picasso_run(void* ctx, int32_t* d_color_out, int32_t* n_rounds);
 
+/* Alg. 1 end to end from host buffers (the problem statement of Alg. 1: the
+ * strings in, a coloring out): copies n strings of q character codes
+ * (h_codes, row-major uint8 [n][q], 0 = I, 1 = X, 2 = Y, 3 = Z) to the
+ * device, packs them, runs every round as picasso_init + picasso_run would
+ * (cfg as there; n >= 1, 1 <= q <= 1024) and copies the global colors to
+ * h_colors [n] (int32); *n_rounds (may be NULL) gets the rounds run.  The
+ * device memory comes from the library's pool and is returned before the
+ * call ends.  Host buffers should be pinned (cudaHostAlloc) for full copy
+ * speed; pageable ones work.  Synchronises stream.                         */
+int picasso_color_host(const picasso_config* cfg, const uint8_t* h_codes, int64_t n, int32_t q,
+                       int32_t* h_colors, int32_t* n_rounds, void* stream);
+
 /* Autotuner of the launch schedule (picasso_schedule) for a workload of one
  * or many sets, given as picasso_init_batch takes them (nsets = 1 with
  * h_set_offsets = {0, n}: one set).  Starting from cfg->sched it tunes one

@@ -1145,6 +1145,7 @@ int color_round(Ctx* c) {
   if (c->bits) {
     a.rinfo = c->rinfo;
     a.bboff = c->bt_boff;
+    a.Lu = c->Lu;
     a.rmask = c->bt_rmask;
     a.bpid = c->bt_bpid;
   }
@@ -1974,6 +1975,46 @@ int picasso_run(void* ctx, int32_t* d_color_out, int32_t* n_rounds) {
   if (d_color_out) ST(picasso_get_colors(ctx, d_color_out));
   if (n_rounds) *n_rounds = c->round - 1;
   return PICASSO_OK;
+}
+
+int picasso_color_host(const picasso_config* cfg, const uint8_t* h_codes, int64_t n, int32_t q,
+                       int32_t* h_colors, int32_t* n_rounds, void* stream) {
+  if (!cfg || !h_codes || !h_colors || n < 1 || n >= (int64_t(1) << 30) || q < 1) return PICASSO_ERR_INVALID_ARG;
+  if (q > kMaxQ) return PICASSO_ERR_UNSUPPORTED;
+  ST(validate_cfg(cfg));
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  cudaMemPool_t pool;
+  {
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = pool_for(dev, &pool);
+    if (ce != cudaSuccess) return map_err(ce);
+  }
+  const int64_t words = 2 * (int64_t)((q + 63) / 64);
+  uint8_t* d_codes = nullptr;
+  uint64_t* d_xz = nullptr;
+  int32_t* d_colors = nullptr;
+  void* ctx = nullptr;
+  auto done = [&](int st) {
+    if (ctx) picasso_destroy(ctx);
+    if (d_codes) cudaFreeAsync(d_codes, s);
+    if (d_xz) cudaFreeAsync(d_xz, s);
+    if (d_colors) cudaFreeAsync(d_colors, s);
+    cudaStreamSynchronize(s);
+    return st;
+  };
+  cudaError_t e = cudaMallocFromPoolAsync((void**)&d_codes, (size_t)n * q, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&d_xz, sizeof(uint64_t) * words * n, pool, s);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&d_colors, sizeof(int32_t) * n, pool, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_codes, h_codes, (size_t)n * q, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_pack(d_codes, n, q, d_xz, s);
+  if (e != cudaSuccess) return done(map_err(e));
+  int st = picasso_init(&ctx, cfg, d_xz, n, q, stream);
+  if (st == PICASSO_OK) st = picasso_run(ctx, d_colors, n_rounds);
+  if (st != PICASSO_OK) return done(st);
+  e = cudaMemcpyAsync(h_colors, d_colors, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return done(map_err(e));
 }
 
 int picasso_autotune(const picasso_config* cfg, const uint64_t* d_xz, const int64_t* h_set_offsets,

@@ -236,8 +236,9 @@ __device__ __forceinline__ void mask_resolve(const ColorArgs& a, int64_t row, in
 
 template <bool FRESH>
 __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
-  const int64_t row = ld_run<FRESH>(a.loff + v);
-  const int L = (int)(ld_run<FRESH>(a.loff + v + 1) - row);
+  // lists of one length (a single set): the row is known without a load
+  const int64_t row = a.Lu ? (int64_t)v * a.Lu : ld_run<FRESH>(a.loff + v);
+  const int L = a.Lu ? a.Lu : (int)(ld_run<FRESH>(a.loff + v + 1) - row);
   const int h = lane >> 4, W = lane & 15;
   int polls = 0;
   int kdone = 0;  // entries [0, kdone) passed and marked resolved

@@ -400,6 +400,7 @@ struct ColorArgs {
   // bpid[bboff[c] + 32 W + t]
   const int64_t* rinfo;
   const int64_t* bboff;
+  int32_t Lu;           // every list has Lu colors (row of v = v Lu; loff unread), or 0
   const uint32_t* rmask;
   const int32_t* bpid;
   // mask coloring (bit layout; null: off): per bucket color c, 32 words at

@@ -429,6 +429,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       ca.rinfo = a.rinfo;
       ca.rmask = a.rmask;
       ca.cmask = a.cmask;
+      ca.Lu = nsets == 1 ? a.ptab[n].y : 0;  // one set: row of rank r = r L
       ca.max_polls = a.max_polls;
       bool ok = true;
       while (ok) {

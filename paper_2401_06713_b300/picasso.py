@@ -134,6 +134,7 @@ _SIGS = {
     "picasso_carry": [_vp, _pi64],
     "picasso_round": [_vp, _pi64],
     "picasso_run": [_vp, _vp, _pi32],
+    "picasso_color_host": [ctypes.POINTER(Config), _vp, _i64, _i32, _vp, _pi32, _vp],
     "picasso_autotune": [ctypes.POINTER(Config), _vp, _pi64, _i32, ctypes.POINTER(ctypes.c_uint64), _i32, _i32,
                          ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                          _vp],
@@ -244,6 +245,29 @@ def philox_draws(seed: int, rnd: int, gid: int, tag: int, i0: int, count: int, d
     out = torch.empty(count, dtype=torch.int32, device=device)
     _ck(_lib().picasso_philox_draws(seed, rnd, gid, tag, i0, count, _ptr(out), _stream()), "picasso_philox_draws")
     return out
+
+
+def color_host(codes: torch.Tensor, q: int, colors: torch.Tensor | None = None, seed: int = 0, palette=(1, 8),
+               alpha: float = 2.0, stream=None):
+    """picasso_color_host: host codes (uint8 [n, q] on the CPU, pinned for
+    full copy speed) in, host colors (int32 [n]) and rounds out."""
+    assert not codes.is_cuda and codes.dtype == torch.uint8 and codes.dim() == 2 and codes.shape[1] == q
+    codes = codes.contiguous()
+    n = int(codes.shape[0])
+    if colors is None:
+        colors = torch.empty(n, dtype=torch.int32, pin_memory=codes.is_pinned())
+    assert not colors.is_cuda and colors.dtype == torch.int32 and colors.numel() >= n
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    cfg = Config()
+    _ck(_lib().picasso_config_default(ctypes.byref(cfg)), "picasso_config_default")
+    cfg.seed = seed
+    cfg.palette_num, cfg.palette_den = palette
+    cfg.alpha = alpha
+    r = ctypes.c_int32()
+    _ck(_lib().picasso_color_host(ctypes.byref(cfg), ctypes.c_void_p(codes.data_ptr()), n, q,
+                                  ctypes.c_void_p(colors.data_ptr()), ctypes.byref(r),
+                                  ctypes.c_void_p(stream.cuda_stream)), "picasso_color_host")
+    return colors[:n], int(r.value)
 
 
 def autotune(xz: torch.Tensor, q: int, set_offsets=None, seeds=None, reps: int = 3, seed: int = 0,

@@ -303,6 +303,20 @@ def test_run_edge_sizes(pc, orc, n, small):
     _run_both(pc, orc, synth.pauli_uniform(n, 6, seed=n), 2, 1, 8, 2.0, small=small)
 
 
+def test_color_host_entry(pc, orc):
+    # Alg. 1 from host buffers to host buffers (picasso_color_host): the
+    # oracle's colors and rounds, from pinned and from pageable memory
+    chars = synth.pauli_weighted(3000, 40, 0.3, seed=8)
+    ref, rounds, _ = orc.run(chars, 5, 1, 8, 2.0)
+    colors, r = pc.color_host(torch.from_numpy(chars).pin_memory(), 40, seed=5, palette=(1, 8), alpha=2.0)
+    assert r == rounds and np.array_equal(colors.numpy(), ref)
+    colors2, r2 = pc.color_host(torch.from_numpy(chars), 40, seed=5, palette=(1, 8), alpha=2.0)
+    assert r2 == rounds and np.array_equal(colors2.numpy(), ref)
+    with pytest.raises(pc.PicassoError) as e:
+        pc.color_host(torch.from_numpy(chars[:0]), 40)
+    assert e.value.status == pc.ERR_INVALID_ARG
+
+
 def test_run_all_identity(pc, orc):
     # G' is complete: each round colors exactly min(P, ...) vertices
     chars = np.zeros((300, 10), dtype=np.uint8)
