@@ -209,8 +209,8 @@ __device__ __forceinline__ bool ordered_vertex(const ColorArgs& a, int32_t v, in
 // A vertex publishes its passes (resolved bits) before it waits and, once
 // decided, its color (colored bit) and every other list color (resolved),
 // so each bit only ever changes from 0 to 1 and a decision taken from any
-// value read is final.  Candidates are examined kMaskCands at a time: lanes
-// 16 h .. 16 h + 15 hold words 0..15 of one candidate's row and masks.
+// value read is final.  Candidates are examined kMaskCands at a time, four
+// lanes per candidate.
 // ---------------------------------------------------------------------------
 constexpr int kMaskCands = 8;
 
@@ -239,7 +239,6 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
   // lists of one length (a single set): the row is known without a load
   const int64_t row = a.Lu ? (int64_t)v * a.Lu : ld_run<FRESH>(a.loff + v);
   const int L = a.Lu ? a.Lu : (int)(ld_run<FRESH>(a.loff + v + 1) - row);
-  const int h = lane >> 4, W = lane & 15;
   int polls = 0;
   int kdone = 0;  // entries [0, kdone) passed and marked resolved
   for (int kb = 0; kb < L; kb += 32) {
@@ -252,35 +251,39 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
     }
     const int kend = min(L - kb, 32);
     for (int k0 = 0; k0 < kend; k0 += kMaskCands) {
-      uint32_t rw[kMaskCands / 2], cw[kMaskCands / 2], sw[kMaskCands / 2];
-#pragma unroll
-      for (int p = 0; p < kMaskCands / 2; ++p) {
-        const int kk = k0 + 2 * p + h;
-        const uint32_t c = __shfl_sync(0xffffffffu, my_c, min(kk, 31));
-        const int64_t rb = __shfl_sync(0xffffffffu, my_rb, min(kk, 31));
-        const bool act = kk < kend && W <= (rinfo_slot(rb) >> 5);
-        rw[p] = act ? ld_run<FRESH>(a.rmask + rinfo_addr(rb) + W) : 0u;
-        cw[p] = act ? __ldcg(a.cmask + (size_t)c * 32 + W) : 0u;
-        sw[p] = act ? __ldcg(a.cmask + (size_t)c * 32 + 16 + W) : 0u;
+      // lanes 4 j .. 4 j + 3 take candidate k0 + j: lane 4 j + q holds its
+      // row words 4 q .. 4 q + 3 and the same words of its bucket's masks
+      // (one 16-byte load each)
+      const int kq = k0 + (lane >> 2), w0 = 4 * (lane & 3);
+      const uint32_t cq = __shfl_sync(0xffffffffu, my_c, min(kq, 31));
+      const int64_t rq = __shfl_sync(0xffffffffu, my_rb, min(kq, 31));
+      const int nw = kq < kend ? (rinfo_slot(rq) >> 5) + 1 : 0;  // row words
+      bool bl = false, pe = false;
+      if (w0 < nw) {
+        const uint4 tk = __ldcg(reinterpret_cast<const uint4*>(a.cmask + (size_t)cq * 32 + w0));
+        const uint4 nv = __ldcg(reinterpret_cast<const uint4*>(a.cmask + (size_t)cq * 32 + 16 + w0));
+        const uint32_t* rp = a.rmask + rinfo_addr(rq) + w0;
+        const int m = nw - w0;
+        const uint32_t r0 = ld_run<FRESH>(rp);
+        const uint32_t r1 = m > 1 ? ld_run<FRESH>(rp + 1) : 0u;
+        const uint32_t r2 = m > 2 ? ld_run<FRESH>(rp + 2) : 0u;
+        const uint32_t r3 = m > 3 ? ld_run<FRESH>(rp + 3) : 0u;
+        bl = ((r0 & tk.x) | (r1 & tk.y) | (r2 & tk.z) | (r3 & tk.w)) != 0u;
+        pe = ((r0 & ~(tk.x | nv.x)) | (r1 & ~(tk.y | nv.y)) | (r2 & ~(tk.z | nv.z)) | (r3 & ~(tk.w | nv.w))) != 0u;
       }
-      uint32_t blockedm = 0u, pendm = 0u;  // bit j: candidate k0 + j
-#pragma unroll
-      for (int p = 0; p < kMaskCands / 2; ++p) {
-        const uint32_t bb = __ballot_sync(0xffffffffu, (rw[p] & cw[p]) != 0u);
-        const uint32_t pp = __ballot_sync(0xffffffffu, (rw[p] & ~(cw[p] | sw[p])) != 0u);
-        blockedm |= ((bb & 0xffffu) ? 1u : 0u) << (2 * p) | ((bb >> 16) ? 1u : 0u) << (2 * p + 1);
-        pendm |= ((pp & 0xffffu) ? 1u : 0u) << (2 * p) | ((pp >> 16) ? 1u : 0u) << (2 * p + 1);
-      }
+      // nibble j of each ballot: candidate k0 + j taken / pending
+      const uint32_t blockedm = __ballot_sync(0xffffffffu, bl);
+      const uint32_t pendm = __ballot_sync(0xffffffffu, pe);
 #pragma unroll 1
       for (int j = 0; j < kMaskCands; ++j) {
         const int kk = k0 + j;
         if (kk >= kend) break;
-        if ((blockedm >> j) & 1u) continue;
+        if ((blockedm >> (4 * j)) & 0xFu) continue;
         // earlier candidates are passed: say so before waiting or deciding
         mask_resolve<FRESH>(a, row, kdone, kb + kk, -1, lane, kb, my_c, my_rb);
         kdone = kb + kk;
         bool blocked = false;
-        if ((pendm >> j) & 1u) {
+        if ((pendm >> (4 * j)) & 0xFu) {
           // wait for the earlier neighbours that may still take c
           const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
           const int64_t rb = __shfl_sync(0xffffffffu, my_rb, kk);

@@ -340,6 +340,8 @@ cudaError_t launch_color_ordered(const ColorArgs& a, const int32_t* order, int32
                                  int per_sm_cap) {
   int dev = 0, sms = 148, per_sm = 0;
   const bool masks = a.cmask != nullptr;
+  // the mask coloring reads the color masks 16 bytes at a time
+  if (reinterpret_cast<uintptr_t>(a.cmask) & 15) return cudaErrorMisalignedAddress;
   const void* kern = masks ? (const void*)k_color_masks : (const void*)k_color_ordered;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

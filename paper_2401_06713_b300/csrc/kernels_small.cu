@@ -503,6 +503,8 @@ cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_bl
                                 cudaStream_t s) {
   int dev = 0, sms = 148, per_sm = 0;
   if (a.qw != 1 && a.qw != 2) return cudaErrorInvalidValue;
+  // the mask coloring reads the color masks 16 bytes at a time
+  if (reinterpret_cast<uintptr_t>(a.cmask) & 15) return cudaErrorMisalignedAddress;
   const size_t smem = small_smem_bytes(a.qw);
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
