@@ -76,8 +76,8 @@ typedef enum {
 /* Launch schedule of the kernels whose shape changes no result (colors,
  * CSRs, rounds and stats other than times are the same under every
  * schedule): the small-round engine's grid, the rounds it gives to one
- * thread-block cluster, and the blocks per SM of the bit pass and of the
- * mask coloring.  All zero = the library's defaults.  picasso_autotune picks
+ * thread-block cluster and to one block, and the blocks per SM of the bit
+ * pass and of the mask coloring.  All zero = the library's defaults.  picasso_autotune picks
  * one for a workload by timing candidates on it.  The paper has no
  * counterpart (its kernels have one launch shape).                          */
 typedef struct {
@@ -98,6 +98,9 @@ typedef struct {
   int32_t engine_max_n;         /* picasso_run hands the rounds to the small-
                                    round engine from a round of at most this
                                    many vertices (0: 16384; else 1 .. 16384) */
+  int32_t block_max_n;          /* engine rounds of at most this many
+                                   vertices run in one block of 256 threads
+                                   (0: 64; -1: never; else 1 .. 16384)       */
 } picasso_schedule;
 
 typedef struct {
@@ -348,9 +351,9 @@ int picasso_color_host(const picasso_config* cfg, const uint8_t* h_codes, int64_
  * or many sets, given as picasso_init_batch takes them (nsets = 1 with
  * h_set_offsets = {0, n}: one set).  Starting from cfg->sched it tunes one
  * field at a time, in the order engine_max_n, engine_blocks_per_sm,
- * cluster_max_n, cluster_blocks, bits_blocks_per_sm, color_blocks_per_sm,
- * over that field's candidates (16384, 8192, 4096; 1, 2; -1, 512, 2048,
- * 8192; 16, 8; 4, 3, 2; 6, 4, 3),
+ * cluster_max_n, cluster_blocks, block_max_n, bits_blocks_per_sm,
+ * color_blocks_per_sm, over that field's candidates (16384, 8192, 4096; 1,
+ * 2; -1, 512, 2048, 8192; 16, 8; -1, 64, 256, 1024; 4, 3, 2; 6, 4, 3),
  * keeping the others at their best so far.  Each candidate is one whole
  * picasso_run of the workload after one untimed run, timed with CUDA events
  * on `stream`, the median of `reps` (1 .. 64) runs.  The fastest schedule

@@ -1332,13 +1332,11 @@ int run_small(Ctx* c) {
   int32_t *gid_a = nullptr, *gid_b = nullptr, *perm = nullptr, *gid_r = nullptr, *lists = nullptr;
   int32_t *err = nullptr, *bmem = nullptr, *brank = nullptr, *ibkt = nullptr, *sid = nullptr, *ent_v = nullptr;
   uint64_t* bxz = nullptr;
-  uint32_t* bitems = nullptr;
   int64_t* iboff = nullptr;
   uint64_t *xz_r = nullptr, *state = nullptr, *key = nullptr;
   int64_t *loff = nullptr, *rinfo = nullptr, *pos = nullptr, *part = nullptr, *ctl = nullptr, *boff = nullptr;
   int64_t *moff = nullptr, *snnz = nullptr;
-  uint32_t *rmask = nullptr, *bwords = nullptr, *flag = nullptr, *bcnt = nullptr, *bcur = nullptr, *cmask = nullptr,
-           *sbar = nullptr;
+  uint32_t *rmask = nullptr, *bcnt = nullptr, *bcur = nullptr, *cmask = nullptr, *sbar = nullptr;
   int st = PICASSO_OK;
   auto cleanup = [&]() {
     release(c, &d_ptab);
@@ -1352,7 +1350,6 @@ int run_small(Ctx* c) {
     release(c, &lists);
     release(c, &ent_v);
     release(c, &rmask);
-    release(c, &bwords);
     release(c, &moff);
     release(c, &snnz);
     release(c, &err);
@@ -1365,7 +1362,6 @@ int run_small(Ctx* c) {
     release(c, &part);
     release(c, &ctl);
     release(c, &sbar);
-    release(c, &flag);
     release(c, &bcnt);
     release(c, &bcur);
     release(c, &boff);
@@ -1373,7 +1369,6 @@ int run_small(Ctx* c) {
     release(c, &brank);
     release(c, &ibkt);
     release(c, &bxz);
-    release(c, &bitems);
     release(c, &iboff);
   };
 #define TRY(expr)           \
@@ -1407,11 +1402,9 @@ int run_small(Ctx* c) {
   TRY(alloc(c, &loff, n0 + 1));
   TRY(alloc(c, &rinfo, E0));
   TRY(alloc(c, &rmask, wcap));
-  TRY(alloc(c, &bwords, P0));
   TRY(alloc(c, &moff, P0 + 1));
   TRY(alloc(c, &snnz, ns));
   TRY(alloc(c, &state, n0));
-  TRY(alloc(c, &flag, n0));
   TRY(alloc(c, &pos, n0 + 1));
   TRY(alloc(c, &key, n0));
   TRY(alloc(c, &bcnt, P0));
@@ -1421,7 +1414,6 @@ int run_small(Ctx* c) {
   TRY(alloc(c, &bmem, E0));
   TRY(alloc(c, &brank, E0));
   TRY(alloc(c, &bxz, 2 * (int64_t)c->qw * E0));
-  TRY(alloc(c, &bitems, P0));
   TRY(alloc(c, &iboff, P0 + 1));
   TRY(alloc(c, &ibkt, E0 / 32 + P0 + 1));
   TRY(alloc(c, &part, kPartCap));
@@ -1469,11 +1461,9 @@ int run_small(Ctx* c) {
   a.loff = loff;
   a.rinfo = rinfo;
   a.rmask = rmask;
-  a.bwords = bwords;
   a.moff = moff;
   a.snnz = snnz;
   a.state = state;
-  a.flag = flag;
   a.pos = pos;
   a.color = c->color;
   a.key = key;
@@ -1481,7 +1471,6 @@ int run_small(Ctx* c) {
   a.bcur = bcur;
   a.cmask = cmask;
   a.boff = boff;
-  a.bitems = bitems;
   a.iboff = iboff;
   a.ibkt = ibkt;
   a.bmem = bmem;
@@ -1497,6 +1486,8 @@ int run_small(Ctx* c) {
   if (cl_blocks[c->qw] < 0) cl_blocks[c->qw] = small_cluster_blocks(c->qw);
   const picasso_schedule& sc = c->cfg.sched;
   a.handoff = sc.cluster_max_n == 0 ? kSmallClusterMaxN : sc.cluster_max_n < 0 ? 0 : sc.cluster_max_n;
+  // and rounds of at most block_max_n vertices in one block
+  a.handoff2 = sc.block_max_n == 0 ? kSmallBlockMaxN : sc.block_max_n < 0 ? 0 : sc.block_max_n;
   int clb = cl_blocks[c->qw];
   if (sc.cluster_blocks > 0) clb = std::min(clb, (int)sc.cluster_blocks);
   TRYC(launch_small_rounds(a, kPartCap, a.handoff > 0 ? clb : 0, sc.engine_blocks_per_sm, s));
@@ -1716,7 +1707,8 @@ int validate_cfg(const picasso_config* cfg) {
   if (sc.engine_blocks_per_sm < 0 || sc.engine_blocks_per_sm > 2 || sc.cluster_max_n < -1 ||
       sc.cluster_max_n > kSmallRoundsMax || !(cb == 0 || cb == 2 || cb == 4 || cb == 8 || cb == 16) ||
       sc.bits_blocks_per_sm < 0 || sc.bits_blocks_per_sm > 4 || sc.color_blocks_per_sm < 0 ||
-      sc.color_blocks_per_sm > 8 || sc.engine_max_n < 0 || sc.engine_max_n > kSmallRoundsMax)
+      sc.color_blocks_per_sm > 8 || sc.engine_max_n < 0 || sc.engine_max_n > kSmallRoundsMax ||
+      sc.block_max_n < -1 || sc.block_max_n > kSmallRoundsMax)
     return PICASSO_ERR_INVALID_ARG;
   return PICASSO_OK;
 }
@@ -2107,6 +2099,7 @@ int picasso_autotune(const picasso_config* cfg, const uint64_t* d_xz, const int6
                           {&picasso_schedule::engine_blocks_per_sm, {1, 2}, 2},
                           {&picasso_schedule::cluster_max_n, {-1, 512, 2048, 8192}, 4},
                           {&picasso_schedule::cluster_blocks, {16, 8}, 2},
+                          {&picasso_schedule::block_max_n, {-1, 64, 256, 1024}, 4},
                           {&picasso_schedule::bits_blocks_per_sm, {4, 3, 2}, 3},
                           {&picasso_schedule::color_blocks_per_sm, {6, 4, 3}, 3}};
   for (const Field& fd : fields) {

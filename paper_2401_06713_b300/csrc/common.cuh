@@ -523,25 +523,22 @@ struct SmallArgs {
   int64_t* rinfo;         // [E0] packed word of every list entry (bit layout)
   uint32_t* rmask;        // [wcap] the buckets' bit rows
   int64_t wcap;           // words rmask holds
-  uint32_t* bwords;       // [P0] words of a bucket's rows
-  int64_t* moff;          // [P0 + 1] their prefix
+  int64_t* moff;          // [P0 + 1] prefix of the words of the buckets' rows
   int64_t* snnz;          // [nsets] run entries of every set in the round
   uint32_t* cmask;        // [32 P0] the buckets' color masks of the mask coloring
   uint64_t* state;        // [n0]
-  uint32_t* flag;         // [n0] in V_l order
-  int64_t* pos;           // [n0 + 1]
+  int64_t* pos;           // [n0 + 1] rank of V_l's i, then the uncolored before i
   int32_t* color;         // [N] global colors
   uint64_t* key;          // [n0] (priority, global id) in V_l order
   uint32_t* bcnt;         // [P0] bucket sizes (P0 = sum of P_k at the start)
   uint32_t* bcur;         // [P0] bucket fill cursors
   int64_t* boff;          // [P0 + 1] bucket offsets
-  uint32_t* bitems;       // [P0] work items of a bucket, ceil(s_c / 32)
-  int64_t* iboff;         // [P0 + 1] their prefix
+  int64_t* iboff;         // [P0 + 1] prefix of the buckets' work items, ceil(s_c / 32)
   int32_t* ibkt;          // [E0 / 32 + P0 + 1] bucket of every work item
   int32_t* bmem;          // [E0] bucket members: list-entry index,
   int32_t* brank;         // [E0]   rank,
   uint64_t* bxz;          // [2 E0] words
-  int64_t* part;          // [gridDim.x] block sums of the grid scans
+  int64_t* part;          // [3 gridDim.x] block sums of the launch's scans
   int32_t* err;           // [4]: 0 ordered-pass poll timeout, 1 work counter, 2 bucket over the cap,
                           //      3 a grid barrier timed out (the launch ended; ctl[9] its site,
                           //      ctl[10] its round, ctl[11] the arrivals it saw)
@@ -551,8 +548,10 @@ struct SmallArgs {
                           //      entries, 5, 8 scratch
   int32_t max_polls;      // polls of one bounded wait before the engine gives up
   unsigned int* bar;      // [2] bounded grid barrier (zero before the grid launch)
-  int64_t handoff;        // grid launch: stop (kSmallHandoff) at a round of at most
-                          // this many vertices, for the cluster launch
+  int64_t handoff;        // the cluster launch takes the rounds of at most this many
+                          // vertices (0: no cluster launch)
+  int64_t handoff2;       // the one-block launch takes the rounds of at most this
+                          // many vertices (0: no block launch)
 };
 
 // Stop reasons in ctl[2].
@@ -561,9 +560,14 @@ constexpr int kSmallCtlWords = 12;
 // Rounds of at most this many vertices run in one thread-block cluster (the
 // default of picasso_schedule.cluster_max_n).
 constexpr int64_t kSmallClusterMaxN = 2048;
-// part_cap: words of a.part; the launch uses at most that many blocks.  The
-// grid launch runs the rounds above a.handoff vertices, then (cluster_blocks
-// > 0) one cluster of cluster_blocks blocks the rest, back to back on s.
+// Rounds of at most this many vertices run in one block (the default of
+// picasso_schedule.block_max_n).
+constexpr int64_t kSmallBlockMaxN = 64;
+// part_cap: words of a.part; a launch uses at most part_cap / 3 blocks.  The
+// grid launch runs the rounds above the later stages' thresholds, then
+// (cluster_blocks > 0, a.handoff > 0) one cluster of cluster_blocks blocks
+// the rounds above a.handoff2, then (a.handoff2 > 0) one block the rest,
+// back to back on s.
 cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_blocks, int blocks_per_sm,
                                 cudaStream_t s);
 // Blocks of the largest cluster the engine can launch (16, 8, 4 or 2), 0 if none.

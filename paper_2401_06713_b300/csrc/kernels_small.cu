@@ -82,18 +82,25 @@ __device__ __forceinline__ int64_t block_excl(int64_t x, int64_t* sm, int64_t* t
   return before + inc - x;
 }
 
-// Barrier of every thread of the launch: the cooperative grid's, or, when
-// the launch is one thread-block cluster (CL), the cluster's hardware
-// barrier (release / acquire at cluster scope, which covers global memory
-// written by the cluster's blocks).
-template <bool CL>
+// Launch shapes of the engine: the cooperative grid (the larger rounds), one
+// thread-block cluster, one block (the smallest rounds).
+constexpr int kModeGrid = 0, kModeCluster = 1, kModeBlock = 2;
+
+// Barrier of every thread of the launch: the cooperative grid's (bounded in
+// time), the cluster's hardware barrier (release / acquire at cluster scope,
+// which covers global memory written by the cluster's blocks), or the
+// block's (which orders the block's global memory accesses as well).
+template <int MODE>
 __device__ __forceinline__ bool engine_sync(const SmallArgs& a, int site, int64_t round) {
-  if constexpr (CL) {
+  if constexpr (MODE == kModeCluster) {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
     return true;
+  } else if constexpr (MODE == kModeBlock) {
+    __syncthreads();
+    return true;
   } else {
-    // the grid's barrier is bounded in time: a block that gives up records
-    // where (first one only) and the launch ends with err[3] set
+    // a block that gives up records where (first one only) and the launch
+    // ends with err[3] set
     int seen = -1;
     if (grid_sync_bounded(a.bar, a.err + 3, kBarrierLimitNs, &seen)) return true;
     if (threadIdx.x == 0 && seen >= 0 && atomicCAS((unsigned long long*)(a.ctl + 9), 0ull, (unsigned long long)site) == 0ull) {
@@ -104,33 +111,111 @@ __device__ __forceinline__ bool engine_sync(const SmallArgs& a, int site, int64_
   }
 }
 
-// Exclusive scan of in[0..m) into out[0..m] (out[m] = the total) by the
-// whole grid: block b scans the b-th contiguous chunk after adding the sums
-// of the chunks before it (part: one word per block).  Contains a grid
-// barrier; every thread of the grid must call it.
-template <bool CL, class TI>
-__device__ bool grid_scan(const SmallArgs& a, int64_t round, const TI* in, int64_t m, int64_t* out, int64_t* part,
-                          int64_t* sm) {
+// Exclusive scans of NV values per element over elements 0 .. m - 1, by the
+// whole launch: block b takes the b-th contiguous chunk, adds the sums of the
+// chunks before it (a.part: NV words per block) and hands each element's
+// prefixes to put(i, ex); the last block calls put(m, totals).  get(i,
+// first, y) gives element i's values, first on the summing pass and again
+// (first = false) on the scanning pass.  Contains one barrier of the launch;
+// every thread must call it.
+template <int MODE, int NV, class Get, class Put>
+__device__ bool engine_scan(const SmallArgs& a, int64_t round, int64_t m, int64_t* sm, Get get, Put put) {
   const int64_t chunk = (m + gridDim.x - 1) / gridDim.x;
   const int64_t lo = min(m, chunk * (int64_t)blockIdx.x), hi = min(m, lo + chunk);
-  int64_t x = 0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) x += (int64_t)in[i];
-  x = block_sum(x, sm);
-  if (threadIdx.x == 0) part[blockIdx.x] = x;
-  if (!engine_sync<CL>(a, __LINE__, round)) return false;
-  int64_t pre = 0;
-  for (int64_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += __ldcg(part + b);
-  pre = block_sum(pre, sm);
+  int64_t x[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) x[v] = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    int64_t y[NV];
+    get(i, true, y);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] += y[v];
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int64_t t = block_sum(x[v], sm);
+    if (threadIdx.x == 0) a.part[NV * blockIdx.x + v] = t;
+  }
+  if (!engine_sync<MODE>(a, __LINE__, round)) return false;
+  int64_t pre[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    int64_t p = 0;
+    for (int64_t b = threadIdx.x; b < blockIdx.x; b += blockDim.x) p += __ldcg(a.part + NV * b + v);
+    pre[v] = block_sum(p, sm);
+  }
   for (int64_t t0 = lo; t0 < hi; t0 += blockDim.x) {
     const int64_t i = t0 + threadIdx.x;
-    const int64_t v = i < hi ? (int64_t)in[i] : 0;
-    int64_t tot = 0;
-    const int64_t ex = block_excl(v, sm, &tot);
-    if (i < hi) out[i] = pre + ex;
-    pre += tot;
+    int64_t y[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) y[v] = 0;
+    if (i < hi) get(i, false, y);
+    int64_t ex[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      int64_t tot = 0;
+      ex[v] = pre[v] + block_excl(y[v], sm, &tot);
+      pre[v] += tot;
+    }
+    if (i < hi) put(i, ex);
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[m] = pre;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) put(m, pre);
   return true;
+}
+
+// One vertex's list drawn by a warp (Alg. 1 assign_rand_list_colors): the
+// same picks as draw_list, Floyd's sampling on the same Philox words, in
+// ascending order.  Lane t computes picks t and t + 32 as if unseen, the
+// picks then take their final values one after another (a pick already
+// chosen is replaced by j = P - L + m), and each goes to the place given by
+// the number of smaller picks (the picks are distinct).  Writes out[0 .. L)
+// (bucket colors: + cofs), owner[0 .. L) = rk, counts every color in
+// bcount; returns the smallest color.  L <= 64.
+__device__ __forceinline__ uint32_t warp_draw_list(uint64_t seed, int32_t round, int64_t g, int64_t P, int L,
+                                                   int64_t cofs, int32_t* __restrict__ out,
+                                                   int32_t* __restrict__ owner, int32_t rk,
+                                                   uint32_t* __restrict__ bcount, int lane) {
+  uint32_t t0 = 0u, t1 = 0u;
+  if (lane < L) {
+    const uint32_t x = pick(philox_block(seed, round, g, kTagList, (uint32_t)(lane >> 2)), (uint32_t)(lane & 3));
+    t0 = (uint32_t)(((uint64_t)x * (uint64_t)(P - L + lane + 1)) >> 32);
+  }
+  if (lane + 32 < L) {
+    const int m = lane + 32;
+    const uint32_t x = pick(philox_block(seed, round, g, kTagList, (uint32_t)(m >> 2)), (uint32_t)(m & 3));
+    t1 = (uint32_t)(((uint64_t)x * (uint64_t)(P - L + m + 1)) >> 32);
+  }
+  uint32_t s0 = 0xFFFFFFFFu, s1 = 0xFFFFFFFFu;
+  for (int m = 0; m < L; ++m) {
+    const uint32_t t = __shfl_sync(0xffffffffu, m < 32 ? t0 : t1, m & 31);
+    const bool hit = (lane < m && s0 == t) || (lane + 32 < m && s1 == t);
+    const uint32_t val = __any_sync(0xffffffffu, hit) ? (uint32_t)(P - L + m) : t;
+    if (lane == (m & 31)) {
+      if (m < 32)
+        s0 = val;
+      else
+        s1 = val;
+    }
+  }
+  int c0 = 0, c1 = 0;
+  for (int m = 0; m < L; ++m) {
+    const uint32_t v = __shfl_sync(0xffffffffu, m < 32 ? s0 : s1, m & 31);
+    c0 += v < s0;
+    c1 += v < s1;
+  }
+  if (lane < L) {
+    const int32_t c = (int32_t)(cofs + s0);
+    out[c0] = c;
+    owner[lane] = rk;
+    atomicAdd(bcount + c, 1u);
+  }
+  if (lane + 32 < L) {
+    const int32_t c = (int32_t)(cofs + s1);
+    out[c1] = c;
+    owner[lane + 32] = rk;
+    atomicAdd(bcount + c, 1u);
+  }
+  return (uint32_t)(cofs + __reduce_min_sync(0xffffffffu, min(s0, s1)));
 }
 }  // namespace
 
@@ -257,7 +342,30 @@ __device__ void bucket_bits(const SmallArgs& a, int32_t* R, uint64_t* X, int lan
   __syncwarp();
 }
 
-template <int W, bool CL>
+// The round's priority keys (priority, global id) in V_l order (gid), the
+// buckets and color masks emptied (P bucket colors), the round's counters
+// zeroed: what a stage does before its first round (later rounds find it
+// done by the round before).
+__device__ void round_init(const SmallArgs& a, const int32_t* gid, int64_t n, int32_t round, int64_t P, int64_t gtid,
+                           int64_t gthreads) {
+  for (int64_t i = gtid; i < n; i += gthreads) {
+    const int32_t g = gid[i];
+    const int k = a.nsets > 1 ? find_set(a.soff, a.nsets, g) : 0;
+    a.key[i] = ((uint64_t)philox_block(a.sseed[k], round, g - a.soff[k], kTagPrio, 0u).x << 32) | (uint32_t)g;
+  }
+  for (int64_t c = gtid; c < P; c += gthreads) {
+    a.bcnt[c] = 0;
+    a.bcur[c] = 0;
+  }
+  for (int64_t t = gtid; t < 32 * P; t += gthreads) a.cmask[t] = 0u;
+  for (int64_t k = gtid; k < a.nsets; k += gthreads) a.snnz[k] = 0;
+  if (gtid == 0) {
+    a.ctl[3] = 0;
+    a.err[1] = 0;
+  }
+}
+
+template <int W, int MODE>
 __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_rounds(SmallArgs a) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   __shared__ int64_t scan_s[32];
@@ -267,16 +375,20 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
-  // per-vertex loops spread over all blocks: thread t of block b takes t G + b
-  const int64_t stid = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
   const int nsets = a.nsets;
 
-  // the cluster launch takes over from a grid launch that handed off (not
-  // from one whose barrier timed out)
-  if (CL && a.err[3] != 0) return;
-  if (CL && gtid == 0 && a.ctl[2] == kSmallHandoff) a.ctl[2] = kSmallOk;
+  // a later stage takes over from one that handed off (not from one whose
+  // grid barrier timed out)
+  if (MODE != kModeGrid && a.err[3] != 0) return;
+  if (MODE != kModeGrid && gtid == 0 && a.ctl[2] == kSmallHandoff) a.ctl[2] = kSmallOk;
   if (blockIdx.x == 0) set_prefixes(a, scan_s);
-  if (!engine_sync<CL>(a, __LINE__, 0)) return;
+  if (!engine_sync<MODE>(a, __LINE__, 0)) return;
+  {
+    const int64_t n = __ldcg(a.ctl + 0);
+    round_init(a, __ldcg(a.ctl + 4) ? a.gid_b : a.gid_a, n, a.round0 + (int32_t)__ldcg(a.ctl + 1), a.scof[nsets],
+               gtid, gthreads);
+  }
+  if (!engine_sync<MODE>(a, __LINE__, 0)) return;
 
   while (true) {
     const int64_t n = __ldcg(a.ctl + 0);
@@ -284,13 +396,13 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     const int32_t round = a.round0 + (int32_t)done;
     if (n == 0 || __ldcg(a.ctl + 2) != kSmallOk) break;
     if (round > a.max_rounds) {
-      if (!engine_sync<CL>(a, __LINE__, round)) return;
+      if (!engine_sync<MODE>(a, __LINE__, round)) return;
       if (gtid == 0) a.ctl[2] = kSmallMaxRounds;
       break;
     }
-    if (!CL && n <= a.handoff) {
-      // small enough for one cluster: its barriers cost far less
-      if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if ((MODE == kModeGrid && n <= a.handoff) || (MODE == kModeCluster && n <= a.handoff2)) {
+      // small enough for the next stage, whose barriers cost less
+      if (!engine_sync<MODE>(a, __LINE__, round)) return;
       if (gtid == 0) a.ctl[2] = kSmallHandoff;
       break;
     }
@@ -299,27 +411,11 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     const int64_t P = a.scof[nsets];
     const int64_t E = a.seoff[nsets];
 
-    // (priority, global id) keys in V_l order; empty buckets
-    for (int64_t i = stid; i < n; i += gthreads) {
-      const int k = nsets > 1 ? find_set(a.svoff, nsets, i) : 0;
-      const int32_t g = gid[i];
-      a.key[i] = ((uint64_t)philox_block(a.sseed[k], round, g - a.soff[k], kTagPrio, 0u).x << 32) | (uint32_t)g;
-    }
-    for (int64_t c = gtid; c < P; c += gthreads) {
-      a.bcnt[c] = 0;
-      a.bcur[c] = 0;
-    }
-    // the buckets' color masks of the mask coloring start empty; the
-    // round's run counts at zero
-    for (int64_t t = gtid; t < 32 * P; t += gthreads) a.cmask[t] = 0u;
-    for (int64_t k = gtid; k < nsets; k += gthreads) a.snnz[k] = 0;
-    if (gtid == 0) a.ctl[3] = 0;
-    if (gtid == 0) a.err[1] = 0;
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
-
     // rank of vertex i = its set's offset + the number of smaller keys in the
-    // set: warp per vertex, lanes over the set; the round's arrays are
-    // written at the rank
+    // set (warp per vertex, lanes over the set); the round's arrays are
+    // written at the rank, the rank at i (pos), and the warp draws the
+    // vertex's list in rank order (bucket colors: + the set's offset): list
+    // offset, entry owners, first candidate, bucket sizes
     for (int64_t i = gwarp; i < n; i += nwarps) {
       const int k = nsets > 1 ? find_set(a.svoff, nsets, i) : 0;
       const int64_t v0 = a.svoff[k], v1 = a.svoff[k + 1];
@@ -327,51 +423,46 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       int r = 0;
       for (int64_t j = v0 + lane; j < v1; j += 32) r += a.key[j] < ki;
       const int64_t rk = v0 + __reduce_add_sync(0xffffffffu, r);
+      const int32_t g = (int32_t)(uint32_t)ki;
       if (lane == 0) {
-        const int32_t g = (int32_t)(uint32_t)ki;
         a.perm[rk] = (int32_t)i;
         a.gid_r[rk] = g;
         a.sid[rk] = k;
-#pragma unroll
-        for (int k = 0; k < 2 * W; ++k) a.xz_r[2 * W * rk + k] = a.xz[2 * W * (int64_t)g + k];
+        a.pos[i] = rk;
       }
-    }
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
-
-    // lists in rank order (bucket colors: + the set's offset), list offsets,
-    // entry owners, first candidates (the ranked coloring reads no priority
-    // from the state word), bucket sizes
-    for (int64_t r = stid; r < n; r += gthreads) {
-      const int k = a.sid[r];
-      const int64_t v0 = a.svoff[k], nk = a.svoff[k + 1] - v0;
-      const int2 pl = a.ptab[nk];
-      const int64_t row = a.seoff[k] + (r - v0) * pl.y;
-      int32_t* out = a.lists + row;
-      draw_list<kSmallLCap>(a.sseed[k], round, a.gid_r[r] - a.soff[k], pl.x, pl.y, a.scof[k], out);
-      a.loff[r] = row;
-      a.state[r] = ((uint64_t)(uint32_t)out[0] << 2) | kUndecided;
-      for (int t = 0; t < pl.y; ++t) {
-        a.ent_v[row + t] = (int32_t)r;
-        atomicAdd(a.bcnt + out[t], 1u);
+      if (lane < 2 * W) a.xz_r[2 * W * rk + lane] = a.xz[2 * W * (int64_t)g + lane];
+      const int2 pl = a.ptab[v1 - v0];
+      const int64_t row = a.seoff[k] + (rk - v0) * pl.y;
+      const uint32_t first = warp_draw_list(a.sseed[k], round, g - a.soff[k], pl.x, pl.y, a.scof[k], a.lists + row,
+                                            a.ent_v + row, (int32_t)rk, a.bcnt, lane);
+      if (lane == 0) {
+        a.loff[rk] = row;
+        a.state[rk] = ((uint64_t)first << 2) | kUndecided;
       }
     }
     if (gtid == 0) a.loff[n] = E;
-    // bucket work items (32 members each); a bucket above the cap stops the
-    // engine
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
-    for (int64_t c = gtid; c < P; c += gthreads) {
-      const uint32_t sc = a.bcnt[c];
-      const uint32_t nwb = (sc + 31) / 32;
-      a.bitems[c] = nwb;
-      a.bwords[c] = 16u * nwb * (nwb + 1u);  // the bucket's lower blocks, row-major
-      if (sc > (uint32_t)kSmallBucketCap) a.err[2] = 1;
+    if (!engine_sync<MODE>(a, __LINE__, round)) return;
+
+    // bucket offsets, work items (32 members each) and words of the bit rows
+    // (the lower blocks, row-major) in one scan; a bucket above the cap stops
+    // the engine
+    {
+      auto get = [&](int64_t c, bool first, int64_t* y) {
+        const uint32_t sc = a.bcnt[c];
+        const int64_t nwb = (sc + 31) / 32;
+        y[0] = sc;
+        y[1] = nwb;
+        y[2] = 16 * nwb * (nwb + 1);
+        if (first && sc > (uint32_t)kSmallBucketCap) a.err[2] = 1;
+      };
+      auto put = [&](int64_t c, const int64_t* ex) {
+        a.boff[c] = ex[0];
+        a.iboff[c] = ex[1];
+        a.moff[c] = ex[2];
+      };
+      if (!engine_scan<MODE, 3>(a, round, P, scan_s, get, put)) return;
     }
-    if (!grid_scan<CL>(a, round, a.bcnt, P, a.boff, a.part, scan_s)) return;
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
-    if (!grid_scan<CL>(a, round, a.bitems, P, a.iboff, a.part, scan_s)) return;
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
-    if (!grid_scan<CL>(a, round, a.bwords, P, a.moff, a.part, scan_s)) return;
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (!engine_sync<MODE>(a, __LINE__, round)) return;
     if (__ldcg(a.err + 2) != 0 || __ldcg(a.moff + P) > a.wcap) {
       if (gtid == 0) a.ctl[2] = kSmallOverflow;
       break;
@@ -384,7 +475,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     for (int64_t c = gtid; c < P; c += gthreads)
       for (int64_t t = a.iboff[c]; t < a.iboff[c + 1]; ++t) a.ibkt[t] = (int32_t)c;
     if (gtid == 0) a.ctl[8] = a.iboff[P];
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (!engine_sync<MODE>(a, __LINE__, round)) return;
 
     // each bucket ascending (entries ascend with the rank), then its
     // members' ranks and words in that order
@@ -400,22 +491,21 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         for (int k = 0; k < 2 * W; ++k) a.bxz[2 * W * (b0 + i) + k] = a.xz_r[2 * W * (int64_t)r + k];
       }
     }
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (!engine_sync<MODE>(a, __LINE__, round)) return;
 
     bucket_bits<W>(a, Rw, Xw, lane, gwarp, nwarps);
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (!engine_sync<MODE>(a, __LINE__, round)) return;
     {
       // the round's CSR, counted as the byte budget counts it (8 bytes per
       // row and one, 4 per run entry): over the budget, the round goes back
       const int64_t nnz = __ldcg(a.ctl + 3);
       const int64_t csr_bytes = 8 * (n + 1) + 4 * nnz;
       if (a.budget > 0 && csr_bytes > a.budget) {
-        if (!engine_sync<CL>(a, __LINE__, round)) return;
+        if (!engine_sync<MODE>(a, __LINE__, round)) return;
         if (gtid == 0) a.ctl[2] = kSmallOverflow;
         break;
       }
     }
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
     if (gtid == 0) a.ctl[6] += __ldcg(a.ctl + 3);
 
     // ordered first fit in rank order; warps take ranks from a counter
@@ -440,28 +530,52 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
         ok = mask_vertex<true>(ca, t, lane, a.err);
       }
     }
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (!engine_sync<MODE>(a, __LINE__, round)) return;
     if (__ldcg(a.err) != 0) {
       if (gtid == 0) a.ctl[2] = kSmallTimeout;
       break;
     }
 
-    // carry: colors at global ids (final color = the set's base + bucket
-    // color - the set's offset), flags in V_l order
-    for (int64_t r = gtid; r < n; r += gthreads) {
-      const uint32_t w = (uint32_t)__ldcg(a.state + r);
-      const bool colored = (w & 3u) == kColored;
-      if (colored) {
-        const int k = a.sid[r];
-        a.color[a.gid_r[r]] = (int32_t)(a.sbase[k] + ((int64_t)(w >> 2) - a.scof[k]));
-      }
-      a.flag[a.perm[r]] = colored ? 0u : 1u;
+    // carry, in the scan of the uncolored flags (V_l order): colors at global
+    // ids (final color = the set's base + bucket color - the set's offset)
+    // on the summing pass; pos[i] (the rank of i) becomes the number of
+    // uncolored vertices before i.  The buckets, masks and counters are
+    // emptied for the next round (its P is at most this round's).
+    for (int64_t c = gtid; c < P; c += gthreads) {
+      a.bcnt[c] = 0;
+      a.bcur[c] = 0;
     }
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
-    if (!grid_scan<CL>(a, round, a.flag, n, a.pos, a.part, scan_s)) return;
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
-    for (int64_t i = gtid; i < n; i += gthreads)
-      if (a.flag[i]) gid_next[a.pos[i]] = gid[i];
+    for (int64_t t = gtid; t < 32 * P; t += gthreads) a.cmask[t] = 0u;
+    if (gtid == 0) {
+      a.ctl[3] = 0;
+      a.err[1] = 0;
+    }
+    {
+      auto get = [&](int64_t i, bool first, int64_t* y) {
+        const int64_t r = __ldcg(a.pos + i);
+        const uint32_t w = (uint32_t)__ldcg(a.state + r);
+        const bool colored = (w & 3u) == kColored;
+        if (first && colored) {
+          const int k = a.sid[r];
+          a.color[gid[i]] = (int32_t)(a.sbase[k] + ((int64_t)(w >> 2) - a.scof[k]));
+        }
+        y[0] = colored ? 0 : 1;
+      };
+      auto put = [&](int64_t i, const int64_t* ex) { a.pos[i] = ex[0]; };
+      if (!engine_scan<MODE, 1>(a, round, n, scan_s, get, put)) return;
+    }
+    if (!engine_sync<MODE>(a, __LINE__, round)) return;
+    // the uncolored set in ascending global id, with its keys for the next
+    // round
+    for (int64_t i = gtid; i < n; i += gthreads) {
+      const int64_t p0 = a.pos[i];
+      if (a.pos[i + 1] != p0) {
+        const int32_t g = gid[i];
+        gid_next[p0] = g;
+        const int k = nsets > 1 ? find_set(a.soff, nsets, g) : 0;
+        a.key[p0] = ((uint64_t)philox_block(a.sseed[k], round + 1, g - a.soff[k], kTagPrio, 0u).x << 32) | (uint32_t)g;
+      }
+    }
     if (blockIdx.x == 0) {
       // per set: next palette base, largest CSR bytes of a round, vertices
       // left; then the next round's offsets
@@ -475,6 +589,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
           a.speak[k] = max(a.speak[k], 8 * (nk + 1) + 4 * nnzk);
           pairs += nk * (nk - 1) / 2;
         }
+        a.snnz[k] = 0;
         a.srem[k] = a.pos[v1] - a.pos[v0];
       }
       pairs = block_sum(pairs, scan_s);
@@ -487,7 +602,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       __syncthreads();
       set_prefixes(a, scan_s);
     }
-    if (!engine_sync<CL>(a, __LINE__, round)) return;
+    if (!engine_sync<MODE>(a, __LINE__, round)) return;
   }
 }
 
@@ -495,10 +610,12 @@ size_t small_smem_bytes(int32_t qw) {
   return (size_t)kSmallWarps * (qw == 2 ? warp_smem_bytes<2>() : warp_smem_bytes<1>());
 }
 
-// The grid launch (cooperative, up to kSmallBlocksPerSm blocks per SM) runs
-// the rounds above a.handoff vertices; the cluster launch (one cluster of
-// cluster_blocks blocks) runs the rest.  `cluster_blocks` 0: no cluster
-// launch (the grid launch runs every round).
+// Up to three stages back to back on s: the grid launch (cooperative, up to
+// kSmallBlocksPerSm blocks per SM) runs the rounds above the cluster's and
+// the block's thresholds, the cluster launch (one cluster of cluster_blocks
+// blocks; a.handoff > 0) the rounds above a.handoff2 vertices, the block
+// launch (a.handoff2 > 0) the rest.  A stage with no round left returns at
+// once.
 cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_blocks, int blocks_per_sm,
                                 cudaStream_t s) {
   int dev = 0, sms = 148, per_sm = 0;
@@ -509,11 +626,14 @@ cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_bl
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  const int64_t hb = std::max<int64_t>(a.handoff2, 0);
+  const int64_t hc = cluster_blocks > 0 ? std::max<int64_t>(a.handoff, 0) : 0;
+  const bool cluster_stage = hc > hb && a.n0 > hb;
   SmallArgs args = a;
-  if (cluster_blocks <= 0) args.handoff = 0;
-  const bool grid_rounds = cluster_blocks <= 0 || a.n0 > args.handoff;
-  if (grid_rounds) {
-    auto kern = a.qw == 2 ? k_small_rounds<2, false> : k_small_rounds<1, false>;
+  args.handoff = std::max(hc, hb);  // where the grid stage stops
+  args.handoff2 = hb;               // where the cluster stage stops
+  if (args.handoff == 0 || a.n0 > args.handoff) {
+    auto kern = a.qw == 2 ? k_small_rounds<2, kModeGrid> : k_small_rounds<1, kModeGrid>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmallThreads, smem);
     if (e != cudaSuccess) return e;
@@ -522,7 +642,7 @@ cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_bl
     // 16 warps per SM for the latency-bound phases
     int blocks = std::min(per_sm, blocks_per_sm > 0 ? std::min(blocks_per_sm, kSmallBlocksPerSm) : kSmallBlocksPerSm) *
                  sms;
-    blocks = std::min(blocks, part_cap);
+    blocks = std::min(blocks, part_cap / 3);  // the scans' block sums: 3 words a block
     blocks = (int)debug_grid(blocks);
     void* params[] = {(void*)&args};
     e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)blocks), dim3(kSmallThreads), params,
@@ -530,26 +650,36 @@ cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_bl
     count_launches(1);
     if (e != cudaSuccess) return e;
   }
-  if (cluster_blocks <= 0) return cudaSuccess;
-  auto kern = a.qw == 2 ? k_small_rounds<2, true> : k_small_rounds<1, true>;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && cluster_blocks > 8)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)std::min(cluster_blocks, part_cap);
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(attr[0].val.clusterDim.x);
-  cfg.blockDim = dim3(kSmallThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, kern, args);
-  count_launches(1);
+  if (cluster_stage) {
+    auto kern = a.qw == 2 ? k_small_rounds<2, kModeCluster> : k_small_rounds<1, kModeCluster>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && cluster_blocks > 8)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)std::min(cluster_blocks, part_cap / 3);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(attr[0].val.clusterDim.x);
+    cfg.blockDim = dim3(kSmallThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, args);
+    count_launches(1);
+    if (e != cudaSuccess) return e;
+  }
+  if (hb > 0) {
+    auto kern = a.qw == 2 ? k_small_rounds<2, kModeBlock> : k_small_rounds<1, kModeBlock>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<1, kSmallThreads, smem, s>>>(args);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
   return e;
 }
 
@@ -558,7 +688,7 @@ cudaError_t launch_small_rounds(const SmallArgs& a, int part_cap, int cluster_bl
 int small_cluster_blocks(int32_t qw) {
   if (qw != 1 && qw != 2) return 0;
   const size_t smem = small_smem_bytes(qw);
-  auto kern = qw == 2 ? k_small_rounds<2, true> : k_small_rounds<1, true>;
+  auto kern = qw == 2 ? k_small_rounds<2, kModeCluster> : k_small_rounds<1, kModeCluster>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
   for (int k = 16; k >= 2; k >>= 1) {

@@ -37,6 +37,7 @@ class Schedule(ctypes.Structure):
         ("bits_blocks_per_sm", ctypes.c_int32),
         ("color_blocks_per_sm", ctypes.c_int32),
         ("engine_max_n", ctypes.c_int32),
+        ("block_max_n", ctypes.c_int32),
     ]
 
     def as_dict(self):

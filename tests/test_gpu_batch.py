@@ -127,8 +127,8 @@ def test_batch_equals_single_runs_larger(pc):
 
 
 # Launch schedules (picasso_schedule): the engine's grid, the rounds it gives
-# to one thread-block cluster, the blocks per SM of the bit pass and of the
-# mask coloring.  None of them may change a color.
+# to one thread-block cluster and to one block, the blocks per SM of the bit
+# pass and of the mask coloring.  None of them may change a color.
 _SCHEDULES = [
     {},
     {"engine_blocks_per_sm": 1},
@@ -139,6 +139,10 @@ _SCHEDULES = [
     {"bits_blocks_per_sm": 1, "color_blocks_per_sm": 1, "engine_blocks_per_sm": 1},
     {"engine_max_n": 4096},
     {"engine_max_n": 64, "cluster_max_n": 16},
+    {"block_max_n": -1},
+    {"block_max_n": 2048, "cluster_max_n": 1024},
+    {"block_max_n": 16384},
+    {"block_max_n": 40, "cluster_max_n": -1},
 ]
 
 
@@ -173,11 +177,11 @@ def test_autotune_picks_a_valid_schedule(pc, orc):
     xz = pc.pack(torch.from_numpy(padded).cuda())
     best, best_ms, start_ms = pc.autotune(xz, q, set_offsets=offs, seeds=seeds, reps=1)
     assert set(best) == {"engine_blocks_per_sm", "cluster_max_n", "cluster_blocks", "bits_blocks_per_sm",
-                         "color_blocks_per_sm", "engine_max_n"}
+                         "color_blocks_per_sm", "engine_max_n", "block_max_n"}
     assert best["engine_max_n"] in (0, 16384, 8192, 4096)
     assert best["engine_blocks_per_sm"] in (0, 1, 2) and best["cluster_max_n"] in (0, -1, 512, 2048, 8192)
     assert best["cluster_blocks"] in (0, 8, 16) and best["bits_blocks_per_sm"] in (0, 2, 3, 4)
-    assert best["color_blocks_per_sm"] in (0, 3, 4, 6)
+    assert best["color_blocks_per_sm"] in (0, 3, 4, 6) and best["block_max_n"] in (0, -1, 64, 256, 1024)
     # a candidate replaces the start only if it is at least 1 % faster
     assert 0 < best_ms <= start_ms
     with pc.Picasso(xz, q, set_offsets=offs, seeds=seeds, schedule=best) as p:
@@ -189,7 +193,8 @@ def test_autotune_picks_a_valid_schedule(pc, orc):
 
 @pytest.mark.parametrize("bad", [{"engine_blocks_per_sm": 3}, {"cluster_max_n": -2}, {"cluster_max_n": 16385},
                                  {"cluster_blocks": 6}, {"bits_blocks_per_sm": 5}, {"color_blocks_per_sm": 9},
-                                 {"engine_max_n": -1}, {"engine_max_n": 16385}])
+                                 {"engine_max_n": -1}, {"engine_max_n": 16385}, {"block_max_n": -2},
+                                 {"block_max_n": 16385}])
 def test_schedule_validated(pc, bad):
     chars = synth.pauli_uniform(50, 10, seed=2)
     xz = pc.pack(torch.from_numpy(chars).cuda())

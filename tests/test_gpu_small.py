@@ -89,8 +89,9 @@ def test_engine_launch_count(pc):
         _, r = p.run()
         torch.cuda.synchronize()
         k = pc.kernel_launches() - k0
-    # iota of V_1, the engine, the gather of the result (none: all colored)
-    assert r > 5 and k <= 3, (r, k)
+    # iota of V_1, the engine's three stages (grid, cluster, block), the
+    # gather of the result (none: all colored)
+    assert r > 5 and k <= 5, (r, k)
 
 
 @pytest.mark.parametrize("stop_after", [1, 4])
