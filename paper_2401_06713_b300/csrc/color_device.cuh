@@ -271,19 +271,24 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
         bl = ((r0 & tk.x) | (r1 & tk.y) | (r2 & tk.z) | (r3 & tk.w)) != 0u;
         pe = ((r0 & ~(tk.x | nv.x)) | (r1 & ~(tk.y | nv.y)) | (r2 & ~(tk.z | nv.z)) | (r3 & ~(tk.w | nv.w))) != 0u;
       }
-      // nibble j of each ballot: candidate k0 + j taken / pending
-      const uint32_t blockedm = __ballot_sync(0xffffffffu, bl);
-      const uint32_t pendm = __ballot_sync(0xffffffffu, pe);
-#pragma unroll 1
-      for (int j = 0; j < kMaskCands; ++j) {
+      // nibble j of each ballot: candidate k0 + j taken / pending; bit 4 j of
+      // `open`: candidate k0 + j exists and is not taken
+      uint32_t taken = __ballot_sync(0xffffffffu, bl), pend = __ballot_sync(0xffffffffu, pe);
+      taken |= taken >> 1;
+      taken |= taken >> 2;
+      pend |= pend >> 1;
+      pend |= pend >> 2;
+      const int ncand = min(kMaskCands, kend - k0);
+      uint32_t open = ~taken & 0x11111111u & (ncand >= 8 ? 0xffffffffu : (1u << (4 * ncand)) - 1u);
+      while (open != 0u) {
+        const int j = (__ffs(open) - 1) >> 2;
+        open &= open - 1u;
         const int kk = k0 + j;
-        if (kk >= kend) break;
-        if ((blockedm >> (4 * j)) & 0xFu) continue;
         // earlier candidates are passed: say so before waiting or deciding
         mask_resolve<FRESH>(a, row, kdone, kb + kk, -1, lane, kb, my_c, my_rb);
         kdone = kb + kk;
         bool blocked = false;
-        if ((pendm >> (4 * j)) & 0xFu) {
+        if ((pend >> (4 * j)) & 1u) {
           // wait for the earlier neighbours that may still take c
           const uint32_t c = __shfl_sync(0xffffffffu, my_c, kk);
           const int64_t rb = __shfl_sync(0xffffffffu, my_rb, kk);

@@ -72,7 +72,7 @@ cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* b
 // same warp then writes the sorted members' words and vertex ids in slot
 // order (bxz, bpid), as k_bucket_gather would.
 template <bool GATHER>
-__global__ void __launch_bounds__(256) k_bucket_sort_warp(const int64_t* __restrict__ boff, int64_t P,
+__global__ void __launch_bounds__(256, 4) k_bucket_sort_warp(const int64_t* __restrict__ boff, int64_t P,
                                                           int32_t* __restrict__ bmem, ConflictArgs a,
                                                           uint4* __restrict__ bxz, int32_t* __restrict__ bpid) {
   const int lane = threadIdx.x & 31;
@@ -95,13 +95,31 @@ __global__ void __launch_bounds__(256) k_bucket_sort_warp(const int64_t* __restr
     else
       warp_sort_bucket<16>(p, s, lane);
     if (GATHER) {
+      // four members a lane at a time, every load issued before the stores
+      // (the words are 16-byte aligned: x, z of a vertex side by side)
       __syncwarp();
-      for (int i = lane; i < s; i += 32) {
-        const int32_t flat = p[i];
-        const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
-        const uint64_t x = a.xz[2 * v], z = a.xz[2 * v + 1];
-        bxz[o + i] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
-        bpid[o + i] = (int32_t)v;
+      for (int i0 = 0; i0 < s; i0 += 128) {
+        int32_t f[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u + lane;
+          f[u] = i < s ? p[i] : -1;
+        }
+        int32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = f[u] < 0 ? 0 : (a.Lu ? f[u] / a.Lu : a.ent_v[f[u]]);
+        uint4 w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          w[u] = f[u] < 0 ? make_uint4(0u, 0u, 0u, 0u) : __ldg(reinterpret_cast<const uint4*>(a.xz + 2 * (int64_t)v[u]));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + 32 * u + lane;
+          if (f[u] >= 0) {
+            bxz[o + i] = w[u];
+            bpid[o + i] = v[u];
+          }
+        }
       }
     }
   }
@@ -161,6 +179,8 @@ cudaError_t launch_bucket_sort_gather(const int64_t* boff, int64_t P, int32_t* b
                                       const ConflictArgs& a, uint4* bxz, int32_t* bpid, cudaStream_t s) {
   if (P <= 0) return cudaSuccess;
   if (smax > kWarpSortMax) return cudaErrorInvalidValue;
+  // a member's words are read 16 bytes at a time
+  if (reinterpret_cast<uintptr_t>(a.xz) & 15) return cudaErrorMisalignedAddress;
   const unsigned wblocks = (unsigned)std::min<int64_t>((P + 7) / 8, 148 * 16);
   k_bucket_sort_warp<true><<<wblocks, 256, 0, s>>>(boff, P, bmem, a, bxz, bpid);
   count_launches(1);
