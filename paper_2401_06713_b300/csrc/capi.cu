@@ -537,8 +537,10 @@ int assign_round(Ctx* c) {
   // bucket sizes counted as the lists are drawn when the build will join
   // through buckets (lists of at most 32 colors)
   const int algo = c->cfg.conflict_algo;
-  const bool buckets = Lmax <= 32 && c->Ptot < kBucketMaxP && algo != PICASSO_CONFLICT_ALLPAIRS &&
-                       !(algo == PICASSO_CONFLICT_AUTO && n <= kSmallRoundAllPairs);
+  // (more bucket colors than one block's shared memory counts: the build
+  // counts them without global atomics otherwise)
+  const bool buckets = Lmax <= 32 && c->Ptot < kBucketMaxP && c->Ptot > kHistMaxP &&
+                       algo != PICASSO_CONFLICT_ALLPAIRS && !(algo == PICASSO_CONFLICT_AUTO && n <= kSmallRoundAllPairs);
   if (buckets) {
     ST(alloc(c, &c->bcount, c->Ptot));
     CK(cudaMemsetAsync(c->bcount, 0, sizeof(uint32_t) * c->Ptot, s));
@@ -555,6 +557,8 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
 
   uint32_t *cnt = nullptr, *bcount = nullptr, *bcursor = nullptr, *dmax = nullptr;
   uint32_t *words = nullptr, *rmask = nullptr;
+  uint16_t* hist = nullptr;  // per entry range and color: counts, then the ranges before
+  int64_t hist_g = 0;
   unsigned long long* dsq = nullptr;
   int64_t *boff = nullptr, *moff = nullptr, *jboff = nullptr;
   int32_t *bmem = nullptr, *ibkt = nullptr, *bpid = nullptr;
@@ -565,6 +569,7 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
     release(c, &cnt);
     release(c, &bcount);
     release(c, &bcursor);
+    release(c, &hist);
     release(c, &dmax);
     release(c, &dsq);
     release(c, &boff);
@@ -617,6 +622,11 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
     if (c->bcount) {
       bcount = c->bcount;  // counted while the lists were drawn
       c->bcount = nullptr;
+    } else if (P <= kHistMaxP) {
+      hist_g = bucket_hist_blocks(E);
+      TRY(alloc(c, &bcount, P));
+      TRY(alloc(c, &hist, hist_g * 2 * ((P + 1) / 2)));
+      TRYC(launch_bucket_count(c->lists, E, P, hist, hist_g, bcount, s));
     } else {
       TRY(alloc(c, &bcount, P));
       TRYC(cudaMemsetAsync(bcount, 0, sizeof(uint32_t) * P, s));
@@ -658,11 +668,16 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
 
   if (algo == PICASSO_CONFLICT_BUCKET) {
     TRYC(launch_scan_u32(bcount, P, boff, tmp, s));
-    TRY(alloc(c, &bcursor, P));
     TRY(alloc(c, &bmem, E));
-    TRYC(cudaMemsetAsync(bcursor, 0, sizeof(uint32_t) * P, s));
-    TRYC(launch_bucket_fill(c->lists, E, boff, bcursor, bmem, s));
-    release(c, &bcursor);
+    if (hist) {
+      TRYC(launch_bucket_place(c->lists, E, P, hist, hist_g, boff, bmem, s));
+      release(c, &hist);
+    } else {
+      TRY(alloc(c, &bcursor, P));
+      TRYC(cudaMemsetAsync(bcursor, 0, sizeof(uint32_t) * P, s));
+      TRYC(launch_bucket_fill(c->lists, E, boff, bcursor, bmem, s));
+      release(c, &bcursor);
+    }
     // the bit layout: EARLIER form, no byte budget, buckets of at most
     // kFusedMax members, strings of one word per part
     // (the bit rows' words, bounded below, must fit rinfo's address field)

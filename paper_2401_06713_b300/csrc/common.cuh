@@ -340,6 +340,18 @@ struct ConflictArgs {
 // member is stored as its list-entry index e (owner ent_v[e], position
 // e - loff[owner]).
 cudaError_t launch_bucket_hist(const int32_t* lists, int64_t E, uint32_t* bcount, cudaStream_t s);
+// The same sizes, and the members' places, without global atomics (kernels
+// in kernels_conflict.cu): entries cut into G = bucket_hist_blocks(E) ranges,
+// hist [G][P rounded up to even] 16-bit counts, then per range and color the
+// count of the ranges before it; bcount[c] the bucket sizes.  P <= kHistMaxP.
+// launch_bucket_place writes bmem[boff[c] + ...] like launch_bucket_fill
+// (members in entry order across ranges, in arrival order within one).
+constexpr int64_t kHistMaxP = 110000;  // 16-bit counters of P colors in one block's shared memory
+int64_t bucket_hist_blocks(int64_t E);
+cudaError_t launch_bucket_count(const int32_t* lists, int64_t E, int64_t P, uint16_t* hist, int64_t G,
+                                uint32_t* bcount, cudaStream_t s);
+cudaError_t launch_bucket_place(const int32_t* lists, int64_t E, int64_t P, const uint16_t* hist, int64_t G,
+                                const int64_t* boff, int32_t* bmem, cudaStream_t s);
 cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* boff, uint32_t* bcursor,
                                int32_t* bmem, cudaStream_t s);
 cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, int32_t smax,

@@ -63,6 +63,117 @@ cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* b
   return cudaGetLastError();
 }
 
+// Bucket sizes and places without global atomics.  The list entries are cut
+// into G contiguous ranges of at most 65,535 entries (so a color occurs at
+// most 65,535 times in one); block b counts its range's colors in shared
+// memory (two 16-bit counters a word) and writes them to hist[b] (P rounded
+// up to even, 16 bits a color).  A column pass turns hist[b][c] into the
+// number of entries of color c in the ranges before b and sums bcount[c].
+// The place pass runs over the same ranges, a block per range and slice of
+// colors: the block keeps boff[c] + hist[b][c] of its colors in shared memory
+// and gives entry e of color c in range b the next place (a shared-memory
+// atomic), so each entry costs one global store.  Within a bucket the ranges
+// are thus in entry order; the bucket sort orders each range's members.
+constexpr int kHistThreads = 1024;
+constexpr int64_t kPlaceSlice = 24576;  // colors of one place block (96 KB of places)
+
+int64_t bucket_hist_blocks(int64_t E) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max<int64_t>(sms, (E + 65534) / 65535);
+}
+
+__global__ void __launch_bounds__(kHistThreads) k_bucket_count(const int32_t* __restrict__ lists, int64_t E,
+                                                               int64_t P, uint16_t* __restrict__ hist) {
+  extern __shared__ uint32_t h2[];  // [(P + 1) / 2]
+  const int64_t hw = (P + 1) / 2;
+  for (int64_t i = threadIdx.x; i < hw; i += blockDim.x) h2[i] = 0u;
+  __syncthreads();
+  const int64_t e0 = E * blockIdx.x / gridDim.x, e1 = E * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int32_t c = lists[e];
+    atomicAdd(&h2[c >> 1], 1u << (16 * (c & 1)));
+  }
+  __syncthreads();
+  uint32_t* out = reinterpret_cast<uint32_t*>(hist + 2 * hw * (int64_t)blockIdx.x);
+  for (int64_t i = threadIdx.x; i < hw; i += blockDim.x) out[i] = h2[i];
+}
+
+__global__ void k_bucket_colsum(uint16_t* __restrict__ hist, int64_t P, int64_t G, uint32_t* __restrict__ bcount) {
+  const int64_t stride = 2 * ((P + 1) / 2);
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < P; c += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t run = 0;
+    // 16 ranges at a time: their loads are in flight together
+    for (int64_t b0 = 0; b0 < G; b0 += 16) {
+      uint32_t x[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) x[u] = b0 + u < G ? (uint32_t)__ldcg(hist + (b0 + u) * stride + c) : 0u;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        if (b0 + u < G) hist[(b0 + u) * stride + c] = (uint16_t)run;  // exact while a bucket has <= 65,535 members
+        run += x[u];
+      }
+    }
+    bcount[c] = run;
+  }
+}
+
+__global__ void __launch_bounds__(kHistThreads) k_bucket_place(const int32_t* __restrict__ lists, int64_t E,
+                                                               int64_t P, int npass, const uint16_t* __restrict__ hist,
+                                                               const int64_t* __restrict__ boff,
+                                                               int32_t* __restrict__ bmem) {
+  // block (range b, color slice p): the slice's next free places of range b
+  // in shared memory, then the range's entries of those colors
+  extern __shared__ uint32_t nxt[];
+  const int64_t b = blockIdx.x / npass, p = blockIdx.x % npass;
+  const int64_t cp0 = P * p / npass, cp1 = P * (p + 1) / npass;
+  const uint16_t* pre = hist + 2 * ((P + 1) / 2) * b;
+  for (int64_t c = cp0 + threadIdx.x; c < cp1; c += blockDim.x) nxt[c - cp0] = (uint32_t)(boff[c] + pre[c]);
+  __syncthreads();
+  const int64_t G = gridDim.x / npass;
+  const int64_t e0 = E * b / G, e1 = E * (b + 1) / G;
+  // four entries a thread at a time: their loads are in flight together
+  for (int64_t e00 = e0; e00 < e1; e00 += 4 * (int64_t)blockDim.x) {
+    int32_t c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t e = e00 + u * (int64_t)blockDim.x + threadIdx.x;
+      c[u] = e < e1 ? lists[e] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (c[u] >= cp0 && c[u] < cp1)
+        bmem[atomicAdd(&nxt[c[u] - cp0], 1u)] = (int32_t)(e00 + u * (int64_t)blockDim.x + threadIdx.x);
+  }
+}
+
+cudaError_t launch_bucket_count(const int32_t* lists, int64_t E, int64_t P, uint16_t* hist, int64_t G,
+                                uint32_t* bcount, cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  if (P > kHistMaxP || G < 1 || E > 65535 * G) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(uint32_t) * (size_t)((P + 1) / 2);
+  cudaError_t e = cudaFuncSetAttribute(k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_bucket_count<<<(unsigned)G, kHistThreads, smem, s>>>(lists, E, P, hist);
+  k_bucket_colsum<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(hist, P, G, bcount);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_place(const int32_t* lists, int64_t E, int64_t P, const uint16_t* hist, int64_t G,
+                                const int64_t* boff, int32_t* bmem, cudaStream_t s) {
+  if (E <= 0 || P <= 0) return cudaSuccess;
+  if (P > kHistMaxP || G < 1 || E > 65535 * G) return cudaErrorInvalidValue;
+  // color slices of at most kPlaceSlice colors: two blocks per SM
+  const int npass = (int)((P + kPlaceSlice - 1) / kPlaceSlice);
+  const size_t smem = sizeof(uint32_t) * (size_t)((P + npass - 1) / npass);
+  cudaError_t e = cudaFuncSetAttribute(k_bucket_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_bucket_place<<<(unsigned)(G * npass), kHistThreads, smem, s>>>(lists, E, P, npass, hist, boff, bmem);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // Ascending order inside each bucket.  Buckets of up to 512 members: one warp
 // per bucket, a bitonic network in registers (lane l holds elements
 // l*E .. l*E+E-1, E = m/32 for the padded size m); partners closer than E
