@@ -23,6 +23,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "bits_device.cuh"
 #include "warp_sort.cuh"
 
 namespace picasso {
@@ -353,8 +354,6 @@ namespace {
 
 constexpr int kMaskThreads = 256;
 constexpr int kMaskWarps = kMaskThreads / 32;
-constexpr int kMaskPlain = 0, kMaskBits = 1;  // k_bucket_mask modes
-constexpr int kTabWords = 32 * 16;  // one warp's tables: 32 chunks x 16 entries
 constexpr int kEmitThreads = 256;
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -370,9 +369,6 @@ __host__ __device__ inline size_t mask_smem_bytes(int smax) {
 // warp's 32 rows hit 32 banks), then copies them to HBM row-major without
 // the padding: row r of block R at 16 R (R + 1) + r (R + 1).
 __host__ __device__ inline int rm_pad_off(int R) { return 32 * (R * (R + 1) / 2 + R / 2); }
-__host__ __device__ inline size_t bits_smem_bytes(int smax) {
-  return mask_smem_bytes(smax) + sizeof(uint32_t) * (size_t)rm_pad_off((smax + 31) >> 5);
-}
 
 // Asynchronous global -> shared copies (the next bucket's members).
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -385,73 +381,6 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// 32 x 32 bit transpose across the warp: on entry lane r holds row r (bit k =
-// M[r][k]); on exit lane k holds column k (bit r = M[r][k]).  Five butterfly
-// stages exchange ever smaller off-diagonal sub-blocks.
-__device__ __forceinline__ uint32_t transpose32(uint32_t w, int lane) {
-#pragma unroll
-  for (int j = 16; j > 0; j >>= 1) {
-    const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu : j == 2 ? 0x33333333u
-                                                                                                   : 0x55555555u;
-    const uint32_t t = __shfl_xor_sync(0xffffffffu, w, j);
-    w = (lane & j) ? ((w & ~m) | ((t >> j) & m)) : ((w & m) | ((t << j) & ~m));
-  }
-  return w;
-}
-
-__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr));
-  return v;
-}
-
-template <int QW>
-__device__ __forceinline__ uint32_t word_of(const uint4& w, int g) {
-  // table word order: x_lo, [x_hi], z_lo, [z_hi]
-  if (QW == 2) return g == 0 ? w.x : g == 1 ? w.y : g == 2 ? w.z : w.w;
-  return g == 0 ? w.x : w.z;
-}
-
-// Build this warp's tables for one row block from the block's bit columns.
-template <int QW>
-__device__ __forceinline__ void build_tables(const uint32_t* __restrict__ colw, uint32_t* __restrict__ tab, int lane) {
-  constexpr int NG = 2 * QW;
-  __syncwarp();  // the warp's lookups in the old tables are done
-  if (lane < 8 * NG) {
-    const int g = lane >> 3, qn = lane & 7;
-    const uint4 a = *reinterpret_cast<const uint4*>(colw + g * 32 + 4 * qn);
-    const uint32_t t3 = a.x ^ a.y, t5 = a.z ^ a.x, t6 = a.z ^ a.y, t7 = a.z ^ t3;
-    uint4* o = reinterpret_cast<uint4*>(tab + lane * 16);
-    o[0] = make_uint4(0u, a.x, a.y, t3);
-    o[1] = make_uint4(a.z, t5, t6, t7);
-    o[2] = make_uint4(a.w, a.w ^ a.x, a.w ^ a.y, a.w ^ t3);
-    o[3] = make_uint4(a.w ^ a.z, a.w ^ t5, a.w ^ t6, a.w ^ t7);
-  }
-  __syncwarp();
-}
-
-// Anticommutation bits of partner words `cw` against the 32 rows whose
-// tables start at shared address tab_addr (bit r = row r).
-template <int QW>
-__device__ __forceinline__ uint32_t lookup(const uint4& cw, uint32_t tab_addr) {
-  constexpr int NG = 2 * QW;
-  uint32_t acc = 0u;
-#pragma unroll
-  for (int g = 0; g < NG; ++g) {
-    // a row's x part meets the partner's z part and vice versa
-    const uint32_t idx = word_of<QW>(cw, (g + QW) % NG);
-    const uint32_t wl = (idx << 2) & 0x3C3C3C3Cu, wh = (idx >> 2) & 0x3C3C3C3Cu;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      // table base | (nibble * 4) in the low byte, chunk offset added
-      const uint32_t lo = lds32(__byte_perm(wl, tab_addr, 0x7650u + k) + (uint32_t)((g * 8 + 2 * k) * 64));
-      const uint32_t hi = lds32(__byte_perm(wh, tab_addr, 0x7650u + k) + (uint32_t)((g * 8 + 2 * k + 1) * 64));
-      acc ^= lo ^ hi;
-    }
-  }
-  return acc;
-}
 
 }  // namespace
 
@@ -497,15 +426,12 @@ __device__ __forceinline__ void emit_rows(const uint32_t* __restrict__ wbuf, con
   }
 }
 
-// MODE: kMaskPlain (members read through bmem and the strings; blocks and
-// counts to HBM, block-major) or kMaskBits (members gathered in slot order
-// and prefetched; the lower blocks, row-major, counts and each entry's row
-// address go to HBM: the bit layout).
-template <int QW, bool LOWER, int MODE>
+// The unfused mask pass: members read through bmem and the strings; blocks
+// (block-major) and per-entry counts to HBM, for the emit pass.
+template <int QW, bool LOWER>
 __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a, const int64_t* __restrict__ boff,
                                                               const int32_t* __restrict__ bmem,
                                                               const int64_t* __restrict__ moff, int smax) {
-  constexpr bool STAGED = MODE != kMaskPlain;     // gathered, prefetched members
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* p = smem_raw;
   uint4* w4 = (uint4*)p;
@@ -514,11 +440,6 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   p += align16(sizeof(int32_t) * smax);
   int32_t* cnt = (int32_t*)p;
   p += align16(sizeof(int32_t) * smax);
-  uint32_t* mwp = nullptr;
-  if (MODE == kMaskBits) {
-    mwp = (uint32_t*)p;
-    p += sizeof(uint32_t) * (size_t)rm_pad_off((smax + 31) >> 5);
-  }
   // 256-byte aligned region: bit columns, then per-warp tables (table bases
   // need a zero low byte)
   {
@@ -527,68 +448,17 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
   }
   uint32_t* colw = (uint32_t*)p;  // [nwb][2 QW][32]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-
-  // bit pass: a bucket's members (words and entry ids, gathered in slot
-  // order beforehand) are copied asynchronously into a staging area while
-  // the previous bucket's rows are written.  The staging area lies in the
-  // bit columns and tables, which only the mask phase uses: the copy starts
-  // after the mask phase and is moved into place before the next one.
-  static_assert(20 * kFusedMax <= kMaskWarps * kTabWords * 4, "staging must fit in the tables");
-  uint4* w4s = (uint4*)colw;
-  int32_t* sfls = (int32_t*)(w4s + smax);
-  auto fetch = [&](int64_t o, int s) {
-    for (int i = threadIdx.x; i < s; i += kMaskThreads) {
-      cp_async16(w4s + i, a.bxz + o + i);
-      cp_async4(sfls + i, bmem + o + i);
-    }
-    cp_async_commit();
-  };
-  int64_t o_nx = 0;
-  int s_nx = 0;
-  if (STAGED && blockIdx.x < a.P) {
-    o_nx = boff[blockIdx.x];
-    s_nx = (int)(boff[blockIdx.x + 1] - o_nx);
-    fetch(o_nx, s_nx);
-  }
   for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x) {
-    int64_t o;
-    int s;
-    int64_t o2 = 0;
-    int s2 = 0;
-    if (STAGED) {
-      const int64_t b2 = b + gridDim.x;
-      if (b2 < a.P) {
-        o2 = boff[b2];
-        s2 = (int)(boff[b2 + 1] - o2);
-      }
-      o = o_nx;
-      s = s_nx;
-      // the staging area holds this bucket (the last fetch went there)
-      cp_async_wait_all();
-      __syncthreads();
-      if (s == 0) {
-        fetch(o2, s2);
-        o_nx = o2;
-        s_nx = s2;
-        continue;
-      }
-      for (int i = threadIdx.x; i < s; i += kMaskThreads) {
-        w4[i] = w4s[i];
-        sfl[i] = sfls[i];
-        cnt[i] = 0;
-      }
-    } else {
-      o = boff[b];
-      s = (int)(boff[b + 1] - o);
-      if (s == 0) continue;
-      for (int i = threadIdx.x; i < s; i += kMaskThreads) {
-        const int32_t flat = bmem[o + i];
-        const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
-        const uint64_t x = a.xz[2 * v], z = a.xz[2 * v + 1];
-        w4[i] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
-        sfl[i] = flat;
-        cnt[i] = 0;
-      }
+    const int64_t o = boff[b];
+    const int s = (int)(boff[b + 1] - o);
+    if (s == 0) continue;
+    for (int i = threadIdx.x; i < s; i += kMaskThreads) {
+      const int32_t flat = bmem[o + i];
+      const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
+      const uint64_t x = a.xz[2 * v], z = a.xz[2 * v + 1];
+      w4[i] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
+      sfl[i] = flat;
+      cnt[i] = 0;
     }
     __syncthreads();
     const int nwb = (s + 31) >> 5;
@@ -604,7 +474,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
     __syncthreads();
 
     uint32_t* rmb = a.rmask + moff[b];
-    const int nblk = nwb * (nwb + 1) / 2;
+    const int nblk = nwb * (nwb + 1) / 2;  // blocks (I, J >= I)
     const int q0 = (int)((int64_t)nblk * wid / kMaskWarps), q1 = (int)((int64_t)nblk * (wid + 1) / kMaskWarps);
     int I = 0, J = 0;
     {
@@ -630,10 +500,7 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       uint32_t cw = jv ? (~anti & rows_ok) : 0u;
       // the diagonal block: no self pair; lower rows keep smaller partners
       if (I == J) cw &= LOWER ? ((1u << lane) - 1u) : ~(1u << lane);
-      if (MODE == kMaskBits)
-        mwp[rm_pad_off(J) + lane * ((J + 1) | 1) + I] = cw;
-      else
-        rmb[mask_block(LOWER, J, I, nwb) * 32 + lane] = cw;
+      rmb[mask_block(LOWER, J, I, nwb) * 32 + lane] = cw;
       if (cw) atomicAdd(&cnt[j], __popc(cw));
       if (!LOWER && I != J) {
         const uint32_t tr = transpose32(cw, lane);
@@ -646,42 +513,152 @@ __global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_mask(ConflictArgs a,
       }
     }
     __syncthreads();
-    // the next bucket's members go to the staging area (the bit columns and
-    // tables are done with) while this one's rows are written
-    if (STAGED) fetch(o2, s2);
-    if (MODE != kMaskBits) {
-      for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
-    } else {
-      // entry of member i: one word with the address of its row's first
-      // word (the row's R + 1 words are consecutive), i and its run length;
-      // the bucket's run total to *a.nnz
-      uint32_t tot = 0;
-      for (int i = threadIdx.x; i < s; i += kMaskThreads) {
-        const int R = i >> 5;
-        const int64_t w0 = moff[b] + 16 * R * (R + 1) + (i & 31) * (R + 1);
-        a.rinfo[sfl[i]] = rinfo_pack(w0, i, cnt[i]);
-        tot += (uint32_t)cnt[i];
+    for (int i = threadIdx.x; i < s; i += kMaskThreads) a.cnt[sfl[i]] = (uint32_t)cnt[i];
+    __syncthreads();
+  }
+}
+
+// The bit pass (the default build; EARLIER form, buckets of at most
+// kFusedMax members, strings of one word per part).  A CTA takes buckets
+// b, b + G, ...; a bucket's members (words and entry ids, gathered in slot
+// order beforehand) arrive by cp.async in one of two buffers while the CTA
+// works on the other.  Per bucket, three CTA barriers:
+//   1. (the bucket's members have landed; the previous bucket is done) warps
+//      make the bit columns of the row blocks (warp transposes);
+//   2. (columns done) every warp takes an even share of the lower blocks
+//      (I, J >= I), builds the nibble tables of each row block I it meets,
+//      and gets, by lookup, the word of row J*32 + lane against rows I*32 ..
+//      (commuting, smaller slot), stored row-major in shared memory (odd row
+//      strides), with the row's run length counted;
+//   3. (every row is complete) the next bucket's copy starts; each entry's
+//      packed word (row address, slot, run length), the bucket's run total,
+//      and the rows to HBM row-major.
+__host__ __device__ inline size_t bits2_smem_bytes(int smax) {
+  const int nwb = (smax + 31) >> 5;
+  return align16(sizeof(uint4) * 2 * smax) + align16(sizeof(int32_t) * 2 * smax) + align16(sizeof(int32_t) * smax) +
+         sizeof(uint32_t) * (size_t)rm_pad_off(nwb) + 256 +
+         sizeof(uint32_t) * ((size_t)kMaskWarps * kTabWords + (size_t)nwb * 128);
+}
+
+template <int QW>
+__global__ void __launch_bounds__(kMaskThreads, 4) k_bucket_bits(ConflictArgs a, const int64_t* __restrict__ boff,
+                                                              const int32_t* __restrict__ bmem,
+                                                              const int64_t* __restrict__ moff, int smax) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  uint8_t* p = smem_raw;
+  uint4* w4b = (uint4*)p;  // [2][smax]
+  p += align16(sizeof(uint4) * 2 * smax);
+  int32_t* sflb = (int32_t*)p;  // [2][smax]
+  p += align16(sizeof(int32_t) * 2 * smax);
+  int32_t* cnt = (int32_t*)p;  // [smax], zero between buckets
+  p += align16(sizeof(int32_t) * smax);
+  uint32_t* mwp = (uint32_t*)p;
+  p += sizeof(uint32_t) * (size_t)rm_pad_off((smax + 31) >> 5);
+  {
+    // table bases need a zero low byte
+    const uint32_t ad = (uint32_t)__cvta_generic_to_shared(p);
+    p += (256u - (ad & 255u)) & 255u;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* tab = (uint32_t*)p + wid * kTabWords;
+  const uint32_t tab_addr = (uint32_t)__cvta_generic_to_shared(tab);
+  uint32_t* colw = (uint32_t*)p + kMaskWarps * kTabWords;  // [nwb][2 QW][32] bit columns
+
+  for (int i = threadIdx.x; i < smax; i += kMaskThreads) cnt[i] = 0;
+  auto fetch = [&](int64_t b, int buf) {
+    if (b >= a.P) return;
+    const int64_t o = boff[b];
+    const int sn = (int)(boff[b + 1] - o);
+    for (int i = threadIdx.x; i < sn; i += kMaskThreads) {
+      cp_async16(w4b + buf * smax + i, a.bxz + o + i);
+      cp_async4(sflb + buf * smax + i, bmem + o + i);
+    }
+    cp_async_commit();
+  };
+  fetch(blockIdx.x, 0);
+  int buf = 0;
+  for (int64_t b = blockIdx.x; b < a.P; b += gridDim.x, buf ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t o = boff[b];
+    const int s = (int)(boff[b + 1] - o);
+    if (s == 0) {
+      fetch(b + gridDim.x, buf ^ 1);
+      continue;
+    }
+    const uint4* w4 = w4b + buf * smax;
+    const int32_t* sfl = sflb + buf * smax;
+    const int nwb = (s + 31) >> 5;
+    for (int I = wid; I < nwb; I += kMaskWarps) {
+      const int r = (I << 5) + lane;
+      const uint4 w = r < s ? w4[r] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int g = 0; g < 2 * QW; ++g) colw[(I * 2 * QW + g) * 32 + lane] = transpose32(word_of<QW>(w, g), lane);
+    }
+    __syncthreads();
+    const int nblk = nwb * (nwb + 1) / 2;
+    const int q0 = (int)((int64_t)nblk * wid / kMaskWarps), q1 = (int)((int64_t)nblk * (wid + 1) / kMaskWarps);
+    int I = 0, J = 0;
+    {
+      int rem = q0;
+      while (rem >= nwb - I) {
+        rem -= nwb - I;
+        ++I;
       }
-      tot = __reduce_add_sync(0xffffffffu, tot);
-      if (lane == 0 && tot) atomicAdd(a.nnz, (unsigned long long)tot);
-      // the rows to HBM, row-major: warp per row block, 32 words a step
-      for (int R = wid; R < nwb; R += kMaskWarps) {
-        const uint32_t d = (uint32_t)(R + 1), m = (65536u + d - 1u) / d, sp = d | 1u;
-        const uint32_t* src = mwp + rm_pad_off(R);
-        uint32_t* dst = rmb + 16 * R * (R + 1);
-        for (uint32_t o = lane; o < 32u * d; o += 32u) {
-          const uint32_t r = (o * m) >> 16, w = o - r * d;  // o = r d + w, exact for o < 4096 / d
-          dst[o] = src[r * sp + w];
-        }
+      J = I + rem;
+    }
+    int tab_I = -1;
+    for (int q = q0; q < q1; ++q) {
+      if (tab_I != I) {
+        build_tables<QW>(colw + I * 2 * QW * 32, tab, lane);
+        tab_I = I;
+      }
+      const int ib = I << 5;
+      const int j = (J << 5) + lane;
+      const bool jv = j < s;
+      const uint4 cwj = jv ? w4[j] : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t anti = lookup<QW>(cwj, tab_addr);
+      const uint32_t rows_ok = s - ib >= 32 ? 0xffffffffu : ((1u << (s - ib)) - 1u);
+      uint32_t cw = jv ? (~anti & rows_ok) : 0u;
+      // the diagonal block: no self pair, smaller partners only
+      if (I == J) cw &= (1u << lane) - 1u;
+      mwp[rm_pad_off(J) + lane * ((J + 1) | 1) + I] = cw;
+      if (cw) atomicAdd(&cnt[j], __popc(cw));
+      if (++J == nwb) {
+        ++I;
+        J = I;
       }
     }
     __syncthreads();
-    if (STAGED) {
-      o_nx = o2;
-      s_nx = s2;
+    // the next bucket's copy (the lookups, which share the shared-memory
+    // pipe with it, are done)
+    fetch(b + gridDim.x, buf ^ 1);
+    // entry of member i: its row's first word, i and its run length; the
+    // bucket's run total to *a.nnz
+    uint32_t tot = 0;
+    for (int i = threadIdx.x; i < s; i += kMaskThreads) {
+      const int R = i >> 5;
+      const int64_t w0 = moff[b] + 16 * R * (R + 1) + (i & 31) * (R + 1);
+      const int ci = cnt[i];
+      a.rinfo[sfl[i]] = rinfo_pack(w0, i, ci);
+      cnt[i] = 0;
+      tot += (uint32_t)ci;
+    }
+    tot = __reduce_add_sync(0xffffffffu, tot);
+    if (lane == 0 && tot) atomicAdd(a.nnz, (unsigned long long)tot);
+    // the rows to HBM, row-major: warp per row block, 32 words a step
+    uint32_t* rmb = a.rmask + moff[b];
+    for (int R = wid; R < nwb; R += kMaskWarps) {
+      const uint32_t d = (uint32_t)(R + 1), m = (65536u + d - 1u) / d, sp = d | 1u;
+      const uint32_t* src = mwp + rm_pad_off(R);
+      uint32_t* dst = rmb + 16 * R * (R + 1);
+      for (uint32_t o2 = lane; o2 < 32u * d; o2 += 32u) {
+        const uint32_t r = (o2 * m) >> 16, w = o2 - r * d;  // o2 = r d + w (exact for o2 < 32 d, d <= 16)
+        dst[o2] = src[r * sp + w];
+      }
     }
   }
-  if (STAGED) cp_async_wait_all();
+  cp_async_wait_all();
 }
 
 // Mask pass for strings of more than one word per part (q > 64): the
@@ -923,8 +900,8 @@ cudaError_t launch_bucket_bits(const ConflictArgs& a, const int64_t* boff, const
   if (a.P <= 0 || a.n <= 0) return cudaSuccess;
   if (smax > kFusedMax || !a.lower || a.qw != 1) return cudaErrorInvalidValue;
   smax = max(smax, 1);
-  const size_t bytes = bits_smem_bytes(smax);
-  auto kern = q <= 32 ? k_bucket_mask<1, true, kMaskBits> : k_bucket_mask<2, true, kMaskBits>;
+  const size_t bytes = bits2_smem_bytes(smax);
+  auto kern = q <= 32 ? k_bucket_bits<1> : k_bucket_bits<2>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -954,8 +931,8 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
     return cudaErrorInvalidValue;
   }
   const size_t bytes = mask_smem_bytes(smax);
-  auto kern = q <= 32 ? (a.lower ? k_bucket_mask<1, true, kMaskPlain> : k_bucket_mask<1, false, kMaskPlain>)
-                      : (a.lower ? k_bucket_mask<2, true, kMaskPlain> : k_bucket_mask<2, false, kMaskPlain>);
+  auto kern = q <= 32 ? (a.lower ? k_bucket_mask<1, true> : k_bucket_mask<1, false>)
+                      : (a.lower ? k_bucket_mask<2, true> : k_bucket_mask<2, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

@@ -32,6 +32,7 @@
 
 #include <algorithm>
 
+#include "bits_device.cuh"
 #include "color_device.cuh"
 #include "common.cuh"
 #include "warp_sort.cuh"
@@ -45,9 +46,12 @@ constexpr int kSmallThreads = 256;
 constexpr int kSmallWarps = kSmallThreads / 32;
 constexpr int kSmallBlocksPerSm = 2;
 // dynamic shared memory of one warp: a bucket's member words (W words per
-// part) and ranks
+// part) and run lengths; for W = 1 also a block's bit columns and nibble
+// tables (with room to align the tables to 256 bytes)
 template <int W>
-__host__ __device__ constexpr int warp_smem_bytes() { return kSmallBucketCap * (16 * W + 4); }
+__host__ __device__ constexpr int warp_smem_bytes() {
+  return W == 1 ? kSmallBucketCap * 20 + 128 * 4 + 256 + kTabWords * 4 : kSmallBucketCap * (16 * W + 4);
+}
 
 // Sum of x over the block (every thread gets it).  sm: 32 words.
 __device__ __forceinline__ int64_t block_sum(int64_t x, int64_t* sm) {
@@ -342,6 +346,79 @@ __device__ void bucket_bits(const SmallArgs& a, int32_t* R, uint64_t* X, int lan
   __syncwarp();
 }
 
+// W = 1: the same rows by nibble tables (bits_device.cuh).  A warp's items
+// in one bucket are the row blocks r0 .. r1; for every column block
+// Wb <= r1 it builds the tables of members 32 Wb .. 32 Wb + 31 once and looks
+// up each of its rows Rb >= max(Wb, r0) in them: word Wb of row i holds i's
+// commutation bits against those members (on the diagonal block, the
+// smaller slots only).  wsm: the warp's shared memory (warp_smem_bytes<1>).
+__device__ void bucket_bits_tab(const SmallArgs& a, unsigned char* wsm, int lane, int64_t gwarp, int64_t nwarps) {
+  uint4* X = reinterpret_cast<uint4*>(wsm);                              // member words x_lo, x_hi, z_lo, z_hi
+  int32_t* cnt = reinterpret_cast<int32_t*>(X + kSmallBucketCap);        // run lengths
+  uint32_t* colw = reinterpret_cast<uint32_t*>(cnt + kSmallBucketCap);   // [4][32] bit columns
+  uint32_t* tab;
+  {
+    unsigned char* p = reinterpret_cast<unsigned char*>(colw + 128);
+    const uint32_t ad = (uint32_t)__cvta_generic_to_shared(p);
+    tab = reinterpret_cast<uint32_t*>(p + ((256u - (ad & 255u)) & 255u));
+  }
+  const uint32_t tab_addr = (uint32_t)__cvta_generic_to_shared(tab);
+  const int64_t nitems = __ldcg(a.ctl + 8);
+  const int64_t per = (nitems + nwarps - 1) / nwarps;
+  const int64_t it0 = min(nitems, gwarp * per), it1 = min(nitems, it0 + per);
+  for (int64_t it = it0; it < it1;) {
+    const int64_t c = a.ibkt[it];
+    const int64_t b0 = a.boff[c], ib0 = a.iboff[c];
+    const int s = (int)(a.boff[c + 1] - b0);
+    const int r0 = (int)(it - ib0);
+    const int r1 = (int)(min(a.iboff[c + 1], it1) - ib0) - 1;
+    const int need = min(s, 32 * (r1 + 1));
+    __syncwarp();
+    for (int i = lane; i < need; i += 32) X[i] = reinterpret_cast<const uint4*>(a.bxz)[b0 + i];
+    for (int i = 32 * r0 + lane; i < 32 * (r1 + 1); i += 32) cnt[i] = 0;
+    __syncwarp();
+    const int64_t m0 = a.moff[c];
+    for (int Wb = 0; Wb <= r1; ++Wb) {
+      const int jm = 32 * Wb + lane;
+      const uint4 wj = jm < s ? X[jm] : make_uint4(0u, 0u, 0u, 0u);
+      __syncwarp();  // the warp is done with the previous block's columns
+      colw[lane] = transpose32(wj.x, lane);
+      colw[32 + lane] = transpose32(wj.y, lane);
+      colw[64 + lane] = transpose32(wj.z, lane);
+      colw[96 + lane] = transpose32(wj.w, lane);
+      build_tables<2>(colw, tab, lane);
+      for (int Rb = max(Wb, r0); Rb <= r1; ++Rb) {
+        const int i = 32 * Rb + lane;
+        const uint4 wi = X[min(i, s - 1)];
+        uint32_t word = ~lookup<2>(wi, tab_addr);
+        if (Rb == Wb) word &= (1u << lane) - 1u;
+        if (i < s) {
+          a.rmask[m0 + 16 * (int64_t)Rb * (Rb + 1) + (int64_t)lane * (Rb + 1) + Wb] = word;
+          cnt[i] += __popc(word);
+        }
+      }
+    }
+    __syncwarp();
+    uint32_t tot = 0;
+    for (int Rb = r0; Rb <= r1; ++Rb) {
+      const int i = 32 * Rb + lane;
+      if (i < s) {
+        const int64_t addr = m0 + 16 * (int64_t)Rb * (Rb + 1) + (int64_t)lane * (Rb + 1);
+        a.rinfo[a.bmem[b0 + i]] = rinfo_pack(addr, i, cnt[i]);
+        tot += (uint32_t)cnt[i];
+      }
+    }
+    const uint32_t wsum = __reduce_add_sync(0xffffffffu, tot);
+    if (lane == 0 && wsum) {
+      const int set = a.nsets > 1 ? find_set(a.scof, a.nsets, c) : 0;
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.snnz + set), (unsigned long long)wsum);
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.ctl + 3), (unsigned long long)wsum);
+    }
+    it = ib0 + r1 + 1;
+  }
+  __syncwarp();
+}
+
 // The round's priority keys (priority, global id) in V_l order (gid), the
 // buckets and color masks emptied (P bucket colors), the round's counters
 // zeroed: what a stage does before its first round (later rounds find it
@@ -493,7 +570,10 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     }
     if (!engine_sync<MODE>(a, __LINE__, round)) return;
 
-    bucket_bits<W>(a, Rw, Xw, lane, gwarp, nwarps);
+    if constexpr (W == 1)
+      bucket_bits_tab(a, smem_dyn + (size_t)wid * warp_smem_bytes<W>(), lane, gwarp, nwarps);
+    else
+      bucket_bits<W>(a, Rw, Xw, lane, gwarp, nwarps);
     if (!engine_sync<MODE>(a, __LINE__, round)) return;
     {
       // the round's CSR, counted as the byte budget counts it (8 bytes per
