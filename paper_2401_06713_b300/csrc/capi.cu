@@ -669,6 +669,7 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
   if (algo == PICASSO_CONFLICT_BUCKET) {
     TRYC(launch_scan_u32(bcount, P, boff, tmp, s));
     TRY(alloc(c, &bmem, E));
+    const bool placed = hist != nullptr;  // members in entry order across the ranges
     if (hist) {
       TRYC(launch_bucket_place(c->lists, E, P, hist, hist_g, boff, bmem, s));
       release(c, &hist);
@@ -688,9 +689,9 @@ int build_conflicts(Ctx* c, bool chunk_ok) {
       // sorted buckets, and the members' words and vertex ids in slot order
       TRY(alloc(c, &bxz, E));
       TRY(alloc(c, &bpid, E));
-      TRYC(launch_bucket_sort_gather(boff, P, bmem, (int32_t)smax, a, bxz, bpid, s));
+      TRYC(launch_bucket_sort_gather(boff, P, bmem, (int32_t)smax, placed, a, bxz, bpid, s));
     } else {
-      TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, (int32_t)smax, s));
+      TRYC(launch_bucket_sort(boff, P, bmem, c->d_err, (int32_t)smax, placed, s));
     }
     if (bitl) {
       // the bit pass: every bucket's lower blocks of pair bits, no run

@@ -354,7 +354,9 @@ cudaError_t launch_bucket_place(const int32_t* lists, int64_t E, int64_t P, cons
                                 const int64_t* boff, int32_t* bmem, cudaStream_t s);
 cudaError_t launch_bucket_fill(const int32_t* lists, int64_t E, const int64_t* boff, uint32_t* bcursor,
                                int32_t* bmem, cudaStream_t s);
-cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, int32_t smax,
+// near: every member lies within a few places of its own (the place pass):
+// odd-even transposition passes instead of the full network.
+cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, int32_t smax, bool near,
                                cudaStream_t s);
 // out32[0] = max bucket size; out64[0] = sum over buckets of s (s - 1).
 cudaError_t launch_bucket_stats(const uint32_t* bcount, int64_t P, uint32_t* out32,
@@ -379,7 +381,7 @@ cudaError_t launch_bucket_bits(const ConflictArgs& a, const int64_t* boff, const
 // bxz[p], bpid[p]: words and vertex id of the member at bucket slot p < E.
 // The warp sort of every bucket (all of at most 512 members) and, by the
 // same warp, the gather of launch_bucket_gather (bit pass).
-cudaError_t launch_bucket_sort_gather(const int64_t* boff, int64_t P, int32_t* bmem, int32_t smax,
+cudaError_t launch_bucket_sort_gather(const int64_t* boff, int64_t P, int32_t* bmem, int32_t smax, bool near,
                                       const ConflictArgs& a, uint4* bxz, int32_t* bpid, cudaStream_t s);
 cudaError_t launch_bucket_gather(const ConflictArgs& a, const int32_t* bmem, uint4* bxz, int32_t* bpid,
                                  cudaStream_t s);

@@ -70,8 +70,9 @@ __global__ void k_prio_bin_sort(const uint32_t* __restrict__ prio, const int64_t
 }
 
 int prio_bins_for(int64_t n) {
+  // about one vertex a bin: the insertion sorts stay a few elements long
   int bins = 2;
-  while (bins < n && bins < 65536) bins <<= 1;
+  while (bins < n && bins < (1 << 20)) bins <<= 1;
   return bins;
 }
 

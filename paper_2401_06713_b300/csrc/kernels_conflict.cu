@@ -186,7 +186,8 @@ cudaError_t launch_bucket_place(const int32_t* lists, int64_t E, int64_t P, cons
 template <bool GATHER>
 __global__ void __launch_bounds__(256, 4) k_bucket_sort_warp(const int64_t* __restrict__ boff, int64_t P,
                                                           int32_t* __restrict__ bmem, ConflictArgs a,
-                                                          uint4* __restrict__ bxz, int32_t* __restrict__ bpid) {
+                                                          uint4* __restrict__ bxz, int32_t* __restrict__ bpid,
+                                                          int near) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < P; b += gw) {
@@ -198,7 +199,16 @@ __global__ void __launch_bounds__(256, 4) k_bucket_sort_warp(const int64_t* __re
       ;
     else if (s <= 32)
       warp_sort_bucket<1>(p, s, lane);
-    else if (s <= 64)
+    else if (near) {
+      if (s <= 64)
+        warp_fix_bucket<2>(p, s, lane);
+      else if (s <= 128)
+        warp_fix_bucket<4>(p, s, lane);
+      else if (s <= 256)
+        warp_fix_bucket<8>(p, s, lane);
+      else
+        warp_fix_bucket<16>(p, s, lane);
+    } else if (s <= 64)
       warp_sort_bucket<2>(p, s, lane);
     else if (s <= 128)
       warp_sort_bucket<4>(p, s, lane);
@@ -273,11 +283,11 @@ __global__ void __launch_bounds__(512) k_bucket_sort(const int64_t* __restrict__
   }
 }
 
-cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, int32_t smax,
+cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, int32_t* err, int32_t smax, bool near,
                                cudaStream_t s) {
   if (P <= 0) return cudaSuccess;
   const unsigned wblocks = (unsigned)std::min<int64_t>((P + 7) / 8, 148 * 16);
-  k_bucket_sort_warp<false><<<wblocks, 256, 0, s>>>(boff, P, bmem, ConflictArgs{}, nullptr, nullptr);
+  k_bucket_sort_warp<false><<<wblocks, 256, 0, s>>>(boff, P, bmem, ConflictArgs{}, nullptr, nullptr, near ? 1 : 0);
   count_launches(1);
   if (smax > kWarpSortMax) {
     const unsigned blocks = (unsigned)std::min<int64_t>(P, 148 * 8);
@@ -287,14 +297,14 @@ cudaError_t launch_bucket_sort(const int64_t* boff, int64_t P, int32_t* bmem, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_sort_gather(const int64_t* boff, int64_t P, int32_t* bmem, int32_t smax,
+cudaError_t launch_bucket_sort_gather(const int64_t* boff, int64_t P, int32_t* bmem, int32_t smax, bool near,
                                       const ConflictArgs& a, uint4* bxz, int32_t* bpid, cudaStream_t s) {
   if (P <= 0) return cudaSuccess;
   if (smax > kWarpSortMax) return cudaErrorInvalidValue;
   // a member's words are read 16 bytes at a time
   if (reinterpret_cast<uintptr_t>(a.xz) & 15) return cudaErrorMisalignedAddress;
   const unsigned wblocks = (unsigned)std::min<int64_t>((P + 7) / 8, 148 * 16);
-  k_bucket_sort_warp<true><<<wblocks, 256, 0, s>>>(boff, P, bmem, a, bxz, bpid);
+  k_bucket_sort_warp<true><<<wblocks, 256, 0, s>>>(boff, P, bmem, a, bxz, bpid, near ? 1 : 0);
   count_launches(1);
   return cudaGetLastError();
 }

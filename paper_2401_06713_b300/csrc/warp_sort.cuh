@@ -63,6 +63,54 @@ __device__ __forceinline__ void warp_sort_bucket(int32_t* __restrict__ p, int s,
   }
 }
 
+// The same for a nearly sorted p (E >= 2): odd-even transposition passes
+// (pairs (2i, 2i+1), then (2i+1, 2i+2); the pair across two lanes by
+// shuffles) until no pair is out of order.  Each pass pair moves an element
+// at least one step towards its place, so a sequence whose elements sit
+// within a few places of their own is sorted in a few passes; after
+// kFixPasses pass pairs the bitonic network finishes whatever is left.
+constexpr int kFixPasses = 12;
+template <int E>
+__device__ __forceinline__ void warp_fix_bucket(int32_t* __restrict__ p, int s, int lane) {
+  static_assert(E >= 2 && (E & 1) == 0, "pairs (2i, 2i+1) must lie in one lane");
+  int32_t key[E];
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int i = lane * E + j;
+    key[j] = i < s ? p[i] : 0x7fffffff;
+  }
+  bool done = false;
+  for (int it = 0; it < kFixPasses && !done; ++it) {
+#pragma unroll
+    for (int j = 0; j + 1 < E; j += 2) {
+      const int32_t x = key[j], y = key[j + 1];
+      key[j] = min(x, y);
+      key[j + 1] = max(x, y);
+    }
+#pragma unroll
+    for (int j = 1; j + 1 < E; j += 2) {
+      const int32_t x = key[j], y = key[j + 1];
+      key[j] = min(x, y);
+      key[j + 1] = max(x, y);
+    }
+    const int32_t nxt = __shfl_down_sync(0xffffffffu, key[0], 1);
+    const int32_t prv = __shfl_up_sync(0xffffffffu, key[E - 1], 1);
+    if (lane < 31) key[E - 1] = min(key[E - 1], nxt);
+    if (lane > 0) key[0] = max(key[0], prv);
+    const int32_t nxt2 = __shfl_down_sync(0xffffffffu, key[0], 1);
+    bool ok = lane == 31 || key[E - 1] <= nxt2;
+#pragma unroll
+    for (int j = 0; j + 1 < E; ++j) ok &= key[j] <= key[j + 1];
+    done = __all_sync(0xffffffffu, ok);
+  }
+  if (!done) warp_bitonic<E>(key, lane);
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int i = lane * E + j;
+    if (i < s) p[i] = key[j];
+  }
+}
+
 // Sort p[0..s) in place, s <= 512, by the warp; dispatches on the smallest
 // power-of-two E with 32 E >= s.
 __device__ __forceinline__ void warp_sort_any(int32_t* __restrict__ p, int s, int lane) {
