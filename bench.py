@@ -358,7 +358,7 @@ def run_gpu(args):
     peak_pairs = n_sm * sm_mhz * 1e6 * 16
     achieved = pairs_launch / (avg_ms / 1e3) if avg_ms > 0 else None
     bytes_launch = st["emit_bytes"] / max(st["emit_launches"], 1)
-    roofline = {"bound": "alu", "kernel": "k_bucket_mask<bits> (pair tests; G_c as bucket bit blocks)",
+    roofline = {"bound": "alu", "kernel": "k_bucket_bits (pair tests; G_c as bucket bit blocks)",
                 "achieved": achieved / 1e9 if achieved else None, "peak": peak_pairs / 1e9,
                 "unit": "Gpair-tests/s", "frac": achieved / peak_pairs if achieved else None,
                 "peak_source": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median under load) x 16 POPC/clk/SM",
@@ -367,7 +367,7 @@ def run_gpu(args):
                 "avg_launch_ms": avg_ms, "tested_pairs_per_launch": pairs_launch,
                 "launches_per_step": st["pairs_launches"]}
     gbs = bytes_launch / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
-    roofline_hbm = {"bound": "hbm", "kernel": "k_bucket_mask<bits>", "achieved": gbs,
+    roofline_hbm = {"bound": "hbm", "kernel": "k_bucket_bits", "achieved": gbs,
                     "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                     "frac": gbs / peaks["hbm_gbs"] if gbs and peaks.get("hbm_gbs") else None,
                     "algorithmic_bytes_per_launch": bytes_launch}

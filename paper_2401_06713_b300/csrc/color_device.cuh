@@ -234,8 +234,20 @@ __device__ __forceinline__ void mask_resolve(const ColorArgs& a, int64_t row, in
   }
 }
 
+// Lane's list entry of v (color and packed word), or 0 past the list: the
+// first loads of mask_vertex, which a caller may issue ahead of time.
 template <bool FRESH>
-__device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err) {
+__device__ __forceinline__ void mask_entry(const ColorArgs& a, int32_t v, int lane, uint32_t* c, int64_t* rb) {
+  const int64_t row = a.Lu ? (int64_t)v * a.Lu : ld_run<FRESH>(a.loff + v);
+  const int L = a.Lu ? a.Lu : (int)(ld_run<FRESH>(a.loff + v + 1) - row);
+  *c = lane < L ? (uint32_t)ld_run<FRESH>(a.lists + row + lane) : 0u;
+  *rb = lane < L ? ld_run<FRESH>(a.rinfo + row + lane) : 0;
+}
+
+// pre: c0 / rb0 hold mask_entry(v) (entries 0 .. 31 need no load).
+template <bool FRESH>
+__device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int lane, int32_t* err, bool pre = false,
+                                            uint32_t c0 = 0u, int64_t rb0 = 0) {
   // lists of one length (a single set): the row is known without a load
   const int64_t row = a.Lu ? (int64_t)v * a.Lu : ld_run<FRESH>(a.loff + v);
   const int L = a.Lu ? a.Lu : (int)(ld_run<FRESH>(a.loff + v + 1) - row);
@@ -245,7 +257,10 @@ __device__ __forceinline__ bool mask_vertex(const ColorArgs& a, int32_t v, int l
     const int kl = kb + lane;
     uint32_t my_c = 0u;
     int64_t my_rb = 0;
-    if (kl < L) {
+    if (pre && kb == 0) {
+      my_c = c0;
+      my_rb = rb0;
+    } else if (kl < L) {
       my_c = (uint32_t)ld_run<FRESH>(a.lists + row + kl);
       my_rb = ld_run<FRESH>(a.rinfo + row + kl);
     }

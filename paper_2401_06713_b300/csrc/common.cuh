@@ -553,7 +553,7 @@ struct SmallArgs {
   int32_t* brank;         // [E0]   rank,
   uint64_t* bxz;          // [2 E0] words
   int64_t* part;          // [3 gridDim.x] block sums of the launch's scans
-  int32_t* err;           // [4]: 0 ordered-pass poll timeout, 1 work counter, 2 bucket over the cap,
+  int32_t* err;           // [4]: 0 ordered-pass poll timeout, 1 unused, 2 bucket over the cap,
                           //      3 a grid barrier timed out (the launch ended; ctl[9] its site,
                           //      ctl[10] its round, ctl[11] the arrivals it saw)
   int64_t* ctl;           // [kSmallCtlWords]: 0 n, 1 rounds done, 2 stop reason, 4 V_l in gid_b (0..4

@@ -436,10 +436,7 @@ __device__ void round_init(const SmallArgs& a, const int32_t* gid, int64_t n, in
   }
   for (int64_t t = gtid; t < 32 * P; t += gthreads) a.cmask[t] = 0u;
   for (int64_t k = gtid; k < a.nsets; k += gthreads) a.snnz[k] = 0;
-  if (gtid == 0) {
-    a.ctl[3] = 0;
-    a.err[1] = 0;
-  }
+  if (gtid == 0) a.ctl[3] = 0;
 }
 
 template <int W, int MODE>
@@ -588,7 +585,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
     }
     if (gtid == 0) a.ctl[6] += __ldcg(a.ctl + 3);
 
-    // ordered first fit in rank order; warps take ranks from a counter
+    // ordered first fit in rank order
     {
       ColorArgs ca{};
       ca.n = n;
@@ -601,13 +598,17 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       ca.cmask = a.cmask;
       ca.Lu = nsets == 1 ? a.ptab[n].y : 0;  // one set: row of rank r = r L
       ca.max_polls = a.max_polls;
-      bool ok = true;
-      while (ok) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(a.err + 1, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if ((int64_t)t >= n || __ldcg(a.err) != 0) break;
-        ok = mask_vertex<true>(ca, t, lane, a.err);
+      // warp w takes ranks w, w + W, ... (every warp of the launch is
+      // resident, so the earliest undecided rank always progresses); the
+      // next rank's list entries are loaded while this one is colored
+      uint32_t nc = 0u;
+      int64_t nrb = 0;
+      if (gwarp < n) mask_entry<true>(ca, (int32_t)gwarp, lane, &nc, &nrb);
+      for (int64_t t = gwarp; t < n; t += nwarps) {
+        const uint32_t c0 = nc;
+        const int64_t rb0 = nrb;
+        if (t + nwarps < n) mask_entry<true>(ca, (int32_t)(t + nwarps), lane, &nc, &nrb);
+        if (__ldcg(a.err) != 0 || !mask_vertex<true>(ca, (int32_t)t, lane, a.err, true, c0, rb0)) break;
       }
     }
     if (!engine_sync<MODE>(a, __LINE__, round)) return;
@@ -626,10 +627,7 @@ __global__ void __launch_bounds__(kSmallThreads, kSmallBlocksPerSm) k_small_roun
       a.bcur[c] = 0;
     }
     for (int64_t t = gtid; t < 32 * P; t += gthreads) a.cmask[t] = 0u;
-    if (gtid == 0) {
-      a.ctl[3] = 0;
-      a.err[1] = 0;
-    }
+    if (gtid == 0) a.ctl[3] = 0;
     {
       auto get = [&](int64_t i, bool first, int64_t* y) {
         const int64_t r = __ldcg(a.pos + i);
