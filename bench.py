@@ -31,11 +31,11 @@ sys.path.insert(0, ROOT)
 
 N_DEFAULT, Q, P_W, NUM, DEN, ALPHA = 1_000_000, 64, 0.25, 1, 16, 1.5
 # DRAM bytes (read + write) per algorithmic byte of the bit pass
-# (k_bucket_mask<.., bits>: every color bucket's pair tests, its lower blocks of
-# pair bits to HBM), from one ncu capture of round 1 of the n = 200,000 case of
-# this workload (the bench's launches are too large to capture): 183.6 MB of
+# (k_bucket_bits: every color bucket's pair tests, its lower blocks of pair
+# bits to HBM), from one ncu capture of round 1 of the n = 200,000 case of
+# this workload (the bench's launches are too large to capture): 182.0 MB of
 # DRAM reads and writes for 194.4 MB of algorithmic bytes.
-BITS_DRAM_PER_ALG_BYTE = 0.944
+BITS_DRAM_PER_ALG_BYTE = 0.936
 METRIC = "pair tests/s (conflict build) and colored strings/s at n=1M; colors, peak bytes"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
