@@ -380,11 +380,9 @@ cudaError_t launch_bucket_bits(const ConflictArgs& a, const int64_t* boff, const
                                int32_t smax, int32_t q, cudaStream_t s, int per_sm_cap = 0);
 // bxz[p], bpid[p]: words and vertex id of the member at bucket slot p < E.
 // The warp sort of every bucket (all of at most 512 members) and, by the
-// same warp, the gather of launch_bucket_gather (bit pass).
+// same warp, the members' words and vertex ids in slot order (bit pass).
 cudaError_t launch_bucket_sort_gather(const int64_t* boff, int64_t P, int32_t* bmem, int32_t smax, bool near,
                                       const ConflictArgs& a, uint4* bxz, int32_t* bpid, cudaStream_t s);
-cudaError_t launch_bucket_gather(const ConflictArgs& a, const int32_t* bmem, uint4* bxz, int32_t* bpid,
-                                 cudaStream_t s);
 cudaError_t launch_bucket_jblocks(const uint32_t* bcount, int64_t P, uint32_t* out, cudaStream_t s);
 // jboff [P+1]: prefix of ceil(s_c / 32); counter: one device int32 (reset here)
 // Rows of vertices in [lo, hi) only (a chunk of the round), written at

@@ -182,7 +182,7 @@ cudaError_t launch_bucket_place(const int32_t* lists, int64_t E, int64_t P, cons
 // buckets: one CTA per bucket, the same network in shared memory.
 // GATHER (the bit pass, buckets of at most kWarpSortMax members): the
 // same warp then writes the sorted members' words and vertex ids in slot
-// order (bxz, bpid), as k_bucket_gather would.
+// order (bxz, bpid).
 template <bool GATHER>
 __global__ void __launch_bounds__(256, 4) k_bucket_sort_warp(const int64_t* __restrict__ boff, int64_t P,
                                                           int32_t* __restrict__ bmem, ConflictArgs a,
@@ -956,26 +956,6 @@ cudaError_t launch_bucket_mask(const ConflictArgs& a, const int64_t* boff, const
   count_launches(1);
   return cudaGetLastError();
 }
-
-__global__ void k_bucket_gather(ConflictArgs a, const int32_t* __restrict__ bmem, uint4* __restrict__ bxz,
-                                int32_t* __restrict__ bpid) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.E) return;
-  const int32_t flat = bmem[p];
-  const int64_t v = a.Lu ? flat / a.Lu : a.ent_v[flat];
-  const uint64_t x = a.xz[2 * v], z = a.xz[2 * v + 1];
-  bxz[p] = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)z, (uint32_t)(z >> 32));
-  bpid[p] = (int32_t)v;
-}
-
-cudaError_t launch_bucket_gather(const ConflictArgs& a, const int32_t* bmem, uint4* bxz, int32_t* bpid,
-                                 cudaStream_t s) {
-  if (a.E <= 0) return cudaSuccess;
-  k_bucket_gather<<<(unsigned)((a.E + 255) / 256), 256, 0, s>>>(a, bmem, bxz, bpid);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
 
 // Mask words of bucket c: nwb x nwb blocks of 32 words (nwb (nwb + 1) / 2
 // with lower), nwb = ceil(s_c / 32).
