@@ -100,22 +100,38 @@ __global__ void __launch_bounds__(kHistThreads) k_bucket_count(const int32_t* __
   for (int64_t i = threadIdx.x; i < hw; i += blockDim.x) out[i] = h2[i];
 }
 
-__global__ void k_bucket_colsum(uint16_t* __restrict__ hist, int64_t P, int64_t G, uint32_t* __restrict__ bcount) {
+// Block of 256 threads: 32 colors x 8 parts of the ranges (warp w takes
+// part w of the ranges for the block's 32 colors, so its loads are
+// coalesced); each part's sum goes to shared memory, then every part writes
+// its ranges' prefixes from the sum of the parts before it.
+constexpr int kColsumParts = 8;
+__global__ void __launch_bounds__(256) k_bucket_colsum(uint16_t* __restrict__ hist, int64_t P, int64_t G,
+                                                       uint32_t* __restrict__ bcount) {
+  __shared__ uint32_t part_sum[kColsumParts][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t stride = 2 * ((P + 1) / 2);
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < P; c += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t run = 0;
-    // 16 ranges at a time: their loads are in flight together
-    for (int64_t b0 = 0; b0 < G; b0 += 16) {
-      uint32_t x[16];
+  const int64_t c = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t b0 = G * w / kColsumParts, b1 = G * (w + 1) / kColsumParts;
+  uint32_t sum = 0;
+  if (c < P)
+    for (int64_t b = b0; b < b1; ++b) sum += __ldcg(hist + b * stride + c);
+  part_sum[w][lane] = sum;
+  __syncthreads();
+  uint32_t run = 0;
+  for (int k = 0; k < w; ++k) run += part_sum[k][lane];
+  if (c < P) {
+    // 8 ranges at a time: their loads are in flight together
+    for (int64_t bb = b0; bb < b1; bb += 8) {
+      uint32_t x[8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) x[u] = b0 + u < G ? (uint32_t)__ldcg(hist + (b0 + u) * stride + c) : 0u;
+      for (int u = 0; u < 8; ++u) x[u] = bb + u < b1 ? (uint32_t)__ldcg(hist + (bb + u) * stride + c) : 0u;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        if (b0 + u < G) hist[(b0 + u) * stride + c] = (uint16_t)run;  // exact while a bucket has <= 65,535 members
+      for (int u = 0; u < 8; ++u) {
+        if (bb + u < b1) hist[(bb + u) * stride + c] = (uint16_t)run;  // exact while a bucket has <= 65,535 members
         run += x[u];
       }
     }
-    bcount[c] = run;
+    if (w == kColsumParts - 1) bcount[c] = run;
   }
 }
 
@@ -156,7 +172,7 @@ cudaError_t launch_bucket_count(const int32_t* lists, int64_t E, int64_t P, uint
   cudaError_t e = cudaFuncSetAttribute(k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_bucket_count<<<(unsigned)G, kHistThreads, smem, s>>>(lists, E, P, hist);
-  k_bucket_colsum<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(hist, P, G, bcount);
+  k_bucket_colsum<<<(unsigned)((P + 31) / 32), 256, 0, s>>>(hist, P, G, bcount);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -188,44 +204,54 @@ __global__ void __launch_bounds__(256, 4) k_bucket_sort_warp(const int64_t* __re
                                                           int32_t* __restrict__ bmem, ConflictArgs a,
                                                           uint4* __restrict__ bxz, int32_t* __restrict__ bpid,
                                                           int near) {
+  // the warp's bucket in shared memory (one pad word every 16), so that the
+  // global reads and writes are coalesced and the lanes' runs of E
+  // consecutive elements are read without bank conflicts
+  __shared__ int32_t sbuf[8][kWarpSortMax + kWarpSortMax / 16];
   const int lane = threadIdx.x & 31;
+  int32_t* sp = sbuf[(threadIdx.x >> 5) & 7];
   const int64_t gw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < P; b += gw) {
     const int64_t o = boff[b];
     const int s = (int)(boff[b + 1] - o);
     if (s > kWarpSortMax) continue;
     int32_t* p = bmem + o;
+    __syncwarp();
+    for (int i = lane; i < s; i += 32) sp[sort_at<true>(i)] = p[i];
+    __syncwarp();
     if (s <= 1)
       ;
     else if (s <= 32)
-      warp_sort_bucket<1>(p, s, lane);
+      warp_sort_bucket<1, true>(sp, s, lane);
     else if (near) {
       if (s <= 64)
-        warp_fix_bucket<2>(p, s, lane);
+        warp_fix_bucket<2, true>(sp, s, lane);
       else if (s <= 128)
-        warp_fix_bucket<4>(p, s, lane);
+        warp_fix_bucket<4, true>(sp, s, lane);
       else if (s <= 256)
-        warp_fix_bucket<8>(p, s, lane);
+        warp_fix_bucket<8, true>(sp, s, lane);
       else
-        warp_fix_bucket<16>(p, s, lane);
+        warp_fix_bucket<16, true>(sp, s, lane);
     } else if (s <= 64)
-      warp_sort_bucket<2>(p, s, lane);
+      warp_sort_bucket<2, true>(sp, s, lane);
     else if (s <= 128)
-      warp_sort_bucket<4>(p, s, lane);
+      warp_sort_bucket<4, true>(sp, s, lane);
     else if (s <= 256)
-      warp_sort_bucket<8>(p, s, lane);
+      warp_sort_bucket<8, true>(sp, s, lane);
     else
-      warp_sort_bucket<16>(p, s, lane);
-    if (GATHER) {
+      warp_sort_bucket<16, true>(sp, s, lane);
+    __syncwarp();
+    if (!GATHER) {
+      for (int i = lane; i < s; i += 32) p[i] = sp[sort_at<true>(i)];
+    } else {
       // four members a lane at a time, every load issued before the stores
       // (the words are 16-byte aligned: x, z of a vertex side by side)
-      __syncwarp();
       for (int i0 = 0; i0 < s; i0 += 128) {
         int32_t f[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = i0 + 32 * u + lane;
-          f[u] = i < s ? p[i] : -1;
+          f[u] = i < s ? sp[sort_at<true>(i)] : -1;
         }
         int32_t v[4];
 #pragma unroll
@@ -238,6 +264,7 @@ __global__ void __launch_bounds__(256, 4) k_bucket_sort_warp(const int64_t* __re
         for (int u = 0; u < 4; ++u) {
           const int i = i0 + 32 * u + lane;
           if (f[u] >= 0) {
+            p[i] = f[u];
             bxz[o + i] = w[u];
             bpid[o + i] = v[u];
           }

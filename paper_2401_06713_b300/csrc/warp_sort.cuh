@@ -47,19 +47,25 @@ __device__ __forceinline__ void warp_bitonic(int32_t (&key)[E], int lane) {
   }
 }
 
-template <int E>
+// Element i of a bucket at p[i], or (PAD: a copy in shared memory with one
+// pad word every 16, so that lanes reading 16 consecutive elements each hit
+// distinct banks) at p[i + i / 16].
+template <bool PAD>
+__device__ __forceinline__ int sort_at(int i) { return PAD ? i + (i >> 4) : i; }
+
+template <int E, bool PAD = false>
 __device__ __forceinline__ void warp_sort_bucket(int32_t* __restrict__ p, int s, int lane) {
   int32_t key[E];
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const int i = lane * E + j;
-    key[j] = i < s ? p[i] : 0x7fffffff;
+    key[j] = i < s ? p[sort_at<PAD>(i)] : 0x7fffffff;
   }
   warp_bitonic<E>(key, lane);
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const int i = lane * E + j;
-    if (i < s) p[i] = key[j];
+    if (i < s) p[sort_at<PAD>(i)] = key[j];
   }
 }
 
@@ -70,14 +76,14 @@ __device__ __forceinline__ void warp_sort_bucket(int32_t* __restrict__ p, int s,
 // within a few places of their own is sorted in a few passes; after
 // kFixPasses pass pairs the bitonic network finishes whatever is left.
 constexpr int kFixPasses = 12;
-template <int E>
+template <int E, bool PAD = false>
 __device__ __forceinline__ void warp_fix_bucket(int32_t* __restrict__ p, int s, int lane) {
   static_assert(E >= 2 && (E & 1) == 0, "pairs (2i, 2i+1) must lie in one lane");
   int32_t key[E];
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const int i = lane * E + j;
-    key[j] = i < s ? p[i] : 0x7fffffff;
+    key[j] = i < s ? p[sort_at<PAD>(i)] : 0x7fffffff;
   }
   bool done = false;
   for (int it = 0; it < kFixPasses && !done; ++it) {
@@ -107,7 +113,7 @@ __device__ __forceinline__ void warp_fix_bucket(int32_t* __restrict__ p, int s, 
 #pragma unroll
   for (int j = 0; j < E; ++j) {
     const int i = lane * E + j;
-    if (i < s) p[i] = key[j];
+    if (i < s) p[sort_at<PAD>(i)] = key[j];
   }
 }
 
