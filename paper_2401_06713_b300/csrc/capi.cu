@@ -1199,10 +1199,12 @@ int color_round(Ctx* c) {
     return e;
   };
   TRYC(cudaMemsetAsync(ctl, 0, sizeof(int32_t) * kCtlWords, s));
-  TRYC(launch_iota(wa, n, s));  // the first work list: every vertex, in coloring order
-  TRYC(launch_color_init(a, c->prio, ctl, s));
   int32_t sweeps = 0;
   bool need_sweeps = c->cfg.color_algo == PICASSO_COLOR_SWEEP;
+  // the ordered pass over runs reads every vertex's starting state (priority,
+  // first candidate); the mask pass writes each vertex's final state and
+  // reads none
+  if (!c->bits && !need_sweeps) TRYC(launch_color_init(a, c->prio, ctl, s));
   if (!need_sweeps) {
     TRYC(launch_color_ordered(a, nullptr, ctl + 5, s, c->bits ? c->cfg.sched.color_blocks_per_sm : 0));
     TRYC(cudaMemcpyAsync(c->sweep_log, ctl, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, s));
@@ -1213,6 +1215,7 @@ int color_round(Ctx* c) {
   }
   if (need_sweeps) {
     TRYC(cudaMemsetAsync(ctl, 0, sizeof(int32_t) * kCtlWords, s));
+    TRYC(launch_iota(wa, n, s));  // the first work list: every vertex, in coloring order
     TRYC(launch_color_init(a, c->prio, ctl, s));
     TRYC(launch_color_all(a, wa, wb, wact, ctl, s));
     TRYC(cudaMemcpyAsync(c->sweep_log, ctl, sizeof(int32_t) * kCtlWords, cudaMemcpyDeviceToHost, s));
