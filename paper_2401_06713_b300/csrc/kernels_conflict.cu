@@ -192,13 +192,15 @@ cudaError_t launch_bucket_place(const int32_t* lists, int64_t E, int64_t P, cons
 }
 
 // Ascending order inside each bucket.  Buckets of up to 512 members: one warp
-// per bucket, a bitonic network in registers (lane l holds elements
-// l*E .. l*E+E-1, E = m/32 for the padded size m); partners closer than E
-// are in the same lane, farther ones are exchanged by shuffles.  Larger
-// buckets: one CTA per bucket, the same network in shared memory.
-// GATHER (the bit pass, buckets of at most kWarpSortMax members): the
-// same warp then writes the sorted members' words and vertex ids in slot
-// order (bxz, bpid).
+// per bucket, the keys in registers (lane l holds elements l*E .. l*E+E-1,
+// E = m/32 for the padded size m): a bitonic network (partners closer than E
+// in the same lane, farther ones exchanged by shuffles), or, with near (the
+// members were placed by ranges, so each sits within a few places of its
+// own), odd-even transposition passes that fall back to the network.
+// Larger buckets: one CTA per bucket, the network in shared memory
+// (k_bucket_sort).  GATHER (the bit pass, buckets of at most kWarpSortMax
+// members): the same warp then writes the sorted members' words and vertex
+// ids in slot order (bxz, bpid).
 template <bool GATHER>
 __global__ void __launch_bounds__(256, 4) k_bucket_sort_warp(const int64_t* __restrict__ boff, int64_t P,
                                                           int32_t* __restrict__ bmem, ConflictArgs a,
