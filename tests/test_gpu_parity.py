@@ -41,7 +41,19 @@ def test_philox_draws(pc, orc):
     assert got.tolist() == [orc.draw_u32(9, 2, 77, 1, 1000 + i) for i in range(8)]
 
 
-@pytest.mark.parametrize("q", [1, 13, 20, 48, 64])
+@pytest.mark.parametrize("q", [20, 64])
+def test_pack_other_bytes(pc, q):
+    # bytes outside 0..3 are no Pauli code: both packing kernels (q = 64 takes
+    # the 16-byte one, q = 20 the byte one) give them neither bit
+    chars = np.random.default_rng(5).integers(0, 256, (513, q), dtype=np.uint8)
+    xz = _xz(pc, chars).cpu().numpy().view(np.uint64)
+    bits = np.uint64(1) << np.arange(q, dtype=np.uint64)
+    x = (((chars == 1) | (chars == 2)).astype(np.uint64) * bits).sum(1, dtype=np.uint64)
+    z = (((chars == 3) | (chars == 2)).astype(np.uint64) * bits).sum(1, dtype=np.uint64)
+    assert np.array_equal(xz[:, 0], x) and np.array_equal(xz[:, 1], z)
+
+
+@pytest.mark.parametrize("q", [1, 13, 16, 20, 32, 48, 64])
 def test_pack_words(pc, orc, q):
     chars = synth.pauli_uniform(777, q, seed=q)
     xz = _xz(pc, chars).cpu().numpy().view(np.uint64)
